@@ -1,0 +1,1184 @@
+/*
+ * Plain FP64 CPU oracle for the non-linear cell-centred multigrid solver of
+ * Gmunu (Cheong et al.): FAS V-cycles with red-black Newton-Gauss-Seidel
+ * smoothing, piecewise-constant restriction and Kwak prolongation, applied to
+ * the xCFC metric equations and to elliptic divergence cleaning.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is slow and literal on purpose: every
+ * cell update is written as a loop over cells in the order the paper states.
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load it.  It shares no code, header, table or constant generator with the
+ * CUDA library; both sides receive the same input arrays and nothing else.
+ *
+ * Paper passages followed (section / equation of arXiv:2012.07322):
+ *   Sec. 2.6, eqs. (X), (psi), (alpha), (beta), (Aij)  -- xCFC equations
+ *   Sec. 2.6, eqs. (bc), (robin)                       -- outer boundary
+ *   Sec. 2.7.1, eq. (elliptic_op) and the Laplacians    -- discretisation
+ *   Sec. 2.7.1, first / second / mixed derivatives      -- incl. block-corner
+ *   Sec. 2.7.2, eq. (ngs_iteration), red-black ordering -- smoother
+ *   Sec. 2.7.3, Kwak prolongation, piecewise-constant restriction
+ *   Sec. 2.2, eqs. (poisson), (update_bfield)           -- div-B cleaning
+ *   Sec. 5.2 (MG performance): V-cycles with 2+2 red-black smoothing steps.
+ *
+ * Readings where the paper is silent or garbled (each listed in the design
+ * notes of the repository):
+ *   - the cylindrical and spherical Laplacians print "u_{j+1} - 2u - u_{j-1}";
+ *     the consistent second difference "+ u_{j-1}" is used;
+ *   - cells are coloured by (i+j+k) mod 2 with 0-based indices, even first;
+ *   - vector equations are smoothed component by component inside a colour
+ *     (all cells of the colour for component 0, then 1, then 2);
+ *   - ghosts of a field are recomputed from its interior before every colour
+ *     (or component) pass; the Newton diagonal treats them as fixed;
+ *   - Cartesian / cylindrical Robin ghosts: g = u_N * rho(x_N) / rho(x_G),
+ *     rho the distance from the origin, which satisfies delta + x.grad delta
+ *     = 0 exactly for delta ~ 1/rho;
+ *   - restriction averages the children weighted by their cell volumes
+ *     (Appendix A); on Cartesian grids that is the printed equal-weight
+ *     stencil;
+ *   - FAS coarse-grid sources are restrictions of the fine sources; coarse
+ *     operators are rediscretised;
+ *   - coarsest grid: Newton-Gauss-Seidel sweeps until its residual falls by
+ *     1e-12 or 100 sweeps;
+ *   - stopping rule: rel = max|w r| / max|w S(u)|, w = r^2 sin(theta)
+ *     (spherical), R (cylindrical), 1 (Cartesian).
+ *
+ * Layout of every ghosted array: one ghost layer in each active dimension,
+ * index (i, j, k) with i in [-1, n0], j in [-1, n1], k in [-1, n2] (3D) or
+ * k = 0 (2D), dimension 0 fastest.
+ */
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+enum { GEOM_CART = 0, GEOM_CYL = 1, GEOM_SPH = 2 };
+enum { BC_ROBIN = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2 };
+enum { EQ_PSI = 0, EQ_LIN = 1, EQ_VEC = 2 };
+enum { MIX_4PT = 0, MIX_CORNER = 1 };
+#define OR_MAX_LEVELS 16
+#define OR_HIST 1024
+
+/* ------------------------------------------------------------------ grid */
+
+typedef struct {
+  int ndim, geom;
+  int n[3];
+  int gz;             /* ghost width in dimension 2: 1 in 3D, 0 in 2D */
+  long s1, s2;        /* strides of dimensions 1 and 2 */
+  long size;          /* ghosted cell count */
+  double lo[3], h[3];
+} OGrid;
+
+static long IX(const OGrid* g, int i, int j, int k) {
+  return (long)(i + 1) + (long)(j + 1) * g->s1 + (long)(k + g->gz) * g->s2;
+}
+
+/* Cell-centre coordinate of index i (ghosts included) in dimension d. */
+static double xc(const OGrid* g, int d, int i) { return g->lo[d] + (i + 0.5) * g->h[d]; }
+/* Face coordinate x_{i-1/2} in dimension d. */
+static double xf(const OGrid* g, int d, int i) { return g->lo[d] + i * g->h[d]; }
+
+static void grid_init(OGrid* g, int ndim, int geom, const int n[3], const double lo[3],
+                      const double h[3]) {
+  memset(g, 0, sizeof(*g));
+  g->ndim = ndim;
+  g->geom = geom;
+  for (int d = 0; d < 3; ++d) {
+    g->n[d] = (d < ndim) ? n[d] : 1;
+    g->lo[d] = (d < ndim) ? lo[d] : 0.0;
+    g->h[d] = (d < ndim) ? h[d] : 1.0;
+  }
+  g->gz = (ndim == 3) ? 1 : 0;
+  g->s1 = g->n[0] + 2;
+  g->s2 = g->s1 * (g->n[1] + 2);
+  g->size = g->s2 * (g->n[2] + 2 * g->gz);
+}
+
+/* sin(theta) at a theta face; exactly zero on the two poles (Sec. 2.7.1:
+ * the flux through a pole vanishes). */
+static double sin_face(const OGrid* g, int j) {
+  if (j == 0 || j == g->n[1]) return 0.0;
+  return sin(xf(g, 1, j));
+}
+
+/* --------------------------------------------------------- ghost filling */
+
+/* Parity of a component under the reflections through the origin / axis
+ * (regularity of physical vector components; comp = -1 is a scalar). */
+static double parity_origin(int geom, int comp) {
+  if (comp < 0) return 1.0;
+  if (geom == GEOM_SPH) return (comp == 1) ? 1.0 : -1.0;   /* V_r -, V_th +, V_ph - */
+  if (geom == GEOM_CYL) return (comp == 1) ? 1.0 : -1.0;   /* V_R -, V_z +, V_ph - */
+  return 1.0;
+}
+static double parity_axis(int comp) {                        /* spherical theta = 0, pi */
+  if (comp < 0) return 1.0;
+  return (comp == 0) ? 1.0 : -1.0;                           /* V_r +, V_th -, V_ph - */
+}
+
+/* Distance from the origin of a cell centre (Cartesian / cylindrical Robin). */
+static double rho_of(const OGrid* g, int i, int j, int k) {
+  double x = xc(g, 0, i), y = xc(g, 1, j);
+  if (g->geom == GEOM_CART) {
+    double z = (g->ndim == 3) ? xc(g, 2, k) : 0.0;
+    return sqrt(x * x + y * y + z * z);
+  }
+  return sqrt(x * x + y * y);                                /* (R, z) */
+}
+
+/* Outer-boundary ghost: 'gi,gj,gk' is the ghost, 'si,sj,sk' the interior
+ * (or previously filled) cell across the face. */
+static double outer_ghost(const OGrid* g, const double* u, int bc, int d, int gi, int gj, int gk,
+                          int si, int sj, int sk) {
+  double us = u[IX(g, si, sj, sk)];
+  if (bc == BC_DIRICHLET) return -us;                        /* face value zero */
+  if (bc == BC_NEUMANN) return us;                           /* zero normal gradient */
+  /* Robin d(r delta)/dr = 0, eq. (robin) */
+  if (g->geom == GEOM_SPH) {
+    (void)d;
+    return us * xc(g, 0, si) / xc(g, 0, gi);
+  }
+  return us * rho_of(g, si, sj, sk) / rho_of(g, gi, gj, gk);
+}
+
+/* Fill every ghost of one field.  Dimensions are filled in the order 0, 1,
+ * 2, each over the index range already extended by the earlier ones, so
+ * edge and corner ghosts are defined. */
+static void fill_ghosts(const OGrid* g, double* u, int bc, int comp) {
+  const int n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
+  const int three = (g->ndim == 3);
+  /* dimension 0 */
+  for (int k = 0; k < n2; ++k)
+    for (int j = 0; j < n1; ++j) {
+      /* low side */
+      if (g->geom == GEOM_CART) {
+        u[IX(g, -1, j, k)] = outer_ghost(g, u, bc, 0, -1, j, k, 0, j, k);
+      } else if (g->geom == GEOM_CYL) {
+        int ks = three ? (k + n2 / 2) % n2 : k;
+        u[IX(g, -1, j, k)] = parity_origin(GEOM_CYL, comp) * u[IX(g, 0, j, ks)];
+      } else {
+        int ks = three ? (k + n2 / 2) % n2 : k;
+        u[IX(g, -1, j, k)] = parity_origin(GEOM_SPH, comp) * u[IX(g, 0, n1 - 1 - j, ks)];
+      }
+      /* high side: always the outer boundary */
+      u[IX(g, n0, j, k)] = outer_ghost(g, u, bc, 0, n0, j, k, n0 - 1, j, k);
+    }
+  /* dimension 1 */
+  for (int k = 0; k < n2; ++k)
+    for (int i = -1; i <= n0; ++i) {
+      if (g->geom == GEOM_SPH) {
+        int ks = three ? (k + n2 / 2) % n2 : k;
+        u[IX(g, i, -1, k)] = parity_axis(comp) * u[IX(g, i, 0, ks)];
+        u[IX(g, i, n1, k)] = parity_axis(comp) * u[IX(g, i, n1 - 1, ks)];
+      } else {
+        u[IX(g, i, -1, k)] = outer_ghost(g, u, bc, 1, i, -1, k, i, 0, k);
+        u[IX(g, i, n1, k)] = outer_ghost(g, u, bc, 1, i, n1, k, i, n1 - 1, k);
+      }
+    }
+  /* dimension 2 */
+  if (three)
+    for (int j = -1; j <= n1; ++j)
+      for (int i = -1; i <= n0; ++i) {
+        if (g->geom == GEOM_CART) {
+          u[IX(g, i, j, -1)] = outer_ghost(g, u, bc, 2, i, j, -1, i, j, 0);
+          u[IX(g, i, j, n2)] = outer_ghost(g, u, bc, 2, i, j, n2, i, j, n2 - 1);
+        } else {                                             /* periodic phi */
+          u[IX(g, i, j, -1)] = u[IX(g, i, j, n2 - 1)];
+          u[IX(g, i, j, n2)] = u[IX(g, i, j, 0)];
+        }
+      }
+}
+
+/* ----------------------------------------------------- discrete operators */
+
+/* Scalar Laplacian in flux form (Sec. 2.7.1). */
+static double lap(const OGrid* g, const double* u, int i, int j, int k) {
+  const double uc = u[IX(g, i, j, k)];
+  const double ue = u[IX(g, i + 1, j, k)], uw = u[IX(g, i - 1, j, k)];
+  const double un = u[IX(g, i, j + 1, k)], us = u[IX(g, i, j - 1, k)];
+  const double h0 = g->h[0], h1 = g->h[1], h2 = g->h[2];
+  double L;
+  if (g->geom == GEOM_CART) {
+    L = (ue - 2.0 * uc + uw) / (h0 * h0) + (un - 2.0 * uc + us) / (h1 * h1);
+    if (g->ndim == 3) L += (u[IX(g, i, j, k + 1)] - 2.0 * uc + u[IX(g, i, j, k - 1)]) / (h2 * h2);
+  } else if (g->geom == GEOM_CYL) {
+    const double R = xc(g, 0, i), Rp = xf(g, 0, i + 1), Rm = xf(g, 0, i);
+    L = (Rp * (ue - uc) / h0 - Rm * (uc - uw) / h0) / (R * h0) + (un - 2.0 * uc + us) / (h1 * h1);
+    if (g->ndim == 3)
+      L += (u[IX(g, i, j, k + 1)] - 2.0 * uc + u[IX(g, i, j, k - 1)]) / (R * R * h2 * h2);
+  } else {
+    const double r = xc(g, 0, i), rp = xf(g, 0, i + 1), rm = xf(g, 0, i);
+    const double st = sin(xc(g, 1, j)), sp = sin_face(g, j + 1), sm = sin_face(g, j);
+    L = (rp * rp * (ue - uc) / h0 - rm * rm * (uc - uw) / h0) / (r * r * h0) +
+        (sp * (un - uc) / h1 - sm * (uc - us) / h1) / (r * r * st * h1);
+    if (g->ndim == 3)
+      L += (u[IX(g, i, j, k + 1)] - 2.0 * uc + u[IX(g, i, j, k - 1)]) / (r * r * st * st * h2 * h2);
+  }
+  return L;
+}
+
+/* d(lap u)/d(u_ijk) with the neighbours (ghosts included) held fixed. */
+static double lap_diag(const OGrid* g, int i, int j, int k) {
+  (void)k;
+  const double h0 = g->h[0], h1 = g->h[1], h2 = g->h[2];
+  double D;
+  if (g->geom == GEOM_CART) {
+    D = -2.0 / (h0 * h0) - 2.0 / (h1 * h1);
+    if (g->ndim == 3) D += -2.0 / (h2 * h2);
+  } else if (g->geom == GEOM_CYL) {
+    const double R = xc(g, 0, i), Rp = xf(g, 0, i + 1), Rm = xf(g, 0, i);
+    D = -(Rp + Rm) / (R * h0 * h0) - 2.0 / (h1 * h1);
+    if (g->ndim == 3) D += -2.0 / (R * R * h2 * h2);
+  } else {
+    const double r = xc(g, 0, i), rp = xf(g, 0, i + 1), rm = xf(g, 0, i);
+    const double st = sin(xc(g, 1, j)), sp = sin_face(g, j + 1), sm = sin_face(g, j);
+    D = -(rp * rp + rm * rm) / (r * r * h0 * h0) - (sp + sm) / (r * r * st * h1 * h1);
+    if (g->ndim == 3) D += -2.0 / (r * r * st * st * h2 * h2);
+  }
+  return D;
+}
+
+/* Central first derivative along dimension d (Sec. 2.7.1); zero along a
+ * dimension the grid does not have (axisymmetry / translation invariance). */
+static double d1(const OGrid* g, const double* u, int d, int i, int j, int k) {
+  if (d >= g->ndim) return 0.0;
+  int di = (d == 0), dj = (d == 1), dk = (d == 2);
+  return (u[IX(g, i + di, j + dj, k + dk)] - u[IX(g, i - di, j - dj, k - dk)]) / (2.0 * g->h[d]);
+}
+/* Compact second derivative along d. */
+static double d2(const OGrid* g, const double* u, int d, int i, int j, int k) {
+  if (d >= g->ndim) return 0.0;
+  int di = (d == 0), dj = (d == 1), dk = (d == 2);
+  return (u[IX(g, i + di, j + dj, k + dk)] - 2.0 * u[IX(g, i, j, k)] +
+          u[IX(g, i - di, j - dj, k - dk)]) / (g->h[d] * g->h[d]);
+}
+/* Mixed second derivative along dimensions a < b: the four-corner stencil,
+ * or the block-corner stencil of Sec. 2.7.1 which avoids one diagonal pair. */
+static double dmix(const OGrid* g, const double* u, int a, int b, int mixed, int i, int j, int k) {
+  if (a >= g->ndim || b >= g->ndim) return 0.0;
+  int ai = (a == 0), aj = (a == 1), ak = (a == 2);
+  int bi = (b == 0), bj = (b == 1), bk = (b == 2);
+#define U_(p, q) u[IX(g, i + (p) * ai + (q) * bi, j + (p) * aj + (q) * bj, k + (p) * ak + (q) * bk)]
+  if (mixed == MIX_4PT)
+    return (U_(1, 1) - U_(1, -1) - U_(-1, 1) + U_(-1, -1)) / (4.0 * g->h[a] * g->h[b]);
+  return (-U_(1, -1) - U_(-1, 1) + U_(1, 0) + U_(-1, 0) + U_(0, 1) + U_(0, -1) - 2.0 * U_(0, 0)) /
+         (2.0 * g->h[a] * g->h[b]);
+#undef U_
+}
+
+/* Vector operator lap V + (1/3) grad div V, physical component c, at a cell;
+ * eqs. (X) and (beta) written out in orthonormal components of the flat
+ * reference metric (Appendix A gives its Christoffel symbols). */
+static double vec_op(const OGrid* g, double* const V[3], int c, int mixed, int i, int j, int k) {
+  const double *A = V[0], *B = V[1], *C = V[2];
+  const double third = 1.0 / 3.0;
+  if (g->geom == GEOM_CART) {
+    double gd;   /* d_c (div V) */
+    if (c == 0)
+      gd = d2(g, A, 0, i, j, k) + dmix(g, B, 0, 1, mixed, i, j, k) + dmix(g, C, 0, 2, mixed, i, j, k);
+    else if (c == 1)
+      gd = dmix(g, A, 0, 1, mixed, i, j, k) + d2(g, B, 1, i, j, k) + dmix(g, C, 1, 2, mixed, i, j, k);
+    else
+      gd = dmix(g, A, 0, 2, mixed, i, j, k) + dmix(g, B, 1, 2, mixed, i, j, k) + d2(g, C, 2, i, j, k);
+    return lap(g, V[c], i, j, k) + third * gd;
+  }
+  if (g->geom == GEOM_CYL) {   /* components (R, z, phi) */
+    const double R = xc(g, 0, i);
+    if (c == 0) {
+      double vl = lap(g, A, i, j, k) - A[IX(g, i, j, k)] / (R * R) - 2.0 / (R * R) * d1(g, C, 2, i, j, k);
+      double gd = d2(g, A, 0, i, j, k) + d1(g, A, 0, i, j, k) / R - A[IX(g, i, j, k)] / (R * R) +
+                  dmix(g, B, 0, 1, mixed, i, j, k) + dmix(g, C, 0, 2, mixed, i, j, k) / R -
+                  d1(g, C, 2, i, j, k) / (R * R);
+      return vl + third * gd;
+    } else if (c == 1) {
+      double vl = lap(g, B, i, j, k);
+      double gd = dmix(g, A, 0, 1, mixed, i, j, k) + d1(g, A, 1, i, j, k) / R + d2(g, B, 1, i, j, k) +
+                  dmix(g, C, 1, 2, mixed, i, j, k) / R;
+      return vl + third * gd;
+    } else {
+      double vl = lap(g, C, i, j, k) - C[IX(g, i, j, k)] / (R * R) + 2.0 / (R * R) * d1(g, A, 2, i, j, k);
+      double gd = dmix(g, A, 0, 2, mixed, i, j, k) / R + d1(g, A, 2, i, j, k) / (R * R) +
+                  dmix(g, B, 1, 2, mixed, i, j, k) / R + d2(g, C, 2, i, j, k) / (R * R);
+      return vl + third * gd;
+    }
+  }
+  /* spherical, components (r, theta, phi) */
+  const double r = xc(g, 0, i), th = xc(g, 1, j);
+  const double st = sin(th), ct = cos(th), cot = ct / st;
+  const double r2 = r * r, st2 = st * st;
+  if (c == 0) {
+    double vl = lap(g, A, i, j, k) - 2.0 * A[IX(g, i, j, k)] / r2 - 2.0 / r2 * d1(g, B, 1, i, j, k) -
+                2.0 * cot / r2 * B[IX(g, i, j, k)] - 2.0 / (r2 * st) * d1(g, C, 2, i, j, k);
+    double gd = d2(g, A, 0, i, j, k) + 2.0 / r * d1(g, A, 0, i, j, k) - 2.0 * A[IX(g, i, j, k)] / r2 +
+                dmix(g, B, 0, 1, mixed, i, j, k) / r - d1(g, B, 1, i, j, k) / r2 +
+                cot / r * d1(g, B, 0, i, j, k) - cot / r2 * B[IX(g, i, j, k)] +
+                dmix(g, C, 0, 2, mixed, i, j, k) / (r * st) - d1(g, C, 2, i, j, k) / (r2 * st);
+    return vl + third * gd;
+  } else if (c == 1) {
+    double vl = lap(g, B, i, j, k) - B[IX(g, i, j, k)] / (r2 * st2) + 2.0 / r2 * d1(g, A, 1, i, j, k) -
+                2.0 * ct / (r2 * st2) * d1(g, C, 2, i, j, k);
+    double gd = dmix(g, A, 0, 1, mixed, i, j, k) / r + 2.0 / r2 * d1(g, A, 1, i, j, k) +
+                d2(g, B, 1, i, j, k) / r2 + cot / r2 * d1(g, B, 1, i, j, k) -
+                B[IX(g, i, j, k)] / (r2 * st2) - ct / (r2 * st2) * d1(g, C, 2, i, j, k) +
+                dmix(g, C, 1, 2, mixed, i, j, k) / (r2 * st);
+    return vl + third * gd;
+  } else {
+    double vl = lap(g, C, i, j, k) - C[IX(g, i, j, k)] / (r2 * st2) +
+                2.0 / (r2 * st) * d1(g, A, 2, i, j, k) + 2.0 * ct / (r2 * st2) * d1(g, B, 2, i, j, k);
+    double gd = dmix(g, A, 0, 2, mixed, i, j, k) / (r * st) + 2.0 / (r2 * st) * d1(g, A, 2, i, j, k) +
+                dmix(g, B, 1, 2, mixed, i, j, k) / (r2 * st) + cot / (r2 * st) * d1(g, B, 2, i, j, k) +
+                d2(g, C, 2, i, j, k) / (r2 * st2);
+    return vl + third * gd;
+  }
+}
+
+/* d(vec_op_c)/d(V_c at the cell), neighbours held fixed. */
+static double vec_diag(const OGrid* g, int c, int i, int j, int k) {
+  const double third = 1.0 / 3.0;
+  const double D = lap_diag(g, i, j, k);
+  const double h0 = g->h[0], h1 = g->h[1], h2 = g->h[2];
+  const int three = (g->ndim == 3);
+  if (g->geom == GEOM_CART) {
+    if (c < g->ndim) return D + third * (-2.0 / (g->h[c] * g->h[c]));
+    return D;
+  }
+  if (g->geom == GEOM_CYL) {
+    const double R = xc(g, 0, i);
+    if (c == 0) return D - 1.0 / (R * R) + third * (-2.0 / (h0 * h0) - 1.0 / (R * R));
+    if (c == 1) return D + third * (-2.0 / (h1 * h1));
+    return D - 1.0 / (R * R) + (three ? third * (-2.0 / (R * R * h2 * h2)) : 0.0);
+  }
+  const double r = xc(g, 0, i), st = sin(xc(g, 1, j));
+  const double r2 = r * r, st2 = st * st;
+  if (c == 0) return D - 2.0 / r2 + third * (-2.0 / (h0 * h0) - 2.0 / r2);
+  if (c == 1) return D - 1.0 / (r2 * st2) + third * (-2.0 / (r2 * h1 * h1) - 1.0 / (r2 * st2));
+  return D - 1.0 / (r2 * st2) + (three ? third * (-2.0 / (r2 * st2 * h2 * h2)) : 0.0);
+}
+
+/* Weight of the stopping norm: the flux-form (volume) weight of a cell. */
+static double norm_weight(const OGrid* g, int i, int j) {
+  if (g->geom == GEOM_SPH) {
+    double r = xc(g, 0, i);
+    return r * r * sin(xc(g, 1, j));
+  }
+  if (g->geom == GEOM_CYL) return xc(g, 0, i);
+  return 1.0;
+}
+
+/* ------------------------------------------------------------ equations */
+
+/* One level of the hierarchy with the arrays an equation needs. */
+typedef struct {
+  OGrid g;
+  double* u[3];    /* unknown (deviation form for psi / alpha*psi) */
+  double* uh[3];   /* restricted fine solution, kept for the FAS correction */
+  double* f[3];    /* right-hand side f of L(u) = f */
+  double* r[3];    /* residual / scratch */
+  double* U;       /* psi equation: conformal energy density U~ */
+  double* A2;      /* psi equation: A~_ij A~^ij */
+  double* c;       /* linear equations: coefficient of u in L(u) = lap u - c u */
+} OLevel;
+
+typedef struct {
+  int kind, bc, ncomp, mixed, zero_mean;
+  int nu1, nu2, max_cycles, stall_window;
+  double tol;
+  int nlev;
+  OLevel lev[OR_MAX_LEVELS];
+} OSolver;
+
+/* The operator L(u) at a cell for component c (eq. elliptic_op), and its
+ * derivative with respect to the cell's own value for the Newton step.
+ *   EQ_PSI : L(u) = lap u + 2 pi U (1+u)^-1 + (1/8) A2 (1+u)^-7      (eq. psi)
+ *   EQ_LIN : L(u) = lap u - c u                 (eq. alpha; Poisson if c = 0)
+ *   EQ_VEC : L(V) = lap V + (1/3) grad div V                (eqs. X, beta) */
+static double op_at(const OSolver* s, const OLevel* L, int c, int i, int j, int k, double* diag) {
+  const OGrid* g = &L->g;
+  long p = IX(g, i, j, k);
+  if (s->kind == EQ_VEC) {
+    if (diag) *diag = vec_diag(g, c, i, j, k);
+    return vec_op(g, (double* const*)L->u, c, s->mixed, i, j, k);
+  }
+  double lu = lap(g, L->u[0], i, j, k);
+  double D = lap_diag(g, i, j, k);
+  if (s->kind == EQ_PSI) {
+    double psi = 1.0 + L->u[0][p];
+    double val = lu + 2.0 * OR_PI * L->U[p] / psi + 0.125 * L->A2[p] / pow(psi, 7);
+    if (diag) *diag = D - 2.0 * OR_PI * L->U[p] / (psi * psi) - 0.875 * L->A2[p] / pow(psi, 8);
+    return val;
+  }
+  double cc = L->c ? L->c[p] : 0.0;
+  if (diag) *diag = D - cc;
+  return lu - cc * L->u[0][p];
+}
+
+/* The source S(u) of the equation as the paper writes it (right-hand side of
+ * eqs. psi / alpha / X / beta / poisson), used to normalise the residual. */
+static double source_at(const OSolver* s, const OLevel* L, int c, long p) {
+  if (s->kind == EQ_PSI) {
+    double psi = 1.0 + L->u[0][p];
+    return -2.0 * OR_PI * L->U[p] / psi - 0.125 * L->A2[p] / pow(psi, 7);
+  }
+  if (s->kind == EQ_LIN) return (L->c ? L->c[p] * L->u[0][p] : 0.0) + L->f[0][p];
+  return L->f[c][p];
+}
+
+static int comp_of(const OSolver* s, int c) { return s->kind == EQ_VEC ? c : -1; }
+
+static void fill_all(const OSolver* s, OLevel* L) {
+  for (int c = 0; c < s->ncomp; ++c) fill_ghosts(&L->g, L->u[c], s->bc, comp_of(s, c));
+}
+
+/* One red-black Newton-Gauss-Seidel sweep, eq. (ngs_iteration): cells with
+ * (i+j+k) even first, then odd.  Vector equations take the components one
+ * after another inside each colour. */
+static void smooth_sweep(const OSolver* s, OLevel* L) {
+  const OGrid* g = &L->g;
+  for (int colour = 0; colour < 2; ++colour)
+    for (int c = 0; c < s->ncomp; ++c) {
+      fill_all(s, L);
+#pragma omp parallel for collapse(2) schedule(static)
+      for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+          for (int i = 0; i < g->n[0]; ++i) {
+            if (((i + j + k) & 1) != colour) continue;
+            double diag;
+            double Lu = op_at(s, L, c, i, j, k, &diag);
+            long p = IX(g, i, j, k);
+            L->u[c][p] = L->u[c][p] - (Lu - L->f[c][p]) / diag;
+          }
+    }
+}
+
+/* r = f - L(u) on the interior; returns max |r| (unweighted). */
+static double residual(const OSolver* s, OLevel* L) {
+  const OGrid* g = &L->g;
+  double m = 0.0;
+  fill_all(s, L);
+  for (int c = 0; c < s->ncomp; ++c)
+#pragma omp parallel for collapse(2) reduction(max : m) schedule(static)
+    for (int k = 0; k < g->n[2]; ++k)
+      for (int j = 0; j < g->n[1]; ++j)
+        for (int i = 0; i < g->n[0]; ++i) {
+          long p = IX(g, i, j, k);
+          L->r[c][p] = L->f[c][p] - op_at(s, L, c, i, j, k, NULL);
+          double a = fabs(L->r[c][p]);
+          if (a > m || a != a) m = (a != a) ? INFINITY : a;
+        }
+  return m;
+}
+
+/* Relative weighted residual of the finest level: the stopping rule. */
+static double rel_residual(const OSolver* s, OLevel* L) {
+  const OGrid* g = &L->g;
+  residual(s, L);
+  double num = 0.0, den = 0.0;
+  int bad = 0;
+  for (int c = 0; c < s->ncomp; ++c)
+    for (int k = 0; k < g->n[2]; ++k)
+      for (int j = 0; j < g->n[1]; ++j)
+        for (int i = 0; i < g->n[0]; ++i) {
+          long p = IX(g, i, j, k);
+          double w = norm_weight(g, i, j);
+          double a = fabs(w * L->r[c][p]), b = fabs(w * source_at(s, L, c, p));
+          if (!(a == a) || !(b == b) || isinf(a) || isinf(b)) bad = 1;
+          if (a > num) num = a;
+          if (b > den) den = b;
+        }
+  if (bad) return NAN;
+  return num / (den > 1e-300 ? den : 1e-300);
+}
+
+/* Cell volume Delta V of Appendix A (cylindrical and spherical; Cartesian
+ * cells all have the same volume).  Only ratios between the children of one
+ * coarse cell are used, so the factors the children share are dropped. */
+static double cell_volume(const OGrid* g, int i, int j) {
+  if (g->geom == GEOM_SPH) {
+    double r = xc(g, 0, i), dr = g->h[0];
+    return (r * r + dr * dr / 12.0) * dr * 2.0 * sin(xc(g, 1, j)) * sin(0.5 * g->h[1]);
+  }
+  if (g->geom == GEOM_CYL) return xc(g, 0, i) * g->h[0];
+  return 1.0;
+}
+
+/* Piecewise-constant restriction (Sec. 2.7.3, Fig. pc): the coarse value is
+ * the average of its 2^d children.  On Cartesian grids this is the printed
+ * 1/4 (2D) or 1/8 (3D) stencil; on curvilinear grids the children are
+ * weighted by their volumes, which keeps the restriction conservative (with
+ * equal weights the V-cycle diverges next to the spherical origin). */
+static void restrict_field(const OGrid* gf, const double* uf, const OGrid* gc, double* uc) {
+  const int three = (gc->ndim == 3);
+  for (int K = 0; K < gc->n[2]; ++K)
+    for (int J = 0; J < gc->n[1]; ++J)
+      for (int I = 0; I < gc->n[0]; ++I) {
+        double sum = 0.0, vol = 0.0;
+        for (int dk = 0; dk <= three; ++dk)
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+              double v = cell_volume(gf, 2 * I + di, 2 * J + dj);
+              sum += v * uf[IX(gf, 2 * I + di, 2 * J + dj, three ? 2 * K + dk : 0)];
+              vol += v;
+            }
+        uc[IX(gc, I, J, K)] = sum / vol;
+      }
+}
+
+/* Kwak prolongation (Sec. 2.7.3, Fig. kwak) of a coarse correction e (with
+ * ghosts filled), added into the fine field.  Each fine cell takes its parent
+ * and, per dimension, the parent's neighbour on the fine cell's side:
+ * 2D 1/4 (2 e_c + e_x + e_y), 3D 1/4 (e_c + e_x + e_y + e_z). */
+static void prolong_add(const OGrid* gf, double* uf, const OGrid* gc, const double* e) {
+  const int three = (gf->ndim == 3);
+  for (int k = 0; k < gf->n[2]; ++k)
+    for (int j = 0; j < gf->n[1]; ++j)
+      for (int i = 0; i < gf->n[0]; ++i) {
+        int I = i / 2, J = j / 2, K = three ? k / 2 : 0;
+        int si = (i % 2 == 0) ? -1 : 1, sj = (j % 2 == 0) ? -1 : 1, sk = (k % 2 == 0) ? -1 : 1;
+        double ec = e[IX(gc, I, J, K)];
+        double ex = e[IX(gc, I + si, J, K)], ey = e[IX(gc, I, J + sj, K)];
+        double add;
+        if (three)
+          add = 0.25 * (ec + ex + ey + e[IX(gc, I, J, K + sk)]);
+        else
+          add = 0.25 * (2.0 * ec + ex + ey);
+        uf[IX(gf, i, j, k)] += add;
+      }
+}
+
+static double interior_mean(const OGrid* g, const double* u) {
+  double sum = 0.0;
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i) sum += u[IX(g, i, j, k)];
+  return sum / ((double)g->n[0] * g->n[1] * g->n[2]);
+}
+
+/* Newton-Gauss-Seidel on the coarsest grid used as the direct solver
+ * (Sec. 2.7.2): sweeps until the residual drops by 1e-12 or 100 sweeps. */
+static void coarse_solve(const OSolver* s, OLevel* L) {
+  double r0 = residual(s, L);
+  if (r0 == 0.0) return;
+  for (int it = 0; it < 100; ++it) {
+    smooth_sweep(s, L);
+    double r = residual(s, L);
+    if (r <= 1e-12 * r0) break;
+  }
+}
+
+/* FAS V(nu1, nu2) cycle (the paper cites the FAS scheme of Cheong et al.):
+ *   pre-smooth; r = f - L(u); u_H = R u, uh_H = u_H; f_H = L_H(u_H) + R r;
+ *   recurse; u += P(u_H - uh_H); post-smooth. */
+static void vcycle(const OSolver* s, OSolver* sm, int l) {
+  OLevel* L = &sm->lev[l];
+  if (l == s->nlev - 1) {
+    coarse_solve(s, L);
+    return;
+  }
+  OLevel* C = &sm->lev[l + 1];
+  for (int it = 0; it < s->nu1; ++it) smooth_sweep(s, L);
+  residual(s, L);
+  for (int c = 0; c < s->ncomp; ++c) {
+    restrict_field(&L->g, L->u[c], &C->g, C->u[c]);
+    memcpy(C->uh[c], C->u[c], sizeof(double) * C->g.size);
+    restrict_field(&L->g, L->r[c], &C->g, C->r[c]);
+  }
+  fill_all(s, C);
+  for (int c = 0; c < s->ncomp; ++c)
+    for (int k = 0; k < C->g.n[2]; ++k)
+      for (int j = 0; j < C->g.n[1]; ++j)
+        for (int i = 0; i < C->g.n[0]; ++i) {
+          long p = IX(&C->g, i, j, k);
+          C->f[c][p] = op_at(s, C, c, i, j, k, NULL) + C->r[c][p];
+        }
+  vcycle(s, sm, l + 1);
+  for (int c = 0; c < s->ncomp; ++c) {
+    /* coarse correction e = u_H - uh_H with homogeneous boundary ghosts */
+    double* e = C->r[c];
+    for (long p = 0; p < C->g.size; ++p) e[p] = C->u[c][p] - C->uh[c][p];
+    fill_ghosts(&C->g, e, s->bc, comp_of(s, c));
+    prolong_add(&L->g, L->u[c], &C->g, e);
+  }
+  for (int it = 0; it < s->nu2; ++it) smooth_sweep(s, L);
+}
+
+/* ------------------------------------------------------------- hierarchy */
+
+static int build_levels(OSolver* s, int ndim, int geom, const int n[3], const double lo[3],
+                        const double hi[3]) {
+  int m[3] = {n[0], ndim > 1 ? n[1] : 1, ndim > 2 ? n[2] : 1};
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (d < ndim) ? (hi[d] - lo[d]) / m[d] : 1.0;
+  int nl = 0;
+  for (;;) {
+    OLevel* L = &s->lev[nl];
+    memset(L, 0, sizeof(*L));
+    grid_init(&L->g, ndim, geom, m, lo, h);
+    long sz = L->g.size;
+    for (int c = 0; c < 3; ++c) {
+      L->u[c] = calloc(sz, sizeof(double));
+      L->uh[c] = calloc(sz, sizeof(double));
+      L->f[c] = calloc(sz, sizeof(double));
+      L->r[c] = calloc(sz, sizeof(double));
+    }
+    L->U = calloc(sz, sizeof(double));
+    L->A2 = calloc(sz, sizeof(double));
+    L->c = calloc(sz, sizeof(double));
+    ++nl;
+    /* halve while every dimension is even and at least 4 */
+    int ok = (nl < OR_MAX_LEVELS);
+    for (int d = 0; d < ndim; ++d)
+      if (m[d] < 4 || m[d] % 2) ok = 0;
+    if (!ok) break;
+    for (int d = 0; d < ndim; ++d) {
+      m[d] /= 2;
+      h[d] *= 2.0;
+    }
+  }
+  s->nlev = nl;
+  return nl;
+}
+
+static void free_levels(OSolver* s) {
+  for (int l = 0; l < s->nlev; ++l) {
+    OLevel* L = &s->lev[l];
+    for (int c = 0; c < 3; ++c) {
+      free(L->u[c]);
+      free(L->uh[c]);
+      free(L->f[c]);
+      free(L->r[c]);
+    }
+    free(L->U);
+    free(L->A2);
+    free(L->c);
+  }
+  s->nlev = 0;
+}
+
+/* Interior (ghost-free, dimension 0 fastest) <-> ghosted copies. */
+static void load_interior(const OGrid* g, double* dst, const double* src) {
+  long q = 0;
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i) dst[IX(g, i, j, k)] = src[q++];
+}
+static void store_interior(const OGrid* g, double* dst, const double* src) {
+  long q = 0;
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i) dst[q++] = src[IX(g, i, j, k)];
+}
+
+/* ------------------------------------------------------------ public API */
+
+typedef struct {
+  int ndim, geom;
+  int n[3];
+  double lo[3], hi[3];
+  int nu1, nu2, max_cycles;
+  double tol;
+  int mixed;
+  int stall_window;   /* cycles over which a 5 % gain is required; 0: off */
+} or_desc;
+
+typedef struct {
+  int status;      /* 0 ok, 3 not converged, 4 stalled, 5 non-finite */
+  int cycles;
+  double rel;      /* final relative weighted residual */
+  int nhist;
+  double hist[OR_HIST];
+} or_report;
+
+/* Restrict the equation's sources down the hierarchy. */
+static void restrict_sources(OSolver* s) {
+  for (int l = 1; l < s->nlev; ++l) {
+    OLevel *F = &s->lev[l - 1], *C = &s->lev[l];
+    restrict_field(&F->g, F->U, &C->g, C->U);
+    restrict_field(&F->g, F->A2, &C->g, C->A2);
+    restrict_field(&F->g, F->c, &C->g, C->c);
+  }
+}
+
+/* Cycle control: V-cycles until rel <= tol, max_cycles (not converged),
+ * no 5 % gain over stall_window cycles (stalled) or a non-finite value. */
+static int run_cycles(OSolver* s, or_report* rep) {
+  OLevel* F = &s->lev[0];
+  double rel = rel_residual(s, F);
+  int cyc = 0, status = 0;
+  double hist[OR_HIST];
+  int nh = 0;
+  hist[nh++] = rel;
+  while (1) {
+    if (rel != rel) { status = 5; break; }
+    if (rel <= s->tol) break;
+    if (cyc >= s->max_cycles) { status = 3; break; }
+    if (s->stall_window > 0 && cyc >= s->stall_window && rel > 0.95 * hist[cyc - s->stall_window]) {
+      status = 4;
+      break;
+    }
+    vcycle(s, s, 0);
+    if (s->zero_mean) {
+      double m = interior_mean(&F->g, F->u[0]);
+      for (int k = 0; k < F->g.n[2]; ++k)
+        for (int j = 0; j < F->g.n[1]; ++j)
+          for (int i = 0; i < F->g.n[0]; ++i) F->u[0][IX(&F->g, i, j, k)] -= m;
+    }
+    ++cyc;
+    rel = rel_residual(s, F);
+    if (nh < OR_HIST) hist[nh++] = rel;
+  }
+  if (rep) {
+    rep->status = status;
+    rep->cycles = cyc;
+    rep->rel = rel;
+    rep->nhist = nh;
+    memcpy(rep->hist, hist, sizeof(double) * nh);
+  }
+  return status;
+}
+
+static void setup(OSolver* s, const or_desc* d, int kind, int bc, int ncomp) {
+  memset(s, 0, sizeof(*s));
+  s->kind = kind;
+  s->bc = bc;
+  s->ncomp = ncomp;
+  s->mixed = d->mixed;
+  s->nu1 = d->nu1;
+  s->nu2 = d->nu2;
+  s->max_cycles = d->max_cycles;
+  s->tol = d->tol;
+  s->stall_window = d->stall_window;
+  build_levels(s, d->ndim, d->geom, d->n, d->lo, d->hi);
+}
+
+static long ncells(const or_desc* d) {
+  long m = 1;
+  for (int k = 0; k < d->ndim; ++k) m *= d->n[k];
+  return m;
+}
+
+/* Number of levels the hierarchy rule gives. */
+int or_num_levels(const or_desc* d) {
+  OSolver s;
+  setup(&s, d, EQ_LIN, BC_NEUMANN, 1);
+  int n = s.nlev;
+  free_levels(&s);
+  return n;
+}
+
+/* Scalar solve: kind EQ_PSI (U, A2 used) or EQ_LIN (c may be NULL, f used).
+ * All arrays are interior layout; u is the initial guess in, solution out. */
+int or_solve_scalar(const or_desc* d, int kind, int bc, int zero_mean, const double* U,
+                    const double* A2, const double* c, const double* f, double* u, or_report* rep) {
+  OSolver s;
+  setup(&s, d, kind, bc, 1);
+  s.zero_mean = zero_mean;
+  OLevel* F = &s.lev[0];
+  if (U) load_interior(&F->g, F->U, U);
+  if (A2) load_interior(&F->g, F->A2, A2);
+  if (c) load_interior(&F->g, F->c, c);
+  if (f) load_interior(&F->g, F->f[0], f);
+  load_interior(&F->g, F->u[0], u);
+  restrict_sources(&s);
+  int st = run_cycles(&s, rep);
+  store_interior(&F->g, u, F->u[0]);
+  free_levels(&s);
+  return st;
+}
+
+/* Vector solve of lap V + 1/3 grad div V = f (three components). */
+int or_solve_vector(const or_desc* d, int bc, double* const f[3], double* const V[3], or_report* rep) {
+  OSolver s;
+  setup(&s, d, EQ_VEC, bc, 3);
+  OLevel* F = &s.lev[0];
+  for (int c = 0; c < 3; ++c) {
+    load_interior(&F->g, F->f[c], f[c]);
+    load_interior(&F->g, F->u[c], V[c]);
+  }
+  int st = run_cycles(&s, rep);
+  for (int c = 0; c < 3; ++c) store_interior(&F->g, V[c], F->u[c]);
+  free_levels(&s);
+  return st;
+}
+
+/* ---- unit-level entry points on ghosted arrays (finest level only) ---- */
+
+/* Ghosted size of the finest grid. */
+long or_ghosted_size(const or_desc* d) {
+  OGrid g;
+  int m[3] = {d->n[0], d->n[1], d->ndim > 2 ? d->n[2] : 1};
+  double h[3];
+  for (int k = 0; k < 3; ++k) h[k] = (k < d->ndim) ? (d->hi[k] - d->lo[k]) / m[k] : 1.0;
+  grid_init(&g, d->ndim, d->geom, m, d->lo, h);
+  return g.size;
+}
+
+static void finest_grid(const or_desc* d, OGrid* g) {
+  int m[3] = {d->n[0], d->n[1], d->ndim > 2 ? d->n[2] : 1};
+  double h[3];
+  for (int k = 0; k < 3; ++k) h[k] = (k < d->ndim) ? (d->hi[k] - d->lo[k]) / m[k] : 1.0;
+  grid_init(g, d->ndim, d->geom, m, d->lo, h);
+}
+
+/* Fill the ghosts of one ghosted field (comp -1 scalar, 0..2 vector). */
+void or_fill_ghosts(const or_desc* d, int bc, int comp, double* u) {
+  OGrid g;
+  finest_grid(d, &g);
+  fill_ghosts(&g, u, bc, comp);
+}
+
+/* Apply L to ghosted fields WITHOUT touching their ghosts; out is ghosted
+ * (interior written).  kind EQ_VEC uses V[0..2] and writes out[0..2]. */
+void or_apply_raw(const or_desc* d, int kind, double* const V[3], const double* U,
+                  const double* A2, const double* c, double* const out[3]) {
+  OSolver s;
+  memset(&s, 0, sizeof(s));
+  s.kind = kind;
+  s.ncomp = (kind == EQ_VEC) ? 3 : 1;
+  s.mixed = d->mixed;
+  OLevel L;
+  memset(&L, 0, sizeof(L));
+  finest_grid(d, &L.g);
+  for (int k = 0; k < 3; ++k) L.u[k] = V[k];
+  L.U = (double*)U;
+  L.A2 = (double*)A2;
+  L.c = (double*)c;
+  for (int cc = 0; cc < s.ncomp; ++cc)
+    for (int k = 0; k < L.g.n[2]; ++k)
+      for (int j = 0; j < L.g.n[1]; ++j)
+        for (int i = 0; i < L.g.n[0]; ++i)
+          out[cc][IX(&L.g, i, j, k)] = op_at(&s, &L, cc, i, j, k, NULL);
+}
+
+/* nsweeps red-black NGS sweeps on the finest level (ghosted arrays; ghosts
+ * are refilled as in the solver).  For EQ_VEC, f and u have 3 components. */
+void or_smooth(const or_desc* d, int kind, int bc, int nsweeps, double* const u[3],
+               double* const f[3], const double* U, const double* A2, const double* c) {
+  OSolver s;
+  memset(&s, 0, sizeof(s));
+  s.kind = kind;
+  s.bc = bc;
+  s.ncomp = (kind == EQ_VEC) ? 3 : 1;
+  s.mixed = d->mixed;
+  OLevel L;
+  memset(&L, 0, sizeof(L));
+  finest_grid(d, &L.g);
+  for (int k = 0; k < 3; ++k) {
+    L.u[k] = u[k];
+    L.f[k] = f[k];
+  }
+  L.U = (double*)U;
+  L.A2 = (double*)A2;
+  L.c = (double*)c;
+  for (int it = 0; it < nsweeps; ++it) smooth_sweep(&s, &L);
+}
+
+/* Restriction / Kwak prolongation between the finest grid of d and the next
+ * coarser grid (ghosted arrays).  'e' must already carry its ghosts. */
+void or_restrict(const or_desc* d, const double* uf, double* uc) {
+  OGrid gf, gc;
+  finest_grid(d, &gf);
+  int m[3];
+  double h[3];
+  for (int k = 0; k < 3; ++k) {
+    m[k] = (k < d->ndim) ? gf.n[k] / 2 : 1;
+    h[k] = gf.h[k] * ((k < d->ndim) ? 2.0 : 1.0);
+  }
+  grid_init(&gc, d->ndim, d->geom, m, gf.lo, h);
+  restrict_field(&gf, uf, &gc, uc);
+}
+void or_prolong_add(const or_desc* d, double* uf, const double* e) {
+  OGrid gf, gc;
+  finest_grid(d, &gf);
+  int m[3];
+  double h[3];
+  for (int k = 0; k < 3; ++k) {
+    m[k] = (k < d->ndim) ? gf.n[k] / 2 : 1;
+    h[k] = gf.h[k] * ((k < d->ndim) ? 2.0 : 1.0);
+  }
+  grid_init(&gc, d->ndim, d->geom, m, gf.lo, h);
+  prolong_add(&gf, uf, &gc, e);
+}
+
+/* ---------------------------------------------------------- xCFC pieces */
+
+/* A~_ij (orthonormal components, eq. Aij) from X with its ghosts filled:
+ * A~ = 2 E - (2/3) div X delta, E the symmetric gradient of X.  Writes the
+ * six independent components (rr, tt, pp, rt, rp, tp) and A2 = sum A~_ij^2. */
+static void aij_at(const OGrid* g, double* const X[3], int i, int j, int k, double A[6]) {
+  const double* a = X[0];
+  const double* b = X[1];
+  const double* cc = X[2];
+  long p = IX(g, i, j, k);
+  double E00, E11, E22, E01, E02, E12, div;
+  if (g->geom == GEOM_CART) {
+    E00 = d1(g, a, 0, i, j, k);
+    E11 = d1(g, b, 1, i, j, k);
+    E22 = d1(g, cc, 2, i, j, k);
+    E01 = 0.5 * (d1(g, a, 1, i, j, k) + d1(g, b, 0, i, j, k));
+    E02 = 0.5 * (d1(g, a, 2, i, j, k) + d1(g, cc, 0, i, j, k));
+    E12 = 0.5 * (d1(g, b, 2, i, j, k) + d1(g, cc, 1, i, j, k));
+  } else if (g->geom == GEOM_CYL) {   /* (R, z, phi) */
+    const double R = xc(g, 0, i);
+    E00 = d1(g, a, 0, i, j, k);
+    E11 = d1(g, b, 1, i, j, k);
+    E22 = d1(g, cc, 2, i, j, k) / R + a[p] / R;
+    E01 = 0.5 * (d1(g, a, 1, i, j, k) + d1(g, b, 0, i, j, k));
+    E02 = 0.5 * (d1(g, a, 2, i, j, k) / R + d1(g, cc, 0, i, j, k) - cc[p] / R);
+    E12 = 0.5 * (d1(g, cc, 1, i, j, k) + d1(g, b, 2, i, j, k) / R);
+  } else {                            /* (r, theta, phi) */
+    const double r = xc(g, 0, i), th = xc(g, 1, j);
+    const double st = sin(th), cot = cos(th) / st;
+    E00 = d1(g, a, 0, i, j, k);
+    E11 = d1(g, b, 1, i, j, k) / r + a[p] / r;
+    E22 = d1(g, cc, 2, i, j, k) / (r * st) + a[p] / r + cot * b[p] / r;
+    E01 = 0.5 * (d1(g, b, 0, i, j, k) - b[p] / r + d1(g, a, 1, i, j, k) / r);
+    E02 = 0.5 * (d1(g, a, 2, i, j, k) / (r * st) + d1(g, cc, 0, i, j, k) - cc[p] / r);
+    E12 = 0.5 * (d1(g, cc, 1, i, j, k) / r - cot * cc[p] / r + d1(g, b, 2, i, j, k) / (r * st));
+  }
+  div = E00 + E11 + E22;
+  A[0] = 2.0 * E00 - 2.0 / 3.0 * div;
+  A[1] = 2.0 * E11 - 2.0 / 3.0 * div;
+  A[2] = 2.0 * E22 - 2.0 / 3.0 * div;
+  A[3] = 2.0 * E01;
+  A[4] = 2.0 * E02;
+  A[5] = 2.0 * E12;
+}
+
+static double a2_of(const double A[6]) {
+  return A[0] * A[0] + A[1] * A[1] + A[2] * A[2] + 2.0 * (A[3] * A[3] + A[4] * A[4] + A[5] * A[5]);
+}
+
+/* Physical gradient of a scalar with ghosts. */
+static void grad_phys(const OGrid* g, const double* s, int i, int j, int k, double G[3]) {
+  G[0] = d1(g, s, 0, i, j, k);
+  G[1] = d1(g, s, 1, i, j, k);
+  G[2] = d1(g, s, 2, i, j, k);
+  if (g->geom == GEOM_CYL) {
+    G[2] /= xc(g, 0, i);
+  } else if (g->geom == GEOM_SPH) {
+    double r = xc(g, 0, i), st = sin(xc(g, 1, j));
+    G[1] /= r;
+    G[2] /= (r * st);
+  }
+}
+
+/* A~_ij and A2 from X given on the interior (Dirichlet-0 outer ghosts,
+ * parity inner ghosts).  Outputs interior arrays: A6[6] (may be NULL) and A2. */
+void or_aij(const or_desc* d, double* const X[3], double* const A6[6], double* A2) {
+  OGrid g;
+  finest_grid(d, &g);
+  double* Xg[3];
+  for (int c = 0; c < 3; ++c) {
+    Xg[c] = calloc(g.size, sizeof(double));
+    load_interior(&g, Xg[c], X[c]);
+    fill_ghosts(&g, Xg[c], BC_DIRICHLET, c);
+  }
+  long q = 0;
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i, ++q) {
+        double A[6];
+        aij_at(&g, Xg, i, j, k, A);
+        if (A6)
+          for (int m = 0; m < 6; ++m) A6[m][q] = A[m];
+        A2[q] = a2_of(A);
+      }
+  for (int c = 0; c < 3; ++c) free(Xg[c]);
+}
+
+typedef struct {
+  int psi_only;     /* 1: solve the psi equation only with A2 = 0 */
+  or_report rep[4]; /* X, psi, alpha*psi, beta */
+  double seconds;
+} or_cfc_report;
+
+/* The xCFC solve order, Steps 1-6 of Sec. 2.6 (Step 4, the primitive
+ * recovery, is replaced by the fixed sources the caller gives):
+ *   1 X:   lap X + 1/3 grad div X = 8 pi S_i                          (eq. X)
+ *   2 A~_ij from X                                                   (eq. Aij)
+ *   3 psi: lap psi = -2 pi U psi^-1 - 1/8 A2 psi^-7                   (eq. psi)
+ *   5 alpha psi: lap(a psi) = (a psi) [2 pi (U + 2 S) psi^-2 + 7/8 A2 psi^-8]
+ *   6 beta: lap b + 1/3 grad div b = 16 pi a psi^-6 S_i
+ *                                    + 2 A~_ij grad_j(a psi^-6)      (eq. beta)
+ * Deviations delta = psi - 1 and alpha psi - 1 are the scalar unknowns, with
+ * the Robin outer condition of eq. (robin); X and beta vanish at the outer
+ * boundary (eq. bc).  Fields are interior arrays; psi, alpha, beta, X carry
+ * the initial guess in and the solution out. */
+int or_solve_cfc(const or_desc* d, const double* U, const double* S, double* const Si[3],
+                 double* psi, double* alpha, double* const beta[3], double* const X[3],
+                 or_cfc_report* rep) {
+  long N = ncells(d);
+  OGrid g;
+  finest_grid(d, &g);
+  int status = 0;
+  double* A2 = calloc(N, sizeof(double));
+  double* f[3];
+  for (int c = 0; c < 3; ++c) f[c] = calloc(N, sizeof(double));
+  if (!rep->psi_only) {
+    /* Step 1 */
+    for (int c = 0; c < 3; ++c)
+      for (long q = 0; q < N; ++q) f[c][q] = 8.0 * OR_PI * Si[c][q];
+    status = or_solve_vector(d, BC_DIRICHLET, f, X, &rep->rep[0]);
+    if (status) goto done;
+    /* Step 2 */
+    or_aij(d, X, NULL, A2);
+  }
+  /* Step 3 */
+  double* dpsi = calloc(N, sizeof(double));
+  for (long q = 0; q < N; ++q) dpsi[q] = psi[q] - 1.0;
+  status = or_solve_scalar(d, EQ_PSI, BC_ROBIN, 0, U, A2, NULL, NULL, dpsi, &rep->rep[1]);
+  for (long q = 0; q < N; ++q) psi[q] = 1.0 + dpsi[q];
+  if (status || rep->psi_only) {
+    free(dpsi);
+    goto done;
+  }
+  /* Step 5 */
+  {
+    double* cf = calloc(N, sizeof(double));
+    double* dap = calloc(N, sizeof(double));
+    for (long q = 0; q < N; ++q) {
+      double p = psi[q];
+      cf[q] = 2.0 * OR_PI * (U[q] + 2.0 * S[q]) / (p * p) + 0.875 * A2[q] / pow(p, 8);
+      dap[q] = alpha[q] * psi[q] - 1.0;
+    }
+    status = or_solve_scalar(d, EQ_LIN, BC_ROBIN, 0, NULL, NULL, cf, cf, dap, &rep->rep[2]);
+    if (status) {
+      for (long q = 0; q < N; ++q) alpha[q] = (1.0 + dap[q]) / psi[q];
+      free(cf);
+      free(dap);
+      free(dpsi);
+      goto done;
+    }
+    /* Step 6: s = alpha psi^-6 = (alpha psi) psi^-7 on the ghosted grid */
+    double* gp = calloc(g.size, sizeof(double));
+    double* ga = calloc(g.size, sizeof(double));
+    double* sg = calloc(g.size, sizeof(double));
+    load_interior(&g, gp, dpsi);
+    load_interior(&g, ga, dap);
+    fill_ghosts(&g, gp, BC_ROBIN, -1);
+    fill_ghosts(&g, ga, BC_ROBIN, -1);
+    for (long p = 0; p < g.size; ++p) sg[p] = (1.0 + ga[p]) / pow(1.0 + gp[p], 7);
+    double* Xg[3];
+    for (int c = 0; c < 3; ++c) {
+      Xg[c] = calloc(g.size, sizeof(double));
+      load_interior(&g, Xg[c], X[c]);
+      fill_ghosts(&g, Xg[c], BC_DIRICHLET, c);
+    }
+    long q = 0;
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i, ++q) {
+          double A[6], G[3];
+          aij_at(&g, Xg, i, j, k, A);
+          grad_phys(&g, sg, i, j, k, G);
+          double sv = sg[IX(&g, i, j, k)];
+          /* (A~ . grad s)_i with A~ symmetric: rows (0: A0 A3 A4), (1: A3 A1 A5), (2: A4 A5 A2) */
+          double AG0 = A[0] * G[0] + A[3] * G[1] + A[4] * G[2];
+          double AG1 = A[3] * G[0] + A[1] * G[1] + A[5] * G[2];
+          double AG2 = A[4] * G[0] + A[5] * G[1] + A[2] * G[2];
+          f[0][q] = 16.0 * OR_PI * sv * Si[0][q] + 2.0 * AG0;
+          f[1][q] = 16.0 * OR_PI * sv * Si[1][q] + 2.0 * AG1;
+          f[2][q] = 16.0 * OR_PI * sv * Si[2][q] + 2.0 * AG2;
+        }
+    for (int c = 0; c < 3; ++c) free(Xg[c]);
+    free(gp);
+    free(ga);
+    free(sg);
+    status = or_solve_vector(d, BC_DIRICHLET, f, beta, &rep->rep[3]);
+    for (long q2 = 0; q2 < N; ++q2) alpha[q2] = (1.0 + dap[q2]) / psi[q2];
+    free(cf);
+    free(dap);
+  }
+  free(dpsi);
+done:
+  free(A2);
+  for (int c = 0; c < 3; ++c) free(f[c]);
+  return status;
+}
+
+/* -------------------------------------------------- divergence cleaning */
+
+typedef struct {
+  or_report solve;
+  double max_div_before, l2_div_before, max_div_after, l2_div_after;
+} or_divb_report;
+
+/* Central divergence of B (Cartesian), B ghosts copied from the boundary
+ * cells (zero normal gradient). */
+static void div_c(const OGrid* g, double* const Bg[3], double* div) {
+  for (int c = 0; c < g->ndim; ++c) fill_ghosts(g, Bg[c], BC_NEUMANN, -1);
+  long q = 0;
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i, ++q) {
+        double s = 0.0;
+        for (int c = 0; c < g->ndim; ++c) s += d1(g, Bg[c], c, i, j, k);
+        div[q] = s;
+      }
+}
+
+static void div_norms(const double* div, long N, double* mx, double* l2) {
+  double m = 0.0, s = 0.0;
+  for (long q = 0; q < N; ++q) {
+    double a = fabs(div[q]);
+    if (a > m) m = a;
+    s += div[q] * div[q];
+  }
+  *mx = m;
+  *l2 = sqrt(s / (double)N);
+}
+
+/* Elliptic divergence cleaning, eqs. (poisson) and (update_bfield), on a
+ * Cartesian grid: b = div B - mean(div B); lap Phi = b with Neumann ghosts,
+ * Phi's mean removed after every cycle; B <- B - grad Phi (central).  B holds
+ * ndim (interior) components, modified in place; phi (interior) out. */
+int or_clean_divb(const or_desc* d, double* const B[3], double* phi, or_divb_report* rep) {
+  OGrid g;
+  finest_grid(d, &g);
+  long N = ncells(d);
+  double* Bg[3] = {NULL, NULL, NULL};
+  for (int c = 0; c < d->ndim; ++c) {
+    Bg[c] = calloc(g.size, sizeof(double));
+    load_interior(&g, Bg[c], B[c]);
+  }
+  double* div = calloc(N, sizeof(double));
+  div_c(&g, Bg, div);
+  div_norms(div, N, &rep->max_div_before, &rep->l2_div_before);
+  double mean = 0.0;
+  for (long q = 0; q < N; ++q) mean += div[q];
+  mean /= (double)N;
+  for (long q = 0; q < N; ++q) div[q] -= mean;
+  for (long q = 0; q < N; ++q) phi[q] = 0.0;
+  int st = or_solve_scalar(d, EQ_LIN, BC_NEUMANN, 1, NULL, NULL, NULL, div, phi, &rep->solve);
+  double* pg = calloc(g.size, sizeof(double));
+  load_interior(&g, pg, phi);
+  fill_ghosts(&g, pg, BC_NEUMANN, -1);
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i)
+        for (int c = 0; c < d->ndim; ++c) Bg[c][IX(&g, i, j, k)] -= d1(&g, pg, c, i, j, k);
+  div_c(&g, Bg, div);
+  div_norms(div, N, &rep->max_div_after, &rep->l2_div_after);
+  for (int c = 0; c < d->ndim; ++c) {
+    store_interior(&g, B[c], Bg[c]);
+    free(Bg[c]);
+  }
+  free(pg);
+  free(div);
+  return st;
+}
+
+/* Central divergence only (for tests / diagnostics). */
+void or_div_c(const or_desc* d, double* const B[3], double* div) {
+  OGrid g;
+  finest_grid(d, &g);
+  double* Bg[3] = {NULL, NULL, NULL};
+  for (int c = 0; c < d->ndim; ++c) {
+    Bg[c] = calloc(g.size, sizeof(double));
+    load_interior(&g, Bg[c], B[c]);
+  }
+  div_c(&g, Bg, div);
+  for (int c = 0; c < d->ndim; ++c) free(Bg[c]);
+}
