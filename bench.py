@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 multigrid xCFC solver.
+
+One step = one full xCFC solve (Steps 1-6 of Sec. 2.6: the X, psi, alpha-psi
+and shift equations, each by FAS V(2,2) cycles to a relative residual of
+1e-10) from the flat initial guess, on the uniformly rotating n = 1
+polytrope on the 3D spherical 128 x 64 x 64 grid (r <= 100), inputs
+resident in HBM.  The metric is smoother cell-updates per second
+(sum over levels of cells x sweeps x components, per second of device time).
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+instead (a bounded sample of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_GRID = (128, 64, 64)
+R_MAX = 100.0
+TOL = 1e-10
+METRIC = "V-cycle Gcell-updates/s"
+UNIT = "Gcell-updates/s"
+WORKLOAD = "xCFC full system (X, psi, alpha*psi, beta), 3D spherical 128x64x64, r<=100, rotating n=1 polytrope"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--max-cycles", type=int, default=1000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def sources():
+    from paper_2012_07322_gb300 import inputs
+    return inputs.rotating_polytrope_sph3d(N_GRID, R_MAX)
+
+
+def level_cells():
+    """Cells per level of the hierarchy (halving while all dims even, >= 4)."""
+    n = list(N_GRID)
+    out = []
+    while True:
+        out.append(n[0] * n[1] * n[2])
+        if any(x < 4 or x % 2 for x in n):
+            break
+        n = [x // 2 for x in n]
+    return out
+
+
+# Algorithmic bytes per cell processed by one launch of each profiled kernel
+# class (every array streamed once per launch):
+#   colour pass, scalar: read all u (2 cells per updated cell), write u, read
+#     two per-cell inputs                        -> 5 words per updated cell
+#   colour pass, vector component: read the 3 components (6 words), write
+#     one, read its right-hand side             -> 8 words per updated cell
+#   finest residual, scalar: read u, 2 inputs, write r -> 4 words per cell
+#   finest residual, vector: read 3 u, 3 f, write 3 r  -> 9 words per cell
+BYTES_PER_CELL = {"smooth64_scalar": 5 * 8, "smooth64_vec": 8 * 8, "smooth32_scalar": 5 * 4,
+                  "smooth32_vec": 8 * 4, "resid64_scalar": 4 * 8, "resid64_vec": 9 * 8 / 3}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(threads):
+    """Bounded sample of the workload on the CPU oracle: 2 V-cycles of the X
+    (vector) equation and 2 of the psi equation on the full grid.  Returns
+    (cell updates, seconds)."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import oracle.oracle as orc
+    U, S, Si = sources()
+    d = orc.desc("sph", list(N_GRID), [0, 0, 0], [R_MAX, np.pi, 2 * np.pi], tol=1e-30, max_cycles=2,
+                 stall_window=0)
+    cells = level_cells()
+    per_cycle = sum(cells[:-1]) * 4          # nu1 + nu2 sweeps on every non-coarsest level
+    f = [8 * np.pi * x for x in Si]
+    V = [np.zeros(U.shape) for _ in range(3)]
+    t0 = time.perf_counter()
+    rv = orc.solve_vector(d, "dirichlet", f, V)
+    u = np.zeros(U.shape)
+    rs = orc.solve_scalar(d, "psi", "robin", u, U=U, A2=np.zeros(U.shape))
+    dt = time.perf_counter() - t0
+    updates = (rv["cycles"] * 3 + rs["cycles"]) * per_cycle
+    return updates, dt
+
+
+def reference_arm(args):
+    """The oracle as the reference arm (rank 0 only under torchrun)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(threads)
+    ups, secs = 0, 0.0
+    for _ in range(args.steps):
+        u, s = oracle_sample(threads)
+        ups += u
+        secs += s
+    value = ups / secs / 1e9
+    sample = "2 V-cycles of eq. X (3 components) + 2 of eq. psi on the full 128x64x64 grid per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "oracle on host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2012_07322_gb300 import mg
+    mg.lib()
+
+    U, S, Si = sources()
+    shp = U.shape
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    Ud, Sd, Sid = dev(U), dev(S), [dev(x) for x in Si]
+    stream = torch.cuda.current_stream()
+    desc = mg.grid_desc("sph", list(N_GRID), hi=[R_MAX, np.pi, 2 * np.pi], precision=args.precision, tol=TOL,
+                        max_cycles=args.max_cycles)
+    h = mg.Hierarchy(desc, stream)
+    psi = torch.ones(shp, dtype=torch.float64, device="cuda")
+    alpha = torch.ones_like(psi)
+    beta = [torch.zeros_like(psi) for _ in range(3)]
+    X = [torch.zeros_like(psi) for _ in range(3)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def reset():
+        psi.fill_(1.0)
+        alpha.fill_(1.0)
+        for t in beta + X:
+            t.zero_()
+
+    def solve():
+        return mg.mg_solve_cfc(h, Ud, Sd, Sid, psi, alpha, beta, X)
+
+    for _ in range(args.warmup):
+        reset()
+        solve()
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------- device-timed
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = ("GPU-" + str(props.uuid)) if hasattr(props, "uuid") else str(local)
+    sampler = ClockSampler(gpu_id)
+    ms_steps, updates = [], 0
+    launches0 = mg.mg_kernel_launches()
+    mg.mg_profile_enable(h, True)
+    reps = []
+    for _ in range(args.steps):
+        reset()
+        flush.fill_(1.0)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_steps.append(e0.elapsed_time(e1))
+        updates += sum(rep[k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta"))
+        reps.append(rep)
+    launches = mg.mg_kernel_launches() - launches0
+    prof = mg.mg_profile_read(h)
+    mg.mg_profile_enable(h, False)
+    clocks = sampler.stop()
+    total_ms = sum(ms_steps)
+    if dist:
+        t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, all_updates = float(tmax[0]), float(tsum[1])
+    else:
+        all_updates = float(updates)
+    value = all_updates / (total_ms * 1e-3) / 1e9
+
+    # ------------------------------------------------------------------ e2e
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        Uh, Sh, Sih = pin(U), pin(S), [pin(x) for x in Si]
+        ph, ah = pin(np.ones(shp)), pin(np.ones(shp))
+        bh = [pin(np.zeros(shp)) for _ in range(3)]
+        xh = [pin(np.zeros(shp)) for _ in range(3)]
+        e2e_ms, e2e_up = 0.0, 0
+        for _ in range(args.steps):
+            ph.fill_(1.0)
+            ah.fill_(1.0)
+            for t in bh + xh:
+                t.zero_()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rep = mg.mg_solve_cfc(h, Uh, Sh, Sih, ph, ah, bh, xh, host=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+            e2e_up += sum(rep[k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta"))
+        nb = 8 * int(np.prod(shp))
+        e2e = {"value": e2e_up / (e2e_ms * 1e-3) / 1e9 * world, "unit": UNIT, "h2d_bytes_per_step": 13 * nb,
+               "d2h_bytes_per_step": 8 * nb}
+
+    # ------------------------------------------------------------ roofline
+    peak, peak_kind = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, kms, kcells) = dom
+    bytes_launch = kcells * BYTES_PER_CELL[name] / max(nl, 1)
+    achieved = bytes_launch / (kms / max(nl, 1) * 1e-3) / 1e9 if nl else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": name, "launches": nl, "avg_launch_us": kms / max(nl, 1) * 1e3,
+                "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_kind,
+                "share_of_step_time": kms / total_ms if total_ms else None,
+                "kernel_classes": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        ups, secs = oracle_sample(threads)
+        cpu = {"value": ups / secs / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "2 V-cycles of eq. X (3 components) + 2 of eq. psi on the full grid (%.1f s)" % secs}
+
+    r0 = reps[-1]
+    if rank == 0:
+        lat = sorted(ms_steps)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(N_GRID), "precision": args.precision, "tol": TOL,
+                       "cycle": "FAS V(2,2) red-black NGS", "l2": "flushed between steps (256 MB write)",
+                       "cycles": {k: r0[k]["cycles"] for k in ("X", "psi", "alphapsi", "beta")},
+                       "rel": {k: r0[k]["rel"] for k in ("X", "psi", "alphapsi", "beta")},
+                       "solves_per_s": 1e3 * args.steps * world / total_ms,
+                       "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "parallelism": "replicas (independent solves per GPU)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    h.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * mg.h -- C ABI of the GB300 multigrid solver for the xCFC metric equations
+ * and elliptic divergence cleaning of Gmunu (arXiv:2012.07322).
+ *
+ * What is solved (section / equation of the paper):
+ *   - the xCFC system, Sec. 2.6, eqs. (X), (psi), (alpha), (beta), (Aij), in
+ *     the solve order Steps 1-6 of Sec. 2.6, with the outer conditions of
+ *     eq. (bc) and the Robin condition of eq. (robin) on the deviations
+ *     psi - 1 and alpha psi - 1;
+ *   - elliptic divergence cleaning, Sec. 2.2, eqs. (poisson) and
+ *     (update_bfield), on Cartesian grids;
+ * each by the non-linear cell-centred multigrid of Sec. 2.7: the flux-form
+ * discretisation of Sec. 2.7.1, red-black Newton-Gauss-Seidel smoothing
+ * (eq. ngs_iteration), piecewise-constant restriction and Kwak prolongation
+ * (Sec. 2.7.3), in FAS V(nu1, nu2) cycles.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are contiguous FP64, cell-centred, WITHOUT ghost cells,
+ *     dimension 0 fastest: element (i, j, k) is at i + n0 * (j + n1 * k).
+ *     2D grids have no dimension 2 (axisymmetric cylindrical (R, z) and
+ *     spherical (r, theta), or planar Cartesian (x, y)).
+ *   - Vector fields are given by their orthonormal (physical) components:
+ *     (x, y, z), (R, z, phi) or (r, theta, phi).
+ *   - Pointers are DEVICE pointers on the hierarchy's device unless a
+ *     function says otherwise (MG_HOST_POINTERS).  The caller owns them and
+ *     keeps them valid until the call returns; the library never frees them.
+ *   - Every function returns an mg_status.  No exception crosses the ABI.
+ *     On an error a solve leaves its output arrays holding the last iterate.
+ *   - Calls on one hierarchy are serialised on its stream and block until
+ *     their result is known; different hierarchies are independent.
+ */
+#ifndef GMUNU_MG_H
+#define GMUNU_MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status */
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,   /* bad descriptor or argument */
+  MG_ERR_OOM = 2,       /* device allocation failed */
+  MG_ERR_NOCONV = 3,    /* max_cycles reached before tol */
+  MG_ERR_STALLED = 4,   /* no 5 % residual gain over stall_window cycles */
+  MG_ERR_NAN = 5,       /* a non-finite residual or source was met */
+  MG_ERR_CUDA = 6,      /* a CUDA runtime call failed */
+  MG_ERR_BUSY = 7,      /* admission refused (request queue) */
+  MG_ERR_NOTFOUND = 8   /* unknown ticket */
+} mg_status;
+
+/* Human-readable name of a status code (static string). */
+const char* mg_strerror(int status);
+
+/* Detail of the last error raised on the calling thread (static buffer;
+ * empty if none). */
+const char* mg_last_error(void);
+
+/* -------------------------------------------------------- descriptor */
+enum { MG_CART = 0, MG_CYL = 1, MG_SPH = 2 };             /* geometry */
+enum { MG_FP64 = 0, MG_MIXED = 1 };                        /* precision */
+enum { MG_MIXED_4PT = 0, MG_MIXED_CORNER = 1 };            /* mixed derivative */
+enum { MG_BC_ROBIN = 0, MG_BC_DIRICHLET = 1, MG_BC_NEUMANN = 2 };
+enum { MG_EQ_PSI = 0, MG_EQ_LIN = 1, MG_EQ_VEC = 2 };      /* equation kinds */
+
+/*
+ * Grid and solver settings.
+ *   ndim      2 or 3.
+ *   geom      MG_CART, MG_CYL (R, z[, phi]) or MG_SPH (r, theta[, phi]).
+ *   n[d]      cells per dimension, each a power of two >= 2 (n[2] ignored
+ *             in 2D).  The hierarchy halves every dimension while all are
+ *             even and >= 4 (so the coarsest has >= 2 cells per dimension).
+ *   lo, hi    domain.  Spherical: lo = (0, 0[, 0]), hi = (r_max, pi[, 2 pi]).
+ *             Cylindrical: lo[0] = 0, and in 3D lo[2] = 0, hi[2] = 2 pi.
+ *   precision MG_FP64, or MG_MIXED: FP32 smoothing / restriction /
+ *             prolongation inside an FP64 defect-correction loop (the FP64
+ *             residual, non-linear sources, coarsest solve and norm).
+ *   nu1, nu2  pre / post smoothing sweeps (the paper uses 2 and 2).
+ *   max_cycles, tol   stop when rel <= tol (see mg_solve_report) or after
+ *             max_cycles V-cycles (MG_ERR_NOCONV).
+ *   mixed_deriv   MG_MIXED_4PT (four-corner stencil) or MG_MIXED_CORNER
+ *             (the block-corner stencil of Sec. 2.7.1, used on every cell).
+ *   stall_window  cycles over which a 5 % gain is required (0: off).
+ */
+typedef struct {
+  int ndim;
+  int geom;
+  int n[3];
+  double lo[3];
+  double hi[3];
+  int precision;
+  int nu1, nu2;
+  int max_cycles;
+  double tol;
+  int mixed_deriv;
+  int stall_window;
+} mg_grid_desc;
+
+#define MG_HIST 1024
+
+/*
+ * Per-solve report.  rel = max_i |w_i r_i| / max_i |w_i S_i(u)| over the
+ * finest cells (and components), r = f - L(u) the residual, S the source
+ * of the equation as the paper writes it, w = r^2 sin(theta) (spherical),
+ * R (cylindrical), 1 (Cartesian).  hist[0] is rel of the initial guess,
+ * hist[c] after c cycles (outer iterations in MG_MIXED).
+ */
+typedef struct {
+  int status;
+  int cycles;
+  double rel;
+  int nhist;
+  double hist[MG_HIST];
+  double ms;             /* wall time of the solve */
+  int64_t cell_updates;  /* smoother cell updates (all levels) */
+} mg_solve_report;
+
+typedef struct mg_hierarchy mg_hierarchy;
+
+/* Device bytes mg_create_hierarchy would allocate for desc (for admission). */
+int mg_hierarchy_bytes(const mg_grid_desc* desc, size_t* bytes);
+
+/*
+ * Validate desc and allocate every level, coefficient table and work array
+ * on the current CUDA device.  cuda_stream is a cudaStream_t (NULL: the
+ * legacy default stream); all work of the hierarchy is enqueued on it.
+ * The hierarchy owns its allocations; mg_destroy_hierarchy frees them.
+ */
+int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarchy** out);
+int mg_destroy_hierarchy(mg_hierarchy* h);
+
+/* Number of levels of the hierarchy (finest = 0). */
+int mg_num_levels(const mg_hierarchy* h, int* nlev);
+
+/* ------------------------------------------------------------- xCFC */
+
+/* Sources of the xCFC equations (Sec. 2.6), held fixed during the solve
+ * (Step 4, the primitive recovery, is the caller's): U = U~ = psi^6 U,
+ * S = S~ = psi^6 gamma_ij S^ij, Si = S~_i (orthonormal components). */
+typedef struct {
+  const double* U;
+  const double* S;
+  const double* Si[3];
+} mg_cfc_sources;
+
+/* Metric fields: initial guess in (flat: psi = alpha = 1, beta = X = 0, or
+ * a warm start), solution out. */
+typedef struct {
+  double* psi;
+  double* alpha;
+  double* beta[3];
+  double* X[3];
+} mg_cfc_fields;
+
+enum {
+  MG_CFC_PSI_ONLY = 1,        /* solve eq. psi only with A~_ij = 0 */
+  MG_HOST_POINTERS = 2        /* sources / fields are host memory */
+};
+
+typedef struct {
+  mg_solve_report eq[4];      /* X, psi, alpha psi, beta */
+  double ms;                  /* total wall time */
+} mg_cfc_report;
+
+/*
+ * The xCFC solve order (Steps 1-6, Sec. 2.6): solve eq. (X) for X, form
+ * A~_ij (eq. Aij), solve eq. (psi), form the alpha-psi coefficient
+ * 2 pi (U + 2 S) psi^-2 + 7/8 A~^2 psi^-8, solve eq. (alpha) for alpha psi,
+ * form the shift source 16 pi alpha psi^-6 S_i + 2 A~_ij grad_j(alpha psi^-6),
+ * solve eq. (beta), and return alpha = (alpha psi) / psi.
+ * flags: MG_CFC_PSI_ONLY, MG_HOST_POINTERS.  rep may be NULL.
+ */
+int mg_solve_cfc(mg_hierarchy* h, const mg_cfc_sources* src, mg_cfc_fields* io, int flags,
+                 mg_cfc_report* rep);
+
+/* --------------------------------------------------- divergence cleaning */
+
+typedef struct {
+  mg_solve_report solve;
+  double max_div_before, l2_div_before;   /* of the central divergence */
+  double max_div_after, l2_div_after;     /* l2 = sqrt(mean(div^2)), Sec. 3.2.4 */
+} mg_divb_report;
+
+/*
+ * Elliptic divergence cleaning (eqs. poisson, update_bfield) on a
+ * Cartesian hierarchy: b = div B - mean(div B) (central differences, B
+ * ghosts copied from the boundary cells), solve lap Phi = b with Neumann
+ * ghosts (zero-mean Phi), then B <- B - grad Phi.  B[0..ndim-1] are
+ * modified in place; phi_out (may be NULL) receives Phi.  Flags:
+ * MG_HOST_POINTERS.
+ */
+int mg_clean_divB(mg_hierarchy* h, double* B[3], double* phi_out, int flags, mg_divb_report* rep);
+
+/* ------------------------------------------- single equations (expert) */
+
+/*
+ * Solve one scalar equation L(u) = f on the hierarchy (Sec. 2.7):
+ *   MG_EQ_PSI: L(u) = lap u + 2 pi U (1+u)^-1 + 1/8 A2 (1+u)^-7, f = 0
+ *              (eq. psi for u = psi - 1; f is ignored and may be NULL);
+ *   MG_EQ_LIN: L(u) = lap u - c u (c may be NULL: Poisson), f given.
+ * bc: outer boundary condition; zero_mean: remove the mean of u after
+ * every cycle (Neumann gauge).  u: initial guess in, solution out.
+ */
+int mg_solve_scalar(mg_hierarchy* h, int kind, int bc, int zero_mean, const double* U,
+                    const double* A2, const double* c, const double* f, double* u,
+                    mg_solve_report* rep);
+
+/* Solve lap V + 1/3 grad div V = f (eqs. X, beta) with outer condition bc
+ * (MG_BC_DIRICHLET for X and beta). */
+int mg_solve_vector(mg_hierarchy* h, int bc, const double* f[3], double* V[3], mg_solve_report* rep);
+
+/* ----------------------------------------------- unit-level (testing) */
+
+/*
+ * Apply L of an equation kind to u on the finest level (ghosts from the
+ * boundary rules): out = L(u).  For MG_EQ_VEC u, out have 3 components;
+ * otherwise component 0 only and U, A2, c as in mg_solve_scalar.
+ */
+int mg_apply_operator(mg_hierarchy* h, int kind, int bc, const double* u[3], const double* U,
+                      const double* A2, const double* c, double* out[3]);
+
+/* nsweeps red-black NGS sweeps of L(u) = f on the finest level, in place. */
+int mg_smooth(mg_hierarchy* h, int kind, int bc, int nsweeps, double* u[3], const double* f[3],
+              const double* U, const double* A2, const double* c);
+
+/* A2 = A~_ij A~^ij (eq. Aij) of X (Dirichlet-0 outer, parity inner ghosts). */
+int mg_compute_a2(mg_hierarchy* h, const double* X[3], double* A2);
+
+/* Central divergence of B (Cartesian; ghosts copied from boundary cells). */
+int mg_divergence(mg_hierarchy* h, const double* B[3], double* div);
+
+/* Restrict a finest-level field to level 1 (out has level-1 size), or
+ * add the Kwak prolongation of a level-1 correction e (Robin/Dirichlet/
+ * Neumann ghosts by bc, scalar parity) into a finest-level field. */
+int mg_restrict(mg_hierarchy* h, const double* fine, double* coarse);
+int mg_prolong_add(mg_hierarchy* h, int bc, const double* coarse_e, double* fine);
+
+/* ------------------------------------------------------ instrumentation */
+
+/* Kernel launches issued by the library since it was loaded (all
+ * hierarchies, all threads). */
+uint64_t mg_kernel_launches(void);
+
+/* Kernel classes timed by mg_profile_*: red-black colour passes (one
+ * launch updates half of the finest cells, one component) and the finest
+ * residual with its norms (every cell, every component). */
+enum {
+  MG_PROF_SMOOTH64_SCALAR = 0,
+  MG_PROF_SMOOTH64_VEC = 1,
+  MG_PROF_SMOOTH32_SCALAR = 2,
+  MG_PROF_SMOOTH32_VEC = 3,
+  MG_PROF_RESID64_SCALAR = 4,
+  MG_PROF_RESID64_VEC = 5,
+  MG_PROF_NCLASS = 6
+};
+
+/* Enable (1) or disable (0) CUDA-event timing, on the hierarchy's stream,
+ * of every finest-level launch of the classes above; clears the records. */
+int mg_profile_enable(mg_hierarchy* h, int enable);
+
+/* Launch count, summed device milliseconds and summed cells processed of
+ * one class since the last mg_profile_enable (synchronises the stream). */
+int mg_profile_read(mg_hierarchy* h, int klass, int64_t* launches, double* ms, int64_t* cells);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMUNU_MG_H */

@@ -18,7 +18,7 @@
  *   Sec. 2.7.2, eq. (ngs_iteration), red-black ordering -- smoother
  *   Sec. 2.7.3, Kwak prolongation, piecewise-constant restriction
  *   Sec. 2.2, eqs. (poisson), (update_bfield)           -- div-B cleaning
- *   Sec. 5.2 (MG performance): V-cycles with 2+2 red-black smoothing steps.
+ *   Sec. 4.2 (metric-solver performance): 2 + 2 red-black smoothing steps.
  *
  * Readings where the paper is silent or garbled (each listed in the design
  * notes of the repository):
@@ -40,7 +40,10 @@
  *   - coarsest grid: Newton-Gauss-Seidel sweeps until its residual falls by
  *     1e-12 or 100 sweeps;
  *   - stopping rule: rel = max|w r| / max|w S(u)|, w = r^2 sin(theta)
- *     (spherical), R (cylindrical), 1 (Cartesian).
+ *     (spherical), R (cylindrical), 1 (Cartesian);
+ *   - optional Anderson mixing of successive V-cycle iterates (not in the
+ *     paper; off when accel_depth = 0): point smoothing converges slowly on
+ *     spherical grids (the paper notes it), mixing restores the rate.
  *
  * Layout of every ghosted array: one ghost layer in each active dimension,
  * index (i, j, k) with i in [-1, n0], j in [-1, n1], k in [-1, n2] (3D) or
@@ -383,7 +386,7 @@ typedef struct {
 
 typedef struct {
   int kind, bc, ncomp, mixed, zero_mean;
-  int nu1, nu2, max_cycles, stall_window;
+  int nu1, nu2, max_cycles, stall_window, accel;
   double tol;
   int nlev;
   OLevel lev[OR_MAX_LEVELS];
@@ -680,6 +683,7 @@ typedef struct {
   double tol;
   int mixed;
   int stall_window;   /* cycles over which a 5 % gain is required; 0: off */
+  int accel_depth;    /* Anderson mixing depth m over the V-cycle map; 0: off */
 } or_desc;
 
 typedef struct {
@@ -700,8 +704,77 @@ static void restrict_sources(OSolver* s) {
   }
 }
 
+/* The fixed-point map of the iteration: one FAS V-cycle from the current
+ * finest u, then (Neumann gauge) removal of the mean. */
+static void cycle_map(OSolver* s) {
+  OLevel* F = &s->lev[0];
+  vcycle(s, s, 0);
+  if (s->zero_mean) {
+    double m = interior_mean(&F->g, F->u[0]);
+    for (int k = 0; k < F->g.n[2]; ++k)
+      for (int j = 0; j < F->g.n[1]; ++j)
+        for (int i = 0; i < F->g.n[0]; ++i) F->u[0][IX(&F->g, i, j, k)] -= m;
+  }
+}
+
+/* Finest unknowns (all components) <-> one flat vector. */
+static void gather_u(const OSolver* s, double* x) {
+  const OLevel* F = &s->lev[0];
+  long q = 0;
+  for (int c = 0; c < s->ncomp; ++c)
+    for (int k = 0; k < F->g.n[2]; ++k)
+      for (int j = 0; j < F->g.n[1]; ++j)
+        for (int i = 0; i < F->g.n[0]; ++i) x[q++] = F->u[c][IX(&F->g, i, j, k)];
+}
+static void scatter_u(OSolver* s, const double* x) {
+  OLevel* F = &s->lev[0];
+  long q = 0;
+  for (int c = 0; c < s->ncomp; ++c)
+    for (int k = 0; k < F->g.n[2]; ++k)
+      for (int j = 0; j < F->g.n[1]; ++j)
+        for (int i = 0; i < F->g.n[0]; ++i) F->u[c][IX(&F->g, i, j, k)] = x[q++];
+}
+
+/* Solve (M + lambda I) y = b for the small symmetric Gram matrix M (order
+ * m, row-major) by Cholesky, lambda = 1e-12 max diag(M).  Returns 0 on
+ * success, -1 if M is degenerate. */
+static int small_spd_solve(int m, const double* M, const double* b, double* y) {
+  double A[64 * 64], L[64 * 64];
+  double dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = M[i * m + i] > dmax ? M[i * m + i] : dmax;
+  if (!(dmax > 0.0)) return -1;
+  for (int i = 0; i < m * m; ++i) A[i] = M[i];
+  for (int i = 0; i < m; ++i) A[i * m + i] += 1e-12 * dmax;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double sum = A[i * m + j];
+      for (int k = 0; k < j; ++k) sum -= L[i * m + k] * L[j * m + k];
+      if (i == j) {
+        if (!(sum > 0.0)) return -1;
+        L[i * m + i] = sqrt(sum);
+      } else {
+        L[i * m + j] = sum / L[j * m + j];
+      }
+    }
+  double z[64];
+  for (int i = 0; i < m; ++i) {
+    double sum = b[i];
+    for (int k = 0; k < i; ++k) sum -= L[i * m + k] * z[k];
+    z[i] = sum / L[i * m + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double sum = z[i];
+    for (int k = i + 1; k < m; ++k) sum -= L[k * m + i] * y[k];
+    y[i] = sum / L[i * m + i];
+  }
+  return 0;
+}
+
 /* Cycle control: V-cycles until rel <= tol, max_cycles (not converged),
- * no 5 % gain over stall_window cycles (stalled) or a non-finite value. */
+ * no 5 % gain over stall_window cycles (stalled) or a non-finite value.
+ * With accel > 0 the iterates are Anderson-mixed (depth m = accel):
+ * f = G(x) - x, x_next = G(x) - dG gamma, gamma = argmin |f - dF gamma|
+ * over the last m differences dF, dG of f and G (one V-cycle each). */
 static int run_cycles(OSolver* s, or_report* rep) {
   OLevel* F = &s->lev[0];
   double rel = rel_residual(s, F);
@@ -709,6 +782,19 @@ static int run_cycles(OSolver* s, or_report* rep) {
   double hist[OR_HIST];
   int nh = 0;
   hist[nh++] = rel;
+  const int m = s->accel < 0 ? 0 : (s->accel > 32 ? 32 : s->accel);
+  const long nv = (long)s->ncomp * F->g.n[0] * F->g.n[1] * F->g.n[2];
+  double *x = NULL, *g = NULL, *fcur = NULL, *fprev = NULL, *gprev = NULL, *dF = NULL, *dG = NULL;
+  int ncol = 0, head = 0;   /* columns kept; ring position of the next column */
+  if (m > 0) {
+    x = malloc(sizeof(double) * nv);
+    g = malloc(sizeof(double) * nv);
+    fcur = malloc(sizeof(double) * nv);
+    fprev = malloc(sizeof(double) * nv);
+    gprev = malloc(sizeof(double) * nv);
+    dF = malloc(sizeof(double) * nv * m);
+    dG = malloc(sizeof(double) * nv * m);
+  }
   while (1) {
     if (rel != rel) { status = 5; break; }
     if (rel <= s->tol) break;
@@ -717,17 +803,65 @@ static int run_cycles(OSolver* s, or_report* rep) {
       status = 4;
       break;
     }
-    vcycle(s, s, 0);
-    if (s->zero_mean) {
-      double m = interior_mean(&F->g, F->u[0]);
-      for (int k = 0; k < F->g.n[2]; ++k)
-        for (int j = 0; j < F->g.n[1]; ++j)
-          for (int i = 0; i < F->g.n[0]; ++i) F->u[0][IX(&F->g, i, j, k)] -= m;
+    if (m == 0) {
+      cycle_map(s);
+    } else {
+      gather_u(s, x);
+      cycle_map(s);
+      gather_u(s, g);
+      for (long q = 0; q < nv; ++q) fcur[q] = g[q] - x[q];
+      if (cyc > 0) {
+        double* cf = dF + (long)head * nv;
+        double* cg = dG + (long)head * nv;
+        for (long q = 0; q < nv; ++q) {
+          cf[q] = fcur[q] - fprev[q];
+          cg[q] = g[q] - gprev[q];
+        }
+        head = (head + 1) % m;
+        if (ncol < m) ++ncol;
+      }
+      memcpy(fprev, fcur, sizeof(double) * nv);
+      memcpy(gprev, g, sizeof(double) * nv);
+      if (ncol > 0) {
+        /* columns in age order: oldest first */
+        double M[32 * 32], b[32], gam[32];
+        int col[32];
+        for (int a = 0; a < ncol; ++a) col[a] = (head - ncol + a + m) % m;
+        for (int a = 0; a < ncol; ++a) {
+          const double* fa = dF + (long)col[a] * nv;
+          double sb = 0.0;
+          for (long q = 0; q < nv; ++q) sb += fa[q] * fcur[q];
+          b[a] = sb;
+          for (int c2 = 0; c2 <= a; ++c2) {
+            const double* fc = dF + (long)col[c2] * nv;
+            double sm = 0.0;
+            for (long q = 0; q < nv; ++q) sm += fa[q] * fc[q];
+            M[a * ncol + c2] = sm;
+            M[c2 * ncol + a] = sm;
+          }
+        }
+        if (small_spd_solve(ncol, M, b, gam) == 0) {
+          for (int a = 0; a < ncol; ++a) {
+            const double* ga = dG + (long)col[a] * nv;
+            for (long q = 0; q < nv; ++q) g[q] -= gam[a] * ga[q];
+          }
+        } else {
+          ncol = 0;   /* degenerate history: restart the mixing */
+        }
+      }
+      scatter_u(s, g);
     }
     ++cyc;
     rel = rel_residual(s, F);
     if (nh < OR_HIST) hist[nh++] = rel;
   }
+  free(x);
+  free(g);
+  free(fcur);
+  free(fprev);
+  free(gprev);
+  free(dF);
+  free(dG);
   if (rep) {
     rep->status = status;
     rep->cycles = cyc;
@@ -749,6 +883,7 @@ static void setup(OSolver* s, const or_desc* d, int kind, int bc, int ncomp) {
   s->max_cycles = d->max_cycles;
   s->tol = d->tol;
   s->stall_window = d->stall_window;
+  s->accel = d->accel_depth;
   build_levels(s, d->ndim, d->geom, d->n, d->lo, d->hi);
 }
 

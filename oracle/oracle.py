@@ -51,7 +51,8 @@ class Desc(C.Structure):
     _fields_ = [("ndim", C.c_int), ("geom", C.c_int), ("n", C.c_int * 3),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int),
-                ("tol", C.c_double), ("mixed", C.c_int), ("stall_window", C.c_int)]
+                ("tol", C.c_double), ("mixed", C.c_int), ("stall_window", C.c_int),
+                ("accel_depth", C.c_int)]
 
 
 class Report(C.Structure):
@@ -97,7 +98,8 @@ def lib():
         return _lib
 
 
-def desc(geom, n, lo, hi, nu1=2, nu2=2, max_cycles=200, tol=1e-10, mixed="4pt", stall_window=10):
+def desc(geom, n, lo, hi, nu1=2, nu2=2, max_cycles=200, tol=1e-10, mixed="4pt", stall_window=10,
+         accel_depth=0):
     """Grid + solver descriptor.  n, lo, hi have one entry per dimension."""
     d = Desc()
     nd = len(n)
@@ -110,6 +112,7 @@ def desc(geom, n, lo, hi, nu1=2, nu2=2, max_cycles=200, tol=1e-10, mixed="4pt", 
     d.nu1, d.nu2, d.max_cycles, d.tol = nu1, nu2, min(max_cycles, 1000), tol
     d.mixed = MIXED[mixed]
     d.stall_window = stall_window
+    d.accel_depth = accel_depth
     return d
 
 

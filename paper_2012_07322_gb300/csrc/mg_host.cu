@@ -1,0 +1,1121 @@
+// Host side of the solver: descriptor validation, the level hierarchy and
+// its coefficient tables, FAS V-cycles and the FP32/FP64 defect-correction
+// loop, the xCFC solve order and divergence cleaning, behind the C ABI of
+// include/mg.h.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mg.h"
+#include "mg_internal.h"
+
+using namespace gmg;
+
+namespace {
+
+constexpr int MAX_LEVELS = 16;
+constexpr int NPARTS = 1024;           // blocks of the deterministic sums
+constexpr int COARSE_SWEEPS = 100;     // coarsest-grid sweep cap (Sec. 2.7.2)
+constexpr double PI = 3.14159265358979323846;
+
+thread_local char g_last_error[256] = "";
+
+struct Level {
+  int n[3];
+  double h[3], lo[3];
+  long sx, sy, off, ng;
+  LevelView<double> v64;
+  LevelView<float> v32;
+  double* ti64 = nullptr;
+  double* tj64 = nullptr;
+  float* ti32 = nullptr;
+  float* tj32 = nullptr;
+  double *u[3] = {}, *uh[3] = {}, *f[3] = {}, *r[3] = {}, *s0 = nullptr, *s1 = nullptr;
+  float *e[3] = {}, *f32[3] = {}, *r32[3] = {}, *k32 = nullptr;
+  long cells() const { return (long)n[0] * n[1] * n[2]; }
+};
+
+}  // namespace
+
+struct mg_hierarchy {
+  mg_grid_desc d;
+  cudaStream_t st = nullptr;
+  int nlev = 0;
+  Level L[MAX_LEVELS];
+  // level-0 arrays of the xCFC sequence (ghosted)
+  double *Xg[3] = {}, *dpsi = nullptr, *dap = nullptr, *sg = nullptr, *Ug = nullptr, *Sg = nullptr,
+         *Sig[3] = {};
+  unsigned long long* d_red = nullptr;   // 8 reduction slots
+  unsigned long long* h_red = nullptr;   // pinned mirror
+  double* d_part = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // staging buffers for MG_HOST_POINTERS (allocated on first use)
+  std::vector<double*> stage;
+  int64_t updates = 0;
+  // optional event timing of finest-level kernels (mg_profile_enable)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_cls;
+  std::vector<int64_t> ev_cells;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+// Event pair around a finest-level launch when profiling is on; returns
+// the pair's slot or -1.
+long prof_begin(mg_hierarchy* H, int l, int cls, int64_t cells) {
+  if (!H->prof_on || l != 0) return -1;
+  const size_t pair = H->ev_used / 2;
+  if (H->ev_used + 2 > H->ev.size()) {
+    for (int q = 0; q < 512; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      H->ev.push_back(e);
+    }
+  }
+  if (H->ev_cls.size() <= pair) {
+    H->ev_cls.resize(pair + 256);
+    H->ev_cells.resize(pair + 256);
+  }
+  H->ev_cls[pair] = cls;
+  H->ev_cells[pair] = cells;
+  cudaEventRecord(H->ev[H->ev_used], H->st);
+  H->ev_used += 1;
+  return (long)pair;
+}
+void prof_end(mg_hierarchy* H, long tok) {
+  if (tok < 0) return;
+  cudaEventRecord(H->ev[H->ev_used], H->st);
+  H->ev_used += 1;
+}
+
+struct Eq {
+  int kind, bc, zero_mean, ncomp;
+  bool has_c;    // EQ_LIN with a coefficient array
+};
+
+int fail(int status, const char* what) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", what);
+  return status;
+}
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", #call, cudaGetErrorString(e_)); \
+      return MG_ERR_CUDA;                                                           \
+    }                                                                               \
+  } while (0)
+
+bool pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+
+int validate(const mg_grid_desc* d) {
+  if (!d) return fail(MG_ERR_INVALID, "null descriptor");
+  if (d->ndim != 2 && d->ndim != 3) return fail(MG_ERR_INVALID, "ndim must be 2 or 3");
+  if (d->geom < MG_CART || d->geom > MG_SPH) return fail(MG_ERR_INVALID, "bad geometry");
+  for (int k = 0; k < d->ndim; ++k) {
+    if (!pow2(d->n[k])) return fail(MG_ERR_INVALID, "each n must be a power of two >= 2");
+    if (!(d->hi[k] > d->lo[k])) return fail(MG_ERR_INVALID, "need lo < hi");
+  }
+  long cells = 1;
+  for (int k = 0; k < d->ndim; ++k) cells *= d->n[k];
+  if (cells > (1L << 31)) return fail(MG_ERR_INVALID, "grid too large");
+  const double tol_ang = 1e-12;
+  if (d->geom == MG_SPH) {
+    if (d->lo[0] != 0.0 || d->lo[1] != 0.0 || std::fabs(d->hi[1] - PI) > tol_ang)
+      return fail(MG_ERR_INVALID, "spherical grids need r in [0, r_max], theta in [0, pi]");
+    if (d->ndim == 3 && (d->lo[2] != 0.0 || std::fabs(d->hi[2] - 2 * PI) > tol_ang))
+      return fail(MG_ERR_INVALID, "spherical 3D grids need phi in [0, 2 pi)");
+  }
+  if (d->geom == MG_CYL) {
+    if (d->lo[0] != 0.0) return fail(MG_ERR_INVALID, "cylindrical grids need R in [0, R_max]");
+    if (d->ndim == 3 && (d->lo[2] != 0.0 || std::fabs(d->hi[2] - 2 * PI) > tol_ang))
+      return fail(MG_ERR_INVALID, "cylindrical 3D grids need phi in [0, 2 pi)");
+  }
+  if (d->precision != MG_FP64 && d->precision != MG_MIXED) return fail(MG_ERR_INVALID, "bad precision");
+  if (d->nu1 < 0 || d->nu2 < 0 || d->nu1 > 64 || d->nu2 > 64 || d->nu1 + d->nu2 == 0)
+    return fail(MG_ERR_INVALID, "bad nu1/nu2");
+  if (d->max_cycles < 0 || d->max_cycles >= MG_HIST) return fail(MG_ERR_INVALID, "max_cycles out of range");
+  if (!(d->tol >= 0.0)) return fail(MG_ERR_INVALID, "bad tol");
+  if (d->mixed_deriv != MG_MIXED_4PT && d->mixed_deriv != MG_MIXED_CORNER)
+    return fail(MG_ERR_INVALID, "bad mixed_deriv");
+  if (d->stall_window < 0) return fail(MG_ERR_INVALID, "bad stall_window");
+  return MG_OK;
+}
+
+// Level sizes: halve every dimension while all are even and >= 4.
+int level_sizes(const mg_grid_desc* d, int n[][3], double h[][3]) {
+  int m[3] = {d->n[0], d->n[1], d->ndim == 3 ? d->n[2] : 1};
+  double hh[3];
+  for (int k = 0; k < 3; ++k) hh[k] = (k < d->ndim) ? (d->hi[k] - d->lo[k]) / m[k] : 1.0;
+  int nl = 0;
+  for (;;) {
+    for (int k = 0; k < 3; ++k) {
+      n[nl][k] = m[k];
+      h[nl][k] = hh[k];
+    }
+    ++nl;
+    bool ok = nl < MAX_LEVELS;
+    for (int k = 0; k < d->ndim; ++k)
+      if (m[k] < 4 || (m[k] & 1)) ok = false;
+    if (!ok) break;
+    for (int k = 0; k < d->ndim; ++k) {
+      m[k] /= 2;
+      hh[k] *= 2;
+    }
+  }
+  return nl;
+}
+
+// Walk the arena layout; with base == nullptr only sizes are summed.
+size_t layout(mg_hierarchy* H, const mg_grid_desc* d, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = (off + 255) & ~size_t(255);
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  int n[MAX_LEVELS][3];
+  double h[MAX_LEVELS][3];
+  const int nl = level_sizes(d, n, h);
+  const bool mixed = d->precision == MG_MIXED;
+  const int three = d->ndim == 3;
+  for (int l = 0; l < nl; ++l) {
+    const long sx = n[l][0] + 2, sy = sx * (n[l][1] + 2);
+    const long ng = sy * (n[l][2] + 2 * three);
+    const size_t b64 = sizeof(double) * ng, b32 = sizeof(float) * ng;
+    Level* L = H ? &H->L[l] : nullptr;
+    auto t64 = [&](double** slot, size_t bytes) {
+      char* p = take(bytes);
+      if (L) *slot = (double*)p;
+    };
+    auto t32 = [&](float** slot, size_t bytes) {
+      char* p = take(bytes);
+      if (L) *slot = (float*)p;
+    };
+    double* dummy64 = nullptr;
+    float* dummy32 = nullptr;
+    t64(L ? &L->ti64 : &dummy64, sizeof(double) * NTI * (n[l][0] + 2));
+    t64(L ? &L->tj64 : &dummy64, sizeof(double) * NTJ * (n[l][1] + 2));
+    t32(L ? &L->ti32 : &dummy32, sizeof(float) * NTI * (n[l][0] + 2));
+    t32(L ? &L->tj32 : &dummy32, sizeof(float) * NTJ * (n[l][1] + 2));
+    for (int c = 0; c < 3; ++c) {
+      t64(L ? &L->u[c] : &dummy64, b64);
+      if (l > 0) t64(L ? &L->uh[c] : &dummy64, b64);
+      t64(L ? &L->f[c] : &dummy64, b64);
+      t64(L ? &L->r[c] : &dummy64, b64);
+    }
+    t64(L ? &L->s0 : &dummy64, b64);
+    t64(L ? &L->s1 : &dummy64, b64);
+    if (mixed) {
+      for (int c = 0; c < 3; ++c) {
+        t32(L ? &L->e[c] : &dummy32, b32);
+        t32(L ? &L->f32[c] : &dummy32, b32);
+        t32(L ? &L->r32[c] : &dummy32, b32);
+      }
+      t32(L ? &L->k32 : &dummy32, b32);
+    }
+    if (l == 0) {
+      double* dm = nullptr;
+      for (int c = 0; c < 3; ++c) {
+        char* p = take(b64);
+        if (H) H->Xg[c] = (double*)p;
+        p = take(b64);
+        if (H) H->Sig[c] = (double*)p;
+      }
+      double** singles[] = {H ? &H->dpsi : &dm, H ? &H->dap : &dm, H ? &H->sg : &dm, H ? &H->Ug : &dm,
+                            H ? &H->Sg : &dm};
+      for (double** s : singles) {
+        char* p = take(b64);
+        if (H) *s = (double*)p;
+      }
+    }
+  }
+  char* p = take(sizeof(unsigned long long) * 8);
+  if (H) H->d_red = (unsigned long long*)p;
+  p = take(sizeof(double) * NPARTS);
+  if (H) H->d_part = (double*)p;
+  return (off + 255) & ~size_t(255);
+}
+
+// 1D coefficient tables of one level (Sec. 2.7.1 flux-form operators,
+// Appendix A cell volumes for the restriction weights).
+void make_tables(const mg_grid_desc* d, const Level& L, std::vector<double>& ti, std::vector<double>& tj) {
+  const int n0 = L.n[0], n1 = L.n[1];
+  ti.assign((size_t)NTI * (n0 + 2), 0.0);
+  tj.assign((size_t)NTJ * (n1 + 2), 0.0);
+  const double h0 = L.h[0], h1 = L.h[1], h2 = L.h[2];
+  for (int i = -1; i <= n0; ++i) {
+    const double x = L.lo[0] + (i + 0.5) * h0, xm = L.lo[0] + i * h0, xp = L.lo[0] + (i + 1) * h0;
+    double* T = ti.data() + (i + 1);
+    auto S = [&](int slot) -> double& { return T[(size_t)slot * (n0 + 2)]; };
+    S(TI_X) = x;
+    S(TI_IX) = 1.0 / x;
+    S(TI_IX2) = 1.0 / (x * x);
+    if (d->geom == MG_CART) {
+      S(TI_CE) = S(TI_CW) = 1.0 / (h0 * h0);
+      S(TI_VW) = 1.0;
+    } else if (d->geom == MG_CYL) {
+      S(TI_CE) = xp / (x * h0 * h0);
+      S(TI_CW) = xm / (x * h0 * h0);
+      S(TI_PHI) = (d->ndim == 3) ? 1.0 / (x * x * h2 * h2) : 0.0;
+      S(TI_VW) = x;
+    } else {
+      S(TI_CE) = xp * xp / (x * x * h0 * h0);
+      S(TI_CW) = xm * xm / (x * x * h0 * h0);
+      S(TI_VW) = x * x + h0 * h0 / 12.0;
+    }
+  }
+  for (int j = -1; j <= n1; ++j) {
+    double* T = tj.data() + (j + 1);
+    auto S = [&](int slot) -> double& { return T[(size_t)slot * (n1 + 2)]; };
+    if (d->geom == MG_SPH) {
+      const double th = L.lo[1] + (j + 0.5) * h1;
+      const double s = std::sin(th), c = std::cos(th);
+      auto sface = [&](int jf) { return (jf == 0 || jf == n1) ? 0.0 : std::sin(L.lo[1] + jf * h1); };
+      S(TJ_S) = s;
+      S(TJ_C) = c;
+      S(TJ_IS) = 1.0 / s;
+      S(TJ_IS2) = 1.0 / (s * s);
+      S(TJ_COT) = c / s;
+      S(TJ_TN) = sface(j + 1) / (s * h1 * h1);
+      S(TJ_TS) = sface(j) / (s * h1 * h1);
+      S(TJ_PF) = (d->ndim == 3) ? 1.0 / (s * s * h2 * h2) : 0.0;
+      S(TJ_VW) = s;
+    } else {
+      S(TJ_S) = 1.0;
+      S(TJ_VW) = 1.0;
+    }
+  }
+}
+
+template <typename T>
+LevelView<T> make_view(const mg_grid_desc* d, const Level& L, const T* ti, const T* tj) {
+  LevelView<T> v;
+  v.n0 = L.n[0];
+  v.n1 = L.n[1];
+  v.n2 = L.n[2];
+  v.three = d->ndim == 3;
+  v.geom = d->geom;
+  v.bc = MG_BC_ROBIN;
+  v.mixed = d->mixed_deriv;
+  v.sx = L.sx;
+  v.sy = L.sy;
+  v.off = L.off;
+  v.h0 = (T)L.h[0];
+  v.h1 = (T)L.h[1];
+  v.h2 = (T)L.h[2];
+  v.lo0 = (T)L.lo[0];
+  v.lo1 = (T)L.lo[1];
+  v.lo2 = (T)L.lo[2];
+  v.ih0s = (T)(1.0 / (L.h[0] * L.h[0]));
+  v.ih1s = (T)(1.0 / (L.h[1] * L.h[1]));
+  v.ih2s = (T)(1.0 / (L.h[2] * L.h[2]));
+  const double rN = L.lo[0] + (L.n[0] - 0.5) * L.h[0], rG = L.lo[0] + (L.n[0] + 0.5) * L.h[0];
+  v.robin0 = (T)(rN / rG);
+  v.ti = ti;
+  v.tj = tj;
+  return v;
+}
+
+template <typename T>
+LevelView<T> with_bc(LevelView<T> v, int bc) {
+  v.bc = bc;
+  return v;
+}
+
+// ------------------------------------------------------------- FP64 FAS
+
+const double* fptr(const mg_hierarchy* H, const Eq& e, int l, int c) {
+  if (l == 0 && e.kind == EQ_PSI) return nullptr;  // finest right-hand side is zero
+  return H->L[l].f[c];
+}
+const double* s0ptr(const mg_hierarchy* H, const Eq& e, int l) {
+  return e.kind == EQ_PSI ? H->L[l].s0 : nullptr;
+}
+const double* s1ptr(const mg_hierarchy* H, const Eq& e, int l) {
+  return (e.kind == EQ_PSI || e.has_c) ? H->L[l].s1 : nullptr;
+}
+
+void fill_all64(mg_hierarchy* H, const Eq& e, int l) {
+  Level& L = H->L[l];
+  auto v = with_bc(L.v64, e.bc);
+  for (int c = 0; c < 3; ++c) launch_fill_ghosts(v, L.u[c], c, H->st);
+}
+
+void smooth64(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
+  Level& L = H->L[l];
+  auto v = with_bc(L.v64, e.bc);
+  for (int s = 0; s < nsweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour) {
+      if (e.kind != EQ_VEC) {
+        long tok = prof_begin(H, l, MG_PROF_SMOOTH64_SCALAR, L.cells() / 2);
+        launch_smooth_scalar(v, e.kind, L.u[0], fptr(H, e, l, 0), s0ptr(H, e, l), s1ptr(H, e, l), colour, H->st);
+        prof_end(H, tok);
+      } else {
+        for (int c = 0; c < 3; ++c) {
+          long tok = prof_begin(H, l, MG_PROF_SMOOTH64_VEC, L.cells() / 2);
+          launch_smooth_vec(v, L.u, fptr(H, e, l, c), c, colour, H->st);
+          prof_end(H, tok);
+          launch_fill_ghosts(v, L.u[c], c, H->st);
+        }
+      }
+    }
+  }
+  H->updates += (int64_t)nsweeps * L.cells() * e.ncomp;
+}
+
+void coarse64(mg_hierarchy* H, const Eq& e, int l) {
+  Level& L = H->L[l];
+  auto v = with_bc(L.v64, e.bc);
+  if (e.kind != EQ_VEC) {
+    launch_coarse_scalar(v, e.kind, L.u[0], fptr(H, e, l, 0), s0ptr(H, e, l), s1ptr(H, e, l), COARSE_SWEEPS, H->st);
+  } else {
+    const double* f[3] = {fptr(H, e, l, 0), fptr(H, e, l, 1), fptr(H, e, l, 2)};
+    launch_coarse_vec(v, L.u, f, COARSE_SWEEPS, H->st);
+  }
+}
+
+// FAS V(nu1, nu2): pre-smooth; r = f - L(u); u_H = R u (kept as uh_H);
+// f_H = L_H(u_H) + R r; recurse; u += P(u_H - uh_H); post-smooth.
+void vcycle64(mg_hierarchy* H, const Eq& e, int l) {
+  if (l == H->nlev - 1) {
+    coarse64(H, e, l);
+    return;
+  }
+  Level& L = H->L[l];
+  Level& C = H->L[l + 1];
+  auto v = with_bc(L.v64, e.bc);
+  auto vc = with_bc(C.v64, e.bc);
+  smooth64(H, e, l, H->d.nu1);
+  if (e.kind != EQ_VEC) {
+    launch_residual_scalar(v, e.kind, L.u[0], fptr(H, e, l, 0), s0ptr(H, e, l), s1ptr(H, e, l), L.r[0],
+                           (unsigned long long*)nullptr, 0, H->st);
+  } else {
+    const double* f[3] = {fptr(H, e, l, 0), fptr(H, e, l, 1), fptr(H, e, l, 2)};
+    launch_residual_vec(v, L.u, f, L.r, (unsigned long long*)nullptr, 0, H->st);
+  }
+  for (int c = 0; c < e.ncomp; ++c) {
+    const double* a[4] = {L.u[c], L.r[c], nullptr, nullptr};
+    double* b[4] = {C.u[c], C.f[c], nullptr, nullptr};
+    double* cp[3] = {C.uh[c], nullptr, nullptr};
+    launch_restrict(v, vc, 2, a, b, cp, H->st);
+  }
+  if (e.kind != EQ_VEC) {
+    launch_apply_scalar(vc, e.kind, C.u[0], s0ptr(H, e, l + 1), s1ptr(H, e, l + 1), C.f[0], 1, H->st);
+  } else {
+    fill_all64(H, e, l + 1);
+    launch_apply_vec(vc, C.u, C.f, 1, H->st);
+  }
+  vcycle64(H, e, l + 1);
+  for (int c = 0; c < e.ncomp; ++c)
+    launch_prolong(v, vc, L.u[c], C.u[c], C.uh[c], e.kind == EQ_VEC ? c : -1, H->st);
+  if (e.kind == EQ_VEC) fill_all64(H, e, l);
+  smooth64(H, e, l, H->d.nu2);
+}
+
+double bits_to_double(unsigned long long b) {
+  double x;
+  std::memcpy(&x, &b, sizeof(x));
+  return x;
+}
+
+// Finest-level residual (into L0.r) and its weighted relative norm.
+int finest_norm(mg_hierarchy* H, const Eq& e, double* rel) {
+  Level& L = H->L[0];
+  auto v = with_bc(L.v64, e.bc);
+  CK(cudaMemsetAsync(H->d_red, 0, sizeof(unsigned long long) * 3, H->st));
+  long tok = prof_begin(H, 0, e.kind == EQ_VEC ? MG_PROF_RESID64_VEC : MG_PROF_RESID64_SCALAR, L.cells());
+  if (e.kind != EQ_VEC) {
+    launch_residual_scalar(v, e.kind, L.u[0], fptr(H, e, 0, 0), s0ptr(H, e, 0), s1ptr(H, e, 0), L.r[0], H->d_red,
+                           1, H->st);
+  } else {
+    const double* f[3] = {L.f[0], L.f[1], L.f[2]};
+    launch_residual_vec(v, L.u, f, L.r, H->d_red, 1, H->st);
+  }
+  prof_end(H, tok);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(H->h_red, H->d_red, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, H->st));
+  CK(cudaStreamSynchronize(H->st));
+  const double num = bits_to_double(H->h_red[1]), den = bits_to_double(H->h_red[2]);
+  if (std::isinf(num) || std::isinf(den) || std::isnan(num) || std::isnan(den)) {
+    *rel = NAN;
+  } else {
+    *rel = num / (den > 1e-300 ? den : 1e-300);
+  }
+  return MG_OK;
+}
+
+void restrict_sources(mg_hierarchy* H, const Eq& e) {
+  if (e.kind == EQ_VEC) return;
+  const int nf = e.kind == EQ_PSI ? 2 : (e.has_c ? 1 : 0);
+  if (!nf) return;
+  for (int l = 1; l < H->nlev; ++l) {
+    Level& F = H->L[l - 1];
+    Level& C = H->L[l];
+    const double* a[4] = {e.kind == EQ_PSI ? F.s0 : F.s1, F.s1, nullptr, nullptr};
+    double* b[4] = {e.kind == EQ_PSI ? C.s0 : C.s1, C.s1, nullptr, nullptr};
+    double* cp[3] = {nullptr, nullptr, nullptr};
+    launch_restrict(F.v64, C.v64, nf, a, b, cp, H->st);
+  }
+}
+
+// ------------------------------------------------ FP32 correction cycle
+
+void smooth32(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
+  Level& L = H->L[l];
+  auto v = with_bc(L.v32, e.bc);
+  const float* K = (e.kind == EQ_PSI || e.has_c) ? L.k32 : nullptr;
+  for (int s = 0; s < nsweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      if (e.kind != EQ_VEC) {
+        long tok = prof_begin(H, l, MG_PROF_SMOOTH32_SCALAR, L.cells() / 2);
+        launch_smooth_scalar<float>(v, EQ_LIN, L.e[0], L.f32[0], nullptr, K, colour, H->st);
+        prof_end(H, tok);
+      } else {
+        for (int c = 0; c < 3; ++c) {
+          long tok = prof_begin(H, l, MG_PROF_SMOOTH32_VEC, L.cells() / 2);
+          launch_smooth_vec<float>(v, L.e, L.f32[c], c, colour, H->st);
+          prof_end(H, tok);
+          launch_fill_ghosts<float>(v, L.e[c], c, H->st);
+        }
+      }
+    }
+  H->updates += (int64_t)nsweeps * L.cells() * e.ncomp;
+}
+
+// Coarsest correction equation solved in FP64 on the level's FP64 scratch.
+void coarse32(mg_hierarchy* H, const Eq& e, int l) {
+  Level& L = H->L[l];
+  auto v = with_bc(L.v64, e.bc);
+  const size_t b64 = sizeof(double) * L.ng;
+  for (int c = 0; c < e.ncomp; ++c) {
+    launch_convert<float, double>(L.v32, L.f32[c], L.f[c], H->st);
+    cudaMemsetAsync(L.u[c], 0, b64, H->st);
+  }
+  if (e.kind != EQ_VEC) {
+    const bool hasK = e.kind == EQ_PSI || e.has_c;
+    if (hasK) launch_convert<float, double>(L.v32, L.k32, L.r[0], H->st);
+    launch_coarse_scalar<double>(v, EQ_LIN, L.u[0], L.f[0], nullptr, hasK ? L.r[0] : nullptr, COARSE_SWEEPS,
+                                 H->st);
+  } else {
+    const double* f[3] = {L.f[0], L.f[1], L.f[2]};
+    launch_coarse_vec<double>(v, L.u, f, COARSE_SWEEPS, H->st);
+  }
+  for (int c = 0; c < e.ncomp; ++c) launch_convert<double, float>(L.v64, L.u[c], L.e[c], H->st);
+  if (e.kind == EQ_VEC)
+    for (int c = 0; c < 3; ++c) launch_fill_ghosts<float>(with_bc(L.v32, e.bc), L.e[c], c, H->st);
+}
+
+// Linear correction-scheme V-cycle on (L - K) e = f32, e = 0 initially.
+void vcycle32(mg_hierarchy* H, const Eq& e, int l) {
+  if (l == H->nlev - 1) {
+    coarse32(H, e, l);
+    return;
+  }
+  Level& L = H->L[l];
+  Level& C = H->L[l + 1];
+  auto v = with_bc(L.v32, e.bc);
+  auto vc = with_bc(C.v32, e.bc);
+  const float* K = (e.kind == EQ_PSI || e.has_c) ? L.k32 : nullptr;
+  smooth32(H, e, l, H->d.nu1);
+  if (e.kind != EQ_VEC) {
+    launch_residual_scalar<float>(v, EQ_LIN, L.e[0], L.f32[0], nullptr, K, L.r32[0], nullptr, 0, H->st);
+  } else {
+    const float* f[3] = {L.f32[0], L.f32[1], L.f32[2]};
+    launch_residual_vec<float>(v, L.e, f, L.r32, nullptr, 0, H->st);
+  }
+  for (int c = 0; c < e.ncomp; ++c) {
+    const float* a[4] = {L.r32[c], nullptr, nullptr, nullptr};
+    float* b[4] = {C.f32[c], nullptr, nullptr, nullptr};
+    float* cp[3] = {nullptr, nullptr, nullptr};
+    launch_restrict<float>(v, vc, 1, a, b, cp, H->st);
+    cudaMemsetAsync(C.e[c], 0, sizeof(float) * C.ng, H->st);
+  }
+  vcycle32(H, e, l + 1);
+  for (int c = 0; c < e.ncomp; ++c)
+    launch_prolong<float>(v, vc, L.e[c], C.e[c], nullptr, e.kind == EQ_VEC ? c : -1, H->st);
+  if (e.kind == EQ_VEC)
+    for (int c = 0; c < 3; ++c) launch_fill_ghosts<float>(v, L.e[c], c, H->st);
+  smooth32(H, e, l, H->d.nu2);
+}
+
+void restrict_k32(mg_hierarchy* H) {
+  for (int l = 1; l < H->nlev; ++l) {
+    Level& F = H->L[l - 1];
+    Level& C = H->L[l];
+    const float* a[4] = {F.k32, nullptr, nullptr, nullptr};
+    float* b[4] = {C.k32, nullptr, nullptr, nullptr};
+    float* cp[3] = {nullptr, nullptr, nullptr};
+    launch_restrict<float>(F.v32, C.v32, 1, a, b, cp, H->st);
+  }
+}
+
+// ---------------------------------------------------------- cycle control
+
+int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
+  auto t0 = std::chrono::steady_clock::now();
+  H->updates = 0;
+  const mg_grid_desc& d = H->d;
+  const bool mixed = d.precision == MG_MIXED;
+  Level& L0 = H->L[0];
+  if (e.kind == EQ_VEC) fill_all64(H, e, 0);
+  restrict_sources(H, e);
+  if (mixed && e.kind == EQ_LIN && e.has_c) {
+    launch_convert<double, float>(L0.v64, L0.s1, L0.k32, H->st);
+    restrict_k32(H);
+  }
+  std::vector<double> hist;
+  double rel;
+  int st = finest_norm(H, e, &rel);
+  if (st) return st;
+  hist.push_back(rel);
+  int cyc = 0, status = MG_OK;
+  for (;;) {
+    if (std::isnan(rel)) {
+      status = MG_ERR_NAN;
+      break;
+    }
+    if (rel <= d.tol) break;
+    if (cyc >= d.max_cycles) {
+      status = MG_ERR_NOCONV;
+      break;
+    }
+    if (d.stall_window > 0 && cyc >= d.stall_window && rel > 0.95 * hist[cyc - d.stall_window]) {
+      status = MG_ERR_STALLED;
+      break;
+    }
+    if (!mixed) {
+      vcycle64(H, e, 0);
+    } else {
+      auto v = with_bc(L0.v64, e.bc);
+      for (int c = 0; c < e.ncomp; ++c) {
+        launch_convert<double, float>(v, L0.r[c], L0.f32[c], H->st);
+        CK(cudaMemsetAsync(L0.e[c], 0, sizeof(float) * L0.ng, H->st));
+      }
+      if (e.kind == EQ_PSI) {
+        launch_psi_linearisation(v, L0.u[0], L0.s0, L0.s1, L0.k32, H->st);
+        restrict_k32(H);
+      }
+      vcycle32(H, e, 0);
+      for (int c = 0; c < e.ncomp; ++c) launch_add_correction<float>(v, L0.u[c], L0.e[c], H->st);
+      if (e.kind == EQ_VEC) fill_all64(H, e, 0);
+    }
+    if (e.zero_mean) launch_sub_mean(L0.v64, L0.u[0], H->d_part, NPARTS, H->st);
+    ++cyc;
+    st = finest_norm(H, e, &rel);
+    if (st) return st;
+    hist.push_back(rel);
+  }
+  CK(cudaGetLastError());
+  auto t1 = std::chrono::steady_clock::now();
+  if (rep) {
+    rep->status = status;
+    rep->cycles = cyc;
+    rep->rel = rel;
+    rep->nhist = (int)std::min<size_t>(hist.size(), MG_HIST);
+    for (int q = 0; q < rep->nhist; ++q) rep->hist[q] = hist[q];
+    rep->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    rep->cell_updates = H->updates;
+  }
+  return status;
+}
+
+// ------------------------------------------------------------ staging
+
+long interior_cells(const mg_hierarchy* H) { return H->L[0].cells(); }
+
+int stage_get(mg_hierarchy* H, int slot, double** out) {
+  while ((int)H->stage.size() <= slot) H->stage.push_back(nullptr);
+  if (!H->stage[slot]) {
+    double* p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * interior_cells(H)) != cudaSuccess)
+      return fail(MG_ERR_OOM, "staging allocation failed");
+    H->stage[slot] = p;
+  }
+  *out = H->stage[slot];
+  return MG_OK;
+}
+
+// Host -> staged device copy (src may be null: the slot is left alone).
+int stage_in(mg_hierarchy* H, int slot, const double* host, double** dev) {
+  if (!host) {
+    *dev = nullptr;
+    return MG_OK;
+  }
+  int st = stage_get(H, slot, dev);
+  if (st) return st;
+  CK(cudaMemcpyAsync(*dev, host, sizeof(double) * interior_cells(H), cudaMemcpyHostToDevice, H->st));
+  return MG_OK;
+}
+int stage_out(mg_hierarchy* H, const double* dev, double* host) {
+  if (!host) return MG_OK;
+  CK(cudaMemcpyAsync(host, dev, sizeof(double) * interior_cells(H), cudaMemcpyDeviceToHost, H->st));
+  return MG_OK;
+}
+
+void copy_in(mg_hierarchy* H, const double* src, double* dst, double shift = 0.0) {
+  launch_copy_in<double, double>(H->L[0].v64, src, dst, shift, H->st);
+}
+void copy_out(mg_hierarchy* H, const double* src, double* dst, double shift = 0.0) {
+  launch_copy_out<double, double>(H->L[0].v64, src, dst, shift, H->st);
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+const char* mg_strerror(int s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID: return "invalid argument";
+    case MG_ERR_OOM: return "out of device memory";
+    case MG_ERR_NOCONV: return "not converged";
+    case MG_ERR_STALLED: return "stalled";
+    case MG_ERR_NAN: return "non-finite value";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_BUSY: return "busy";
+    case MG_ERR_NOTFOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+const char* mg_last_error(void) { return g_last_error; }
+
+int mg_hierarchy_bytes(const mg_grid_desc* desc, size_t* bytes) {
+  int st = validate(desc);
+  if (st) return st;
+  if (!bytes) return fail(MG_ERR_INVALID, "null output");
+  *bytes = layout(nullptr, desc, nullptr);
+  return MG_OK;
+}
+
+int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarchy** out) {
+  int st = validate(desc);
+  if (st) return st;
+  if (!out) return fail(MG_ERR_INVALID, "null output");
+  mg_hierarchy* H = new (std::nothrow) mg_hierarchy();
+  if (!H) return fail(MG_ERR_OOM, "host allocation failed");
+  H->d = *desc;
+  if (H->d.ndim == 2) {
+    H->d.n[2] = 1;
+    H->d.lo[2] = 0.0;
+    H->d.hi[2] = 1.0;
+  }
+  H->st = (cudaStream_t)cuda_stream;
+  int n[MAX_LEVELS][3];
+  double h[MAX_LEVELS][3];
+  H->nlev = level_sizes(&H->d, n, h);
+  const size_t bytes = layout(nullptr, &H->d, nullptr);
+  if (cudaMalloc(&H->arena, bytes) != cudaSuccess) {
+    delete H;
+    return fail(MG_ERR_OOM, "arena allocation failed");
+  }
+  H->arena_bytes = bytes;
+  layout(H, &H->d, H->arena);
+  if (cudaMallocHost(&H->h_red, sizeof(unsigned long long) * 8) != cudaSuccess) {
+    cudaFree(H->arena);
+    delete H;
+    return fail(MG_ERR_OOM, "pinned allocation failed");
+  }
+  cudaMemsetAsync(H->arena, 0, bytes, H->st);
+  const int three = H->d.ndim == 3;
+  for (int l = 0; l < H->nlev; ++l) {
+    Level& L = H->L[l];
+    for (int k = 0; k < 3; ++k) {
+      L.n[k] = n[l][k];
+      L.h[k] = h[l][k];
+      L.lo[k] = H->d.lo[k];
+    }
+    L.sx = L.n[0] + 2;
+    L.sy = L.sx * (L.n[1] + 2);
+    L.off = 1 + L.sx + three * L.sy;
+    L.ng = L.sy * (L.n[2] + 2 * three);
+    std::vector<double> ti, tj;
+    make_tables(&H->d, L, ti, tj);
+    std::vector<float> ti32(ti.begin(), ti.end()), tj32(tj.begin(), tj.end());
+    CK(cudaMemcpyAsync(L.ti64, ti.data(), sizeof(double) * ti.size(), cudaMemcpyHostToDevice, H->st));
+    CK(cudaMemcpyAsync(L.tj64, tj.data(), sizeof(double) * tj.size(), cudaMemcpyHostToDevice, H->st));
+    CK(cudaMemcpyAsync(L.ti32, ti32.data(), sizeof(float) * ti32.size(), cudaMemcpyHostToDevice, H->st));
+    CK(cudaMemcpyAsync(L.tj32, tj32.data(), sizeof(float) * tj32.size(), cudaMemcpyHostToDevice, H->st));
+    CK(cudaStreamSynchronize(H->st));  // host tables go out of scope
+    L.v64 = make_view<double>(&H->d, L, L.ti64, L.tj64);
+    L.v32 = make_view<float>(&H->d, L, L.ti32, L.tj32);
+  }
+  *out = H;
+  return MG_OK;
+}
+
+uint64_t mg_kernel_launches(void) { return (uint64_t)launch_count(); }
+
+int mg_profile_enable(mg_hierarchy* H, int enable) {
+  if (!H) return fail(MG_ERR_INVALID, "null hierarchy");
+  CK(cudaStreamSynchronize(H->st));
+  H->prof_on = enable != 0;
+  H->ev_used = 0;
+  return MG_OK;
+}
+
+int mg_profile_read(mg_hierarchy* H, int klass, int64_t* launches, double* ms, int64_t* cells) {
+  if (!H || !launches || !ms || !cells || klass < 0 || klass >= MG_PROF_NCLASS)
+    return fail(MG_ERR_INVALID, "bad argument");
+  CK(cudaStreamSynchronize(H->st));
+  int64_t n = 0, c = 0;
+  double t = 0.0;
+  for (size_t pr = 0; pr < H->ev_used / 2; ++pr) {
+    if (H->ev_cls[pr] != klass) continue;
+    float m = 0.f;
+    CK(cudaEventElapsedTime(&m, H->ev[2 * pr], H->ev[2 * pr + 1]));
+    ++n;
+    c += H->ev_cells[pr];
+    t += m;
+  }
+  *launches = n;
+  *ms = t;
+  *cells = c;
+  return MG_OK;
+}
+
+int mg_destroy_hierarchy(mg_hierarchy* H) {
+  if (!H) return MG_OK;
+  cudaStreamSynchronize(H->st);
+  for (cudaEvent_t e : H->ev) cudaEventDestroy(e);
+  for (double* p : H->stage) cudaFree(p);
+  cudaFree(H->arena);
+  cudaFreeHost(H->h_red);
+  delete H;
+  return MG_OK;
+}
+
+int mg_num_levels(const mg_hierarchy* H, int* nlev) {
+  if (!H || !nlev) return fail(MG_ERR_INVALID, "null argument");
+  *nlev = H->nlev;
+  return MG_OK;
+}
+
+int mg_solve_scalar(mg_hierarchy* H, int kind, int bc, int zero_mean, const double* U, const double* A2,
+                    const double* c, const double* f, double* u, mg_solve_report* rep) {
+  if (!H || !u) return fail(MG_ERR_INVALID, "null argument");
+  if (kind != MG_EQ_PSI && kind != MG_EQ_LIN) return fail(MG_ERR_INVALID, "bad equation kind");
+  if (bc < MG_BC_ROBIN || bc > MG_BC_NEUMANN) return fail(MG_ERR_INVALID, "bad boundary condition");
+  if (kind == MG_EQ_PSI && (!U || !A2)) return fail(MG_ERR_INVALID, "psi equation needs U and A2");
+  if (kind == MG_EQ_LIN && !f) return fail(MG_ERR_INVALID, "linear equation needs f");
+  Level& L0 = H->L[0];
+  Eq e{kind, bc, zero_mean ? 1 : 0, 1, kind == MG_EQ_LIN && c != nullptr};
+  copy_in(H, u, L0.u[0]);
+  if (kind == MG_EQ_PSI) {
+    copy_in(H, U, L0.s0);
+    copy_in(H, A2, L0.s1);
+  } else {
+    if (c) copy_in(H, c, L0.s1);
+    copy_in(H, f, L0.f[0]);
+  }
+  int st = run_solve(H, e, rep);
+  copy_out(H, L0.u[0], u);
+  CK(cudaStreamSynchronize(H->st));
+  return st;
+}
+
+int mg_solve_vector(mg_hierarchy* H, int bc, const double* f[3], double* V[3], mg_solve_report* rep) {
+  if (!H || !f || !V) return fail(MG_ERR_INVALID, "null argument");
+  for (int c = 0; c < 3; ++c)
+    if (!f[c] || !V[c]) return fail(MG_ERR_INVALID, "null component");
+  Level& L0 = H->L[0];
+  Eq e{MG_EQ_VEC, bc, 0, 3, false};
+  for (int c = 0; c < 3; ++c) {
+    copy_in(H, V[c], L0.u[c]);
+    copy_in(H, f[c], L0.f[c]);
+  }
+  int st = run_solve(H, e, rep);
+  for (int c = 0; c < 3; ++c) copy_out(H, L0.u[c], V[c]);
+  CK(cudaStreamSynchronize(H->st));
+  return st;
+}
+
+int mg_solve_cfc(mg_hierarchy* H, const mg_cfc_sources* src, mg_cfc_fields* io, int flags, mg_cfc_report* rep) {
+  if (!H || !src || !io) return fail(MG_ERR_INVALID, "null argument");
+  auto t0 = std::chrono::steady_clock::now();
+  const bool psi_only = flags & MG_CFC_PSI_ONLY;
+  const bool host = flags & MG_HOST_POINTERS;
+  if (!src->U || !io->psi) return fail(MG_ERR_INVALID, "missing U or psi");
+  if (!psi_only) {
+    if (!src->S || !io->alpha) return fail(MG_ERR_INVALID, "missing S or alpha");
+    for (int c = 0; c < 3; ++c)
+      if (!src->Si[c] || !io->beta[c] || !io->X[c]) return fail(MG_ERR_INVALID, "missing vector component");
+  }
+  // device views of the caller's arrays
+  const double *U = src->U, *S = src->S, *Si[3] = {src->Si[0], src->Si[1], src->Si[2]};
+  double *psi = io->psi, *alpha = io->alpha, *beta[3] = {io->beta[0], io->beta[1], io->beta[2]},
+         *X[3] = {io->X[0], io->X[1], io->X[2]};
+  int st = MG_OK;
+  if (host) {
+    double* dv;
+    if ((st = stage_in(H, 0, src->U, &dv))) return st;
+    U = dv;
+    if ((st = stage_in(H, 1, io->psi, &psi))) return st;
+    if (!psi_only) {
+      if ((st = stage_in(H, 2, src->S, &dv))) return st;
+      S = dv;
+      if ((st = stage_in(H, 3, io->alpha, &alpha))) return st;
+      for (int c = 0; c < 3; ++c) {
+        if ((st = stage_in(H, 4 + c, src->Si[c], &dv))) return st;
+        Si[c] = dv;
+        if ((st = stage_in(H, 7 + c, io->beta[c], &beta[c]))) return st;
+        if ((st = stage_in(H, 10 + c, io->X[c], &X[c]))) return st;
+      }
+    }
+  }
+  Level& L0 = H->L[0];
+  const LevelView<double>& v = L0.v64;
+  mg_solve_report* reps = rep ? rep->eq : nullptr;
+  if (rep) std::memset(rep, 0, sizeof(*rep));
+  const size_t b64 = sizeof(double) * L0.ng;
+  copy_in(H, U, H->Ug);
+  if (!psi_only) {
+    copy_in(H, S, H->Sg);
+    for (int c = 0; c < 3; ++c) copy_in(H, Si[c], H->Sig[c]);
+    // Step 1: lap X + 1/3 grad div X = 8 pi S_i
+    Eq ex{MG_EQ_VEC, MG_BC_DIRICHLET, 0, 3, false};
+    for (int c = 0; c < 3; ++c) {
+      copy_in(H, X[c], L0.u[c]);
+      launch_scale_into(v, H->Sig[c], 8.0 * PI, L0.f[c], H->st);
+    }
+    st = run_solve(H, ex, reps ? &reps[0] : nullptr);
+    for (int c = 0; c < 3; ++c) {
+      copy_out(H, L0.u[c], X[c]);
+      CK(cudaMemcpyAsync(H->Xg[c], L0.u[c], b64, cudaMemcpyDeviceToDevice, H->st));
+      launch_fill_ghosts(with_bc(v, MG_BC_DIRICHLET), H->Xg[c], c, H->st);
+    }
+    if (st) goto out;
+    // Step 2: A2 = A~_ij A~^ij (into the psi equation's s1)
+    launch_xcfc_a2(v, H->Xg, L0.s1, H->st);
+  } else {
+    CK(cudaMemsetAsync(L0.s1, 0, b64, H->st));
+  }
+  {
+    // Step 3: psi equation for delta = psi - 1
+    Eq ep{MG_EQ_PSI, MG_BC_ROBIN, 0, 1, false};
+    copy_in(H, psi, L0.u[0], -1.0);
+    CK(cudaMemcpyAsync(L0.s0, H->Ug, b64, cudaMemcpyDeviceToDevice, H->st));
+    st = run_solve(H, ep, reps ? &reps[1] : nullptr);
+    copy_out(H, L0.u[0], psi, 1.0);
+    CK(cudaMemcpyAsync(H->dpsi, L0.u[0], b64, cudaMemcpyDeviceToDevice, H->st));
+    if (st || psi_only) goto out;
+    // Step 5: alpha psi equation, coefficient c = 2 pi (U + 2 S) psi^-2 + 7/8 A2 psi^-8
+    launch_xcfc_alpha_coef(v, H->Ug, H->Sg, L0.s1, H->dpsi, L0.f[0], H->st);
+    CK(cudaMemcpyAsync(L0.s1, L0.f[0], b64, cudaMemcpyDeviceToDevice, H->st));
+    launch_xcfc_ap_init(v, alpha, H->dpsi, L0.u[0], H->st);
+    Eq ea{MG_EQ_LIN, MG_BC_ROBIN, 0, 1, true};
+    st = run_solve(H, ea, reps ? &reps[2] : nullptr);
+    CK(cudaMemcpyAsync(H->dap, L0.u[0], b64, cudaMemcpyDeviceToDevice, H->st));
+    launch_xcfc_alpha_out(v, H->dap, H->dpsi, alpha, H->st);
+    if (st) goto out;
+    // Step 6: shift, source 16 pi alpha psi^-6 S_i + 2 A~_ij grad_j(alpha psi^-6)
+    launch_fill_ghosts(with_bc(v, MG_BC_ROBIN), H->dpsi, -1, H->st);
+    launch_fill_ghosts(with_bc(v, MG_BC_ROBIN), H->dap, -1, H->st);
+    launch_xcfc_beta_rhs(v, H->Xg, H->dpsi, H->dap, H->sg, H->Sig, L0.f, H->st);
+    Eq eb{MG_EQ_VEC, MG_BC_DIRICHLET, 0, 3, false};
+    for (int c = 0; c < 3; ++c) copy_in(H, beta[c], L0.u[c]);
+    st = run_solve(H, eb, reps ? &reps[3] : nullptr);
+    for (int c = 0; c < 3; ++c) copy_out(H, L0.u[c], beta[c]);
+  }
+out:
+  if (host) {
+    int s2 = stage_out(H, psi, io->psi);
+    if (!s2 && !psi_only) {
+      s2 = stage_out(H, alpha, io->alpha);
+      for (int c = 0; c < 3 && !s2; ++c) {
+        s2 = stage_out(H, beta[c], io->beta[c]);
+        if (!s2) s2 = stage_out(H, X[c], io->X[c]);
+      }
+    }
+    if (s2 && !st) st = s2;
+  }
+  CK(cudaStreamSynchronize(H->st));
+  CK(cudaGetLastError());
+  if (rep) rep->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+int mg_clean_divB(mg_hierarchy* H, double* B[3], double* phi_out, int flags, mg_divb_report* rep) {
+  if (!H || !B) return fail(MG_ERR_INVALID, "null argument");
+  if (H->d.geom != MG_CART) return fail(MG_ERR_INVALID, "divergence cleaning needs a Cartesian grid");
+  const int nd = H->d.ndim;
+  for (int c = 0; c < nd; ++c)
+    if (!B[c]) return fail(MG_ERR_INVALID, "null B component");
+  const bool host = flags & MG_HOST_POINTERS;
+  double* Bd[3] = {B[0], B[1], nd == 3 ? B[2] : B[0]};
+  int st = MG_OK;
+  if (host)
+    for (int c = 0; c < nd; ++c)
+      if ((st = stage_in(H, c, B[c], &Bd[c]))) return st;
+  if (nd == 2) Bd[2] = Bd[0];
+  Level& L0 = H->L[0];
+  const LevelView<double>& v = L0.v64;
+  const double N = (double)L0.cells();
+  auto norms = [&](double* mx, double* l2) -> int {
+    CK(cudaMemsetAsync(H->d_red, 0, sizeof(unsigned long long), H->st));
+    launch_div_norms(v, L0.r[0], H->d_part, NPARTS, H->d_red, H->st);
+    std::vector<double> part(NPARTS);
+    CK(cudaMemcpyAsync(H->h_red, H->d_red, sizeof(unsigned long long), cudaMemcpyDeviceToHost, H->st));
+    CK(cudaMemcpyAsync(part.data(), H->d_part, sizeof(double) * NPARTS, cudaMemcpyDeviceToHost, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    double s = 0.0;
+    for (double x : part) s += x;
+    *mx = bits_to_double(H->h_red[0]);
+    *l2 = std::sqrt(s / N);
+    return MG_OK;
+  };
+  double mb, lb, ma, la;
+  launch_div_central(v, Bd, L0.r[0], H->d_part, NPARTS, H->st);
+  launch_sub_mean_into(v, L0.r[0], H->d_part, NPARTS, L0.f[0], H->st);
+  if ((st = norms(&mb, &lb))) return st;
+  CK(cudaMemsetAsync(L0.u[0], 0, sizeof(double) * L0.ng, H->st));
+  Eq e{MG_EQ_LIN, MG_BC_NEUMANN, 1, 1, false};
+  st = run_solve(H, e, rep ? &rep->solve : nullptr);
+  launch_grad_update(v, L0.u[0], Bd, H->st);
+  launch_div_central(v, Bd, L0.r[0], H->d_part, NPARTS, H->st);
+  int s2 = norms(&ma, &la);
+  if (s2) return s2;
+  if (phi_out) {
+    double* pd = phi_out;
+    if (host && (s2 = stage_get(H, 3, &pd))) return s2;
+    copy_out(H, L0.u[0], pd);
+    if (host && (s2 = stage_out(H, pd, phi_out))) return s2;
+  }
+  if (host)
+    for (int c = 0; c < nd; ++c)
+      if ((s2 = stage_out(H, Bd[c], B[c]))) return s2;
+  CK(cudaStreamSynchronize(H->st));
+  if (rep) {
+    rep->max_div_before = mb;
+    rep->l2_div_before = lb;
+    rep->max_div_after = ma;
+    rep->l2_div_after = la;
+  }
+  return st;
+}
+
+int mg_apply_operator(mg_hierarchy* H, int kind, int bc, const double* u[3], const double* U, const double* A2,
+                      const double* c, double* out[3]) {
+  if (!H || !u || !out) return fail(MG_ERR_INVALID, "null argument");
+  Level& L0 = H->L[0];
+  auto v = with_bc(L0.v64, bc);
+  if (kind == MG_EQ_VEC) {
+    for (int q = 0; q < 3; ++q) {
+      copy_in(H, u[q], L0.u[q]);
+      launch_fill_ghosts(v, L0.u[q], q, H->st);
+    }
+    launch_apply_vec(v, L0.u, L0.r, 0, H->st);
+    for (int q = 0; q < 3; ++q) copy_out(H, L0.r[q], out[q]);
+  } else if (kind == MG_EQ_PSI || kind == MG_EQ_LIN) {
+    copy_in(H, u[0], L0.u[0]);
+    if (kind == MG_EQ_PSI) {
+      if (!U || !A2) return fail(MG_ERR_INVALID, "psi operator needs U and A2");
+      copy_in(H, U, L0.s0);
+      copy_in(H, A2, L0.s1);
+    } else if (c) {
+      copy_in(H, c, L0.s1);
+    }
+    launch_apply_scalar(v, kind, L0.u[0], L0.s0, (kind == MG_EQ_PSI || c) ? L0.s1 : nullptr, L0.r[0], 0, H->st);
+    copy_out(H, L0.r[0], out[0]);
+  } else {
+    return fail(MG_ERR_INVALID, "bad equation kind");
+  }
+  CK(cudaStreamSynchronize(H->st));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+int mg_smooth(mg_hierarchy* H, int kind, int bc, int nsweeps, double* u[3], const double* f[3], const double* U,
+              const double* A2, const double* c) {
+  if (!H || !u || nsweeps < 0) return fail(MG_ERR_INVALID, "bad argument");
+  Level& L0 = H->L[0];
+  const int nc = kind == MG_EQ_VEC ? 3 : 1;
+  Eq e{kind, bc, 0, nc, kind == MG_EQ_LIN && c != nullptr};
+  for (int q = 0; q < nc; ++q) {
+    copy_in(H, u[q], L0.u[q]);
+    if (f && f[q]) copy_in(H, f[q], L0.f[q]);
+    else cudaMemsetAsync(L0.f[q], 0, sizeof(double) * L0.ng, H->st);
+  }
+  if (kind == MG_EQ_PSI) {
+    copy_in(H, U, L0.s0);
+    copy_in(H, A2, L0.s1);
+  } else if (c) {
+    copy_in(H, c, L0.s1);
+  }
+  if (kind == MG_EQ_VEC) fill_all64(H, e, 0);
+  smooth64(H, e, 0, nsweeps);
+  for (int q = 0; q < nc; ++q) copy_out(H, L0.u[q], u[q]);
+  CK(cudaStreamSynchronize(H->st));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+int mg_compute_a2(mg_hierarchy* H, const double* X[3], double* A2) {
+  if (!H || !X || !A2) return fail(MG_ERR_INVALID, "null argument");
+  Level& L0 = H->L[0];
+  auto v = with_bc(L0.v64, MG_BC_DIRICHLET);
+  for (int c = 0; c < 3; ++c) {
+    copy_in(H, X[c], H->Xg[c]);
+    launch_fill_ghosts(v, H->Xg[c], c, H->st);
+  }
+  launch_xcfc_a2(v, H->Xg, L0.r[0], H->st);
+  copy_out(H, L0.r[0], A2);
+  CK(cudaStreamSynchronize(H->st));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+int mg_divergence(mg_hierarchy* H, const double* B[3], double* div) {
+  if (!H || !B || !div) return fail(MG_ERR_INVALID, "null argument");
+  if (H->d.geom != MG_CART) return fail(MG_ERR_INVALID, "Cartesian only");
+  Level& L0 = H->L[0];
+  double* Bd[3] = {(double*)B[0], (double*)B[1], (double*)(H->d.ndim == 3 ? B[2] : B[0])};
+  launch_div_central(L0.v64, Bd, L0.r[0], H->d_part, NPARTS, H->st);
+  copy_out(H, L0.r[0], div);
+  CK(cudaStreamSynchronize(H->st));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+int mg_restrict(mg_hierarchy* H, const double* fine, double* coarse) {
+  if (!H || !fine || !coarse) return fail(MG_ERR_INVALID, "null argument");
+  if (H->nlev < 2) return fail(MG_ERR_INVALID, "hierarchy has one level");
+  Level& F = H->L[0];
+  Level& C = H->L[1];
+  copy_in(H, fine, F.r[0]);
+  const double* a[4] = {F.r[0], nullptr, nullptr, nullptr};
+  double* b[4] = {C.r[0], nullptr, nullptr, nullptr};
+  double* cp[3] = {nullptr, nullptr, nullptr};
+  launch_restrict(F.v64, C.v64, 1, a, b, cp, H->st);
+  launch_copy_out<double, double>(C.v64, C.r[0], coarse, 0.0, H->st);
+  CK(cudaStreamSynchronize(H->st));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+int mg_prolong_add(mg_hierarchy* H, int bc, const double* coarse_e, double* fine) {
+  if (!H || !coarse_e || !fine) return fail(MG_ERR_INVALID, "null argument");
+  if (H->nlev < 2) return fail(MG_ERR_INVALID, "hierarchy has one level");
+  Level& F = H->L[0];
+  Level& C = H->L[1];
+  launch_copy_in<double, double>(C.v64, coarse_e, C.r[0], 0.0, H->st);
+  copy_in(H, fine, F.u[0]);
+  launch_prolong(with_bc(F.v64, bc), with_bc(C.v64, bc), F.u[0], C.r[0], (const double*)nullptr, -1, H->st);
+  copy_out(H, F.u[0], fine);
+  CK(cudaStreamSynchronize(H->st));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,570 @@
+// Grid-wide multigrid kernels (red-black Newton-Gauss-Seidel, residual with
+// fused norms, FAS coarse right-hand side, ghost fill, volume-weighted
+// restriction, Kwak prolongation) and the single-block coarsest solver, with
+// their host-side launchers.  Sec. 2.7 of the paper.
+#include <atomic>
+
+#include "mg_internal.h"
+#include "mg_kernels.cuh"
+
+namespace gmg {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+static inline dim3 block_for(int three) { return three ? dim3(32, 4, 2) : dim3(32, 8, 1); }
+static inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ smoothers
+
+// One colour of the red-black sweep: cells with (i + j + k) % 2 == colour.
+// Thread t of a row handles i = 2 t + ((j + k + colour) & 1).
+template <typename T, int G, int KIND>
+__global__ void k_smooth_scalar(LevelView<T> L, T* __restrict__ u, const T* __restrict__ f,
+                                const T* __restrict__ s0, const T* __restrict__ s1, int colour) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (2 * t >= L.n0 || j >= L.n1 || k >= L.n2) return;
+  const int i = 2 * t + ((j + k + colour) & 1);
+  scalar_update<T, G, KIND>(L, u, f, s0, s1, i, j, k);
+}
+
+template <typename T, int G>
+__global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
+                             const T* __restrict__ f, int comp, int colour) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (2 * t >= L.n0 || j >= L.n1 || k >= L.n2) return;
+  const int i = 2 * t + ((j + k + colour) & 1);
+  vec_update<T, G>(L, A, B, C, f, comp, i, j, k);
+}
+
+template <typename T>
+__global__ void k_fill_ghosts(LevelView<T> L, T* __restrict__ u, int comp) {
+  const long n = ghost_count(L);
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x)
+    fill_one_ghost(L, u, comp, g);
+}
+
+// ------------------------------------------------------------ residuals
+
+// r = f - L(u) on every interior cell.  red (if non-null) receives
+// max |r| (slot 0) and, when weighted, max |w r| (slot 1), max |w S| (slot 2).
+template <typename T, int G, int KIND>
+__global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const T* __restrict__ f,
+                                  const T* __restrict__ s0, const T* __restrict__ s1, T* __restrict__ r,
+                                  unsigned long long* red, int weighted) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  double m[3] = {0.0, 0.0, 0.0};
+  if (i < L.n0 && j < L.n1 && k < L.n2) {
+    const long p = L.idx(i, j, k);
+    T D;
+    const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
+    const T rv = (f ? f[p] : T(0)) - Lu;
+    if (r) r[p] = rv;
+    m[0] = fabs((double)rv);
+    if (weighted) {
+      const double w = (double)norm_weight(L, i, j);
+      m[1] = fabs(w * (double)rv);
+      m[2] = fabs(w * (double)scalar_source<T, KIND>(u, s0, s1, f, p));
+    }
+  }
+  if (red) block_max_atomic<3>(m, red);
+}
+
+template <typename T, int G>
+__global__ void k_residual_vec(LevelView<T> L, const T* __restrict__ A, const T* __restrict__ B,
+                               const T* __restrict__ C, const T* __restrict__ f0, const T* __restrict__ f1,
+                               const T* __restrict__ f2, T* __restrict__ r0, T* __restrict__ r1,
+                               T* __restrict__ r2, unsigned long long* red, int weighted) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  double m[3] = {0.0, 0.0, 0.0};
+  if (i < L.n0 && j < L.n1 && k < L.n2) {
+    const long p = L.idx(i, j, k);
+    const double w = weighted ? (double)norm_weight(L, i, j) : 1.0;
+    const T* fs[3] = {f0, f1, f2};
+    T* rs[3] = {r0, r1, r2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T D;
+      const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+      const T fv = fs[c] ? fs[c][p] : T(0);
+      const T rv = fv - Lu;
+      if (rs[c]) rs[c][p] = rv;
+      m[0] = fmax(m[0], fabs((double)rv));
+      if (weighted) {
+        m[1] = fmax(m[1], fabs(w * (double)rv));
+        m[2] = fmax(m[2], fabs(w * (double)fv));
+      }
+      if (rv != rv) m[0] = m[1] = INFINITY;
+    }
+  }
+  if (red) block_max_atomic<3>(m, red);
+}
+
+// f <- L(u) + f (the FAS coarse right-hand side after restriction placed
+// R r into f), or out = L(u) when add == 0.
+template <typename T, int G, int KIND>
+__global__ void k_apply_scalar(LevelView<T> L, const T* __restrict__ u, const T* __restrict__ s0,
+                               const T* __restrict__ s1, T* __restrict__ out, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= L.n0 || j >= L.n1 || k >= L.n2) return;
+  const long p = L.idx(i, j, k);
+  T D;
+  const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
+  out[p] = add ? out[p] + Lu : Lu;
+}
+
+template <typename T, int G>
+__global__ void k_apply_vec(LevelView<T> L, const T* __restrict__ A, const T* __restrict__ B,
+                            const T* __restrict__ C, T* __restrict__ o0, T* __restrict__ o1,
+                            T* __restrict__ o2, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= L.n0 || j >= L.n1 || k >= L.n2) return;
+  const long p = L.idx(i, j, k);
+  T* os[3] = {o0, o1, o2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T D;
+    const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+    os[c][p] = add ? os[c][p] + Lu : Lu;
+  }
+}
+
+// --------------------------------------------------------- grid transfer
+
+// Piecewise-constant restriction (Sec. 2.7.3): coarse = volume-weighted mean
+// of the 2^d children (Cartesian: the equal-weight 1/4, 1/8 stencil).
+// Restricts up to 4 fields; copy (if non-null) receives a second copy of
+// field 0 (the FAS u_H kept for the correction).
+template <typename T>
+__global__ void k_restrict(LevelView<T> F, LevelView<T> Cv, int nf, const T* __restrict__ a0,
+                           const T* __restrict__ a1, const T* __restrict__ a2, const T* __restrict__ a3,
+                           T* __restrict__ b0, T* __restrict__ b1, T* __restrict__ b2, T* __restrict__ b3,
+                           T* __restrict__ copy0, T* __restrict__ copy1, T* __restrict__ copy2) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z * blockDim.z + threadIdx.z;
+  if (I >= Cv.n0 || J >= Cv.n1 || K >= Cv.n2) return;
+  const T* as[4] = {a0, a1, a2, a3};
+  T* bs[4] = {b0, b1, b2, b3};
+  T* cs[3] = {copy0, copy1, copy2};
+  T wi[2], wj[2];
+  wi[0] = F.TI(TI_VW, 2 * I);
+  wi[1] = F.TI(TI_VW, 2 * I + 1);
+  wj[0] = F.TJ(TJ_VW, 2 * J);
+  wj[1] = F.TJ(TJ_VW, 2 * J + 1);
+  T wsum = T(0);
+  const int nk = F.three ? 2 : 1;
+  for (int dk = 0; dk < nk; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) wsum += wi[di] * wj[dj];
+  const T inv = T(1) / wsum;
+  const long q = Cv.idx(I, J, K);
+  for (int m = 0; m < nf; ++m) {
+    T s = T(0);
+    for (int dk = 0; dk < nk; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di)
+          s += wi[di] * wj[dj] * as[m][F.idx(2 * I + di, 2 * J + dj, F.three ? 2 * K + dk : 0)];
+    const T v = s * inv;
+    bs[m][q] = v;
+    if (m < 3 && cs[m]) cs[m][q] = v;
+  }
+}
+
+// Kwak prolongation (Sec. 2.7.3, Fig. kwak) of e = uH - uhH (uhH may be
+// null: e = uH), added into the fine field u.  Each fine cell takes its
+// parent and, per dimension, the parent's face neighbour on its side:
+// 2D 1/4 (2 e_c + e_x + e_y), 3D 1/4 (e_c + e_x + e_y + e_z).
+template <typename T>
+__global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, const T* __restrict__ uH,
+                          const T* __restrict__ uhH, int comp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
+  const int I = i >> 1, J = j >> 1, K = F.three ? (k >> 1) : 0;
+  const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
+  const T ec = coarse_corr(Cv, uH, uhH, comp, I, J, K);
+  const T ex = coarse_corr(Cv, uH, uhH, comp, I + si, J, K);
+  const T ey = coarse_corr(Cv, uH, uhH, comp, I, J + sj, K);
+  T add;
+  if (F.three) {
+    const T ez = coarse_corr(Cv, uH, uhH, comp, I, J, K + sk);
+    add = T(0.25) * (ec + ex + ey + ez);
+  } else {
+    add = T(0.25) * (T(2) * ec + ex + ey);
+  }
+  u[F.idx(i, j, k)] += add;
+}
+
+// --------------------------------------------------------- coarsest grid
+
+// Newton-Gauss-Seidel as the coarsest-grid solver (Sec. 2.7.2): one block
+// sweeps until the max residual falls below 1e-12 of its initial value or
+// 100 sweeps.  Storage type T, arithmetic in T.
+template <typename T, int G, int KIND>
+__global__ void k_coarse_scalar(LevelView<T> L, T* __restrict__ u, const T* __restrict__ f,
+                                const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps) {
+  __shared__ double red[32];
+  __shared__ double r0s;
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  const int tid = threadIdx.x;
+  auto resmax = [&]() -> double {
+    double m = 0.0;
+    for (long q = tid; q < n; q += blockDim.x) {
+      const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+      const long p = L.idx(i, j, k);
+      T D;
+      const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
+      const double rv = fabs((double)((f ? f[p] : T(0)) - Lu));
+      m = (rv > m || rv != rv) ? rv : m;
+    }
+    m = warp_max(m);
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
+    __syncthreads();
+    return b;
+  };
+  const double r0 = resmax();
+  if (tid == 0) r0s = r0;
+  __syncthreads();
+  if (!(r0s > 0.0)) return;
+  for (int it = 0; it < max_sweeps; ++it) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const long nh = n / 2;
+      for (long q = tid; q < nh; q += blockDim.x) {
+        const int t = (int)(q % (L.n0 / 2)), j = (int)((q / (L.n0 / 2)) % L.n1),
+                  k = (int)(q / ((long)(L.n0 / 2) * L.n1));
+        const int i = 2 * t + ((j + k + colour) & 1);
+        scalar_update<T, G, KIND>(L, u, f, s0, s1, i, j, k);
+      }
+      __syncthreads();
+    }
+    const double r = resmax();
+    if (!(r > 1e-12 * r0s)) break;
+  }
+}
+
+template <typename T, int G>
+__global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
+                             const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
+                             int max_sweeps) {
+  __shared__ double red[32];
+  __shared__ double r0s;
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  const long ng = ghost_count(L);
+  const int tid = threadIdx.x;
+  T* V[3] = {A, B, C};
+  const T* fs[3] = {f0, f1, f2};
+  auto fill = [&](int c) {
+    for (long g = tid; g < ng; g += blockDim.x) fill_one_ghost(L, V[c], c, g);
+    __syncthreads();
+  };
+  auto resmax = [&]() -> double {
+    double m = 0.0;
+    for (long q = tid; q < n; q += blockDim.x) {
+      const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+      const long p = L.idx(i, j, k);
+      for (int c = 0; c < 3; ++c) {
+        T D;
+        const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+        const double rv = fabs((double)((fs[c] ? fs[c][p] : T(0)) - Lu));
+        m = (rv > m || rv != rv) ? rv : m;
+      }
+    }
+    m = warp_max(m);
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
+    __syncthreads();
+    return b;
+  };
+  for (int c = 0; c < 3; ++c) fill(c);
+  const double r0 = resmax();
+  if (tid == 0) r0s = r0;
+  __syncthreads();
+  if (!(r0s > 0.0)) return;
+  for (int it = 0; it < max_sweeps; ++it) {
+    for (int colour = 0; colour < 2; ++colour)
+      for (int c = 0; c < 3; ++c) {
+        const long nh = n / 2;
+        for (long q = tid; q < nh; q += blockDim.x) {
+          const int t = (int)(q % (L.n0 / 2)), j = (int)((q / (L.n0 / 2)) % L.n1),
+                    k = (int)(q / ((long)(L.n0 / 2) * L.n1));
+          const int i = 2 * t + ((j + k + colour) & 1);
+          vec_update<T, G>(L, A, B, C, fs[c], c, i, j, k);
+        }
+        __syncthreads();
+        fill(c);
+      }
+    const double r = resmax();
+    if (!(r > 1e-12 * r0s)) break;
+  }
+}
+
+// ------------------------------------------------------------- helpers
+
+// u -= mean(u interior); sums in a fixed order (deterministic).
+template <typename T>
+__global__ void k_partial_sum(LevelView<T> L, const T* __restrict__ u, double* __restrict__ part) {
+  __shared__ double sm[32];
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  double s = 0.0;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    s += (double)u[L.idx(i, j, k)];
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b += sm[w];
+    part[blockIdx.x] = b;
+  }
+}
+
+template <typename T>
+__global__ void k_sub_mean(LevelView<T> L, T* __restrict__ u, const double* __restrict__ part, int nparts) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[b];
+    mean = s / ((double)L.n0 * L.n1 * L.n2);
+  }
+  __syncthreads();
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    const long p = L.idx(i, j, k);
+    u[p] = (T)((double)u[p] - mean);
+  }
+}
+
+// Interior <-> ghosted copies, FP64 <-> storage type conversions.
+template <typename A, typename B>
+__global__ void k_copy_in(LevelView<B> L, const A* __restrict__ src, B* __restrict__ dst, A shift) {
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    dst[L.idx(i, j, k)] = (B)(src[q] + shift);
+  }
+}
+template <typename A, typename B>
+__global__ void k_copy_out(LevelView<A> L, const A* __restrict__ src, B* __restrict__ dst, A shift) {
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    dst[q] = (B)(src[L.idx(i, j, k)] + shift);
+  }
+}
+// Ghosted-to-ghosted interior conversion (e.g. FP64 residual -> FP32 rhs).
+template <typename A, typename B>
+__global__ void k_convert(LevelView<A> L, const A* __restrict__ src, B* __restrict__ dst) {
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    const long p = L.idx(i, j, k);
+    dst[p] = (B)src[p];
+  }
+}
+// u64 += e32 (interior), the defect-correction update.
+template <typename T>
+__global__ void k_add_correction(LevelView<double> L, double* __restrict__ u, const T* __restrict__ e) {
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    const long p = L.idx(i, j, k);
+    u[p] += (double)e[p];
+  }
+}
+
+// ======================================================== host launchers
+
+template <typename T>
+static dim3 grid_colour(const LevelView<T>& L, dim3 b) {
+  return dim3(cdiv(L.n0 / 2, b.x), cdiv(L.n1, b.y), cdiv(L.n2, b.z));
+}
+template <typename T>
+static dim3 grid_cells(const LevelView<T>& L, dim3 b) {
+  return dim3(cdiv(L.n0, b.x), cdiv(L.n1, b.y), cdiv(L.n2, b.z));
+}
+static unsigned grid_flat(long n, int threads) {
+  long g = (n + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+#define GMG_GEOM_DISPATCH(G_, ...)              \
+  switch (G_) {                                  \
+    case CART: { constexpr int GG = CART; __VA_ARGS__; } break; \
+    case CYL:  { constexpr int GG = CYL;  __VA_ARGS__; } break; \
+    default:   { constexpr int GG = SPH;  __VA_ARGS__; } break; \
+  }
+
+template <typename T>
+void launch_smooth_scalar(const LevelView<T>& L, int kind, T* u, const T* f, const T* s0, const T* s1,
+                          int colour, cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(L.three), g = grid_colour(L, b);
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_smooth_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, colour);
+                    else k_smooth_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, colour));
+}
+
+template <typename T>
+void launch_fill_ghosts(const LevelView<T>& L, T* u, int comp, cudaStream_t st) {
+  count_launch();
+  const long nk = L.n2 + 2 * L.three;
+  const long n = 2L * (L.n1 + 2) * nk + 2L * L.n0 * nk + (L.three ? 2L * L.n0 * L.n1 : 0L);
+  k_fill_ghosts<T><<<grid_flat(n, 256), 256, 0, st>>>(L, u, comp);
+}
+
+template <typename T>
+void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(L.three), g = grid_colour(L, b);
+  GMG_GEOM_DISPATCH(L.geom, k_smooth_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], f, comp, colour));
+}
+
+template <typename T>
+void launch_residual_scalar(const LevelView<T>& L, int kind, const T* u, const T* f, const T* s0,
+                            const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(L.three), g = grid_cells(L, b);
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_residual_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, r, red, weighted);
+                    else k_residual_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, r, red, weighted));
+}
+
+template <typename T>
+void launch_residual_vec(const LevelView<T>& L, T* const V[3], const T* const f[3], T* const r[3],
+                         unsigned long long* red, int weighted, cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(L.three), g = grid_cells(L, b);
+  GMG_GEOM_DISPATCH(L.geom, k_residual_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], r[0], r[1], r[2], red, weighted));
+}
+
+template <typename T>
+void launch_apply_scalar(const LevelView<T>& L, int kind, const T* u, const T* s0, const T* s1, T* out, int add,
+                         cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(L.three), g = grid_cells(L, b);
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_apply_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, s0, s1, out, add);
+                    else k_apply_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, s0, s1, out, add));
+}
+
+template <typename T>
+void launch_apply_vec(const LevelView<T>& L, T* const V[3], T* const out[3], int add, cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(L.three), g = grid_cells(L, b);
+  GMG_GEOM_DISPATCH(L.geom, k_apply_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], out[0], out[1], out[2], add));
+}
+
+template <typename T>
+void launch_restrict(const LevelView<T>& F, const LevelView<T>& C, int nf, const T* const a[4], T* const b[4],
+                     T* const copy[3], cudaStream_t st) {
+  count_launch();
+  dim3 bl = block_for(C.three), g = grid_cells(C, bl);
+  k_restrict<T><<<g, bl, 0, st>>>(F, C, nf, a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3], copy[0], copy[1],
+                                   copy[2]);
+}
+
+template <typename T>
+void launch_prolong(const LevelView<T>& F, const LevelView<T>& C, T* u, const T* uH, const T* uhH, int comp,
+                    cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(F.three), g = grid_cells(F, b);
+  k_prolong<T><<<g, b, 0, st>>>(F, C, u, uH, uhH, comp);
+}
+
+template <typename T>
+void launch_coarse_scalar(const LevelView<T>& L, int kind, T* u, const T* f, const T* s0, const T* s1,
+                          int max_sweeps, cudaStream_t st) {
+  count_launch();
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_coarse_scalar<T, GG, EQ_PSI><<<1, 256, 0, st>>>(L, u, f, s0, s1, max_sweeps);
+                    else k_coarse_scalar<T, GG, EQ_LIN><<<1, 256, 0, st>>>(L, u, f, s0, s1, max_sweeps));
+}
+
+template <typename T>
+void launch_coarse_vec(const LevelView<T>& L, T* V[3], const T* const f[3], int max_sweeps, cudaStream_t st) {
+  count_launch();
+  GMG_GEOM_DISPATCH(L.geom, k_coarse_vec<T, GG><<<1, 256, 0, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], max_sweeps));
+}
+
+template <typename T>
+void launch_sub_mean(const LevelView<T>& L, T* u, double* part, int nparts, cudaStream_t st) {
+  count_launch(2);
+  k_partial_sum<T><<<nparts, 256, 0, st>>>(L, u, part);
+  k_sub_mean<T><<<nparts, 256, 0, st>>>(L, u, part, nparts);
+}
+
+template <typename A, typename B>
+void launch_copy_in(const LevelView<B>& L, const A* src, B* dst, A shift, cudaStream_t st) {
+  count_launch();
+  long n = (long)L.n0 * L.n1 * L.n2;
+  k_copy_in<A, B><<<grid_flat(n, 256), 256, 0, st>>>(L, src, dst, shift);
+}
+template <typename A, typename B>
+void launch_copy_out(const LevelView<A>& L, const A* src, B* dst, A shift, cudaStream_t st) {
+  count_launch();
+  long n = (long)L.n0 * L.n1 * L.n2;
+  k_copy_out<A, B><<<grid_flat(n, 256), 256, 0, st>>>(L, src, dst, shift);
+}
+template <typename A, typename B>
+void launch_convert(const LevelView<A>& L, const A* src, B* dst, cudaStream_t st) {
+  count_launch();
+  long n = (long)L.n0 * L.n1 * L.n2;
+  k_convert<A, B><<<grid_flat(n, 256), 256, 0, st>>>(L, src, dst);
+}
+template <typename T>
+void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st) {
+  count_launch();
+  long n = (long)L.n0 * L.n1 * L.n2;
+  k_add_correction<T><<<grid_flat(n, 256), 256, 0, st>>>(L, u, e);
+}
+
+// explicit instantiations
+#define GMG_INST(T)                                                                                            \
+  template void launch_smooth_scalar<T>(const LevelView<T>&, int, T*, const T*, const T*, const T*, int,       \
+                                        cudaStream_t);                                                          \
+  template void launch_fill_ghosts<T>(const LevelView<T>&, T*, int, cudaStream_t);                             \
+  template void launch_smooth_vec<T>(const LevelView<T>&, T* [3], const T*, int, int, cudaStream_t);           \
+  template void launch_residual_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, const T*, T*, \
+                                          unsigned long long*, int, cudaStream_t);                              \
+  template void launch_residual_vec<T>(const LevelView<T>&, T* const[3], const T* const[3], T* const[3],       \
+                                       unsigned long long*, int, cudaStream_t);                                 \
+  template void launch_apply_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*, int,        \
+                                       cudaStream_t);                                                           \
+  template void launch_apply_vec<T>(const LevelView<T>&, T* const[3], T* const[3], int, cudaStream_t);         \
+  template void launch_restrict<T>(const LevelView<T>&, const LevelView<T>&, int, const T* const[4],           \
+                                   T* const[4], T* const[3], cudaStream_t);                                     \
+  template void launch_prolong<T>(const LevelView<T>&, const LevelView<T>&, T*, const T*, const T*, int,       \
+                                  cudaStream_t);                                                                \
+  template void launch_coarse_scalar<T>(const LevelView<T>&, int, T*, const T*, const T*, const T*, int,       \
+                                        cudaStream_t);                                                          \
+  template void launch_coarse_vec<T>(const LevelView<T>&, T* [3], const T* const[3], int, cudaStream_t);       \
+  template void launch_sub_mean<T>(const LevelView<T>&, T*, double*, int, cudaStream_t);
+GMG_INST(double)
+GMG_INST(float)
+template void launch_copy_in<double, double>(const LevelView<double>&, const double*, double*, double, cudaStream_t);
+template void launch_copy_out<double, double>(const LevelView<double>&, const double*, double*, double, cudaStream_t);
+template void launch_convert<double, float>(const LevelView<double>&, const double*, float*, cudaStream_t);
+template void launch_convert<float, double>(const LevelView<float>&, const float*, double*, cudaStream_t);
+template void launch_add_correction<float>(const LevelView<double>&, double*, const float*, cudaStream_t);
+
+}  // namespace gmg

@@ -2,7 +2,7 @@
 
 This module only samples source fields on the cell centres of a grid; it
 holds none of the solver's arithmetic.  The paper's own sources (rotating
-neutron stars from XNS initial data, Secs. 4.1-4.2) are not available, so
+neutron stars from XNS initial data, Sec. 3.3.2) are not available, so
 analytic Gamma = 2 polytropes stand in for them (G = c = M_sun = 1):
 
     rho(xi) = rho_c sin(pi xi) / (pi xi) for xi < 1, else 0,

@@ -1,0 +1,354 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Unit level (one operator application, one red-black sweep, restriction,
+prolongation, A2, divergence) on seeded random fields: element by element
+within a few units of round-off.  Solver level (scalar, vector, xCFC,
+divergence cleaning): the same V-cycle count (+-1) and every field within
+1e-9 relative (max |gpu - oracle| / max |oracle|) at a converged relative
+residual of 1e-10."""
+import numpy as np
+import pytest
+
+import oracle.oracle as o
+from paper_2012_07322_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PI = np.pi
+CASES = [
+    ("sph2d", "sph", [32, 16], [0.0, 0.0], [30.0, PI]),
+    ("sph3d", "sph", [16, 8, 8], [0.0, 0.0, 0.0], [30.0, PI, 2 * PI]),
+    ("cyl2d", "cyl", [16, 32], [0.0, -30.0], [30.0, 34.0]),
+    ("cyl3d", "cyl", [16, 16, 8], [0.0, -30.0, 0.0], [30.0, 34.0, 2 * PI]),
+    ("cart2d", "cart", [32, 16], [-30.0, -25.0], [34.0, 27.0]),
+    ("cart3d", "cart", [16, 8, 16], [-30.0, -25.0, -20.0], [34.0, 27.0, 31.0]),
+]
+IDS = [c[0] for c in CASES]
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_07322_gb300 import mg as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def ghosted(d, a):
+    g = np.zeros(o.shape(d, True))
+    g[(slice(1, -1),) * d.ndim] = a
+    return g
+
+
+def interior(d, g):
+    return np.ascontiguousarray(g[(slice(1, -1),) * d.ndim])
+
+
+def relerr(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def descs(mg, geom, n, lo, hi, **kw):
+    okw = {k: v for k, v in kw.items() if k in ("tol", "max_cycles", "nu1", "nu2", "mixed", "stall_window")}
+    gkw = dict(okw)
+    if "precision" in kw:
+        gkw["precision"] = kw["precision"]
+    return o.desc(geom, n, lo, hi, **okw), mg.grid_desc(geom, n, lo, hi, **gkw)
+
+
+# --------------------------------------------------------------- unit level
+
+
+@pytest.mark.parametrize("mixed", ["4pt", "corner"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_operator_parity(mg, case, mixed):
+    """L(u) with boundary ghosts: scalar psi, scalar linear, vector."""
+    _, geom, n, lo, hi = case
+    d, gd = descs(mg, geom, n, lo, hi, mixed=mixed)
+    h = mg.Hierarchy(gd)
+    shp = o.shape(d)
+    rng = np.random.default_rng(1)
+    u = rng.uniform(-0.3, 0.3, shp)
+    U, A2, c = rng.uniform(0, 0.01, shp), rng.uniform(0, 0.01, shp), rng.uniform(0, 0.05, shp)
+    for kind, bc in [("psi", "robin"), ("lin", "robin"), ("lin", "neumann"), ("lin", "dirichlet")]:
+        ug = ghosted(d, u)
+        o.fill_ghosts(d, bc, -1, ug)
+        want = interior(d, o.apply_raw(d, kind, ug, U=ghosted(d, U), A2=ghosted(d, A2), c=ghosted(d, c)))
+        out = torch.zeros(shp, dtype=torch.float64, device="cuda")
+        mg.mg_apply_operator(h, kind, bc, dev(u), out, U=dev(U), A2=dev(A2), c=dev(c))
+        assert relerr(host(out), want) < 1e-12, (kind, bc)
+    V = [rng.uniform(-0.3, 0.3, shp) for _ in range(3)]
+    for bc in ["dirichlet", "robin"]:
+        Vg = [ghosted(d, x) for x in V]
+        for k in range(3):
+            o.fill_ghosts(d, bc, k, Vg[k])
+        want = [interior(d, x) for x in o.apply_raw(d, "vec", Vg)]
+        outs = [torch.zeros(shp, dtype=torch.float64, device="cuda") for _ in range(3)]
+        mg.mg_apply_operator(h, "vec", bc, [dev(x) for x in V], outs)
+        scale = max(np.abs(w).max() for w in want)
+        for k in range(3):
+            assert np.abs(host(outs[k]) - want[k]).max() < 1e-12 * scale, (bc, k)
+    h.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_red_black_sweep_parity(mg, case):
+    """Three red-black Newton-Gauss-Seidel sweeps (eq. ngs_iteration)."""
+    _, geom, n, lo, hi = case
+    d, gd = descs(mg, geom, n, lo, hi)
+    h = mg.Hierarchy(gd)
+    shp = o.shape(d)
+    rng = np.random.default_rng(2)
+    u = rng.uniform(-0.3, 0.3, shp)
+    f = rng.uniform(-0.01, 0.01, shp)
+    U, A2, c = rng.uniform(0, 0.01, shp), rng.uniform(0, 0.01, shp), rng.uniform(0, 0.05, shp)
+    for kind, bc in [("psi", "robin"), ("lin", "neumann"), ("lin", "robin")]:
+        ug, fg = ghosted(d, u), ghosted(d, f if kind == "lin" else 0 * f)
+        o.smooth(d, kind, bc, 3, ug, fg, U=ghosted(d, U), A2=ghosted(d, A2), c=ghosted(d, c))
+        ut = dev(u)
+        mg.mg_smooth(h, kind, bc, 3, ut, f=dev(f) if kind == "lin" else None, U=dev(U), A2=dev(A2), c=dev(c))
+        assert relerr(host(ut), interior(d, ug)) < 1e-12, kind
+    V = [rng.uniform(-0.3, 0.3, shp) for _ in range(3)]
+    F = [rng.uniform(-0.01, 0.01, shp) for _ in range(3)]
+    Vg, Fg = [ghosted(d, x) for x in V], [ghosted(d, x) for x in F]
+    o.smooth(d, "vec", "dirichlet", 3, Vg, Fg)
+    Vt = [dev(x) for x in V]
+    mg.mg_smooth(h, "vec", "dirichlet", 3, Vt, f=[dev(x) for x in F])
+    for k in range(3):
+        assert relerr(host(Vt[k]), interior(d, Vg[k])) < 1e-12, k
+    h.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_transfer_parity(mg, case):
+    """Volume-weighted restriction and Kwak prolongation (Sec. 2.7.3)."""
+    _, geom, n, lo, hi = case
+    d, gd = descs(mg, geom, n, lo, hi)
+    h = mg.Hierarchy(gd)
+    shp = o.shape(d)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(shp)
+    want = interior(o.coarse_desc(d), o.restrict(d, ghosted(d, u)))
+    out = torch.zeros(h.level_shape(1), dtype=torch.float64, device="cuda")
+    mg.mg_restrict(h, dev(u), out)
+    assert relerr(host(out), want) < 1e-14
+    dc = o.coarse_desc(d)
+    e = rng.standard_normal(o.shape(dc))
+    for bc in ["robin", "dirichlet", "neumann"]:
+        eg = ghosted(dc, e)
+        o.fill_ghosts(dc, bc, -1, eg)
+        ug = ghosted(d, u)
+        o.prolong_add(d, ug, eg)
+        ut = dev(u)
+        mg.mg_prolong_add(h, bc, dev(e), ut)
+        assert relerr(host(ut), interior(d, ug)) < 1e-14, bc
+    h.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_aij_parity(mg, case):
+    """A2 = A~_ij A~^ij from X (eq. Aij)."""
+    _, geom, n, lo, hi = case
+    d, gd = descs(mg, geom, n, lo, hi)
+    h = mg.Hierarchy(gd)
+    rng = np.random.default_rng(4)
+    X = [rng.uniform(-1, 1, o.shape(d)) for _ in range(3)]
+    want = o.aij(d, X)
+    out = torch.zeros(o.shape(d), dtype=torch.float64, device="cuda")
+    mg.mg_compute_a2(h, [dev(x) for x in X], out)
+    assert relerr(host(out), want) < 1e-12
+    h.close()
+
+
+def test_divergence_parity(mg):
+    d, gd = descs(mg, "cart", [16, 32, 8], [-1, -1, -1], [1, 1, 1])
+    h = mg.Hierarchy(gd)
+    rng = np.random.default_rng(5)
+    B = [rng.standard_normal(o.shape(d)) for _ in range(3)]
+    out = torch.zeros(o.shape(d), dtype=torch.float64, device="cuda")
+    mg.mg_divergence(h, [dev(x) for x in B], out)
+    assert relerr(host(out), o.div_c(d, B)) < 1e-13
+    h.close()
+
+
+# ------------------------------------------------------------- solver level
+
+
+def check_report(rg, ro, tol):
+    assert rg["status"] == "ok" and ro["status"] == "ok"
+    assert abs(rg["cycles"] - ro["cycles"]) <= 1, (rg["cycles"], ro["cycles"])
+    assert rg["rel"] <= tol
+
+
+@pytest.mark.parametrize("geom,n,lo,hi,bc,zero_mean", [
+    ("cyl", [32, 64], [0.0, -40.0], [40.0, 40.0], "robin", False),
+    ("sph", [32, 16], [0.0, 0.0], [40.0, PI], "robin", False),
+    ("cart", [16, 16, 16], [-1, -1, -1], [1, 1, 1], "neumann", True),
+    ("sph", [16, 8, 8], [0, 0, 0], [40.0, PI, 2 * PI], "dirichlet", False),
+])
+def test_linear_scalar_solve_parity(mg, geom, n, lo, hi, bc, zero_mean):
+    d, gd = descs(mg, geom, n, lo, hi, tol=1e-10, max_cycles=1000)
+    h = mg.Hierarchy(gd)
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal(o.shape(d))
+    if zero_mean:
+        f -= f.mean()
+    c = None if zero_mean else rng.uniform(0, 0.01, o.shape(d))
+    u = np.zeros(o.shape(d))
+    ro = o.solve_scalar(d, "lin", bc, u, c=c, f=f, zero_mean=zero_mean)
+    ut = torch.zeros(o.shape(d), dtype=torch.float64, device="cuda")
+    rg = mg.mg_solve_scalar(h, "lin", bc, ut, c=dev(c) if c is not None else None, f=dev(f), zero_mean=zero_mean)
+    check_report(rg, ro, 1e-10)
+    assert relerr(host(ut), u) < 1e-9
+    h.close()
+
+
+@pytest.mark.parametrize("geom,n,lo,hi,mixed", [
+    ("sph", [32, 16], [0.0, 0.0], [30.0, PI], "4pt"),
+    ("cyl", [16, 16, 8], [0.0, -30.0, 0.0], [30.0, 30.0, 2 * PI], "4pt"),
+    ("cart", [16, 16, 16], [-30.0] * 3, [30.0] * 3, "corner"),
+    ("sph", [16, 8, 8], [0, 0, 0], [30.0, PI, 2 * PI], "4pt"),
+])
+def test_vector_solve_parity(mg, geom, n, lo, hi, mixed):
+    d, gd = descs(mg, geom, n, lo, hi, tol=1e-10, max_cycles=1000, mixed=mixed)
+    h = mg.Hierarchy(gd)
+    rng = np.random.default_rng(7)
+    f = [rng.standard_normal(o.shape(d)) for _ in range(3)]
+    V = [np.zeros(o.shape(d)) for _ in range(3)]
+    ro = o.solve_vector(d, "dirichlet", f, V)
+    Vt = [torch.zeros(o.shape(d), dtype=torch.float64, device="cuda") for _ in range(3)]
+    rg = mg.mg_solve_vector(h, "dirichlet", [dev(x) for x in f], Vt)
+    check_report(rg, ro, 1e-10)
+    scale = max(np.abs(x).max() for x in V)
+    for k in range(3):
+        assert np.abs(host(Vt[k]) - V[k]).max() < 1e-9 * scale, k
+    h.close()
+
+
+def run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="fp64", psi_only=False, tol=1e-10):
+    d, gd = descs(mg, geom, n, lo, hi, tol=tol, max_cycles=1000, precision=precision)
+    shp = o.shape(d)
+    psi, alpha = np.ones(shp), np.ones(shp)
+    beta = [np.zeros(shp) for _ in range(3)]
+    X = [np.zeros(shp) for _ in range(3)]
+    ro = o.solve_cfc(d, U, S, Si, psi, alpha, beta, X, psi_only=psi_only)
+    h = mg.Hierarchy(gd)
+    t = {k: torch.ones(shp, dtype=torch.float64, device="cuda") for k in ("psi", "alpha")}
+    tb = [torch.zeros(shp, dtype=torch.float64, device="cuda") for _ in range(3)]
+    tx = [torch.zeros(shp, dtype=torch.float64, device="cuda") for _ in range(3)]
+    rg = mg.mg_solve_cfc(h, dev(U), dev(S), [dev(x) for x in Si], t["psi"], t["alpha"], tb, tx, psi_only=psi_only)
+    h.close()
+    got = {"psi": host(t["psi"]), "alpha": host(t["alpha"]), "beta": [host(x) for x in tb],
+           "X": [host(x) for x in tx]}
+    want = {"psi": psi, "alpha": alpha, "beta": beta, "X": X}
+    return rg, ro, got, want
+
+
+def field_errors(got, want, psi_only=False):
+    errs = {"psi": relerr(got["psi"], want["psi"]), "dpsi": relerr(got["psi"] - 1, want["psi"] - 1)}
+    if not psi_only:
+        errs["alpha"] = relerr(got["alpha"], want["alpha"])
+        errs["dalpha"] = relerr(got["alpha"] - 1, want["alpha"] - 1)
+        for name in ("beta", "X"):
+            scale = max(np.abs(x).max() for x in want[name])
+            errs[name] = max(np.abs(a - b).max() for a, b in zip(got[name], want[name])) / (scale or 1.0)
+    return errs
+
+
+def test_c1_psi_parity(mg):
+    """Static n = 1 polytrope on the 64 x 32 spherical grid, eq. psi only."""
+    U = inputs.static_polytrope_sph2d()
+    z = np.zeros_like(U)
+    rg, ro, got, want = run_cfc_pair(mg, "sph", [64, 32], [0, 0], [100.0, PI], U, z, [z, z, z], psi_only=True)
+    check_report(rg["psi"], ro["psi"], 1e-10)
+    errs = field_errors(got, want, psi_only=True)
+    assert errs["psi"] < 1e-9 and errs["dpsi"] < 1e-9, errs
+
+
+@pytest.mark.parametrize("geom,n,hi", [
+    ("sph", [64, 32], [100.0, PI]),
+    ("sph", [32, 16, 16], [100.0, PI, 2 * PI]),
+    ("cyl", [32, 64], [100.0, 100.0]),
+])
+def test_xcfc_parity(mg, geom, n, hi):
+    """Full xCFC sequence on a rotating polytrope (Steps 1-6, Sec. 2.6)."""
+    if geom == "sph" and len(n) == 2:
+        U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], hi[0])
+        lo = [0.0, 0.0]
+    elif geom == "sph":
+        U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), hi[0])
+        lo = [0.0, 0.0, 0.0]
+    else:
+        U, S, Si = inputs.rotating_polytrope_cyl(n, hi[0])
+        lo = [0.0, -hi[1]]
+    rg, ro, got, want = run_cfc_pair(mg, geom, n, lo, hi, U, S, Si)
+    for k in ("X", "psi", "alphapsi", "beta"):
+        check_report(rg[k], ro[k], 1e-10)
+    errs = field_errors(got, want)
+    assert max(errs.values()) < 1e-9, errs
+
+
+def test_divb_cleaning_parity(mg):
+    """Elliptic divergence cleaning on a 32^3 curl field with noise."""
+    n = 32
+    B = inputs.divb_field(n=n, n_modes=32, k_max=8)
+    d, gd = descs(mg, "cart", [n] * 3, [-1.0] * 3, [1.0] * 3, tol=1e-10, max_cycles=1000)
+    Bo = [b.copy() for b in B]
+    phi = np.zeros((n, n, n))
+    ro = o.clean_divb(d, Bo, phi)
+    h = mg.Hierarchy(gd)
+    Bt = [dev(b) for b in B]
+    pt = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    rg = mg.mg_clean_divB(h, Bt, pt)
+    h.close()
+    check_report(rg["solve"], ro["solve"], 1e-10)
+    assert relerr(host(pt), phi) < 1e-9
+    for k in range(3):
+        assert relerr(host(Bt[k]), Bo[k]) < 1e-9
+    for key in ("max_div_before", "l2_div_before", "max_div_after", "l2_div_after"):
+        assert abs(rg[key] - ro[key]) <= 1e-9 * ro["max_div_before"], key
+
+
+# ------------------------------------------------------ mixed precision
+
+
+def test_mixed_precision_xcfc_error_vs_oracle(mg):
+    """FP32 smoothing inside FP64 defect correction: every equation reaches
+    the FP64 relative residual 1e-10 and every field stays within 1e-8 of
+    the FP64 oracle."""
+    n = [32, 16, 16]
+    U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
+    rg, ro, got, want = run_cfc_pair(mg, "sph", n, [0, 0, 0], [100.0, PI, 2 * PI], U, S, Si, precision="mixed")
+    for k in ("X", "psi", "alphapsi", "beta"):
+        assert rg[k]["status"] == "ok" and rg[k]["rel"] <= 1e-10
+    errs = field_errors(got, want)
+    assert max(errs.values()) < 1e-8, errs
+
+
+def test_mixed_precision_divb_error_vs_oracle(mg):
+    n = 32
+    B = inputs.divb_field(n=n)
+    d, gd = descs(mg, "cart", [n] * 3, [-1.0] * 3, [1.0] * 3, tol=1e-10, max_cycles=1000, precision="mixed")
+    Bo = [b.copy() for b in B]
+    phi = np.zeros((n, n, n))
+    o.clean_divb(d, Bo, phi)
+    h = mg.Hierarchy(gd)
+    Bt = [dev(b) for b in B]
+    pt = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    rg = mg.mg_clean_divB(h, Bt, pt)
+    h.close()
+    assert rg["status"] == "ok" and rg["solve"]["rel"] <= 1e-10
+    assert relerr(host(pt), phi) < 1e-8
+    for k in range(3):
+        assert relerr(host(Bt[k]), Bo[k]) < 1e-8

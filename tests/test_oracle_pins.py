@@ -531,7 +531,7 @@ def test_newtonian_polytrope_second_order():
     (1 + sin(kr)/(kr)) inside, -M/r outside, M = 4 rho_c R^3 / pi; the
     exterior 1/r satisfies the Robin condition exactly.  Outside the star
     the discrete error falls at second order (R_N = log2(delta_N/2 /
-    delta_N) ~ 2, the convergence measure of Sec. 4.1); with the innermost
+    delta_N) ~ 2, the convergence measure of Sec. 3.1.1); with the innermost
     shell included (printed r_i^2 form) at least at first order."""
     rho_c, R, rmax = 1.28e-3, 10.0, 40.0
     k = PI / R
