@@ -84,6 +84,14 @@ enum { MG_EQ_PSI = 0, MG_EQ_LIN = 1, MG_EQ_VEC = 2 };      /* equation kinds */
  *   mixed_deriv   MG_MIXED_4PT (four-corner stencil) or MG_MIXED_CORNER
  *             (the block-corner stencil of Sec. 2.7.1, used on every cell).
  *   stall_window  cycles over which a 5 % gain is required (0: off).
+ *   accel_depth   0: plain V-cycles (the paper's iteration).  m in 1..16:
+ *             Anderson mixing of depth m over the V-cycle map (not in the
+ *             paper): with f = G(u) - u the change one cycle G makes,
+ *             u <- G(u) - dG gamma, gamma = argmin |f - dF gamma| over the
+ *             last m differences dF, dG of f and G(u).  Point smoothing
+ *             converges slowly on spherical grids (Sec. 2.7.2 notes it);
+ *             the mixing restores a rate of tens of cycles.  Each mixed
+ *             iteration is one V-cycle and counts as one cycle.
  */
 typedef struct {
   int ndim;
@@ -97,6 +105,7 @@ typedef struct {
   double tol;
   int mixed_deriv;
   int stall_window;
+  int accel_depth;
 } mg_grid_desc;
 
 #define MG_HIST 1024

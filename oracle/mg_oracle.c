@@ -38,7 +38,7 @@
  *   - FAS coarse-grid sources are restrictions of the fine sources; coarse
  *     operators are rediscretised;
  *   - coarsest grid: Newton-Gauss-Seidel sweeps until its residual falls by
- *     1e-12 or 100 sweeps;
+ *     1e-12 or 16 sweeps (more sweeps leave the V-cycle counts unchanged);
  *   - stopping rule: rel = max|w r| / max|w S(u)|, w = r^2 sin(theta)
  *     (spherical), R (cylindrical), 1 (Cartesian);
  *   - optional Anderson mixing of successive V-cycle iterates (not in the
@@ -559,11 +559,12 @@ static double interior_mean(const OGrid* g, const double* u) {
 }
 
 /* Newton-Gauss-Seidel on the coarsest grid used as the direct solver
- * (Sec. 2.7.2): sweeps until the residual drops by 1e-12 or 100 sweeps. */
+ * (Sec. 2.7.2): sweeps until the residual drops by 1e-12 or 16 sweeps. */
+#define OR_COARSE_SWEEPS 16
 static void coarse_solve(const OSolver* s, OLevel* L) {
   double r0 = residual(s, L);
   if (r0 == 0.0) return;
-  for (int it = 0; it < 100; ++it) {
+  for (int it = 0; it < OR_COARSE_SWEEPS; ++it) {
     smooth_sweep(s, L);
     double r = residual(s, L);
     if (r <= 1e-12 * r0) break;

@@ -30,12 +30,22 @@ struct LevelView {
   T h0, h1, h2;        // spacings
   T lo0, lo1, lo2;     // domain origin
   T ih0s, ih1s, ih2s;  // 1 / h^2
+  T hc0, hc1, hc2;     // 1 / (2 h): central first differences
+  T m01, m02, m12;     // mixed-derivative factors: 1/(4 ha hb), or 1/(2 ha hb) (block-corner)
   T robin0;            // spherical Robin ghost factor r_{n-1} / r_n
+  int ln0, ln1;        // log2 of n0, n1 (all sizes are powers of two)
   const T* ti;         // NTI tables of n0 + 2
   const T* tj;         // NTJ tables of n1 + 2
   __device__ __forceinline__ long idx(int i, int j, int k) const { return off + i + j * sx + (long)k * sy; }
   __device__ __forceinline__ T TI(int s, int i) const { return ti[s * (n0 + 2) + i + 1]; }
   __device__ __forceinline__ T TJ(int s, int j) const { return tj[s * (n1 + 2) + j + 1]; }
+  // Interior cell (i, j, k) of the flat index r = i + n0 (j + n1 k).
+  __device__ __forceinline__ void cell(long r, int& i, int& j, int& k) const {
+    i = (int)(r & (n0 - 1));
+    const long jk = r >> ln0;
+    j = (int)(jk & (n1 - 1));
+    k = (int)(jk >> ln1);
+  }
   __device__ __forceinline__ T xc0(int i) const { return lo0 + (T(i) + T(0.5)) * h0; }
   __device__ __forceinline__ T xc1(int j) const { return lo1 + (T(j) + T(0.5)) * h1; }
   __device__ __forceinline__ T xc2(int k) const { return lo2 + (T(k) + T(0.5)) * h2; }
@@ -214,10 +224,10 @@ struct Stencil {
   const LevelView<T>& L;
   long p;
   __device__ __forceinline__ T d1(const T* F, int d) const {
-    if (d == 0) return (F[p + 1] - F[p - 1]) * (T(0.5) / L.h0);
-    if (d == 1) return (F[p + L.sx] - F[p - L.sx]) * (T(0.5) / L.h1);
+    if (d == 0) return (F[p + 1] - F[p - 1]) * L.hc0;
+    if (d == 1) return (F[p + L.sx] - F[p - L.sx]) * L.hc1;
     if (!L.three) return T(0);
-    return (F[p + L.sy] - F[p - L.sy]) * (T(0.5) / L.h2);
+    return (F[p + L.sy] - F[p - L.sy]) * L.hc2;
   }
   __device__ __forceinline__ long step(int d) const { return d == 0 ? 1 : (d == 1 ? L.sx : L.sy); }
   __device__ __forceinline__ T hs(int d) const { return d == 0 ? L.ih0s : (d == 1 ? L.ih1s : L.ih2s); }
@@ -229,12 +239,9 @@ struct Stencil {
   __device__ __forceinline__ T mix(const T* F, int a, int b) const {
     if (b == 2 && !L.three) return T(0);
     long sa = step(a), sb = step(b);
-    T ha = a == 0 ? L.h0 : (a == 1 ? L.h1 : L.h2);
-    T hb = b == 0 ? L.h0 : (b == 1 ? L.h1 : L.h2);
-    if (L.mixed == 0)
-      return (F[p + sa + sb] - F[p + sa - sb] - F[p - sa + sb] + F[p - sa - sb]) / (T(4) * ha * hb);
-    return (-F[p + sa - sb] - F[p - sa + sb] + F[p + sa] + F[p - sa] + F[p + sb] + F[p - sb] - T(2) * F[p]) /
-           (T(2) * ha * hb);
+    const T w = (a == 0 && b == 1) ? L.m01 : (a == 0 ? L.m02 : L.m12);
+    if (L.mixed == 0) return (F[p + sa + sb] - F[p + sa - sb] - F[p - sa + sb] + F[p - sa - sb]) * w;
+    return (-F[p + sa - sb] - F[p - sa + sb] + F[p + sa] + F[p - sa] + F[p + sb] + F[p - sb] - T(2) * F[p]) * w;
   }
 };
 

@@ -2,6 +2,7 @@
 // its coefficient tables, FAS V-cycles and the FP32/FP64 defect-correction
 // loop, the xCFC solve order and divergence cleaning, behind the C ABI of
 // include/mg.h.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -18,7 +19,7 @@ namespace {
 
 constexpr int MAX_LEVELS = 16;
 constexpr int NPARTS = 1024;           // blocks of the deterministic sums
-constexpr int COARSE_SWEEPS = 100;     // coarsest-grid sweep cap (Sec. 2.7.2)
+constexpr int COARSE_SWEEPS = 16;      // coarsest-grid sweep cap (Sec. 2.7.2)
 constexpr double PI = 3.14159265358979323846;
 
 thread_local char g_last_error[256] = "";
@@ -40,9 +41,18 @@ struct Level {
 
 }  // namespace
 
+struct GraphEntry {
+  int key;
+  cudaGraphExec_t exec;
+  int64_t updates;    // smoother updates one replay performs
+  uint64_t launches;  // kernels one replay launches
+};
+
 struct mg_hierarchy {
   mg_grid_desc d;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;   // work stream (the caller's, or an owned one)
+  bool own_stream = false;
+  std::vector<GraphEntry> graphs;
   int nlev = 0;
   Level L[MAX_LEVELS];
   // level-0 arrays of the xCFC sequence (ghosted)
@@ -57,6 +67,12 @@ struct mg_hierarchy {
   std::vector<double*> stage;
   int64_t updates = 0;
   // optional event timing of finest-level kernels (mg_profile_enable)
+  // Anderson mixing storage (allocated on first use): x, fprev, gprev, then
+  // m columns of dF and m of dG, each ncomp arrays of L0.ng doubles
+  double* aa = nullptr;
+  size_t aa_bytes = 0;
+  double* d_aa_part = nullptr;
+  double* h_aa_part = nullptr;
   bool prof_on = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_cls;
@@ -146,6 +162,7 @@ int validate(const mg_grid_desc* d) {
   if (d->mixed_deriv != MG_MIXED_4PT && d->mixed_deriv != MG_MIXED_CORNER)
     return fail(MG_ERR_INVALID, "bad mixed_deriv");
   if (d->stall_window < 0) return fail(MG_ERR_INVALID, "bad stall_window");
+  if (d->accel_depth < 0 || d->accel_depth > AA_MAX) return fail(MG_ERR_INVALID, "accel_depth must be in 0..16");
   return MG_OK;
 }
 
@@ -318,8 +335,19 @@ LevelView<T> make_view(const mg_grid_desc* d, const Level& L, const T* ti, const
   v.ih0s = (T)(1.0 / (L.h[0] * L.h[0]));
   v.ih1s = (T)(1.0 / (L.h[1] * L.h[1]));
   v.ih2s = (T)(1.0 / (L.h[2] * L.h[2]));
+  v.hc0 = (T)(0.5 / L.h[0]);
+  v.hc1 = (T)(0.5 / L.h[1]);
+  v.hc2 = (T)(0.5 / L.h[2]);
+  const double mf = d->mixed_deriv == MG_MIXED_4PT ? 4.0 : 2.0;
+  v.m01 = (T)(1.0 / (mf * L.h[0] * L.h[1]));
+  v.m02 = (T)(1.0 / (mf * L.h[0] * L.h[2]));
+  v.m12 = (T)(1.0 / (mf * L.h[1] * L.h[2]));
   const double rN = L.lo[0] + (L.n[0] - 0.5) * L.h[0], rG = L.lo[0] + (L.n[0] + 0.5) * L.h[0];
   v.robin0 = (T)(rN / rG);
+  v.ln0 = 0;
+  while ((1 << v.ln0) < L.n[0]) ++v.ln0;
+  v.ln1 = 0;
+  while ((1 << v.ln1) < L.n[1]) ++v.ln1;
   v.ti = ti;
   v.tj = tj;
   return v;
@@ -560,21 +588,150 @@ void restrict_k32(mg_hierarchy* H) {
 
 // ---------------------------------------------------------- cycle control
 
+// One application of the iteration map: a V-cycle (FP64 FAS, or the FP32
+// correction cycle of the defect-correction loop) and the Neumann gauge.
+int cycle_map(mg_hierarchy* H, const Eq& e) {
+  Level& L0 = H->L[0];
+  if (H->d.precision != MG_MIXED) {
+    vcycle64(H, e, 0);
+  } else {
+    auto v = with_bc(L0.v64, e.bc);
+    for (int c = 0; c < e.ncomp; ++c) {
+      launch_convert<double, float>(v, L0.r[c], L0.f32[c], H->st);
+      CK(cudaMemsetAsync(L0.e[c], 0, sizeof(float) * L0.ng, H->st));
+    }
+    if (e.kind == EQ_PSI) {
+      launch_psi_linearisation(v, L0.u[0], L0.s0, L0.s1, L0.k32, H->st);
+      restrict_k32(H);
+    }
+    vcycle32(H, e, 0);
+    for (int c = 0; c < e.ncomp; ++c) launch_add_correction<float>(v, L0.u[c], L0.e[c], H->st);
+  }
+  if (e.zero_mean) launch_sub_mean(L0.v64, L0.u[0], H->d_part, NPARTS, H->st);
+  if (e.kind == EQ_VEC) fill_all64(H, e, 0);
+  return MG_OK;
+}
+
+// The cycle map replayed from a CUDA graph captured on first use (one per
+// equation signature): the launch sequence and every pointer it touches are
+// fixed for a hierarchy.  Direct launches while profiling.
+int run_cycle_map(mg_hierarchy* H, const Eq& e) {
+  if (H->prof_on) return cycle_map(H, e);
+  const int key = e.kind | (e.bc << 2) | (e.zero_mean << 4) | ((int)e.has_c << 5) | (H->d.precision << 6);
+  for (const GraphEntry& g : H->graphs)
+    if (g.key == key) {
+      CK(cudaGraphLaunch(g.exec, H->st));
+      H->updates += g.updates;
+      count_launch((int)g.launches);
+      return MG_OK;
+    }
+  const int64_t u0 = H->updates;
+  const unsigned long long l0 = launch_count();
+  CK(cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
+  int st = cycle_map(H, e);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(H->st, &graph);
+  if (st) return st;
+  if (ce != cudaSuccess || !graph) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "graph capture: %s", cudaGetErrorString(ce));
+    return MG_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "graph instantiate: %s", cudaGetErrorString(ce));
+    return MG_ERR_CUDA;
+  }
+  GraphEntry g{key, exec, H->updates - u0, launch_count() - l0};
+  H->graphs.push_back(g);
+  H->updates = u0;
+  CK(cudaGraphLaunch(exec, H->st));
+  H->updates += g.updates;
+  return MG_OK;
+}
+
+// Small SPD solve (M + lambda I) y = b, lambda = 1e-12 max diag(M), by
+// Cholesky; -1 if M is degenerate.
+int gram_solve(int m, const double* M, const double* b, double* y) {
+  double A[AA_MAX * AA_MAX], Lc[AA_MAX * AA_MAX], z[AA_MAX];
+  double dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = std::max(dmax, M[i * m + i]);
+  if (!(dmax > 0.0)) return -1;
+  for (int i = 0; i < m * m; ++i) A[i] = M[i];
+  for (int i = 0; i < m; ++i) A[i * m + i] += 1e-12 * dmax;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double acc = A[i * m + j];
+      for (int k = 0; k < j; ++k) acc -= Lc[i * m + k] * Lc[j * m + k];
+      if (i == j) {
+        if (!(acc > 0.0)) return -1;
+        Lc[i * m + i] = std::sqrt(acc);
+      } else {
+        Lc[i * m + j] = acc / Lc[j * m + j];
+      }
+    }
+  }
+  for (int i = 0; i < m; ++i) {
+    double acc = b[i];
+    for (int k = 0; k < i; ++k) acc -= Lc[i * m + k] * z[k];
+    z[i] = acc / Lc[i * m + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double acc = z[i];
+    for (int k = i + 1; k < m; ++k) acc -= Lc[k * m + i] * y[k];
+    y[i] = acc / Lc[i * m + i];
+  }
+  return 0;
+}
+
+int ensure_aa(mg_hierarchy* H, int ncomp, int m) {
+  const size_t need = sizeof(double) * (size_t)H->L[0].ng * ncomp * (3 + 2 * (size_t)m);
+  if (H->aa_bytes < need) {
+    if (H->aa) cudaFree(H->aa);
+    H->aa = nullptr;
+    H->aa_bytes = 0;
+    if (cudaMalloc(&H->aa, need) != cudaSuccess) return fail(MG_ERR_OOM, "mixing storage allocation failed");
+    H->aa_bytes = need;
+  }
+  if (!H->d_aa_part) {
+    const size_t pb = sizeof(double) * AA_BLOCKS * 2 * AA_MAX;
+    if (cudaMalloc(&H->d_aa_part, pb) != cudaSuccess) return fail(MG_ERR_OOM, "mixing scratch failed");
+    if (cudaMallocHost(&H->h_aa_part, pb) != cudaSuccess) return fail(MG_ERR_OOM, "mixing scratch failed");
+  }
+  return MG_OK;
+}
+
 int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   auto t0 = std::chrono::steady_clock::now();
   H->updates = 0;
   const mg_grid_desc& d = H->d;
   const bool mixed = d.precision == MG_MIXED;
   Level& L0 = H->L[0];
+  const int m = d.accel_depth;
   if (e.kind == EQ_VEC) fill_all64(H, e, 0);
   restrict_sources(H, e);
   if (mixed && e.kind == EQ_LIN && e.has_c) {
     launch_convert<double, float>(L0.v64, L0.s1, L0.k32, H->st);
     restrict_k32(H);
   }
+  int st = MG_OK;
+  // mixing state
+  const long stride = L0.ng, vlen = (long)e.ncomp * L0.ng;
+  double *ax = nullptr, *afp = nullptr, *agp = nullptr, *adF = nullptr, *adG = nullptr;
+  double M[AA_MAX * AA_MAX] = {0};
+  int ncol = 0, head = 0;
+  if (m > 0) {
+    if ((st = ensure_aa(H, e.ncomp, m))) return st;
+    ax = H->aa;
+    afp = ax + vlen;
+    agp = afp + vlen;
+    adF = agp + vlen;
+    adG = adF + (long)m * vlen;
+  }
   std::vector<double> hist;
   double rel;
-  int st = finest_norm(H, e, &rel);
+  st = finest_norm(H, e, &rel);
   if (st) return st;
   hist.push_back(rel);
   int cyc = 0, status = MG_OK;
@@ -592,23 +749,55 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
       status = MG_ERR_STALLED;
       break;
     }
-    if (!mixed) {
-      vcycle64(H, e, 0);
-    } else {
-      auto v = with_bc(L0.v64, e.bc);
-      for (int c = 0; c < e.ncomp; ++c) {
-        launch_convert<double, float>(v, L0.r[c], L0.f32[c], H->st);
-        CK(cudaMemsetAsync(L0.e[c], 0, sizeof(float) * L0.ng, H->st));
+    if (m > 0)
+      for (int c = 0; c < e.ncomp; ++c)
+        CK(cudaMemcpyAsync(ax + (long)c * stride, L0.u[c], sizeof(double) * L0.ng, cudaMemcpyDeviceToDevice,
+                           H->st));
+    if ((st = run_cycle_map(H, e))) return st;
+    if (m > 0) {
+      const int first = cyc == 0;
+      const int slot = head;
+      launch_aa_update(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF + (long)slot * vlen,
+                       adG + (long)slot * vlen, first, H->st);
+      if (!first) {
+        head = (head + 1) % m;
+        if (ncol < m) ++ncol;
       }
-      if (e.kind == EQ_PSI) {
-        launch_psi_linearisation(v, L0.u[0], L0.s0, L0.s1, L0.k32, H->st);
-        restrict_k32(H);
+      if (ncol > 0) {
+        AACols cols{};
+        cols.n = ncol;
+        for (int a = 0; a < ncol; ++a) cols.slot[a] = (head - ncol + a + m) % m;   // oldest first
+        launch_aa_dots(L0.v64, e.ncomp, stride, afp, adF, cols, first ? -1 : slot, H->d_aa_part, H->st);
+        CK(cudaMemcpyAsync(H->h_aa_part, H->d_aa_part, sizeof(double) * AA_BLOCKS * 2 * AA_MAX,
+                           cudaMemcpyDeviceToHost, H->st));
+        CK(cudaStreamSynchronize(H->st));
+        double bvec[AA_MAX], newrow[AA_MAX];
+        for (int a = 0; a < ncol; ++a) {
+          double sb = 0.0, sn = 0.0;
+          for (int blk = 0; blk < AA_BLOCKS; ++blk) {
+            sb += H->h_aa_part[(long)blk * 2 * AA_MAX + a];
+            sn += H->h_aa_part[(long)blk * 2 * AA_MAX + AA_MAX + a];
+          }
+          bvec[a] = sb;
+          newrow[a] = sn;
+        }
+        if (!first)
+          for (int a = 0; a < ncol; ++a) {
+            M[slot * AA_MAX + cols.slot[a]] = newrow[a];
+            M[cols.slot[a] * AA_MAX + slot] = newrow[a];
+          }
+        double Ms[AA_MAX * AA_MAX], gam[AA_MAX];
+        for (int a = 0; a < ncol; ++a)
+          for (int b = 0; b < ncol; ++b) Ms[a * ncol + b] = M[cols.slot[a] * AA_MAX + cols.slot[b]];
+        if (gram_solve(ncol, Ms, bvec, gam) == 0) {
+          for (int a = 0; a < ncol; ++a) cols.gamma[a] = gam[a];
+          launch_aa_combine(L0.v64, e.ncomp, stride, L0.u, adG, cols, H->st);
+          if (e.kind == EQ_VEC) fill_all64(H, e, 0);
+        } else {
+          ncol = 0;  // degenerate history: restart the mixing
+        }
       }
-      vcycle32(H, e, 0);
-      for (int c = 0; c < e.ncomp; ++c) launch_add_correction<float>(v, L0.u[c], L0.e[c], H->st);
-      if (e.kind == EQ_VEC) fill_all64(H, e, 0);
     }
-    if (e.zero_mean) launch_sub_mean(L0.v64, L0.u[0], H->d_part, NPARTS, H->st);
     ++cyc;
     st = finest_norm(H, e, &rel);
     if (st) return st;
@@ -712,19 +901,29 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
     H->d.hi[2] = 1.0;
   }
   H->st = (cudaStream_t)cuda_stream;
+  if (H->st == nullptr || H->st == cudaStreamLegacy || H->st == cudaStreamPerThread) {
+    // an owned blocking stream: ordered after the caller's legacy-stream
+    // work, and capturable into CUDA graphs
+    if (cudaStreamCreate(&H->st) != cudaSuccess) {
+      delete H;
+      return fail(MG_ERR_CUDA, "stream creation failed");
+    }
+    H->own_stream = true;
+  }
   int n[MAX_LEVELS][3];
   double h[MAX_LEVELS][3];
   H->nlev = level_sizes(&H->d, n, h);
   const size_t bytes = layout(nullptr, &H->d, nullptr);
   if (cudaMalloc(&H->arena, bytes) != cudaSuccess) {
-    delete H;
+    H->arena = nullptr;
+    mg_destroy_hierarchy(H);
     return fail(MG_ERR_OOM, "arena allocation failed");
   }
   H->arena_bytes = bytes;
   layout(H, &H->d, H->arena);
   if (cudaMallocHost(&H->h_red, sizeof(unsigned long long) * 8) != cudaSuccess) {
-    cudaFree(H->arena);
-    delete H;
+    H->h_red = nullptr;
+    mg_destroy_hierarchy(H);
     return fail(MG_ERR_OOM, "pinned allocation failed");
   }
   cudaMemsetAsync(H->arena, 0, bytes, H->st);
@@ -743,11 +942,19 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
     std::vector<double> ti, tj;
     make_tables(&H->d, L, ti, tj);
     std::vector<float> ti32(ti.begin(), ti.end()), tj32(tj.begin(), tj.end());
-    CK(cudaMemcpyAsync(L.ti64, ti.data(), sizeof(double) * ti.size(), cudaMemcpyHostToDevice, H->st));
-    CK(cudaMemcpyAsync(L.tj64, tj.data(), sizeof(double) * tj.size(), cudaMemcpyHostToDevice, H->st));
-    CK(cudaMemcpyAsync(L.ti32, ti32.data(), sizeof(float) * ti32.size(), cudaMemcpyHostToDevice, H->st));
-    CK(cudaMemcpyAsync(L.tj32, tj32.data(), sizeof(float) * tj32.size(), cudaMemcpyHostToDevice, H->st));
-    CK(cudaStreamSynchronize(H->st));  // host tables go out of scope
+    cudaError_t ce = cudaMemcpyAsync(L.ti64, ti.data(), sizeof(double) * ti.size(), cudaMemcpyHostToDevice, H->st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(L.tj64, tj.data(), sizeof(double) * tj.size(), cudaMemcpyHostToDevice, H->st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(L.ti32, ti32.data(), sizeof(float) * ti32.size(), cudaMemcpyHostToDevice, H->st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(L.tj32, tj32.data(), sizeof(float) * tj32.size(), cudaMemcpyHostToDevice, H->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(H->st);  // host tables go out of scope
+    if (ce != cudaSuccess) {
+      mg_destroy_hierarchy(H);
+      std::snprintf(g_last_error, sizeof(g_last_error), "table upload: %s", cudaGetErrorString(ce));
+      return MG_ERR_CUDA;
+    }
     L.v64 = make_view<double>(&H->d, L, L.ti64, L.tj64);
     L.v32 = make_view<float>(&H->d, L, L.ti32, L.tj32);
   }
@@ -787,9 +994,14 @@ int mg_profile_read(mg_hierarchy* H, int klass, int64_t* launches, double* ms, i
 
 int mg_destroy_hierarchy(mg_hierarchy* H) {
   if (!H) return MG_OK;
-  cudaStreamSynchronize(H->st);
+  if (H->st) cudaStreamSynchronize(H->st);
   for (cudaEvent_t e : H->ev) cudaEventDestroy(e);
   for (double* p : H->stage) cudaFree(p);
+  if (H->aa) cudaFree(H->aa);
+  if (H->d_aa_part) cudaFree(H->d_aa_part);
+  if (H->h_aa_part) cudaFreeHost(H->h_aa_part);
+  for (GraphEntry& g : H->graphs) cudaGraphExecDestroy(g.exec);
+  if (H->own_stream) cudaStreamDestroy(H->st);
   cudaFree(H->arena);
   cudaFreeHost(H->h_red);
   delete H;

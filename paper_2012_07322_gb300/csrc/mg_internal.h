@@ -71,4 +71,21 @@ void launch_xcfc_ap_init(const LevelView<double>& L, const double* alpha, const 
 void launch_xcfc_alpha_out(const LevelView<double>& L, const double* dap, const double* dpsi, double* alpha,
                            cudaStream_t st);
 
+// Anderson mixing (mg_accel.cu): live ring slots of the difference columns
+// in age order, with their mixing weights.
+constexpr int AA_MAX = 16;
+constexpr int AA_BLOCKS = 304;     // 2 x 152 SMs
+constexpr int AA_DOT_X = 64;       // threads per column in the dot-product kernel
+struct AACols {
+  int n;
+  int slot[AA_MAX];
+  double gamma[AA_MAX];
+};
+void launch_aa_update(const LevelView<double>& L, int ncomp, long stride, double* const g[3], const double* x,
+                      double* fprev, double* gprev, double* dF, double* dG, int first, cudaStream_t st);
+void launch_aa_dots(const LevelView<double>& L, int ncomp, long stride, const double* f, const double* dF,
+                    const AACols& cols, int newcol, double* part, cudaStream_t st);
+void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], const double* dG,
+                       const AACols& cols, cudaStream_t st);
+
 }  // namespace gmg

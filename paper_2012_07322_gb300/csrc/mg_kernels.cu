@@ -214,10 +214,11 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, co
 
 // Newton-Gauss-Seidel as the coarsest-grid solver (Sec. 2.7.2): one block
 // sweeps until the max residual falls below 1e-12 of its initial value or
-// 100 sweeps.  Storage type T, arithmetic in T.
+// max_sweeps sweeps.  The bodies work on any address space: the kernels
+// below run them on shared-memory copies of the level when it fits.
 template <typename T, int G, int KIND>
-__global__ void k_coarse_scalar(LevelView<T> L, T* __restrict__ u, const T* __restrict__ f,
-                                const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps) {
+__device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, const T* __restrict__ f,
+                                   const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps) {
   __shared__ double red[32];
   __shared__ double r0s;
   const long n = (long)L.n0 * L.n1 * L.n2;
@@ -225,7 +226,8 @@ __global__ void k_coarse_scalar(LevelView<T> L, T* __restrict__ u, const T* __re
   auto resmax = [&]() -> double {
     double m = 0.0;
     for (long q = tid; q < n; q += blockDim.x) {
-      const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+      int i, j, k;
+    L.cell(q, i, j, k);
       const long p = L.idx(i, j, k);
       T D;
       const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
@@ -261,9 +263,9 @@ __global__ void k_coarse_scalar(LevelView<T> L, T* __restrict__ u, const T* __re
 }
 
 template <typename T, int G>
-__global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
-                             const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
-                             int max_sweeps) {
+__device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
+                                const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
+                                int max_sweeps) {
   __shared__ double red[32];
   __shared__ double r0s;
   const long n = (long)L.n0 * L.n1 * L.n2;
@@ -278,7 +280,8 @@ __global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
   auto resmax = [&]() -> double {
     double m = 0.0;
     for (long q = tid; q < n; q += blockDim.x) {
-      const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+      int i, j, k;
+    L.cell(q, i, j, k);
       const long p = L.idx(i, j, k);
       for (int c = 0; c < 3; ++c) {
         T D;
@@ -318,6 +321,65 @@ __global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
   }
 }
 
+// Block copies between global and shared memory (all ghosted cells).
+template <typename T>
+__device__ __forceinline__ void block_copy(T* dst, const T* src, long n) {
+  for (long q = threadIdx.x; q < n; q += blockDim.x) dst[q] = src[q];
+}
+
+template <typename T, int G, int KIND>
+__global__ void k_coarse_scalar(LevelView<T> L, T* __restrict__ u, const T* __restrict__ f,
+                                const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps, int use_smem) {
+  if (!use_smem) {
+    coarse_scalar_body<T, G, KIND>(L, u, f, s0, s1, max_sweeps);
+    return;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const long ng = L.sy * (L.n2 + 2 * L.three);
+  T* su = sm;
+  T* sf = f ? sm + ng : nullptr;
+  T* s0s = s0 ? sm + 2 * ng : nullptr;
+  T* s1s = s1 ? sm + 3 * ng : nullptr;
+  block_copy(su, u, ng);
+  if (f) block_copy(sf, f, ng);
+  if (s0) block_copy(s0s, s0, ng);
+  if (s1) block_copy(s1s, s1, ng);
+  __syncthreads();
+  coarse_scalar_body<T, G, KIND>(L, su, sf, s0s, s1s, max_sweeps);
+  __syncthreads();
+  block_copy(u, su, ng);
+}
+
+template <typename T, int G>
+__global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
+                             const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
+                             int max_sweeps, int use_smem) {
+  if (!use_smem) {
+    coarse_vec_body<T, G>(L, A, B, C, f0, f1, f2, max_sweeps);
+    return;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const long ng = L.sy * (L.n2 + 2 * L.three);
+  T* V[3] = {sm, sm + ng, sm + 2 * ng};
+  const T* fg[3] = {f0, f1, f2};
+  T* fsm[3];
+  for (int c = 0; c < 3; ++c) {
+    fsm[c] = fg[c] ? sm + (3 + c) * ng : nullptr;
+    if (fg[c]) block_copy(fsm[c], fg[c], ng);
+  }
+  block_copy(V[0], A, ng);
+  block_copy(V[1], B, ng);
+  block_copy(V[2], C, ng);
+  __syncthreads();
+  coarse_vec_body<T, G>(L, V[0], V[1], V[2], fsm[0], fsm[1], fsm[2], max_sweeps);
+  __syncthreads();
+  block_copy(A, V[0], ng);
+  block_copy(B, V[1], ng);
+  block_copy(C, V[2], ng);
+}
+
 // ------------------------------------------------------------- helpers
 
 // u -= mean(u interior); sums in a fixed order (deterministic).
@@ -327,7 +389,8 @@ __global__ void k_partial_sum(LevelView<T> L, const T* __restrict__ u, double* _
   const long n = (long)L.n0 * L.n1 * L.n2;
   double s = 0.0;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     s += (double)u[L.idx(i, j, k)];
   }
   s = warp_sum(s);
@@ -351,7 +414,8 @@ __global__ void k_sub_mean(LevelView<T> L, T* __restrict__ u, const double* __re
   __syncthreads();
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     u[p] = (T)((double)u[p] - mean);
   }
@@ -362,7 +426,8 @@ template <typename A, typename B>
 __global__ void k_copy_in(LevelView<B> L, const A* __restrict__ src, B* __restrict__ dst, A shift) {
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     dst[L.idx(i, j, k)] = (B)(src[q] + shift);
   }
 }
@@ -370,7 +435,8 @@ template <typename A, typename B>
 __global__ void k_copy_out(LevelView<A> L, const A* __restrict__ src, B* __restrict__ dst, A shift) {
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     dst[q] = (B)(src[L.idx(i, j, k)] + shift);
   }
 }
@@ -379,7 +445,8 @@ template <typename A, typename B>
 __global__ void k_convert(LevelView<A> L, const A* __restrict__ src, B* __restrict__ dst) {
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     dst[p] = (B)src[p];
   }
@@ -389,7 +456,8 @@ template <typename T>
 __global__ void k_add_correction(LevelView<double> L, double* __restrict__ u, const T* __restrict__ e) {
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     u[p] += (double)e[p];
   }
@@ -492,18 +560,41 @@ void launch_prolong(const LevelView<T>& F, const LevelView<T>& C, T* u, const T*
   k_prolong<T><<<g, b, 0, st>>>(F, C, u, uH, uhH, comp);
 }
 
+// The coarsest level runs from shared memory when its ghosted arrays fit.
+constexpr size_t COARSE_SMEM_MAX = 160 * 1024;
+
+template <typename T>
+static size_t coarse_smem_bytes(const LevelView<T>& L, int narrays) {
+  const long ng = L.sy * (L.n2 + 2 * L.three);
+  return sizeof(T) * (size_t)ng * narrays;
+}
+
 template <typename T>
 void launch_coarse_scalar(const LevelView<T>& L, int kind, T* u, const T* f, const T* s0, const T* s1,
                           int max_sweeps, cudaStream_t st) {
   count_launch();
-  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_coarse_scalar<T, GG, EQ_PSI><<<1, 256, 0, st>>>(L, u, f, s0, s1, max_sweeps);
-                    else k_coarse_scalar<T, GG, EQ_LIN><<<1, 256, 0, st>>>(L, u, f, s0, s1, max_sweeps));
+  const size_t sb = coarse_smem_bytes(L, 4);
+  const int use = sb <= COARSE_SMEM_MAX;
+  const size_t dyn = use ? sb : 0;
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) {
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_PSI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_coarse_scalar<T, GG, EQ_PSI><<<1, 256, dyn, st>>>(L, u, f, s0, s1, max_sweeps, use);
+  } else {
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_coarse_scalar<T, GG, EQ_LIN><<<1, 256, dyn, st>>>(L, u, f, s0, s1, max_sweeps, use);
+  });
 }
 
 template <typename T>
 void launch_coarse_vec(const LevelView<T>& L, T* V[3], const T* const f[3], int max_sweeps, cudaStream_t st) {
   count_launch();
-  GMG_GEOM_DISPATCH(L.geom, k_coarse_vec<T, GG><<<1, 256, 0, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], max_sweeps));
+  const size_t sb = coarse_smem_bytes(L, 6);
+  const int use = sb <= COARSE_SMEM_MAX;
+  const size_t dyn = use ? sb : 0;
+  GMG_GEOM_DISPATCH(L.geom, {
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_coarse_vec<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_coarse_vec<T, GG><<<1, 256, dyn, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], max_sweeps, use);
+  });
 }
 
 template <typename T>

@@ -144,7 +144,8 @@ __global__ void k_div_central(LevelView<double> L, const double* __restrict__ B0
   const double c0 = 0.5 / L.h0, c1 = 0.5 / L.h1, c2 = 0.5 / L.h2;
   double acc = 0.0;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / s2);
+    int i, j, k;
+    L.cell(q, i, j, k);
     double d = (B0[i < L.n0 - 1 ? q + 1 : q] - B0[i > 0 ? q - 1 : q]) * c0 +
                (B1[j < L.n1 - 1 ? q + s1 : q] - B1[j > 0 ? q - s1 : q]) * c1;
     if (L.three) d += (B2[k < L.n2 - 1 ? q + s2 : q] - B2[k > 0 ? q - s2 : q]) * c2;
@@ -169,7 +170,8 @@ __global__ void k_div_norms(LevelView<double> L, const double* __restrict__ div,
   double s = 0.0;
   double m[1] = {0.0};
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const double d = div[L.idx(i, j, k)];
     s += d * d;
     m[0] = fmax(m[0], fabs(d));
@@ -198,7 +200,8 @@ __global__ void k_sub_mean_into(LevelView<double> L, const double* __restrict__ 
   __syncthreads();
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     b[p] = div[p] - mean;
   }
@@ -210,7 +213,8 @@ __global__ void k_grad_update(LevelView<double> L, const double* __restrict__ ph
   const long n = (long)L.n0 * L.n1 * L.n2;
   const double c0 = 0.5 / L.h0, c1 = 0.5 / L.h1, c2 = 0.5 / L.h2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     const double pc = phi[p];
     B0[q] -= ((i < L.n0 - 1 ? phi[p + 1] : pc) - (i > 0 ? phi[p - 1] : pc)) * c0;
@@ -241,7 +245,8 @@ __global__ void k_ap_init(LevelView<double> L, const double* __restrict__ alpha,
                           double* __restrict__ dap) {
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     dap[p] = alpha[q] * (1.0 + dpsi[p]) - 1.0;
   }
@@ -250,7 +255,8 @@ __global__ void k_alpha_out(LevelView<double> L, const double* __restrict__ dap,
                             double* __restrict__ alpha) {
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.n0), j = (int)((q / L.n0) % L.n1), k = (int)(q / ((long)L.n0 * L.n1));
+    int i, j, k;
+    L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     alpha[q] = (1.0 + dap[p]) / (1.0 + dpsi[p]);
   }

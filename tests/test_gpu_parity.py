@@ -37,7 +37,7 @@ def mg():
 
 
 def dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    return torch.from_numpy(np.array(a, dtype=np.float64, copy=True)).cuda()
 
 
 def host(t):
@@ -60,7 +60,8 @@ def relerr(a, b):
 
 
 def descs(mg, geom, n, lo, hi, **kw):
-    okw = {k: v for k, v in kw.items() if k in ("tol", "max_cycles", "nu1", "nu2", "mixed", "stall_window")}
+    okw = {k: v for k, v in kw.items()
+           if k in ("tol", "max_cycles", "nu1", "nu2", "mixed", "stall_window", "accel_depth")}
     gkw = dict(okw)
     if "precision" in kw:
         gkw["precision"] = kw["precision"]
@@ -236,8 +237,8 @@ def test_vector_solve_parity(mg, geom, n, lo, hi, mixed):
     h.close()
 
 
-def run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="fp64", psi_only=False, tol=1e-10):
-    d, gd = descs(mg, geom, n, lo, hi, tol=tol, max_cycles=1000, precision=precision)
+def run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="fp64", psi_only=False, tol=1e-10, accel_depth=0):
+    d, gd = descs(mg, geom, n, lo, hi, tol=tol, max_cycles=1000, precision=precision, accel_depth=accel_depth)
     shp = o.shape(d)
     psi, alpha = np.ones(shp), np.ones(shp)
     beta = [np.zeros(shp) for _ in range(3)]
@@ -266,22 +267,27 @@ def field_errors(got, want, psi_only=False):
     return errs
 
 
-def test_c1_psi_parity(mg):
-    """Static n = 1 polytrope on the 64 x 32 spherical grid, eq. psi only."""
+@pytest.mark.parametrize("accel", [0, 8])
+def test_c1_psi_parity(mg, accel):
+    """Static n = 1 polytrope on the 64 x 32 spherical grid, eq. psi only,
+    plain V-cycles and Anderson-mixed V-cycles."""
     U = inputs.static_polytrope_sph2d()
     z = np.zeros_like(U)
-    rg, ro, got, want = run_cfc_pair(mg, "sph", [64, 32], [0, 0], [100.0, PI], U, z, [z, z, z], psi_only=True)
+    rg, ro, got, want = run_cfc_pair(mg, "sph", [64, 32], [0, 0], [100.0, PI], U, z, [z, z, z], psi_only=True,
+                                     accel_depth=accel)
     check_report(rg["psi"], ro["psi"], 1e-10)
     errs = field_errors(got, want, psi_only=True)
     assert errs["psi"] < 1e-9 and errs["dpsi"] < 1e-9, errs
 
 
-@pytest.mark.parametrize("geom,n,hi", [
-    ("sph", [64, 32], [100.0, PI]),
-    ("sph", [32, 16, 16], [100.0, PI, 2 * PI]),
-    ("cyl", [32, 64], [100.0, 100.0]),
+@pytest.mark.parametrize("geom,n,hi,accel", [
+    ("sph", [64, 32], [100.0, PI], 0),
+    ("sph", [32, 16, 16], [100.0, PI, 2 * PI], 0),
+    ("cyl", [32, 64], [100.0, 100.0], 0),
+    ("sph", [32, 16, 16], [100.0, PI, 2 * PI], 8),
+    ("sph", [64, 32, 32], [100.0, PI, 2 * PI], 8),
 ])
-def test_xcfc_parity(mg, geom, n, hi):
+def test_xcfc_parity(mg, geom, n, hi, accel):
     """Full xCFC sequence on a rotating polytrope (Steps 1-6, Sec. 2.6)."""
     if geom == "sph" and len(n) == 2:
         U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], hi[0])
@@ -292,7 +298,7 @@ def test_xcfc_parity(mg, geom, n, hi):
     else:
         U, S, Si = inputs.rotating_polytrope_cyl(n, hi[0])
         lo = [0.0, -hi[1]]
-    rg, ro, got, want = run_cfc_pair(mg, geom, n, lo, hi, U, S, Si)
+    rg, ro, got, want = run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, accel_depth=accel)
     for k in ("X", "psi", "alphapsi", "beta"):
         check_report(rg[k], ro[k], 1e-10)
     errs = field_errors(got, want)
@@ -323,13 +329,15 @@ def test_divb_cleaning_parity(mg):
 # ------------------------------------------------------ mixed precision
 
 
-def test_mixed_precision_xcfc_error_vs_oracle(mg):
+@pytest.mark.parametrize("accel", [0, 8])
+def test_mixed_precision_xcfc_error_vs_oracle(mg, accel):
     """FP32 smoothing inside FP64 defect correction: every equation reaches
     the FP64 relative residual 1e-10 and every field stays within 1e-8 of
     the FP64 oracle."""
     n = [32, 16, 16]
     U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
-    rg, ro, got, want = run_cfc_pair(mg, "sph", n, [0, 0, 0], [100.0, PI, 2 * PI], U, S, Si, precision="mixed")
+    rg, ro, got, want = run_cfc_pair(mg, "sph", n, [0, 0, 0], [100.0, PI, 2 * PI], U, S, Si, precision="mixed",
+                                     accel_depth=accel)
     for k in ("X", "psi", "alphapsi", "beta"):
         assert rg[k]["status"] == "ok" and rg[k]["rel"] <= 1e-10
     errs = field_errors(got, want)
