@@ -274,6 +274,39 @@ int mg_profile_enable(mg_hierarchy* h, int enable);
  * one class since the last mg_profile_enable (synchronises the stream). */
 int mg_profile_read(mg_hierarchy* h, int klass, int64_t* launches, double* ms, int64_t* cells);
 
+/* ------------------------------------------ allocation-free diagnostics */
+
+/* Largest grid (cells) mg_divb_norms_noalloc accepts: the size of its
+ * static device scratch (16 MiB on every GPU that loads the library). */
+#define MG_NOALLOC_MAX_CELLS 2097152
+
+/*
+ * Max |div B| and |div B|_2 = sqrt(mean(div^2)) of the central divergence
+ * of a Cartesian field (the same numbers mg_clean_divB reports as
+ * max_div_before / l2_div_before), for callers that cannot allocate device
+ * memory and so cannot create a hierarchy: a host framework that owns all
+ * device memory and forbids allocation inside its time loop, or code whose
+ * cudaMalloc would synchronise the device.  The paper has no counterpart:
+ * this entry point exists only for such callers.
+ *   ndim, n, lo, hi   the grid (n[d] >= 1, lo < hi; n[2], lo[2], hi[2]
+ *                     ignored in 2D); at most MG_NOALLOC_MAX_CELLS cells,
+ *                     larger grids get MG_ERR_INVALID (see mg_last_error).
+ *   B                 ndim device arrays, ghost-free, dimension 0 fastest;
+ *                     ghosts are copies of the boundary cells.
+ *   cuda_stream       cudaStream_t to run on (NULL: the legacy stream); the
+ *                     call synchronises it before returning.
+ *   max_div, l2_div   host outputs.
+ * It allocates nothing: its scratch (the divergence values, per-block sums
+ * and the max word) is a file-scope __device__ array.  The first call on a
+ * device looks up that array's device address with the device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents (the
+ * max word is cleared by each call): calls whose work overlaps on the GPU
+ * (different streams or threads at once) race, so serialise them.
+ */
+int mg_divb_norms_noalloc(int ndim, const int n[3], const double lo[3], const double hi[3],
+                          const double* B[3], void* cuda_stream, double* max_div, double* l2_div);
+
 #ifdef __cplusplus
 }
 #endif

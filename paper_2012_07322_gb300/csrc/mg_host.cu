@@ -859,6 +859,8 @@ void copy_out(mg_hierarchy* H, const double* src, double* dst, double shift = 0.
 
 }  // namespace
 
+int gmg::set_last_error(int status, const char* msg) { return fail(status, msg); }
+
 // ================================================================== C ABI
 
 extern "C" {

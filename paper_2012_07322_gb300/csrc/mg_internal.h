@@ -5,6 +5,9 @@
 
 namespace gmg {
 
+// Record a message for mg_last_error on the calling thread; returns status.
+int set_last_error(int status, const char* msg);
+
 // Count of kernel launches issued by the library (all hierarchies).
 void count_launch(int n = 1);
 unsigned long long launch_count();

@@ -35,7 +35,8 @@ STATUS = {0: "ok", 1: "invalid", 2: "oom", 3: "noconv", 4: "stalled", 5: "nan", 
 EXPORTS = ["mg_strerror", "mg_last_error", "mg_hierarchy_bytes", "mg_create_hierarchy", "mg_destroy_hierarchy",
            "mg_num_levels", "mg_solve_cfc", "mg_clean_divB", "mg_solve_scalar", "mg_solve_vector",
            "mg_apply_operator", "mg_smooth", "mg_compute_a2", "mg_divergence", "mg_restrict", "mg_prolong_add",
-           "mg_kernel_launches", "mg_profile_enable", "mg_profile_read"]
+           "mg_kernel_launches", "mg_profile_enable", "mg_profile_read", "mg_divb_norms_noalloc"]
+MG_NOALLOC_MAX_CELLS = 2097152
 PROF_CLASSES = ["smooth64_scalar", "smooth64_vec", "smooth32_scalar", "smooth32_vec", "resid64_scalar",
                 "resid64_vec"]
 
@@ -109,6 +110,9 @@ def lib():
         L.mg_kernel_launches.argtypes = []
         L.mg_profile_enable.argtypes = [P, I]
         L.mg_profile_read.argtypes = [P, I, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.mg_divb_norms_noalloc.argtypes = [I, C.POINTER(C.c_int * 3), C.POINTER(C.c_double * 3),
+                                            C.POINTER(C.c_double * 3), C.POINTER(P), P,
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
         return L
 
@@ -327,3 +331,28 @@ def mg_profile_read(h):
         _check(lib().mg_profile_read(h.handle, k, C.byref(n), C.byref(ms), C.byref(cells)), "mg_profile_read")
         out[name] = (n.value, ms.value, cells.value)
     return out
+
+
+def mg_divb_norms_noalloc(B, lo, hi, stream=None, allow=(MG_OK,)):
+    """(max |div B|, |div B|_2) of a Cartesian field through the
+    allocation-free entry point; B is a list of ndim CUDA float64 tensors
+    shaped (n1, n0) or (n2, n1, n0).  Returns (status, max, l2)."""
+    import torch
+    nd = len(B)
+    shp = tuple(B[0].shape)
+    n = (C.c_int * 3)(*([shp[nd - 1 - d] for d in range(nd)] + [1] * (3 - nd)))
+    lo3 = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - nd)))
+    hi3 = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - nd)))
+    arr = (C.c_void_p * 3)()
+    for k, t in enumerate(B):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and tuple(t.shape) == shp):
+            raise ValueError("B[%d] must be a contiguous CUDA float64 tensor of shape %s" % (k, shp))
+        arr[k] = t.data_ptr()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    mx, l2 = C.c_double(), C.c_double()
+    st = lib().mg_divb_norms_noalloc(nd, C.byref(n), C.byref(lo3), C.byref(hi3), arr,
+                                     C.c_void_p(stream.cuda_stream), C.byref(mx), C.byref(l2))
+    _check(st, "mg_divb_norms_noalloc", allow)
+    return st, mx.value, l2.value
