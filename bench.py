@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-divb", action="store_true", help="skip the 256^3 div-B cleaning measurement")
+    p.add_argument("--no-serve", action="store_true", help="skip the request-serving measurement")
     return p.parse_args()
 
 
@@ -85,8 +86,11 @@ def level_cells():
 #     one, read its right-hand side             -> 8 words per updated cell
 #   finest residual, scalar: read u, 2 inputs, write r -> 4 words per cell
 #   finest residual, vector: read 3 u, 3 f, write 3 r  -> 9 words per cell
+#   fused red-black sweep (Cartesian scalar): read u and f (and c), write u
+#                                               -> 3 words per cell (4 with c)
 BYTES_PER_CELL = {"smooth64_scalar": 5 * 8, "smooth64_vec": 8 * 8, "smooth32_scalar": 5 * 4,
-                  "smooth32_vec": 8 * 4, "resid64_scalar": 4 * 8, "resid64_vec": 9 * 8 / 3}
+                  "smooth32_vec": 8 * 4, "resid64_scalar": 4 * 8, "resid64_vec": 9 * 8 / 3,
+                  "sweep64_fused": 3 * 8, "sweep32_fused": 3 * 4}
 
 
 class ClockSampler:
@@ -174,7 +178,7 @@ def divb_measurement(mg, torch, stream, steps, precision, peak):
     prof = mg.mg_profile_read(h)
     mg.mg_profile_enable(h, False)
     h.close()
-    key = "smooth32_scalar" if precision == "mixed" else "smooth64_scalar"
+    key = "sweep32_fused" if precision == "mixed" else "sweep64_fused"
     nl, kms, kcells = prof[key]
     bpl = kcells * BYTES_PER_CELL[key] / max(nl, 1)
     ach = bpl / (kms / max(nl, 1) * 1e-3) / 1e9 if nl else 0.0
@@ -187,6 +191,91 @@ def divb_measurement(mg, torch, stream, steps, precision, peak):
             "roofline": {"bound": "hbm", "kernel": key, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "avg_launch_us": kms / max(nl, 1) * 1e3,
                          "algorithmic_bytes_per_launch": bpl, "launches": nl}}
+
+
+def serving_measurement(mg, torch, n_requests=160, rate=2000.0, slots=8):
+    """Request serving: Poisson arrivals (mean `rate` per second, seed 3) of
+    a mix of xCFC solves (80 %) and div-B cleanings (20 %) of several sizes,
+    16 warm-started streams, through mg_submit / mg_poll."""
+    import time
+    from paper_2012_07322_gb300 import inputs
+    rng = np.random.default_rng(3)
+    kinds = [("sph", [64, 32], [0.0, 0.0], [100.0, np.pi]),
+             ("sph", [128, 64], [0.0, 0.0], [100.0, np.pi]),
+             ("cyl", [64, 128], [0.0, -100.0], [100.0, 100.0]),
+             ("sph", [32, 16, 16], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]),
+             ("sph", [64, 32, 32], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi])]
+    dev = lambda a: torch.from_numpy(np.array(a)).cuda()
+    streams = []
+    for sid in range(16):
+        geom, n, lo, hi = kinds[sid % len(kinds)]
+        rho_c, R = rng.uniform(5e-4, 2e-3), rng.uniform(8.0, 14.0)
+        if geom == "cyl":
+            U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0, rho_c, R)
+        elif len(n) == 2:
+            U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], 100.0, rho_c, R)
+        else:
+            U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0, rho_c, R)
+        desc = mg.grid_desc(geom, n, lo, hi, precision="mixed", tol=TOL, max_cycles=800, accel_depth=16,
+                            stall_window=0)
+        streams.append((desc, dev(U), dev(S), [dev(x) for x in Si]))
+    divbs = []
+    for n in (32, 64):
+        B = inputs.divb_field(n=n, n_modes=16, k_max=6)
+        desc = mg.grid_desc("cart", [n] * 3, [-1.0] * 3, [1.0] * 3, precision="mixed", tol=TOL, max_cycles=200,
+                            stall_window=0)
+        divbs.append((desc, [dev(b) for b in B]))
+    plan = []
+    t = 0.0
+    for q in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        plan.append((t, "divb" if rng.uniform() < 0.2 else "cfc", int(rng.integers(0, 16)), int(rng.integers(0, 2))))
+    srv = mg.Server(hbm_budget=48 << 30, max_slots=slots, max_queue=4 * n_requests)
+    # warm the hierarchy cache and the resident streams once
+    for sid, (desc, U, S, Si) in enumerate(streams):
+        psi = torch.ones(U.shape, dtype=torch.float64, device="cuda")
+        f = (psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)],
+             [torch.zeros_like(psi) for _ in range(3)])
+        srv.wait(srv.submit_cfc(desc, U, S, Si, *f, stream_id=sid + 1))
+    for desc, B in divbs:
+        srv.wait(srv.submit_divb(desc, [b.clone() for b in B]))
+    torch.cuda.synchronize()
+    pending, lat, statuses = {}, [], []
+    t0 = time.perf_counter()
+    for (ta, kind, sid, which) in plan:
+        while time.perf_counter() - t0 < ta:
+            for tk in list(pending):
+                done, res = srv.poll(tk)
+                if done:
+                    lat.append(res["latency_ms"])
+                    statuses.append(res["status"])
+                    del pending[tk]
+        if kind == "cfc":
+            desc, U, S, Si = streams[sid]
+            psi = torch.ones(U.shape, dtype=torch.float64, device="cuda")
+            f = (psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)],
+                 [torch.zeros_like(psi) for _ in range(3)])
+            tk = srv.submit_cfc(desc, U, S, Si, *f, stream_id=sid + 1)
+        else:
+            desc, B = divbs[which]
+            tk = srv.submit_divb(desc, [b.clone() for b in B])
+        pending[tk] = True
+    while pending:
+        for tk in list(pending):
+            done, res = srv.poll(tk)
+            if done:
+                lat.append(res["latency_ms"])
+                statuses.append(res["status"])
+                del pending[tk]
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat.sort()
+    return {"workload": "Poisson arrivals (mean %.0f/s, seed 3) of %d requests: 80%% xCFC (2D sph 64x32, "
+                        "128x64, 2D cyl 64x128, 3D sph 32x16x16, 64x32x32; 16 warm-started streams), 20%% "
+                        "div-B (32^3, 64^3); mixed precision, %d slots" % (rate, n_requests, slots),
+            "solves_per_s": n_requests / wall, "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "wall_s": wall,
+            "ok": sum(1 for s in statuses if s == "ok"), "requests": n_requests}
 
 
 def oracle_sample(threads):
@@ -376,6 +465,9 @@ def main():
     divb = None
     if not args.no_divb:
         divb = divb_measurement(mg, torch, stream, args.steps, args.precision, peak)
+    serving = None
+    if not args.no_serve and world == 1:
+        serving = serving_measurement(mg, torch)
 
     r0 = reps[-1]
     if rank == 0:
@@ -394,7 +486,7 @@ def main():
                        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "parallelism": "replicas (independent solves per GPU)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "divb_256": divb,
+            "clocks": clocks, "divb_256": divb, "serving": serving,
         }
         print(json.dumps(line))
     h.close()

@@ -137,6 +137,10 @@ int mg_hierarchy_bytes(const mg_grid_desc* desc, size_t* bytes);
  * on the current CUDA device.  cuda_stream is a cudaStream_t (NULL: the
  * legacy default stream); all work of the hierarchy is enqueued on it.
  * The hierarchy owns its allocations; mg_destroy_hierarchy frees them.
+ * With a default stream (NULL, legacy or per-thread) the work runs on a
+ * stream the hierarchy owns, ordered after the work already queued on the
+ * default stream at each call (default streams cannot be captured into
+ * the CUDA graphs the cycle replays).
  */
 int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarchy** out);
 int mg_destroy_hierarchy(mg_hierarchy* h);
@@ -247,6 +251,57 @@ int mg_divergence(mg_hierarchy* h, const double* B[3], double* div);
 int mg_restrict(mg_hierarchy* h, const double* fine, double* coarse);
 int mg_prolong_add(mg_hierarchy* h, int bc, const double* coarse_e, double* fine);
 
+/* --------------------------------------------------------------- serving */
+
+/*
+ * A request server: a FIFO queue feeding max_slots worker slots, each a
+ * host thread with its own CUDA stream, so requests admitted while others
+ * run overlap on the device.  Hierarchies are cached per grid descriptor
+ * and reused; with a stream_id the solution of a CFC request stays resident
+ * and warm-starts the next request of that stream (the previous time
+ * step's metric as initial guess, Sec. 4.2.1), and the requests of one
+ * stream run in submission order.  Cached hierarchies and resident
+ * solutions stay within hbm_budget bytes (idle hierarchies are evicted,
+ * least recently used first; a request that does not fit waits).
+ */
+typedef struct mg_server mg_server;
+
+enum { MG_REQ_CFC = 0, MG_REQ_DIVB = 1 };
+
+typedef struct {
+  mg_grid_desc desc;       /* grid and solver settings of the request */
+  int kind;                /* MG_REQ_CFC or MG_REQ_DIVB */
+  int flags;               /* MG_CFC_PSI_ONLY (CFC) */
+  uint64_t stream_id;      /* 0: no warm start; else the request stream */
+  mg_cfc_sources src;      /* CFC: device pointers, caller-owned until done */
+  mg_cfc_fields io;        /* CFC: initial guess in (ignored when warm-started), solution out */
+  double* B[3];            /* DIVB: field cleaned in place */
+  double* phi;             /* DIVB: optional potential out */
+  void* wait_stream;       /* cudaStream_t whose work queued before mg_submit
+                              produced the inputs (NULL: the legacy stream) */
+} mg_request;
+
+typedef struct {
+  int status;
+  mg_cfc_report cfc;       /* CFC reports */
+  mg_divb_report divb;     /* DIVB report */
+  double latency_ms;       /* submission to completion */
+  double queue_ms;         /* submission to start */
+  int warm_started;        /* 1 if the stream's resident solution was the guess */
+} mg_result;
+
+/* Start a server on the current device. */
+int mg_server_create(size_t hbm_budget, int max_slots, int max_queue, mg_server** out);
+/* Stop it: running requests finish, queued ones complete with MG_ERR_BUSY;
+ * frees every hierarchy and resident solution. */
+int mg_server_destroy(mg_server* s);
+/* Queue a request (never blocks).  MG_ERR_BUSY when max_queue requests
+ * wait already, MG_ERR_OOM when the request alone exceeds the budget. */
+int mg_submit(mg_server* s, const mg_request* req, uint64_t* ticket);
+/* Non-blocking: *done = 1 once finished; then out (may be NULL) receives
+ * the result, the ticket is released and the request's status returned. */
+int mg_poll(mg_server* s, uint64_t ticket, int* done, mg_result* out);
+
 /* ------------------------------------------------------ instrumentation */
 
 /* Kernel launches issued by the library since it was loaded (all
@@ -254,8 +309,9 @@ int mg_prolong_add(mg_hierarchy* h, int bc, const double* coarse_e, double* fine
 uint64_t mg_kernel_launches(void);
 
 /* Kernel classes timed by mg_profile_*: red-black colour passes (one
- * launch updates half of the finest cells, one component) and the finest
- * residual with its norms (every cell, every component). */
+ * launch updates half of the finest cells, one component), fused
+ * red-black sweeps (both colours of a Cartesian scalar level in one launch)
+ * and the finest residual with its norms (every cell, every component). */
 enum {
   MG_PROF_SMOOTH64_SCALAR = 0,
   MG_PROF_SMOOTH64_VEC = 1,
@@ -263,7 +319,9 @@ enum {
   MG_PROF_SMOOTH32_VEC = 3,
   MG_PROF_RESID64_SCALAR = 4,
   MG_PROF_RESID64_VEC = 5,
-  MG_PROF_NCLASS = 6
+  MG_PROF_SWEEP64_FUSED = 6,  /* fused red-black sweep: all finest cells */
+  MG_PROF_SWEEP32_FUSED = 7,
+  MG_PROF_NCLASS = 8
 };
 
 /* Enable (1) or disable (0) CUDA-event timing, on the hierarchy's stream,

@@ -52,6 +52,8 @@ struct mg_hierarchy {
   mg_grid_desc d;
   cudaStream_t st = nullptr;   // work stream (the caller's, or an owned one)
   bool own_stream = false;
+  cudaStream_t user_st = nullptr;   // the caller's stream when st is owned
+  cudaEvent_t ev_in = nullptr;      // orders st after the caller's stream
   std::vector<GraphEntry> graphs;
   int nlev = 0;
   Level L[MAX_LEVELS];
@@ -381,7 +383,14 @@ void fill_all64(mg_hierarchy* H, const Eq& e, int l) {
 void smooth64(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
   Level& L = H->L[l];
   auto v = with_bc(L.v64, e.bc);
+  const bool fused = e.kind == EQ_LIN && fused_sweep_applies(v);
   for (int s = 0; s < nsweeps; ++s) {
+    if (fused) {
+      long tok = prof_begin(H, l, MG_PROF_SWEEP64_FUSED, L.cells());
+      launch_sweep_fused<double>(v, L.u[0], fptr(H, e, l, 0), s1ptr(H, e, l), H->st);
+      prof_end(H, tok);
+      continue;
+    }
     for (int colour = 0; colour < 2; ++colour) {
       if (e.kind != EQ_VEC) {
         long tok = prof_begin(H, l, MG_PROF_SMOOTH64_SCALAR, L.cells() / 2);
@@ -501,7 +510,14 @@ void smooth32(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
   Level& L = H->L[l];
   auto v = with_bc(L.v32, e.bc);
   const float* K = (e.kind == EQ_PSI || e.has_c) ? L.k32 : nullptr;
-  for (int s = 0; s < nsweeps; ++s)
+  const bool fused = e.kind != EQ_VEC && fused_sweep_applies(v);
+  for (int s = 0; s < nsweeps; ++s) {
+    if (fused) {
+      long tok = prof_begin(H, l, MG_PROF_SWEEP32_FUSED, L.cells());
+      launch_sweep_fused<float>(v, L.e[0], L.f32[0], K, H->st);
+      prof_end(H, tok);
+      continue;
+    }
     for (int colour = 0; colour < 2; ++colour) {
       if (e.kind != EQ_VEC) {
         long tok = prof_begin(H, l, MG_PROF_SMOOTH32_SCALAR, L.cells() / 2);
@@ -516,6 +532,7 @@ void smooth32(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
         }
       }
     }
+  }
   H->updates += (int64_t)nsweeps * L.cells() * e.ncomp;
 }
 
@@ -850,6 +867,15 @@ int stage_out(mg_hierarchy* H, const double* dev, double* host) {
   return MG_OK;
 }
 
+// Order the hierarchy's own stream after the work the caller queued on its
+// stream (every entry point that enqueues work calls this first).
+int enter(mg_hierarchy* H) {
+  if (!H->own_stream) return MG_OK;
+  CK(cudaEventRecord(H->ev_in, H->user_st));
+  CK(cudaStreamWaitEvent(H->st, H->ev_in, 0));
+  return MG_OK;
+}
+
 void copy_in(mg_hierarchy* H, const double* src, double* dst, double shift = 0.0) {
   launch_copy_in<double, double>(H->L[0].v64, src, dst, shift, H->st);
 }
@@ -860,6 +886,11 @@ void copy_out(mg_hierarchy* H, const double* src, double* dst, double shift = 0.
 }  // namespace
 
 int gmg::set_last_error(int status, const char* msg) { return fail(status, msg); }
+
+void gmg::hier_set_stream(mg_hierarchy* H, cudaStream_t st) {
+  if (H->own_stream || st == nullptr) return;
+  H->st = st;
+}
 
 // ================================================================== C ABI
 
@@ -904,9 +935,13 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
   }
   H->st = (cudaStream_t)cuda_stream;
   if (H->st == nullptr || H->st == cudaStreamLegacy || H->st == cudaStreamPerThread) {
-    // an owned blocking stream: ordered after the caller's legacy-stream
-    // work, and capturable into CUDA graphs
-    if (cudaStreamCreate(&H->st) != cudaSuccess) {
+    // the default streams cannot be captured into CUDA graphs: work runs on
+    // an owned non-blocking stream that each call orders after the caller's
+    // stream with an event (a blocking stream would tie the legacy stream to
+    // our captures)
+    H->user_st = H->st;
+    if (cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming) != cudaSuccess) {
       delete H;
       return fail(MG_ERR_CUDA, "stream creation failed");
     }
@@ -929,6 +964,8 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
     return fail(MG_ERR_OOM, "pinned allocation failed");
   }
   cudaMemsetAsync(H->arena, 0, bytes, H->st);
+  init_fused_sweep_attributes<double>();
+  init_fused_sweep_attributes<float>();
   const int three = H->d.ndim == 3;
   for (int l = 0; l < H->nlev; ++l) {
     Level& L = H->L[l];
@@ -1004,6 +1041,7 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   if (H->h_aa_part) cudaFreeHost(H->h_aa_part);
   for (GraphEntry& g : H->graphs) cudaGraphExecDestroy(g.exec);
   if (H->own_stream) cudaStreamDestroy(H->st);
+  if (H->ev_in) cudaEventDestroy(H->ev_in);
   cudaFree(H->arena);
   cudaFreeHost(H->h_red);
   delete H;
@@ -1023,6 +1061,7 @@ int mg_solve_scalar(mg_hierarchy* H, int kind, int bc, int zero_mean, const doub
   if (bc < MG_BC_ROBIN || bc > MG_BC_NEUMANN) return fail(MG_ERR_INVALID, "bad boundary condition");
   if (kind == MG_EQ_PSI && (!U || !A2)) return fail(MG_ERR_INVALID, "psi equation needs U and A2");
   if (kind == MG_EQ_LIN && !f) return fail(MG_ERR_INVALID, "linear equation needs f");
+  if (int est = enter(H)) return est;
   Level& L0 = H->L[0];
   Eq e{kind, bc, zero_mean ? 1 : 0, 1, kind == MG_EQ_LIN && c != nullptr};
   copy_in(H, u, L0.u[0]);
@@ -1043,6 +1082,7 @@ int mg_solve_vector(mg_hierarchy* H, int bc, const double* f[3], double* V[3], m
   if (!H || !f || !V) return fail(MG_ERR_INVALID, "null argument");
   for (int c = 0; c < 3; ++c)
     if (!f[c] || !V[c]) return fail(MG_ERR_INVALID, "null component");
+  if (int est = enter(H)) return est;
   Level& L0 = H->L[0];
   Eq e{MG_EQ_VEC, bc, 0, 3, false};
   for (int c = 0; c < 3; ++c) {
@@ -1057,6 +1097,7 @@ int mg_solve_vector(mg_hierarchy* H, int bc, const double* f[3], double* V[3], m
 
 int mg_solve_cfc(mg_hierarchy* H, const mg_cfc_sources* src, mg_cfc_fields* io, int flags, mg_cfc_report* rep) {
   if (!H || !src || !io) return fail(MG_ERR_INVALID, "null argument");
+  if (int est = enter(H)) return est;
   auto t0 = std::chrono::steady_clock::now();
   const bool psi_only = flags & MG_CFC_PSI_ONLY;
   const bool host = flags & MG_HOST_POINTERS;
@@ -1166,6 +1207,7 @@ int mg_clean_divB(mg_hierarchy* H, double* B[3], double* phi_out, int flags, mg_
   const int nd = H->d.ndim;
   for (int c = 0; c < nd; ++c)
     if (!B[c]) return fail(MG_ERR_INVALID, "null B component");
+  if (int est = enter(H)) return est;
   const bool host = flags & MG_HOST_POINTERS;
   double* Bd[3] = {B[0], B[1], nd == 3 ? B[2] : B[0]};
   int st = MG_OK;
@@ -1222,6 +1264,7 @@ int mg_clean_divB(mg_hierarchy* H, double* B[3], double* phi_out, int flags, mg_
 int mg_apply_operator(mg_hierarchy* H, int kind, int bc, const double* u[3], const double* U, const double* A2,
                       const double* c, double* out[3]) {
   if (!H || !u || !out) return fail(MG_ERR_INVALID, "null argument");
+  if (int est = enter(H)) return est;
   Level& L0 = H->L[0];
   auto v = with_bc(L0.v64, bc);
   if (kind == MG_EQ_VEC) {
@@ -1253,6 +1296,7 @@ int mg_apply_operator(mg_hierarchy* H, int kind, int bc, const double* u[3], con
 int mg_smooth(mg_hierarchy* H, int kind, int bc, int nsweeps, double* u[3], const double* f[3], const double* U,
               const double* A2, const double* c) {
   if (!H || !u || nsweeps < 0) return fail(MG_ERR_INVALID, "bad argument");
+  if (int est = enter(H)) return est;
   Level& L0 = H->L[0];
   const int nc = kind == MG_EQ_VEC ? 3 : 1;
   Eq e{kind, bc, 0, nc, kind == MG_EQ_LIN && c != nullptr};
@@ -1277,6 +1321,7 @@ int mg_smooth(mg_hierarchy* H, int kind, int bc, int nsweeps, double* u[3], cons
 
 int mg_compute_a2(mg_hierarchy* H, const double* X[3], double* A2) {
   if (!H || !X || !A2) return fail(MG_ERR_INVALID, "null argument");
+  if (int est = enter(H)) return est;
   Level& L0 = H->L[0];
   auto v = with_bc(L0.v64, MG_BC_DIRICHLET);
   for (int c = 0; c < 3; ++c) {
@@ -1293,6 +1338,7 @@ int mg_compute_a2(mg_hierarchy* H, const double* X[3], double* A2) {
 int mg_divergence(mg_hierarchy* H, const double* B[3], double* div) {
   if (!H || !B || !div) return fail(MG_ERR_INVALID, "null argument");
   if (H->d.geom != MG_CART) return fail(MG_ERR_INVALID, "Cartesian only");
+  if (int est = enter(H)) return est;
   Level& L0 = H->L[0];
   double* Bd[3] = {(double*)B[0], (double*)B[1], (double*)(H->d.ndim == 3 ? B[2] : B[0])};
   launch_div_central(L0.v64, Bd, L0.r[0], H->d_part, NPARTS, H->st);
@@ -1305,6 +1351,7 @@ int mg_divergence(mg_hierarchy* H, const double* B[3], double* div) {
 int mg_restrict(mg_hierarchy* H, const double* fine, double* coarse) {
   if (!H || !fine || !coarse) return fail(MG_ERR_INVALID, "null argument");
   if (H->nlev < 2) return fail(MG_ERR_INVALID, "hierarchy has one level");
+  if (int est = enter(H)) return est;
   Level& F = H->L[0];
   Level& C = H->L[1];
   copy_in(H, fine, F.r[0]);
@@ -1321,6 +1368,7 @@ int mg_restrict(mg_hierarchy* H, const double* fine, double* coarse) {
 int mg_prolong_add(mg_hierarchy* H, int bc, const double* coarse_e, double* fine) {
   if (!H || !coarse_e || !fine) return fail(MG_ERR_INVALID, "null argument");
   if (H->nlev < 2) return fail(MG_ERR_INVALID, "hierarchy has one level");
+  if (int est = enter(H)) return est;
   Level& F = H->L[0];
   Level& C = H->L[1];
   launch_copy_in<double, double>(C.v64, coarse_e, C.r[0], 0.0, H->st);

@@ -3,10 +3,16 @@
 #include <cuda_runtime.h>
 #include "mg_dev.cuh"
 
+struct mg_hierarchy;
+
 namespace gmg {
 
 // Record a message for mg_last_error on the calling thread; returns status.
 int set_last_error(int status, const char* msg);
+
+// Move a hierarchy's work to another stream (serving workers share cached
+// hierarchies; captured graphs are stream-independent).
+void hier_set_stream(mg_hierarchy* h, cudaStream_t st);
 
 // Count of kernel launches issued by the library (all hierarchies).
 void count_launch(int n = 1);
@@ -17,6 +23,16 @@ void launch_smooth_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
                           int colour, cudaStream_t st);
 template <typename T>
 void launch_fill_ghosts(const LevelView<T>& L, T* u, int comp, cudaStream_t st);
+// One fused red-black sweep (Cartesian 3D linear scalar equations, levels of
+// at least one tile); returns false when it does not apply.
+template <typename T>
+bool launch_sweep_fused(const LevelView<T>& L, T* u, const T* f, const T* c, cudaStream_t st);
+template <typename T>
+void init_fused_sweep_attributes();
+template <typename T>
+inline bool fused_sweep_applies(const LevelView<T>& L) {
+  return L.geom == CART && L.three && L.n0 >= 32 && L.n1 >= 8 && L.n2 >= 8;
+}
 template <typename T>
 void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st);
 template <typename T>

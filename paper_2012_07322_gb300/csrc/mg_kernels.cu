@@ -42,6 +42,84 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
   vec_update<T, G>(L, A, B, C, f, comp, i, j, k);
 }
 
+// One full red-black sweep of a Cartesian linear scalar equation in one
+// launch.  A block stages a TX x TY x TZ tile of u, f (and c) with a
+// two-cell halo in shared memory, relaxes the red cells of the tile and of
+// a one-cell ring around it (the ring is recomputed by the neighbouring
+// tiles with the same arithmetic), then the black cells of the tile, and
+// writes the tile back: u and f cross DRAM once per sweep instead of once
+// per colour.  The cell updates are the ones of k_smooth_scalar.
+constexpr int FT_X = 32, FT_Y = 8, FT_Z = 8, FH = 2;
+constexpr int FS_X = FT_X + 2 * FH, FS_Y = FT_Y + 2 * FH, FS_Z = FT_Z + 2 * FH;
+constexpr int FS_N = FS_X * FS_Y * FS_Z;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_fused_cart(LevelView<T> L, T* __restrict__ u,
+                                                          const T* __restrict__ f, const T* __restrict__ c) {
+  extern __shared__ unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* sf = su + FS_N;
+  T* sc = sf + FS_N;
+  const int i0 = blockIdx.x * FT_X - FH, j0 = blockIdx.y * FT_Y - FH, k0 = blockIdx.z * FT_Z - FH;
+  const int tid = threadIdx.x;
+  const bool inner = i0 >= 0 && j0 >= 0 && k0 >= 0 && i0 + FS_X <= L.n0 && j0 + FS_Y <= L.n1 &&
+                     k0 + FS_Z <= L.n2;
+  // stage the tile with its halo, one smem row (FS_X cells) per step
+  for (int q = tid; q < FS_N; q += blockDim.x) {
+    const int row = q / FS_X, a = q - row * FS_X;
+    const int b = row % FS_Y, cz = row / FS_Y;
+    const int i = i0 + a, j = j0 + b, k = k0 + cz;
+    const bool in = inner || (i >= 0 && i < L.n0 && j >= 0 && j < L.n1 && k >= 0 && k < L.n2);
+    const long p = in ? L.idx(i, j, k) : 0;
+    su[q] = in ? u[p] : T(0);
+    sf[q] = (in && f) ? f[p] : T(0);
+    if (c) sc[q] = in ? c[p] : T(0);
+  }
+  __syncthreads();
+  LevelView<T> S = L;  // shared-memory view: same geometry, tile strides
+  S.sx = FS_X;
+  S.sy = (long)FS_X * FS_Y;
+  // red over the tile and a one-cell ring (recomputed identically by the
+  // neighbouring tiles), then black over the tile; work items enumerate
+  // only the cells of the colour: (row, t) -> x = lo + 2 t + parity
+  for (int colour = 0; colour < 2; ++colour) {
+    const int ring = colour == 0 ? 1 : 0;
+    const int ex = FT_X + 2 * ring, ey = FT_Y + 2 * ring, ez = FT_Z + 2 * ring;
+    const int half = ex / 2;
+    const int nwork = half * ey * ez;
+    const int xlo = FH - ring, ylo = FH - ring, zlo = FH - ring;  // smem coordinates
+    for (int q = tid; q < nwork; q += blockDim.x) {
+      const int row = q / half, t = q - row * half;
+      const int b = ylo + row % ey, cz = zlo + row / ey;
+      const int j = j0 + b, k = k0 + cz;
+      // i0 + a with a = xlo + 2 t + shift has parity colour
+      const int shift = (colour - (i0 + xlo + j + k)) & 1;
+      const int a = xlo + 2 * t + shift;
+      const int i = i0 + a;
+      if (a >= xlo + ex) continue;
+      if (!inner && (i < 0 || i >= L.n0 || j < 0 || j >= L.n1 || k < 0 || k >= L.n2)) continue;
+      const long ps = a + (long)b * FS_X + (long)cz * FS_X * FS_Y;
+      T D;
+      T Lu = lap_scalar<T, CART>(S, su, i, j, k, ps, D);
+      if (c) {
+        const T cv = sc[ps];
+        Lu -= cv * su[ps];
+        D -= cv;
+      }
+      su[ps] = su[ps] - (Lu - sf[ps]) / D;
+    }
+    __syncthreads();
+  }
+  // write the tile back
+  for (int q = tid; q < FT_X * FT_Y * FT_Z; q += blockDim.x) {
+    const int row = q / FT_X, a = q - row * FT_X;
+    const int b = row % FT_Y, cz = row / FT_Y;
+    const int i = i0 + FH + a, j = j0 + FH + b, k = k0 + FH + cz;
+    if (!inner && (i >= L.n0 || j >= L.n1 || k >= L.n2)) continue;
+    u[L.idx(i, j, k)] = su[(a + FH) + (long)(b + FH) * FS_X + (long)(cz + FH) * FS_X * FS_Y];
+  }
+}
+
 template <typename T>
 __global__ void k_fill_ghosts(LevelView<T> L, T* __restrict__ u, int comp) {
   const long n = ghost_count(L);
@@ -64,14 +142,29 @@ __global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const
   if (i < L.n0 && j < L.n1 && k < L.n2) {
     const long p = L.idx(i, j, k);
     T D;
-    const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
-    const T rv = (f ? f[p] : T(0)) - Lu;
+    const T lap = lap_scalar<T, G>(L, u, i, j, k, p, D);
+    const T fv = f ? f[p] : T(0);
+    // S(u) as the paper writes the right-hand side; L(u) = lap u - S(u)
+    // (eq. psi) or lap u - c u (linear, S = f + c u)
+    T Sv, Lu;
+    if (KIND == EQ_PSI) {
+      const T ip = T(1) / (T(1) + u[p]);
+      const T ip2 = ip * ip;
+      const T ip7 = ip2 * ip2 * ip2 * ip;
+      Sv = -T(2 * PI_D) * s0[p] * ip - T(0.125) * s1[p] * ip7;
+      Lu = lap - Sv;
+    } else {
+      const T cu = s1 ? s1[p] * u[p] : T(0);
+      Lu = lap - cu;
+      Sv = fv + cu;
+    }
+    const T rv = fv - Lu;
     if (r) r[p] = rv;
     m[0] = fabs((double)rv);
     if (weighted) {
       const double w = (double)norm_weight(L, i, j);
       m[1] = fabs(w * (double)rv);
-      m[2] = fabs(w * (double)scalar_source<T, KIND>(u, s0, s1, f, p));
+      m[2] = fabs(w * (double)Sv);
     }
   }
   if (red) block_max_atomic<3>(m, red);
@@ -212,6 +305,9 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, co
 
 // --------------------------------------------------------- coarsest grid
 
+constexpr int COARSE_INV_MAX = 1024;      // scalar cells with a cached inverse diagonal
+constexpr int COARSE_VEC_INV_MAX = 256;   // vector cells with cached inverse diagonals
+
 // Newton-Gauss-Seidel as the coarsest-grid solver (Sec. 2.7.2): one block
 // sweeps until the max residual falls below 1e-12 of its initial value or
 // max_sweeps sweeps.  The bodies work on any address space: the kernels
@@ -246,6 +342,20 @@ __device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, con
   if (tid == 0) r0s = r0;
   __syncthreads();
   if (!(r0s > 0.0)) return;
+  // linear equations: the Newton diagonal is fixed, invert it once
+  __shared__ T invd[COARSE_INV_MAX];
+  const bool use_inv = KIND == EQ_LIN && n <= COARSE_INV_MAX;
+  if (use_inv) {
+    for (long q = tid; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      T D;
+      lap_scalar<T, G>(L, u, i, j, k, L.idx(i, j, k), D);
+      if (s1) D -= s1[L.idx(i, j, k)];
+      invd[q] = T(1) / D;
+    }
+    __syncthreads();
+  }
   for (int it = 0; it < max_sweeps; ++it) {
     for (int colour = 0; colour < 2; ++colour) {
       const long nh = n / 2;
@@ -253,7 +363,10 @@ __device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, con
         const int t = (int)(q % (L.n0 / 2)), j = (int)((q / (L.n0 / 2)) % L.n1),
                   k = (int)(q / ((long)(L.n0 / 2) * L.n1));
         const int i = 2 * t + ((j + k + colour) & 1);
-        scalar_update<T, G, KIND>(L, u, f, s0, s1, i, j, k);
+        if (use_inv)
+          scalar_update_lin_inv<T, G>(L, u, f, s1, invd[i + (long)L.n0 * (j + (long)L.n1 * k)], i, j, k);
+        else
+          scalar_update<T, G, KIND>(L, u, f, s0, s1, i, j, k);
       }
       __syncthreads();
     }
@@ -303,6 +416,21 @@ __device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __r
   if (tid == 0) r0s = r0;
   __syncthreads();
   if (!(r0s > 0.0)) return;
+  // the Newton diagonal of each component is fixed: invert it once
+  __shared__ T invd[3 * COARSE_VEC_INV_MAX];
+  const bool use_inv = n <= COARSE_VEC_INV_MAX;
+  if (use_inv) {
+    for (long q = tid; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      for (int c = 0; c < 3; ++c) {
+        T D;
+        vec_op<T, G>(L, A, B, C, c, i, j, L.idx(i, j, k), D);
+        invd[c * COARSE_VEC_INV_MAX + q] = T(1) / D;
+      }
+    }
+    __syncthreads();
+  }
   for (int it = 0; it < max_sweeps; ++it) {
     for (int colour = 0; colour < 2; ++colour)
       for (int c = 0; c < 3; ++c) {
@@ -311,7 +439,16 @@ __device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __r
           const int t = (int)(q % (L.n0 / 2)), j = (int)((q / (L.n0 / 2)) % L.n1),
                     k = (int)(q / ((long)(L.n0 / 2) * L.n1));
           const int i = 2 * t + ((j + k + colour) & 1);
-          vec_update<T, G>(L, A, B, C, fs[c], c, i, j, k);
+          if (use_inv) {
+            const long p = L.idx(i, j, k);
+            T D;
+            const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+            T* Vc = V[c];
+            const T fv = fs[c] ? fs[c][p] : T(0);
+            Vc[p] = Vc[p] - (Lu - fv) * invd[c * COARSE_VEC_INV_MAX + i + (long)L.n0 * (j + (long)L.n1 * k)];
+          } else {
+            vec_update<T, G>(L, A, B, C, fs[c], c, i, j, k);
+          }
         }
         __syncthreads();
         fill(c);
@@ -496,6 +633,26 @@ void launch_smooth_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
 }
 
 template <typename T>
+size_t fused_sweep_smem(bool with_c) {
+  return sizeof(T) * (size_t)FS_N * (with_c ? 3 : 2);
+}
+
+template <typename T>
+void init_fused_sweep_attributes() {
+  cudaFuncSetAttribute(k_sweep_fused_cart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fused_sweep_smem<T>(true));
+}
+
+template <typename T>
+bool launch_sweep_fused(const LevelView<T>& L, T* u, const T* f, const T* c, cudaStream_t st) {
+  if (L.geom != CART || !L.three || L.n0 < FT_X || L.n1 < FT_Y || L.n2 < FT_Z) return false;
+  count_launch();
+  dim3 g(cdiv(L.n0, FT_X), cdiv(L.n1, FT_Y), cdiv(L.n2, FT_Z));
+  k_sweep_fused_cart<T><<<g, 256, fused_sweep_smem<T>(c != nullptr), st>>>(L, u, f, c);
+  return true;
+}
+
+template <typename T>
 void launch_fill_ghosts(const LevelView<T>& L, T* u, int comp, cudaStream_t st) {
   count_launch();
   const long nk = L.n2 + 2 * L.three;
@@ -577,10 +734,10 @@ void launch_coarse_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
   const int use = sb <= COARSE_SMEM_MAX;
   const size_t dyn = use ? sb : 0;
   GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) {
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_PSI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (dyn + 16 * 1024 > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_PSI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     k_coarse_scalar<T, GG, EQ_PSI><<<1, 256, dyn, st>>>(L, u, f, s0, s1, max_sweeps, use);
   } else {
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (dyn + 16 * 1024 > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     k_coarse_scalar<T, GG, EQ_LIN><<<1, 256, dyn, st>>>(L, u, f, s0, s1, max_sweeps, use);
   });
 }
@@ -592,7 +749,7 @@ void launch_coarse_vec(const LevelView<T>& L, T* V[3], const T* const f[3], int 
   const int use = sb <= COARSE_SMEM_MAX;
   const size_t dyn = use ? sb : 0;
   GMG_GEOM_DISPATCH(L.geom, {
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(k_coarse_vec<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (dyn + 16 * 1024 > 48 * 1024) cudaFuncSetAttribute(k_coarse_vec<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     k_coarse_vec<T, GG><<<1, 256, dyn, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], max_sweeps, use);
   });
 }
@@ -631,6 +788,8 @@ void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cu
 
 // explicit instantiations
 #define GMG_INST(T)                                                                                            \
+  template bool launch_sweep_fused<T>(const LevelView<T>&, T*, const T*, const T*, cudaStream_t);              \
+  template void init_fused_sweep_attributes<T>();                                                              \
   template void launch_smooth_scalar<T>(const LevelView<T>&, int, T*, const T*, const T*, const T*, int,       \
                                         cudaStream_t);                                                          \
   template void launch_fill_ghosts<T>(const LevelView<T>&, T*, int, cudaStream_t);                             \

@@ -51,15 +51,49 @@ __device__ __forceinline__ T scalar_source(const T* __restrict__ u, const T* __r
 }
 
 // One Newton-Gauss-Seidel update (eq. ngs_iteration) of a scalar cell.
+// For eq. psi the step N / dN is evaluated with one division: numerator and
+// denominator are both multiplied by p^8, p = 1 + u (p ~ 1, no overflow).
 template <typename T, int G, int KIND>
 __device__ __forceinline__ void scalar_update(const LevelView<T>& L, T* __restrict__ u,
                                               const T* __restrict__ f, const T* __restrict__ s0,
                                               const T* __restrict__ s1, int i, int j, int k) {
   const long p = L.idx(i, j, k);
   T D;
-  T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
+  const T lap = lap_scalar<T, G>(L, u, i, j, k, p, D);
   const T fv = f ? f[p] : T(0);
-  u[p] = u[p] - (Lu - fv) / D;
+  if (KIND == EQ_PSI) {
+    const T q = T(1) + u[p];
+    const T q2 = q * q;
+    const T q4 = q2 * q2;
+    const T q6 = q4 * q2;
+    const T q8 = q4 * q4;
+    const T a = T(2 * PI_D) * s0[p];
+    const T b = s1[p];
+    const T num = (lap - fv) * q8 + a * q6 * q + T(0.125) * b * q;
+    const T den = D * q8 - a * q6 - T(0.875) * b;
+    u[p] = u[p] - num / den;
+  } else {
+    T Lu = lap;
+    if (s1) {
+      const T c = s1[p];
+      Lu -= c * u[p];
+      D -= c;
+    }
+    u[p] = u[p] - (Lu - fv) / D;
+  }
+}
+
+// Linear update with a precomputed inverse diagonal (coarsest solver).
+template <typename T, int G>
+__device__ __forceinline__ void scalar_update_lin_inv(const LevelView<T>& L, T* __restrict__ u,
+                                                      const T* __restrict__ f, const T* __restrict__ c,
+                                                      T invD, int i, int j, int k) {
+  const long p = L.idx(i, j, k);
+  T D;
+  T Lu = lap_scalar<T, G>(L, u, i, j, k, p, D);
+  if (c) Lu -= c[p] * u[p];
+  const T fv = f ? f[p] : T(0);
+  u[p] = u[p] - (Lu - fv) * invD;
 }
 
 // One Newton-Gauss-Seidel update of vector component c (ghosts current).

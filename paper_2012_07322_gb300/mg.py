@@ -35,10 +35,12 @@ STATUS = {0: "ok", 1: "invalid", 2: "oom", 3: "noconv", 4: "stalled", 5: "nan", 
 EXPORTS = ["mg_strerror", "mg_last_error", "mg_hierarchy_bytes", "mg_create_hierarchy", "mg_destroy_hierarchy",
            "mg_num_levels", "mg_solve_cfc", "mg_clean_divB", "mg_solve_scalar", "mg_solve_vector",
            "mg_apply_operator", "mg_smooth", "mg_compute_a2", "mg_divergence", "mg_restrict", "mg_prolong_add",
-           "mg_kernel_launches", "mg_profile_enable", "mg_profile_read", "mg_divb_norms_noalloc"]
+           "mg_kernel_launches", "mg_profile_enable", "mg_profile_read", "mg_divb_norms_noalloc",
+           "mg_server_create", "mg_server_destroy", "mg_submit", "mg_poll"]
+MG_REQ_CFC, MG_REQ_DIVB = 0, 1
 MG_NOALLOC_MAX_CELLS = 2097152
 PROF_CLASSES = ["smooth64_scalar", "smooth64_vec", "smooth32_scalar", "smooth32_vec", "resid64_scalar",
-                "resid64_vec"]
+                "resid64_vec", "sweep64_fused", "sweep32_fused"]
 
 
 class mg_grid_desc(C.Structure):
@@ -72,6 +74,17 @@ class mg_cfc_report(C.Structure):
 class mg_divb_report(C.Structure):
     _fields_ = [("solve", mg_solve_report), ("max_div_before", C.c_double), ("l2_div_before", C.c_double),
                 ("max_div_after", C.c_double), ("l2_div_after", C.c_double)]
+
+
+class mg_request(C.Structure):
+    _fields_ = [("desc", mg_grid_desc), ("kind", C.c_int), ("flags", C.c_int), ("stream_id", C.c_uint64),
+                ("src", mg_cfc_sources), ("io", mg_cfc_fields), ("B", C.c_void_p * 3), ("phi", C.c_void_p),
+                ("wait_stream", C.c_void_p)]
+
+
+class mg_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("cfc", mg_cfc_report), ("divb", mg_divb_report), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("warm_started", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -110,6 +123,10 @@ def lib():
         L.mg_kernel_launches.argtypes = []
         L.mg_profile_enable.argtypes = [P, I]
         L.mg_profile_read.argtypes = [P, I, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.mg_server_create.argtypes = [C.c_size_t, I, I, C.POINTER(P)]
+        L.mg_server_destroy.argtypes = [P]
+        L.mg_submit.argtypes = [P, C.POINTER(mg_request), C.POINTER(C.c_uint64)]
+        L.mg_poll.argtypes = [P, C.c_uint64, C.POINTER(I), C.POINTER(mg_result)]
         L.mg_divb_norms_noalloc.argtypes = [I, C.POINTER(C.c_int * 3), C.POINTER(C.c_double * 3),
                                             C.POINTER(C.c_double * 3), C.POINTER(P), P,
                                             C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -356,3 +373,97 @@ def mg_divb_norms_noalloc(B, lo, hi, stream=None, allow=(MG_OK,)):
                                      C.c_void_p(stream.cuda_stream), C.byref(mx), C.byref(l2))
     _check(st, "mg_divb_norms_noalloc", allow)
     return st, mx.value, l2.value
+
+
+class Server:
+    """A request server (mg_server_create): submit() queues a CFC or div-B
+    request and returns a ticket; poll() is non-blocking.  The tensors of a
+    request are kept referenced until it has been collected."""
+
+    def __init__(self, hbm_budget, max_slots=4, max_queue=256):
+        h = C.c_void_p()
+        _check(lib().mg_server_create(int(hbm_budget), max_slots, max_queue, C.byref(h)), "mg_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mg_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit_cfc(self, desc, U, S, Si, psi, alpha, beta, X, psi_only=False, stream_id=0, allow=(MG_OK,)):
+        r = mg_request()
+        r.desc = desc
+        r.kind = MG_REQ_CFC
+        r.flags = MG_CFC_PSI_ONLY if psi_only else 0
+        r.stream_id = stream_id
+        r.src.U = U.data_ptr()
+        r.io.psi = psi.data_ptr()
+        if not psi_only:
+            r.src.S = S.data_ptr()
+            r.io.alpha = alpha.data_ptr()
+            for k in range(3):
+                r.src.Si[k] = Si[k].data_ptr()
+                r.io.beta[k] = beta[k].data_ptr()
+                r.io.X[k] = X[k].data_ptr()
+        return self._submit(r, (U, S, Si, psi, alpha, beta, X), allow)
+
+    def submit_divb(self, desc, B, phi=None, allow=(MG_OK,)):
+        r = mg_request()
+        r.desc = desc
+        r.kind = MG_REQ_DIVB
+        for k, t in enumerate(B):
+            r.B[k] = t.data_ptr()
+        r.phi = phi.data_ptr() if phi is not None else None
+        return self._submit(r, (B, phi), allow)
+
+    def _submit(self, r, keep, allow):
+        import torch
+        r.wait_stream = torch.cuda.current_stream().cuda_stream
+        t = C.c_uint64()
+        st = lib().mg_submit(self.handle, C.byref(r), C.byref(t))
+        _check(st, "mg_submit", allow)
+        if st != MG_OK:
+            return None
+        self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, ticket):
+        """(done, result dict or None)."""
+        done = C.c_int()
+        res = mg_result()
+        st = lib().mg_poll(self.handle, ticket, C.byref(done), C.byref(res))
+        if st == MG_ERR_NOTFOUND:
+            raise MgError(st, "mg_poll")
+        if not done.value:
+            return False, None
+        self._keep.pop(ticket, None)
+        names = ["X", "psi", "alphapsi", "beta"]
+        out = {"status": STATUS.get(res.status, res.status), "latency_ms": res.latency_ms,
+               "queue_ms": res.queue_ms, "warm_started": bool(res.warm_started),
+               "cfc": {names[k]: res.cfc.eq[k].as_dict() for k in range(4)},
+               "divb": {"solve": res.divb.solve.as_dict(), "max_div_before": res.divb.max_div_before,
+                        "max_div_after": res.divb.max_div_after}}
+        return True, out
+
+    def wait(self, ticket, timeout_s=600.0):
+        import time
+        t0 = time.time()
+        while True:
+            done, res = self.poll(ticket)
+            if done:
+                return res
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("ticket %d not done after %.0f s" % (ticket, timeout_s))
+            time.sleep(0.0005)
+
+
+def mg_server_create(hbm_budget, max_slots=4, max_queue=256):
+    return Server(hbm_budget, max_slots, max_queue)

@@ -1,0 +1,45 @@
+"""Fixed workloads for kernel profiling (ncu), run from the repository root:
+
+    python -m paper_2012_07322_gb300.profile_cases divb256   # mixed 256^3 div-B cleaning, twice
+    python -m paper_2012_07322_gb300.profile_cases xeq       # 10 mixed cycles of eq. X, 128x64x64
+
+Each case runs through the C ABI and exits 0 on success, so the same command
+can be profiled after it has run once without a profiler.
+"""
+import sys
+
+import numpy as np
+
+
+def divb256(precision="mixed"):
+    import torch
+    from . import inputs, mg
+    n = 256
+    B = [torch.from_numpy(b).cuda() for b in inputs.divb_field(n=n)]
+    h = mg.Hierarchy(mg.grid_desc("cart", [n] * 3, [-1.0] * 3, [1.0] * 3, precision=precision, tol=1e-10,
+                                  max_cycles=200, stall_window=0))
+    rep = None
+    for _ in range(2):
+        rep = mg.mg_clean_divB(h, [b.clone() for b in B])
+    h.close()
+    print("divb256", precision, rep["solve"]["cycles"], rep["max_div_before"], rep["max_div_after"])
+
+
+def xeq(precision="mixed"):
+    import torch
+    from . import inputs, mg
+    n = (128, 64, 64)
+    U, S, Si = inputs.rotating_polytrope_sph3d(n, 100.0)
+    h = mg.Hierarchy(mg.grid_desc("sph", list(n), hi=[100.0, np.pi, 2 * np.pi], precision=precision, tol=1e-10,
+                                  max_cycles=10, stall_window=0, accel_depth=16))
+    f = [torch.from_numpy(8 * np.pi * x).cuda() for x in Si]
+    V = [torch.zeros(U.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    rep = mg.mg_solve_vector(h, "dirichlet", f, V, allow=(mg.MG_OK, mg.MG_ERR_NOCONV))
+    h.close()
+    print("xeq", precision, rep["status"], rep["cycles"], rep["rel"])
+
+
+if __name__ == "__main__":
+    case = sys.argv[1] if len(sys.argv) > 1 else "divb256"
+    prec = sys.argv[2] if len(sys.argv) > 2 else "mixed"
+    {"divb256": divb256, "xeq": xeq}[case](prec)

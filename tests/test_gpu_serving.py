@@ -1,0 +1,161 @@
+"""Request serving (mg_submit / mg_poll): continuous admission into worker
+slots whose kernels overlap on the device, hierarchy reuse, resident warm
+starts per stream, admission by HBM budget.
+
+Each result must be the same alone and in the mix: the solver's arithmetic
+does not depend on what runs beside it (fixed reduction orders, per-request
+hierarchies), so results are compared bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2012_07322_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+PI = np.pi
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_07322_gb300 import mg as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.array(a, dtype=np.float64, copy=True)).cuda()
+
+
+def cfc_case(kind, seed):
+    """(desc args, U, S, Si) of a jittered rotating star."""
+    rng = np.random.default_rng(seed)
+    rho_c, R = rng.uniform(8e-4, 1.6e-3), rng.uniform(8.0, 12.0)
+    if kind == "sph2d":
+        U, S, Si = inputs.rotating_polytrope_sph2d(64, 32, 100.0, rho_c, R)
+        return ("sph", [64, 32], [0.0, 0.0], [100.0, PI]), U, S, Si
+    if kind == "sph3d":
+        U, S, Si = inputs.rotating_polytrope_sph3d((32, 16, 16), 100.0, rho_c, R)
+        return ("sph", [32, 16, 16], [0.0, 0.0, 0.0], [100.0, PI, 2 * PI]), U, S, Si
+    U, S, Si = inputs.rotating_polytrope_cyl([32, 64], 100.0, rho_c, R)
+    return ("cyl", [32, 64], [0.0, -100.0], [100.0, 100.0]), U, S, Si
+
+
+def fields(shape):
+    psi = torch.ones(shape, dtype=torch.float64, device="cuda")
+    return psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)], [torch.zeros_like(psi) for _ in range(3)]
+
+
+def desc_of(mg, args, accel=8):
+    geom, n, lo, hi = args
+    return mg.grid_desc(geom, n, lo, hi, tol=1e-10, max_cycles=600, accel_depth=accel, stall_window=0)
+
+
+def test_results_identical_alone_and_in_the_mix(mg):
+    cases = [("sph2d", 1), ("sph3d", 2), ("cyl2d", 3), ("sph2d", 4), ("sph3d", 5), ("cyl2d", 6)]
+    reqs = []
+    for kind, seed in cases:
+        args, U, S, Si = cfc_case(kind, seed)
+        reqs.append(("cfc", args, [dev(U), dev(S), [dev(x) for x in Si]]))
+    for n, seed in [(32, 7), (16, 8)]:
+        B = inputs.divb_field(n=n, n_modes=8, k_max=4, seed_modes=seed, seed_noise=seed + 1)
+        reqs.append(("divb", ("cart", [n] * 3, [-1.0] * 3, [1.0] * 3), [dev(b) for b in B]))
+    # alone: one hierarchy per request, direct calls
+    alone = []
+    for kind, args, data in reqs:
+        h = mg.Hierarchy(desc_of(mg, args))
+        if kind == "cfc":
+            psi, alpha, beta, X = fields(data[0].shape)
+            mg.mg_solve_cfc(h, data[0], data[1], data[2], psi, alpha, beta, X)
+            alone.append([psi, alpha] + beta + X)
+        else:
+            B = [b.clone() for b in data]
+            mg.mg_clean_divB(h, B)
+            alone.append(B)
+        h.close()
+    # in the mix: everything submitted at once, twice over, to 4 slots
+    srv = mg.Server(hbm_budget=8 << 30, max_slots=4, max_queue=64)
+    tickets, outs = [], []
+    for rep in range(2):
+        for kind, args, data in reqs:
+            if kind == "cfc":
+                psi, alpha, beta, X = fields(data[0].shape)
+                t = srv.submit_cfc(desc_of(mg, args), data[0], data[1], data[2], psi, alpha, beta, X)
+                outs.append([psi, alpha] + beta + X)
+            else:
+                B = [b.clone() for b in data]
+                t = srv.submit_divb(desc_of(mg, args), B)
+                outs.append(B)
+            tickets.append(t)
+    results = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert all(r["status"] == "ok" for r in results)
+    for q, out in enumerate(outs):
+        ref = alone[q % len(reqs)]
+        for a, b in zip(out, ref):
+            assert torch.equal(a, b), q
+
+
+def test_warm_start_of_a_stream(mg):
+    """The second request of a stream starts from the first one's resident
+    solution: with unchanged sources it is converged at cycle 0."""
+    args, U, S, Si = cfc_case("sph2d", 11)
+    d = desc_of(mg, args)
+    srv = mg.Server(hbm_budget=2 << 30, max_slots=2, max_queue=8)
+    Ud, Sd, Sid = dev(U), dev(S), [dev(x) for x in Si]
+    f1 = fields(U.shape)
+    r1 = srv.wait(srv.submit_cfc(d, Ud, Sd, Sid, *f1, stream_id=42))
+    f2 = fields(U.shape)
+    r2 = srv.wait(srv.submit_cfc(d, Ud, Sd, Sid, *f2, stream_id=42))
+    srv.close()
+    assert r1["status"] == "ok" and r2["status"] == "ok"
+    assert not r1["warm_started"] and r2["warm_started"]
+    assert r1["cfc"]["psi"]["cycles"] > 0
+    assert all(r2["cfc"][k]["cycles"] == 0 for k in ("X", "psi", "alphapsi", "beta"))
+    assert torch.equal(f1[0], f2[0])
+
+
+def test_admission_by_budget_and_queue(mg):
+    args, U, S, Si = cfc_case("sph3d", 12)
+    d = desc_of(mg, args)
+    need = mg.mg_hierarchy_bytes(d)
+    # a request larger than the whole budget is refused at submission
+    small = mg.Server(hbm_budget=need // 2, max_slots=1, max_queue=4)
+    Ud, Sd, Sid = dev(U), dev(S), [dev(x) for x in Si]
+    st = small.submit_cfc(d, Ud, Sd, Sid, *fields(U.shape), allow=(mg.MG_OK, mg.MG_ERR_OOM))
+    assert st is None
+    small.close()
+    # a full queue refuses with MG_ERR_BUSY; everything admitted completes
+    srv = mg.Server(hbm_budget=need + (64 << 20), max_slots=1, max_queue=2)
+    tickets, busy = [], 0
+    for _ in range(8):
+        t = srv.submit_cfc(d, Ud, Sd, Sid, *fields(U.shape), allow=(mg.MG_OK, mg.MG_ERR_BUSY))
+        if t is None:
+            busy += 1
+        else:
+            tickets.append(t)
+    results = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert busy > 0
+    assert all(r["status"] == "ok" for r in results)
+
+
+def test_eviction_keeps_results_correct(mg):
+    """A budget for one hierarchy at a time: alternating grids evict and
+    recreate hierarchies; each result still equals the direct solve."""
+    a_args, Ua, Sa, Sia = cfc_case("sph2d", 21)
+    b_args, Ub, Sb, Sib = cfc_case("cyl2d", 22)
+    da, db = desc_of(mg, a_args), desc_of(mg, b_args)
+    budget = max(mg.mg_hierarchy_bytes(da), mg.mg_hierarchy_bytes(db)) + (1 << 20)
+    srv = mg.Server(hbm_budget=budget, max_slots=1, max_queue=16)
+    outs, tickets = [], []
+    for q in range(4):
+        d, U, S, Si = (da, Ua, Sa, Sia) if q % 2 == 0 else (db, Ub, Sb, Sib)
+        f = fields(U.shape)
+        tickets.append(srv.submit_cfc(d, dev(U), dev(S), [dev(x) for x in Si], *f))
+        outs.append(f)
+    res = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert all(r["status"] == "ok" for r in res)
+    assert torch.equal(outs[0][0], outs[2][0]) and torch.equal(outs[1][0], outs[3][0])
