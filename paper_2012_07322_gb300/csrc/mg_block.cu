@@ -1,0 +1,225 @@
+// The FP32 correction V-cycle (Sec. 2.7.2 / 2.7.3 in correction form, the
+// inner cycle of the mixed-precision defect correction) over the coarse
+// levels of a hierarchy in ONE thread block.  Below a few thousand cells a
+// level's kernels are too small to fill the GPU and each launch costs more
+// than its work; inside one block the same phases are separated by block
+// barriers instead of kernel boundaries, and every level lives in shared
+// memory (the same ghosted layout as in HBM).  Every phase applies the
+// per-cell functions the grid-wide kernels apply, in the same order, so the
+// result is identical to the launched cycle.
+#include "mg_internal.h"
+#include "mg_kernels.cuh"
+
+namespace gmg {
+
+constexpr int BC_THREADS = 512;
+
+// One level with its arrays resolved to shared memory.  The view is copied
+// out of the kernel parameters: indexed by a run-time level, the parameter
+// would be read through memory on every access of the stencil loops.
+struct BcLevel {
+  LevelView<float> v;
+  float* e[3];
+  float* f[3];
+  float* r[3];
+  const float* k;
+};
+
+__device__ __forceinline__ BcLevel bc_level(const BlockCycle32& P, float* sm, int l) {
+  const BlockLevel32& B = P.lv[l];
+  BcLevel o;
+  o.v = B.v;
+  for (int c = 0; c < 3; ++c) {
+    o.e[c] = sm + B.e[c];
+    o.f[c] = sm + B.f32[c];
+    o.r[c] = sm + B.r32[c];
+  }
+  o.k = B.k32;
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void bc_fill(const LevelView<T>& L, T* u, int comp) {
+  const long ng = ghost_count(L);
+  for (long g = threadIdx.x; g < ng; g += blockDim.x) fill_one_ghost(L, u, comp, g);
+  __syncthreads();
+}
+
+// smooth32: nsweeps red-black sweeps (vector: component by component, the
+// ghosts of a component refreshed after its pass).
+template <int G, bool VEC>
+__device__ void bc_smooth(const BcLevel& B, int nsweeps) {
+  const LevelView<float> L = B.v;
+  const long nh = (long)L.n0 * L.n1 * L.n2 / 2;
+  for (int s = 0; s < nsweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      if (!VEC) {
+        for (long q = threadIdx.x; q < nh; q += blockDim.x) {
+          int i, j, k;
+          L.colour_cell(q, colour, i, j, k);
+          scalar_update<float, G, EQ_LIN>(L, B.e[0], B.f[0], nullptr, B.k, i, j, k);
+        }
+        __syncthreads();
+      } else {
+        for (int c = 0; c < 3; ++c) {
+          for (long q = threadIdx.x; q < nh; q += blockDim.x) {
+            int i, j, k;
+            L.colour_cell(q, colour, i, j, k);
+            vec_update<float, G>(L, B.e[0], B.e[1], B.e[2], B.f[c], c, i, j, k);
+          }
+          __syncthreads();
+          bc_fill(L, B.e[c], c);
+        }
+      }
+    }
+}
+
+template <int G, bool VEC>
+__device__ void bc_residual(const BcLevel& B) {
+  const LevelView<float> L = B.v;
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    if (!VEC) {
+      float Sv;
+      B.r[0][p] = scalar_residual_cell<float, G, EQ_LIN>(L, B.e[0], B.f[0], nullptr, B.k, i, j, k, p, Sv);
+    } else {
+      for (int c = 0; c < 3; ++c) B.r[c][p] = vec_residual_cell<float, G>(L, B.e[0], B.e[1], B.e[2], B.f[c], c, i, j, p);
+    }
+  }
+  __syncthreads();
+}
+
+// coarse32: the coarsest correction equation in FP64 (right-hand side and
+// c converted up, zero start), the solution rounded back into e.
+template <int G, bool VEC>
+__device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) {
+  const LevelView<double>& L = P.c64;
+  const int nc = VEC ? 3 : 1;
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  const long ng = L.sy * (L.n2 + 2 * L.three);
+  double* cu[3] = {smd + P.cu[0], smd + P.cu[1], smd + P.cu[2]};
+  double* cf[3] = {smd + P.cf[0], smd + P.cf[1], smd + P.cf[2]};
+  double* ck = P.ck >= 0 ? smd + P.ck : nullptr;
+  for (int c = 0; c < nc; ++c) {
+    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      cf[c][p] = (double)B.f[c][p];
+      if (!VEC && ck) ck[p] = (double)B.k[p];
+    }
+    for (long q = threadIdx.x; q < ng; q += blockDim.x) cu[c][q] = 0.0;
+  }
+  __syncthreads();
+  if (!VEC)
+    coarse_scalar_body<double, G, EQ_LIN>(L, cu[0], cf[0], nullptr, ck, P.coarse_sweeps);
+  else
+    coarse_vec_body<double, G>(L, cu[0], cu[1], cu[2], cf[0], cf[1], cf[2], P.coarse_sweeps);
+  __syncthreads();
+  for (int c = 0; c < nc; ++c)
+    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      B.e[c][p] = (float)cu[c][p];
+    }
+  __syncthreads();
+  if (VEC)
+    for (int c = 0; c < 3; ++c) bc_fill(B.v, B.e[c], c);
+}
+
+template <int G, bool VEC>
+__global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_constant__ BlockCycle32 P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  double* smd = reinterpret_cast<double*>(smem_raw + P.fp64_at);
+  const int nc = VEC ? 3 : 1;
+  {
+    // level l0: right-hand side in, zero correction
+    const BcLevel B = bc_level(P, sm, 0);
+    for (int c = 0; c < nc; ++c)
+      for (long q = threadIdx.x; q < P.ng0; q += blockDim.x) {
+        B.f[c][q] = P.f_in[c][q];
+        B.e[c][q] = 0.0f;
+      }
+    __syncthreads();
+  }
+  // down: pre-smooth, residual, restriction into the next level's
+  // right-hand side, zero correction there
+  for (int l = 0; l + 1 < P.nl; ++l) {
+    const BcLevel F = bc_level(P, sm, l), C = bc_level(P, sm, l + 1);
+    bc_smooth<G, VEC>(F, P.nu1);
+    bc_residual<G, VEC>(F);
+    const LevelView<float> Cv = C.v;
+    const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2;
+    const long ngC = Cv.sy * (Cv.n2 + 2 * Cv.three);
+    for (int c = 0; c < nc; ++c) {
+      const float* const as[4] = {F.r[c], nullptr, nullptr, nullptr};
+      float* const bs[4] = {C.f[c], nullptr, nullptr, nullptr};
+      float* const cs[3] = {nullptr, nullptr, nullptr};
+      for (long q = threadIdx.x; q < nC; q += blockDim.x) {
+        int I, J, K;
+        Cv.cell(q, I, J, K);
+        restrict_cell(F.v, Cv, 1, as, bs, cs, I, J, K);
+      }
+      for (long q = threadIdx.x; q < ngC; q += blockDim.x) C.e[c][q] = 0.0f;
+    }
+    __syncthreads();
+  }
+  bc_coarse<G, VEC>(P, bc_level(P, sm, P.nl - 1), smd);
+  // up: Kwak prolongation of the correction, post-smooth
+  for (int l = P.nl - 2; l >= 0; --l) {
+    const BcLevel F = bc_level(P, sm, l), C = bc_level(P, sm, l + 1);
+    const LevelView<float> Fv = F.v;
+    const long nF = (long)Fv.n0 * Fv.n1 * Fv.n2;
+    for (int c = 0; c < nc; ++c)
+      for (long q = threadIdx.x; q < nF; q += blockDim.x) {
+        int i, j, k;
+        Fv.cell(q, i, j, k);
+        prolong_cell(Fv, C.v, F.e[c], C.e[c], (const float*)nullptr, VEC ? c : -1, i, j, k);
+      }
+    __syncthreads();
+    if (VEC)
+      for (int c = 0; c < 3; ++c) bc_fill(Fv, F.e[c], c);
+    bc_smooth<G, VEC>(F, P.nu2);
+  }
+  // level l0 correction out (ghosts included)
+  const BcLevel B = bc_level(P, sm, 0);
+  for (int c = 0; c < nc; ++c)
+    for (long q = threadIdx.x; q < P.ng0; q += blockDim.x) P.e_out[c][q] = B.e[c][q];
+}
+
+template <int G>
+static void launch_g(const BlockCycle32& P, cudaStream_t st) {
+  if (P.vec)
+    k_block_vcycle32<G, true><<<1, BC_THREADS, P.smem, st>>>(P);
+  else
+    k_block_vcycle32<G, false><<<1, BC_THREADS, P.smem, st>>>(P);
+}
+
+void launch_block_vcycle32(const BlockCycle32& P, int geom, cudaStream_t st) {
+  count_launch();
+  if (geom == CART)
+    launch_g<CART>(P, st);
+  else if (geom == CYL)
+    launch_g<CYL>(P, st);
+  else
+    launch_g<SPH>(P, st);
+}
+
+template <int G>
+static void set_attrs() {
+  cudaFuncSetAttribute(k_block_vcycle32<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BC_SMEM_MAX);
+  cudaFuncSetAttribute(k_block_vcycle32<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BC_SMEM_MAX);
+}
+
+void init_block_cycle_attributes() {
+  set_attrs<CART>();
+  set_attrs<CYL>();
+  set_attrs<SPH>();
+}
+
+}  // namespace gmg

@@ -46,6 +46,15 @@ struct LevelView {
     j = (int)(jk & (n1 - 1));
     k = (int)(jk >> ln1);
   }
+  // Cell (i, j, k) of colour (i + j + k) % 2 from its rank r among the
+  // cells of that colour (n0 even): i = 2 t + parity, t the rank in the row.
+  __device__ __forceinline__ void colour_cell(long r, int colour, int& i, int& j, int& k) const {
+    const int t = (int)(r & ((n0 >> 1) - 1));
+    const long jk = r >> (ln0 - 1);
+    j = (int)(jk & (n1 - 1));
+    k = (int)(jk >> ln1);
+    i = 2 * t + ((j + k + colour) & 1);
+  }
   __device__ __forceinline__ T xc0(int i) const { return lo0 + (T(i) + T(0.5)) * h0; }
   __device__ __forceinline__ T xc1(int j) const { return lo1 + (T(j) + T(0.5)) * h1; }
   __device__ __forceinline__ T xc2(int k) const { return lo2 + (T(k) + T(0.5)) * h2; }
@@ -75,6 +84,20 @@ __device__ __forceinline__ T rho_at(const LevelView<T>& L, int i, int j, int k) 
   return sqrt(s);
 }
 
+// rho(source cell) / rho(ghost) for the Cartesian / cylindrical Robin
+// rule (z = 0 when the distance has no third term).  Out of line: inlined,
+// the compiler may evaluate its square roots and division speculatively on
+// every stencil that only might touch the boundary, which costs FP64 kernels
+// far more than the rare call.
+template <typename T>
+__device__ __noinline__ T robin_rho_ratio(T xs, T ys, T zs, T xg, T yg, T zg) {
+  T s = xs * xs + ys * ys;
+  s += zs * zs;
+  T g = xg * xg + yg * yg;
+  g += zg * zg;
+  return sqrt(s) / sqrt(g);
+}
+
 // Factor g / u_src of an outer-boundary ghost (eq. bc / eq. robin):
 // Dirichlet-0 -> -1, Neumann -> +1, Robin -> u ~ 1/distance.
 template <typename T>
@@ -83,7 +106,9 @@ __device__ __forceinline__ T outer_factor(const LevelView<T>& L, int gi, int gj,
   if (L.bc == BC_DIRICHLET) return T(-1);
   if (L.bc == BC_NEUMANN) return T(1);
   if (L.geom == SPH) return L.robin0;
-  return rho_at(L, si, sj, sk) / rho_at(L, gi, gj, gk);
+  const bool z3 = L.geom == CART && L.three;
+  return robin_rho_ratio(L.xc0(si), L.xc1(sj), z3 ? L.xc2(sk) : T(0), L.xc0(gi), L.xc1(gj),
+                         z3 ? L.xc2(gk) : T(0));
 }
 
 // Source of a face ghost: the ghost at (i,j,k) lies outside exactly one
@@ -160,6 +185,47 @@ __device__ __forceinline__ T ghost_value(const LevelView<T>& L, const T* __restr
 
 // ------------------------------------------------------ scalar operator
 
+// The six neighbour values a cell's scalar Laplacian uses.
+template <typename T>
+struct Nb6 {
+  T e, w, n, s, up, dn;
+};
+
+// Neighbours of a cell on the edge of the level: outer ghosts from the
+// boundary rule on the fly, the origin / axis neighbours replaced by the
+// cell itself (their face areas vanish, so they drop out of the flux),
+// periodic phi neighbours wrapped.  Out of line: interior cells, the vast
+// majority, never evaluate the boundary rules.
+template <typename T, int G>
+__device__ __noinline__ Nb6<T> lap_edge_neighbours(const LevelView<T>& L, const T* __restrict__ u, int i, int j,
+                                                   int k, long p) {
+  const T uc = u[p];
+  Nb6<T> nb;
+  nb.e = (i < L.n0 - 1) ? u[p + 1] : outer_factor(L, L.n0, j, k, L.n0 - 1, j, k) * uc;
+  if (G == CART)
+    nb.w = (i > 0) ? u[p - 1] : outer_factor(L, -1, j, k, 0, j, k) * uc;
+  else
+    nb.w = (i > 0) ? u[p - 1] : uc;  // R_{-1/2} = 0 / r_{-1/2} = 0
+  if (G == SPH) {
+    nb.n = (j < L.n1 - 1) ? u[p + L.sx] : uc;  // sin(theta) = 0 on the poles
+    nb.s = (j > 0) ? u[p - L.sx] : uc;
+  } else {
+    nb.n = (j < L.n1 - 1) ? u[p + L.sx] : outer_factor(L, i, L.n1, k, i, L.n1 - 1, k) * uc;
+    nb.s = (j > 0) ? u[p - L.sx] : outer_factor(L, i, -1, k, i, 0, k) * uc;
+  }
+  nb.up = nb.dn = uc;
+  if (L.three) {
+    if (G == CART) {
+      nb.up = (k < L.n2 - 1) ? u[p + L.sy] : outer_factor(L, i, j, L.n2, i, j, L.n2 - 1) * uc;
+      nb.dn = (k > 0) ? u[p - L.sy] : outer_factor(L, i, j, -1, i, j, 0) * uc;
+    } else {
+      nb.up = (k < L.n2 - 1) ? u[p + L.sy] : u[p - (long)(L.n2 - 1) * L.sy];
+      nb.dn = (k > 0) ? u[p - L.sy] : u[p + (long)(L.n2 - 1) * L.sy];
+    }
+  }
+  return nb;
+}
+
 // Flux-form Laplacian (Sec. 2.7.1) at an interior cell, with outer ghosts
 // taken from the boundary rule on the fly and the origin / axis fluxes
 // (whose face areas vanish) dropped; periodic phi neighbours wrap.  D gets
@@ -168,40 +234,31 @@ template <typename T, int G>
 __device__ __forceinline__ T lap_scalar(const LevelView<T>& L, const T* __restrict__ u, int i, int j, int k,
                                         long p, T& D) {
   const T uc = u[p];
-  T uE, uW, uN, uS;
-  uE = (i < L.n0 - 1) ? u[p + 1] : outer_factor(L, L.n0, j, k, L.n0 - 1, j, k) * uc;
-  if (G == CART)
-    uW = (i > 0) ? u[p - 1] : outer_factor(L, -1, j, k, 0, j, k) * uc;
-  else
-    uW = (i > 0) ? u[p - 1] : uc;  // R_{-1/2} = 0 / r_{-1/2} = 0
-  if (G == SPH) {
-    uN = (j < L.n1 - 1) ? u[p + L.sx] : uc;  // sin(theta) = 0 on the poles
-    uS = (j > 0) ? u[p - L.sx] : uc;
+  Nb6<T> nb;
+  const bool inner = i > 0 && i < L.n0 - 1 && j > 0 && j < L.n1 - 1 && (!L.three || (k > 0 && k < L.n2 - 1));
+  if (inner) {
+    nb.e = u[p + 1];
+    nb.w = u[p - 1];
+    nb.n = u[p + L.sx];
+    nb.s = u[p - L.sx];
+    nb.up = L.three ? u[p + L.sy] : uc;
+    nb.dn = L.three ? u[p - L.sy] : uc;
   } else {
-    uN = (j < L.n1 - 1) ? u[p + L.sx] : outer_factor(L, i, L.n1, k, i, L.n1 - 1, k) * uc;
-    uS = (j > 0) ? u[p - L.sx] : outer_factor(L, i, -1, k, i, 0, k) * uc;
+    nb = lap_edge_neighbours<T, G>(L, u, i, j, k, p);
   }
   const T cE = L.TI(TI_CE, i), cW = L.TI(TI_CW, i);
-  T Lu = cE * (uE - uc) - cW * (uc - uW);
+  T Lu = cE * (nb.e - uc) - cW * (uc - nb.w);
   D = -(cE + cW);
   if (G == SPH) {
     const T ir2 = L.TI(TI_IX2, i);
     const T tN = L.TJ(TJ_TN, j), tS = L.TJ(TJ_TS, j);
-    Lu += ir2 * (tN * (uN - uc) - tS * (uc - uS));
+    Lu += ir2 * (tN * (nb.n - uc) - tS * (uc - nb.s));
     D -= ir2 * (tN + tS);
   } else {
-    Lu += L.ih1s * (uN - T(2) * uc + uS);
+    Lu += L.ih1s * (nb.n - T(2) * uc + nb.s);
     D -= T(2) * L.ih1s;
   }
   if (L.three) {
-    T uU, uD;
-    if (G == CART) {
-      uU = (k < L.n2 - 1) ? u[p + L.sy] : outer_factor(L, i, j, L.n2, i, j, L.n2 - 1) * uc;
-      uD = (k > 0) ? u[p - L.sy] : outer_factor(L, i, j, -1, i, j, 0) * uc;
-    } else {
-      uU = (k < L.n2 - 1) ? u[p + L.sy] : u[p - (long)(L.n2 - 1) * L.sy];
-      uD = (k > 0) ? u[p - L.sy] : u[p + (long)(L.n2 - 1) * L.sy];
-    }
     T c;
     if (G == CART)
       c = L.ih2s;
@@ -209,7 +266,7 @@ __device__ __forceinline__ T lap_scalar(const LevelView<T>& L, const T* __restri
       c = L.TI(TI_PHI, i);
     else
       c = L.TI(TI_IX2, i) * L.TJ(TJ_PF, j);
-    Lu += c * (uU - T(2) * uc + uD);
+    Lu += c * (nb.up - T(2) * uc + nb.dn);
     D -= T(2) * c;
   }
   return Lu;
@@ -367,19 +424,32 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-wide max of NV values, one atomicMax per value per block.  Every
-// thread of the block must call it.  NaN inputs are mapped to +inf.
+// |v| as ordered bits (non-negative doubles order like their bit
+// patterns); NaN -> +inf.  Integer work only: on GPUs with few FP64 units
+// the norms of a residual must not compete with its stencil for them.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+  return b > 0x7ff0000000000000ULL ? 0x7ff0000000000000ULL : b;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide max of NV values given as abs_bits, one atomicMax per value
+// per block.  Every thread of the block must call it.
 template <int NV>
-__device__ __forceinline__ void block_max_atomic(double (&v)[NV], unsigned long long* out) {
-  __shared__ double sm[NV][32];
+__device__ __forceinline__ void block_max_bits(unsigned long long (&v)[NV], unsigned long long* out) {
+  __shared__ unsigned long long sm[NV][32];
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    double x = v[q];
-    if (!(x <= 1.7976931348623157e308)) x = __longlong_as_double(0x7ff0000000000000LL);
-    x = warp_max(x);
+    const unsigned long long x = warp_max_bits(v[q]);
     if (lane == 0) sm[q][warp] = x;
   }
   __syncthreads();
@@ -387,11 +457,19 @@ __device__ __forceinline__ void block_max_atomic(double (&v)[NV], unsigned long 
     const int nw = (nthr + 31) >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double x = (lane < nw) ? sm[q][lane] : 0.0;
-      x = warp_max(x);
-      if (lane == 0 && x > 0.0) atomicMax(out + q, ord_bits(x));
+      const unsigned long long x = warp_max_bits((lane < nw) ? sm[q][lane] : 0ULL);
+      if (lane == 0 && x > 0ULL) atomicMax(out + q, x);
     }
   }
+}
+
+// Block-wide max of NV non-negative doubles (NaN -> +inf).
+template <int NV>
+__device__ __forceinline__ void block_max_atomic(double (&v)[NV], unsigned long long* out) {
+  unsigned long long b[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) b[q] = abs_bits(v[q]);
+  block_max_bits<NV>(b, out);
 }
 
 }  // namespace gmg

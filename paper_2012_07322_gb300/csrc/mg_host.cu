@@ -207,7 +207,7 @@ size_t layout(mg_hierarchy* H, const mg_grid_desc* d, char* base) {
   const bool mixed = d->precision == MG_MIXED;
   const int three = d->ndim == 3;
   for (int l = 0; l < nl; ++l) {
-    const long sx = n[l][0] + 2, sy = sx * (n[l][1] + 2);
+    const long sx = row_stride(n[l][0]), sy = sx * (n[l][1] + 2);
     const long ng = sy * (n[l][2] + 2 * three);
     const size_t b64 = sizeof(double) * ng, b32 = sizeof(float) * ng;
     Level* L = H ? &H->L[l] : nullptr;
@@ -383,14 +383,19 @@ void fill_all64(mg_hierarchy* H, const Eq& e, int l) {
 void smooth64(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
   Level& L = H->L[l];
   auto v = with_bc(L.v64, e.bc);
-  const bool fused = e.kind == EQ_LIN && fused_sweep_applies(v);
-  for (int s = 0; s < nsweeps; ++s) {
-    if (fused) {
-      long tok = prof_begin(H, l, MG_PROF_SWEEP64_FUSED, L.cells());
-      launch_sweep_fused<double>(v, L.u[0], fptr(H, e, l, 0), s1ptr(H, e, l), H->st);
-      prof_end(H, tok);
-      continue;
+  int s0 = 0;
+  if (e.kind == EQ_LIN && fused_sweep_applies(v)) {
+    // sweeps in pairs, out of place through the free component-1 array:
+    // u[0] -> u[1] -> u[0]; an odd last sweep runs as two colour passes
+    for (; s0 + 2 <= nsweeps; s0 += 2) {
+      for (int leg = 0; leg < 2; ++leg) {
+        long tok = prof_begin(H, l, MG_PROF_SWEEP64_FUSED, L.cells());
+        launch_sweep_fused<double>(v, L.u[leg], L.u[1 - leg], fptr(H, e, l, 0), s1ptr(H, e, l), H->st);
+        prof_end(H, tok);
+      }
     }
+  }
+  for (int s = s0; s < nsweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
       if (e.kind != EQ_VEC) {
         long tok = prof_begin(H, l, MG_PROF_SMOOTH64_SCALAR, L.cells() / 2);
@@ -464,18 +469,23 @@ double bits_to_double(unsigned long long b) {
   return x;
 }
 
-// Finest-level residual (into L0.r) and its weighted relative norm.
+// Finest-level residual and its weighted relative norm; in mixed precision
+// the residual is also stored, rounded, as the FP32 right-hand side f32.
 int finest_norm(mg_hierarchy* H, const Eq& e, double* rel) {
   Level& L = H->L[0];
   auto v = with_bc(L.v64, e.bc);
   CK(cudaMemsetAsync(H->d_red, 0, sizeof(unsigned long long) * 3, H->st));
   long tok = prof_begin(H, 0, e.kind == EQ_VEC ? MG_PROF_RESID64_VEC : MG_PROF_RESID64_SCALAR, L.cells());
+  // the residual itself is needed only as the FP32 right-hand side of the
+  // next correction cycle (mixed); the FP64 V-cycle recomputes its own
+  const bool mixed = H->d.precision == MG_MIXED;
   if (e.kind != EQ_VEC) {
-    launch_residual_scalar(v, e.kind, L.u[0], fptr(H, e, 0, 0), s0ptr(H, e, 0), s1ptr(H, e, 0), L.r[0], H->d_red,
-                           1, H->st);
+    launch_residual_scalar(v, e.kind, L.u[0], fptr(H, e, 0, 0), s0ptr(H, e, 0), s1ptr(H, e, 0),
+                           (double*)nullptr, H->d_red, 1, H->st, mixed ? L.f32[0] : nullptr);
   } else {
     const double* f[3] = {L.f[0], L.f[1], L.f[2]};
-    launch_residual_vec(v, L.u, f, L.r, H->d_red, 1, H->st);
+    double* const none[3] = {nullptr, nullptr, nullptr};
+    launch_residual_vec(v, L.u, f, none, H->d_red, 1, H->st, mixed ? L.f32 : nullptr);
   }
   prof_end(H, tok);
   CK(cudaGetLastError());
@@ -510,14 +520,18 @@ void smooth32(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
   Level& L = H->L[l];
   auto v = with_bc(L.v32, e.bc);
   const float* K = (e.kind == EQ_PSI || e.has_c) ? L.k32 : nullptr;
-  const bool fused = e.kind != EQ_VEC && fused_sweep_applies(v);
-  for (int s = 0; s < nsweeps; ++s) {
-    if (fused) {
-      long tok = prof_begin(H, l, MG_PROF_SWEEP32_FUSED, L.cells());
-      launch_sweep_fused<float>(v, L.e[0], L.f32[0], K, H->st);
-      prof_end(H, tok);
-      continue;
+  int s0 = 0;
+  if (e.kind != EQ_VEC && fused_sweep_applies(v)) {
+    // as in smooth64: pairs of out-of-place sweeps e[0] -> e[1] -> e[0]
+    for (; s0 + 2 <= nsweeps; s0 += 2) {
+      for (int leg = 0; leg < 2; ++leg) {
+        long tok = prof_begin(H, l, MG_PROF_SWEEP32_FUSED, L.cells());
+        launch_sweep_fused<float>(v, L.e[leg], L.e[1 - leg], L.f32[0], K, H->st);
+        prof_end(H, tok);
+      }
     }
+  }
+  for (int s = s0; s < nsweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
       if (e.kind != EQ_VEC) {
         long tok = prof_begin(H, l, MG_PROF_SMOOTH32_SCALAR, L.cells() / 2);
@@ -559,8 +573,89 @@ void coarse32(mg_hierarchy* H, const Eq& e, int l) {
     for (int c = 0; c < 3; ++c) launch_fill_ghosts<float>(with_bc(L.v32, e.bc), L.e[c], c, H->st);
 }
 
+// Parameters of the one-block coarse cycle from level l0 (mg_block.cu):
+// shared-memory offsets of every level's arrays; P.smem = 0 when they do
+// not fit.
+BlockCycle32 block_cycle_params(mg_hierarchy* H, const Eq& e, int l0) {
+  BlockCycle32 P{};
+  const bool hasK = e.kind == EQ_PSI || e.has_c;
+  const int nc = e.kind == EQ_VEC ? 3 : 1;
+  P.nl = H->nlev - l0;
+  if (P.nl > BC_MAX) return P;
+  P.vec = e.kind == EQ_VEC;
+  P.nu1 = H->d.nu1;
+  P.nu2 = H->d.nu2;
+  P.coarse_sweeps = COARSE_SWEEPS;
+  long fl = 0;  // floats
+  auto take = [&](long n) {
+    const long at = fl;
+    fl += (n + 3) & ~3L;
+    return (int)at;
+  };
+  for (int q = 0; q < P.nl; ++q) {
+    Level& L = H->L[l0 + q];
+    BlockLevel32& B = P.lv[q];
+    B.v = with_bc(L.v32, e.bc);
+    for (int c = 0; c < 3; ++c) {
+      if (c < nc) {
+        B.e[c] = take(L.ng);
+        B.f32[c] = take(L.ng);
+        B.r32[c] = take(L.ng);
+      } else {
+        B.e[c] = B.e[0];
+        B.f32[c] = B.f32[0];
+        B.r32[c] = B.r32[0];
+      }
+    }
+    B.k32 = hasK ? L.k32 : nullptr;
+  }
+  Level& Lc = H->L[H->nlev - 1];
+  P.c64 = with_bc(Lc.v64, e.bc);
+  P.fp64_at = (long)sizeof(float) * fl;
+  long dl = 0;  // doubles
+  auto taked = [&](long n) {
+    const long at = dl;
+    dl += (n + 1) & ~1L;
+    return (int)at;
+  };
+  for (int c = 0; c < 3; ++c) {
+    P.cu[c] = c < nc ? taked(Lc.ng) : P.cu[0];
+    P.cf[c] = c < nc ? taked(Lc.ng) : P.cf[0];
+  }
+  P.ck = (hasK && !P.vec) ? taked(Lc.ng) : -1;
+  Level& L0 = H->L[l0];
+  P.ng0 = L0.ng;
+  for (int c = 0; c < 3; ++c) {
+    P.f_in[c] = L0.f32[c];
+    P.e_out[c] = L0.e[c];
+  }
+  const size_t bytes = (size_t)P.fp64_at + sizeof(double) * (size_t)dl;
+  P.smem = bytes <= BC_SMEM_MAX ? bytes : 0;
+  return P;
+}
+
+// First level of the one-block coarse cycle: the first level of at most
+// BLOCK_CYCLE_CELLS cells whose levels down to the coarsest fit the block's
+// shared memory.
+int block_cycle_level(mg_hierarchy* H, const Eq& e) {
+  for (int l = 0; l < H->nlev; ++l)
+    if (H->L[l].cells() <= BLOCK_CYCLE_CELLS && block_cycle_params(H, e, l).smem > 0) return l;
+  return H->nlev;
+}
+
+// vcycle32 from level l0 down, in one block.
+void block_vcycle32(mg_hierarchy* H, const Eq& e, int l0) {
+  const BlockCycle32 P = block_cycle_params(H, e, l0);
+  for (int l = l0; l + 1 < H->nlev; ++l) H->updates += (int64_t)(H->d.nu1 + H->d.nu2) * H->L[l].cells() * e.ncomp;
+  launch_block_vcycle32(P, H->d.geom, H->st);
+}
+
 // Linear correction-scheme V-cycle on (L - K) e = f32, e = 0 initially.
 void vcycle32(mg_hierarchy* H, const Eq& e, int l) {
+  if (l >= block_cycle_level(H, e)) {
+    block_vcycle32(H, e, l);
+    return;
+  }
   if (l == H->nlev - 1) {
     coarse32(H, e, l);
     return;
@@ -613,18 +708,18 @@ int cycle_map(mg_hierarchy* H, const Eq& e) {
     vcycle64(H, e, 0);
   } else {
     auto v = with_bc(L0.v64, e.bc);
-    for (int c = 0; c < e.ncomp; ++c) {
-      launch_convert<double, float>(v, L0.r[c], L0.f32[c], H->st);
-      CK(cudaMemsetAsync(L0.e[c], 0, sizeof(float) * L0.ng, H->st));
-    }
+    // f32 holds the FP32 residual written by the preceding finest_norm
+    for (int c = 0; c < e.ncomp; ++c) CK(cudaMemsetAsync(L0.e[c], 0, sizeof(float) * L0.ng, H->st));
     if (e.kind == EQ_PSI) {
       launch_psi_linearisation(v, L0.u[0], L0.s0, L0.s1, L0.k32, H->st);
       restrict_k32(H);
     }
     vcycle32(H, e, 0);
-    for (int c = 0; c < e.ncomp; ++c) launch_add_correction<float>(v, L0.u[c], L0.e[c], H->st);
+    for (int c = 0; c < e.ncomp; ++c)
+      launch_add_correction<float>(v, L0.u[c], L0.e[c], H->st, (e.zero_mean && c == 0) ? H->d_part : nullptr,
+                                   NPARTS);
   }
-  if (e.zero_mean) launch_sub_mean(L0.v64, L0.u[0], H->d_part, NPARTS, H->st);
+  if (e.zero_mean) launch_sub_mean(L0.v64, L0.u[0], H->d_part, NPARTS, H->st, H->d.precision == MG_MIXED);
   if (e.kind == EQ_VEC) fill_all64(H, e, 0);
   return MG_OK;
 }
@@ -966,6 +1061,7 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
   cudaMemsetAsync(H->arena, 0, bytes, H->st);
   init_fused_sweep_attributes<double>();
   init_fused_sweep_attributes<float>();
+  init_block_cycle_attributes();
   const int three = H->d.ndim == 3;
   for (int l = 0; l < H->nlev; ++l) {
     Level& L = H->L[l];
@@ -974,9 +1070,9 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
       L.h[k] = h[l][k];
       L.lo[k] = H->d.lo[k];
     }
-    L.sx = L.n[0] + 2;
+    L.sx = row_stride(L.n[0]);
     L.sy = L.sx * (L.n[1] + 2);
-    L.off = 1 + L.sx + three * L.sy;
+    L.off = ROW_PAD + L.sx + three * L.sy;
     L.ng = L.sy * (L.n[2] + 2 * three);
     std::vector<double> ti, tj;
     make_tables(&H->d, L, ti, tj);

@@ -23,24 +23,37 @@ void launch_smooth_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
                           int colour, cudaStream_t st);
 template <typename T>
 void launch_fill_ghosts(const LevelView<T>& L, T* u, int comp, cudaStream_t st);
-// One fused red-black sweep (Cartesian 3D linear scalar equations, levels of
-// at least one tile); returns false when it does not apply.
+// Row layout of every level array: ROW_PAD - 1 padding cells, the low
+// ghost, the n0 interior cells, the high ghost, then padding to a multiple
+// of ROW_PAD cells.  Interior rows (i = 0) and row strides are then 16-byte
+// aligned for FP32 and FP64 arrays alike, and a row can be read in 16-byte
+// pieces from i = -ROW_PAD to i = n0 + ROW_PAD - 1 without leaving it.
+constexpr long ROW_PAD = 4;
+inline long row_stride(int n0) { return (n0 + 2 * ROW_PAD + ROW_PAD - 1) / ROW_PAD * ROW_PAD; }
+
+// One red-black sweep in one launch (Cartesian 3D linear scalar equations,
+// levels of at least one 64 x 8 column), out of place: uin -> uout, which
+// must not alias; only the interior of uout is written.  Returns false when
+// it does not apply.
 template <typename T>
-bool launch_sweep_fused(const LevelView<T>& L, T* u, const T* f, const T* c, cudaStream_t st);
+bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st);
 template <typename T>
 void init_fused_sweep_attributes();
 template <typename T>
 inline bool fused_sweep_applies(const LevelView<T>& L) {
-  return L.geom == CART && L.three && L.n0 >= 32 && L.n1 >= 8 && L.n2 >= 8;
+  return L.geom == CART && L.three && L.n0 >= 64 && L.n1 >= 8 && L.n2 >= 4;
 }
 template <typename T>
 void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st);
+// r = f - L(u) into r (nullable) and, rounded to FP32, into r32 (nullable);
+// red (nullable) receives the norms of the finest-level stopping rule.
 template <typename T>
 void launch_residual_scalar(const LevelView<T>& L, int kind, const T* u, const T* f, const T* s0,
-                            const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st);
+                            const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st,
+                            float* r32 = nullptr);
 template <typename T>
 void launch_residual_vec(const LevelView<T>& L, T* const V[3], const T* const f[3], T* const r[3],
-                         unsigned long long* red, int weighted, cudaStream_t st);
+                         unsigned long long* red, int weighted, cudaStream_t st, float* const r32[3] = nullptr);
 template <typename T>
 void launch_apply_scalar(const LevelView<T>& L, int kind, const T* u, const T* s0, const T* s1, T* out,
                          int add, cudaStream_t st);
@@ -57,16 +70,22 @@ void launch_coarse_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
                           int max_sweeps, cudaStream_t st);
 template <typename T>
 void launch_coarse_vec(const LevelView<T>& L, T* V[3], const T* const f[3], int max_sweeps, cudaStream_t st);
+// u -= mean(u) over the interior (the Neumann gauge); the nparts block sums
+// are computed first unless have_part (left by launch_add_correction).
 template <typename T>
-void launch_sub_mean(const LevelView<T>& L, T* u, double* part, int nparts, cudaStream_t st);
+void launch_sub_mean(const LevelView<T>& L, T* u, double* part, int nparts, cudaStream_t st,
+                     bool have_part = false);
 template <typename A, typename B>
 void launch_copy_in(const LevelView<B>& L, const A* src, B* dst, A shift, cudaStream_t st);
 template <typename A, typename B>
 void launch_copy_out(const LevelView<A>& L, const A* src, B* dst, A shift, cudaStream_t st);
 template <typename A, typename B>
 void launch_convert(const LevelView<A>& L, const A* src, B* dst, cudaStream_t st);
+// u += e over the interior; with part non-null also the nparts block sums
+// of the updated u for launch_sub_mean.
 template <typename T>
-void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st);
+void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st,
+                           double* part = nullptr, int nparts = 0);
 
 // xCFC and divergence-cleaning pointwise kernels (mg_xcfc.cu).
 void launch_xcfc_a2(const LevelView<double>& L, double* const X[3], double* A2, cudaStream_t st);
@@ -106,5 +125,30 @@ void launch_aa_dots(const LevelView<double>& L, int ncomp, long stride, const do
                     const AACols& cols, int newcol, double* part, cudaStream_t st);
 void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], const double* dG,
                        const AACols& cols, cudaStream_t st);
+
+// One-block FP32 correction V-cycle over the coarse levels (mg_block.cu):
+// the levels l0 .. l0 + nl - 1 of a hierarchy, the last the coarsest, all
+// held in the block's shared memory (same ghosted layout as in HBM).
+constexpr int BC_MAX = 8;                     // levels one block cycle may span
+constexpr long BLOCK_CYCLE_CELLS = 4096;       // levels this small run in the block cycle
+constexpr size_t BC_SMEM_MAX = 200 * 1024;     // dynamic shared memory of the block cycle
+struct BlockLevel32 {
+  LevelView<float> v;        // boundary rule applied
+  int e[3], f32[3], r32[3];  // offsets (floats) of correction, right-hand side, residual in shared memory
+  const float* k32;          // c of (L - c) e = f in HBM, null without
+};
+struct BlockCycle32 {
+  int nl, vec, nu1, nu2, coarse_sweeps;
+  BlockLevel32 lv[BC_MAX];
+  LevelView<double> c64;  // the coarsest level, boundary rule applied
+  int cu[3], cf[3], ck;   // offsets (doubles, from fp64_at) of the FP64 coarsest solve; ck < 0: no c
+  long fp64_at;           // byte offset of the FP64 area in shared memory
+  long ng0;               // ghosted size of level l0
+  const float* f_in[3];   // level l0 right-hand side in HBM
+  float* e_out[3];        // level l0 correction in HBM (written at the end)
+  size_t smem;            // dynamic shared memory bytes
+};
+void launch_block_vcycle32(const BlockCycle32& P, int geom, cudaStream_t st);
+void init_block_cycle_attributes();
 
 }  // namespace gmg

@@ -42,82 +42,274 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
   vec_update<T, G>(L, A, B, C, f, comp, i, j, k);
 }
 
-// One full red-black sweep of a Cartesian linear scalar equation in one
-// launch.  A block stages a TX x TY x TZ tile of u, f (and c) with a
-// two-cell halo in shared memory, relaxes the red cells of the tile and of
-// a one-cell ring around it (the ring is recomputed by the neighbouring
-// tiles with the same arithmetic), then the black cells of the tile, and
-// writes the tile back: u and f cross DRAM once per sweep instead of once
-// per colour.  The cell updates are the ones of k_smooth_scalar.
-constexpr int FT_X = 32, FT_Y = 8, FT_Z = 8, FH = 2;
-constexpr int FS_X = FT_X + 2 * FH, FS_Y = FT_Y + 2 * FH, FS_Z = FT_Z + 2 * FH;
-constexpr int FS_N = FS_X * FS_Y * FS_Z;
+// One full red-black sweep of a Cartesian 3D linear scalar equation in one
+// launch, out of place (uin -> uout).  A block owns a column of TX x RB_TY
+// cells over a chunk of planes [z0, z1) and marches along k.  Plane by
+// plane it stages a (TX + 8) x (RB_TY + 4) box of u, f and c (the column
+// with a 4-cell halo in i, 2 cells in j; rows are 16-byte aligned, so the
+// box moves in 16-byte asynchronous copies issued two planes ahead),
+// relaxes the red cells of plane s over its column and a one-cell ring
+// around it (the ring cells are relaxed with the same arithmetic by the
+// neighbouring columns), then the black cells of plane s - 1, and stores
+// plane s - 1.  The red cells of planes z0 - 1 and z1 are likewise relaxed
+// by two chunks.  Every value read comes from uin, which no block writes, so
+// the result is the red-black sweep of k_smooth_scalar whatever order the
+// blocks run in, and u, f and c cross DRAM once per sweep instead of once
+// per colour.  Warp w owns row w; each lane owns TX / 64 pairs of cells.
+constexpr int RB_TY = 8, RB_THREADS = 256;
+constexpr int RB_HX = 4, RB_HY = 2;  // staged halo
+constexpr int RB_BY = RB_TY + 2 * RB_HY;
+// plane buffers: u planes s-3..s+2 and f, c planes s-2..s+1 are in use or
+// in flight at step s (the f ring is indexed by plane & 3)
+constexpr int RB_NU = 6, RB_NF = 4;
+static_assert(RB_HX == ROW_PAD, "the staged box starts on a 16-byte boundary");
+
+template <int TX>
+struct RbShape {
+  static constexpr int BX = TX + 2 * RB_HX, BP = BX * RB_BY;
+  static constexpr int RING = TX + 2 + RB_TY;  // red ring cells: two rows of (TX+2)/2, two columns of TY/2
+};
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_fused_cart(LevelView<T> L, T* __restrict__ u,
-                                                          const T* __restrict__ f, const T* __restrict__ c) {
-  extern __shared__ unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);
-  T* sf = su + FS_N;
-  T* sc = sf + FS_N;
-  const int i0 = blockIdx.x * FT_X - FH, j0 = blockIdx.y * FT_Y - FH, k0 = blockIdx.z * FT_Z - FH;
-  const int tid = threadIdx.x;
-  const bool inner = i0 >= 0 && j0 >= 0 && k0 >= 0 && i0 + FS_X <= L.n0 && j0 + FS_Y <= L.n1 &&
-                     k0 + FS_Z <= L.n2;
-  // stage the tile with its halo, one smem row (FS_X cells) per step
-  for (int q = tid; q < FS_N; q += blockDim.x) {
-    const int row = q / FS_X, a = q - row * FS_X;
-    const int b = row % FS_Y, cz = row / FS_Y;
-    const int i = i0 + a, j = j0 + b, k = k0 + cz;
-    const bool in = inner || (i >= 0 && i < L.n0 && j >= 0 && j < L.n1 && k >= 0 && k < L.n2);
-    const long p = in ? L.idx(i, j, k) : 0;
-    su[q] = in ? u[p] : T(0);
-    sf[q] = (in && f) ? f[p] : T(0);
-    if (c) sc[q] = in ? c[p] : T(0);
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The 16-byte pieces of the staged box this thread copies, fixed for the
+// whole march: global offset within a plane, offset in the plane buffer.
+template <typename T, int TX>
+struct RbPieces {
+  static constexpr int BX = RbShape<TX>::BX;
+  static constexpr int PER_ROW = BX * (int)sizeof(T) / 16, N = RB_BY * PER_ROW;
+  static constexpr int ITEMS = (N + RB_THREADS - 1) / RB_THREADS;
+  long g[ITEMS];
+  int s[ITEMS];
+  bool ok[ITEMS];
+  __device__ __forceinline__ RbPieces(const LevelView<T>& L, int i0, int j0) {
+#pragma unroll
+    for (int m = 0; m < ITEMS; ++m) {
+      const int q = threadIdx.x + m * RB_THREADS;
+      const int ly = q / PER_ROW, cx = q - ly * PER_ROW;
+      const int j = j0 - RB_HY + ly, x = cx * (16 / (int)sizeof(T));
+      ok[m] = q < N && j >= -1 && j <= L.n1;  // rows of the ghosted array
+      g[m] = L.off + (i0 - RB_HX + x) + (long)j * L.sx;
+      s[m] = ly * BX + x;
+    }
   }
-  __syncthreads();
-  LevelView<T> S = L;  // shared-memory view: same geometry, tile strides
-  S.sx = FS_X;
-  S.sy = (long)FS_X * FS_Y;
-  // red over the tile and a one-cell ring (recomputed identically by the
-  // neighbouring tiles), then black over the tile; work items enumerate
-  // only the cells of the colour: (row, t) -> x = lo + 2 t + parity
-  for (int colour = 0; colour < 2; ++colour) {
-    const int ring = colour == 0 ? 1 : 0;
-    const int ex = FT_X + 2 * ring, ey = FT_Y + 2 * ring, ez = FT_Z + 2 * ring;
-    const int half = ex / 2;
-    const int nwork = half * ey * ez;
-    const int xlo = FH - ring, ylo = FH - ring, zlo = FH - ring;  // smem coordinates
-    for (int q = tid; q < nwork; q += blockDim.x) {
-      const int row = q / half, t = q - row * half;
-      const int b = ylo + row % ey, cz = zlo + row / ey;
-      const int j = j0 + b, k = k0 + cz;
-      // i0 + a with a = xlo + 2 t + shift has parity colour
-      const int shift = (colour - (i0 + xlo + j + k)) & 1;
-      const int a = xlo + 2 * t + shift;
-      const int i = i0 + a;
-      if (a >= xlo + ex) continue;
-      if (!inner && (i < 0 || i >= L.n0 || j < 0 || j >= L.n1 || k < 0 || k >= L.n2)) continue;
-      const long ps = a + (long)b * FS_X + (long)cz * FS_X * FS_Y;
-      T D;
-      T Lu = lap_scalar<T, CART>(S, su, i, j, k, ps, D);
-      if (c) {
-        const T cv = sc[ps];
-        Lu -= cv * su[ps];
-        D -= cv;
-      }
-      su[ps] = su[ps] - (Lu - sf[ps]) / D;
+  __device__ __forceinline__ void copy(T* buf, const T* __restrict__ src, long plane) const {
+#pragma unroll
+    for (int m = 0; m < ITEMS; ++m)
+      if (ok[m]) cp_async16(buf + s[m], src + g[m] + plane);
+  }
+};
+
+// The staged planes of one relaxation step.
+template <typename T>
+struct RbPlanes {
+  const T* Pd;  // plane s - 1
+  T* P;         // plane s (updated in place)
+  const T* Pu;  // plane s + 1
+  const T* F;   // f of plane s
+  const T* Cc;  // c of plane s
+};
+
+// Newton-Gauss-Seidel update of cell (i0 + x, j0 + y, s): the arithmetic of
+// lap_scalar<CART> and scalar_update<EQ_LIN>.  The outer ghosts a boundary
+// cell needs sit in the staged planes already (rb_fix_ghosts), so every
+// cell takes the same path; RING cells outside the domain are skipped.
+template <typename T, int TX, bool HAS_C, bool RING>
+__device__ __forceinline__ void rb_relax(const LevelView<T>& L, const RbPlanes<T>& R, int i0, int j0, int x, int y,
+                                         T cE, T cW, T D0, T iD0) {
+  constexpr int BX = RbShape<TX>::BX;
+  if (RING) {
+    const int i = i0 + x, j = j0 + y;
+    if (i < 0 || i >= L.n0 || j < 0 || j >= L.n1) return;
+  }
+  const int q = (x + RB_HX) + (y + RB_HY) * BX;
+  const T uc = R.P[q];
+  T Lu = cE * (R.P[q + 1] - uc) - cW * (uc - R.P[q - 1]);
+  Lu += L.ih1s * (R.P[q + BX] - T(2) * uc + R.P[q - BX]);
+  Lu += L.ih2s * (R.Pu[q] - T(2) * uc + R.Pd[q]);
+  if (HAS_C) {
+    const T cv = R.Cc[q];
+    Lu -= cv * uc;
+    R.P[q] = uc - (Lu - R.F[q]) / (D0 - cv);
+  } else {
+    R.P[q] = uc - (Lu - R.F[q]) * iD0;
+  }
+}
+
+// Outer ghosts of staged plane p (just landed, still the sweep's input) in
+// the i and j directions: g = factor * u of the boundary cell, the values
+// lap_scalar folds in.  A ghost is read only by its own boundary cell, whose
+// value is unchanged until that cell's own update, so a ghost written from
+// the input stays exact.
+template <typename T, int TX>
+__device__ __forceinline__ void rb_fix_ghosts(const LevelView<T>& L, T* P, int i0, int j0, int p) {
+  constexpr int BX = RbShape<TX>::BX, NY = RB_TY + 2, NX = TX + 2;
+  const bool xl = i0 == 0, xh = i0 + TX == L.n0, yl = j0 == 0, yh = j0 + RB_TY == L.n1;
+  for (int t = threadIdx.x; t < 2 * NY + 2 * NX; t += RB_THREADS) {
+    if (t < 2 * NY) {  // i ghosts, rows y = -1 .. TY
+      const int y = t % NY - 1, j = j0 + y;
+      const bool hi = t >= NY;
+      if ((hi ? !xh : !xl) || j < 0 || j >= L.n1) continue;
+      const int xs = hi ? TX - 1 : 0, xg = hi ? TX : -1;
+      const T fac = hi ? outer_factor(L, L.n0, j, p, L.n0 - 1, j, p) : outer_factor(L, -1, j, p, 0, j, p);
+      P[(xg + RB_HX) + (y + RB_HY) * BX] = fac * P[(xs + RB_HX) + (y + RB_HY) * BX];
+    } else {  // j ghosts, columns x = -1 .. TX
+      const int u = t - 2 * NY;
+      const int x = u % NX - 1, i = i0 + x;
+      const bool hi = u >= NX;
+      if ((hi ? !yh : !yl) || i < 0 || i >= L.n0) continue;
+      const int ys = hi ? RB_TY - 1 : 0, yg = hi ? RB_TY : -1;
+      const T fac = hi ? outer_factor(L, i, L.n1, p, i, L.n1 - 1, p) : outer_factor(L, i, -1, p, i, 0, p);
+      P[(x + RB_HX) + (yg + RB_HY) * BX] = fac * P[(x + RB_HX) + (ys + RB_HY) * BX];
+    }
+  }
+}
+
+// Ghost plane pg (-1 or n2) from the staged plane ps next to it.
+template <typename T, int TX>
+__device__ __forceinline__ void rb_ghost_plane(const LevelView<T>& L, T* G, const T* S, int i0, int j0, int pg,
+                                               int ps) {
+  constexpr int BX = RbShape<TX>::BX, NY = RB_TY + 2, NX = TX + 2;
+  for (int t = threadIdx.x; t < NX * NY; t += RB_THREADS) {
+    const int y = t / NX - 1, x = t % NX - 1, i = i0 + x, j = j0 + y;
+    if (i < 0 || i >= L.n0 || j < 0 || j >= L.n1) continue;
+    const int q = (x + RB_HX) + (y + RB_HY) * BX;
+    G[q] = outer_factor(L, i, j, pg, i, j, ps) * S[q];
+  }
+}
+
+// Red cells of plane s: the lane's cells of its row, then the ring.
+template <typename T, int TX, bool HAS_C>
+__device__ __forceinline__ void rb_red_plane(const LevelView<T>& L, const RbPlanes<T>& R, int i0, int j0, int s,
+                                             T cE, T cW, T D0, T iD0) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
+  const int par = (i0 + j0 + s) & 1;  // red: (i + j + s) even
+#pragma unroll
+  for (int h = 0; h < TX / 64; ++h)
+    rb_relax<T, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + ((par + w) & 1), w, cE, cW, D0, iD0);
+  if (t < RbShape<TX>::RING) {
+    constexpr int HR = (TX + 2) / 2, HC = RB_TY / 2;
+    int x, y;
+    if (t < HR) {
+      y = -1;
+      x = -1 + 2 * t + par;
+    } else if (t < 2 * HR) {
+      y = RB_TY;
+      x = -1 + 2 * (t - HR) + (par ^ 1);
+    } else if (t < 2 * HR + HC) {
+      x = -1;
+      y = 2 * (t - 2 * HR) + (par ^ 1);
+    } else {
+      x = TX;
+      y = 2 * (t - 2 * HR - HC) + par;
+    }
+    rb_relax<T, TX, HAS_C, true>(L, R, i0, j0, x, y, cE, cW, D0, iD0);
+  }
+}
+
+template <typename T, int TX, bool HAS_C>
+__global__ void __launch_bounds__(RB_THREADS) k_sweep_rb_cart(LevelView<T> L, const T* __restrict__ uin,
+                                                              T* __restrict__ uout, const T* __restrict__ f,
+                                                              const T* __restrict__ c, int zc) {
+  constexpr int BX = RbShape<TX>::BX, BP = RbShape<TX>::BP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* sf = su + RB_NU * BP;
+  T* sc = sf + RB_NF * BP;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * RB_TY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.n2);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const T cE = L.TI(TI_CE, 0), cW = L.TI(TI_CW, 0);  // uniform on a Cartesian grid
+  const T D0 = -(cE + cW) - T(2) * L.ih1s - T(2) * L.ih2s;
+  const T iD0 = T(1) / D0;
+  const bool edge_xy = i0 == 0 || j0 == 0 || i0 + TX >= L.n0 || j0 + RB_TY >= L.n1;
+  const RbPieces<T, TX> pc(L, i0, j0);
+  // group p: u plane p (into u buffer bu) and f, c plane p - 1, for the
+  // planes the chunk needs
+  auto stage = [&](int p, int bu) {
+    if (p >= 0 && p < L.n2 && p >= z0 - 2 && p <= z1 + 1) pc.copy(su + bu * BP, uin, (long)p * L.sy);
+    const int pf = p - 1;
+    if (pf >= 0 && pf < L.n2 && pf >= z0 - 1 && pf <= z1) {
+      const int bf = (pf & (RB_NF - 1)) * BP;
+      pc.copy(sf + bf, f, (long)pf * L.sy);
+      if (HAS_C) pc.copy(sc + bf, c, (long)pf * L.sy);
+    }
+    cp_async_commit();
+  };
+  auto next6 = [](int b) { return b == RB_NU - 1 ? 0 : b + 1; };
+  // u buffers of consecutive planes are consecutive modulo RB_NU
+  int b = ((z0 - 2) % RB_NU + RB_NU) % RB_NU;  // plane z0 - 2
+  stage(z0 - 2, b);
+  int bd = next6(b);  // plane z0 - 1
+  stage(z0 - 1, bd);
+  int bs = next6(bd);  // plane z0
+  stage(z0, bs);
+  // at step s: b, bd, bs, bu: u buffers of planes s - 2, s - 1, s, s + 1
+  int bu = bs;
+  bs = bd;
+  bd = b;
+  b = (b + RB_NU - 1) % RB_NU;
+  for (int s = z0 - 1; s <= z1; ++s) {
+    const int bn2 = next6(bu);
+    stage(s + 2, bn2);
+    cp_async_wait<1>();  // u plane s + 1 and f, c plane s have landed
+    __syncthreads();
+    // outer ghosts of the planes about to be relaxed
+    if (edge_xy) {
+      if (s == z0 - 1 && s >= 0) rb_fix_ghosts<T, TX>(L, su + bs * BP, i0, j0, s);
+      if (s + 1 >= 0 && s + 1 < L.n2) rb_fix_ghosts<T, TX>(L, su + bu * BP, i0, j0, s + 1);
+    }
+    if (s + 1 == 0) rb_ghost_plane<T, TX>(L, su + bs * BP, su + bu * BP, i0, j0, -1, 0);
+    if (s + 1 == L.n2 - 1) rb_ghost_plane<T, TX>(L, su + bn2 * BP, su + bu * BP, i0, j0, L.n2, L.n2 - 1);
+    if (s == z0 - 1) __syncthreads();
+    if (s >= 0 && s < L.n2) {
+      const int bf = (s & (RB_NF - 1)) * BP;
+      const RbPlanes<T> R{su + bd * BP, su + bs * BP, su + bu * BP, sf + bf, sc + bf};
+      rb_red_plane<T, TX, HAS_C>(L, R, i0, j0, s, cE, cW, D0, iD0);
     }
     __syncthreads();
+    const int sb = s - 1;
+    if (sb >= z0) {
+      // black cells of plane sb = s - 1 (planes s - 2, s - 1, s), then store
+      const int bf = (sb & (RB_NF - 1)) * BP;
+      const RbPlanes<T> R{su + b * BP, su + bd * BP, su + bs * BP, sf + bf, sc + bf};
+      const int par = (i0 + j0 + sb + w + 1) & 1;  // black: (i + j + sb) odd
+#pragma unroll
+      for (int h = 0; h < TX / 64; ++h)
+        rb_relax<T, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + par, w, cE, cW, D0, iD0);
+      using V2 = typename Vec2<T>::type;  // pairs (i, i + 1): n0 a multiple of TX, rows 16-byte aligned
+#pragma unroll
+      for (int h = 0; h < TX / 64; ++h) {
+        const int x = 64 * h + 2 * lane;
+        *reinterpret_cast<V2*>(uout + L.idx(i0 + x, j0 + w, sb)) =
+            *reinterpret_cast<const V2*>(R.P + (x + RB_HX) + (w + RB_HY) * BX);
+      }
+    }
+    b = bd;
+    bd = bs;
+    bs = bu;
+    bu = bn2;
   }
-  // write the tile back
-  for (int q = tid; q < FT_X * FT_Y * FT_Z; q += blockDim.x) {
-    const int row = q / FT_X, a = q - row * FT_X;
-    const int b = row % FT_Y, cz = row / FT_Y;
-    const int i = i0 + FH + a, j = j0 + FH + b, k = k0 + FH + cz;
-    if (!inner && (i >= L.n0 || j >= L.n1 || k >= L.n2)) continue;
-    u[L.idx(i, j, k)] = su[(a + FH) + (long)(b + FH) * FS_X + (long)(cz + FH) * FS_X * FS_Y];
-  }
+  cp_async_wait<0>();
 }
 
 template <typename T>
@@ -131,75 +323,77 @@ __global__ void k_fill_ghosts(LevelView<T> L, T* __restrict__ u, int comp) {
 
 // r = f - L(u) on every interior cell.  red (if non-null) receives
 // max |r| (slot 0) and, when weighted, max |w r| (slot 1), max |w S| (slot 2).
+// A thread walks RES_KZ planes (k strided by blockDim.z) so that the block
+// reduction of the norms is paid once per RES_KZ cells.
+constexpr int RES_KZ = 4;
+
 template <typename T, int G, int KIND>
 __global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                   const T* __restrict__ s0, const T* __restrict__ s1, T* __restrict__ r,
-                                  unsigned long long* red, int weighted) {
+                                  float* __restrict__ r32, unsigned long long* red, int weighted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z * blockDim.z + threadIdx.z;
-  double m[3] = {0.0, 0.0, 0.0};
-  if (i < L.n0 && j < L.n1 && k < L.n2) {
-    const long p = L.idx(i, j, k);
-    T D;
-    const T lap = lap_scalar<T, G>(L, u, i, j, k, p, D);
-    const T fv = f ? f[p] : T(0);
-    // S(u) as the paper writes the right-hand side; L(u) = lap u - S(u)
-    // (eq. psi) or lap u - c u (linear, S = f + c u)
-    T Sv, Lu;
-    if (KIND == EQ_PSI) {
-      const T ip = T(1) / (T(1) + u[p]);
-      const T ip2 = ip * ip;
-      const T ip7 = ip2 * ip2 * ip2 * ip;
-      Sv = -T(2 * PI_D) * s0[p] * ip - T(0.125) * s1[p] * ip7;
-      Lu = lap - Sv;
-    } else {
-      const T cu = s1 ? s1[p] * u[p] : T(0);
-      Lu = lap - cu;
-      Sv = fv + cu;
+  unsigned long long m[3] = {0ULL, 0ULL, 0ULL};
+  if (i < L.n0 && j < L.n1) {
+    const double w = weighted ? (double)norm_weight(L, i, j) : 1.0;
+#pragma unroll
+    for (int it = 0; it < RES_KZ; ++it) {
+      const int k = (blockIdx.z * RES_KZ + it) * blockDim.z + threadIdx.z;
+      if (k >= L.n2) continue;
+      const long p = L.idx(i, j, k);
+      T Sv;
+      const T rv = scalar_residual_cell<T, G, KIND>(L, u, f, s0, s1, i, j, k, p, Sv);
+      if (r) r[p] = rv;
+      if (r32) r32[p] = (float)rv;
+      if (red) {
+        m[0] = umax64(m[0], abs_bits((double)rv));
+        if (weighted) {
+          if (G != CART) m[1] = umax64(m[1], abs_bits(w * (double)rv));
+          m[2] = umax64(m[2], abs_bits(G == CART ? (double)Sv : w * (double)Sv));
+        }
+      }
     }
-    const T rv = fv - Lu;
-    if (r) r[p] = rv;
-    m[0] = fabs((double)rv);
-    if (weighted) {
-      const double w = (double)norm_weight(L, i, j);
-      m[1] = fabs(w * (double)rv);
-      m[2] = fabs(w * (double)Sv);
-    }
+    if (G == CART && weighted) m[1] = m[0];  // unit weight
   }
-  if (red) block_max_atomic<3>(m, red);
+  if (red) block_max_bits<3>(m, red);
 }
 
 template <typename T, int G>
 __global__ void k_residual_vec(LevelView<T> L, const T* __restrict__ A, const T* __restrict__ B,
                                const T* __restrict__ C, const T* __restrict__ f0, const T* __restrict__ f1,
                                const T* __restrict__ f2, T* __restrict__ r0, T* __restrict__ r1,
-                               T* __restrict__ r2, unsigned long long* red, int weighted) {
+                               T* __restrict__ r2, float* __restrict__ q0, float* __restrict__ q1,
+                               float* __restrict__ q2, unsigned long long* red, int weighted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z * blockDim.z + threadIdx.z;
-  double m[3] = {0.0, 0.0, 0.0};
-  if (i < L.n0 && j < L.n1 && k < L.n2) {
-    const long p = L.idx(i, j, k);
+  unsigned long long m[3] = {0ULL, 0ULL, 0ULL};
+  if (i < L.n0 && j < L.n1) {
     const double w = weighted ? (double)norm_weight(L, i, j) : 1.0;
     const T* fs[3] = {f0, f1, f2};
     T* rs[3] = {r0, r1, r2};
+    float* qs[3] = {q0, q1, q2};
+#pragma unroll 1
+    for (int it = 0; it < RES_KZ; ++it) {
+      const int k = (blockIdx.z * RES_KZ + it) * blockDim.z + threadIdx.z;
+      if (k >= L.n2) continue;
+      const long p = L.idx(i, j, k);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T D;
-      const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
-      const T fv = fs[c] ? fs[c][p] : T(0);
-      const T rv = fv - Lu;
-      if (rs[c]) rs[c][p] = rv;
-      m[0] = fmax(m[0], fabs((double)rv));
-      if (weighted) {
-        m[1] = fmax(m[1], fabs(w * (double)rv));
-        m[2] = fmax(m[2], fabs(w * (double)fv));
+      for (int c = 0; c < 3; ++c) {
+        const T fv = fs[c] ? fs[c][p] : T(0);
+        const T rv = vec_residual_cell<T, G>(L, A, B, C, fs[c], c, i, j, p);
+        if (rs[c]) rs[c][p] = rv;
+        if (qs[c]) qs[c][p] = (float)rv;
+        if (red) {
+          m[0] = umax64(m[0], abs_bits((double)rv));
+          if (weighted) {
+            m[1] = umax64(m[1], abs_bits(w * (double)rv));
+            m[2] = umax64(m[2], abs_bits(w * (double)fv));
+          }
+        }
       }
-      if (rv != rv) m[0] = m[1] = INFINITY;
     }
   }
-  if (red) block_max_atomic<3>(m, red);
+  if (red) block_max_bits<3>(m, red);
 }
 
 // f <- L(u) + f (the FAS coarse right-hand side after restriction placed
@@ -253,34 +447,10 @@ __global__ void k_restrict(LevelView<T> F, LevelView<T> Cv, int nf, const T* __r
   const T* as[4] = {a0, a1, a2, a3};
   T* bs[4] = {b0, b1, b2, b3};
   T* cs[3] = {copy0, copy1, copy2};
-  T wi[2], wj[2];
-  wi[0] = F.TI(TI_VW, 2 * I);
-  wi[1] = F.TI(TI_VW, 2 * I + 1);
-  wj[0] = F.TJ(TJ_VW, 2 * J);
-  wj[1] = F.TJ(TJ_VW, 2 * J + 1);
-  T wsum = T(0);
-  const int nk = F.three ? 2 : 1;
-  for (int dk = 0; dk < nk; ++dk)
-    for (int dj = 0; dj < 2; ++dj)
-      for (int di = 0; di < 2; ++di) wsum += wi[di] * wj[dj];
-  const T inv = T(1) / wsum;
-  const long q = Cv.idx(I, J, K);
-  for (int m = 0; m < nf; ++m) {
-    T s = T(0);
-    for (int dk = 0; dk < nk; ++dk)
-      for (int dj = 0; dj < 2; ++dj)
-        for (int di = 0; di < 2; ++di)
-          s += wi[di] * wj[dj] * as[m][F.idx(2 * I + di, 2 * J + dj, F.three ? 2 * K + dk : 0)];
-    const T v = s * inv;
-    bs[m][q] = v;
-    if (m < 3 && cs[m]) cs[m][q] = v;
-  }
+  restrict_cell(F, Cv, nf, as, bs, cs, I, J, K);
 }
 
-// Kwak prolongation (Sec. 2.7.3, Fig. kwak) of e = uH - uhH (uhH may be
-// null: e = uH), added into the fine field u.  Each fine cell takes its
-// parent and, per dimension, the parent's face neighbour on its side:
-// 2D 1/4 (2 e_c + e_x + e_y), 3D 1/4 (e_c + e_x + e_y + e_z).
+// Kwak prolongation (Sec. 2.7.3, Fig. kwak) of e = uH - uhH, added into u.
 template <typename T>
 __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, const T* __restrict__ uH,
                           const T* __restrict__ uhH, int comp) {
@@ -288,175 +458,10 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, co
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
   if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
-  const int I = i >> 1, J = j >> 1, K = F.three ? (k >> 1) : 0;
-  const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
-  const T ec = coarse_corr(Cv, uH, uhH, comp, I, J, K);
-  const T ex = coarse_corr(Cv, uH, uhH, comp, I + si, J, K);
-  const T ey = coarse_corr(Cv, uH, uhH, comp, I, J + sj, K);
-  T add;
-  if (F.three) {
-    const T ez = coarse_corr(Cv, uH, uhH, comp, I, J, K + sk);
-    add = T(0.25) * (ec + ex + ey + ez);
-  } else {
-    add = T(0.25) * (T(2) * ec + ex + ey);
-  }
-  u[F.idx(i, j, k)] += add;
+  prolong_cell(F, Cv, u, uH, uhH, comp, i, j, k);
 }
 
 // --------------------------------------------------------- coarsest grid
-
-constexpr int COARSE_INV_MAX = 1024;      // scalar cells with a cached inverse diagonal
-constexpr int COARSE_VEC_INV_MAX = 256;   // vector cells with cached inverse diagonals
-
-// Newton-Gauss-Seidel as the coarsest-grid solver (Sec. 2.7.2): one block
-// sweeps until the max residual falls below 1e-12 of its initial value or
-// max_sweeps sweeps.  The bodies work on any address space: the kernels
-// below run them on shared-memory copies of the level when it fits.
-template <typename T, int G, int KIND>
-__device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, const T* __restrict__ f,
-                                   const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps) {
-  __shared__ double red[32];
-  __shared__ double r0s;
-  const long n = (long)L.n0 * L.n1 * L.n2;
-  const int tid = threadIdx.x;
-  auto resmax = [&]() -> double {
-    double m = 0.0;
-    for (long q = tid; q < n; q += blockDim.x) {
-      int i, j, k;
-    L.cell(q, i, j, k);
-      const long p = L.idx(i, j, k);
-      T D;
-      const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
-      const double rv = fabs((double)((f ? f[p] : T(0)) - Lu));
-      m = (rv > m || rv != rv) ? rv : m;
-    }
-    m = warp_max(m);
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    double b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
-    __syncthreads();
-    return b;
-  };
-  const double r0 = resmax();
-  if (tid == 0) r0s = r0;
-  __syncthreads();
-  if (!(r0s > 0.0)) return;
-  // linear equations: the Newton diagonal is fixed, invert it once
-  __shared__ T invd[COARSE_INV_MAX];
-  const bool use_inv = KIND == EQ_LIN && n <= COARSE_INV_MAX;
-  if (use_inv) {
-    for (long q = tid; q < n; q += blockDim.x) {
-      int i, j, k;
-      L.cell(q, i, j, k);
-      T D;
-      lap_scalar<T, G>(L, u, i, j, k, L.idx(i, j, k), D);
-      if (s1) D -= s1[L.idx(i, j, k)];
-      invd[q] = T(1) / D;
-    }
-    __syncthreads();
-  }
-  for (int it = 0; it < max_sweeps; ++it) {
-    for (int colour = 0; colour < 2; ++colour) {
-      const long nh = n / 2;
-      for (long q = tid; q < nh; q += blockDim.x) {
-        const int t = (int)(q % (L.n0 / 2)), j = (int)((q / (L.n0 / 2)) % L.n1),
-                  k = (int)(q / ((long)(L.n0 / 2) * L.n1));
-        const int i = 2 * t + ((j + k + colour) & 1);
-        if (use_inv)
-          scalar_update_lin_inv<T, G>(L, u, f, s1, invd[i + (long)L.n0 * (j + (long)L.n1 * k)], i, j, k);
-        else
-          scalar_update<T, G, KIND>(L, u, f, s0, s1, i, j, k);
-      }
-      __syncthreads();
-    }
-    const double r = resmax();
-    if (!(r > 1e-12 * r0s)) break;
-  }
-}
-
-template <typename T, int G>
-__device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
-                                const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
-                                int max_sweeps) {
-  __shared__ double red[32];
-  __shared__ double r0s;
-  const long n = (long)L.n0 * L.n1 * L.n2;
-  const long ng = ghost_count(L);
-  const int tid = threadIdx.x;
-  T* V[3] = {A, B, C};
-  const T* fs[3] = {f0, f1, f2};
-  auto fill = [&](int c) {
-    for (long g = tid; g < ng; g += blockDim.x) fill_one_ghost(L, V[c], c, g);
-    __syncthreads();
-  };
-  auto resmax = [&]() -> double {
-    double m = 0.0;
-    for (long q = tid; q < n; q += blockDim.x) {
-      int i, j, k;
-    L.cell(q, i, j, k);
-      const long p = L.idx(i, j, k);
-      for (int c = 0; c < 3; ++c) {
-        T D;
-        const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
-        const double rv = fabs((double)((fs[c] ? fs[c][p] : T(0)) - Lu));
-        m = (rv > m || rv != rv) ? rv : m;
-      }
-    }
-    m = warp_max(m);
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    double b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
-    __syncthreads();
-    return b;
-  };
-  for (int c = 0; c < 3; ++c) fill(c);
-  const double r0 = resmax();
-  if (tid == 0) r0s = r0;
-  __syncthreads();
-  if (!(r0s > 0.0)) return;
-  // the Newton diagonal of each component is fixed: invert it once
-  __shared__ T invd[3 * COARSE_VEC_INV_MAX];
-  const bool use_inv = n <= COARSE_VEC_INV_MAX;
-  if (use_inv) {
-    for (long q = tid; q < n; q += blockDim.x) {
-      int i, j, k;
-      L.cell(q, i, j, k);
-      for (int c = 0; c < 3; ++c) {
-        T D;
-        vec_op<T, G>(L, A, B, C, c, i, j, L.idx(i, j, k), D);
-        invd[c * COARSE_VEC_INV_MAX + q] = T(1) / D;
-      }
-    }
-    __syncthreads();
-  }
-  for (int it = 0; it < max_sweeps; ++it) {
-    for (int colour = 0; colour < 2; ++colour)
-      for (int c = 0; c < 3; ++c) {
-        const long nh = n / 2;
-        for (long q = tid; q < nh; q += blockDim.x) {
-          const int t = (int)(q % (L.n0 / 2)), j = (int)((q / (L.n0 / 2)) % L.n1),
-                    k = (int)(q / ((long)(L.n0 / 2) * L.n1));
-          const int i = 2 * t + ((j + k + colour) & 1);
-          if (use_inv) {
-            const long p = L.idx(i, j, k);
-            T D;
-            const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
-            T* Vc = V[c];
-            const T fv = fs[c] ? fs[c][p] : T(0);
-            Vc[p] = Vc[p] - (Lu - fv) * invd[c * COARSE_VEC_INV_MAX + i + (long)L.n0 * (j + (long)L.n1 * k)];
-          } else {
-            vec_update<T, G>(L, A, B, C, fs[c], c, i, j, k);
-          }
-        }
-        __syncthreads();
-        fill(c);
-      }
-    const double r = resmax();
-    if (!(r > 1e-12 * r0s)) break;
-  }
-}
 
 // Block copies between global and shared memory (all ghosted cells).
 template <typename T>
@@ -520,41 +525,99 @@ __global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
 // ------------------------------------------------------------- helpers
 
 // u -= mean(u interior); sums in a fixed order (deterministic).
+// Elementwise passes over the interior in groups of four consecutive cells
+// of a row: rows start 16-byte aligned and n0 (a power of two) is a
+// multiple of 4 on every level but the smallest, which take one cell at a
+// time.  Values travel as doubles (exact for both storage types).
 template <typename T>
-__global__ void k_partial_sum(LevelView<T> L, const T* __restrict__ u, double* __restrict__ part) {
+__device__ __forceinline__ long group4(const LevelView<T>& L, long q) {
+  const int i = (int)(q & ((L.n0 >> 2) - 1)) << 2;
+  const long jk = q >> (L.ln0 - 2);
+  return L.idx(i, (int)(jk & (L.n1 - 1)), (int)(jk >> L.ln1));
+}
+__device__ __forceinline__ void ld4(const float* p, double (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const double (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+template <typename T>
+__device__ __forceinline__ long interior_p(const LevelView<T>& L, long q) {
+  int i, j, k;
+  L.cell(q, i, j, k);
+  return L.idx(i, j, k);
+}
+
+// Sum of a block's doubles into part[blockIdx.x] (fixed order).
+__device__ __forceinline__ void block_sum_to(double s, double* part) {
   __shared__ double sm[32];
-  const long n = (long)L.n0 * L.n1 * L.n2;
-  double s = 0.0;
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    L.cell(q, i, j, k);
-    s += (double)u[L.idx(i, j, k)];
-  }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b += sm[w];
-    part[blockIdx.x] = b;
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x + 31) / 32 ? sm[threadIdx.x] : 0.0;
+    b = warp_sum(b);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
   }
+}
+
+// Mean of the interior from nparts partial sums (warp 0 of every block).
+__device__ __forceinline__ double mean_of(const double* __restrict__ part, int nparts, double ncells) {
+  __shared__ double mean;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += 32) s += part[b];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) mean = s / ncells;
+  }
+  __syncthreads();
+  return mean;
+}
+
+template <typename T>
+__global__ void k_partial_sum(LevelView<T> L, const T* __restrict__ u, double* __restrict__ part) {
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  const long stride = (long)gridDim.x * blockDim.x;
+  double s = 0.0;
+  if (L.n0 >= 4) {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n / 4; q += stride) {
+      double v[4];
+      ld4(u + group4(L, q), v);
+      s += (v[0] + v[1]) + (v[2] + v[3]);
+    }
+  } else {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += stride) s += (double)u[interior_p(L, q)];
+  }
+  block_sum_to(s, part);
 }
 
 template <typename T>
 __global__ void k_sub_mean(LevelView<T> L, T* __restrict__ u, const double* __restrict__ part, int nparts) {
-  __shared__ double mean;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[b];
-    mean = s / ((double)L.n0 * L.n1 * L.n2);
-  }
-  __syncthreads();
   const long n = (long)L.n0 * L.n1 * L.n2;
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    L.cell(q, i, j, k);
-    const long p = L.idx(i, j, k);
-    u[p] = (T)((double)u[p] - mean);
+  const double mean = mean_of(part, nparts, (double)n);
+  const long stride = (long)gridDim.x * blockDim.x;
+  if (L.n0 >= 4) {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n / 4; q += stride) {
+      const long p = group4(L, q);
+      double v[4];
+      ld4(u + p, v);
+      for (int t = 0; t < 4; ++t) v[t] -= mean;
+      st4(u + p, v);
+    }
+  } else {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += stride) {
+      const long p = interior_p(L, q);
+      u[p] = (T)((double)u[p] - mean);
+    }
   }
 }
 
@@ -581,23 +644,47 @@ __global__ void k_copy_out(LevelView<A> L, const A* __restrict__ src, B* __restr
 template <typename A, typename B>
 __global__ void k_convert(LevelView<A> L, const A* __restrict__ src, B* __restrict__ dst) {
   const long n = (long)L.n0 * L.n1 * L.n2;
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    L.cell(q, i, j, k);
-    const long p = L.idx(i, j, k);
-    dst[p] = (B)src[p];
+  const long stride = (long)gridDim.x * blockDim.x;
+  if (L.n0 >= 4) {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n / 4; q += stride) {
+      const long p = group4(L, q);
+      double v[4];
+      ld4(src + p, v);
+      st4(dst + p, v);
+    }
+  } else {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += stride) {
+      const long p = interior_p(L, q);
+      dst[p] = (B)src[p];
+    }
   }
 }
-// u64 += e32 (interior), the defect-correction update.
+// u64 += e32 (interior), the defect-correction update; with part non-null
+// also the block sums of the updated u (for the Neumann gauge).
 template <typename T>
-__global__ void k_add_correction(LevelView<double> L, double* __restrict__ u, const T* __restrict__ e) {
+__global__ void k_add_correction(LevelView<double> L, double* __restrict__ u, const T* __restrict__ e,
+                                 double* __restrict__ part) {
   const long n = (long)L.n0 * L.n1 * L.n2;
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    L.cell(q, i, j, k);
-    const long p = L.idx(i, j, k);
-    u[p] += (double)e[p];
+  const long stride = (long)gridDim.x * blockDim.x;
+  double s = 0.0;
+  if (L.n0 >= 4) {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n / 4; q += stride) {
+      const long p = group4(L, q);
+      double a[4], b[4];
+      ld4(u + p, a);
+      ld4(e + p, b);
+      for (int t = 0; t < 4; ++t) a[t] += b[t];
+      st4(u + p, a);
+      s += (a[0] + a[1]) + (a[2] + a[3]);
+    }
+  } else {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += stride) {
+      const long p = interior_p(L, q);
+      u[p] += (double)e[p];
+      s += u[p];
+    }
   }
+  if (part) block_sum_to(s, part);
 }
 
 // ======================================================== host launchers
@@ -632,23 +719,94 @@ void launch_smooth_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
                     else k_smooth_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, colour));
 }
 
-template <typename T>
+template <typename T, int TX>
 size_t fused_sweep_smem(bool with_c) {
-  return sizeof(T) * (size_t)FS_N * (with_c ? 3 : 2);
+  return sizeof(T) * (size_t)RbShape<TX>::BP * (RB_NU + RB_NF * (with_c ? 2 : 1));
+}
+
+// Column width of the one-launch sweep: 128 cells for FP32 levels at least
+// that wide (fewer instructions per cell), else 64.
+template <typename T>
+int fused_sweep_tx(const LevelView<T>& L) {
+  return (sizeof(T) == 4 && L.n0 >= 128) ? 128 : 64;
+}
+
+// Blocks of k_sweep_rb_cart resident on the whole device, [TX == 128][with
+// c], set when a hierarchy is created (outside any stream capture).
+template <typename T>
+struct FusedCapacity {
+  static int blocks[2][2];
+};
+template <typename T>
+int FusedCapacity<T>::blocks[2][2] = {{1, 1}, {1, 1}};
+
+template <typename T, int TX, bool HAS_C>
+static void set_fused_capacity(int sms) {
+  const size_t smem = fused_sweep_smem<T, TX>(HAS_C);
+  cudaFuncSetAttribute(k_sweep_rb_cart<T, TX, HAS_C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_rb_cart<T, TX, HAS_C>, RB_THREADS, smem) !=
+          cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  FusedCapacity<T>::blocks[TX == 128][HAS_C] = nb * sms;
 }
 
 template <typename T>
 void init_fused_sweep_attributes() {
-  cudaFuncSetAttribute(k_sweep_fused_cart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)fused_sweep_smem<T>(true));
+  int d = 0, sms = 0;
+  cudaGetDevice(&d);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms < 1) sms = 1;
+  set_fused_capacity<T, 64, false>(sms);
+  set_fused_capacity<T, 64, true>(sms);
+  if constexpr (sizeof(T) == 4) {
+    set_fused_capacity<T, 128, false>(sms);
+    set_fused_capacity<T, 128, true>(sms);
+  }
+}
+
+// Planes per block: each block re-relaxes two red planes beyond its chunk,
+// and blocks beyond one device-full run in further waves; take the chunk
+// length with the fewest plane steps per SM slot.
+template <typename T>
+int fused_sweep_chunk(const LevelView<T>& L, int tx, bool with_c) {
+  const long cols = (long)cdiv(L.n0, tx) * cdiv(L.n1, RB_TY);
+  const long cap = FusedCapacity<T>::blocks[tx == 128][with_c];
+  int best = 8;
+  long best_cost = -1;
+  for (int zc = 4; zc <= 64; zc *= 2) {
+    const long blocks = cols * (long)cdiv(L.n2, zc);
+    const long cost = ((blocks + cap - 1) / cap) * (2L * (zc < L.n2 ? zc : L.n2) + 5);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  return best;
+}
+
+template <typename T, int TX>
+static void launch_rb(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
+  const int zc = fused_sweep_chunk(L, TX, c != nullptr);
+  dim3 g(cdiv(L.n0, TX), cdiv(L.n1, RB_TY), cdiv(L.n2, zc));
+  if (c)
+    k_sweep_rb_cart<T, TX, true><<<g, RB_THREADS, fused_sweep_smem<T, TX>(true), st>>>(L, uin, uout, f, c, zc);
+  else
+    k_sweep_rb_cart<T, TX, false><<<g, RB_THREADS, fused_sweep_smem<T, TX>(false), st>>>(L, uin, uout, f, nullptr,
+                                                                                         zc);
 }
 
 template <typename T>
-bool launch_sweep_fused(const LevelView<T>& L, T* u, const T* f, const T* c, cudaStream_t st) {
-  if (L.geom != CART || !L.three || L.n0 < FT_X || L.n1 < FT_Y || L.n2 < FT_Z) return false;
+bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
+  if (!fused_sweep_applies(L)) return false;
   count_launch();
-  dim3 g(cdiv(L.n0, FT_X), cdiv(L.n1, FT_Y), cdiv(L.n2, FT_Z));
-  k_sweep_fused_cart<T><<<g, 256, fused_sweep_smem<T>(c != nullptr), st>>>(L, u, f, c);
+  if constexpr (sizeof(T) == 4) {
+    if (fused_sweep_tx(L) == 128) {
+      launch_rb<T, 128>(L, uin, uout, f, c, st);
+      return true;
+    }
+  }
+  launch_rb<T, 64>(L, uin, uout, f, c, st);
   return true;
 }
 
@@ -669,19 +827,24 @@ void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int
 
 template <typename T>
 void launch_residual_scalar(const LevelView<T>& L, int kind, const T* u, const T* f, const T* s0,
-                            const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st) {
+                            const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st, float* r32) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_cells(L, b);
-  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_residual_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, r, red, weighted);
-                    else k_residual_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, r, red, weighted));
+  g.z = cdiv(L.n2, (long)b.z * RES_KZ);
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_residual_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, red, weighted);
+                    else k_residual_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, red, weighted));
 }
 
 template <typename T>
 void launch_residual_vec(const LevelView<T>& L, T* const V[3], const T* const f[3], T* const r[3],
-                         unsigned long long* red, int weighted, cudaStream_t st) {
+                         unsigned long long* red, int weighted, cudaStream_t st, float* const r32[3]) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_cells(L, b);
-  GMG_GEOM_DISPATCH(L.geom, k_residual_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], r[0], r[1], r[2], red, weighted));
+  g.z = cdiv(L.n2, (long)b.z * RES_KZ);
+  float* q[3] = {nullptr, nullptr, nullptr};
+  if (r32)
+    for (int c = 0; c < 3; ++c) q[c] = r32[c];
+  GMG_GEOM_DISPATCH(L.geom, k_residual_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], r[0], r[1], r[2], q[0], q[1], q[2], red, weighted));
 }
 
 template <typename T>
@@ -755,9 +918,9 @@ void launch_coarse_vec(const LevelView<T>& L, T* V[3], const T* const f[3], int 
 }
 
 template <typename T>
-void launch_sub_mean(const LevelView<T>& L, T* u, double* part, int nparts, cudaStream_t st) {
-  count_launch(2);
-  k_partial_sum<T><<<nparts, 256, 0, st>>>(L, u, part);
+void launch_sub_mean(const LevelView<T>& L, T* u, double* part, int nparts, cudaStream_t st, bool have_part) {
+  count_launch(have_part ? 1 : 2);
+  if (!have_part) k_partial_sum<T><<<nparts, 256, 0, st>>>(L, u, part);
   k_sub_mean<T><<<nparts, 256, 0, st>>>(L, u, part, nparts);
 }
 
@@ -777,27 +940,29 @@ template <typename A, typename B>
 void launch_convert(const LevelView<A>& L, const A* src, B* dst, cudaStream_t st) {
   count_launch();
   long n = (long)L.n0 * L.n1 * L.n2;
-  k_convert<A, B><<<grid_flat(n, 256), 256, 0, st>>>(L, src, dst);
+  k_convert<A, B><<<grid_flat(L.n0 >= 4 ? n / 4 : n, 256), 256, 0, st>>>(L, src, dst);
 }
 template <typename T>
-void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st) {
+void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st, double* part,
+                           int nparts) {
   count_launch();
   long n = (long)L.n0 * L.n1 * L.n2;
-  k_add_correction<T><<<grid_flat(n, 256), 256, 0, st>>>(L, u, e);
+  const unsigned g = part ? (unsigned)nparts : grid_flat(L.n0 >= 4 ? n / 4 : n, 256);
+  k_add_correction<T><<<g, 256, 0, st>>>(L, u, e, part);
 }
 
 // explicit instantiations
 #define GMG_INST(T)                                                                                            \
-  template bool launch_sweep_fused<T>(const LevelView<T>&, T*, const T*, const T*, cudaStream_t);              \
+  template bool launch_sweep_fused<T>(const LevelView<T>&, const T*, T*, const T*, const T*, cudaStream_t);    \
   template void init_fused_sweep_attributes<T>();                                                              \
   template void launch_smooth_scalar<T>(const LevelView<T>&, int, T*, const T*, const T*, const T*, int,       \
                                         cudaStream_t);                                                          \
   template void launch_fill_ghosts<T>(const LevelView<T>&, T*, int, cudaStream_t);                             \
   template void launch_smooth_vec<T>(const LevelView<T>&, T* [3], const T*, int, int, cudaStream_t);           \
   template void launch_residual_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, const T*, T*, \
-                                          unsigned long long*, int, cudaStream_t);                              \
+                                          unsigned long long*, int, cudaStream_t, float*);                      \
   template void launch_residual_vec<T>(const LevelView<T>&, T* const[3], const T* const[3], T* const[3],       \
-                                       unsigned long long*, int, cudaStream_t);                                 \
+                                       unsigned long long*, int, cudaStream_t, float* const[3]);                \
   template void launch_apply_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*, int,        \
                                        cudaStream_t);                                                           \
   template void launch_apply_vec<T>(const LevelView<T>&, T* const[3], T* const[3], int, cudaStream_t);         \
@@ -808,13 +973,14 @@ void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cu
   template void launch_coarse_scalar<T>(const LevelView<T>&, int, T*, const T*, const T*, const T*, int,       \
                                         cudaStream_t);                                                          \
   template void launch_coarse_vec<T>(const LevelView<T>&, T* [3], const T* const[3], int, cudaStream_t);       \
-  template void launch_sub_mean<T>(const LevelView<T>&, T*, double*, int, cudaStream_t);
+  template void launch_sub_mean<T>(const LevelView<T>&, T*, double*, int, cudaStream_t, bool);
 GMG_INST(double)
 GMG_INST(float)
 template void launch_copy_in<double, double>(const LevelView<double>&, const double*, double*, double, cudaStream_t);
 template void launch_copy_out<double, double>(const LevelView<double>&, const double*, double*, double, cudaStream_t);
 template void launch_convert<double, float>(const LevelView<double>&, const double*, float*, cudaStream_t);
 template void launch_convert<float, double>(const LevelView<float>&, const float*, double*, cudaStream_t);
-template void launch_add_correction<float>(const LevelView<double>&, double*, const float*, cudaStream_t);
+template void launch_add_correction<float>(const LevelView<double>&, double*, const float*, cudaStream_t, double*,
+                                           int);
 
 }  // namespace gmg

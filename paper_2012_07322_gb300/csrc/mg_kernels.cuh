@@ -119,32 +119,31 @@ __device__ __forceinline__ long ghost_count(const LevelView<T>& L) {
   return 2L * (L.n1 + 2) * nk + 2L * L.n0 * nk + (L.three ? 2L * L.n0 * L.n1 : 0L);
 }
 template <typename T>
-__device__ __forceinline__ void ghost_coords(const LevelView<T>& L, long g, int& i, int& j, int& k) {
-  const long nk = L.n2 + 2 * L.three;
-  const long a = 2L * (L.n1 + 2) * nk;
+__device__ __forceinline__ void ghost_coords(const LevelView<T>& L, long gl, int& i, int& j, int& k) {
+  // 32-bit arithmetic: a level's ghost count is far below 2^31
+  int g = (int)gl;
+  const int nk = L.n2 + 2 * L.three;
+  const int a = 2 * (L.n1 + 2) * nk;
   if (g < a) {
-    int side = (int)(g % 2);
-    long q = g / 2;
-    j = (int)(q % (L.n1 + 2)) - 1;
-    k = (int)(q / (L.n1 + 2)) - L.three;
+    const int side = g & 1, q = g >> 1;
+    j = q % (L.n1 + 2) - 1;
+    k = q / (L.n1 + 2) - L.three;
     i = side ? L.n0 : -1;
     return;
   }
   g -= a;
-  const long b = 2L * L.n0 * nk;
+  const int b = 2 * L.n0 * nk;
   if (g < b) {
-    int side = (int)(g % 2);
-    long q = g / 2;
-    i = (int)(q % L.n0);
-    k = (int)(q / L.n0) - L.three;
+    const int side = g & 1, q = g >> 1;
+    i = q & (L.n0 - 1);
+    k = (q >> L.ln0) - L.three;
     j = side ? L.n1 : -1;
     return;
   }
   g -= b;
-  int side = (int)(g % 2);
-  long q = g / 2;
-  i = (int)(q % L.n0);
-  j = (int)(q / L.n0);
+  const int side = g & 1, q = g >> 1;
+  i = q & (L.n0 - 1);
+  j = q >> L.ln0;
   k = side ? L.n2 : -1;
 }
 
@@ -171,6 +170,253 @@ __device__ __forceinline__ T coarse_corr(const LevelView<T>& C, const T* __restr
   const long q = C.idx(I, J, K);
   const T e = uhH ? (uH[q] - uhH[q]) : uH[q];
   return f * e;
+}
+
+// Residual f - L(u) of a scalar equation at an interior cell; Sv gets the
+// source S(u) as the paper writes the right-hand side (L(u) = lap u - S(u)
+// for eq. psi; lap u - c u with S = f + c u for linear equations).
+template <typename T, int G, int KIND>
+__device__ __forceinline__ T scalar_residual_cell(const LevelView<T>& L, const T* __restrict__ u,
+                                                  const T* __restrict__ f, const T* __restrict__ s0,
+                                                  const T* __restrict__ s1, int i, int j, int k, long p, T& Sv) {
+  T D;
+  const T lap = lap_scalar<T, G>(L, u, i, j, k, p, D);
+  const T fv = f ? f[p] : T(0);
+  T Lu;
+  if (KIND == EQ_PSI) {
+    const T ip = T(1) / (T(1) + u[p]);
+    const T ip2 = ip * ip;
+    const T ip7 = ip2 * ip2 * ip2 * ip;
+    Sv = -T(2 * PI_D) * s0[p] * ip - T(0.125) * s1[p] * ip7;
+    Lu = lap - Sv;
+  } else if (s1) {
+    const T cu = s1[p] * u[p];
+    Lu = lap - cu;
+    Sv = fv + cu;
+  } else {
+    Lu = lap;
+    Sv = fv;
+  }
+  return fv - Lu;
+}
+
+// Residual f_c - (lap V + 1/3 grad div V)_c of a vector equation (ghosts
+// current).
+template <typename T, int G>
+__device__ __forceinline__ T vec_residual_cell(const LevelView<T>& L, const T* __restrict__ A,
+                                               const T* __restrict__ B, const T* __restrict__ C,
+                                               const T* __restrict__ f, int c, int i, int j, long p) {
+  T D;
+  const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+  const T fv = f ? f[p] : T(0);
+  return fv - Lu;
+}
+
+// Volume-weighted piecewise-constant restriction (Sec. 2.7.3, weights
+// Delta V of the fine cells) of nf fields a[m] into b[m] at coarse cell
+// (I, J, K); copies into cs[m] too when non-null.
+template <typename T>
+__device__ __forceinline__ void restrict_cell(const LevelView<T>& F, const LevelView<T>& Cv, int nf,
+                                              const T* const (&as)[4], T* const (&bs)[4], T* const (&cs)[3],
+                                              int I, int J, int K) {
+  T wi[2], wj[2];
+  wi[0] = F.TI(TI_VW, 2 * I);
+  wi[1] = F.TI(TI_VW, 2 * I + 1);
+  wj[0] = F.TJ(TJ_VW, 2 * J);
+  wj[1] = F.TJ(TJ_VW, 2 * J + 1);
+  T wsum = T(0);
+  const int nk = F.three ? 2 : 1;
+  for (int dk = 0; dk < nk; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) wsum += wi[di] * wj[dj];
+  const T inv = T(1) / wsum;
+  const long q = Cv.idx(I, J, K);
+  for (int m = 0; m < nf; ++m) {
+    T s = T(0);
+    for (int dk = 0; dk < nk; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di)
+          s += wi[di] * wj[dj] * as[m][F.idx(2 * I + di, 2 * J + dj, F.three ? 2 * K + dk : 0)];
+    const T v = s * inv;
+    bs[m][q] = v;
+    if (m < 3 && cs[m]) cs[m][q] = v;
+  }
+}
+
+// Kwak prolongation (Sec. 2.7.3, Fig. kwak) of e = uH - uhH (uhH may be
+// null: e = uH) into fine cell (i, j, k): the parent and, per dimension,
+// the parent's face neighbour on the cell's side;
+// 2D 1/4 (2 e_c + e_x + e_y), 3D 1/4 (e_c + e_x + e_y + e_z).
+template <typename T>
+__device__ __forceinline__ void prolong_cell(const LevelView<T>& F, const LevelView<T>& Cv, T* __restrict__ u,
+                                             const T* __restrict__ uH, const T* __restrict__ uhH, int comp, int i,
+                                             int j, int k) {
+  const int I = i >> 1, J = j >> 1, K = F.three ? (k >> 1) : 0;
+  const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
+  const T ec = coarse_corr(Cv, uH, uhH, comp, I, J, K);
+  const T ex = coarse_corr(Cv, uH, uhH, comp, I + si, J, K);
+  const T ey = coarse_corr(Cv, uH, uhH, comp, I, J + sj, K);
+  T add;
+  if (F.three) {
+    const T ez = coarse_corr(Cv, uH, uhH, comp, I, J, K + sk);
+    add = T(0.25) * (ec + ex + ey + ez);
+  } else {
+    add = T(0.25) * (T(2) * ec + ex + ey);
+  }
+  u[F.idx(i, j, k)] += add;
+}
+
+// ----------------------------------------------------------- coarsest grid
+
+constexpr int COARSE_INV_MAX = 1024;      // scalar cells with a cached inverse diagonal
+constexpr int COARSE_VEC_INV_MAX = 256;   // vector cells with cached inverse diagonals
+
+// Newton-Gauss-Seidel as the coarsest-grid solver (Sec. 2.7.2): one block
+// sweeps until the max residual falls below 1e-12 of its initial value or
+// max_sweeps sweeps.  The bodies work on any address space: the kernels
+// below run them on shared-memory copies of the level when it fits.
+template <typename T, int G, int KIND>
+__device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, const T* __restrict__ f,
+                                   const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps) {
+  __shared__ double red[32];
+  __shared__ double r0s;
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  const int tid = threadIdx.x;
+  auto resmax = [&]() -> double {
+    double m = 0.0;
+    for (long q = tid; q < n; q += blockDim.x) {
+      int i, j, k;
+    L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      T D;
+      const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
+      const double rv = fabs((double)((f ? f[p] : T(0)) - Lu));
+      m = (rv > m || rv != rv) ? rv : m;
+    }
+    m = warp_max(m);
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
+    __syncthreads();
+    return b;
+  };
+  const double r0 = resmax();
+  if (tid == 0) r0s = r0;
+  __syncthreads();
+  if (!(r0s > 0.0)) return;
+  // linear equations: the Newton diagonal is fixed, invert it once
+  __shared__ T invd[COARSE_INV_MAX];
+  const bool use_inv = KIND == EQ_LIN && n <= COARSE_INV_MAX;
+  if (use_inv) {
+    for (long q = tid; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      T D;
+      lap_scalar<T, G>(L, u, i, j, k, L.idx(i, j, k), D);
+      if (s1) D -= s1[L.idx(i, j, k)];
+      invd[q] = T(1) / D;
+    }
+    __syncthreads();
+  }
+  for (int it = 0; it < max_sweeps; ++it) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const long nh = n / 2;
+      for (long q = tid; q < nh; q += blockDim.x) {
+        int i, j, k;
+        L.colour_cell(q, colour, i, j, k);
+        if (use_inv)
+          scalar_update_lin_inv<T, G>(L, u, f, s1, invd[i + (long)L.n0 * (j + (long)L.n1 * k)], i, j, k);
+        else
+          scalar_update<T, G, KIND>(L, u, f, s0, s1, i, j, k);
+      }
+      __syncthreads();
+    }
+    const double r = resmax();
+    if (!(r > 1e-12 * r0s)) break;
+  }
+}
+
+template <typename T, int G>
+__device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
+                                const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
+                                int max_sweeps) {
+  __shared__ double red[32];
+  __shared__ double r0s;
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  const long ng = ghost_count(L);
+  const int tid = threadIdx.x;
+  T* V[3] = {A, B, C};
+  const T* fs[3] = {f0, f1, f2};
+  auto fill = [&](int c) {
+    for (long g = tid; g < ng; g += blockDim.x) fill_one_ghost(L, V[c], c, g);
+    __syncthreads();
+  };
+  auto resmax = [&]() -> double {
+    double m = 0.0;
+    for (long q = tid; q < n; q += blockDim.x) {
+      int i, j, k;
+    L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      for (int c = 0; c < 3; ++c) {
+        T D;
+        const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+        const double rv = fabs((double)((fs[c] ? fs[c][p] : T(0)) - Lu));
+        m = (rv > m || rv != rv) ? rv : m;
+      }
+    }
+    m = warp_max(m);
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
+    __syncthreads();
+    return b;
+  };
+  for (int c = 0; c < 3; ++c) fill(c);
+  const double r0 = resmax();
+  if (tid == 0) r0s = r0;
+  __syncthreads();
+  if (!(r0s > 0.0)) return;
+  // the Newton diagonal of each component is fixed: invert it once
+  __shared__ T invd[3 * COARSE_VEC_INV_MAX];
+  const bool use_inv = n <= COARSE_VEC_INV_MAX;
+  if (use_inv) {
+    for (long q = tid; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      for (int c = 0; c < 3; ++c) {
+        T D;
+        vec_op<T, G>(L, A, B, C, c, i, j, L.idx(i, j, k), D);
+        invd[c * COARSE_VEC_INV_MAX + q] = T(1) / D;
+      }
+    }
+    __syncthreads();
+  }
+  for (int it = 0; it < max_sweeps; ++it) {
+    for (int colour = 0; colour < 2; ++colour)
+      for (int c = 0; c < 3; ++c) {
+        const long nh = n / 2;
+        for (long q = tid; q < nh; q += blockDim.x) {
+          int i, j, k;
+          L.colour_cell(q, colour, i, j, k);
+          if (use_inv) {
+            const long p = L.idx(i, j, k);
+            T D;
+            const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+            T* Vc = V[c];
+            const T fv = fs[c] ? fs[c][p] : T(0);
+            Vc[p] = Vc[p] - (Lu - fv) * invd[c * COARSE_VEC_INV_MAX + i + (long)L.n0 * (j + (long)L.n1 * k)];
+          } else {
+            vec_update<T, G>(L, A, B, C, fs[c], c, i, j, k);
+          }
+        }
+        __syncthreads();
+        fill(c);
+      }
+    const double r = resmax();
+    if (!(r > 1e-12 * r0s)) break;
+  }
 }
 
 }  // namespace gmg

@@ -2,6 +2,7 @@
 
     python -m paper_2012_07322_gb300.profile_cases divb256   # mixed 256^3 div-B cleaning, twice
     python -m paper_2012_07322_gb300.profile_cases xeq       # 10 mixed cycles of eq. X, 128x64x64
+    python -m paper_2012_07322_gb300.profile_cases xcfc      # one full mixed xCFC solve, 128x64x64
 
 Each case runs through the C ABI and exits 0 on success, so the same command
 can be profiled after it has run once without a profiler.
@@ -39,7 +40,25 @@ def xeq(precision="mixed"):
     print("xeq", precision, rep["status"], rep["cycles"], rep["rel"])
 
 
+def xcfc(precision="mixed"):
+    import torch
+    from . import inputs, mg
+    n = (128, 64, 64)
+    U, S, Si = inputs.rotating_polytrope_sph3d(n, 100.0)
+    h = mg.Hierarchy(mg.grid_desc("sph", list(n), hi=[100.0, np.pi, 2 * np.pi], precision=precision, tol=1e-10,
+                                  max_cycles=400, stall_window=0, accel_depth=16))
+    dev = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (U, S)]
+    Sid = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in Si]
+    psi = torch.ones(U.shape, dtype=torch.float64, device="cuda")
+    alpha = torch.ones_like(psi)
+    beta = [torch.zeros_like(psi) for _ in range(3)]
+    X = [torch.zeros_like(psi) for _ in range(3)]
+    rep = mg.mg_solve_cfc(h, dev[0], dev[1], Sid, psi, alpha, beta, X)
+    h.close()
+    print("xcfc", precision, {k: rep[k]["cycles"] for k in ("X", "psi", "alphapsi", "beta")})
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "divb256"
     prec = sys.argv[2] if len(sys.argv) > 2 else "mixed"
-    {"divb256": divb256, "xeq": xeq}[case](prec)
+    {"divb256": divb256, "xeq": xeq, "xcfc": xcfc}[case](prec)

@@ -305,9 +305,10 @@ def test_xcfc_parity(mg, geom, n, hi, accel):
     assert max(errs.values()) < 1e-9, errs
 
 
-def test_divb_cleaning_parity(mg):
-    """Elliptic divergence cleaning on a 32^3 curl field with noise."""
-    n = 32
+@pytest.mark.parametrize("n", [32, 64])
+def test_divb_cleaning_parity(mg, n):
+    """Elliptic divergence cleaning on a curl field with noise (at 64^3 the
+    finest level relaxes with the one-launch sweep)."""
     B = inputs.divb_field(n=n, n_modes=32, k_max=8)
     d, gd = descs(mg, "cart", [n] * 3, [-1.0] * 3, [1.0] * 3, tol=1e-10, max_cycles=1000)
     Bo = [b.copy() for b in B]
@@ -329,23 +330,36 @@ def test_divb_cleaning_parity(mg):
 # ------------------------------------------------------ mixed precision
 
 
-@pytest.mark.parametrize("accel", [0, 8])
-def test_mixed_precision_xcfc_error_vs_oracle(mg, accel):
+MIXED_CASES = {
+    # the finest level is above the one-block cycle's size: levels 1.. run in one block
+    "sph3d": ("sph", [32, 16, 16], [0, 0, 0], [100.0, PI, 2 * PI]),
+    # the whole correction cycle runs in one block (2048 and 2048 cells)
+    "sph2d": ("sph", [64, 32], [0, 0], [100.0, PI]),
+    "cyl2d": ("cyl", [32, 64], [0.0, -100.0], [100.0, 100.0]),
+}
+
+
+@pytest.mark.parametrize("case,accel", [("sph3d", 0), ("sph3d", 8), ("sph2d", 8), ("cyl2d", 8)])
+def test_mixed_precision_xcfc_error_vs_oracle(mg, case, accel):
     """FP32 smoothing inside FP64 defect correction: every equation reaches
     the FP64 relative residual 1e-10 and every field stays within 1e-8 of
     the FP64 oracle."""
-    n = [32, 16, 16]
-    U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
-    rg, ro, got, want = run_cfc_pair(mg, "sph", n, [0, 0, 0], [100.0, PI, 2 * PI], U, S, Si, precision="mixed",
-                                     accel_depth=accel)
+    geom, n, lo, hi = MIXED_CASES[case]
+    if case == "sph3d":
+        U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
+    elif case == "sph2d":
+        U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], 100.0)
+    else:
+        U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0)
+    rg, ro, got, want = run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="mixed", accel_depth=accel)
     for k in ("X", "psi", "alphapsi", "beta"):
         assert rg[k]["status"] == "ok" and rg[k]["rel"] <= 1e-10
     errs = field_errors(got, want)
     assert max(errs.values()) < 1e-8, errs
 
 
-def test_mixed_precision_divb_error_vs_oracle(mg):
-    n = 32
+@pytest.mark.parametrize("n", [32, 64])
+def test_mixed_precision_divb_error_vs_oracle(mg, n):
     B = inputs.divb_field(n=n)
     d, gd = descs(mg, "cart", [n] * 3, [-1.0] * 3, [1.0] * 3, tol=1e-10, max_cycles=1000, precision="mixed")
     Bo = [b.copy() for b in B]
@@ -362,22 +376,42 @@ def test_mixed_precision_divb_error_vs_oracle(mg):
         assert relerr(host(Bt[k]), Bo[k]) < 1e-8
 
 
+FUSED_CASES = [
+    # (n, sweeps): one 64 x 8 column in x, y with fewer planes than a chunk;
+    # several columns and z-chunks (re-relaxed red planes at chunk edges);
+    # more blocks than fit on the device at once (blocks of a later wave
+    # must still read only the sweep's input)
+    ([64, 8, 4], 2),
+    ([128, 32, 64], 3),
+    ([64, 16, 32], 4),
+    ([256, 128, 64], 2),
+]
+
+
+@pytest.mark.parametrize("case", range(len(FUSED_CASES)))
 @pytest.mark.parametrize("bc", ["robin", "neumann", "dirichlet"])
-def test_fused_sweep_parity(mg, bc):
-    """Cartesian 3D levels of at least one 32x8x8 tile relax both colours in
-    one fused launch; three sweeps equal the oracle's red-black sweeps."""
-    n, lo, hi = [64, 16, 32], [-30.0, -25.0, -20.0], [34.0, 27.0, 31.0]
+def test_fused_sweep_parity(mg, bc, case):
+    """Cartesian 3D levels at least 64 x 8 cells wide relax both colours in
+    one out-of-place launch per sweep (pairs of sweeps; an odd last sweep
+    runs as two colour passes); the result equals the oracle's red-black
+    sweeps, with and without the c u term and the right-hand side."""
+    n, sweeps = FUSED_CASES[case]
+    if n[0] * n[1] * n[2] > 1 << 20 and bc != "robin":
+        pytest.skip("the largest case runs once")
+    lo, hi = [-30.0, -25.0, -20.0], [34.0, 27.0, 31.0]
     d, gd = descs(mg, "cart", n, lo, hi)
     h = mg.Hierarchy(gd)
     shp = o.shape(d)
-    rng = np.random.default_rng(12)
+    rng = np.random.default_rng(12 + case)
     u = rng.uniform(-0.3, 0.3, shp)
     f = rng.uniform(-0.01, 0.01, shp)
     c = rng.uniform(0, 0.05, shp)
-    for cc in (None, c):
-        ug, fg = ghosted(d, u), ghosted(d, f)
-        o.smooth(d, "lin", bc, 3, ug, fg, c=ghosted(d, cc) if cc is not None else None)
+    for ff, cc in ((f, None), (f, c), (None, c)):
+        ug = ghosted(d, u)
+        fg = ghosted(d, ff) if ff is not None else ghosted(d, np.zeros(shp))
+        o.smooth(d, "lin", bc, sweeps, ug, fg, c=ghosted(d, cc) if cc is not None else None)
         ut = dev(u)
-        mg.mg_smooth(h, "lin", bc, 3, ut, f=dev(f), c=dev(cc) if cc is not None else None)
-        assert relerr(host(ut), interior(d, ug)) < 1e-12, (bc, cc is None)
+        mg.mg_smooth(h, "lin", bc, sweeps, ut, f=dev(ff) if ff is not None else None,
+                     c=dev(cc) if cc is not None else None)
+        assert relerr(host(ut), interior(d, ug)) < 1e-12, (bc, ff is None, cc is None)
     h.close()
