@@ -114,10 +114,29 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
     for (long q = threadIdx.x; q < ng; q += blockDim.x) cu[c][q] = 0.0;
   }
   __syncthreads();
-  if (!VEC)
+  if (!VEC) {
     coarse_scalar_body<double, G, EQ_LIN>(L, cu[0], cf[0], nullptr, ck, P.coarse_sweeps);
-  else
+  } else if (P.cinv) {
+    // exact solve with the precomputed inverse of the coarsest operator:
+    // unknown r = c * cells + q (q the interior flat index)
+    __shared__ double fp[BC_CINV_MAX];
+    const int n = P.cn, cells = n / 3;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      int i, j, k;
+      L.cell(r % cells, i, j, k);
+      fp[r] = cf[r / cells][L.idx(i, j, k)];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      double x = 0.0;
+      for (int col = 0; col < n; ++col) x += P.cinv[(long)col * n + r] * fp[col];
+      int i, j, k;
+      L.cell(r % cells, i, j, k);
+      cu[r / cells][L.idx(i, j, k)] = x;
+    }
+  } else {
     coarse_vec_body<double, G>(L, cu[0], cu[1], cu[2], cf[0], cf[1], cf[2], P.coarse_sweeps);
+  }
   __syncthreads();
   for (int c = 0; c < nc; ++c)
     for (long q = threadIdx.x; q < n; q += blockDim.x) {
@@ -190,6 +209,47 @@ __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_cons
   const BcLevel B = bc_level(P, sm, 0);
   for (int c = 0; c < nc; ++c)
     for (long q = threadIdx.x; q < P.ng0; q += blockDim.x) P.e_out[c][q] = B.e[c][q];
+}
+
+// Column col of the coarsest vector operator (lap V + 1/3 grad div V with
+// the level's ghost rules): the operator applied to unit field col, stored
+// in A[col * n + r], unknown r = c * cells + q.  One block per column;
+// scratch holds n fields of 3 ghosted components.
+template <int G>
+__global__ void k_coarse_assemble_vec(LevelView<double> L, double* __restrict__ scratch, double* __restrict__ A,
+                                      int n) {
+  const int col = blockIdx.x, cells = n / 3;
+  const long ng = L.sy * (L.n2 + 2 * L.three);
+  double* U[3];
+  for (int c = 0; c < 3; ++c) U[c] = scratch + ((long)col * 3 + c) * ng;
+  for (long q = threadIdx.x; q < 3 * ng; q += blockDim.x) U[0][q] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int i, j, k;
+    L.cell(col % cells, i, j, k);
+    U[col / cells][L.idx(i, j, k)] = 1.0;
+  }
+  __syncthreads();
+  const long ngh = ghost_count(L);
+  for (int c = 0; c < 3; ++c)
+    for (long g = threadIdx.x; g < ngh; g += blockDim.x) fill_one_ghost(L, U[c], c, g);
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    int i, j, k;
+    L.cell(r % cells, i, j, k);
+    double D;
+    A[(long)col * n + r] = vec_op<double, G>(L, U[0], U[1], U[2], r / cells, i, j, L.idx(i, j, k), D);
+  }
+}
+
+void launch_coarse_assemble_vec(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st) {
+  count_launch();
+  if (L.geom == CART)
+    k_coarse_assemble_vec<CART><<<n, 256, 0, st>>>(L, scratch, A, n);
+  else if (L.geom == CYL)
+    k_coarse_assemble_vec<CYL><<<n, 256, 0, st>>>(L, scratch, A, n);
+  else
+    k_coarse_assemble_vec<SPH><<<n, 256, 0, st>>>(L, scratch, A, n);
 }
 
 template <int G>

@@ -143,6 +143,8 @@ struct BlockCycle32 {
   LevelView<double> c64;  // the coarsest level, boundary rule applied
   int cu[3], cf[3], ck;   // offsets (doubles, from fp64_at) of the FP64 coarsest solve; ck < 0: no c
   long fp64_at;           // byte offset of the FP64 area in shared memory
+  const double* cinv;     // vector equations: inverse of the coarsest operator (transposed), or null
+  int cn;                 // its order (3 x coarsest cells)
   long ng0;               // ghosted size of level l0
   const float* f_in[3];   // level l0 right-hand side in HBM
   float* e_out[3];        // level l0 correction in HBM (written at the end)
@@ -150,5 +152,10 @@ struct BlockCycle32 {
 };
 void launch_block_vcycle32(const BlockCycle32& P, int geom, cudaStream_t st);
 void init_block_cycle_attributes();
+// The largest coarsest vector system solved exactly (3 x cells).
+constexpr int BC_CINV_MAX = 768;
+// Columns of the coarsest vector operator (L with its boundary rule) into
+// A[col * n + r], n = 3 x coarsest cells; scratch holds 3 n ghosted fields.
+void launch_coarse_assemble_vec(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st);
 
 }  // namespace gmg
