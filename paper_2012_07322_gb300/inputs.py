@@ -150,3 +150,24 @@ def random_field(shape, seed, scale=1.0):
     """I.i.d. uniform [-scale, scale) values (operator-level parity tests)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-scale, scale, size=shape)
+
+
+def batch_static_stars_2d(count=512, seed=2):
+    """Uneven batch of 2D axisymmetric static stars (Omega = 0, spherical
+    n = 1 polytropes): half on spherical grids N_r in {32..256} x N_theta in
+    {16..128} (r <= 100), half on cylindrical grids N_R in {32..256} x N_z in
+    {64..512} (R <= 100, |z| <= 100); rho_c ~ U[5e-4, 2e-3], R ~ U[8, 14].
+    Returns (geom, n, lo, hi, U, S, Si) tuples."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        rho_c, R = rng.uniform(5e-4, 2e-3), rng.uniform(8.0, 14.0)
+        if q % 2 == 0:
+            n = [int(rng.choice([32, 64, 128, 256])), int(rng.choice([16, 32, 64, 128]))]
+            U, S, Si = rotating_polytrope_sph2d(n[0], n[1], 100.0, rho_c, R, axis_ratio=1.0, omega=0.0)
+            out.append(("sph", n, [0.0, 0.0], [100.0, np.pi], U, S, Si))
+        else:
+            n = [int(rng.choice([32, 64, 128, 256])), int(rng.choice([64, 128, 256, 512]))]
+            U, S, Si = rotating_polytrope_cyl(n, 100.0, rho_c, R, axis_ratio=1.0, omega=0.0)
+            out.append(("cyl", n, [0.0, -100.0], [100.0, 100.0], U, S, Si))
+    return out

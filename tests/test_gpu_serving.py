@@ -159,3 +159,33 @@ def test_eviction_keeps_results_correct(mg):
     srv.close()
     assert all(r["status"] == "ok" for r in res)
     assert torch.equal(outs[0][0], outs[2][0]) and torch.equal(outs[1][0], outs[3][0])
+
+
+def test_uneven_2d_batch_identical_alone_and_batched(mg):
+    """A batch of uneven 2D static stars (spherical and cylindrical grids of
+    different sizes, mixed precision) through the worker slots: every result
+    is bitwise the one of its own solve."""
+    batch = inputs.batch_static_stars_2d(count=10, seed=5)
+    descs = [mg.grid_desc(g, n, lo, hi, precision="mixed", tol=1e-10, max_cycles=800, accel_depth=8,
+                          stall_window=0) for (g, n, lo, hi, _, _, _) in batch]
+    data = [(dev(U), dev(S), [dev(x) for x in Si]) for (_, _, _, _, U, S, Si) in batch]
+    alone = []
+    for d, (U, S, Si) in zip(descs, data):
+        h = mg.Hierarchy(d)
+        f = fields(U.shape)
+        rep = mg.mg_solve_cfc(h, U, S, Si, *f)
+        h.close()
+        assert rep["psi"]["cycles"] > 0
+        alone.append([f[0], f[1]] + f[2] + f[3])
+    srv = mg.Server(hbm_budget=8 << 30, max_slots=4, max_queue=64)
+    outs, tickets = [], []
+    for d, (U, S, Si) in zip(descs, data):
+        f = fields(U.shape)
+        tickets.append(srv.submit_cfc(d, U, S, Si, *f))
+        outs.append([f[0], f[1]] + f[2] + f[3])
+    res = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert all(r["status"] == "ok" for r in res)
+    for q, (a, b) in enumerate(zip(outs, alone)):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y), q
