@@ -18,7 +18,8 @@
  *   Sec. 2.7.2, eq. (ngs_iteration), red-black ordering -- smoother
  *   Sec. 2.7.3, Kwak prolongation, piecewise-constant restriction
  *   Sec. 2.2, eqs. (poisson), (update_bfield)           -- div-B cleaning
- *   Sec. 4.2 (metric-solver performance): 2 + 2 red-black smoothing steps.
+ *   Sec. 4.2 (metric-solver performance): 2 + 2 red-black smoothing steps,
+ *     full multigrid (FMG) cycles.
  *
  * Readings where the paper is silent or garbled (each listed in the design
  * notes of the repository):
@@ -41,6 +42,10 @@
  *     1e-12 or 16 sweeps (more sweeps leave the V-cycle counts unchanged);
  *   - stopping rule: rel = max|w r| / max|w S(u)|, w = r^2 sin(theta)
  *     (spherical), R (cylindrical), 1 (Cartesian);
+ *   - FMG cycle (the paper times FMG cycles but does not spell one out): the
+ *     textbook FAS form -- restrict the current solution and FAS sources to
+ *     every level, solve the coarsest, then per level up: FAS correction from
+ *     below and one V-cycle from that level;
  *   - optional Anderson mixing of successive V-cycle iterates (not in the
  *     paper; off when accel_depth = 0): point smoothing converges slowly on
  *     spherical grids (the paper notes it), mixing restores the rate.
@@ -386,7 +391,7 @@ typedef struct {
 
 typedef struct {
   int kind, bc, ncomp, mixed, zero_mean;
-  int nu1, nu2, max_cycles, stall_window, accel;
+  int nu1, nu2, max_cycles, stall_window, accel, fmg;
   double tol;
   int nlev;
   OLevel lev[OR_MAX_LEVELS];
@@ -571,17 +576,11 @@ static void coarse_solve(const OSolver* s, OLevel* L) {
   }
 }
 
-/* FAS V(nu1, nu2) cycle (the paper cites the FAS scheme of Cheong et al.):
- *   pre-smooth; r = f - L(u); u_H = R u, uh_H = u_H; f_H = L_H(u_H) + R r;
- *   recurse; u += P(u_H - uh_H); post-smooth. */
-static void vcycle(const OSolver* s, OSolver* sm, int l) {
+/* FAS restriction from level l to l + 1 at the current u_l:
+ *   r = f - L(u); u_H = R u, uh_H = u_H; f_H = L_H(u_H) + R r. */
+static void fas_down(const OSolver* s, OSolver* sm, int l) {
   OLevel* L = &sm->lev[l];
-  if (l == s->nlev - 1) {
-    coarse_solve(s, L);
-    return;
-  }
   OLevel* C = &sm->lev[l + 1];
-  for (int it = 0; it < s->nu1; ++it) smooth_sweep(s, L);
   residual(s, L);
   for (int c = 0; c < s->ncomp; ++c) {
     restrict_field(&L->g, L->u[c], &C->g, C->u[c]);
@@ -596,15 +595,48 @@ static void vcycle(const OSolver* s, OSolver* sm, int l) {
           long p = IX(&C->g, i, j, k);
           C->f[c][p] = op_at(s, C, c, i, j, k, NULL) + C->r[c][p];
         }
-  vcycle(s, sm, l + 1);
+}
+
+/* FAS correction of level l from level l + 1: u += P(u_H - uh_H), the
+ * coarse change taking the homogeneous boundary ghosts. */
+static void fas_up(const OSolver* s, OSolver* sm, int l) {
+  OLevel* L = &sm->lev[l];
+  OLevel* C = &sm->lev[l + 1];
   for (int c = 0; c < s->ncomp; ++c) {
-    /* coarse correction e = u_H - uh_H with homogeneous boundary ghosts */
     double* e = C->r[c];
     for (long p = 0; p < C->g.size; ++p) e[p] = C->u[c][p] - C->uh[c][p];
     fill_ghosts(&C->g, e, s->bc, comp_of(s, c));
     prolong_add(&L->g, L->u[c], &C->g, e);
   }
+}
+
+/* FAS V(nu1, nu2) cycle (the paper cites the FAS scheme of Cheong et al.):
+ *   pre-smooth; restrict (fas_down); recurse; correct (fas_up); post-smooth. */
+static void vcycle(const OSolver* s, OSolver* sm, int l) {
+  OLevel* L = &sm->lev[l];
+  if (l == s->nlev - 1) {
+    coarse_solve(s, L);
+    return;
+  }
+  for (int it = 0; it < s->nu1; ++it) smooth_sweep(s, L);
+  fas_down(s, sm, l);
+  vcycle(s, sm, l + 1);
+  fas_up(s, sm, l);
   for (int it = 0; it < s->nu2; ++it) smooth_sweep(s, L);
+}
+
+/* Full multigrid (FMG) cycle in FAS form, the cycle the paper times in its
+ * solver-performance tests (Sec. 4.2): the current solution and its FAS
+ * right-hand sides are restricted to every level without smoothing, the
+ * coarsest level is solved, then each finer level is corrected from the
+ * level below and improved by one V-cycle starting at that level. */
+static void fmg_cycle(const OSolver* s, OSolver* sm) {
+  for (int l = 0; l + 1 < s->nlev; ++l) fas_down(s, sm, l);
+  coarse_solve(s, &sm->lev[s->nlev - 1]);
+  for (int l = s->nlev - 2; l >= 0; --l) {
+    fas_up(s, sm, l);
+    vcycle(s, sm, l);
+  }
 }
 
 /* ------------------------------------------------------------- hierarchy */
@@ -685,6 +717,7 @@ typedef struct {
   int mixed;
   int stall_window;   /* cycles over which a 5 % gain is required; 0: off */
   int accel_depth;    /* Anderson mixing depth m over the V-cycle map; 0: off */
+  int cycle;          /* 0: V-cycles, 1: FMG cycles */
 } or_desc;
 
 typedef struct {
@@ -709,7 +742,10 @@ static void restrict_sources(OSolver* s) {
  * finest u, then (Neumann gauge) removal of the mean. */
 static void cycle_map(OSolver* s) {
   OLevel* F = &s->lev[0];
-  vcycle(s, s, 0);
+  if (s->fmg)
+    fmg_cycle(s, s);
+  else
+    vcycle(s, s, 0);
   if (s->zero_mean) {
     double m = interior_mean(&F->g, F->u[0]);
     for (int k = 0; k < F->g.n[2]; ++k)
@@ -885,6 +921,7 @@ static void setup(OSolver* s, const or_desc* d, int kind, int bc, int ncomp) {
   s->tol = d->tol;
   s->stall_window = d->stall_window;
   s->accel = d->accel_depth;
+  s->fmg = d->cycle == 1;
   build_levels(s, d->ndim, d->geom, d->n, d->lo, d->hi);
 }
 

@@ -52,7 +52,7 @@ class Desc(C.Structure):
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int),
                 ("tol", C.c_double), ("mixed", C.c_int), ("stall_window", C.c_int),
-                ("accel_depth", C.c_int)]
+                ("accel_depth", C.c_int), ("cycle", C.c_int)]
 
 
 class Report(C.Structure):
@@ -99,7 +99,7 @@ def lib():
 
 
 def desc(geom, n, lo, hi, nu1=2, nu2=2, max_cycles=200, tol=1e-10, mixed="4pt", stall_window=10,
-         accel_depth=0):
+         accel_depth=0, cycle="v"):
     """Grid + solver descriptor.  n, lo, hi have one entry per dimension."""
     d = Desc()
     nd = len(n)
@@ -113,6 +113,7 @@ def desc(geom, n, lo, hi, nu1=2, nu2=2, max_cycles=200, tol=1e-10, mixed="4pt", 
     d.mixed = MIXED[mixed]
     d.stall_window = stall_window
     d.accel_depth = accel_depth
+    d.cycle = {"v": 0, "fmg": 1}[cycle]
     return d
 
 

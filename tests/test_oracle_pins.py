@@ -657,3 +657,85 @@ def test_divb_cleaning_removes_gradient_part():
         errs.append(max(np.abs(B[c] - sol[c]).max() for c in range(3)))
     assert div_in[0] / div_in[1] > 3.0, div_in
     assert errs[0] / errs[1] > 1.5, errs
+
+
+# -------------------------------------------------------- FMG cycle
+
+
+def _dirichlet_poisson_mms(n):
+    """lap u = f on [0, 1]^3 with u* = sin(pi x) sin(pi y) sin(pi z) (zero on
+    the faces, the Dirichlet-0 ghost rule), f = -3 pi^2 u*."""
+    x = (np.arange(n) + 0.5) / n
+    zz, yy, xx = np.meshgrid(x, x, x, indexing="ij")
+    ustar = np.sin(PI * xx) * np.sin(PI * yy) * np.sin(PI * zz)
+    return ustar, -3 * PI ** 2 * ustar
+
+
+def test_one_fmg_cycle_reaches_discretisation_accuracy():
+    """The defining property of full multigrid: one FMG cycle from a zero
+    guess leaves an algebraic error no larger than the discretisation error
+    (here within 3x of the converged discrete solution's error against the
+    continuous one, which the low-order Kwak transfer of the corrections
+    allows), so that error falls at second order under refinement; one
+    V-cycle from zero is orders of magnitude away."""
+    errs = []
+    for n in (32, 64):
+        ustar, f = _dirichlet_poisson_mms(n)
+        conv = np.zeros_like(f)
+        o.solve_scalar(o.desc("cart", [n] * 3, [0] * 3, [1] * 3, tol=1e-13, max_cycles=200), "lin",
+                       "dirichlet", conv, f=f)
+        disc = np.abs(conv - ustar).max()
+        assert disc < 2e-3  # second order: ~ pi^2 h^2 / 8
+        fmg1 = np.zeros_like(f)
+        o.solve_scalar(o.desc("cart", [n] * 3, [0] * 3, [1] * 3, tol=1e-300, max_cycles=1, stall_window=0,
+                              cycle="fmg"), "lin", "dirichlet", fmg1, f=f)
+        v1 = np.zeros_like(f)
+        o.solve_scalar(o.desc("cart", [n] * 3, [0] * 3, [1] * 3, tol=1e-300, max_cycles=1, stall_window=0),
+                       "lin", "dirichlet", v1, f=f)
+        errs.append(np.abs(fmg1 - ustar).max())
+        assert errs[-1] < 3.0 * disc
+        assert np.abs(v1 - ustar).max() > 50.0 * disc
+    assert errs[0] / errs[1] > 3.0
+
+
+@pytest.mark.parametrize("case", ["cart_poisson", "sph2d_psi", "cyl2d_vec"])
+def test_fmg_and_v_cycles_share_the_fixed_point(case):
+    """FMG changes the route, not the discrete solution: FMG and V-cycles
+    converge to the same fields, FMG in fewer cycles on the Cartesian
+    Poisson problem."""
+    if case == "cart_poisson":
+        n = 32
+        ustar, f = _dirichlet_poisson_mms(n)
+        res = {}
+        for cyc in ("v", "fmg"):
+            u = np.zeros_like(f)
+            rep = o.solve_scalar(o.desc("cart", [n] * 3, [0] * 3, [1] * 3, tol=1e-12, max_cycles=200,
+                                        cycle=cyc), "lin", "dirichlet", u, f=f)
+            assert rep["status"] == "ok"
+            res[cyc] = (u, rep["cycles"])
+        assert res["fmg"][1] < res["v"][1]
+        np.testing.assert_allclose(res["fmg"][0], res["v"][0], rtol=0, atol=1e-10 * np.abs(ustar).max())
+    elif case == "sph2d_psi":
+        U = inputs.static_polytrope_sph2d()
+        out = []
+        for cyc in ("v", "fmg"):
+            d = o.desc("sph", [64, 32], [0, 0], [100.0, PI], tol=1e-12, max_cycles=1000, cycle=cyc,
+                       accel_depth=8, stall_window=0)
+            u = np.zeros(o.shape(d))
+            rep = o.solve_scalar(d, "psi", "robin", u, U=U, A2=np.zeros_like(U))
+            assert rep["status"] == "ok"
+            out.append(u)
+        np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-9 * np.abs(out[0]).max())
+    else:
+        U, S, Si = inputs.rotating_polytrope_cyl([32, 64], 100.0)
+        out = []
+        for cyc in ("v", "fmg"):
+            d = o.desc("cyl", [32, 64], [0.0, -100.0], [100.0, 100.0], tol=1e-12, max_cycles=1000, cycle=cyc,
+                       accel_depth=8, stall_window=0)
+            V = [np.zeros(o.shape(d)) for _ in range(3)]
+            rep = o.solve_vector(d, "dirichlet", [8 * PI * s for s in Si], V)
+            assert rep["status"] == "ok"
+            out.append(V)
+        scale = max(np.abs(v).max() for v in out[0])
+        for a, b in zip(out[1], out[0]):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-9 * scale)
