@@ -65,6 +65,7 @@ enum { MG_FP64 = 0, MG_MIXED = 1 };                        /* precision */
 enum { MG_MIXED_4PT = 0, MG_MIXED_CORNER = 1 };            /* mixed derivative */
 enum { MG_BC_ROBIN = 0, MG_BC_DIRICHLET = 1, MG_BC_NEUMANN = 2 };
 enum { MG_EQ_PSI = 0, MG_EQ_LIN = 1, MG_EQ_VEC = 2 };      /* equation kinds */
+enum { MG_CYCLE_V = 0, MG_CYCLE_FMG = 1 };                 /* iteration */
 
 /*
  * Grid and solver settings.
@@ -92,6 +93,14 @@ enum { MG_EQ_PSI = 0, MG_EQ_LIN = 1, MG_EQ_VEC = 2 };      /* equation kinds */
  *             converges slowly on spherical grids (Sec. 2.7.2 notes it);
  *             the mixing restores a rate of tens of cycles.  Each mixed
  *             iteration is one V-cycle and counts as one cycle.
+ *   cycle     MG_CYCLE_V: FAS V(nu1, nu2) cycles.  MG_CYCLE_FMG: full
+ *             multigrid cycles (the cycle Sec. 4.2 times; the paper does not
+ *             spell it out, the FAS form is used): the current solution and
+ *             FAS sources restricted to every level, the coarsest solved,
+ *             then per level upward the FAS correction from below and one
+ *             V-cycle from that level.  In MG_MIXED the FP32 correction
+ *             equation gets the same structure from a zero correction.
+ *             One FMG cycle counts as one cycle.
  */
 typedef struct {
   int ndim;
@@ -106,6 +115,7 @@ typedef struct {
   int mixed_deriv;
   int stall_window;
   int accel_depth;
+  int cycle;
 } mg_grid_desc;
 
 #define MG_HIST 1024

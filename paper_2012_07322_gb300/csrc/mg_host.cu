@@ -174,6 +174,7 @@ int validate(const mg_grid_desc* d) {
     return fail(MG_ERR_INVALID, "bad mixed_deriv");
   if (d->stall_window < 0) return fail(MG_ERR_INVALID, "bad stall_window");
   if (d->accel_depth < 0 || d->accel_depth > AA_MAX) return fail(MG_ERR_INVALID, "accel_depth must be in 0..16");
+  if (d->cycle != MG_CYCLE_V && d->cycle != MG_CYCLE_FMG) return fail(MG_ERR_INVALID, "cycle must be V or FMG");
   return MG_OK;
 }
 
@@ -436,16 +437,13 @@ void coarse64(mg_hierarchy* H, const Eq& e, int l) {
 
 // FAS V(nu1, nu2): pre-smooth; r = f - L(u); u_H = R u (kept as uh_H);
 // f_H = L_H(u_H) + R r; recurse; u += P(u_H - uh_H); post-smooth.
-void vcycle64(mg_hierarchy* H, const Eq& e, int l) {
-  if (l == H->nlev - 1) {
-    coarse64(H, e, l);
-    return;
-  }
+// FAS restriction from level l to l + 1 at the current u_l:
+// r = f - L(u); u_H = R u (kept as uh_H); f_H = L_H(u_H) + R r.
+void fas_down64(mg_hierarchy* H, const Eq& e, int l) {
   Level& L = H->L[l];
   Level& C = H->L[l + 1];
   auto v = with_bc(L.v64, e.bc);
   auto vc = with_bc(C.v64, e.bc);
-  smooth64(H, e, l, H->d.nu1);
   if (e.kind != EQ_VEC) {
     launch_residual_scalar(v, e.kind, L.u[0], fptr(H, e, l, 0), s0ptr(H, e, l), s1ptr(H, e, l), L.r[0],
                            (unsigned long long*)nullptr, 0, H->st);
@@ -465,11 +463,41 @@ void vcycle64(mg_hierarchy* H, const Eq& e, int l) {
     fill_all64(H, e, l + 1);
     launch_apply_vec(vc, C.u, C.f, 1, H->st);
   }
-  vcycle64(H, e, l + 1);
+}
+
+// FAS correction of level l from level l + 1: u += P(u_H - uh_H).
+void fas_up64(mg_hierarchy* H, const Eq& e, int l) {
+  Level& L = H->L[l];
+  Level& C = H->L[l + 1];
+  auto v = with_bc(L.v64, e.bc);
+  auto vc = with_bc(C.v64, e.bc);
   for (int c = 0; c < e.ncomp; ++c)
     launch_prolong(v, vc, L.u[c], C.u[c], C.uh[c], e.kind == EQ_VEC ? c : -1, H->st);
   if (e.kind == EQ_VEC) fill_all64(H, e, l);
+}
+
+void vcycle64(mg_hierarchy* H, const Eq& e, int l) {
+  if (l == H->nlev - 1) {
+    coarse64(H, e, l);
+    return;
+  }
+  smooth64(H, e, l, H->d.nu1);
+  fas_down64(H, e, l);
+  vcycle64(H, e, l + 1);
+  fas_up64(H, e, l);
   smooth64(H, e, l, H->d.nu2);
+}
+
+// FAS full-multigrid cycle (Sec. 4.2 times FMG cycles): restrict the
+// current solution and FAS sources to every level, solve the coarsest, then
+// per level upward: FAS correction from below and one V-cycle from there.
+void fmg64(mg_hierarchy* H, const Eq& e) {
+  for (int l = 0; l + 1 < H->nlev; ++l) fas_down64(H, e, l);
+  coarse64(H, e, H->nlev - 1);
+  for (int l = H->nlev - 2; l >= 0; --l) {
+    fas_up64(H, e, l);
+    vcycle64(H, e, l);
+  }
 }
 
 double bits_to_double(unsigned long long b) {
@@ -711,14 +739,54 @@ void restrict_k32(mg_hierarchy* H) {
   }
 }
 
+// FMG for the correction equation (L - K) e = f32 from e = 0: the
+// right-hand side restricted down (the residual of e = 0 is f32 itself) to
+// the first level of the one-block cycle (or the coarsest), one correction
+// cycle there, then per level upward: e_l = P e_{l+1} and one correction
+// V-cycle from that level.
+void fmg32(mg_hierarchy* H, const Eq& e) {
+  const int lb = std::min(block_cycle_level(H, e), H->nlev - 1);
+  for (int l = 0; l < lb; ++l) {
+    Level& L = H->L[l];
+    Level& C = H->L[l + 1];
+    auto v = with_bc(L.v32, e.bc);
+    auto vc = with_bc(C.v32, e.bc);
+    for (int c = 0; c < e.ncomp; ++c) {
+      const float* a[4] = {L.f32[c], nullptr, nullptr, nullptr};
+      float* b[4] = {C.f32[c], nullptr, nullptr, nullptr};
+      float* cp[3] = {nullptr, nullptr, nullptr};
+      launch_restrict<float>(v, vc, 1, a, b, cp, H->st);
+    }
+  }
+  for (int c = 0; c < e.ncomp; ++c) cudaMemsetAsync(H->L[lb].e[c], 0, sizeof(float) * H->L[lb].ng, H->st);
+  vcycle32(H, e, lb);
+  for (int l = lb - 1; l >= 0; --l) {
+    Level& L = H->L[l];
+    Level& C = H->L[l + 1];
+    auto v = with_bc(L.v32, e.bc);
+    auto vc = with_bc(C.v32, e.bc);
+    for (int c = 0; c < e.ncomp; ++c) {
+      cudaMemsetAsync(L.e[c], 0, sizeof(float) * L.ng, H->st);
+      launch_prolong<float>(v, vc, L.e[c], C.e[c], nullptr, e.kind == EQ_VEC ? c : -1, H->st);
+    }
+    if (e.kind == EQ_VEC)
+      for (int c = 0; c < 3; ++c) launch_fill_ghosts<float>(v, L.e[c], c, H->st);
+    vcycle32(H, e, l);
+  }
+}
+
 // ---------------------------------------------------------- cycle control
 
 // One application of the iteration map: a V-cycle (FP64 FAS, or the FP32
 // correction cycle of the defect-correction loop) and the Neumann gauge.
 int cycle_map(mg_hierarchy* H, const Eq& e) {
   Level& L0 = H->L[0];
+  const bool fmg = H->d.cycle == MG_CYCLE_FMG;
   if (H->d.precision != MG_MIXED) {
-    vcycle64(H, e, 0);
+    if (fmg)
+      fmg64(H, e);
+    else
+      vcycle64(H, e, 0);
   } else {
     auto v = with_bc(L0.v64, e.bc);
     // f32 holds the FP32 residual written by the preceding finest_norm
@@ -727,7 +795,10 @@ int cycle_map(mg_hierarchy* H, const Eq& e) {
       launch_psi_linearisation(v, L0.u[0], L0.s0, L0.s1, L0.k32, H->st);
       restrict_k32(H);
     }
-    vcycle32(H, e, 0);
+    if (fmg)
+      fmg32(H, e);
+    else
+      vcycle32(H, e, 0);
     for (int c = 0; c < e.ncomp; ++c)
       launch_add_correction<float>(v, L0.u[c], L0.e[c], H->st, (e.zero_mean && c == 0) ? H->d_part : nullptr,
                                    NPARTS);

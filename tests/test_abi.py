@@ -44,4 +44,9 @@ def test_host_only_entry_points():
     bad = mg.grid_desc("sph", [64, 32], hi=[100.0, 3.0])             # theta must end at pi
     with pytest.raises(mg.MgError):
         mg.mg_hierarchy_bytes(bad)
+    assert mg.mg_hierarchy_bytes(mg.grid_desc("sph", [64, 32], hi=[100.0, np.pi], cycle="fmg")) > 0
+    bad = mg.grid_desc("sph", [64, 32], hi=[100.0, np.pi])
+    bad.cycle = 7                                                     # neither V nor FMG
+    with pytest.raises(mg.MgError):
+        mg.mg_hierarchy_bytes(bad)
     assert mg.lib().mg_strerror(3) == b"not converged"

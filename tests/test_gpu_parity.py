@@ -61,7 +61,7 @@ def relerr(a, b):
 
 def descs(mg, geom, n, lo, hi, **kw):
     okw = {k: v for k, v in kw.items()
-           if k in ("tol", "max_cycles", "nu1", "nu2", "mixed", "stall_window", "accel_depth")}
+           if k in ("tol", "max_cycles", "nu1", "nu2", "mixed", "stall_window", "accel_depth", "cycle")}
     gkw = dict(okw)
     if "precision" in kw:
         gkw["precision"] = kw["precision"]
@@ -237,8 +237,10 @@ def test_vector_solve_parity(mg, geom, n, lo, hi, mixed):
     h.close()
 
 
-def run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="fp64", psi_only=False, tol=1e-10, accel_depth=0):
-    d, gd = descs(mg, geom, n, lo, hi, tol=tol, max_cycles=1000, precision=precision, accel_depth=accel_depth)
+def run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="fp64", psi_only=False, tol=1e-10, accel_depth=0,
+                 cycle="v"):
+    d, gd = descs(mg, geom, n, lo, hi, tol=tol, max_cycles=1000, precision=precision, accel_depth=accel_depth,
+                  cycle=cycle)
     shp = o.shape(d)
     psi, alpha = np.ones(shp), np.ones(shp)
     beta = [np.zeros(shp) for _ in range(3)]
@@ -415,3 +417,51 @@ def test_fused_sweep_parity(mg, bc, case):
                      c=dev(cc) if cc is not None else None)
         assert relerr(host(ut), interior(d, ug)) < 1e-12, (bc, ff is None, cc is None)
     h.close()
+
+
+# ------------------------------------------------------------- FMG cycles
+
+
+@pytest.mark.parametrize("geom,n,lo,hi,bc,zero_mean", [
+    ("cart", [32, 32, 32], [0, 0, 0], [1, 1, 1], "dirichlet", False),
+    ("cart", [32, 32, 32], [-1, -1, -1], [1, 1, 1], "neumann", True),
+    ("cyl", [32, 64], [0.0, -40.0], [40.0, 40.0], "robin", False),
+])
+def test_fmg_linear_scalar_parity(mg, geom, n, lo, hi, bc, zero_mean):
+    """FMG cycles (FAS form): cycles within one and fields within 1e-9 of
+    the oracle's FMG."""
+    d, gd = descs(mg, geom, n, lo, hi, tol=1e-10, max_cycles=200, cycle="fmg")
+    rng = np.random.default_rng(21)
+    f = rng.standard_normal(o.shape(d))
+    if zero_mean:
+        f -= f.mean()
+    c = None if bc == "neumann" else rng.uniform(0, 0.05, o.shape(d))
+    u = np.zeros(o.shape(d))
+    ro = o.solve_scalar(d, "lin", bc, u, c=c, f=f, zero_mean=zero_mean)
+    h = mg.Hierarchy(gd)
+    ut = torch.zeros(o.shape(d), dtype=torch.float64, device="cuda")
+    rg = mg.mg_solve_scalar(h, "lin", bc, ut, c=dev(c) if c is not None else None, f=dev(f), zero_mean=zero_mean)
+    h.close()
+    check_report(rg, ro, 1e-10)
+    assert relerr(host(ut), u) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fmg_xcfc_parity(mg, precision):
+    """Full xCFC system on the 3D spherical 32x16x16 grid with FMG cycles
+    and Anderson mixing: FP64 matches the oracle's FMG (cycles within one,
+    fields within 1e-9); the mixed-precision FMG path reaches the FP64
+    tolerance with every field within 1e-8 of the oracle."""
+    n = [32, 16, 16]
+    U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
+    rg, ro, got, want = run_cfc_pair(mg, "sph", n, [0, 0, 0], [100.0, PI, 2 * PI], U, S, Si, precision=precision,
+                                     accel_depth=8, cycle="fmg")
+    errs = field_errors(got, want)
+    if precision == "fp64":
+        for k in ("X", "psi", "alphapsi", "beta"):
+            check_report(rg[k], ro[k], 1e-10)
+        assert max(errs.values()) < 1e-9, errs
+    else:
+        for k in ("X", "psi", "alphapsi", "beta"):
+            assert rg[k]["status"] == "ok" and rg[k]["rel"] <= 1e-10
+        assert max(errs.values()) < 1e-8, errs
