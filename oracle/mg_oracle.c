@@ -1278,16 +1278,43 @@ typedef struct {
   double max_div_before, l2_div_before, max_div_after, l2_div_after;
 } or_divb_report;
 
-/* Central divergence of B (Cartesian), B ghosts copied from the boundary
- * cells (zero normal gradient). */
+/* Central divergence of B (physical components), (1/sqrt(g)) d_i (sqrt(g)
+ * q^i) of Sec. 2.2 with sqrt(g) = 1, R, r^2 sin(theta), every factor taken
+ * at the centre of the cell it multiplies:
+ *   Cartesian   sum_d (B_d,+ - B_d,-) / (2 h_d)
+ *   cylindrical (R+ B_R,+ - R- B_R,-) / (2 h_R R) + (B_z,+ - B_z,-) / (2 h_z)
+ *               + (B_phi,+ - B_phi,-) / (2 h_phi R)
+ *   spherical   (r+^2 B_r,+ - r-^2 B_r,-) / (2 h_r r^2)
+ *               + (s+ B_th,+ - s- B_th,-) / (2 h_th r s)
+ *               + (B_phi,+ - B_phi,-) / (2 h_phi r s),   s = sin(theta).
+ * B ghosts: copies of the boundary cell on the outer faces (zero normal
+ * gradient), the component parities across the origin / axis. */
 static void div_c(const OGrid* g, double* const Bg[3], double* div) {
-  for (int c = 0; c < g->ndim; ++c) fill_ghosts(g, Bg[c], BC_NEUMANN, -1);
+  for (int c = 0; c < g->ndim; ++c) fill_ghosts(g, Bg[c], BC_NEUMANN, g->geom == GEOM_CART ? -1 : c);
   long q = 0;
   for (int k = 0; k < g->n[2]; ++k)
     for (int j = 0; j < g->n[1]; ++j)
       for (int i = 0; i < g->n[0]; ++i, ++q) {
         double s = 0.0;
-        for (int c = 0; c < g->ndim; ++c) s += d1(g, Bg[c], c, i, j, k);
+        if (g->geom == GEOM_CART) {
+          for (int c = 0; c < g->ndim; ++c) s += d1(g, Bg[c], c, i, j, k);
+        } else {
+          const double x = xc(g, 0, i), xp = xc(g, 0, i + 1), xm = xc(g, 0, i - 1);
+          const double* B0 = Bg[0];
+          const double* B1 = Bg[1];
+          if (g->geom == GEOM_CYL) {
+            s = (xp * B0[IX(g, i + 1, j, k)] - xm * B0[IX(g, i - 1, j, k)]) / (2.0 * g->h[0] * x) +
+                (B1[IX(g, i, j + 1, k)] - B1[IX(g, i, j - 1, k)]) / (2.0 * g->h[1]);
+            if (g->ndim == 3)
+              s += (Bg[2][IX(g, i, j, k + 1)] - Bg[2][IX(g, i, j, k - 1)]) / (2.0 * g->h[2] * x);
+          } else {
+            const double st = sin(xc(g, 1, j)), sp = sin(xc(g, 1, j + 1)), sm = sin(xc(g, 1, j - 1));
+            s = (xp * xp * B0[IX(g, i + 1, j, k)] - xm * xm * B0[IX(g, i - 1, j, k)]) / (2.0 * g->h[0] * x * x) +
+                (sp * B1[IX(g, i, j + 1, k)] - sm * B1[IX(g, i, j - 1, k)]) / (2.0 * g->h[1] * x * st);
+            if (g->ndim == 3)
+              s += (Bg[2][IX(g, i, j, k + 1)] - Bg[2][IX(g, i, j, k - 1)]) / (2.0 * g->h[2] * x * st);
+          }
+        }
         div[q] = s;
       }
 }
@@ -1303,10 +1330,13 @@ static void div_norms(const double* div, long N, double* mx, double* l2) {
   *l2 = sqrt(s / (double)N);
 }
 
-/* Elliptic divergence cleaning, eqs. (poisson) and (update_bfield), on a
- * Cartesian grid: b = div B - mean(div B); lap Phi = b with Neumann ghosts,
- * Phi's mean removed after every cycle; B <- B - grad Phi (central).  B holds
- * ndim (interior) components, modified in place; phi (interior) out. */
+/* Elliptic divergence cleaning, eqs. (poisson) and (update_bfield):
+ * b = div B - <div B>, the mean weighted by w = 1, R, r^2 sin(theta) (the
+ * weights under which the flux-form Laplacian with Neumann ghosts sums to
+ * zero, so that the Neumann problem is compatible); lap Phi = b with
+ * Neumann outer ghosts, Phi's mean removed after every cycle; B <- B -
+ * grad Phi (central, physical components).  B holds ndim (interior)
+ * components, modified in place; phi (interior) out. */
 int or_clean_divb(const or_desc* d, double* const B[3], double* phi, or_divb_report* rep) {
   OGrid g;
   finest_grid(d, &g);
@@ -1319,9 +1349,18 @@ int or_clean_divb(const or_desc* d, double* const B[3], double* phi, or_divb_rep
   double* div = calloc(N, sizeof(double));
   div_c(&g, Bg, div);
   div_norms(div, N, &rep->max_div_before, &rep->l2_div_before);
-  double mean = 0.0;
-  for (long q = 0; q < N; ++q) mean += div[q];
-  mean /= (double)N;
+  double sw = 0.0, swd = 0.0;
+  {
+    long q = 0;
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i, ++q) {
+          const double w = norm_weight(&g, i, j);
+          sw += w;
+          swd += w * div[q];
+        }
+  }
+  const double mean = swd / sw;
   for (long q = 0; q < N; ++q) div[q] -= mean;
   for (long q = 0; q < N; ++q) phi[q] = 0.0;
   int st = or_solve_scalar(d, EQ_LIN, BC_NEUMANN, 1, NULL, NULL, NULL, div, phi, &rep->solve);
@@ -1330,8 +1369,11 @@ int or_clean_divb(const or_desc* d, double* const B[3], double* phi, or_divb_rep
   fill_ghosts(&g, pg, BC_NEUMANN, -1);
   for (int k = 0; k < g.n[2]; ++k)
     for (int j = 0; j < g.n[1]; ++j)
-      for (int i = 0; i < g.n[0]; ++i)
-        for (int c = 0; c < d->ndim; ++c) Bg[c][IX(&g, i, j, k)] -= d1(&g, pg, c, i, j, k);
+      for (int i = 0; i < g.n[0]; ++i) {
+        double G[3];
+        grad_phys(&g, pg, i, j, k, G);
+        for (int c = 0; c < d->ndim; ++c) Bg[c][IX(&g, i, j, k)] -= G[c];
+      }
   div_c(&g, Bg, div);
   div_norms(div, N, &rep->max_div_after, &rep->l2_div_after);
   for (int c = 0; c < d->ndim; ++c) {

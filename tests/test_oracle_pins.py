@@ -739,3 +739,84 @@ def test_fmg_and_v_cycles_share_the_fixed_point(case):
         scale = max(np.abs(v).max() for v in out[0])
         for a, b in zip(out[1], out[0]):
             np.testing.assert_allclose(a, b, rtol=0, atol=1e-9 * scale)
+
+
+# ------------------------------------------- curvilinear divergence cleaning
+
+
+def _centres(n, lo, hi, ext=0):
+    h = (hi - lo) / n
+    return lo + (np.arange(-ext, n + ext) + 0.5) * h, h
+
+
+def _dc(f, ax, h):
+    return (np.roll(f, -1, ax) - np.roll(f, 1, ax)) / (2 * h)
+
+
+@pytest.mark.parametrize("geom", ["sph", "cyl"])
+def test_curvilinear_discrete_curl_is_divergence_free_inside(geom):
+    """B = central curl of A in physical components (metric factors at the
+    neighbours' centres): the central divergence (1/sqrt(g)) d_i (sqrt(g)
+    B^i) of Sec. 2.2 vanishes to round-off on every cell whose stencil stays
+    inside; a wrong metric factor, sign or index would leave O(1)."""
+    if geom == "sph":
+        n, lo, hi = [16, 8, 8], [0, 0, 0], [1.0, PI, 2 * PI]
+    else:
+        n, lo, hi = [16, 16, 8], [0, -1.0, 0], [1.0, 1.0, 2 * PI]
+    (x0, h0), (x1, h1), (x2, h2) = (_centres(n[k], lo[k], hi[k], 1) for k in range(3))
+    P, Y, X = np.meshgrid(x2, x1, x0, indexing="ij")
+    if geom == "sph":
+        R, T = X, Y
+        Ar = np.sin(2 * R) * np.cos(P) * np.sin(T) + 0.1
+        At = R * np.cos(T) * np.sin(P) ** 2
+        Ap = R ** 2 * np.sin(T) * np.cos(2 * P)
+        s = np.sin(T)
+        B = [(_dc(s * Ap, 1, h1) - _dc(At, 0, h2)) / (R * s),
+             (_dc(Ar, 0, h2) / s - _dc(R * Ap, 2, h0)) / R,
+             (_dc(R * At, 2, h0) - _dc(Ar, 1, h1)) / R]
+    else:
+        R, Z = X, Y
+        AR = np.sin(2 * R) * np.cos(P) * Z + 0.1
+        Az = R * np.cos(Z) * np.sin(P) ** 2
+        Ap = R ** 2 * np.sin(Z) * np.cos(2 * P)
+        # components (R, z, phi): curl_R = (1/R) d_phi A_z - d_z A_phi,
+        # curl_z = (1/R) (d_R (R A_phi) - d_phi A_R), curl_phi = d_z A_R - d_R A_z
+        B = [_dc(Az, 0, h2) / R - _dc(Ap, 1, h1),
+             (_dc(R * Ap, 2, h0) - _dc(AR, 0, h2)) / R,
+             _dc(AR, 1, h1) - _dc(Az, 2, h0)]
+    B = [np.ascontiguousarray(b[1:-1, 1:-1, 1:-1]) for b in B]
+    d = o.desc(geom, n, lo, hi)
+    div = o.div_c(d, B)
+    scale = max(np.abs(b).max() for b in B) / h0
+    assert np.abs(div[:, 1:-1, 1:-1]).max() < 1e-12 * scale
+    assert np.abs(div).max() > 1e-3 * scale  # boundary ghosts (copies, parities) do not commute
+
+
+@pytest.mark.parametrize("geom", ["sph", "cyl"])
+def test_curvilinear_cleaning_removes_gradient_field(geom):
+    """B = grad chi (physical components) with a Neumann-compatible chi on
+    2D axisymmetric grids: cleaning cuts the L2 divergence by > 4x and the
+    cleaned field tends to zero under refinement away from the boundaries
+    (first order: the copied outer B ghosts make an O(1) divergence in the
+    boundary cells, whose O(h) layer feeds Phi)."""
+    far_max = []
+    for m in (32, 64, 128):
+        if geom == "sph":
+            n, lo, hi = [m, m // 2], [0, 0], [1.0, PI]
+            (r, _), (t, _) = _centres(n[0], 0, 1.0), _centres(n[1], 0, PI)
+            T, R = np.meshgrid(t, r, indexing="ij")
+            B = [-PI * np.sin(PI * R) + 0.5 * (1 - R ** 2) * np.cos(T), -0.5 * (1 - R ** 2 / 3) * np.sin(T)]
+            far = (R > 0.2) & (R < 0.9) & (T > 0.3) & (T < PI - 0.3)
+        else:
+            n, lo, hi = [m, 2 * m], [0, -1.0], [1.0, 1.0]
+            (r, _), (z, _) = _centres(n[0], 0, 1.0), _centres(n[1], -1.0, 1.0)
+            Z, R = np.meshgrid(z, r, indexing="ij")
+            B = [-PI * np.sin(PI * R) * np.cos(PI * Z), -PI * np.cos(PI * R) * np.sin(PI * Z)]
+            far = (R > 0.2) & (R < 0.9) & (np.abs(Z) < 0.8)
+        B = [np.ascontiguousarray(b) for b in B]
+        d = o.desc(geom, n, lo, hi, tol=1e-11, max_cycles=1000, accel_depth=8, stall_window=0)
+        rep = o.clean_divb(d, B, np.zeros(B[0].shape))
+        assert rep["solve"]["status"] == "ok"
+        assert rep["l2_div_after"] < 0.25 * rep["l2_div_before"]
+        far_max.append(max(np.abs(b[far]).max() for b in B))
+    assert far_max[0] / far_max[1] > 1.8 and far_max[1] / far_max[2] > 1.8, far_max
