@@ -208,12 +208,22 @@ typedef struct {
 } mg_divb_report;
 
 /*
- * Elliptic divergence cleaning (eqs. poisson, update_bfield) on a
- * Cartesian hierarchy: b = div B - mean(div B) (central differences, B
- * ghosts copied from the boundary cells), solve lap Phi = b with Neumann
- * ghosts (zero-mean Phi), then B <- B - grad Phi.  B[0..ndim-1] are
+ * Elliptic divergence cleaning (Sec. 2.2, eqs. poisson, update_bfield):
+ * b = div B - <div B>, solve lap Phi = b with Neumann outer ghosts
+ * (zero-mean Phi), then B <- B - grad Phi.  B[0..ndim-1] hold physical
+ * (orthonormal) components, ghost-free, dimension 0 fastest, and are
  * modified in place; phi_out (may be NULL) receives Phi.  Flags:
  * MG_HOST_POINTERS.
+ *   Cartesian: div B = sum_d central differences, B ghosts copied from the
+ *     boundary cells, <.> the plain mean.
+ *   Cylindrical / spherical: div B = (1/sqrt(g)) d_i (sqrt(g) q^i) by
+ *     central differences of sqrt(g) q^i, every metric factor at the centre
+ *     of the cell it multiplies; B ghosts copied on the outer faces, the
+ *     vector parities across the origin / axis; <.> weighted by R or
+ *     r^2 sin(theta), the weights under which the flux-form Laplacian with
+ *     Neumann ghosts sums to zero (so the Neumann problem is compatible);
+ *     grad Phi in physical components.
+ * The report's divergence norms are unweighted over the cells.
  */
 int mg_clean_divB(mg_hierarchy* h, double* B[3], double* phi_out, int flags, mg_divb_report* rep);
 

@@ -1466,8 +1466,8 @@ out:
 
 int mg_clean_divB(mg_hierarchy* H, double* B[3], double* phi_out, int flags, mg_divb_report* rep) {
   if (!H || !B) return fail(MG_ERR_INVALID, "null argument");
-  if (H->d.geom != MG_CART) return fail(MG_ERR_INVALID, "divergence cleaning needs a Cartesian grid");
   const int nd = H->d.ndim;
+  const bool curv = H->d.geom != MG_CART;
   for (int c = 0; c < nd; ++c)
     if (!B[c]) return fail(MG_ERR_INVALID, "null B component");
   if (int est = enter(H)) return est;
@@ -1494,15 +1494,49 @@ int mg_clean_divB(mg_hierarchy* H, double* B[3], double* phi_out, int flags, mg_
     *l2 = std::sqrt(s / N);
     return MG_OK;
   };
+  // curvilinear grids: B into ghosted copies with the vector rules (outer
+  // copies, origin / axis parities), then the divergence of Sec. 2.2
+  auto vn = with_bc(v, MG_BC_NEUMANN);
+  auto div_into_r = [&]() {
+    if (!curv) {
+      launch_div_central(v, Bd, L0.r[0], H->d_part, NPARTS, H->st);
+      return;
+    }
+    for (int c = 0; c < nd; ++c) {
+      copy_in(H, Bd[c], H->Xg[c]);
+      launch_fill_ghosts(vn, H->Xg[c], c, H->st);
+    }
+    double* Xg[3] = {H->Xg[0], H->Xg[1], nd == 3 ? H->Xg[2] : H->Xg[0]};
+    launch_div_curv(v, Xg, L0.r[0], H->d_part, NPARTS, H->st);
+  };
+  // sum of the weights w (1, R, r^2 sin theta) of the compatible mean
+  double wsum = N;
+  if (curv) {
+    double si = 0.0, sj = 0.0;
+    for (int i = 0; i < L0.n[0]; ++i) {
+      const double x = L0.lo[0] + (i + 0.5) * L0.h[0];
+      si += H->d.geom == MG_SPH ? x * x : x;
+    }
+    for (int j = 0; j < L0.n[1]; ++j) sj += H->d.geom == MG_SPH ? std::sin(L0.lo[1] + (j + 0.5) * L0.h[1]) : 1.0;
+    wsum = si * sj * L0.n[2];
+  }
   double mb, lb, ma, la;
-  launch_div_central(v, Bd, L0.r[0], H->d_part, NPARTS, H->st);
-  launch_sub_mean_into(v, L0.r[0], H->d_part, NPARTS, L0.f[0], H->st);
+  div_into_r();
+  if (curv)
+    launch_sub_wmean_into(v, L0.r[0], H->d_part, NPARTS, wsum, L0.f[0], H->st);
+  else
+    launch_sub_mean_into(v, L0.r[0], H->d_part, NPARTS, L0.f[0], H->st);
   if ((st = norms(&mb, &lb))) return st;
   CK(cudaMemsetAsync(L0.u[0], 0, sizeof(double) * L0.ng, H->st));
   Eq e{MG_EQ_LIN, MG_BC_NEUMANN, 1, 1, false};
   st = run_solve(H, e, rep ? &rep->solve : nullptr);
-  launch_grad_update(v, L0.u[0], Bd, H->st);
-  launch_div_central(v, Bd, L0.r[0], H->d_part, NPARTS, H->st);
+  if (curv) {
+    launch_fill_ghosts(vn, L0.u[0], -1, H->st);
+    launch_grad_update_curv(v, L0.u[0], Bd, H->st);
+  } else {
+    launch_grad_update(v, L0.u[0], Bd, H->st);
+  }
+  div_into_r();
   int s2 = norms(&ma, &la);
   if (s2) return s2;
   if (phi_out) {

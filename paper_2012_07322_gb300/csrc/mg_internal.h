@@ -99,6 +99,13 @@ void launch_div_central(const LevelView<double>& L, double* const B[3], double* 
                         cudaStream_t st);
 void launch_div_norms(const LevelView<double>& L, const double* div, double* part, int nparts,
                       unsigned long long* red, cudaStream_t st);
+// Curvilinear divergence cleaning: divergence from ghosted B with weighted
+// block sums, weighted-mean removal, gradient update of ghost-free B.
+void launch_div_curv(const LevelView<double>& L, double* const Bg[3], double* div, double* part, int nparts,
+                     cudaStream_t st);
+void launch_sub_wmean_into(const LevelView<double>& L, const double* div, const double* part, int nparts,
+                           double wsum, double* b, cudaStream_t st);
+void launch_grad_update_curv(const LevelView<double>& L, const double* phi, double* const B[3], cudaStream_t st);
 void launch_sub_mean_into(const LevelView<double>& L, const double* div, const double* part, int nparts,
                           double* b, cudaStream_t st);
 void launch_grad_update(const LevelView<double>& L, const double* phi, double* const B[3], cudaStream_t st);

@@ -223,6 +223,92 @@ __global__ void k_grad_update(LevelView<double> L, const double* __restrict__ ph
   }
 }
 
+// Central divergence on cylindrical / spherical grids (Sec. 2.2,
+// (1/sqrt(g)) d_i (sqrt(g) q^i) in physical components, every metric factor
+// at the centre of the cell it multiplies) from ghosted B (outer ghosts
+// copied, origin / axis parities); part gets the block sums of w div, w the
+// weight under which the flux-form Laplacian sums to zero (R, r^2 sin).
+template <int G>
+__global__ void k_div_curv(LevelView<double> L, const double* __restrict__ B0, const double* __restrict__ B1,
+                           const double* __restrict__ B2, double* __restrict__ div, double* __restrict__ part) {
+  __shared__ double sm[32];
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  double acc = 0.0;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    const double x = L.TI(TI_X, i), xp = L.TI(TI_X, i + 1), xm = L.TI(TI_X, i - 1);
+    double d;
+    if (G == CYL) {
+      d = (xp * B0[p + 1] - xm * B0[p - 1]) / (2.0 * L.h0 * x) + (B1[p + L.sx] - B1[p - L.sx]) / (2.0 * L.h1);
+      if (L.three) d += (B2[p + L.sy] - B2[p - L.sy]) / (2.0 * L.h2 * x);
+    } else {
+      const double st = L.TJ(TJ_S, j), sp = L.TJ(TJ_S, j + 1), sn = L.TJ(TJ_S, j - 1);
+      d = (xp * xp * B0[p + 1] - xm * xm * B0[p - 1]) / (2.0 * L.h0 * x * x) +
+          (sp * B1[p + L.sx] - sn * B1[p - L.sx]) / (2.0 * L.h1 * x * st);
+      if (L.three) d += (B2[p + L.sy] - B2[p - L.sy]) / (2.0 * L.h2 * x * st);
+    }
+    div[p] = d;
+    acc += norm_weight(L, i, j) * d;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += sm[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// b = div - (sum of part) / wsum (the weighted mean).
+__global__ void k_sub_wmean_into(LevelView<double> L, const double* __restrict__ div,
+                                 const double* __restrict__ part, int nparts, double wsum,
+                                 double* __restrict__ b) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += part[q];
+    mean = s / wsum;
+  }
+  __syncthreads();
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    b[p] = div[p] - mean;
+  }
+}
+
+// B <- B - grad Phi in physical components (central differences, Phi's
+// ghosts filled): (d_0, d_1, d_2 / R) cylindrical, (d_0, d_1 / r,
+// d_2 / (r sin)) spherical.  B ghost-free (the caller's layout).
+template <int G>
+__global__ void k_grad_update_curv(LevelView<double> L, const double* __restrict__ phi, double* __restrict__ B0,
+                                   double* __restrict__ B1, double* __restrict__ B2) {
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    const double x = L.TI(TI_X, i);
+    const double g0 = (phi[p + 1] - phi[p - 1]) / (2.0 * L.h0);
+    double g1 = (phi[p + L.sx] - phi[p - L.sx]) / (2.0 * L.h1);
+    double g2 = L.three ? (phi[p + L.sy] - phi[p - L.sy]) / (2.0 * L.h2) : 0.0;
+    if (G == CYL) {
+      g2 /= x;
+    } else {
+      g1 /= x;
+      g2 /= (x * L.TJ(TJ_S, j));
+    }
+    B0[q] -= g0;
+    B1[q] -= g1;
+    if (L.three) B2[q] -= g2;
+  }
+}
+
 // Linearisation of eq. psi for the FP32 correction: K = 2 pi U (1+u)^-2 +
 // 7/8 A2 (1+u)^-8 (so that dL/du = lap - K), computed in FP64.
 __global__ void k_psi_linearisation(LevelView<double> L, const double* __restrict__ u,
@@ -323,6 +409,32 @@ void launch_grad_update(const LevelView<double>& L, const double* phi, double* c
   long g = (n + 255) / 256;
   if (g > 8192) g = 8192;
   k_grad_update<<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
+}
+
+void launch_div_curv(const LevelView<double>& L, double* const Bg[3], double* div, double* part, int nparts,
+                     cudaStream_t st) {
+  count_launch();
+  if (L.geom == CYL)
+    k_div_curv<CYL><<<nparts, 256, 0, st>>>(L, Bg[0], Bg[1], Bg[2], div, part);
+  else
+    k_div_curv<SPH><<<nparts, 256, 0, st>>>(L, Bg[0], Bg[1], Bg[2], div, part);
+}
+
+void launch_sub_wmean_into(const LevelView<double>& L, const double* div, const double* part, int nparts,
+                           double wsum, double* b, cudaStream_t st) {
+  count_launch();
+  k_sub_wmean_into<<<nparts, 256, 0, st>>>(L, div, part, nparts, wsum, b);
+}
+
+void launch_grad_update_curv(const LevelView<double>& L, const double* phi, double* const B[3], cudaStream_t st) {
+  count_launch();
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  long g = (n + 255) / 256;
+  if (g > 8192) g = 8192;
+  if (L.geom == CYL)
+    k_grad_update_curv<CYL><<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
+  else
+    k_grad_update_curv<SPH><<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
 }
 
 void launch_psi_linearisation(const LevelView<double>& L, const double* u, const double* U, const double* A2,
