@@ -885,8 +885,6 @@ int ensure_aa(mg_hierarchy* H, int ncomp, int m) {
   const size_t need = sizeof(double) * (size_t)H->L[0].ng * ncomp * (3 + 2 * (size_t)m);
   if (H->aa_bytes < need) {
     if (H->aa) cudaFree(H->aa);
-  for (double* p : H->cinv)
-    if (p) cudaFree(p);
     H->aa = nullptr;
     H->aa_bytes = 0;
     if (cudaMalloc(&H->aa, need) != cudaSuccess) return fail(MG_ERR_OOM, "mixing storage allocation failed");
