@@ -518,7 +518,8 @@ int finest_norm(mg_hierarchy* H, const Eq& e, double* rel) {
   const bool mixed = H->d.precision == MG_MIXED;
   if (e.kind != EQ_VEC) {
     launch_residual_scalar(v, e.kind, L.u[0], fptr(H, e, 0, 0), s0ptr(H, e, 0), s1ptr(H, e, 0),
-                           (double*)nullptr, H->d_red, 1, H->st, mixed ? L.f32[0] : nullptr);
+                           (double*)nullptr, H->d_red, 1, H->st, mixed ? L.f32[0] : nullptr,
+                           (mixed && e.kind == EQ_PSI) ? L.k32 : nullptr);
   } else {
     const double* f[3] = {L.f[0], L.f[1], L.f[2]};
     double* const none[3] = {nullptr, nullptr, nullptr};
@@ -791,10 +792,8 @@ int cycle_map(mg_hierarchy* H, const Eq& e) {
     auto v = with_bc(L0.v64, e.bc);
     // f32 holds the FP32 residual written by the preceding finest_norm
     for (int c = 0; c < e.ncomp; ++c) CK(cudaMemsetAsync(L0.e[c], 0, sizeof(float) * L0.ng, H->st));
-    if (e.kind == EQ_PSI) {
-      launch_psi_linearisation(v, L0.u[0], L0.s0, L0.s1, L0.k32, H->st);
-      restrict_k32(H);
-    }
+    // eq. psi: K = dS/du at this u was written by finest_norm with f32
+    if (e.kind == EQ_PSI) restrict_k32(H);
     if (fmg)
       fmg32(H, e);
     else
@@ -881,8 +880,11 @@ int gram_solve(int m, const double* M, const double* b, double* y) {
   return 0;
 }
 
-int ensure_aa(mg_hierarchy* H, int ncomp, int m) {
-  const size_t need = sizeof(double) * (size_t)H->L[0].ng * ncomp * (3 + 2 * (size_t)m);
+// Mixing storage: x, fprev, gprev (FP64) and 2 m history columns of
+// col_bytes per value, each ncomp arrays of L0.ng values.
+int ensure_aa(mg_hierarchy* H, int ncomp, int m, size_t col_bytes) {
+  const size_t vals = (size_t)H->L[0].ng * ncomp;
+  const size_t need = vals * (3 * sizeof(double) + 2 * (size_t)m * col_bytes);
   if (H->aa_bytes < need) {
     if (H->aa) cudaFree(H->aa);
     H->aa = nullptr;
@@ -993,16 +995,23 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   int st = MG_OK;
   // mixing state
   const long stride = L0.ng, vlen = (long)e.ncomp * L0.ng;
+  // history columns in FP32 in mixed precision (mg_accel.cu)
   double *ax = nullptr, *afp = nullptr, *agp = nullptr, *adF = nullptr, *adG = nullptr;
+  float *adF32 = nullptr, *adG32 = nullptr;
   double M[AA_MAX * AA_MAX] = {0};
   int ncol = 0, head = 0;
   if (m > 0) {
-    if ((st = ensure_aa(H, e.ncomp, m))) return st;
+    if ((st = ensure_aa(H, e.ncomp, m, mixed ? sizeof(float) : sizeof(double)))) return st;
     ax = H->aa;
     afp = ax + vlen;
     agp = afp + vlen;
-    adF = agp + vlen;
-    adG = adF + (long)m * vlen;
+    if (mixed) {
+      adF32 = reinterpret_cast<float*>(agp + vlen);
+      adG32 = adF32 + (long)m * vlen;
+    } else {
+      adF = agp + vlen;
+      adG = adF + (long)m * vlen;
+    }
   }
   std::vector<double> hist;
   double rel;
@@ -1032,8 +1041,12 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
     if (m > 0) {
       const int first = cyc == 0;
       const int slot = head;
-      launch_aa_update(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF + (long)slot * vlen,
-                       adG + (long)slot * vlen, first, H->st);
+      if (mixed)
+        launch_aa_update<float>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF32 + (long)slot * vlen,
+                                adG32 + (long)slot * vlen, first, H->st);
+      else
+        launch_aa_update<double>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF + (long)slot * vlen,
+                                 adG + (long)slot * vlen, first, H->st);
       if (!first) {
         head = (head + 1) % m;
         if (ncol < m) ++ncol;
@@ -1042,7 +1055,11 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
         AACols cols{};
         cols.n = ncol;
         for (int a = 0; a < ncol; ++a) cols.slot[a] = (head - ncol + a + m) % m;   // oldest first
-        launch_aa_dots(L0.v64, e.ncomp, stride, afp, adF, cols, first ? -1 : slot, H->d_aa_part, H->st);
+        if (mixed)
+          launch_aa_dots<float>(L0.v64, e.ncomp, stride, afp, adF32, cols, first ? -1 : slot, H->d_aa_part,
+                                H->st);
+        else
+          launch_aa_dots<double>(L0.v64, e.ncomp, stride, afp, adF, cols, first ? -1 : slot, H->d_aa_part, H->st);
         CK(cudaMemcpyAsync(H->h_aa_part, H->d_aa_part, sizeof(double) * AA_BLOCKS * 2 * AA_MAX,
                            cudaMemcpyDeviceToHost, H->st));
         CK(cudaStreamSynchronize(H->st));
@@ -1066,7 +1083,10 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
           for (int b = 0; b < ncol; ++b) Ms[a * ncol + b] = M[cols.slot[a] * AA_MAX + cols.slot[b]];
         if (gram_solve(ncol, Ms, bvec, gam) == 0) {
           for (int a = 0; a < ncol; ++a) cols.gamma[a] = gam[a];
-          launch_aa_combine(L0.v64, e.ncomp, stride, L0.u, adG, cols, H->st);
+          if (mixed)
+            launch_aa_combine<float>(L0.v64, e.ncomp, stride, L0.u, adG32, cols, H->st);
+          else
+            launch_aa_combine<double>(L0.v64, e.ncomp, stride, L0.u, adG, cols, H->st);
           if (e.kind == EQ_VEC) fill_all64(H, e, 0);
         } else {
           ncol = 0;  // degenerate history: restart the mixing

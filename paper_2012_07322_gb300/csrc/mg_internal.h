@@ -46,11 +46,13 @@ inline bool fused_sweep_applies(const LevelView<T>& L) {
 template <typename T>
 void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st);
 // r = f - L(u) into r (nullable) and, rounded to FP32, into r32 (nullable);
-// red (nullable) receives the norms of the finest-level stopping rule.
+// red (nullable) receives the norms of the finest-level stopping rule; for
+// eq. psi, k32 (nullable) receives the linearisation 2 pi U (1+u)^-2 +
+// 7/8 A2 (1+u)^-8 at the same u, rounded to FP32.
 template <typename T>
 void launch_residual_scalar(const LevelView<T>& L, int kind, const T* u, const T* f, const T* s0,
                             const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st,
-                            float* r32 = nullptr);
+                            float* r32 = nullptr, float* k32 = nullptr);
 template <typename T>
 void launch_residual_vec(const LevelView<T>& L, T* const V[3], const T* const f[3], T* const r[3],
                          unsigned long long* red, int weighted, cudaStream_t st, float* const r32[3] = nullptr);
@@ -109,8 +111,6 @@ void launch_grad_update_curv(const LevelView<double>& L, const double* phi, doub
 void launch_sub_mean_into(const LevelView<double>& L, const double* div, const double* part, int nparts,
                           double* b, cudaStream_t st);
 void launch_grad_update(const LevelView<double>& L, const double* phi, double* const B[3], cudaStream_t st);
-void launch_psi_linearisation(const LevelView<double>& L, const double* u, const double* U, const double* A2,
-                              float* K, cudaStream_t st);
 void launch_xcfc_ap_init(const LevelView<double>& L, const double* alpha, const double* dpsi, double* dap,
                          cudaStream_t st);
 void launch_xcfc_alpha_out(const LevelView<double>& L, const double* dap, const double* dpsi, double* alpha,
@@ -126,11 +126,15 @@ struct AACols {
   int slot[AA_MAX];
   double gamma[AA_MAX];
 };
+// History columns TC: double, or float in mixed precision.
+template <typename TC>
 void launch_aa_update(const LevelView<double>& L, int ncomp, long stride, double* const g[3], const double* x,
-                      double* fprev, double* gprev, double* dF, double* dG, int first, cudaStream_t st);
-void launch_aa_dots(const LevelView<double>& L, int ncomp, long stride, const double* f, const double* dF,
+                      double* fprev, double* gprev, TC* dF, TC* dG, int first, cudaStream_t st);
+template <typename TC>
+void launch_aa_dots(const LevelView<double>& L, int ncomp, long stride, const double* f, const TC* dF,
                     const AACols& cols, int newcol, double* part, cudaStream_t st);
-void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], const double* dG,
+template <typename TC>
+void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], const TC* dG,
                        const AACols& cols, cudaStream_t st);
 
 // One-block FP32 correction V-cycle over the coarse levels (mg_block.cu):

@@ -330,7 +330,8 @@ constexpr int RES_KZ = 4;
 template <typename T, int G, int KIND>
 __global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                   const T* __restrict__ s0, const T* __restrict__ s1, T* __restrict__ r,
-                                  float* __restrict__ r32, unsigned long long* red, int weighted) {
+                                  float* __restrict__ r32, float* __restrict__ k32, unsigned long long* red,
+                                  int weighted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   unsigned long long m[3] = {0ULL, 0ULL, 0ULL};
@@ -341,10 +342,11 @@ __global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const
       const int k = (blockIdx.z * RES_KZ + it) * blockDim.z + threadIdx.z;
       if (k >= L.n2) continue;
       const long p = L.idx(i, j, k);
-      T Sv;
-      const T rv = scalar_residual_cell<T, G, KIND>(L, u, f, s0, s1, i, j, k, p, Sv);
+      T Sv, kp;
+      const T rv = scalar_residual_cell<T, G, KIND>(L, u, f, s0, s1, i, j, k, p, Sv, k32 ? &kp : nullptr);
       if (r) r[p] = rv;
       if (r32) r32[p] = (float)rv;
+      if (KIND == EQ_PSI && k32) k32[p] = (float)kp;
       if (red) {
         m[0] = umax64(m[0], abs_bits((double)rv));
         if (weighted) {
@@ -827,12 +829,13 @@ void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int
 
 template <typename T>
 void launch_residual_scalar(const LevelView<T>& L, int kind, const T* u, const T* f, const T* s0,
-                            const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st, float* r32) {
+                            const T* s1, T* r, unsigned long long* red, int weighted, cudaStream_t st, float* r32,
+                            float* k32) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_cells(L, b);
   g.z = cdiv(L.n2, (long)b.z * RES_KZ);
-  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_residual_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, red, weighted);
-                    else k_residual_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, red, weighted));
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_residual_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, k32, red, weighted);
+                    else k_residual_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, nullptr, red, weighted));
 }
 
 template <typename T>
@@ -960,7 +963,7 @@ void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cu
   template void launch_fill_ghosts<T>(const LevelView<T>&, T*, int, cudaStream_t);                             \
   template void launch_smooth_vec<T>(const LevelView<T>&, T* [3], const T*, int, int, cudaStream_t);           \
   template void launch_residual_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, const T*, T*, \
-                                          unsigned long long*, int, cudaStream_t, float*);                      \
+                                          unsigned long long*, int, cudaStream_t, float*, float*);              \
   template void launch_residual_vec<T>(const LevelView<T>&, T* const[3], const T* const[3], T* const[3],       \
                                        unsigned long long*, int, cudaStream_t, float* const[3]);                \
   template void launch_apply_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*, int,        \

@@ -175,10 +175,14 @@ __device__ __forceinline__ T coarse_corr(const LevelView<T>& C, const T* __restr
 // Residual f - L(u) of a scalar equation at an interior cell; Sv gets the
 // source S(u) as the paper writes the right-hand side (L(u) = lap u - S(u)
 // for eq. psi; lap u - c u with S = f + c u for linear equations).
+// For eq. psi, kpsi (if non-null) also receives its linearisation
+// dS/du = 2 pi U (1+u)^-2 + 7/8 A2 (1+u)^-8 at the same u, the c of the
+// mixed-precision correction equation (L - c) e = r.
 template <typename T, int G, int KIND>
 __device__ __forceinline__ T scalar_residual_cell(const LevelView<T>& L, const T* __restrict__ u,
                                                   const T* __restrict__ f, const T* __restrict__ s0,
-                                                  const T* __restrict__ s1, int i, int j, int k, long p, T& Sv) {
+                                                  const T* __restrict__ s1, int i, int j, int k, long p, T& Sv,
+                                                  T* kpsi = nullptr) {
   T D;
   const T lap = lap_scalar<T, G>(L, u, i, j, k, p, D);
   const T fv = f ? f[p] : T(0);
@@ -189,6 +193,7 @@ __device__ __forceinline__ T scalar_residual_cell(const LevelView<T>& L, const T
     const T ip7 = ip2 * ip2 * ip2 * ip;
     Sv = -T(2 * PI_D) * s0[p] * ip - T(0.125) * s1[p] * ip7;
     Lu = lap - Sv;
+    if (kpsi) *kpsi = T(2 * PI_D) * s0[p] * ip2 + T(0.875) * s1[p] * ((ip2 * ip2) * (ip2 * ip2));
   } else if (s1) {
     const T cu = s1[p] * u[p];
     Lu = lap - cu;

@@ -309,22 +309,6 @@ __global__ void k_grad_update_curv(LevelView<double> L, const double* __restrict
   }
 }
 
-// Linearisation of eq. psi for the FP32 correction: K = 2 pi U (1+u)^-2 +
-// 7/8 A2 (1+u)^-8 (so that dL/du = lap - K), computed in FP64.
-__global__ void k_psi_linearisation(LevelView<double> L, const double* __restrict__ u,
-                                    const double* __restrict__ U, const double* __restrict__ A2,
-                                    float* __restrict__ K) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (i >= L.n0 || j >= L.n1 || k >= L.n2) return;
-  const long p = L.idx(i, j, k);
-  const double ip = 1.0 / (1.0 + u[p]);
-  const double ip2 = ip * ip;
-  const double ip8 = (ip2 * ip2) * (ip2 * ip2);
-  K[p] = (float)(2.0 * PI_D * U[p] * ip2 + 0.875 * A2[p] * ip8);
-}
-
 // Initial alpha psi deviation from the caller's alpha (ghost-free) and the
 // solved psi deviation; and alpha = (alpha psi) / psi back to the caller.
 __global__ void k_ap_init(LevelView<double> L, const double* __restrict__ alpha, const double* __restrict__ dpsi,
@@ -435,13 +419,6 @@ void launch_grad_update_curv(const LevelView<double>& L, const double* phi, doub
     k_grad_update_curv<CYL><<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
   else
     k_grad_update_curv<SPH><<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
-}
-
-void launch_psi_linearisation(const LevelView<double>& L, const double* u, const double* U, const double* A2,
-                              float* K, cudaStream_t st) {
-  count_launch();
-  dim3 b = blk(L.three), g = grd(L, b);
-  k_psi_linearisation<<<g, b, 0, st>>>(L, u, U, A2, K);
 }
 
 static unsigned flat_grid(const LevelView<double>& L) {
