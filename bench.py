@@ -90,8 +90,23 @@ def level_cells():
 #   fused red-black sweep (Cartesian scalar): read u and f (and c), write u
 #                                               -> 3 words per cell (4 with c)
 BYTES_PER_CELL = {"smooth64_scalar": 5 * 8, "smooth64_vec": 8 * 8, "smooth32_scalar": 5 * 4,
-                  "smooth32_vec": 8 * 4, "resid64_scalar": 4 * 8, "resid64_vec": 9 * 8 / 3,
+                  "smooth32_vec": 8 * 4, "resid64_scalar": 4 * 8, "resid64_vec": 9 * 8,
                   "sweep64_fused": 3 * 8, "sweep32_fused": 3 * 4}
+
+# The finest FP64 residuals are bound by the FP64 pipe (GB300 issues 2 FP64
+# FMA per SM and clock, 1/64 of its FP32 rate), not by memory.  Algorithmic
+# FP64 flops per cell of the spherical operators as written (+, -, x count
+# one, a multiply-add two; the Newton diagonal excluded):
+#   vector (lap V + 1/3 grad div V, 3 components, and f - L): 80 + 72 + 68 + 3
+#   scalar, linear (flux-form Laplacian 18, - c u, f - L): 22
+FLOPS_PER_CELL = {"resid64_vec": 223, "resid64_scalar": 22}
+FP64_FMA_PER_SM_CLK = 2
+
+# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of the current kernel version: the 128x64x64
+# spherical vector residual (its working set sits in L2) and the 256^3
+# one-launch FP32 sweep.
+TRAFFIC_PER_LAUNCH = {"resid64_vec": 27.68e6, "sweep32_fused": 185.76e6}
 
 
 class ClockSampler:
@@ -190,7 +205,8 @@ def divb_measurement(mg, torch, stream, steps, precision, peak):
             "max_div_before": rep["max_div_before"], "max_div_after": rep["max_div_after"],
             "l2_div_before": rep["l2_div_before"], "l2_div_after": rep["l2_div_after"],
             "roofline": {"bound": "hbm", "kernel": key, "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "avg_launch_us": kms / max(nl, 1) * 1e3,
+                         "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get(key),
+                         "avg_launch_us": kms / max(nl, 1) * 1e3,
                          "algorithmic_bytes_per_launch": bpl, "launches": nl}}
 
 
@@ -495,15 +511,31 @@ def main():
     peak, peak_kind = load_peaks()
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (nl, kms, kcells) = dom
-    bytes_launch = kcells * BYTES_PER_CELL[name] / max(nl, 1)
-    achieved = bytes_launch / (kms / max(nl, 1) * 1e-3) / 1e9 if nl else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": name, "launches": nl, "avg_launch_us": kms / max(nl, 1) * 1e3,
-                "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_kind,
-                "share_of_step_time": kms / prof_step_ms if prof_step_ms else None,
-                "measured": "CUDA events around each finest-level launch of this kernel during one profiled "
-                            "solve right after the timed steps (direct launches instead of graph replay)",
-                "kernel_classes": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    launch_s = kms / max(nl, 1) * 1e-3
+    common = {"kernel": name, "launches": nl, "avg_launch_us": launch_s * 1e6,
+              "share_of_step_time": kms / prof_step_ms if prof_step_ms else None,
+              "measured": "CUDA events around each finest-level launch of this kernel during one profiled "
+                          "solve right after the timed steps (direct launches instead of graph replay)",
+              "kernel_classes": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    if name in FLOPS_PER_CELL:
+        # FP64-pipe bound: peak from the unit count and the maximum SM clock
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        fpeak = FP64_FMA_PER_SM_CLK * 2 * sms * mhz * 1e6 / 1e9
+        flops_launch = kcells * FLOPS_PER_CELL[name] / max(nl, 1)
+        achieved = flops_launch / launch_s / 1e9 if nl else 0.0
+        roofline = dict({"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "GFLOP/s (FP64)",
+                         "frac": achieved / fpeak, "traffic": TRAFFIC_PER_LAUNCH.get(name),
+                         "algorithmic_flops_per_launch": flops_launch,
+                         "peak_source": "derived: %d FP64 FMA/SM/clock x 2 x %d SMs x %.0f MHz"
+                                        % (FP64_FMA_PER_SM_CLK, sms, mhz)}, **common)
+    else:
+        bytes_launch = kcells * BYTES_PER_CELL[name] / max(nl, 1)
+        achieved = bytes_launch / launch_s / 1e9 if nl else 0.0
+        roofline = dict({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(name),
+                         "algorithmic_bytes_per_launch": bytes_launch,
+                         "peak_source": peak_kind}, **common)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
