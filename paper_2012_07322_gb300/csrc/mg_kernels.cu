@@ -164,24 +164,27 @@ template <typename T, int TX>
 __device__ __forceinline__ void rb_fix_ghosts(const LevelView<T>& L, T* P, int i0, int j0, int p) {
   constexpr int BX = RbShape<TX>::BX, NY = RB_TY + 2, NX = TX + 2;
   const bool xl = i0 == 0, xh = i0 + TX == L.n0, yl = j0 == 0, yh = j0 + RB_TY == L.n1;
-  for (int t = threadIdx.x; t < 2 * NY + 2 * NX; t += RB_THREADS) {
-    if (t < 2 * NY) {  // i ghosts, rows y = -1 .. TY
-      const int y = t % NY - 1, j = j0 + y;
-      const bool hi = t >= NY;
-      if ((hi ? !xh : !xl) || j < 0 || j >= L.n1) continue;
+  const int t = threadIdx.x;
+  // i ghosts of rows y = -1 .. TY on the low / high faces (threads 0 .. 2 NY)
+  if (t < 2 * NY) {
+    const bool hi = t >= NY;
+    const int y = (hi ? t - NY : t) - 1, j = j0 + y;
+    if ((hi ? xh : xl) && j >= 0 && j < L.n1) {
       const int xs = hi ? TX - 1 : 0, xg = hi ? TX : -1;
       const T fac = hi ? outer_factor(L, L.n0, j, p, L.n0 - 1, j, p) : outer_factor(L, -1, j, p, 0, j, p);
       P[(xg + RB_HX) + (y + RB_HY) * BX] = fac * P[(xs + RB_HX) + (y + RB_HY) * BX];
-    } else {  // j ghosts, columns x = -1 .. TX
-      const int u = t - 2 * NY;
-      const int x = u % NX - 1, i = i0 + x;
+    }
+  }
+  // j ghosts of columns x = -1 .. TX, only on blocks at a j face
+  if (yl || yh)
+    for (int u = t; u < 2 * NX; u += RB_THREADS) {
       const bool hi = u >= NX;
-      if ((hi ? !yh : !yl) || i < 0 || i >= L.n0) continue;
+      const int x = (hi ? u - NX : u) - 1, i = i0 + x;
+      if (!(hi ? yh : yl) || i < 0 || i >= L.n0) continue;
       const int ys = hi ? RB_TY - 1 : 0, yg = hi ? RB_TY : -1;
       const T fac = hi ? outer_factor(L, i, L.n1, p, i, L.n1 - 1, p) : outer_factor(L, i, -1, p, i, 0, p);
       P[(x + RB_HX) + (yg + RB_HY) * BX] = fac * P[(x + RB_HX) + (ys + RB_HY) * BX];
     }
-  }
 }
 
 // Ghost plane pg (-1 or n2) from the staged plane ps next to it.
@@ -326,6 +329,10 @@ __global__ void k_fill_ghosts(LevelView<T> L, T* __restrict__ u, int comp) {
 // A thread walks RES_KZ planes (k strided by blockDim.z) so that the block
 // reduction of the norms is paid once per RES_KZ cells.
 constexpr int RES_KZ = 4;
+// The vector residual carries three components' worth of FP64 work per
+// cell: one plane per thread and at most 128 registers (two blocks per SM)
+// spread it over more blocks.
+constexpr int RES_KZ_VEC = 1;
 
 template <typename T, int G, int KIND>
 __global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const T* __restrict__ f,
@@ -361,7 +368,7 @@ __global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const
 }
 
 template <typename T, int G>
-__global__ void k_residual_vec(LevelView<T> L, const T* __restrict__ A, const T* __restrict__ B,
+__global__ void __launch_bounds__(256, 2) k_residual_vec(LevelView<T> L, const T* __restrict__ A, const T* __restrict__ B,
                                const T* __restrict__ C, const T* __restrict__ f0, const T* __restrict__ f1,
                                const T* __restrict__ f2, T* __restrict__ r0, T* __restrict__ r1,
                                T* __restrict__ r2, float* __restrict__ q0, float* __restrict__ q1,
@@ -375,8 +382,8 @@ __global__ void k_residual_vec(LevelView<T> L, const T* __restrict__ A, const T*
     T* rs[3] = {r0, r1, r2};
     float* qs[3] = {q0, q1, q2};
 #pragma unroll 1
-    for (int it = 0; it < RES_KZ; ++it) {
-      const int k = (blockIdx.z * RES_KZ + it) * blockDim.z + threadIdx.z;
+    for (int it = 0; it < RES_KZ_VEC; ++it) {
+      const int k = (blockIdx.z * RES_KZ_VEC + it) * blockDim.z + threadIdx.z;
       if (k >= L.n2) continue;
       const long p = L.idx(i, j, k);
 #pragma unroll
@@ -843,7 +850,7 @@ void launch_residual_vec(const LevelView<T>& L, T* const V[3], const T* const f[
                          unsigned long long* red, int weighted, cudaStream_t st, float* const r32[3]) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_cells(L, b);
-  g.z = cdiv(L.n2, (long)b.z * RES_KZ);
+  g.z = cdiv(L.n2, (long)b.z * RES_KZ_VEC);
   float* q[3] = {nullptr, nullptr, nullptr};
   if (r32)
     for (int c = 0; c < 3; ++c) q[c] = r32[c];
