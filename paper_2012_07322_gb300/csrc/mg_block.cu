@@ -152,6 +152,7 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
 
 template <int G, bool VEC>
 __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_constant__ BlockCycle32 P) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   double* smd = reinterpret_cast<double*>(smem_raw + P.fp64_at);
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_cons
 template <int G>
 __global__ void k_coarse_assemble_vec(LevelView<double> L, double* __restrict__ scratch, double* __restrict__ A,
                                       int n) {
+  pdl_entry();
   const int col = blockIdx.x, cells = n / 3;
   const long ng = L.sy * (L.n2 + 2 * L.three);
   double* U[3];
@@ -245,19 +247,19 @@ __global__ void k_coarse_assemble_vec(LevelView<double> L, double* __restrict__ 
 void launch_coarse_assemble_vec(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st) {
   count_launch();
   if (L.geom == CART)
-    k_coarse_assemble_vec<CART><<<n, 256, 0, st>>>(L, scratch, A, n);
+    launch_k(k_coarse_assemble_vec<CART>, n, 256, 0, st, L, scratch, A, n);
   else if (L.geom == CYL)
-    k_coarse_assemble_vec<CYL><<<n, 256, 0, st>>>(L, scratch, A, n);
+    launch_k(k_coarse_assemble_vec<CYL>, n, 256, 0, st, L, scratch, A, n);
   else
-    k_coarse_assemble_vec<SPH><<<n, 256, 0, st>>>(L, scratch, A, n);
+    launch_k(k_coarse_assemble_vec<SPH>, n, 256, 0, st, L, scratch, A, n);
 }
 
 template <int G>
 static void launch_g(const BlockCycle32& P, cudaStream_t st) {
   if (P.vec)
-    k_block_vcycle32<G, true><<<1, BC_THREADS, P.smem, st>>>(P);
+    launch_k(k_block_vcycle32<G, true>, 1, BC_THREADS, P.smem, st, P);
   else
-    k_block_vcycle32<G, false><<<1, BC_THREADS, P.smem, st>>>(P);
+    launch_k(k_block_vcycle32<G, false>, 1, BC_THREADS, P.smem, st, P);
 }
 
 void launch_block_vcycle32(const BlockCycle32& P, int geom, cudaStream_t st) {

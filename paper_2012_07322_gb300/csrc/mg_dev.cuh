@@ -13,6 +13,17 @@
 
 namespace gmg {
 
+// Programmatic dependent launch (every kernel is launched with it, see
+// launch_k): wait until the preceding kernel in the stream has completed and
+// its writes are visible (a no-op for a kernel launched without it), then
+// allow the next kernel to be scheduled while this one runs.  Called first
+// in every kernel, so no kernel touches memory before its predecessor is
+// done; what it saves is the launch latency between dependent kernels.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 enum Geom { CART = 0, CYL = 1, SPH = 2 };
 enum Bc { BC_ROBIN = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2 };
 enum Kind { EQ_PSI = 0, EQ_LIN = 1, EQ_VEC = 2 };

@@ -82,8 +82,7 @@ struct mg_hierarchy {
   // boundary rule (transposed), state 0 not built, 1 built, -1 unavailable
   double* cinv[3] = {};
   int cinv_state[3] = {0, 0, 0};
-  double* d_aa_part = nullptr;
-  double* h_aa_part = nullptr;
+  double* d_aa_part = nullptr;  // AA_SCRATCH_DOUBLES of device scratch
   bool prof_on = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_cls;
@@ -527,7 +526,8 @@ int finest_norm(mg_hierarchy* H, const Eq& e, double* rel) {
   }
   prof_end(H, tok);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(H->h_red, H->d_red, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, H->st));
+  // slot 3: status of this cycle's mixing solve (read by run_solve)
+  CK(cudaMemcpyAsync(H->h_red, H->d_red, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, H->st));
   CK(cudaStreamSynchronize(H->st));
   const double num = bits_to_double(H->h_red[1]), den = bits_to_double(H->h_red[2]);
   if (std::isinf(num) || std::isinf(den) || std::isnan(num) || std::isnan(den)) {
@@ -846,40 +846,6 @@ int run_cycle_map(mg_hierarchy* H, const Eq& e) {
   return MG_OK;
 }
 
-// Small SPD solve (M + lambda I) y = b, lambda = 1e-12 max diag(M), by
-// Cholesky; -1 if M is degenerate.
-int gram_solve(int m, const double* M, const double* b, double* y) {
-  double A[AA_MAX * AA_MAX], Lc[AA_MAX * AA_MAX], z[AA_MAX];
-  double dmax = 0.0;
-  for (int i = 0; i < m; ++i) dmax = std::max(dmax, M[i * m + i]);
-  if (!(dmax > 0.0)) return -1;
-  for (int i = 0; i < m * m; ++i) A[i] = M[i];
-  for (int i = 0; i < m; ++i) A[i * m + i] += 1e-12 * dmax;
-  for (int i = 0; i < m; ++i) {
-    for (int j = 0; j <= i; ++j) {
-      double acc = A[i * m + j];
-      for (int k = 0; k < j; ++k) acc -= Lc[i * m + k] * Lc[j * m + k];
-      if (i == j) {
-        if (!(acc > 0.0)) return -1;
-        Lc[i * m + i] = std::sqrt(acc);
-      } else {
-        Lc[i * m + j] = acc / Lc[j * m + j];
-      }
-    }
-  }
-  for (int i = 0; i < m; ++i) {
-    double acc = b[i];
-    for (int k = 0; k < i; ++k) acc -= Lc[i * m + k] * z[k];
-    z[i] = acc / Lc[i * m + i];
-  }
-  for (int i = m - 1; i >= 0; --i) {
-    double acc = z[i];
-    for (int k = i + 1; k < m; ++k) acc -= Lc[k * m + i] * y[k];
-    y[i] = acc / Lc[i * m + i];
-  }
-  return 0;
-}
-
 // Mixing storage: x, fprev, gprev (FP64) and 2 m history columns of
 // col_bytes per value, each ncomp arrays of L0.ng values.
 int ensure_aa(mg_hierarchy* H, int ncomp, int m, size_t col_bytes) {
@@ -893,9 +859,12 @@ int ensure_aa(mg_hierarchy* H, int ncomp, int m, size_t col_bytes) {
     H->aa_bytes = need;
   }
   if (!H->d_aa_part) {
-    const size_t pb = sizeof(double) * AA_BLOCKS * 2 * AA_MAX;
-    if (cudaMalloc(&H->d_aa_part, pb) != cudaSuccess) return fail(MG_ERR_OOM, "mixing scratch failed");
-    if (cudaMallocHost(&H->h_aa_part, pb) != cudaSuccess) return fail(MG_ERR_OOM, "mixing scratch failed");
+    if (cudaMalloc(&H->d_aa_part, sizeof(double) * AA_SCRATCH_DOUBLES) != cudaSuccess) {
+      H->d_aa_part = nullptr;
+      return fail(MG_ERR_OOM, "mixing scratch failed");
+    }
+    // the finished-block counter starts at zero
+    CK(cudaMemsetAsync(H->d_aa_part, 0, sizeof(double) * AA_SCRATCH_DOUBLES, H->st));
   }
   return MG_OK;
 }
@@ -998,7 +967,6 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   // history columns in FP32 in mixed precision (mg_accel.cu)
   double *ax = nullptr, *afp = nullptr, *agp = nullptr, *adF = nullptr, *adG = nullptr;
   float *adF32 = nullptr, *adG32 = nullptr;
-  double M[AA_MAX * AA_MAX] = {0};
   int ncol = 0, head = 0;
   if (m > 0) {
     if ((st = ensure_aa(H, e.ncomp, m, mixed ? sizeof(float) : sizeof(double)))) return st;
@@ -1033,69 +1001,44 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
       status = MG_ERR_STALLED;
       break;
     }
-    if (m > 0)
+    // x holds the iterate the cycle starts from: copied once, then kept by
+    // the mixing kernels
+    if (m > 0 && cyc == 0)
       for (int c = 0; c < e.ncomp; ++c)
         CK(cudaMemcpyAsync(ax + (long)c * stride, L0.u[c], sizeof(double) * L0.ng, cudaMemcpyDeviceToDevice,
                            H->st));
     if ((st = run_cycle_map(H, e))) return st;
+    bool mixed_step = false;
     if (m > 0) {
-      const int first = cyc == 0;
-      const int slot = head;
-      if (mixed)
-        launch_aa_update<float>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF32 + (long)slot * vlen,
-                                adG32 + (long)slot * vlen, first, H->st);
-      else
-        launch_aa_update<double>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF + (long)slot * vlen,
-                                 adG + (long)slot * vlen, first, H->st);
-      if (!first) {
+      // dF, dG of this cycle go to ring slot head (none on the first cycle)
+      AACols cols{};
+      if (cyc > 0) {
+        const int slot = head;
         head = (head + 1) % m;
         if (ncol < m) ++ncol;
-      }
-      if (ncol > 0) {
-        AACols cols{};
         cols.n = ncol;
-        for (int a = 0; a < ncol; ++a) cols.slot[a] = (head - ncol + a + m) % m;   // oldest first
+        for (int a = 0; a < ncol; ++a) cols.slot[a] = (slot - ncol + 1 + a + m) % m;  // oldest first
+      }
+      double* scr = H->d_aa_part;
+      if (mixed)
+        launch_aa_update_dots<float>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF32, adG32, cols, scr,
+                                     H->d_red + 3, H->st);
+      else
+        launch_aa_update_dots<double>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF, adG, cols, scr,
+                                      H->d_red + 3, H->st);
+      if (cols.n > 0) {
         if (mixed)
-          launch_aa_dots<float>(L0.v64, e.ncomp, stride, afp, adF32, cols, first ? -1 : slot, H->d_aa_part,
-                                H->st);
+          launch_aa_combine<float>(L0.v64, e.ncomp, stride, L0.u, ax, adG32, cols, scr, H->d_red + 3, H->st);
         else
-          launch_aa_dots<double>(L0.v64, e.ncomp, stride, afp, adF, cols, first ? -1 : slot, H->d_aa_part, H->st);
-        CK(cudaMemcpyAsync(H->h_aa_part, H->d_aa_part, sizeof(double) * AA_BLOCKS * 2 * AA_MAX,
-                           cudaMemcpyDeviceToHost, H->st));
-        CK(cudaStreamSynchronize(H->st));
-        double bvec[AA_MAX], newrow[AA_MAX];
-        for (int a = 0; a < ncol; ++a) {
-          double sb = 0.0, sn = 0.0;
-          for (int blk = 0; blk < AA_BLOCKS; ++blk) {
-            sb += H->h_aa_part[(long)blk * 2 * AA_MAX + a];
-            sn += H->h_aa_part[(long)blk * 2 * AA_MAX + AA_MAX + a];
-          }
-          bvec[a] = sb;
-          newrow[a] = sn;
-        }
-        if (!first)
-          for (int a = 0; a < ncol; ++a) {
-            M[slot * AA_MAX + cols.slot[a]] = newrow[a];
-            M[cols.slot[a] * AA_MAX + slot] = newrow[a];
-          }
-        double Ms[AA_MAX * AA_MAX], gam[AA_MAX];
-        for (int a = 0; a < ncol; ++a)
-          for (int b = 0; b < ncol; ++b) Ms[a * ncol + b] = M[cols.slot[a] * AA_MAX + cols.slot[b]];
-        if (gram_solve(ncol, Ms, bvec, gam) == 0) {
-          for (int a = 0; a < ncol; ++a) cols.gamma[a] = gam[a];
-          if (mixed)
-            launch_aa_combine<float>(L0.v64, e.ncomp, stride, L0.u, adG32, cols, H->st);
-          else
-            launch_aa_combine<double>(L0.v64, e.ncomp, stride, L0.u, adG, cols, H->st);
-          if (e.kind == EQ_VEC) fill_all64(H, e, 0);
-        } else {
-          ncol = 0;  // degenerate history: restart the mixing
-        }
+          launch_aa_combine<double>(L0.v64, e.ncomp, stride, L0.u, ax, adG, cols, scr, H->d_red + 3, H->st);
+        if (e.kind == EQ_VEC) fill_all64(H, e, 0);
+        mixed_step = true;
       }
     }
     ++cyc;
     st = finest_norm(H, e, &rel);
     if (st) return st;
+    if (mixed_step && H->h_red[3] != 0) ncol = 0;  // degenerate history: restart the mixing
     hist.push_back(rel);
   }
   CK(cudaGetLastError());
@@ -1319,7 +1262,6 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   for (double* p : H->cinv)
     if (p) cudaFree(p);
   if (H->d_aa_part) cudaFree(H->d_aa_part);
-  if (H->h_aa_part) cudaFreeHost(H->h_aa_part);
   for (GraphEntry& g : H->graphs) cudaGraphExecDestroy(g.exec);
   if (H->own_stream) cudaStreamDestroy(H->st);
   if (H->ev_in) cudaEventDestroy(H->ev_in);

@@ -1,11 +1,33 @@
 // Host-side declarations shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <utility>
+
 #include "mg_dev.cuh"
 
 struct mg_hierarchy;
 
 namespace gmg {
+
+// Kernel launch with programmatic stream serialisation: the kernel may be
+// scheduled before its predecessor in the stream has finished and waits for
+// it in pdl_entry().  Inside a captured graph the dependency becomes a
+// programmatic edge.
+template <typename... K, typename... A>
+inline void launch_k(void (*k)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // Record a message for mg_last_error on the calling thread; returns status.
 int set_last_error(int status, const char* msg);
@@ -117,25 +139,41 @@ void launch_xcfc_alpha_out(const LevelView<double>& L, const double* dap, const 
                            cudaStream_t st);
 
 // Anderson mixing (mg_accel.cu): live ring slots of the difference columns
-// in age order, with their mixing weights.
+// in age order (the newest last).
 constexpr int AA_MAX = 16;
-constexpr int AA_BLOCKS = 304;     // 2 x 152 SMs
-constexpr int AA_DOT_X = 64;       // threads per column in the dot-product kernel
+constexpr int AA_BLOCKS = 304;  // 2 x 152 SMs: partial sums of the dot products
 struct AACols {
   int n;
   int slot[AA_MAX];
-  double gamma[AA_MAX];
 };
-// History columns TC: double, or float in mixed precision.
+// Device scratch of the mixing step (doubles): AA_BLOCKS x 2 AA_MAX partial
+// sums, the Gram matrix (AA_MAX x AA_MAX), the weights (AA_MAX) and a
+// finished-block counter (zero between launches).
+constexpr size_t AA_SCRATCH_DOUBLES = (size_t)AA_BLOCKS * 2 * AA_MAX + AA_MAX * AA_MAX + AA_MAX + 1;
+struct AAScratch {
+  double* part;
+  double* M;
+  double* gamma;
+  unsigned int* done;
+};
+inline AAScratch aa_scratch(double* s) {
+  AAScratch o;
+  o.part = s;
+  o.M = s + (size_t)AA_BLOCKS * 2 * AA_MAX;
+  o.gamma = o.M + AA_MAX * AA_MAX;
+  o.done = reinterpret_cast<unsigned int*>(o.gamma + AA_MAX);
+  return o;
+}
+// History columns TC: double, or float in mixed precision.  status gets the
+// least-squares outcome (0 solved, 1 degenerate) when cols.n > 0.
 template <typename TC>
-void launch_aa_update(const LevelView<double>& L, int ncomp, long stride, double* const g[3], const double* x,
-                      double* fprev, double* gprev, TC* dF, TC* dG, int first, cudaStream_t st);
+void launch_aa_update_dots(const LevelView<double>& L, int ncomp, long stride, double* const g[3], double* x,
+                           double* fprev, double* gprev, TC* dF, TC* dG, const AACols& cols, double* scratch,
+                           unsigned long long* status, cudaStream_t st);
 template <typename TC>
-void launch_aa_dots(const LevelView<double>& L, int ncomp, long stride, const double* f, const TC* dF,
-                    const AACols& cols, int newcol, double* part, cudaStream_t st);
-template <typename TC>
-void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], const TC* dG,
-                       const AACols& cols, cudaStream_t st);
+void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], double* x,
+                       const TC* dG, const AACols& cols, const double* scratch, const unsigned long long* status,
+                       cudaStream_t st);
 
 // One-block FP32 correction V-cycle over the coarse levels (mg_block.cu):
 // the levels l0 .. l0 + nl - 1 of a hierarchy, the last the coarsest, all

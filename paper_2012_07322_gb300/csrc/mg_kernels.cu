@@ -23,6 +23,7 @@ static inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b)
 template <typename T, int G, int KIND>
 __global__ void k_smooth_scalar(LevelView<T> L, T* __restrict__ u, const T* __restrict__ f,
                                 const T* __restrict__ s0, const T* __restrict__ s1, int colour) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -34,6 +35,7 @@ __global__ void k_smooth_scalar(LevelView<T> L, T* __restrict__ u, const T* __re
 template <typename T, int G>
 __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
                              const T* __restrict__ f, int comp, int colour) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -233,6 +235,7 @@ template <typename T, int TX, bool HAS_C>
 __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb_cart(LevelView<T> L, const T* __restrict__ uin,
                                                               T* __restrict__ uout, const T* __restrict__ f,
                                                               const T* __restrict__ c, int zc) {
+  pdl_entry();
   constexpr int BX = RbShape<TX>::BX, BP = RbShape<TX>::BP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);
@@ -317,6 +320,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb_cart(LevelView<T> L, co
 
 template <typename T>
 __global__ void k_fill_ghosts(LevelView<T> L, T* __restrict__ u, int comp) {
+  pdl_entry();
   const long n = ghost_count(L);
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x)
     fill_one_ghost(L, u, comp, g);
@@ -339,6 +343,7 @@ __global__ void k_residual_scalar(LevelView<T> L, const T* __restrict__ u, const
                                   const T* __restrict__ s0, const T* __restrict__ s1, T* __restrict__ r,
                                   float* __restrict__ r32, float* __restrict__ k32, unsigned long long* red,
                                   int weighted) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   unsigned long long m[3] = {0ULL, 0ULL, 0ULL};
@@ -373,6 +378,7 @@ __global__ void __launch_bounds__(256, 2) k_residual_vec(LevelView<T> L, const T
                                const T* __restrict__ f2, T* __restrict__ r0, T* __restrict__ r1,
                                T* __restrict__ r2, float* __restrict__ q0, float* __restrict__ q1,
                                float* __restrict__ q2, unsigned long long* red, int weighted) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   unsigned long long m[3] = {0ULL, 0ULL, 0ULL};
@@ -410,6 +416,7 @@ __global__ void __launch_bounds__(256, 2) k_residual_vec(LevelView<T> L, const T
 template <typename T, int G, int KIND>
 __global__ void k_apply_scalar(LevelView<T> L, const T* __restrict__ u, const T* __restrict__ s0,
                                const T* __restrict__ s1, T* __restrict__ out, int add) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -424,6 +431,7 @@ template <typename T, int G>
 __global__ void k_apply_vec(LevelView<T> L, const T* __restrict__ A, const T* __restrict__ B,
                             const T* __restrict__ C, T* __restrict__ o0, T* __restrict__ o1,
                             T* __restrict__ o2, int add) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -449,6 +457,7 @@ __global__ void k_restrict(LevelView<T> F, LevelView<T> Cv, int nf, const T* __r
                            const T* __restrict__ a1, const T* __restrict__ a2, const T* __restrict__ a3,
                            T* __restrict__ b0, T* __restrict__ b1, T* __restrict__ b2, T* __restrict__ b3,
                            T* __restrict__ copy0, T* __restrict__ copy1, T* __restrict__ copy2) {
+  pdl_entry();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z * blockDim.z + threadIdx.z;
@@ -463,6 +472,7 @@ __global__ void k_restrict(LevelView<T> F, LevelView<T> Cv, int nf, const T* __r
 template <typename T>
 __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, const T* __restrict__ uH,
                           const T* __restrict__ uhH, int comp) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -481,6 +491,7 @@ __device__ __forceinline__ void block_copy(T* dst, const T* src, long n) {
 template <typename T, int G, int KIND>
 __global__ void k_coarse_scalar(LevelView<T> L, T* __restrict__ u, const T* __restrict__ f,
                                 const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps, int use_smem) {
+  pdl_entry();
   if (!use_smem) {
     coarse_scalar_body<T, G, KIND>(L, u, f, s0, s1, max_sweeps);
     return;
@@ -506,6 +517,7 @@ template <typename T, int G>
 __global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
                              const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
                              int max_sweeps, int use_smem) {
+  pdl_entry();
   if (!use_smem) {
     coarse_vec_body<T, G>(L, A, B, C, f0, f1, f2, max_sweeps);
     return;
@@ -534,51 +546,6 @@ __global__ void k_coarse_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
 // ------------------------------------------------------------- helpers
 
 // u -= mean(u interior); sums in a fixed order (deterministic).
-// Elementwise passes over the interior in groups of four consecutive cells
-// of a row: rows start 16-byte aligned and n0 (a power of two) is a
-// multiple of 4 on every level but the smallest, which take one cell at a
-// time.  Values travel as doubles (exact for both storage types).
-template <typename T>
-__device__ __forceinline__ long group4(const LevelView<T>& L, long q) {
-  const int i = (int)(q & ((L.n0 >> 2) - 1)) << 2;
-  const long jk = q >> (L.ln0 - 2);
-  return L.idx(i, (int)(jk & (L.n1 - 1)), (int)(jk >> L.ln1));
-}
-__device__ __forceinline__ void ld4(const float* p, double (&v)[4]) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-}
-__device__ __forceinline__ void st4(float* p, const double (&v)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
-}
-__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
-  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
-}
-template <typename T>
-__device__ __forceinline__ long interior_p(const LevelView<T>& L, long q) {
-  int i, j, k;
-  L.cell(q, i, j, k);
-  return L.idx(i, j, k);
-}
-
-// Sum of a block's doubles into part[blockIdx.x] (fixed order).
-__device__ __forceinline__ void block_sum_to(double s, double* part) {
-  __shared__ double sm[32];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double b = threadIdx.x < (blockDim.x + 31) / 32 ? sm[threadIdx.x] : 0.0;
-    b = warp_sum(b);
-    if (threadIdx.x == 0) part[blockIdx.x] = b;
-  }
-}
-
 // Mean of the interior from nparts partial sums (warp 0 of every block).
 __device__ __forceinline__ double mean_of(const double* __restrict__ part, int nparts, double ncells) {
   __shared__ double mean;
@@ -594,6 +561,7 @@ __device__ __forceinline__ double mean_of(const double* __restrict__ part, int n
 
 template <typename T>
 __global__ void k_partial_sum(LevelView<T> L, const T* __restrict__ u, double* __restrict__ part) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   const long stride = (long)gridDim.x * blockDim.x;
   double s = 0.0;
@@ -611,6 +579,7 @@ __global__ void k_partial_sum(LevelView<T> L, const T* __restrict__ u, double* _
 
 template <typename T>
 __global__ void k_sub_mean(LevelView<T> L, T* __restrict__ u, const double* __restrict__ part, int nparts) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   const double mean = mean_of(part, nparts, (double)n);
   const long stride = (long)gridDim.x * blockDim.x;
@@ -633,6 +602,7 @@ __global__ void k_sub_mean(LevelView<T> L, T* __restrict__ u, const double* __re
 // Interior <-> ghosted copies, FP64 <-> storage type conversions.
 template <typename A, typename B>
 __global__ void k_copy_in(LevelView<B> L, const A* __restrict__ src, B* __restrict__ dst, A shift) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -642,6 +612,7 @@ __global__ void k_copy_in(LevelView<B> L, const A* __restrict__ src, B* __restri
 }
 template <typename A, typename B>
 __global__ void k_copy_out(LevelView<A> L, const A* __restrict__ src, B* __restrict__ dst, A shift) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -652,6 +623,7 @@ __global__ void k_copy_out(LevelView<A> L, const A* __restrict__ src, B* __restr
 // Ghosted-to-ghosted interior conversion (e.g. FP64 residual -> FP32 rhs).
 template <typename A, typename B>
 __global__ void k_convert(LevelView<A> L, const A* __restrict__ src, B* __restrict__ dst) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   const long stride = (long)gridDim.x * blockDim.x;
   if (L.n0 >= 4) {
@@ -673,6 +645,7 @@ __global__ void k_convert(LevelView<A> L, const A* __restrict__ src, B* __restri
 template <typename T>
 __global__ void k_add_correction(LevelView<double> L, double* __restrict__ u, const T* __restrict__ e,
                                  double* __restrict__ part) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   const long stride = (long)gridDim.x * blockDim.x;
   double s = 0.0;
@@ -724,8 +697,8 @@ void launch_smooth_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
                           int colour, cudaStream_t st) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_colour(L, b);
-  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_smooth_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, colour);
-                    else k_smooth_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, colour));
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) launch_k(k_smooth_scalar<T, GG, EQ_PSI>, g, b, 0, st, L, u, f, s0, s1, colour);
+                    else launch_k(k_smooth_scalar<T, GG, EQ_LIN>, g, b, 0, st, L, u, f, s0, s1, colour));
 }
 
 template <typename T, int TX>
@@ -799,9 +772,9 @@ static void launch_rb(const LevelView<T>& L, const T* uin, T* uout, const T* f, 
   const int zc = fused_sweep_chunk(L, TX, c != nullptr);
   dim3 g(cdiv(L.n0, TX), cdiv(L.n1, RB_TY), cdiv(L.n2, zc));
   if (c)
-    k_sweep_rb_cart<T, TX, true><<<g, RB_THREADS, fused_sweep_smem<T, TX>(true), st>>>(L, uin, uout, f, c, zc);
+    launch_k(k_sweep_rb_cart<T, TX, true>, g, RB_THREADS, fused_sweep_smem<T, TX>(true), st, L, uin, uout, f, c, zc);
   else
-    k_sweep_rb_cart<T, TX, false><<<g, RB_THREADS, fused_sweep_smem<T, TX>(false), st>>>(L, uin, uout, f, nullptr,
+    launch_k(k_sweep_rb_cart<T, TX, false>, g, RB_THREADS, fused_sweep_smem<T, TX>(false), st, L, uin, uout, f, nullptr,
                                                                                          zc);
 }
 
@@ -824,14 +797,14 @@ void launch_fill_ghosts(const LevelView<T>& L, T* u, int comp, cudaStream_t st) 
   count_launch();
   const long nk = L.n2 + 2 * L.three;
   const long n = 2L * (L.n1 + 2) * nk + 2L * L.n0 * nk + (L.three ? 2L * L.n0 * L.n1 : 0L);
-  k_fill_ghosts<T><<<grid_flat(n, 256), 256, 0, st>>>(L, u, comp);
+  launch_k(k_fill_ghosts<T>, grid_flat(n, 256), 256, 0, st, L, u, comp);
 }
 
 template <typename T>
 void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_colour(L, b);
-  GMG_GEOM_DISPATCH(L.geom, k_smooth_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], f, comp, colour));
+  GMG_GEOM_DISPATCH(L.geom, launch_k(k_smooth_vec<T, GG>, g, b, 0, st, L, V[0], V[1], V[2], f, comp, colour));
 }
 
 template <typename T>
@@ -841,8 +814,8 @@ void launch_residual_scalar(const LevelView<T>& L, int kind, const T* u, const T
   count_launch();
   dim3 b = block_for(L.three), g = grid_cells(L, b);
   g.z = cdiv(L.n2, (long)b.z * RES_KZ);
-  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_residual_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, k32, red, weighted);
-                    else k_residual_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, f, s0, s1, r, r32, nullptr, red, weighted));
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) launch_k(k_residual_scalar<T, GG, EQ_PSI>, g, b, 0, st, L, u, f, s0, s1, r, r32, k32, red, weighted);
+                    else launch_k(k_residual_scalar<T, GG, EQ_LIN>, g, b, 0, st, L, u, f, s0, s1, r, r32, nullptr, red, weighted));
 }
 
 template <typename T>
@@ -854,7 +827,7 @@ void launch_residual_vec(const LevelView<T>& L, T* const V[3], const T* const f[
   float* q[3] = {nullptr, nullptr, nullptr};
   if (r32)
     for (int c = 0; c < 3; ++c) q[c] = r32[c];
-  GMG_GEOM_DISPATCH(L.geom, k_residual_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], r[0], r[1], r[2], q[0], q[1], q[2], red, weighted));
+  GMG_GEOM_DISPATCH(L.geom, launch_k(k_residual_vec<T, GG>, g, b, 0, st, L, V[0], V[1], V[2], f[0], f[1], f[2], r[0], r[1], r[2], q[0], q[1], q[2], red, weighted));
 }
 
 template <typename T>
@@ -862,15 +835,15 @@ void launch_apply_scalar(const LevelView<T>& L, int kind, const T* u, const T* s
                          cudaStream_t st) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_cells(L, b);
-  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) k_apply_scalar<T, GG, EQ_PSI><<<g, b, 0, st>>>(L, u, s0, s1, out, add);
-                    else k_apply_scalar<T, GG, EQ_LIN><<<g, b, 0, st>>>(L, u, s0, s1, out, add));
+  GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) launch_k(k_apply_scalar<T, GG, EQ_PSI>, g, b, 0, st, L, u, s0, s1, out, add);
+                    else launch_k(k_apply_scalar<T, GG, EQ_LIN>, g, b, 0, st, L, u, s0, s1, out, add));
 }
 
 template <typename T>
 void launch_apply_vec(const LevelView<T>& L, T* const V[3], T* const out[3], int add, cudaStream_t st) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_cells(L, b);
-  GMG_GEOM_DISPATCH(L.geom, k_apply_vec<T, GG><<<g, b, 0, st>>>(L, V[0], V[1], V[2], out[0], out[1], out[2], add));
+  GMG_GEOM_DISPATCH(L.geom, launch_k(k_apply_vec<T, GG>, g, b, 0, st, L, V[0], V[1], V[2], out[0], out[1], out[2], add));
 }
 
 template <typename T>
@@ -878,7 +851,7 @@ void launch_restrict(const LevelView<T>& F, const LevelView<T>& C, int nf, const
                      T* const copy[3], cudaStream_t st) {
   count_launch();
   dim3 bl = block_for(C.three), g = grid_cells(C, bl);
-  k_restrict<T><<<g, bl, 0, st>>>(F, C, nf, a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3], copy[0], copy[1],
+  launch_k(k_restrict<T>, g, bl, 0, st, F, C, nf, a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3], copy[0], copy[1],
                                    copy[2]);
 }
 
@@ -887,7 +860,7 @@ void launch_prolong(const LevelView<T>& F, const LevelView<T>& C, T* u, const T*
                     cudaStream_t st) {
   count_launch();
   dim3 b = block_for(F.three), g = grid_cells(F, b);
-  k_prolong<T><<<g, b, 0, st>>>(F, C, u, uH, uhH, comp);
+  launch_k(k_prolong<T>, g, b, 0, st, F, C, u, uH, uhH, comp);
 }
 
 // The coarsest level runs from shared memory when its ghosted arrays fit.
@@ -908,10 +881,10 @@ void launch_coarse_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
   const size_t dyn = use ? sb : 0;
   GMG_GEOM_DISPATCH(L.geom, if (kind == EQ_PSI) {
     if (dyn + 16 * 1024 > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_PSI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    k_coarse_scalar<T, GG, EQ_PSI><<<1, 256, dyn, st>>>(L, u, f, s0, s1, max_sweeps, use);
+    launch_k(k_coarse_scalar<T, GG, EQ_PSI>, 1, 256, dyn, st, L, u, f, s0, s1, max_sweeps, use);
   } else {
     if (dyn + 16 * 1024 > 48 * 1024) cudaFuncSetAttribute(k_coarse_scalar<T, GG, EQ_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    k_coarse_scalar<T, GG, EQ_LIN><<<1, 256, dyn, st>>>(L, u, f, s0, s1, max_sweeps, use);
+    launch_k(k_coarse_scalar<T, GG, EQ_LIN>, 1, 256, dyn, st, L, u, f, s0, s1, max_sweeps, use);
   });
 }
 
@@ -923,34 +896,34 @@ void launch_coarse_vec(const LevelView<T>& L, T* V[3], const T* const f[3], int 
   const size_t dyn = use ? sb : 0;
   GMG_GEOM_DISPATCH(L.geom, {
     if (dyn + 16 * 1024 > 48 * 1024) cudaFuncSetAttribute(k_coarse_vec<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    k_coarse_vec<T, GG><<<1, 256, dyn, st>>>(L, V[0], V[1], V[2], f[0], f[1], f[2], max_sweeps, use);
+    launch_k(k_coarse_vec<T, GG>, 1, 256, dyn, st, L, V[0], V[1], V[2], f[0], f[1], f[2], max_sweeps, use);
   });
 }
 
 template <typename T>
 void launch_sub_mean(const LevelView<T>& L, T* u, double* part, int nparts, cudaStream_t st, bool have_part) {
   count_launch(have_part ? 1 : 2);
-  if (!have_part) k_partial_sum<T><<<nparts, 256, 0, st>>>(L, u, part);
-  k_sub_mean<T><<<nparts, 256, 0, st>>>(L, u, part, nparts);
+  if (!have_part) launch_k(k_partial_sum<T>, nparts, 256, 0, st, L, u, part);
+  launch_k(k_sub_mean<T>, nparts, 256, 0, st, L, u, part, nparts);
 }
 
 template <typename A, typename B>
 void launch_copy_in(const LevelView<B>& L, const A* src, B* dst, A shift, cudaStream_t st) {
   count_launch();
   long n = (long)L.n0 * L.n1 * L.n2;
-  k_copy_in<A, B><<<grid_flat(n, 256), 256, 0, st>>>(L, src, dst, shift);
+  launch_k(k_copy_in<A, B>, grid_flat(n, 256), 256, 0, st, L, src, dst, shift);
 }
 template <typename A, typename B>
 void launch_copy_out(const LevelView<A>& L, const A* src, B* dst, A shift, cudaStream_t st) {
   count_launch();
   long n = (long)L.n0 * L.n1 * L.n2;
-  k_copy_out<A, B><<<grid_flat(n, 256), 256, 0, st>>>(L, src, dst, shift);
+  launch_k(k_copy_out<A, B>, grid_flat(n, 256), 256, 0, st, L, src, dst, shift);
 }
 template <typename A, typename B>
 void launch_convert(const LevelView<A>& L, const A* src, B* dst, cudaStream_t st) {
   count_launch();
   long n = (long)L.n0 * L.n1 * L.n2;
-  k_convert<A, B><<<grid_flat(L.n0 >= 4 ? n / 4 : n, 256), 256, 0, st>>>(L, src, dst);
+  launch_k(k_convert<A, B>, grid_flat(L.n0 >= 4 ? n / 4 : n, 256), 256, 0, st, L, src, dst);
 }
 template <typename T>
 void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st, double* part,
@@ -958,7 +931,7 @@ void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cu
   count_launch();
   long n = (long)L.n0 * L.n1 * L.n2;
   const unsigned g = part ? (unsigned)nparts : grid_flat(L.n0 >= 4 ? n / 4 : n, 256);
-  k_add_correction<T><<<g, 256, 0, st>>>(L, u, e, part);
+  launch_k(k_add_correction<T>, g, 256, 0, st, L, u, e, part);
 }
 
 // explicit instantiations

@@ -424,4 +424,51 @@ __device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __r
   }
 }
 
+// ------------------------------------------------- elementwise helpers
+
+// Elementwise passes over the interior in groups of four consecutive cells
+// of a row: rows start 16-byte aligned and n0 (a power of two) is a
+// multiple of 4 on every level but the smallest, which take one cell at a
+// time.  Values travel as doubles (exact for both storage types).
+template <typename T>
+__device__ __forceinline__ long group4(const LevelView<T>& L, long q) {
+  const int i = (int)(q & ((L.n0 >> 2) - 1)) << 2;
+  const long jk = q >> (L.ln0 - 2);
+  return L.idx(i, (int)(jk & (L.n1 - 1)), (int)(jk >> L.ln1));
+}
+__device__ __forceinline__ void ld4(const float* p, double (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const double (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+template <typename T>
+__device__ __forceinline__ long interior_p(const LevelView<T>& L, long q) {
+  int i, j, k;
+  L.cell(q, i, j, k);
+  return L.idx(i, j, k);
+}
+
+// Sum of a block's doubles into part[blockIdx.x] (fixed order).
+__device__ __forceinline__ void block_sum_to(double s, double* part) {
+  __shared__ double sm[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x + 31) / 32 ? sm[threadIdx.x] : 0.0;
+    b = warp_sum(b);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+  }
+}
+
 }  // namespace gmg

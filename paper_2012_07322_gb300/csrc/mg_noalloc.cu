@@ -43,6 +43,7 @@ double* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
 __global__ void k_noalloc_div(int n0, int n1, int n2, int three, double c0, double c1, double c2,
                               const double* __restrict__ B0, const double* __restrict__ B1,
                               const double* __restrict__ B2, double* __restrict__ div) {
+  gmg::pdl_entry();
   const long n = (long)n0 * n1 * n2;
   const long s1 = n0, s2 = (long)n0 * n1;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
@@ -57,6 +58,7 @@ __global__ void k_noalloc_div(int n0, int n1, int n2, int three, double c0, doub
 // Per-block sums of div^2 into part[], max |div| into *maxw (atomic).
 __global__ void k_noalloc_norms(long n, const double* __restrict__ div, double* __restrict__ part,
                                 unsigned long long* maxw) {
+  gmg::pdl_entry();
   __shared__ double sm[32];
   double s = 0.0;
   double m[1] = {0.0};
@@ -129,9 +131,9 @@ extern "C" int mg_divb_norms_noalloc(int ndim, const int n[3], const double lo[3
   long g = (cells + 255) / 256;
   if (g > NOALLOC_BLOCKS) g = NOALLOC_BLOCKS;
   gmg::count_launch(2);
-  k_noalloc_div<<<(unsigned)g, 256, 0, s>>>(n0, n1, n2, ndim == 3, c0, c1, c2, B[0], B[1],
+  gmg::launch_k(k_noalloc_div, (unsigned)g, 256, 0, s, n0, n1, n2, ndim == 3, c0, c1, c2, B[0], B[1],
                                              ndim == 3 ? B[2] : B[0], div);
-  k_noalloc_norms<<<NOALLOC_BLOCKS, 256, 0, s>>>(cells, div, part, maxw);
+  gmg::launch_k(k_noalloc_norms, NOALLOC_BLOCKS, 256, 0, s, cells, div, part, maxw);
   double hpart[NOALLOC_BLOCKS];
   unsigned long long hmax = 0;
   if (cudaMemcpyAsync(hpart, part, sizeof(hpart), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -55,6 +55,7 @@ __device__ __forceinline__ void aij_cell(const LevelView<double>& L, const doubl
 template <int G>
 __global__ void k_a2(LevelView<double> L, const double* __restrict__ a, const double* __restrict__ b,
                      const double* __restrict__ c, double* __restrict__ A2) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -69,6 +70,7 @@ __global__ void k_a2(LevelView<double> L, const double* __restrict__ a, const do
 __global__ void k_alpha_coef(LevelView<double> L, const double* __restrict__ U, const double* __restrict__ S,
                              const double* __restrict__ A2, const double* __restrict__ dpsi,
                              double* __restrict__ c) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -84,6 +86,7 @@ __global__ void k_alpha_coef(LevelView<double> L, const double* __restrict__ U, 
 // (the ghosts of both deviations carry their boundary values).
 __global__ void k_lapse_factor(long n, const double* __restrict__ dpsi, const double* __restrict__ dap,
                                double* __restrict__ s) {
+  pdl_entry();
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
     const double ip = 1.0 / (1.0 + dpsi[p]);
     const double ip2 = ip * ip;
@@ -98,6 +101,7 @@ __global__ void k_beta_rhs(LevelView<double> L, const double* __restrict__ a, co
                            const double* __restrict__ S0, const double* __restrict__ S1,
                            const double* __restrict__ S2, double* __restrict__ f0, double* __restrict__ f1,
                            double* __restrict__ f2) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -123,6 +127,7 @@ __global__ void k_beta_rhs(LevelView<double> L, const double* __restrict__ a, co
 
 __global__ void k_scale_into(LevelView<double> L, const double* __restrict__ src, double a,
                              double* __restrict__ dst) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -138,6 +143,7 @@ __global__ void k_scale_into(LevelView<double> L, const double* __restrict__ src
 __global__ void k_div_central(LevelView<double> L, const double* __restrict__ B0,
                               const double* __restrict__ B1, const double* __restrict__ B2,
                               double* __restrict__ div, double* __restrict__ part) {
+  pdl_entry();
   __shared__ double sm[32];
   const long n = (long)L.n0 * L.n1 * L.n2;
   const long s1 = L.n0, s2 = (long)L.n0 * L.n1;
@@ -165,6 +171,7 @@ __global__ void k_div_central(LevelView<double> L, const double* __restrict__ B0
 // max |div| -> red[0] (atomic), sum div^2 -> part (per block).
 __global__ void k_div_norms(LevelView<double> L, const double* __restrict__ div, double* __restrict__ part,
                             unsigned long long* red) {
+  pdl_entry();
   __shared__ double sm[32];
   const long n = (long)L.n0 * L.n1 * L.n2;
   double s = 0.0;
@@ -191,6 +198,7 @@ __global__ void k_div_norms(LevelView<double> L, const double* __restrict__ div,
 
 __global__ void k_sub_mean_into(LevelView<double> L, const double* __restrict__ div,
                                 const double* __restrict__ part, int nparts, double* __restrict__ b) {
+  pdl_entry();
   __shared__ double mean;
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -210,6 +218,7 @@ __global__ void k_sub_mean_into(LevelView<double> L, const double* __restrict__ 
 // B <- B - grad Phi (central differences, Neumann ghosts of Phi).
 __global__ void k_grad_update(LevelView<double> L, const double* __restrict__ phi, double* __restrict__ B0,
                               double* __restrict__ B1, double* __restrict__ B2) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   const double c0 = 0.5 / L.h0, c1 = 0.5 / L.h1, c2 = 0.5 / L.h2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
@@ -231,6 +240,7 @@ __global__ void k_grad_update(LevelView<double> L, const double* __restrict__ ph
 template <int G>
 __global__ void k_div_curv(LevelView<double> L, const double* __restrict__ B0, const double* __restrict__ B1,
                            const double* __restrict__ B2, double* __restrict__ div, double* __restrict__ part) {
+  pdl_entry();
   __shared__ double sm[32];
   const long n = (long)L.n0 * L.n1 * L.n2;
   double acc = 0.0;
@@ -266,6 +276,7 @@ __global__ void k_div_curv(LevelView<double> L, const double* __restrict__ B0, c
 __global__ void k_sub_wmean_into(LevelView<double> L, const double* __restrict__ div,
                                  const double* __restrict__ part, int nparts, double wsum,
                                  double* __restrict__ b) {
+  pdl_entry();
   __shared__ double mean;
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -288,6 +299,7 @@ __global__ void k_sub_wmean_into(LevelView<double> L, const double* __restrict__
 template <int G>
 __global__ void k_grad_update_curv(LevelView<double> L, const double* __restrict__ phi, double* __restrict__ B0,
                                    double* __restrict__ B1, double* __restrict__ B2) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -313,6 +325,7 @@ __global__ void k_grad_update_curv(LevelView<double> L, const double* __restrict
 // solved psi deviation; and alpha = (alpha psi) / psi back to the caller.
 __global__ void k_ap_init(LevelView<double> L, const double* __restrict__ alpha, const double* __restrict__ dpsi,
                           double* __restrict__ dap) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -323,6 +336,7 @@ __global__ void k_ap_init(LevelView<double> L, const double* __restrict__ alpha,
 }
 __global__ void k_alpha_out(LevelView<double> L, const double* __restrict__ dap, const double* __restrict__ dpsi,
                             double* __restrict__ alpha) {
+  pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -343,48 +357,48 @@ __global__ void k_alpha_out(LevelView<double> L, const double* __restrict__ dap,
 void launch_xcfc_a2(const LevelView<double>& L, double* const X[3], double* A2, cudaStream_t st) {
   count_launch();
   dim3 b = blk(L.three), g = grd(L, b);
-  GEOMS(L.geom, k_a2<GG><<<g, b, 0, st>>>(L, X[0], X[1], X[2], A2));
+  GEOMS(L.geom, launch_k(k_a2<GG>, g, b, 0, st, L, X[0], X[1], X[2], A2));
 }
 
 void launch_xcfc_alpha_coef(const LevelView<double>& L, const double* U, const double* S, const double* A2,
                             const double* dpsi, double* c, cudaStream_t st) {
   count_launch();
   dim3 b = blk(L.three), g = grd(L, b);
-  k_alpha_coef<<<g, b, 0, st>>>(L, U, S, A2, dpsi, c);
+  launch_k(k_alpha_coef, g, b, 0, st, L, U, S, A2, dpsi, c);
 }
 
 void launch_xcfc_beta_rhs(const LevelView<double>& L, double* const X[3], const double* dpsi, const double* dap,
                           double* sg, double* const Si[3], double* const f[3], cudaStream_t st) {
   count_launch(2);
   const long ng = L.sy * (L.n2 + 2 * L.three);
-  k_lapse_factor<<<(unsigned)((ng + 255) / 256 > 4096 ? 4096 : (ng + 255) / 256), 256, 0, st>>>(ng, dpsi, dap,
+  launch_k(k_lapse_factor, (unsigned)((ng + 255) / 256 > 4096 ? 4096 : (ng + 255) / 256), 256, 0, st, ng, dpsi, dap,
                                                                                                   sg);
   dim3 b = blk(L.three), g = grd(L, b);
-  GEOMS(L.geom, k_beta_rhs<GG><<<g, b, 0, st>>>(L, X[0], X[1], X[2], sg, Si[0], Si[1], Si[2], f[0], f[1], f[2]));
+  GEOMS(L.geom, launch_k(k_beta_rhs<GG>, g, b, 0, st, L, X[0], X[1], X[2], sg, Si[0], Si[1], Si[2], f[0], f[1], f[2]));
 }
 
 void launch_scale_into(const LevelView<double>& L, const double* src, double a, double* dst, cudaStream_t st) {
   count_launch();
   dim3 b = blk(L.three), g = grd(L, b);
-  k_scale_into<<<g, b, 0, st>>>(L, src, a, dst);
+  launch_k(k_scale_into, g, b, 0, st, L, src, a, dst);
 }
 
 void launch_div_central(const LevelView<double>& L, double* const B[3], double* div, double* part, int nparts,
                         cudaStream_t st) {
   count_launch();
-  k_div_central<<<nparts, 256, 0, st>>>(L, B[0], B[1], B[2], div, part);
+  launch_k(k_div_central, nparts, 256, 0, st, L, B[0], B[1], B[2], div, part);
 }
 
 void launch_div_norms(const LevelView<double>& L, const double* div, double* part, int nparts,
                       unsigned long long* red, cudaStream_t st) {
   count_launch();
-  k_div_norms<<<nparts, 256, 0, st>>>(L, div, part, red);
+  launch_k(k_div_norms, nparts, 256, 0, st, L, div, part, red);
 }
 
 void launch_sub_mean_into(const LevelView<double>& L, const double* div, const double* part, int nparts,
                           double* b, cudaStream_t st) {
   count_launch();
-  k_sub_mean_into<<<nparts, 256, 0, st>>>(L, div, part, nparts, b);
+  launch_k(k_sub_mean_into, nparts, 256, 0, st, L, div, part, nparts, b);
 }
 
 void launch_grad_update(const LevelView<double>& L, const double* phi, double* const B[3], cudaStream_t st) {
@@ -392,22 +406,22 @@ void launch_grad_update(const LevelView<double>& L, const double* phi, double* c
   const long n = (long)L.n0 * L.n1 * L.n2;
   long g = (n + 255) / 256;
   if (g > 8192) g = 8192;
-  k_grad_update<<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
+  launch_k(k_grad_update, (unsigned)g, 256, 0, st, L, phi, B[0], B[1], B[2]);
 }
 
 void launch_div_curv(const LevelView<double>& L, double* const Bg[3], double* div, double* part, int nparts,
                      cudaStream_t st) {
   count_launch();
   if (L.geom == CYL)
-    k_div_curv<CYL><<<nparts, 256, 0, st>>>(L, Bg[0], Bg[1], Bg[2], div, part);
+    launch_k(k_div_curv<CYL>, nparts, 256, 0, st, L, Bg[0], Bg[1], Bg[2], div, part);
   else
-    k_div_curv<SPH><<<nparts, 256, 0, st>>>(L, Bg[0], Bg[1], Bg[2], div, part);
+    launch_k(k_div_curv<SPH>, nparts, 256, 0, st, L, Bg[0], Bg[1], Bg[2], div, part);
 }
 
 void launch_sub_wmean_into(const LevelView<double>& L, const double* div, const double* part, int nparts,
                            double wsum, double* b, cudaStream_t st) {
   count_launch();
-  k_sub_wmean_into<<<nparts, 256, 0, st>>>(L, div, part, nparts, wsum, b);
+  launch_k(k_sub_wmean_into, nparts, 256, 0, st, L, div, part, nparts, wsum, b);
 }
 
 void launch_grad_update_curv(const LevelView<double>& L, const double* phi, double* const B[3], cudaStream_t st) {
@@ -416,9 +430,9 @@ void launch_grad_update_curv(const LevelView<double>& L, const double* phi, doub
   long g = (n + 255) / 256;
   if (g > 8192) g = 8192;
   if (L.geom == CYL)
-    k_grad_update_curv<CYL><<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
+    launch_k(k_grad_update_curv<CYL>, (unsigned)g, 256, 0, st, L, phi, B[0], B[1], B[2]);
   else
-    k_grad_update_curv<SPH><<<(unsigned)g, 256, 0, st>>>(L, phi, B[0], B[1], B[2]);
+    launch_k(k_grad_update_curv<SPH>, (unsigned)g, 256, 0, st, L, phi, B[0], B[1], B[2]);
 }
 
 static unsigned flat_grid(const LevelView<double>& L) {
@@ -430,13 +444,13 @@ static unsigned flat_grid(const LevelView<double>& L) {
 void launch_xcfc_ap_init(const LevelView<double>& L, const double* alpha, const double* dpsi, double* dap,
                          cudaStream_t st) {
   count_launch();
-  k_ap_init<<<flat_grid(L), 256, 0, st>>>(L, alpha, dpsi, dap);
+  launch_k(k_ap_init, flat_grid(L), 256, 0, st, L, alpha, dpsi, dap);
 }
 
 void launch_xcfc_alpha_out(const LevelView<double>& L, const double* dap, const double* dpsi, double* alpha,
                            cudaStream_t st) {
   count_launch();
-  k_alpha_out<<<flat_grid(L), 256, 0, st>>>(L, dap, dpsi, alpha);
+  launch_k(k_alpha_out, flat_grid(L), 256, 0, st, L, dap, dpsi, alpha);
 }
 
 }  // namespace gmg
