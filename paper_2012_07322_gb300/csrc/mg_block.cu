@@ -61,6 +61,7 @@ __device__ void bc_smooth(const BcLevel& B, int nsweeps) {
         }
         __syncthreads();
       } else {
+        #pragma unroll
         for (int c = 0; c < 3; ++c) {
           for (long q = threadIdx.x; q < nh; q += blockDim.x) {
             int i, j, k;
@@ -86,6 +87,7 @@ __device__ void bc_residual(const BcLevel& B) {
       float Sv;
       B.r[0][p] = scalar_residual_cell<float, G, EQ_LIN>(L, B.e[0], B.f[0], nullptr, B.k, i, j, k, p, Sv);
     } else {
+      #pragma unroll
       for (int c = 0; c < 3; ++c) B.r[c][p] = vec_residual_cell<float, G>(L, B.e[0], B.e[1], B.e[2], B.f[c], c, i, j, p);
     }
   }
@@ -97,12 +99,13 @@ __device__ void bc_residual(const BcLevel& B) {
 template <int G, bool VEC>
 __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) {
   const LevelView<double>& L = P.c64;
-  const int nc = VEC ? 3 : 1;
+  constexpr int nc = VEC ? 3 : 1;
   const long n = (long)L.n0 * L.n1 * L.n2;
   const long ng = L.sy * (L.n2 + 2 * L.three);
   double* cu[3] = {smd + P.cu[0], smd + P.cu[1], smd + P.cu[2]};
   double* cf[3] = {smd + P.cf[0], smd + P.cf[1], smd + P.cf[2]};
   double* ck = P.ck >= 0 ? smd + P.ck : nullptr;
+  #pragma unroll
   for (int c = 0; c < nc; ++c) {
     for (long q = threadIdx.x; q < n; q += blockDim.x) {
       int i, j, k;
@@ -124,7 +127,8 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
       int i, j, k;
       L.cell(r % cells, i, j, k);
-      fp[r] = cf[r / cells][L.idx(i, j, k)];
+      const int c = r / cells;
+      fp[r] = (c == 0 ? cf[0] : (c == 1 ? cf[1] : cf[2]))[L.idx(i, j, k)];
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
@@ -132,12 +136,14 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
       for (int col = 0; col < n; ++col) x += P.cinv[(long)col * n + r] * fp[col];
       int i, j, k;
       L.cell(r % cells, i, j, k);
-      cu[r / cells][L.idx(i, j, k)] = x;
+      const int c = r / cells;
+      (c == 0 ? cu[0] : (c == 1 ? cu[1] : cu[2]))[L.idx(i, j, k)] = x;
     }
   } else {
     coarse_vec_body<double, G>(L, cu[0], cu[1], cu[2], cf[0], cf[1], cf[2], P.coarse_sweeps);
   }
   __syncthreads();
+  #pragma unroll
   for (int c = 0; c < nc; ++c)
     for (long q = threadIdx.x; q < n; q += blockDim.x) {
       int i, j, k;
@@ -147,6 +153,7 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
     }
   __syncthreads();
   if (VEC)
+    #pragma unroll
     for (int c = 0; c < 3; ++c) bc_fill(B.v, B.e[c], c);
 }
 
@@ -156,10 +163,11 @@ __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_cons
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   double* smd = reinterpret_cast<double*>(smem_raw + P.fp64_at);
-  const int nc = VEC ? 3 : 1;
+  constexpr int nc = VEC ? 3 : 1;
   {
     // level l0: right-hand side in, zero correction
     const BcLevel B = bc_level(P, sm, 0);
+    #pragma unroll
     for (int c = 0; c < nc; ++c)
       for (long q = threadIdx.x; q < P.ng0; q += blockDim.x) {
         B.f[c][q] = P.f_in[c][q];
@@ -176,6 +184,7 @@ __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_cons
     const LevelView<float> Cv = C.v;
     const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2;
     const long ngC = Cv.sy * (Cv.n2 + 2 * Cv.three);
+    #pragma unroll
     for (int c = 0; c < nc; ++c) {
       const float* const as[4] = {F.r[c], nullptr, nullptr, nullptr};
       float* const bs[4] = {C.f[c], nullptr, nullptr, nullptr};
@@ -195,6 +204,7 @@ __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_cons
     const BcLevel F = bc_level(P, sm, l), C = bc_level(P, sm, l + 1);
     const LevelView<float> Fv = F.v;
     const long nF = (long)Fv.n0 * Fv.n1 * Fv.n2;
+    #pragma unroll
     for (int c = 0; c < nc; ++c)
       for (long q = threadIdx.x; q < nF; q += blockDim.x) {
         int i, j, k;
@@ -203,11 +213,13 @@ __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_cons
       }
     __syncthreads();
     if (VEC)
+      #pragma unroll
       for (int c = 0; c < 3; ++c) bc_fill(Fv, F.e[c], c);
     bc_smooth<G, VEC>(F, P.nu2);
   }
   // level l0 correction out (ghosts included)
   const BcLevel B = bc_level(P, sm, 0);
+  #pragma unroll
   for (int c = 0; c < nc; ++c)
     for (long q = threadIdx.x; q < P.ng0; q += blockDim.x) P.e_out[c][q] = B.e[c][q];
 }

@@ -205,11 +205,12 @@ struct Nb6 {
 // Neighbours of a cell on the edge of the level: outer ghosts from the
 // boundary rule on the fly, the origin / axis neighbours replaced by the
 // cell itself (their face areas vanish, so they drop out of the flux),
-// periodic phi neighbours wrapped.  Out of line: interior cells, the vast
-// majority, never evaluate the boundary rules.
+// periodic phi neighbours wrapped.  FP64 kernels call it out of line
+// (lap_edge_neighbours): interior cells, the vast majority, never evaluate
+// the boundary rules there.
 template <typename T, int G>
-__device__ __noinline__ Nb6<T> lap_edge_neighbours(const LevelView<T>& L, const T* __restrict__ u, int i, int j,
-                                                   int k, long p) {
+__device__ __forceinline__ Nb6<T> lap_edge_neighbours_body(const LevelView<T>& L, const T* __restrict__ u, int i,
+                                                           int j, int k, long p) {
   const T uc = u[p];
   Nb6<T> nb;
   nb.e = (i < L.n0 - 1) ? u[p + 1] : outer_factor(L, L.n0, j, k, L.n0 - 1, j, k) * uc;
@@ -236,6 +237,11 @@ __device__ __noinline__ Nb6<T> lap_edge_neighbours(const LevelView<T>& L, const 
   }
   return nb;
 }
+template <typename T, int G>
+__device__ __noinline__ Nb6<T> lap_edge_neighbours(const LevelView<T>& L, const T* __restrict__ u, int i, int j,
+                                                   int k, long p) {
+  return lap_edge_neighbours_body<T, G>(L, u, i, j, k, p);
+}
 
 // Flux-form Laplacian (Sec. 2.7.1) at an interior cell, with outer ghosts
 // taken from the boundary rule on the fly and the origin / axis fluxes
@@ -254,6 +260,10 @@ __device__ __forceinline__ T lap_scalar(const LevelView<T>& L, const T* __restri
     nb.s = u[p - L.sx];
     nb.up = L.three ? u[p + L.sy] : uc;
     nb.dn = L.three ? u[p - L.sy] : uc;
+  } else if constexpr (sizeof(T) == 4) {
+    // FP32: the edge rules inline (speculating them costs the FP32 units
+    // little; a call passes the neighbours through local memory)
+    nb = lap_edge_neighbours_body<T, G>(L, u, i, j, k, p);
   } else {
     nb = lap_edge_neighbours<T, G>(L, u, i, j, k, p);
   }

@@ -84,6 +84,7 @@ struct mg_hierarchy {
   int cinv_state[3] = {0, 0, 0};
   double* d_aa_part = nullptr;  // AA_SCRATCH_DOUBLES of device scratch
   bool prof_on = false;
+  bool fold_k32 = false;  // while capturing a V-cycle of eq. psi: K is restricted on the way down
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_cls;
   std::vector<int64_t> ev_cells;
@@ -385,8 +386,7 @@ const double* s1ptr(const mg_hierarchy* H, const Eq& e, int l) {
 
 void fill_all64(mg_hierarchy* H, const Eq& e, int l) {
   Level& L = H->L[l];
-  auto v = with_bc(L.v64, e.bc);
-  for (int c = 0; c < 3; ++c) launch_fill_ghosts(v, L.u[c], c, H->st);
+  launch_fill_ghosts3(with_bc(L.v64, e.bc), L.u, 3, 1, H->st);
 }
 
 void smooth64(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
@@ -470,8 +470,9 @@ void fas_up64(mg_hierarchy* H, const Eq& e, int l) {
   Level& C = H->L[l + 1];
   auto v = with_bc(L.v64, e.bc);
   auto vc = with_bc(C.v64, e.bc);
-  for (int c = 0; c < e.ncomp; ++c)
-    launch_prolong(v, vc, L.u[c], C.u[c], C.uh[c], e.kind == EQ_VEC ? c : -1, H->st);
+  const double* uH[3] = {C.u[0], C.u[1], C.u[2]};
+  const double* uhH[3] = {C.uh[0], C.uh[1], C.uh[2]};
+  launch_prolong3(v, vc, L.u, uH, uhH, e.ncomp, e.kind == EQ_VEC, H->st);
   if (e.kind == EQ_VEC) fill_all64(H, e, l);
 }
 
@@ -607,8 +608,7 @@ void coarse32(mg_hierarchy* H, const Eq& e, int l) {
     launch_coarse_vec<double>(v, L.u, f, COARSE_SWEEPS, H->st);
   }
   for (int c = 0; c < e.ncomp; ++c) launch_convert<double, float>(L.v64, L.u[c], L.e[c], H->st);
-  if (e.kind == EQ_VEC)
-    for (int c = 0; c < 3; ++c) launch_fill_ghosts<float>(with_bc(L.v32, e.bc), L.e[c], c, H->st);
+  if (e.kind == EQ_VEC) launch_fill_ghosts3<float>(with_bc(L.v32, e.bc), L.e, 3, 1, H->st);
 }
 
 // Parameters of the one-block coarse cycle from level l0 (mg_block.cu):
@@ -685,8 +685,12 @@ int block_cycle_level(mg_hierarchy* H, const Eq& e) {
   return H->nlev;
 }
 
+void restrict_k32(mg_hierarchy* H, int from);
+
 // vcycle32 from level l0 down, in one block.
 void block_vcycle32(mg_hierarchy* H, const Eq& e, int l0) {
+  // K of eq. psi reached level l0 with the down leg; on to the block's levels
+  if (H->fold_k32) restrict_k32(H, l0 + 1);
   const BlockCycle32 P = block_cycle_params(H, e, l0);
   for (int l = l0; l + 1 < H->nlev; ++l) H->updates += (int64_t)(H->d.nu1 + H->d.nu2) * H->L[l].cells() * e.ncomp;
   launch_block_vcycle32(P, H->d.geom, H->st);
@@ -708,29 +712,20 @@ void vcycle32(mg_hierarchy* H, const Eq& e, int l) {
   auto vc = with_bc(C.v32, e.bc);
   const float* K = (e.kind == EQ_PSI || e.has_c) ? L.k32 : nullptr;
   smooth32(H, e, l, H->d.nu1);
-  if (e.kind != EQ_VEC) {
-    launch_residual_scalar<float>(v, EQ_LIN, L.e[0], L.f32[0], nullptr, K, L.r32[0], nullptr, 0, H->st);
-  } else {
-    const float* f[3] = {L.f32[0], L.f32[1], L.f32[2]};
-    launch_residual_vec<float>(v, L.e, f, L.r32, nullptr, 0, H->st);
-  }
-  for (int c = 0; c < e.ncomp; ++c) {
-    const float* a[4] = {L.r32[c], nullptr, nullptr, nullptr};
-    float* b[4] = {C.f32[c], nullptr, nullptr, nullptr};
-    float* cp[3] = {nullptr, nullptr, nullptr};
-    launch_restrict<float>(v, vc, 1, a, b, cp, H->st);
-    cudaMemsetAsync(C.e[c], 0, sizeof(float) * C.ng, H->st);
-  }
+  // residual restricted into the coarse right-hand side, coarse e zeroed
+  // (and K of eq. psi restricted) in one launch
+  launch_resid_restrict32(v, vc, e.kind == EQ_VEC, L.e, L.f32, K, C.f32, C.e, H->fold_k32 ? C.k32 : nullptr,
+                          H->st);
   vcycle32(H, e, l + 1);
-  for (int c = 0; c < e.ncomp; ++c)
-    launch_prolong<float>(v, vc, L.e[c], C.e[c], nullptr, e.kind == EQ_VEC ? c : -1, H->st);
-  if (e.kind == EQ_VEC)
-    for (int c = 0; c < 3; ++c) launch_fill_ghosts<float>(v, L.e[c], c, H->st);
+  const float* eH[3] = {C.e[0], C.e[1], C.e[2]};
+  launch_prolong3<float>(v, vc, L.e, eH, nullptr, e.ncomp, e.kind == EQ_VEC, H->st);
+  if (e.kind == EQ_VEC) launch_fill_ghosts3<float>(v, L.e, 3, 1, H->st);
   smooth32(H, e, l, H->d.nu2);
 }
 
-void restrict_k32(mg_hierarchy* H) {
-  for (int l = 1; l < H->nlev; ++l) {
+// K of the correction equation restricted into levels from .. nlev - 1.
+void restrict_k32(mg_hierarchy* H, int from) {
+  for (int l = from; l < H->nlev; ++l) {
     Level& F = H->L[l - 1];
     Level& C = H->L[l];
     const float* a[4] = {F.k32, nullptr, nullptr, nullptr};
@@ -766,12 +761,10 @@ void fmg32(mg_hierarchy* H, const Eq& e) {
     Level& C = H->L[l + 1];
     auto v = with_bc(L.v32, e.bc);
     auto vc = with_bc(C.v32, e.bc);
-    for (int c = 0; c < e.ncomp; ++c) {
-      cudaMemsetAsync(L.e[c], 0, sizeof(float) * L.ng, H->st);
-      launch_prolong<float>(v, vc, L.e[c], C.e[c], nullptr, e.kind == EQ_VEC ? c : -1, H->st);
-    }
-    if (e.kind == EQ_VEC)
-      for (int c = 0; c < 3; ++c) launch_fill_ghosts<float>(v, L.e[c], c, H->st);
+    for (int c = 0; c < e.ncomp; ++c) cudaMemsetAsync(L.e[c], 0, sizeof(float) * L.ng, H->st);
+    const float* eH[3] = {C.e[0], C.e[1], C.e[2]};
+    launch_prolong3<float>(v, vc, L.e, eH, nullptr, e.ncomp, e.kind == EQ_VEC, H->st);
+    if (e.kind == EQ_VEC) launch_fill_ghosts3<float>(v, L.e, 3, 1, H->st);
     vcycle32(H, e, l);
   }
 }
@@ -792,15 +785,17 @@ int cycle_map(mg_hierarchy* H, const Eq& e) {
     auto v = with_bc(L0.v64, e.bc);
     // f32 holds the FP32 residual written by the preceding finest_norm
     for (int c = 0; c < e.ncomp; ++c) CK(cudaMemsetAsync(L0.e[c], 0, sizeof(float) * L0.ng, H->st));
-    // eq. psi: K = dS/du at this u was written by finest_norm with f32
-    if (e.kind == EQ_PSI) restrict_k32(H);
+    // eq. psi: K = dS/du at this u was written by finest_norm with f32; the
+    // V-cycle restricts it level by level on its way down (fold_k32)
+    if (e.kind == EQ_PSI && fmg) restrict_k32(H, 1);
+    H->fold_k32 = e.kind == EQ_PSI && !fmg;
     if (fmg)
       fmg32(H, e);
     else
       vcycle32(H, e, 0);
-    for (int c = 0; c < e.ncomp; ++c)
-      launch_add_correction<float>(v, L0.u[c], L0.e[c], H->st, (e.zero_mean && c == 0) ? H->d_part : nullptr,
-                                   NPARTS);
+    H->fold_k32 = false;
+    const float* ee[3] = {L0.e[0], L0.e[1], L0.e[2]};
+    launch_add_correction<float>(v, e.ncomp, L0.u, ee, H->st, e.zero_mean ? H->d_part : nullptr, NPARTS);
   }
   if (e.zero_mean) launch_sub_mean(L0.v64, L0.u[0], H->d_part, NPARTS, H->st, H->d.precision == MG_MIXED);
   if (e.kind == EQ_VEC) fill_all64(H, e, 0);
@@ -959,7 +954,7 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   restrict_sources(H, e);
   if (mixed && e.kind == EQ_LIN && e.has_c) {
     launch_convert<double, float>(L0.v64, L0.s1, L0.k32, H->st);
-    restrict_k32(H);
+    restrict_k32(H, 1);
   }
   int st = MG_OK;
   // mixing state

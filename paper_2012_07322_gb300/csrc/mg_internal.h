@@ -37,6 +37,38 @@ int set_last_error(int status, const char* msg);
 void hier_set_stream(mg_hierarchy* h, cudaStream_t st);
 
 // Count of kernel launches issued by the library (all hierarchies).
+// Up to three field pointers passed by value to a kernel (entries past
+// the field count repeat the first).
+template <typename T>
+struct Ptr3 {
+  T* p[3];
+  // selected, not indexed: a run-time index into a kernel parameter array
+  // would copy the array to local memory in every thread
+  __host__ __device__ __forceinline__ T* at(int c) const { return c == 0 ? p[0] : (c == 1 ? p[1] : p[2]); }
+  template <typename P>
+  static Ptr3 of(const P* a, int n) {
+    Ptr3 o{};
+    for (int c = 0; c < 3; ++c) o.p[c] = a[c < n ? c : 0];
+    return o;
+  }
+};
+template <typename T>
+struct CPtr3 {
+  const T* p[3];
+  __host__ __device__ __forceinline__ const T* at(int c) const { return c == 0 ? p[0] : (c == 1 ? p[1] : p[2]); }
+  template <typename P>
+  static CPtr3 of(const P* a, int n) {
+    CPtr3 o{};
+    for (int c = 0; c < 3; ++c) o.p[c] = a[c < n ? c : 0];
+    return o;
+  }
+};
+template <typename T>
+inline long ghost_count_host(const LevelView<T>& L) {
+  const long nk = L.n2 + 2 * L.three;
+  return 2L * (L.n1 + 2) * nk + 2L * L.n0 * nk + (L.three ? 2L * L.n0 * L.n1 : 0L);
+}
+
 void count_launch(int n = 1);
 unsigned long long launch_count();
 
@@ -45,6 +77,9 @@ void launch_smooth_scalar(const LevelView<T>& L, int kind, T* u, const T* f, con
                           int colour, cudaStream_t st);
 template <typename T>
 void launch_fill_ghosts(const LevelView<T>& L, T* u, int comp, cudaStream_t st);
+// The ghosts of ncomp fields in one launch (vector components when vec).
+template <typename T>
+void launch_fill_ghosts3(const LevelView<T>& L, T* const u[3], int ncomp, int vec, cudaStream_t st);
 // Row layout of every level array: ROW_PAD - 1 padding cells, the low
 // ghost, the n0 interior cells, the high ghost, then padding to a multiple
 // of ROW_PAD cells.  Interior rows (i = 0) and row strides are then 16-byte
@@ -89,6 +124,15 @@ void launch_restrict(const LevelView<T>& F, const LevelView<T>& C, int nf, const
 template <typename T>
 void launch_prolong(const LevelView<T>& F, const LevelView<T>& C, T* u, const T* uH, const T* uhH, int comp,
                     cudaStream_t st);
+// Kwak prolongation of ncomp fields in one launch (uhH may be null).
+template <typename T>
+void launch_prolong3(const LevelView<T>& F, const LevelView<T>& C, T* const u[3], const T* const uH[3],
+                     const T* const uhH[3], int ncomp, int vec, cudaStream_t st);
+// Down leg of the FP32 correction cycle: residual of (L - K) e = f (or the
+// vector operator) restricted into fc, K into Kc (if non-null), ec zeroed.
+void launch_resid_restrict32(const LevelView<float>& F, const LevelView<float>& C, int vec, float* const e[3],
+                             float* const f[3], const float* K, float* const fc[3], float* const ec[3], float* Kc,
+                             cudaStream_t st);
 template <typename T>
 void launch_coarse_scalar(const LevelView<T>& L, int kind, T* u, const T* f, const T* s0, const T* s1,
                           int max_sweeps, cudaStream_t st);
@@ -105,11 +149,11 @@ template <typename A, typename B>
 void launch_copy_out(const LevelView<A>& L, const A* src, B* dst, A shift, cudaStream_t st);
 template <typename A, typename B>
 void launch_convert(const LevelView<A>& L, const A* src, B* dst, cudaStream_t st);
-// u += e over the interior; with part non-null also the nparts block sums
-// of the updated u for launch_sub_mean.
+// u += e over the interior of ncomp fields; with part non-null also the
+// nparts block sums of the updated field 0 for launch_sub_mean.
 template <typename T>
-void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st,
-                           double* part = nullptr, int nparts = 0);
+void launch_add_correction(const LevelView<double>& L, int ncomp, double* const u[3], const T* const e[3],
+                           cudaStream_t st, double* part = nullptr, int nparts = 0);
 
 // xCFC and divergence-cleaning pointwise kernels (mg_xcfc.cu).
 void launch_xcfc_a2(const LevelView<double>& L, double* const X[3], double* A2, cudaStream_t st);

@@ -326,6 +326,19 @@ __global__ void k_fill_ghosts(LevelView<T> L, T* __restrict__ u, int comp) {
     fill_one_ghost(L, u, comp, g);
 }
 
+// The ghosts of ncomp fields in one launch: field c is vector component c
+// (vec != 0) or a scalar.
+template <typename T>
+__global__ void k_fill_ghosts3(LevelView<T> L, T* __restrict__ u0, T* __restrict__ u1, T* __restrict__ u2,
+                               int ncomp, int vec) {
+  pdl_entry();
+  const long n = ghost_count(L);
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < ncomp * n; g += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(g / n);
+    fill_one_ghost(L, c == 0 ? u0 : (c == 1 ? u1 : u2), vec ? c : -1, g - (long)c * n);
+  }
+}
+
 // ------------------------------------------------------------ residuals
 
 // r = f - L(u) on every interior cell.  red (if non-null) receives
@@ -478,6 +491,92 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, co
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
   if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
   prolong_cell(F, Cv, u, uH, uhH, comp, i, j, k);
+}
+
+template <typename T>
+__global__ void k_prolong3(LevelView<T> F, LevelView<T> Cv, Ptr3<T> u, CPtr3<T> uH, CPtr3<T> uhH, int ncomp,
+                           int vec) {
+  pdl_entry();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
+  for (int c = 0; c < ncomp; ++c) prolong_cell(F, Cv, u.at(c), uH.at(c), uhH.at(c), vec ? c : -1, i, j, k);
+}
+
+// Down leg of the FP32 correction cycle at one level in one launch: the
+// residual f - (L - K) e (scalar) or f - (lap + 1/3 grad div) e (vector) of
+// every fine cell, with the per-cell functions of the residual kernels,
+// restricted with the weights and summation order of restrict_cell into the
+// coarse right-hand side fc; K restricted into Kc alongside when Kc is
+// non-null; the coarse corrections ec zeroed (ghosts included).  A block
+// covers a tile of fine cells whose 2 x 2 (x 2) groups are whole, keeps its
+// residuals in shared memory, and one thread per coarse cell and component
+// sums them: the result equals the residual kernel followed by the
+// restriction, without the residual's round trip through memory.
+template <int G, bool VEC>
+__global__ void __launch_bounds__(256) k_resid_restrict32(LevelView<float> F, LevelView<float> Cv,
+                                                          CPtr3<float> e, CPtr3<float> f,
+                                                          const float* __restrict__ K, Ptr3<float> fc,
+                                                          Ptr3<float> ec, float* __restrict__ Kc) {
+  pdl_entry();
+  constexpr int NC = VEC ? 3 : 1;
+  __shared__ float rt[NC][256];
+  const int bx = blockDim.x, by = blockDim.y, bz = blockDim.z;
+  const int t = threadIdx.x + bx * (threadIdx.y + by * threadIdx.z);
+  const int i = blockIdx.x * bx + threadIdx.x;
+  const int j = blockIdx.y * by + threadIdx.y;
+  const int k = blockIdx.z * bz + threadIdx.z;
+  if (i < F.n0 && j < F.n1 && k < F.n2) {
+    const long p = F.idx(i, j, k);
+    if (VEC) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) rt[c][t] = vec_residual_cell<float, G>(F, e.p[0], e.p[1], e.p[2], f.at(c), c, i, j, p);
+    } else {
+      float Sv;
+      rt[0][t] = scalar_residual_cell<float, G, EQ_LIN>(F, e.p[0], f.p[0], nullptr, K, i, j, k, p, Sv);
+    }
+  }
+  __syncthreads();
+  const int cx = bx >> 1, cy = by >> 1, cz = F.three ? (bz >> 1) : 1;
+  const int ncell = cx * cy * cz, nk = F.three ? 2 : 1;
+  for (int w = t; w < NC * ncell; w += bx * by * bz) {
+    const int c = w / ncell, q = w - c * ncell;
+    const int ci = q % cx, cj = (q / cx) % cy, ck = q / (cx * cy);
+    const int I = blockIdx.x * cx + ci, J = blockIdx.y * cy + cj, KK = F.three ? blockIdx.z * cz + ck : 0;
+    if (I >= Cv.n0 || J >= Cv.n1 || KK >= Cv.n2) continue;
+    float wi[2], wj[2];
+    wi[0] = F.TI(TI_VW, 2 * I);
+    wi[1] = F.TI(TI_VW, 2 * I + 1);
+    wj[0] = F.TJ(TJ_VW, 2 * J);
+    wj[1] = F.TJ(TJ_VW, 2 * J + 1);
+    float wsum = 0.0f;
+    for (int dk = 0; dk < nk; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) wsum += wi[di] * wj[dj];
+    const float inv = 1.0f / wsum;
+    float sr = 0.0f;
+    for (int dk = 0; dk < nk; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di)
+          sr += wi[di] * wj[dj] * rt[c][(2 * ci + di) + bx * ((2 * cj + dj) + by * (2 * ck + dk))];
+    const long qc = Cv.idx(I, J, KK);
+    fc.at(c)[qc] = sr * inv;
+    if (c == 0 && Kc) {
+      float sk = 0.0f;
+      for (int dk = 0; dk < nk; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+          for (int di = 0; di < 2; ++di)
+            sk += wi[di] * wj[dj] * K[F.idx(2 * I + di, 2 * J + dj, F.three ? 2 * KK + dk : 0)];
+      Kc[qc] = sk * inv;
+    }
+  }
+  const long nz = Cv.sy * (Cv.n2 + 2 * Cv.three);
+  const long gt = (long)t + (long)bx * by * bz * (blockIdx.x + gridDim.x * (blockIdx.y + (long)gridDim.y * blockIdx.z));
+  const long gs = (long)bx * by * bz * gridDim.x * gridDim.y * gridDim.z;
+  for (long q = gt; q < nz; q += gs)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ec.at(c)[q] = 0.0f;
 }
 
 // --------------------------------------------------------- coarsest grid
@@ -640,30 +739,35 @@ __global__ void k_convert(LevelView<A> L, const A* __restrict__ src, B* __restri
     }
   }
 }
-// u64 += e32 (interior), the defect-correction update; with part non-null
-// also the block sums of the updated u (for the Neumann gauge).
+// u64 += e32 (interior) for ncomp fields, the defect-correction update;
+// with part non-null also the block sums of the updated field 0 (for the
+// Neumann gauge).
 template <typename T>
-__global__ void k_add_correction(LevelView<double> L, double* __restrict__ u, const T* __restrict__ e,
+__global__ void k_add_correction(LevelView<double> L, Ptr3<double> u, CPtr3<T> e, int ncomp,
                                  double* __restrict__ part) {
   pdl_entry();
   const long n = (long)L.n0 * L.n1 * L.n2;
   const long stride = (long)gridDim.x * blockDim.x;
   double s = 0.0;
-  if (L.n0 >= 4) {
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n / 4; q += stride) {
-      const long p = group4(L, q);
-      double a[4], b[4];
-      ld4(u + p, a);
-      ld4(e + p, b);
-      for (int t = 0; t < 4; ++t) a[t] += b[t];
-      st4(u + p, a);
-      s += (a[0] + a[1]) + (a[2] + a[3]);
-    }
-  } else {
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += stride) {
-      const long p = interior_p(L, q);
-      u[p] += (double)e[p];
-      s += u[p];
+  for (int c = 0; c < ncomp; ++c) {
+    double* __restrict__ uc = u.at(c);
+    const T* __restrict__ ecp = e.at(c);
+    if (L.n0 >= 4) {
+      for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n / 4; q += stride) {
+        const long p = group4(L, q);
+        double a[4], b[4];
+        ld4(uc + p, a);
+        ld4(ecp + p, b);
+        for (int t = 0; t < 4; ++t) a[t] += b[t];
+        st4(uc + p, a);
+        if (c == 0) s += (a[0] + a[1]) + (a[2] + a[3]);
+      }
+    } else {
+      for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += stride) {
+        const long p = interior_p(L, q);
+        uc[p] += (double)ecp[p];
+        if (c == 0) s += uc[p];
+      }
     }
   }
   if (part) block_sum_to(s, part);
@@ -856,6 +960,39 @@ void launch_restrict(const LevelView<T>& F, const LevelView<T>& C, int nf, const
 }
 
 template <typename T>
+void launch_fill_ghosts3(const LevelView<T>& L, T* const u[3], int ncomp, int vec, cudaStream_t st) {
+  count_launch();
+  const long n = ghost_count_host(L) * ncomp;
+  launch_k(k_fill_ghosts3<T>, grid_flat(n, 256), 256, 0, st, L, u[0], ncomp > 1 ? u[1] : u[0],
+           ncomp > 2 ? u[2] : u[0], ncomp, vec);
+}
+
+template <typename T>
+void launch_prolong3(const LevelView<T>& F, const LevelView<T>& C, T* const u[3], const T* const uH[3],
+                     const T* const uhH[3], int ncomp, int vec, cudaStream_t st) {
+  count_launch();
+  dim3 b = block_for(F.three), g = grid_cells(F, b);
+  CPtr3<T> hh{};
+  if (uhH) hh = CPtr3<T>::of(uhH, ncomp);
+  launch_k(k_prolong3<T>, g, b, 0, st, F, C, Ptr3<T>::of(u, ncomp), CPtr3<T>::of(uH, ncomp), hh, ncomp, vec);
+}
+
+void launch_resid_restrict32(const LevelView<float>& F, const LevelView<float>& C, int vec, float* const e[3],
+                             float* const f[3], const float* K, float* const fc[3], float* const ec[3], float* Kc,
+                             cudaStream_t st) {
+  count_launch();
+  const int nc = vec ? 3 : 1;
+  dim3 b = block_for(F.three), g = grid_cells(F, b);
+  const CPtr3<float> ce = CPtr3<float>::of(e, nc), cf = CPtr3<float>::of(f, nc);
+  const Ptr3<float> pfc = Ptr3<float>::of(fc, nc), pec = Ptr3<float>::of(ec, nc);
+  if (vec) {
+    GMG_GEOM_DISPATCH(F.geom, launch_k(k_resid_restrict32<GG, true>, g, b, 0, st, F, C, ce, cf, K, pfc, pec, Kc));
+  } else {
+    GMG_GEOM_DISPATCH(F.geom, launch_k(k_resid_restrict32<GG, false>, g, b, 0, st, F, C, ce, cf, K, pfc, pec, Kc));
+  }
+}
+
+template <typename T>
 void launch_prolong(const LevelView<T>& F, const LevelView<T>& C, T* u, const T* uH, const T* uhH, int comp,
                     cudaStream_t st) {
   count_launch();
@@ -926,12 +1063,13 @@ void launch_convert(const LevelView<A>& L, const A* src, B* dst, cudaStream_t st
   launch_k(k_convert<A, B>, grid_flat(L.n0 >= 4 ? n / 4 : n, 256), 256, 0, st, L, src, dst);
 }
 template <typename T>
-void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cudaStream_t st, double* part,
-                           int nparts) {
+void launch_add_correction(const LevelView<double>& L, int ncomp, double* const u[3], const T* const e[3],
+                           cudaStream_t st, double* part, int nparts) {
   count_launch();
   long n = (long)L.n0 * L.n1 * L.n2;
-  const unsigned g = part ? (unsigned)nparts : grid_flat(L.n0 >= 4 ? n / 4 : n, 256);
-  launch_k(k_add_correction<T>, g, 256, 0, st, L, u, e, part);
+  const unsigned g = part ? (unsigned)nparts : grid_flat((L.n0 >= 4 ? n / 4 : n) * ncomp, 256);
+  launch_k(k_add_correction<T>, g, 256, 0, st, L, Ptr3<double>::of(u, ncomp), CPtr3<T>::of(e, ncomp), ncomp,
+           part);
 }
 
 // explicit instantiations
@@ -941,6 +1079,9 @@ void launch_add_correction(const LevelView<double>& L, double* u, const T* e, cu
   template void launch_smooth_scalar<T>(const LevelView<T>&, int, T*, const T*, const T*, const T*, int,       \
                                         cudaStream_t);                                                          \
   template void launch_fill_ghosts<T>(const LevelView<T>&, T*, int, cudaStream_t);                             \
+  template void launch_fill_ghosts3<T>(const LevelView<T>&, T* const[3], int, int, cudaStream_t);             \
+  template void launch_prolong3<T>(const LevelView<T>&, const LevelView<T>&, T* const[3], const T* const[3],  \
+                                   const T* const[3], int, int, cudaStream_t);                                 \
   template void launch_smooth_vec<T>(const LevelView<T>&, T* [3], const T*, int, int, cudaStream_t);           \
   template void launch_residual_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, const T*, T*, \
                                           unsigned long long*, int, cudaStream_t, float*, float*);              \
@@ -963,7 +1104,8 @@ template void launch_copy_in<double, double>(const LevelView<double>&, const dou
 template void launch_copy_out<double, double>(const LevelView<double>&, const double*, double*, double, cudaStream_t);
 template void launch_convert<double, float>(const LevelView<double>&, const double*, float*, cudaStream_t);
 template void launch_convert<float, double>(const LevelView<float>&, const float*, double*, cudaStream_t);
-template void launch_add_correction<float>(const LevelView<double>&, double*, const float*, cudaStream_t, double*,
+template void launch_add_correction<float>(const LevelView<double>&, int, double* const[3], const float* const[3],
+                                           cudaStream_t, double*,
                                            int);
 
 }  // namespace gmg

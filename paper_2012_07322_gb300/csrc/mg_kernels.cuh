@@ -236,7 +236,9 @@ __device__ __forceinline__ void restrict_cell(const LevelView<T>& F, const Level
       for (int di = 0; di < 2; ++di) wsum += wi[di] * wj[dj];
   const T inv = T(1) / wsum;
   const long q = Cv.idx(I, J, K);
-  for (int m = 0; m < nf; ++m) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    if (m >= nf) break;
     T s = T(0);
     for (int dk = 0; dk < nk; ++dk)
       for (int dj = 0; dj < 2; ++dj)
@@ -280,31 +282,43 @@ constexpr int COARSE_VEC_INV_MAX = 256;   // vector cells with cached inverse di
 // sweeps until the max residual falls below 1e-12 of its initial value or
 // max_sweeps sweeps.  The bodies work on any address space: the kernels
 // below run them on shared-memory copies of the level when it fits.
+// Block-wide max of non-negative values given as abs_bits, returned to
+// every thread (1D blocks).  Integer work only: the single block of a coarse
+// solve must not queue its reductions on the few FP64 units.
+__device__ __forceinline__ double block_max_abs(unsigned long long m) {
+  __shared__ unsigned long long red[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  m = warp_max_bits(m);
+  if (lane == 0) red[warp] = m;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    const unsigned long long b = warp_max_bits(lane < nw ? red[lane] : 0ULL);
+    if (lane == 0) red[32] = b;
+  }
+  __syncthreads();
+  const unsigned long long b = red[32];
+  __syncthreads();
+  return __longlong_as_double((long long)b);
+}
+
 template <typename T, int G, int KIND>
 __device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, const T* __restrict__ f,
                                    const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps) {
-  __shared__ double red[32];
   __shared__ double r0s;
   const long n = (long)L.n0 * L.n1 * L.n2;
   const int tid = threadIdx.x;
   auto resmax = [&]() -> double {
-    double m = 0.0;
+    unsigned long long m = 0ULL;
     for (long q = tid; q < n; q += blockDim.x) {
       int i, j, k;
-    L.cell(q, i, j, k);
+      L.cell(q, i, j, k);
       const long p = L.idx(i, j, k);
       T D;
       const T Lu = scalar_op<T, G, KIND>(L, u, s0, s1, i, j, k, p, D);
-      const double rv = fabs((double)((f ? f[p] : T(0)) - Lu));
-      m = (rv > m || rv != rv) ? rv : m;
+      m = umax64(m, abs_bits((double)((f ? f[p] : T(0)) - Lu)));
     }
-    m = warp_max(m);
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    double b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
-    __syncthreads();
-    return b;
+    return block_max_abs(m);
   };
   const double r0 = resmax();
   if (tid == 0) r0s = r0;
@@ -346,7 +360,6 @@ template <typename T, int G>
 __device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
                                 const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
                                 int max_sweeps) {
-  __shared__ double red[32];
   __shared__ double r0s;
   const long n = (long)L.n0 * L.n1 * L.n2;
   const long ng = ghost_count(L);
@@ -358,25 +371,18 @@ __device__ void coarse_vec_body(const LevelView<T>& L, T* __restrict__ A, T* __r
     __syncthreads();
   };
   auto resmax = [&]() -> double {
-    double m = 0.0;
+    unsigned long long m = 0ULL;
     for (long q = tid; q < n; q += blockDim.x) {
       int i, j, k;
-    L.cell(q, i, j, k);
+      L.cell(q, i, j, k);
       const long p = L.idx(i, j, k);
       for (int c = 0; c < 3; ++c) {
         T D;
         const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
-        const double rv = fabs((double)((fs[c] ? fs[c][p] : T(0)) - Lu));
-        m = (rv > m || rv != rv) ? rv : m;
+        m = umax64(m, abs_bits((double)((fs[c] ? fs[c][p] : T(0)) - Lu)));
       }
     }
-    m = warp_max(m);
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    double b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) b = fmax(b, red[w]);
-    __syncthreads();
-    return b;
+    return block_max_abs(m);
   };
   for (int c = 0; c < 3; ++c) fill(c);
   const double r0 = resmax();
