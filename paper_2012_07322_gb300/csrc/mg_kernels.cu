@@ -493,15 +493,15 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, co
   prolong_cell(F, Cv, u, uH, uhH, comp, i, j, k);
 }
 
-template <typename T>
-__global__ void k_prolong3(LevelView<T> F, LevelView<T> Cv, Ptr3<T> u, CPtr3<T> uH, CPtr3<T> uhH, int ncomp,
-                           int vec) {
+template <typename T, int NC>
+__global__ void k_prolong3(LevelView<T> F, LevelView<T> Cv, Ptr3<T> u, CPtr3<T> uH, CPtr3<T> uhH, int vec) {
   pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
   if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
-  for (int c = 0; c < ncomp; ++c) prolong_cell(F, Cv, u.at(c), uH.at(c), uhH.at(c), vec ? c : -1, i, j, k);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) prolong_cell(F, Cv, u.at(c), uH.at(c), uhH.at(c), vec ? c : -1, i, j, k);
 }
 
 // Down leg of the FP32 correction cycle at one level in one launch: the
@@ -974,7 +974,10 @@ void launch_prolong3(const LevelView<T>& F, const LevelView<T>& C, T* const u[3]
   dim3 b = block_for(F.three), g = grid_cells(F, b);
   CPtr3<T> hh{};
   if (uhH) hh = CPtr3<T>::of(uhH, ncomp);
-  launch_k(k_prolong3<T>, g, b, 0, st, F, C, Ptr3<T>::of(u, ncomp), CPtr3<T>::of(uH, ncomp), hh, ncomp, vec);
+  if (ncomp == 1)
+    launch_k(k_prolong3<T, 1>, g, b, 0, st, F, C, Ptr3<T>::of(u, 1), CPtr3<T>::of(uH, 1), hh, vec);
+  else
+    launch_k(k_prolong3<T, 3>, g, b, 0, st, F, C, Ptr3<T>::of(u, 3), CPtr3<T>::of(uH, 3), hh, vec);
 }
 
 void launch_resid_restrict32(const LevelView<float>& F, const LevelView<float>& C, int vec, float* const e[3],
