@@ -281,6 +281,16 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Blocks for a hierarchy's values: enough to stream them, at most cap (a
+// small hierarchy must not fill the GPU with idle blocks that other
+// streams' solves could use).
+static unsigned aa_grid(const LevelView<double>& L, int ncomp, int per_block, int cap) {
+  const long nq = (long)L.n0 * L.n1 * L.n2 / (L.n0 >= 4 ? 4 : 1) * ncomp;
+  long g = (nq + per_block - 1) / per_block;
+  if (g > cap) g = cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
 template <typename TC>
 void launch_aa_update_dots(const LevelView<double>& L, int ncomp, long stride, double* const g[3], double* x,
                            double* fprev, double* gprev, TC* dF, TC* dG, const AACols& cols, double* scratch,
@@ -288,10 +298,10 @@ void launch_aa_update_dots(const LevelView<double>& L, int ncomp, long stride, d
   count_launch();
   AAScratch S = aa_scratch(scratch);
   if (L.n0 >= 4)
-    launch_k(k_aa_update_dots<TC, 4>, AA_BLOCKS, 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
+    launch_k(k_aa_update_dots<TC, 4>, aa_grid(L, ncomp, 4 * 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
                                                        cols, S.part, S.done, S.M, S.gamma, status);
   else
-    launch_k(k_aa_update_dots<TC, 1>, AA_BLOCKS, 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
+    launch_k(k_aa_update_dots<TC, 1>, aa_grid(L, ncomp, 4 * 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
                                                        cols, S.part, S.done, S.M, S.gamma, status);
 }
 template <typename TC>
@@ -301,10 +311,10 @@ void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, doubl
   count_launch();
   const double* gamma = aa_scratch(const_cast<double*>(scratch)).gamma;
   if (L.n0 >= 4)
-    launch_k(k_aa_combine<TC, 4>, AA_BLOCKS * 2, 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, gamma,
+    launch_k(k_aa_combine<TC, 4>, aa_grid(L, ncomp, 256, AA_BLOCKS * 2), 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, gamma,
                                                        status);
   else
-    launch_k(k_aa_combine<TC, 1>, AA_BLOCKS * 2, 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, gamma,
+    launch_k(k_aa_combine<TC, 1>, aa_grid(L, ncomp, 256, AA_BLOCKS * 2), 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, gamma,
                                                        status);
 }
 
