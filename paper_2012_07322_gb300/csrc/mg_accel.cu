@@ -23,24 +23,47 @@ __device__ __forceinline__ long aa_pos(const LevelView<double>& L, long q) {
   if (G == 4) return group4(L, q);
   return interior_p(L, q);
 }
+// Loads and stores of the mixing streams are marked evict-first: every
+// array is touched once per cycle, and the multigrid cycle's working set
+// (which fits the L2 at the bench sizes) should stay cached across them.
 template <int G, typename T>
 __device__ __forceinline__ void aa_ld(const T* p, T (&v)[G]) {
   if constexpr (G == 1) {
-    v[0] = *p;
+    v[0] = __ldcs(p);
   } else if constexpr (sizeof(T) == 4) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
     v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
   } else {
-    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p)), b = __ldcs(reinterpret_cast<const double2*>(p + 2));
     v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
   }
 }
 template <int G, typename T>
 __device__ __forceinline__ void aa_st(T* p, const T (&v)[G]) {
   if constexpr (G == 1) {
-    *p = v[0];
+    __stcs(p, v[0]);
   } else if constexpr (sizeof(T) == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  } else {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+    __stcs(reinterpret_cast<double2*>(p + 2), make_double2(v[2], v[3]));
+  }
+}
+
+// u itself stays cached (the residual reads it next).
+template <int G>
+__device__ __forceinline__ void aa_ld_u(const double* p, double (&v)[G]) {
+  if constexpr (G == 1) {
+    v[0] = *p;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+}
+template <int G>
+__device__ __forceinline__ void aa_st_u(double* p, const double (&v)[G]) {
+  if constexpr (G == 1) {
+    *p = v[0];
   } else {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
     *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
@@ -49,97 +72,196 @@ __device__ __forceinline__ void aa_st(T* p, const T (&v)[G]) {
 
 // Sum over the warp of 32 values per lane; afterwards lane l holds the sum
 // of value l (31 exchanges instead of 32 x 5).
-__device__ __forceinline__ double warp_sum32(double (&v)[32]) {
+template <typename T>
+__device__ __forceinline__ T warp_sum32(T (&v)[32]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
     const bool upper = lane & s;
 #pragma unroll
     for (int q = 0; q < s; ++q) {
-      const double send = upper ? v[q] : v[q + s];
-      const double keep = upper ? v[q + s] : v[q];
+      const T send = upper ? v[q] : v[q + s];
+      const T keep = upper ? v[q + s] : v[q];
       v[q] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
   }
   return v[0];
 }
 
+// Relative shift of the Gram system scaled to unit maximum diagonal:
+// 1e-12 in FP64; in mixed precision the system is solved in FP32 (its dot
+// products are FP32 sums already) and the shift is about one FP32 ulp of
+// the unit diagonal (1e-6 and 1e-5 cost 3-5 % more cycles on the
+// 128 x 64 x 64 xCFC solve).
+// FP64 is long-latency on this GPU (a dependent FMA takes ~64 cycles, a
+// reciprocal square root ~430): the 16-step factorisation costs tens of
+// microseconds in FP64 and a few in FP32 registers.
+template <typename T>
+constexpr T AA_SHIFT = T(1e-12);
+template <>
+constexpr float AA_SHIFT<float> = 1e-7f;
+
+// Cholesky solve of the n x n system held by one warp, lane t owning row t
+// (entries k < n) and right-hand side z; rows and columns n .. AA_MAX - 1
+// are the identity, so every loop runs its full static length.  On return
+// lane t holds y_t (0 beyond n); false for a non-positive pivot.
+__device__ __forceinline__ bool chol_warp_f32(float (&row)[AA_MAX], float& z, int t) {
+  __shared__ float Ls[AA_MAX][AA_MAX + 1];
+  bool ok = true;
+  float idt = 1.0f;
+#pragma unroll
+  for (int j = 0; j < AA_MAX; ++j) {
+    const float piv = __shfl_sync(0xffffffffu, row[j], j);
+    ok = ok && piv > 0.0f;
+    const float id = rsqrtf(piv);
+    if (t == j) {
+      row[j] = piv * id;
+      z *= id;
+      idt = id;
+    } else if (t > j) {
+      row[j] *= id;  // L[t][j]
+    }
+    const float zj = __shfl_sync(0xffffffffu, z, j);
+#pragma unroll
+    for (int k = j + 1; k < AA_MAX; ++k) {
+      const float lkj = __shfl_sync(0xffffffffu, row[j], k);  // L[k][j]
+      if (t >= k) row[k] -= row[j] * lkj;
+    }
+    if (t > j) z -= row[j] * zj;
+  }
+  // back substitution L^T y = z with L transposed through shared memory:
+  // lane r needs L[i][r], held by lane i
+  if (t < AA_MAX)
+#pragma unroll
+    for (int k = 0; k < AA_MAX; ++k) Ls[t][k] = row[k];
+  __syncwarp();
+#pragma unroll
+  for (int i = AA_MAX - 1; i >= 0; --i) {
+    const float yi = __shfl_sync(0xffffffffu, z * idt, i);
+    if (t == i) z = yi;
+    if (t < i) z -= Ls[i][t] * yi;
+  }
+  return ok;
+}
+
 // The least-squares step (run by the last block of k_aa_update_dots to
 // finish): reduce the blocks' partial dot products in a fixed order, enter
 // the newest column's row into the Gram matrix M (AA_MAX x AA_MAX over ring
-// slots), and solve (M_live + lambda I) gamma = b with lambda = 1e-12
-// max diag(M_live) by Cholesky.  status = 0 with gamma written, or 1 when
-// the history is degenerate (non-positive pivot, non-finite values): the
-// host then restarts the mixing and the combination is skipped.
-__device__ void aa_solve_block(const AACols& cols, const double* part, int nblocks, double* __restrict__ M,
+// slots, stored in TC), and solve (M_live / dmax + shift I) gamma = b / dmax
+// by Cholesky, dmax the largest live diagonal entry.  status = 0 with gamma
+// written, or 1 when the history is degenerate (non-positive pivot,
+// non-finite values): the host then restarts the mixing and the
+// combination is skipped.
+template <typename TC>
+__device__ void aa_solve_block(const AACols& cols, const double* part_d, int nblocks, double* __restrict__ M_d,
                                double* __restrict__ gamma, unsigned long long* __restrict__ status) {
-  __shared__ double red[8][2 * AA_MAX];
-  __shared__ double s[2 * AA_MAX];
-  __shared__ double A[AA_MAX][AA_MAX + 1];
-  __shared__ double z[AA_MAX];
+  const TC* part = reinterpret_cast<const TC*>(part_d);
+  TC* M = reinterpret_cast<TC*>(M_d);
+  __shared__ TC red[8][2 * AA_MAX];
+  __shared__ TC s[2 * AA_MAX];
+  __shared__ TC Ms[AA_MAX * AA_MAX];
   const int t = threadIdx.x, q = t & 31, w = t >> 5;
-  double acc = 0.0;
-#pragma unroll 8
-  for (int b = w; b < nblocks; b += 8) acc += __ldcg(part + (long)b * 2 * AA_MAX + q);
-  red[w][q] = acc;
+  // every load issued at once: the stored Gram matrix and the partial sums
+  // (at most AA_BLOCKS / 8 per thread), summed pairwise
+  if (t < AA_MAX * AA_MAX) Ms[t] = __ldcg(M + t);
+  TC pv[AA_BLOCKS / 8];
+#pragma unroll
+  for (int r = 0; r < AA_BLOCKS / 8; ++r) {
+    const int b = w + 8 * r;
+    pv[r] = b < nblocks ? __ldcg(part + (long)b * 2 * AA_MAX + q) : TC(0);
+  }
+#pragma unroll
+  for (int h = 1; h < AA_BLOCKS / 8; h *= 2)
+#pragma unroll
+    for (int r = 0; r + h < AA_BLOCKS / 8; r += 2 * h) pv[r] += pv[r + h];
+  red[w][q] = pv[0];
   __syncthreads();
   if (t >= 32) return;
-  double sum = 0.0;
-  for (int k = 0; k < 8; ++k) sum += red[k][t];
-  s[t] = sum;
+  s[t] = ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) + ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
   const int n = cols.n, slot = cols.slot[n - 1];
   __syncwarp();
   if (t < n) {
-    M[slot * AA_MAX + cols.slot[t]] = s[AA_MAX + t];
-    M[cols.slot[t] * AA_MAX + slot] = s[AA_MAX + t];
+    const int c = cols.slot[t];
+    const TC v = s[AA_MAX + t];
+    Ms[slot * AA_MAX + c] = v;
+    Ms[c * AA_MAX + slot] = v;
+    M[slot * AA_MAX + c] = v;
+    M[c * AA_MAX + slot] = v;
   }
   __syncwarp();
-  for (int e = t; e < n * n; e += 32) {
-    const int a = e / n, b = e - a * n;
-    A[a][b] = M[cols.slot[a] * AA_MAX + cols.slot[b]];
-  }
-  __syncwarp();
-  double dmax = 0.0;
-  for (int a = 0; a < n; ++a) dmax = fmax(dmax, A[a][a]);
-  bool ok = dmax > 0.0;
-  __syncwarp();
-  if (ok && t < n) A[t][t] += 1e-12 * dmax;
-  __syncwarp();
-  // right-looking Cholesky, lane t owns row t; L overwrites the lower triangle
-  for (int j = 0; ok && j < n; ++j) {
-    const double piv = A[j][j];
-    if (!(piv > 0.0)) {
-      ok = false;
-      break;
+  TC dmax = TC(0);
+  for (int a = 0; a < n; ++a) dmax = fmax(dmax, Ms[cols.slot[a] * AA_MAX + cols.slot[a]]);
+  bool ok = dmax > TC(0) && dmax <= (sizeof(TC) == 4 ? TC(3.4e38f) : TC(1.7976931348623157e308));
+  const TC sc = ok ? TC(1) / dmax : TC(0);
+  if constexpr (sizeof(TC) == 4) {
+    float row[AA_MAX];
+    const int ra = t < n ? cols.slot[t] : 0;
+#pragma unroll
+    for (int k = 0; k < AA_MAX; ++k)
+      row[k] = (t < n && k < n) ? Ms[ra * AA_MAX + cols.slot[k]] * sc + (k == t ? AA_SHIFT<float> : 0.0f)
+                                : (k == t ? 1.0f : 0.0f);
+    float z = t < n ? s[t] * sc : 0.0f;
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) ok = chol_warp_f32(row, z, t);
+    if (ok) ok = __all_sync(0xffffffffu, z - z == 0.0f);
+    if (ok && t < n) gamma[t] = (double)z;
+  } else {
+    // FP64: the augmented matrix in shared memory, lane t owning row t;
+    // L overwrites the lower triangle and L^-1 b column n
+    __shared__ double A[AA_MAX][AA_MAX + 2];
+    __shared__ double inv[AA_MAX];
+    if (t < n) {
+      const int ra = cols.slot[t];
+      for (int b = 0; b < n; ++b) A[t][b] = Ms[ra * AA_MAX + cols.slot[b]] * sc;
+      A[t][n] = s[t] * sc;
+      A[t][t] += AA_SHIFT<double>;
     }
-    const double d = sqrt(piv), id = 1.0 / d;
     __syncwarp();
-    if (t == j) A[j][j] = d;
-    if (t > j && t < n) A[t][j] *= id;
-    __syncwarp();
-    if (t > j && t < n) {
-      const double lt = A[t][j];
-      for (int k = j + 1; k <= t; ++k) A[t][k] -= lt * A[k][j];
-    }
-    __syncwarp();
-  }
-  if (t == 0) {
-    if (ok) {
-      for (int i = 0; i < n; ++i) {
-        double a = s[i];
-        for (int k = 0; k < i; ++k) a -= A[i][k] * z[k];
-        z[i] = a / A[i][i];
+    for (int j = 0; ok && j < n; ++j) {
+      const double piv = A[j][j];
+      if (!(piv > 0.0)) {
+        ok = false;
+        break;
       }
-      for (int i = n - 1; i >= 0; --i) {
-        double a = z[i];
-        for (int k = i + 1; k < n; ++k) a -= A[k][i] * z[k];
-        z[i] = a / A[i][i];
+      const double id = rsqrt(piv);
+      __syncwarp();
+      if (t == j) {
+        A[j][j] = piv * id;
+        A[j][n] *= id;
+        inv[j] = id;
       }
-      for (int i = 0; i < n; ++i) ok = ok && (z[i] - z[i] == 0.0);
-      for (int i = 0; i < n; ++i) gamma[i] = z[i];
+      if (t > j && t < n) A[t][j] *= id;
+      __syncwarp();
+      if (t > j && t < n) {
+        // all operands first: the updates are independent, but stores and
+        // loads to the same array would otherwise serialise them
+        const double lt = A[t][j], zj = A[j][n];
+        double rw[AA_MAX], cl[AA_MAX];
+#pragma unroll
+        for (int k = 1; k < AA_MAX; ++k) {
+          const bool in = j + k <= t;
+          rw[k] = in ? A[t][j + k] : 0.0;
+          cl[k] = in ? A[j + k][j] : 0.0;
+        }
+        const double rn = A[t][n];
+#pragma unroll
+        for (int k = 1; k < AA_MAX; ++k)
+          if (j + k <= t) A[t][j + k] = rw[k] - lt * cl[k];
+        A[t][n] = rn - lt * zj;
+      }
+      __syncwarp();
     }
-    *status = ok ? 0ULL : 1ULL;
+    // back substitution L^T y = z, lane r holding z_r
+    double z = (ok && t < n) ? A[t][n] : 0.0;
+    for (int i = n - 1; ok && i >= 0; --i) {
+      const double yi = __shfl_sync(0xffffffffu, z * inv[t < n ? t : 0], i);
+      if (t == i) z = yi;
+      if (t < i) z -= A[i][t] * yi;
+    }
+    if (ok) ok = __all_sync(0xffffffffu, t >= n || z - z == 0.0);
+    if (ok && t < n) gamma[t] = z;
   }
+  if (t == 0) *status = ok ? 0ULL : 1ULL;
 }
 
 // With the live columns cols (oldest first; the newest, slot cols.n - 1, is
@@ -171,7 +293,7 @@ __global__ void __launch_bounds__(256, 2)
       const long p = aa_pos<G>(L, q);
       const long o = (long)c * stride + p;
       double g[G], xv[G], fp[G], gp[G], f[G];
-      aa_ld<G>(gc + p, g);
+      aa_ld_u<G>(gc + p, g);
       aa_ld<G>(x + o, xv);
       aa_ld<G>(fprev + o, fp);
       aa_ld<G>(gprev + o, gp);
@@ -208,21 +330,24 @@ __global__ void __launch_bounds__(256, 2)
       }
     }
   }
-  __shared__ double sm[8][2 * AA_MAX];
-  double v[32];
+  // block sums in the history's precision (FP32 in mixed precision: FP64
+  // additions are long-latency on this GPU, and the products are FP32)
+  __shared__ TC sm[8][2 * AA_MAX];
+  TC v[32];
 #pragma unroll
   for (int a = 0; a < AA_MAX; ++a) {
-    v[a] = (double)sb[a];
-    v[AA_MAX + a] = (double)sn[a];
+    v[a] = sb[a];
+    v[AA_MAX + a] = sn[a];
   }
-  const double w = warp_sum32(v);
+  const TC w = warp_sum32(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   sm[warp][lane] = w;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sm[k][threadIdx.x];
-    part[(long)blockIdx.x * 2 * AA_MAX + threadIdx.x] = s;
+    TC s = TC(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += sm[k][threadIdx.x];
+    reinterpret_cast<TC*>(part)[(long)blockIdx.x * 2 * AA_MAX + threadIdx.x] = s;
   }
   if (nc == 0) return;
   __shared__ bool last;
@@ -235,7 +360,7 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
   if (last) {
     __threadfence();
-    aa_solve_block(cols, part, gridDim.x, M, gamma, status);
+    aa_solve_block<TC>(cols, part, gridDim.x, M, gamma, status);
   }
 }
 
@@ -272,10 +397,10 @@ __global__ void __launch_bounds__(256)
         for (int t = 0; t < G; ++t) sacc[t] += gm[a] * d[t];
       }
       double uv[G];
-      aa_ld<G>(uc + p, uv);
+      aa_ld_u<G>(uc + p, uv);
 #pragma unroll
       for (int t = 0; t < G; ++t) uv[t] -= (double)sacc[t];
-      aa_st<G>(uc + p, uv);
+      aa_st_u<G>(uc + p, uv);
       aa_st<G>(x + o, uv);
     }
   }
@@ -298,10 +423,10 @@ void launch_aa_update_dots(const LevelView<double>& L, int ncomp, long stride, d
   count_launch();
   AAScratch S = aa_scratch(scratch);
   if (L.n0 >= 4)
-    launch_k(k_aa_update_dots<TC, 4>, aa_grid(L, ncomp, 4 * 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
+    launch_k(k_aa_update_dots<TC, 4>, aa_grid(L, ncomp, 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
                                                        cols, S.part, S.done, S.M, S.gamma, status);
   else
-    launch_k(k_aa_update_dots<TC, 1>, aa_grid(L, ncomp, 4 * 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
+    launch_k(k_aa_update_dots<TC, 1>, aa_grid(L, ncomp, 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
                                                        cols, S.part, S.done, S.M, S.gamma, status);
 }
 template <typename TC>
