@@ -40,7 +40,7 @@ struct Level {
   float* ti32 = nullptr;
   float* tj32 = nullptr;
   double *u[3] = {}, *uh[3] = {}, *f[3] = {}, *r[3] = {}, *s0 = nullptr, *s1 = nullptr;
-  float *e[3] = {}, *f32[3] = {}, *r32[3] = {}, *k32 = nullptr;
+  float *e[3] = {}, *f32[3] = {}, *k32 = nullptr;
   long cells() const { return (long)n[0] * n[1] * n[2]; }
 };
 
@@ -247,7 +247,6 @@ size_t layout(mg_hierarchy* H, const mg_grid_desc* d, char* base) {
       for (int c = 0; c < 3; ++c) {
         t32(L ? &L->e[c] : &dummy32, b32);
         t32(L ? &L->f32[c] : &dummy32, b32);
-        t32(L ? &L->r32[c] : &dummy32, b32);
       }
       t32(L ? &L->k32 : &dummy32, b32);
     }
