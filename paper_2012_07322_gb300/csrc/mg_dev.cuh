@@ -32,6 +32,11 @@ enum Kind { EQ_PSI = 0, EQ_LIN = 1, EQ_VEC = 2 };
 enum { TI_X = 0, TI_IX, TI_IX2, TI_CE, TI_CW, TI_PHI, TI_VW, NTI };
 // Per-j table slots (length n1 + 2, entry j + 1).
 enum { TJ_S = 0, TJ_C, TJ_IS, TJ_IS2, TJ_COT, TJ_TN, TJ_TS, TJ_PF, TJ_VW, NTJ };
+// Per-(i, j) stencil coefficients of the vector operator on spherical
+// levels with four-point mixed derivatives (FP64 residual), stored
+// coefficient-major: vc[(q * n1 + j) * n0 + i].  Slots 0-11 component r,
+// 12-21 theta, 22-31 phi (k_residual_vec_sph), 32 the norm weight.
+constexpr int VC_N = 34;
 
 template <typename T>
 struct LevelView {
@@ -47,6 +52,7 @@ struct LevelView {
   int ln0, ln1;        // log2 of n0, n1 (all sizes are powers of two)
   const T* ti;         // NTI tables of n0 + 2
   const T* tj;         // NTJ tables of n1 + 2
+  const T* vc;         // VC_N per-(i, j) coefficients of the vector operator, or null
   __device__ __forceinline__ long idx(int i, int j, int k) const { return off + i + j * sx + (long)k * sy; }
   __device__ __forceinline__ T TI(int s, int i) const { return ti[s * (n0 + 2) + i + 1]; }
   __device__ __forceinline__ T TJ(int s, int j) const { return tj[s * (n1 + 2) + j + 1]; }

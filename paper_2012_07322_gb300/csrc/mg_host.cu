@@ -37,6 +37,7 @@ struct Level {
   LevelView<float> v32;
   double* ti64 = nullptr;
   double* tj64 = nullptr;
+  double* vc64 = nullptr;  // spherical, four-point mixed derivatives: VC_N x n0 x n1
   float* ti32 = nullptr;
   float* tj32 = nullptr;
   double *u[3] = {}, *uh[3] = {}, *f[3] = {}, *r[3] = {}, *s0 = nullptr, *s1 = nullptr;
@@ -234,6 +235,8 @@ size_t layout(mg_hierarchy* H, const mg_grid_desc* d, char* base) {
     t64(L ? &L->ti64 : &dummy64, sizeof(double) * NTI * (n[l][0] + 2));
     t64(L ? &L->tj64 : &dummy64, sizeof(double) * NTJ * (n[l][1] + 2));
     t32(L ? &L->ti32 : &dummy32, sizeof(float) * NTI * (n[l][0] + 2));
+    if (d->geom == MG_SPH && d->mixed_deriv == MG_MIXED_4PT)
+      t64(L ? &L->vc64 : &dummy64, sizeof(double) * VC_N * n[l][0] * n[l][1]);
     t32(L ? &L->tj32 : &dummy32, sizeof(float) * NTJ * (n[l][1] + 2));
     for (int c = 0; c < 3; ++c) {
       t64(L ? &L->u[c] : &dummy64, b64);
@@ -324,6 +327,76 @@ void make_tables(const mg_grid_desc* d, const Level& L, std::vector<double>& ti,
   }
 }
 
+// The vector operator lap V + 1/3 grad div V on a spherical level as a
+// stencil per component: the coefficients of vec_op (metric factors, the
+// 1/3 of the grad-div part and the difference scales) multiplied out per
+// (i, j), so that the FP64 residual spends one FMA per stencil term.  Same
+// operator, different rounding order.
+void make_vec_coeffs(const mg_grid_desc* d, const Level& L, const std::vector<double>& ti,
+                     const std::vector<double>& tj, std::vector<double>& vc) {
+  const int n0 = L.n[0], n1 = L.n[1];
+  const bool three = d->ndim == 3;
+  vc.assign((size_t)VC_N * n0 * n1, 0.0);
+  const double ih0s = 1.0 / (L.h[0] * L.h[0]), ih1s = 1.0 / (L.h[1] * L.h[1]), ih2s = 1.0 / (L.h[2] * L.h[2]);
+  const double hc0 = 0.5 / L.h[0], hc1 = 0.5 / L.h[1], hc2 = 0.5 / L.h[2];
+  const double m01 = 1.0 / (4.0 * L.h[0] * L.h[1]), m02 = 1.0 / (4.0 * L.h[0] * L.h[2]);
+  const double m12 = 1.0 / (4.0 * L.h[1] * L.h[2]);
+  const double t3 = 1.0 / 3.0;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      auto I = [&](int s) { return ti[(size_t)s * (n0 + 2) + i + 1]; };
+      auto J = [&](int s) { return tj[(size_t)s * (n1 + 2) + j + 1]; };
+      const double x = I(TI_X), ir = I(TI_IX), ir2 = I(TI_IX2), cE = I(TI_CE), cW = I(TI_CW);
+      const double s = J(TJ_S), ct = J(TJ_C), ist = J(TJ_IS), ist2 = J(TJ_IS2), cot = J(TJ_COT);
+      const double tN = J(TJ_TN), tS = J(TJ_TS), pf = three ? J(TJ_PF) : 0.0;
+      const double lapc = cE + cW + ir2 * (tN + tS) + 2.0 * ir2 * pf;
+      double c[VC_N] = {0.0};
+      // r: lap V_r + 1/3 d_rr V_r + 2/3 r^-1 d_r V_r - 8/3 r^-2 V_r
+      //    - 7/3 r^-2 d_th V_th - 7/3 cot r^-2 V_th + 1/3 cot r^-1 d_r V_th + 1/3 r^-1 d_r d_th V_th
+      //    - 7/3 r^-2 sin^-1 d_ph V_ph + 1/3 r^-1 sin^-1 d_r d_ph V_ph
+      c[0] = cE + t3 * ih0s + 2.0 * t3 * ir * hc0;
+      c[1] = cW + t3 * ih0s - 2.0 * t3 * ir * hc0;
+      c[2] = ir2 * tN;
+      c[3] = ir2 * tS;
+      c[4] = ir2 * pf;
+      c[5] = -lapc - 2.0 * t3 * ih0s - 8.0 * t3 * ir2;
+      c[6] = -7.0 * t3 * ir2 * hc1;
+      c[7] = -7.0 * t3 * cot * ir2;
+      c[8] = t3 * cot * ir * hc0;
+      c[9] = t3 * ir * m01;
+      c[10] = three ? -7.0 * t3 * ir2 * ist * hc2 : 0.0;
+      c[11] = three ? t3 * ir * ist * m02 : 0.0;
+      // theta: lap V_th + 1/3 r^-2 d_thth V_th + 1/3 cot r^-2 d_th V_th - 4/3 r^-2 sin^-2 V_th
+      //    + 8/3 r^-2 d_th V_r + 1/3 r^-1 d_r d_th V_r
+      //    - 7/3 cos r^-2 sin^-2 d_ph V_ph + 1/3 r^-2 sin^-1 d_th d_ph V_ph
+      c[12] = cE;
+      c[13] = cW;
+      c[14] = ir2 * tN + t3 * ir2 * ih1s + t3 * cot * ir2 * hc1;
+      c[15] = ir2 * tS + t3 * ir2 * ih1s - t3 * cot * ir2 * hc1;
+      c[16] = ir2 * pf;
+      c[17] = -lapc - 2.0 * t3 * ir2 * ih1s - 4.0 * t3 * ir2 * ist2;
+      c[18] = 8.0 * t3 * ir2 * hc1;
+      c[19] = t3 * ir * m01;
+      c[20] = three ? -7.0 * t3 * ct * ir2 * ist2 * hc2 : 0.0;
+      c[21] = three ? t3 * ir2 * ist * m12 : 0.0;
+      // phi: lap V_ph + 1/3 r^-2 sin^-2 d_phph V_ph - r^-2 sin^-2 V_ph
+      //    + 8/3 r^-2 sin^-1 d_ph V_r + 1/3 r^-1 sin^-1 d_r d_ph V_r
+      //    + 7/3 cos r^-2 sin^-2 d_ph V_th + 1/3 r^-2 sin^-1 d_th d_ph V_th
+      c[22] = cE;
+      c[23] = cW;
+      c[24] = ir2 * tN;
+      c[25] = ir2 * tS;
+      c[26] = ir2 * pf + (three ? t3 * ir2 * ist2 * ih2s : 0.0);
+      c[27] = -lapc - (three ? 2.0 * t3 * ir2 * ist2 * ih2s : 0.0) - ir2 * ist2;
+      c[28] = three ? 8.0 * t3 * ir2 * ist * hc2 : 0.0;
+      c[29] = three ? t3 * ir * ist * m02 : 0.0;
+      c[30] = three ? 7.0 * t3 * ct * ir2 * ist2 * hc2 : 0.0;
+      c[31] = three ? t3 * ir2 * ist * m12 : 0.0;
+      c[32] = x * x * s;  // norm weight r^2 sin(theta)
+      for (int q = 0; q < VC_N; ++q) vc[((size_t)q * n1 + j) * n0 + i] = c[q];
+    }
+}
+
 template <typename T>
 LevelView<T> make_view(const mg_grid_desc* d, const Level& L, const T* ti, const T* tj) {
   LevelView<T> v;
@@ -361,6 +434,7 @@ LevelView<T> make_view(const mg_grid_desc* d, const Level& L, const T* ti, const
   while ((1 << v.ln1) < L.n[1]) ++v.ln1;
   v.ti = ti;
   v.tj = tj;
+  v.vc = nullptr;
   return v;
 }
 
@@ -1204,6 +1278,12 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
       ce = cudaMemcpyAsync(L.ti32, ti32.data(), sizeof(float) * ti32.size(), cudaMemcpyHostToDevice, H->st);
     if (ce == cudaSuccess)
       ce = cudaMemcpyAsync(L.tj32, tj32.data(), sizeof(float) * tj32.size(), cudaMemcpyHostToDevice, H->st);
+    std::vector<double> vc;
+    if (L.vc64) {
+      make_vec_coeffs(&H->d, L, ti, tj, vc);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(L.vc64, vc.data(), sizeof(double) * vc.size(), cudaMemcpyHostToDevice, H->st);
+    }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(H->st);  // host tables go out of scope
     if (ce != cudaSuccess) {
       mg_destroy_hierarchy(H);
@@ -1211,6 +1291,7 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
       return MG_ERR_CUDA;
     }
     L.v64 = make_view<double>(&H->d, L, L.ti64, L.tj64);
+    L.v64.vc = L.vc64;
     L.v32 = make_view<float>(&H->d, L, L.ti32, L.tj32);
   }
   *out = H;

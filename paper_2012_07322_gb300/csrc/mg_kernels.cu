@@ -424,6 +424,68 @@ __global__ void __launch_bounds__(256, 2) k_residual_vec(LevelView<T> L, const T
   if (red) block_max_bits<3>(m, red);
 }
 
+// The FP64 vector residual on a spherical level with four-point mixed
+// derivatives from the per-(i, j) stencil coefficients L.vc (make_vec_coeffs):
+// the operator of vec_op with its metric factors multiplied out, one FMA per
+// stencil term, about a third of vec_op's FP64 operations (the FP64 pipe
+// bounds this kernel).  Outputs and norms as k_residual_vec.  A 3D block is
+// 32 x 2 x 4 cells, so four k-planes share each (i, j) coefficient load.
+__global__ void __launch_bounds__(256, 2)
+    k_residual_vec_sph(LevelView<double> L, const double* __restrict__ A, const double* __restrict__ B,
+                       const double* __restrict__ C, const double* __restrict__ f0, const double* __restrict__ f1,
+                       const double* __restrict__ f2, double* __restrict__ r0, double* __restrict__ r1,
+                       double* __restrict__ r2, float* __restrict__ q0, float* __restrict__ q1,
+                       float* __restrict__ q2, unsigned long long* red, int weighted) {
+  pdl_entry();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  unsigned long long m[3] = {0ULL, 0ULL, 0ULL};
+  if (i < L.n0 && j < L.n1 && k < L.n2) {
+    const long p = L.idx(i, j, k), sx = L.sx, sy = L.sy;
+    const long qs = (long)L.n0 * L.n1;
+    const double* __restrict__ V = L.vc + (long)j * L.n0 + i;
+    auto cf = [&](int q) { return V[q * qs]; };
+    // mix4(F; a, b) = F(+a+b) - F(+a-b) - F(-a+b) + F(-a-b)
+    auto mix4 = [&](const double* F, long a, long b) {
+      return ((F[p + a + b] - F[p + a - b]) - F[p - a + b]) + F[p - a - b];
+    };
+    const double Ac = A[p], Bc = B[p], Cc = C[p];
+    double Lu0 = cf(0) * A[p + 1] + cf(1) * A[p - 1] + cf(2) * A[p + sx] + cf(3) * A[p - sx] + cf(5) * Ac +
+                 cf(6) * (B[p + sx] - B[p - sx]) + cf(7) * Bc + cf(8) * (B[p + 1] - B[p - 1]) +
+                 cf(9) * mix4(B, 1, sx);
+    double Lu1 = cf(12) * B[p + 1] + cf(13) * B[p - 1] + cf(14) * B[p + sx] + cf(15) * B[p - sx] + cf(17) * Bc +
+                 cf(18) * (A[p + sx] - A[p - sx]) + cf(19) * mix4(A, 1, sx);
+    double Lu2 = cf(22) * C[p + 1] + cf(23) * C[p - 1] + cf(24) * C[p + sx] + cf(25) * C[p - sx] + cf(27) * Cc;
+    if (L.three) {
+      Lu0 += cf(4) * (A[p + sy] + A[p - sy]) + cf(10) * (C[p + sy] - C[p - sy]) + cf(11) * mix4(C, 1, sy);
+      Lu1 += cf(16) * (B[p + sy] + B[p - sy]) + cf(20) * (C[p + sy] - C[p - sy]) + cf(21) * mix4(C, sx, sy);
+      Lu2 += cf(26) * (C[p + sy] + C[p - sy]) + cf(28) * (A[p + sy] - A[p - sy]) + cf(29) * mix4(A, 1, sy) +
+             cf(30) * (B[p + sy] - B[p - sy]) + cf(31) * mix4(B, sx, sy);
+    }
+    const double w = weighted ? cf(32) : 1.0;
+    const double* fs[3] = {f0, f1, f2};
+    double* rs[3] = {r0, r1, r2};
+    float* qo[3] = {q0, q1, q2};
+    const double Lu[3] = {Lu0, Lu1, Lu2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double fv = fs[c] ? fs[c][p] : 0.0;
+      const double rv = fv - Lu[c];
+      if (rs[c]) rs[c][p] = rv;
+      if (qo[c]) qo[c][p] = (float)rv;
+      if (red) {
+        m[0] = umax64(m[0], abs_bits(rv));
+        if (weighted) {
+          m[1] = umax64(m[1], abs_bits(w * rv));
+          m[2] = umax64(m[2], abs_bits(w * fv));
+        }
+      }
+    }
+  }
+  if (red) block_max_bits<3>(m, red);
+}
+
 // f <- L(u) + f (the FAS coarse right-hand side after restriction placed
 // R r into f), or out = L(u) when add == 0.
 template <typename T, int G, int KIND>
@@ -931,6 +993,15 @@ void launch_residual_vec(const LevelView<T>& L, T* const V[3], const T* const f[
   float* q[3] = {nullptr, nullptr, nullptr};
   if (r32)
     for (int c = 0; c < 3; ++c) q[c] = r32[c];
+  if constexpr (sizeof(T) == 8) {
+    if (L.geom == SPH && L.vc && L.mixed == 0) {
+      const dim3 bs(32, L.three ? 2 : 8, L.three ? 4 : 1);
+      const dim3 gs(cdiv(L.n0, 32), cdiv(L.n1, bs.y), cdiv(L.n2, bs.z));
+      launch_k(k_residual_vec_sph, gs, bs, 0, st, L, V[0], V[1], V[2], f[0], f[1], f[2], r[0], r[1], r[2], q[0],
+               q[1], q[2], red, weighted);
+      return;
+    }
+  }
   GMG_GEOM_DISPATCH(L.geom, launch_k(k_residual_vec<T, GG>, g, b, 0, st, L, V[0], V[1], V[2], f[0], f[1], f[2], r[0], r[1], r[2], q[0], q[1], q[2], red, weighted));
 }
 
