@@ -95,18 +95,18 @@ BYTES_PER_CELL = {"smooth64_scalar": 5 * 8, "smooth64_vec": 8 * 8, "smooth32_sca
 
 # The finest FP64 residuals are bound by the FP64 pipe (GB300 issues 2 FP64
 # FMA per SM and clock, 1/64 of its FP32 rate), not by memory.  Algorithmic
-# FP64 flops per cell of the spherical operators as written (+, -, x count
-# one, a multiply-add two; the Newton diagonal excluded):
-#   vector (lap V + 1/3 grad div V, 3 components, and f - L): 80 + 72 + 68 + 3
+# FP64 flops per cell of the spherical operators as the kernels evaluate them
+# (+, -, x count one, a multiply-add two; the Newton diagonal excluded):
+#   vector, from per-(i, j) stencil coefficients (3 components: 34 + 29 + 29,
+#   and f - L: 3); vec_op as written costs 220
 #   scalar, linear (flux-form Laplacian 18, - c u, f - L): 22
-FLOPS_PER_CELL = {"resid64_vec": 223, "resid64_scalar": 22}
+FLOPS_PER_CELL = {"resid64_vec": 95, "resid64_scalar": 22}
 FP64_FMA_PER_SM_CLK = 2
 
 # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of the current kernel version: the 128x64x64
-# spherical vector residual (its working set sits in L2) and the 256^3
-# one-launch FP32 sweep.
-TRAFFIC_PER_LAUNCH = {"resid64_vec": 27.68e6, "sweep32_fused": 185.76e6}
+# from one ncu capture of the current kernel version: the 256^3 one-launch
+# FP32 sweep.
+TRAFFIC_PER_LAUNCH = {"sweep32_fused": 185.76e6}
 
 
 class ClockSampler:

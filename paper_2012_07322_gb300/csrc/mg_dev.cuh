@@ -354,10 +354,52 @@ __device__ __forceinline__ T lap_ghosted(const LevelView<T>& L, const T* __restr
   return Lu;
 }
 
+// Component c of lap V + 1/3 grad div V on a spherical level from the
+// per-(i, j) stencil coefficients L.vc (four-point mixed derivatives; slot
+// layout of VC_N), and its own-value derivative (the centre coefficient).
+// The operator of the flux form below with the metric factors multiplied
+// out: about a third of the arithmetic and a third of the table loads.
+template <typename T>
+__device__ __forceinline__ T vec_op_vc(const LevelView<T>& L, const T* __restrict__ A, const T* __restrict__ B,
+                                       const T* __restrict__ C, int c, int i, int j, long p, T& diag) {
+  const long sx = L.sx, sy = L.sy, qs = (long)L.n0 * L.n1;
+  const T* __restrict__ V = L.vc + (long)j * L.n0 + i;
+  auto cf = [&](int q) { return V[q * qs]; };
+  auto mix4 = [&](const T* F, long a, long b) {
+    return ((F[p + a + b] - F[p + a - b]) - F[p - a + b]) + F[p - a - b];
+  };
+  T Lu;
+  if (c == 0) {
+    diag = cf(5);
+    Lu = cf(0) * A[p + 1] + cf(1) * A[p - 1] + cf(2) * A[p + sx] + cf(3) * A[p - sx] + diag * A[p] +
+         cf(6) * (B[p + sx] - B[p - sx]) + cf(7) * B[p] + cf(8) * (B[p + 1] - B[p - 1]) + cf(9) * mix4(B, 1, sx);
+    if (L.three)
+      Lu += cf(4) * (A[p + sy] + A[p - sy]) + cf(10) * (C[p + sy] - C[p - sy]) + cf(11) * mix4(C, 1, sy);
+  } else if (c == 1) {
+    diag = cf(17);
+    Lu = cf(12) * B[p + 1] + cf(13) * B[p - 1] + cf(14) * B[p + sx] + cf(15) * B[p - sx] + diag * B[p] +
+         cf(18) * (A[p + sx] - A[p - sx]) + cf(19) * mix4(A, 1, sx);
+    if (L.three)
+      Lu += cf(16) * (B[p + sy] + B[p - sy]) + cf(20) * (C[p + sy] - C[p - sy]) + cf(21) * mix4(C, sx, sy);
+  } else {
+    diag = cf(27);
+    Lu = cf(22) * C[p + 1] + cf(23) * C[p - 1] + cf(24) * C[p + sx] + cf(25) * C[p - sx] + diag * C[p];
+    if (L.three)
+      Lu += cf(26) * (C[p + sy] + C[p - sy]) + cf(28) * (A[p + sy] - A[p - sy]) + cf(29) * mix4(A, 1, sy) +
+            cf(30) * (B[p + sy] - B[p - sy]) + cf(31) * mix4(B, sx, sy);
+  }
+  return Lu;
+}
+
 // Component c of lap V + 1/3 grad div V and its own-value derivative.
 template <typename T, int G>
 __device__ __forceinline__ T vec_op(const LevelView<T>& L, const T* __restrict__ A, const T* __restrict__ B,
                                     const T* __restrict__ C, int c, int i, int j, long p, T& diag) {
+  if constexpr (G == SPH && sizeof(T) == 4) {
+    // FP32 (smoother and correction residual of mixed precision): the
+    // coefficient form when the level carries the table
+    if (L.vc && L.mixed == 0) return vec_op_vc<T>(L, A, B, C, c, i, j, p, diag);
+  }
   const T third = T(1) / T(3);
   Stencil<T> s{L, p};
   T LD;

@@ -38,6 +38,7 @@ struct Level {
   double* ti64 = nullptr;
   double* tj64 = nullptr;
   double* vc64 = nullptr;  // spherical, four-point mixed derivatives: VC_N x n0 x n1
+  float* vc32 = nullptr;   // the same in FP32 (FP32 vector smoother and residual)
   float* ti32 = nullptr;
   float* tj32 = nullptr;
   double *u[3] = {}, *uh[3] = {}, *f[3] = {}, *r[3] = {}, *s0 = nullptr, *s1 = nullptr;
@@ -235,8 +236,10 @@ size_t layout(mg_hierarchy* H, const mg_grid_desc* d, char* base) {
     t64(L ? &L->ti64 : &dummy64, sizeof(double) * NTI * (n[l][0] + 2));
     t64(L ? &L->tj64 : &dummy64, sizeof(double) * NTJ * (n[l][1] + 2));
     t32(L ? &L->ti32 : &dummy32, sizeof(float) * NTI * (n[l][0] + 2));
-    if (d->geom == MG_SPH && d->mixed_deriv == MG_MIXED_4PT)
+    if (d->geom == MG_SPH && d->mixed_deriv == MG_MIXED_4PT) {
       t64(L ? &L->vc64 : &dummy64, sizeof(double) * VC_N * n[l][0] * n[l][1]);
+      if (mixed) t32(L ? &L->vc32 : &dummy32, sizeof(float) * VC_N * n[l][0] * n[l][1]);
+    }
     t32(L ? &L->tj32 : &dummy32, sizeof(float) * NTJ * (n[l][1] + 2));
     for (int c = 0; c < 3; ++c) {
       t64(L ? &L->u[c] : &dummy64, b64);
@@ -1279,10 +1282,16 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
     if (ce == cudaSuccess)
       ce = cudaMemcpyAsync(L.tj32, tj32.data(), sizeof(float) * tj32.size(), cudaMemcpyHostToDevice, H->st);
     std::vector<double> vc;
+    std::vector<float> vc32;
     if (L.vc64) {
       make_vec_coeffs(&H->d, L, ti, tj, vc);
       if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(L.vc64, vc.data(), sizeof(double) * vc.size(), cudaMemcpyHostToDevice, H->st);
+      if (L.vc32) {
+        vc32.assign(vc.begin(), vc.end());
+        if (ce == cudaSuccess)
+          ce = cudaMemcpyAsync(L.vc32, vc32.data(), sizeof(float) * vc32.size(), cudaMemcpyHostToDevice, H->st);
+      }
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(H->st);  // host tables go out of scope
     if (ce != cudaSuccess) {
@@ -1293,6 +1302,7 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
     L.v64 = make_view<double>(&H->d, L, L.ti64, L.tj64);
     L.v64.vc = L.vc64;
     L.v32 = make_view<float>(&H->d, L, L.ti32, L.tj32);
+    L.v32.vc = L.vc32;
   }
   *out = H;
   return MG_OK;
