@@ -66,7 +66,7 @@ __device__ void bc_smooth(const BcLevel& B, int nsweeps) {
           for (long q = threadIdx.x; q < nh; q += blockDim.x) {
             int i, j, k;
             L.colour_cell(q, colour, i, j, k);
-            vec_update<float, G>(L, B.e[0], B.e[1], B.e[2], B.f[c], c, i, j, k);
+            vec_update<float, G, false>(L, B.e[0], B.e[1], B.e[2], B.f[c], c, i, j, k);
           }
           __syncthreads();
           bc_fill(L, B.e[c], c);
@@ -88,7 +88,7 @@ __device__ void bc_residual(const BcLevel& B) {
       B.r[0][p] = scalar_residual_cell<float, G, EQ_LIN>(L, B.e[0], B.f[0], nullptr, B.k, i, j, k, p, Sv);
     } else {
       #pragma unroll
-      for (int c = 0; c < 3; ++c) B.r[c][p] = vec_residual_cell<float, G>(L, B.e[0], B.e[1], B.e[2], B.f[c], c, i, j, p);
+      for (int c = 0; c < 3; ++c) B.r[c][p] = vec_residual_cell<float, G, false>(L, B.e[0], B.e[1], B.e[2], B.f[c], c, i, j, p);
     }
   }
   __syncthreads();

@@ -391,11 +391,13 @@ __device__ __forceinline__ T vec_op_vc(const LevelView<T>& L, const T* __restric
   return Lu;
 }
 
-// Component c of lap V + 1/3 grad div V and its own-value derivative.
-template <typename T, int G>
+// Component c of lap V + 1/3 grad div V and its own-value derivative.  VC
+// false compiles the flux form only (the one-block cycle: its register
+// budget of 128 would spill with both forms).
+template <typename T, int G, bool VC = true>
 __device__ __forceinline__ T vec_op(const LevelView<T>& L, const T* __restrict__ A, const T* __restrict__ B,
                                     const T* __restrict__ C, int c, int i, int j, long p, T& diag) {
-  if constexpr (G == SPH && sizeof(T) == 4) {
+  if constexpr (VC && G == SPH && sizeof(T) == 4) {
     // FP32 (smoother and correction residual of mixed precision): the
     // coefficient form when the level carries the table
     if (L.vc && L.mixed == 0) return vec_op_vc<T>(L, A, B, C, c, i, j, p, diag);

@@ -97,13 +97,13 @@ __device__ __forceinline__ void scalar_update_lin_inv(const LevelView<T>& L, T* 
 }
 
 // One Newton-Gauss-Seidel update of vector component c (ghosts current).
-template <typename T, int G>
+template <typename T, int G, bool VC = true>
 __device__ __forceinline__ void vec_update(const LevelView<T>& L, T* __restrict__ A, T* __restrict__ B,
                                            T* __restrict__ C, const T* __restrict__ f, int c, int i, int j,
                                            int k) {
   const long p = L.idx(i, j, k);
   T D;
-  T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+  T Lu = vec_op<T, G, VC>(L, A, B, C, c, i, j, p, D);
   T* V = (c == 0) ? A : (c == 1 ? B : C);
   const T fv = f ? f[p] : T(0);
   V[p] = V[p] - (Lu - fv) / D;
@@ -207,12 +207,12 @@ __device__ __forceinline__ T scalar_residual_cell(const LevelView<T>& L, const T
 
 // Residual f_c - (lap V + 1/3 grad div V)_c of a vector equation (ghosts
 // current).
-template <typename T, int G>
+template <typename T, int G, bool VC = true>
 __device__ __forceinline__ T vec_residual_cell(const LevelView<T>& L, const T* __restrict__ A,
                                                const T* __restrict__ B, const T* __restrict__ C,
                                                const T* __restrict__ f, int c, int i, int j, long p) {
   T D;
-  const T Lu = vec_op<T, G>(L, A, B, C, c, i, j, p, D);
+  const T Lu = vec_op<T, G, VC>(L, A, B, C, c, i, j, p, D);
   const T fv = f ? f[p] : T(0);
   return fv - Lu;
 }
