@@ -1179,6 +1179,67 @@ typedef struct {
  * the Robin outer condition of eq. (robin); X and beta vanish at the outer
  * boundary (eq. bc).  Fields are interior arrays; psi, alpha, beta, X carry
  * the initial guess in and the solution out. */
+/* Step 6 of Sec. 2.6: the right-hand side of eq. (beta),
+ * 16 pi alpha psi^-6 S_i + 2 A~_ij grad_j(alpha psi^-6), from the interior
+ * fields X[3], dpsi = psi - 1 and dap = alpha psi - 1.  s = alpha psi^-6 =
+ * (alpha psi) psi^-7 is formed on the ghosted grid (Robin ghosts of the two
+ * deviations), X with its Dirichlet ghosts. */
+static void beta_rhs(const or_desc* d, double* const X[3], const double* dpsi, const double* dap,
+                     double* const Si[3], double* const f[3]) {
+  OGrid g;
+  finest_grid(d, &g);
+  double* gp = calloc(g.size, sizeof(double));
+  double* ga = calloc(g.size, sizeof(double));
+  double* sg = calloc(g.size, sizeof(double));
+  load_interior(&g, gp, dpsi);
+  load_interior(&g, ga, dap);
+  fill_ghosts(&g, gp, BC_ROBIN, -1);
+  fill_ghosts(&g, ga, BC_ROBIN, -1);
+  for (long p = 0; p < g.size; ++p) sg[p] = (1.0 + ga[p]) / pow(1.0 + gp[p], 7);
+  double* Xg[3];
+  for (int c = 0; c < 3; ++c) {
+    Xg[c] = calloc(g.size, sizeof(double));
+    load_interior(&g, Xg[c], X[c]);
+    fill_ghosts(&g, Xg[c], BC_DIRICHLET, c);
+  }
+  long q = 0;
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i, ++q) {
+        double A[6], G[3];
+        aij_at(&g, Xg, i, j, k, A);
+        grad_phys(&g, sg, i, j, k, G);
+        double sv = sg[IX(&g, i, j, k)];
+        /* (A~ . grad s)_i with A~ symmetric: rows (0: A0 A3 A4), (1: A3 A1 A5), (2: A4 A5 A2) */
+        double AG0 = A[0] * G[0] + A[3] * G[1] + A[4] * G[2];
+        double AG1 = A[3] * G[0] + A[1] * G[1] + A[5] * G[2];
+        double AG2 = A[4] * G[0] + A[5] * G[1] + A[2] * G[2];
+        f[0][q] = 16.0 * OR_PI * sv * Si[0][q] + 2.0 * AG0;
+        f[1][q] = 16.0 * OR_PI * sv * Si[1][q] + 2.0 * AG1;
+        f[2][q] = 16.0 * OR_PI * sv * Si[2][q] + 2.0 * AG2;
+      }
+  for (int c = 0; c < 3; ++c) free(Xg[c]);
+  free(gp);
+  free(ga);
+  free(sg);
+}
+
+/* Exported Step 6 (interior psi and alpha in): used by the tests to check
+ * full-size GPU solutions against the discrete equations. */
+void or_beta_rhs(const or_desc* d, double* const X[3], const double* psi, const double* alpha,
+                 double* const Si[3], double* const f[3]) {
+  long N = ncells(d);
+  double* dpsi = calloc(N, sizeof(double));
+  double* dap = calloc(N, sizeof(double));
+  for (long q = 0; q < N; ++q) {
+    dpsi[q] = psi[q] - 1.0;
+    dap[q] = alpha[q] * psi[q] - 1.0;
+  }
+  beta_rhs(d, X, dpsi, dap, Si, f);
+  free(dpsi);
+  free(dap);
+}
+
 int or_solve_cfc(const or_desc* d, const double* U, const double* S, double* const Si[3],
                  double* psi, double* alpha, double* const beta[3], double* const X[3],
                  or_cfc_report* rep) {
@@ -1224,41 +1285,8 @@ int or_solve_cfc(const or_desc* d, const double* U, const double* S, double* con
       free(dpsi);
       goto done;
     }
-    /* Step 6: s = alpha psi^-6 = (alpha psi) psi^-7 on the ghosted grid */
-    double* gp = calloc(g.size, sizeof(double));
-    double* ga = calloc(g.size, sizeof(double));
-    double* sg = calloc(g.size, sizeof(double));
-    load_interior(&g, gp, dpsi);
-    load_interior(&g, ga, dap);
-    fill_ghosts(&g, gp, BC_ROBIN, -1);
-    fill_ghosts(&g, ga, BC_ROBIN, -1);
-    for (long p = 0; p < g.size; ++p) sg[p] = (1.0 + ga[p]) / pow(1.0 + gp[p], 7);
-    double* Xg[3];
-    for (int c = 0; c < 3; ++c) {
-      Xg[c] = calloc(g.size, sizeof(double));
-      load_interior(&g, Xg[c], X[c]);
-      fill_ghosts(&g, Xg[c], BC_DIRICHLET, c);
-    }
-    long q = 0;
-    for (int k = 0; k < g.n[2]; ++k)
-      for (int j = 0; j < g.n[1]; ++j)
-        for (int i = 0; i < g.n[0]; ++i, ++q) {
-          double A[6], G[3];
-          aij_at(&g, Xg, i, j, k, A);
-          grad_phys(&g, sg, i, j, k, G);
-          double sv = sg[IX(&g, i, j, k)];
-          /* (A~ . grad s)_i with A~ symmetric: rows (0: A0 A3 A4), (1: A3 A1 A5), (2: A4 A5 A2) */
-          double AG0 = A[0] * G[0] + A[3] * G[1] + A[4] * G[2];
-          double AG1 = A[3] * G[0] + A[1] * G[1] + A[5] * G[2];
-          double AG2 = A[4] * G[0] + A[5] * G[1] + A[2] * G[2];
-          f[0][q] = 16.0 * OR_PI * sv * Si[0][q] + 2.0 * AG0;
-          f[1][q] = 16.0 * OR_PI * sv * Si[1][q] + 2.0 * AG1;
-          f[2][q] = 16.0 * OR_PI * sv * Si[2][q] + 2.0 * AG2;
-        }
-    for (int c = 0; c < 3; ++c) free(Xg[c]);
-    free(gp);
-    free(ga);
-    free(sg);
+    /* Step 6 */
+    beta_rhs(d, X, dpsi, dap, Si, f);
     status = or_solve_vector(d, BC_DIRICHLET, f, beta, &rep->rep[3]);
     for (long q2 = 0; q2 < N; ++q2) alpha[q2] = (1.0 + dap[q2]) / psi[q2];
     free(cf);

@@ -95,6 +95,7 @@ def lib():
             _lib.or_solve_cfc.argtypes = [D, P, P, P, P, P, P, P, C.POINTER(CfcReport)]
             _lib.or_clean_divb.argtypes = [D, P, P, C.POINTER(DivbReport)]
             _lib.or_div_c.argtypes = [D, P, P]
+            _lib.or_beta_rhs.argtypes = [D, P, P, P, P, P]
         return _lib
 
 
@@ -231,3 +232,10 @@ def div_c(d, B):
     Bs = list(B) + [B[0]] * (3 - len(B))
     lib().or_div_c(C.byref(d), _parr(Bs), _p(out))
     return out
+
+
+def beta_rhs(d, X, psi, alpha, Si):
+    """Right-hand side of eq. (beta) from X, psi, alpha and S_i (Sec. 2.6 Step 6)."""
+    f = [np.zeros(shape(d)) for _ in range(3)]
+    lib().or_beta_rhs(C.byref(d), _parr(X), _p(psi), _p(alpha), _parr(Si), _parr(f))
+    return f
