@@ -820,3 +820,38 @@ def test_curvilinear_cleaning_removes_gradient_field(geom):
         assert rep["l2_div_after"] < 0.25 * rep["l2_div_before"]
         far_max.append(max(np.abs(b[far]).max() for b in B))
     assert far_max[0] / far_max[1] > 1.8 and far_max[1] / far_max[2] > 1.8, far_max
+
+
+def test_beta_source_terms():
+    """Right-hand side of eq. (beta), Sec. 2.6 Step 6: 16 pi alpha psi^-6 S_i
+    + 2 A~_ij d_j(alpha psi^-6).  With X = 0 (A~ = 0) it is the first term
+    alone; with psi = 1 and alpha linear in x (central differences exact) the
+    second term is 2 A~_ix times the slope, which pins the row/column pairing
+    of A~ (xx, xy, xz for the components x, y, z)."""
+    n, lo, hi = [12, 10, 8], [-1.0, -1.2, -0.9], [1.3, 1.1, 1.0]
+    d = o.desc("cart", n, lo, hi)
+    shp = o.shape(d)
+    rng = np.random.default_rng(5)
+    Si = [np.ascontiguousarray(rng.standard_normal(shp)) for _ in range(3)]
+    z, y, x = np.meshgrid(*[lo[k] + (np.arange(n[k]) + 0.5) * (hi[k] - lo[k]) / n[k] for k in (2, 1, 0)],
+                          indexing="ij")
+    psi = 1.0 + 0.1 * np.cos(x) * np.cos(y) * np.cos(z)
+    alpha = 0.9 - 0.05 * x * y
+    zero = [np.zeros(shp) for _ in range(3)]
+    f = o.beta_rhs(d, zero, psi, alpha, Si)
+    s = alpha / psi ** 6
+    for k in range(3):
+        assert np.allclose(f[k], 16 * PI * s * Si[k], rtol=1e-14, atol=0)
+
+    slope = 0.3
+    psi1 = np.ones(shp)
+    alpha1 = 0.8 + slope * x
+    X = [np.ascontiguousarray(np.sin(1.1 * x + 0.3 * y) * np.cos(0.7 * z)),
+         np.ascontiguousarray(np.cos(0.9 * y - 0.2 * z) * x),
+         np.ascontiguousarray(np.sin(0.5 * z + 0.4 * x) * y)]
+    A2, A6 = o.aij(d, X, want_components=True)
+    f = o.beta_rhs(d, X, psi1, alpha1, Si)
+    inner = (slice(1, -1),) * 3  # away from the outer (Robin) ghosts of alpha psi
+    for k, a in zip(range(3), (A6[0], A6[3], A6[4])):
+        want = 16 * PI * alpha1 * Si[k] + 2 * a * slope
+        assert np.allclose(f[k][inner], want[inner], rtol=1e-12, atol=1e-12)
