@@ -510,33 +510,41 @@ def main():
 
     # ------------------------------------------------------------ roofline
     peak, peak_kind = load_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, kms, kcells) = dom
-    launch_s = kms / max(nl, 1) * 1e-3
-    common = {"kernel": name, "launches": nl, "avg_launch_us": launch_s * 1e6,
-              "share_of_step_time": kms / prof_step_ms if prof_step_ms else None,
-              "measured": "CUDA events around each finest-level launch of this kernel during one profiled "
-                          "solve right after the timed steps (direct launches instead of graph replay)",
-              "kernel_classes": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
-    if name in FLOPS_PER_CELL:
-        # FP64-pipe bound: peak from the unit count and the maximum SM clock
-        sms = torch.cuda.get_device_properties(0).multi_processor_count
-        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-        fpeak = FP64_FMA_PER_SM_CLK * 2 * sms * mhz * 1e6 / 1e9
-        flops_launch = kcells * FLOPS_PER_CELL[name] / max(nl, 1)
-        achieved = flops_launch / launch_s / 1e9 if nl else 0.0
-        roofline = dict({"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "GFLOP/s (FP64)",
-                         "frac": achieved / fpeak, "traffic": TRAFFIC_PER_LAUNCH.get(name),
-                         "algorithmic_flops_per_launch": flops_launch,
-                         "peak_source": "derived: %d FP64 FMA/SM/clock x 2 x %d SMs x %.0f MHz"
-                                        % (FP64_FMA_PER_SM_CLK, sms, mhz)}, **common)
-    else:
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fpeak = FP64_FMA_PER_SM_CLK * 2 * sms * mhz * 1e6 / 1e9
+
+    def class_roofline(name, nl, kms, kcells):
+        launch_s = kms / max(nl, 1) * 1e-3
+        if name in FLOPS_PER_CELL:
+            # FP64-pipe bound: peak from the unit count and the maximum SM clock
+            flops_launch = kcells * FLOPS_PER_CELL[name] / max(nl, 1)
+            achieved = flops_launch / launch_s / 1e9 if nl else 0.0
+            return {"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "GFLOP/s (FP64)",
+                    "frac": achieved / fpeak, "traffic": TRAFFIC_PER_LAUNCH.get(name),
+                    "algorithmic_flops_per_launch": flops_launch,
+                    "peak_source": "derived: %d FP64 FMA/SM/clock x 2 x %d SMs x %.0f MHz"
+                                   % (FP64_FMA_PER_SM_CLK, sms, mhz)}
         bytes_launch = kcells * BYTES_PER_CELL[name] / max(nl, 1)
         achieved = bytes_launch / launch_s / 1e9 if nl else 0.0
-        roofline = dict({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(name),
-                         "algorithmic_bytes_per_launch": bytes_launch,
-                         "peak_source": peak_kind}, **common)
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": TRAFFIC_PER_LAUNCH.get(name), "algorithmic_bytes_per_launch": bytes_launch,
+                "peak_source": peak_kind}
+
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, kms, kcells) = dom
+    classes = {}
+    for k, v in prof.items():
+        classes[k] = {"launches": v[0], "ms": v[1]}
+        if v[0]:
+            cr = class_roofline(k, *v)
+            classes[k].update({"avg_launch_us": v[1] / v[0] * 1e3, "bound": cr["bound"], "frac": cr["frac"]})
+    roofline = dict(class_roofline(name, nl, kms, kcells),
+                    kernel=name, launches=nl, avg_launch_us=kms / max(nl, 1) * 1e3,
+                    share_of_step_time=kms / prof_step_ms if prof_step_ms else None,
+                    measured="CUDA events around each finest-level launch of this kernel during one profiled "
+                             "solve right after the timed steps (direct launches instead of graph replay)",
+                    kernel_classes=classes)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
