@@ -35,6 +35,21 @@ UNIT = "Gcell-updates/s"
 WORKLOAD = "xCFC full system (X, psi, alpha*psi, beta), 3D spherical 128x64x64, r<=100, rotating n=1 polytrope"
 
 
+def aggregate_ranks(dist, total_ms, updates, device):
+    """Whole-job numbers over the ranks: the slowest rank's timed milliseconds
+    and the cell updates of all ranks (each rank solves its own replica, weak
+    scaling).  dist is torch.distributed or None (one rank)."""
+    if dist is None:
+        return total_ms, float(updates)
+    import torch
+    t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -469,16 +484,7 @@ def main():
     prof = mg.mg_profile_read(h)
     mg.mg_profile_enable(h, False)
     prof_step_ms = prof_rep["ms"]
-    total_ms = sum(ms_steps)
-    if dist:
-        t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, all_updates = float(tmax[0]), float(tsum[1])
-    else:
-        all_updates = float(updates)
+    total_ms, all_updates = aggregate_ranks(dist, sum(ms_steps), updates, "cuda")
     value = all_updates / (total_ms * 1e-3) / 1e9
 
     # ------------------------------------------------------------------ e2e
