@@ -188,15 +188,24 @@ __device__ __forceinline__ T ghost_rule(const LevelView<T>& L, int comp, int d, 
   return f;
 }
 
-// Value of any ghost (face, edge or corner) of field u from its interior,
-// composing the per-dimension rules in the fill order 0, 1, 2.
+// Interior source of any ghost (face, edge or corner): (i, j, k) becomes
+// the cell the ghost derives from, f0, f1, f2 the factors of the
+// per-dimension rules, composed in the fill order 0, 1, 2.
 template <typename T>
-__device__ __forceinline__ T ghost_value(const LevelView<T>& L, const T* __restrict__ u, int comp, int i,
-                                         int j, int k) {
-  T f2 = T(1), f1 = T(1), f0 = T(1);
+__device__ __forceinline__ void ghost_source(const LevelView<T>& L, int comp, int& i, int& j, int& k, T& f0,
+                                             T& f1, T& f2) {
+  f2 = f1 = f0 = T(1);
   if (L.three && (k < 0 || k >= L.n2)) f2 = ghost_rule(L, comp, 2, i, j, k);
   if (j < 0 || j >= L.n1) f1 = ghost_rule(L, comp, 1, i, j, k);
   if (i < 0 || i >= L.n0) f0 = ghost_rule(L, comp, 0, i, j, k);
+}
+
+// Value of any ghost of field u from its interior.
+template <typename T>
+__device__ __forceinline__ T ghost_value(const LevelView<T>& L, const T* __restrict__ u, int comp, int i,
+                                         int j, int k) {
+  T f0, f1, f2;
+  ghost_source(L, comp, i, j, k, f0, f1, f2);
   return ((u[L.idx(i, j, k)] * f0) * f1) * f2;
 }
 

@@ -43,6 +43,7 @@ struct Level {
   float* tj32 = nullptr;
   double *u[3] = {}, *uh[3] = {}, *f[3] = {}, *r[3] = {}, *s0 = nullptr, *s1 = nullptr;
   float *e[3] = {}, *f32[3] = {}, *k32 = nullptr;
+  GhostPush push[3][2];  // per component and colour (Dirichlet-0 ghosts), or empty
   long cells() const { return (long)n[0] * n[1] * n[2]; }
 };
 
@@ -85,6 +86,10 @@ struct mg_hierarchy {
   double* cinv[3] = {};
   int cinv_state[3] = {0, 0, 0};
   double* d_aa_part = nullptr;  // AA_SCRATCH_DOUBLES of device scratch
+  // ghost-push tables of the vector colour passes: state 0 not built, 1
+  // built, -1 unavailable; one device buffer holds every level's tables
+  int push_state = 0;
+  int* push_buf = nullptr;
   bool prof_on = false;
   bool fold_k32 = false;  // while capturing a V-cycle of eq. psi: K is restricted on the way down
   std::vector<cudaEvent_t> ev;
@@ -447,6 +452,13 @@ LevelView<T> with_bc(LevelView<T> v, int bc) {
   return v;
 }
 
+// Ghost-push table of a vector colour pass, when built and the pass's ghost
+// rule is the one it was built for.
+GhostPush ghost_push(const mg_hierarchy* H, int l, int c, int colour, int bc) {
+  if (H->push_state != 1 || bc != MG_BC_DIRICHLET) return GhostPush{};
+  return H->L[l].push[c][colour];
+}
+
 // ------------------------------------------------------------- FP64 FAS
 
 const double* fptr(const mg_hierarchy* H, const Eq& e, int l, int c) {
@@ -489,9 +501,10 @@ void smooth64(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
       } else {
         for (int c = 0; c < 3; ++c) {
           long tok = prof_begin(H, l, MG_PROF_SMOOTH64_VEC, L.cells() / 2);
-          launch_smooth_vec(v, L.u, fptr(H, e, l, c), c, colour, H->st);
+          const GhostPush gp = ghost_push(H, l, c, colour, e.bc);
+          launch_smooth_vec(v, L.u, fptr(H, e, l, c), c, colour, H->st, gp);
           prof_end(H, tok);
-          launch_fill_ghosts(v, L.u[c], c, H->st);
+          if (!gp.off) launch_fill_ghosts(v, L.u[c], c, H->st);
         }
       }
     }
@@ -655,9 +668,10 @@ void smooth32(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
       } else {
         for (int c = 0; c < 3; ++c) {
           long tok = prof_begin(H, l, MG_PROF_SMOOTH32_VEC, L.cells() / 2);
-          launch_smooth_vec<float>(v, L.e, L.f32[c], c, colour, H->st);
+          const GhostPush gp = ghost_push(H, l, c, colour, e.bc);
+          launch_smooth_vec<float>(v, L.e, L.f32[c], c, colour, H->st, gp);
           prof_end(H, tok);
-          launch_fill_ghosts<float>(v, L.e[c], c, H->st);
+          if (!gp.off) launch_fill_ghosts<float>(v, L.e[c], c, H->st);
         }
       }
     }
@@ -1017,6 +1031,130 @@ int ensure_coarse_inverse(mg_hierarchy* H, int bc) {
   return MG_OK;
 }
 
+// Ghost-push tables (GhostPush) of the vector colour passes with Dirichlet-0
+// ghosts, for every level below the coarsest, built once per hierarchy
+// before its first vector solve (outside graph capture).  The sources come
+// from the device's own ghost rules.  A level and component keep the
+// ghost-fill launch when a ghost is not plus or minus one interior cell, or
+// when a cell of the pass that updates a ghost's source reads that ghost
+// (as a face neighbour; a component's own stencil reaches no further) from
+// another block.
+int ensure_ghost_push(mg_hierarchy* H) {
+  if (H->push_state != 0) return MG_OK;
+  H->push_state = -1;
+  const int nl = H->nlev - 1;
+  if (nl <= 0) return MG_OK;
+  long gmax = 0;
+  for (int l = 0; l < nl; ++l) gmax = std::max(gmax, ghost_count_host(H->L[l].v64));
+  int* dgc = nullptr;
+  double* dfac = nullptr;
+  if (cudaMalloc(&dgc, sizeof(int) * 8 * 3 * (size_t)gmax) != cudaSuccess ||
+      cudaMalloc(&dfac, sizeof(double) * 3 * (size_t)gmax) != cudaSuccess) {
+    cudaFree(dgc);
+    cudaFree(dfac);
+    cudaGetLastError();
+    return MG_OK;
+  }
+  std::vector<int> gc(8 * 3 * (size_t)gmax);
+  std::vector<double> fac(3 * (size_t)gmax);
+  std::vector<int> buf;  // per (level, component, colour): off[nb + 1], then 2 ints per entry
+  struct Where {
+    long off, ent;
+  };
+  std::vector<Where> at((size_t)nl * 6, Where{-1, -1});
+  cudaError_t ce = cudaSuccess;
+  for (int l = 0; l < nl && ce == cudaSuccess; ++l) {
+    const LevelView<double> v = with_bc(H->L[l].v64, MG_BC_DIRICHLET);
+    const long ng = ghost_count_host(v);
+    for (int c = 0; c < 3; ++c) launch_ghost_sources(v, c, dgc + 8 * c * ng, dfac + c * ng, H->st);
+    ce = cudaMemcpyAsync(gc.data(), dgc, sizeof(int) * 8 * 3 * ng, cudaMemcpyDeviceToHost, H->st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(fac.data(), dfac, sizeof(double) * 3 * ng, cudaMemcpyDeviceToHost, H->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(H->st);
+    if (ce != cudaSuccess) break;
+    const int n0 = v.n0, n1 = v.n1, n2 = v.three ? v.n2 : 1;
+    const long ncell = H->L[l].ng;  // cells of the level array, ghosts and padding included
+    const int nb = push_blocks(v);
+    auto interior = [&](int i, int j, int k) { return i >= 0 && i < n0 && j >= 0 && j < n1 && k >= 0 && k < n2; };
+    for (int c = 0; c < 3; ++c) {
+      const int* G = gc.data() + 8 * c * ng;
+      const double* F = fac.data() + c * ng;
+      std::vector<int> blk(ng), slot(ng), col(ng);
+      bool ok = true;
+      for (long g = 0; g < ng && ok; ++g) {
+        const int* o = G + 8 * g;
+        if (interior(o[0], o[1], o[2]) || !interior(o[3], o[4], o[5]) || (F[g] != 1.0 && F[g] != -1.0) ||
+            o[6] < 0 || o[6] >= ncell || o[7] < 0 || o[7] >= ncell) {
+          ok = false;
+          break;
+        }
+        push_slot(v, o[3], o[4], o[5], &blk[g], &slot[g]);
+        col[g] = (o[3] + o[4] + o[5]) & 1;
+        if (blk[g] < 0 || blk[g] >= nb || slot[g] < 0 || slot[g] >= 256) ok = false;
+        // face neighbours of the ghost updated in the same pass as its source
+        for (int d = 0; d < (v.three ? 3 : 2) && ok; ++d)
+          for (int s = -1; s <= 1 && ok; s += 2) {
+            const int r[3] = {o[0] + (d == 0) * s, o[1] + (d == 1) * s, o[2] + (d == 2) * s};
+            if (!interior(r[0], r[1], r[2]) || ((r[0] + r[1] + r[2]) & 1) != col[g]) continue;
+            if (r[0] == o[3] && r[1] == o[4] && r[2] == o[5]) continue;
+            int rb, rt;
+            push_slot(v, r[0], r[1], r[2], &rb, &rt);
+            if (rb != blk[g]) ok = false;
+          }
+      }
+      if (!ok) continue;
+      for (int colour = 0; colour < 2; ++colour) {
+        Where w;
+        w.off = (long)buf.size();
+        buf.resize(buf.size() + nb + 1, 0);
+        if (buf.size() & 1) buf.push_back(0);  // entries 8-byte aligned
+        w.ent = (long)buf.size();
+        int* offp = nullptr;
+        long cnt = 0;
+        for (long g = 0; g < ng; ++g) cnt += col[g] == colour;
+        buf.resize(buf.size() + 2 * cnt);
+        offp = buf.data() + w.off;
+        for (long g = 0; g < ng; ++g)
+          if (col[g] == colour) offp[blk[g] + 1] += 1;
+        for (int b = 0; b < nb; ++b) offp[b + 1] += offp[b];
+        std::vector<int> fillp(offp, offp + nb);
+        for (long g = 0; g < ng; ++g) {
+          if (col[g] != colour) continue;
+          int* q = buf.data() + w.ent + 2 * (long)(fillp[blk[g]]++);
+          q[0] = G[8 * g + 6];
+          q[1] = 2 * slot[g] + (F[g] < 0.0 ? 1 : 0);
+        }
+        at[(size_t)(l * 3 + c) * 2 + colour] = w;
+      }
+    }
+  }
+  cudaFree(dgc);
+  cudaFree(dfac);
+  if (ce != cudaSuccess) return fail(MG_ERR_CUDA, cudaGetErrorString(ce));
+  if (buf.empty()) return MG_OK;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int) * buf.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_OK;
+  }
+  ce = cudaMemcpyAsync(d, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice, H->st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(H->st);
+  if (ce != cudaSuccess) {
+    cudaFree(d);
+    return fail(MG_ERR_CUDA, cudaGetErrorString(ce));
+  }
+  H->push_buf = d;
+  for (int l = 0; l < nl; ++l)
+    for (int c = 0; c < 3; ++c)
+      for (int colour = 0; colour < 2; ++colour) {
+        const Where w = at[(size_t)(l * 3 + c) * 2 + colour];
+        if (w.off < 0) continue;
+        H->L[l].push[c][colour].off = d + w.off;
+        H->L[l].push[c][colour].ent = reinterpret_cast<const int2*>(d + w.ent);
+      }
+  H->push_state = 1;
+  return MG_OK;
+}
+
 int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   auto t0 = std::chrono::steady_clock::now();
   H->updates = 0;
@@ -1026,6 +1164,8 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   const int m = d.accel_depth;
   if (mixed && e.kind == EQ_VEC)
     if (int est = ensure_coarse_inverse(H, e.bc)) return est;
+  if (e.kind == EQ_VEC && e.bc == MG_BC_DIRICHLET)
+    if (int est = ensure_ghost_push(H)) return est;
   if (e.kind == EQ_VEC) fill_all64(H, e, 0);
   restrict_sources(H, e);
   if (mixed && e.kind == EQ_LIN && e.has_c) {
@@ -1347,6 +1487,7 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   for (double* p : H->cinv)
     if (p) cudaFree(p);
   if (H->d_aa_part) cudaFree(H->d_aa_part);
+  if (H->push_buf) cudaFree(H->push_buf);
   for (GraphEntry& g : H->graphs) cudaGraphExecDestroy(g.exec);
   if (H->own_stream) cudaStreamDestroy(H->st);
   if (H->ev_in) cudaEventDestroy(H->ev_in);
@@ -1653,6 +1794,8 @@ int mg_smooth(mg_hierarchy* H, int kind, int bc, int nsweeps, double* u[3], cons
   } else if (c) {
     copy_in(H, c, L0.s1);
   }
+  if (kind == MG_EQ_VEC && bc == MG_BC_DIRICHLET)
+    if (int est = ensure_ghost_push(H)) return est;
   if (kind == MG_EQ_VEC) fill_all64(H, e, 0);
   smooth64(H, e, 0, nsweeps);
   for (int q = 0; q < nc; ++q) copy_out(H, L0.u[q], u[q]);

@@ -100,8 +100,33 @@ template <typename T>
 inline bool fused_sweep_applies(const LevelView<T>& L) {
   return L.geom == CART && L.three && L.n0 >= 64 && L.n1 >= 8 && L.n2 >= 4;
 }
+// Ghost push of the vector smoother's colour passes.  With a table, the
+// pass of component c also rewrites, at its end, every ghost of c whose
+// source cell it has just updated, in place of a ghost-fill launch after
+// it.  The entries of block b (blocks numbered x fastest) are ent[off[b]]
+// .. ent[off[b + 1] - 1]: x = the ghost's index in the level array, y = 2 *
+// (the source cell's thread in the block) + 1 when the ghost is the negated
+// source.  A 3D pass with a table puts planes k and k + n2 / 2 in one block
+// (thread z), so that a pole ghost and the same-colour cell that reads it
+// in the same pass belong to one block, which reads before it writes.
+struct GhostPush {
+  const int* off = nullptr;
+  const int2* ent = nullptr;
+};
 template <typename T>
-void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st);
+void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st,
+                       GhostPush gp = GhostPush{});
+// Block count of a pass with a ghost-push table, and the block and thread
+// of that pass which update cell (i, j, k).
+template <typename T>
+int push_blocks(const LevelView<T>& L);
+template <typename T>
+void push_slot(const LevelView<T>& L, int i, int j, int k, int* block, int* thread);
+// Source of every ghost of vector component comp, in the enumeration of
+// the ghost fill: gc[8 g ..] = ghost i, j, k, source i, j, k, ghost index,
+// source index; fac[g] = the product of the boundary factors.
+template <typename T>
+void launch_ghost_sources(const LevelView<T>& L, int comp, int* gc, T* fac, cudaStream_t st);
 // r = f - L(u) into r (nullable) and, rounded to FP32, into r32 (nullable);
 // red (nullable) receives the norms of the finest-level stopping rule; for
 // eq. psi, k32 (nullable) receives the linearisation 2 pi U (1+u)^-2 +

@@ -32,16 +32,49 @@ __global__ void k_smooth_scalar(LevelView<T> L, T* __restrict__ u, const T* __re
   scalar_update<T, G, KIND>(L, u, f, s0, s1, i, j, k);
 }
 
+// One colour of component comp of the vector sweep.  With a ghost-push
+// table the block then rewrites the ghosts sourced by the cells it updated
+// (their new values kept in shared memory), and in 3D thread z takes plane
+// blockIdx.z + z n2 / 2.
 template <typename T, int G>
 __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
-                             const T* __restrict__ f, int comp, int colour) {
-  pdl_entry();
+                             const T* __restrict__ f, int comp, int colour, GhostPush gp) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (2 * t >= L.n0 || j >= L.n1 || k >= L.n2) return;
-  const int i = 2 * t + ((j + k + colour) & 1);
-  vec_update<T, G>(L, A, B, C, f, comp, i, j, k);
+  if (!gp.off) {
+    pdl_entry();
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (2 * t >= L.n0 || j >= L.n1 || k >= L.n2) return;
+    const int i = 2 * t + ((j + k + colour) & 1);
+    vec_update<T, G>(L, A, B, C, f, comp, i, j, k);
+    return;
+  }
+  __shared__ T nv[256];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  // the table is written once, when the hierarchy builds it: its first
+  // entries are read before waiting for the preceding launch
+  const int e0 = gp.off[b], e1 = gp.off[b + 1];
+  int2 q0 = make_int2(0, 0);
+  if (e0 + tid < e1) q0 = gp.ent[e0 + tid];
+  pdl_entry();
+  const int k = L.three ? (int)blockIdx.z + (int)threadIdx.z * (L.n2 >> 1) : 0;
+  T* V = comp == 0 ? A : (comp == 1 ? B : C);
+  if (2 * t < L.n0 && j < L.n1 && k < L.n2) {
+    const int i = 2 * t + ((j + k + colour) & 1);
+    const long p = L.idx(i, j, k);
+    const T v = vec_new_value<T, G>(L, A, B, C, f, comp, i, j, p);
+    V[p] = v;
+    nv[tid] = v;
+  }
+  if (e0 == e1) return;  // the same for the whole block
+  __syncthreads();
+  for (int e = e0 + tid; e < e1; e += nthr) {
+    const int2 q = e == e0 + tid ? q0 : gp.ent[e];
+    const T v = nv[q.y >> 1];
+    V[q.x] = (q.y & 1) ? -v : v;
+  }
 }
 
 // One full red-black sweep of a Cartesian 3D linear scalar equation in one
@@ -967,10 +1000,56 @@ void launch_fill_ghosts(const LevelView<T>& L, T* u, int comp, cudaStream_t st) 
 }
 
 template <typename T>
-void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st) {
+void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st,
+                       GhostPush gp) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_colour(L, b);
-  GMG_GEOM_DISPATCH(L.geom, launch_k(k_smooth_vec<T, GG>, g, b, 0, st, L, V[0], V[1], V[2], f, comp, colour));
+  if (gp.off && L.three) g.z = (unsigned)(L.n2 / 2);  // b.z = 2: planes k and k + n2 / 2
+  GMG_GEOM_DISPATCH(L.geom,
+                    launch_k(k_smooth_vec<T, GG>, g, b, 0, st, L, V[0], V[1], V[2], f, comp, colour, gp));
+}
+
+template <typename T>
+int push_blocks(const LevelView<T>& L) {
+  const dim3 b = block_for(L.three), g = grid_colour(L, b);
+  return (int)(g.x * g.y * (L.three ? L.n2 / 2 : 1));
+}
+
+template <typename T>
+void push_slot(const LevelView<T>& L, int i, int j, int k, int* block, int* thread) {
+  const dim3 b = block_for(L.three), g = grid_colour(L, b);
+  const int t = i >> 1;
+  const int h = L.three ? L.n2 / 2 : 1;
+  const int bz = L.three ? k % h : 0, tz = L.three ? k / h : 0;
+  *block = (int)(t / b.x + g.x * (j / b.y + g.y * bz));
+  *thread = (int)(t % b.x + b.x * (j % b.y + b.y * tz));
+}
+
+template <typename T>
+__global__ void k_ghost_sources(LevelView<T> L, int comp, int* __restrict__ gc, T* __restrict__ fac) {
+  const long n = ghost_count(L);
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    ghost_coords(L, g, i, j, k);
+    int* o = gc + 8 * g;
+    o[0] = i;
+    o[1] = j;
+    o[2] = k;
+    o[6] = (int)L.idx(i, j, k);
+    T f0, f1, f2;
+    ghost_source(L, comp, i, j, k, f0, f1, f2);
+    o[3] = i;
+    o[4] = j;
+    o[5] = k;
+    o[7] = (int)L.idx(i, j, k);
+    fac[g] = (f0 * f1) * f2;
+  }
+}
+
+template <typename T>
+void launch_ghost_sources(const LevelView<T>& L, int comp, int* gc, T* fac, cudaStream_t st) {
+  count_launch();
+  k_ghost_sources<T><<<grid_flat(ghost_count_host(L), 256), 256, 0, st>>>(L, comp, gc, fac);
 }
 
 template <typename T>
@@ -1156,7 +1235,9 @@ void launch_add_correction(const LevelView<double>& L, int ncomp, double* const 
   template void launch_fill_ghosts3<T>(const LevelView<T>&, T* const[3], int, int, cudaStream_t);             \
   template void launch_prolong3<T>(const LevelView<T>&, const LevelView<T>&, T* const[3], const T* const[3],  \
                                    const T* const[3], int, int, cudaStream_t);                                 \
-  template void launch_smooth_vec<T>(const LevelView<T>&, T* [3], const T*, int, int, cudaStream_t);           \
+  template void launch_smooth_vec<T>(const LevelView<T>&, T* [3], const T*, int, int, cudaStream_t, GhostPush); \
+  template int push_blocks<T>(const LevelView<T>&);                                                            \
+  template void push_slot<T>(const LevelView<T>&, int, int, int, int*, int*);                                  \
   template void launch_residual_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, const T*, T*, \
                                           unsigned long long*, int, cudaStream_t, float*, float*);              \
   template void launch_residual_vec<T>(const LevelView<T>&, T* const[3], const T* const[3], T* const[3],       \
@@ -1174,6 +1255,7 @@ void launch_add_correction(const LevelView<double>& L, int ncomp, double* const 
   template void launch_sub_mean<T>(const LevelView<T>&, T*, double*, int, cudaStream_t, bool);
 GMG_INST(double)
 GMG_INST(float)
+template void launch_ghost_sources<double>(const LevelView<double>&, int, int*, double*, cudaStream_t);
 template void launch_copy_in<double, double>(const LevelView<double>&, const double*, double*, double, cudaStream_t);
 template void launch_copy_out<double, double>(const LevelView<double>&, const double*, double*, double, cudaStream_t);
 template void launch_convert<double, float>(const LevelView<double>&, const double*, float*, cudaStream_t);

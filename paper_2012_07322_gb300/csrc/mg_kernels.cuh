@@ -96,17 +96,27 @@ __device__ __forceinline__ void scalar_update_lin_inv(const LevelView<T>& L, T* 
   u[p] = u[p] - (Lu - fv) * invD;
 }
 
+// New value of vector component c at a cell after one Newton-Gauss-Seidel
+// update (ghosts current).
+template <typename T, int G, bool VC = true>
+__device__ __forceinline__ T vec_new_value(const LevelView<T>& L, T* __restrict__ A, T* __restrict__ B,
+                                           T* __restrict__ C, const T* __restrict__ f, int c, int i, int j,
+                                           long p) {
+  T D;
+  T Lu = vec_op<T, G, VC>(L, A, B, C, c, i, j, p, D);
+  const T* V = (c == 0) ? A : (c == 1 ? B : C);
+  const T fv = f ? f[p] : T(0);
+  return V[p] - (Lu - fv) / D;
+}
+
 // One Newton-Gauss-Seidel update of vector component c (ghosts current).
 template <typename T, int G, bool VC = true>
 __device__ __forceinline__ void vec_update(const LevelView<T>& L, T* __restrict__ A, T* __restrict__ B,
                                            T* __restrict__ C, const T* __restrict__ f, int c, int i, int j,
                                            int k) {
   const long p = L.idx(i, j, k);
-  T D;
-  T Lu = vec_op<T, G, VC>(L, A, B, C, c, i, j, p, D);
   T* V = (c == 0) ? A : (c == 1 ? B : C);
-  const T fv = f ? f[p] : T(0);
-  V[p] = V[p] - (Lu - fv) / D;
+  V[p] = vec_new_value<T, G, VC>(L, A, B, C, f, c, i, j, p);
 }
 
 // Ghost cells of one field, enumerated as three disjoint layers:

@@ -131,6 +131,33 @@ def test_red_black_sweep_parity(mg, case):
     h.close()
 
 
+@pytest.mark.parametrize("geom,n,lo,hi,mixed", [
+    ("sph", [128, 16, 16], [0.0, 0.0, 0.0], [30.0, PI, 2 * PI], "4pt"),
+    ("sph", [128, 16, 16], [0.0, 0.0, 0.0], [30.0, PI, 2 * PI], "corner"),
+    ("cyl", [128, 16, 8], [0.0, -30.0, 0.0], [30.0, 34.0, 2 * PI], "4pt"),
+    ("sph", [128, 64], [0.0, 0.0], [30.0, PI], "4pt"),
+])
+def test_vector_sweep_parity_many_blocks(mg, geom, n, lo, hi, mixed):
+    """Vector sweeps (Dirichlet-0) on levels of several blocks in every
+    direction: the colour passes rewrite the ghosts of the cells they update
+    themselves, and the pole ghosts of 3D grids pair planes k and k + n/2;
+    the result is the oracle's, whose ghosts are refilled before each
+    colour."""
+    d, gd = descs(mg, geom, n, lo, hi, mixed=mixed)
+    h = mg.Hierarchy(gd)
+    shp = o.shape(d)
+    rng = np.random.default_rng(5)
+    V = [rng.uniform(-0.3, 0.3, shp) for _ in range(3)]
+    F = [rng.uniform(-0.01, 0.01, shp) for _ in range(3)]
+    Vg, Fg = [ghosted(d, x) for x in V], [ghosted(d, x) for x in F]
+    o.smooth(d, "vec", "dirichlet", 2, Vg, Fg)
+    Vt = [dev(x) for x in V]
+    mg.mg_smooth(h, "vec", "dirichlet", 2, Vt, f=[dev(x) for x in F])
+    h.close()
+    for k in range(3):
+        assert relerr(host(Vt[k]), interior(d, Vg[k])) < 1e-12, k
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_transfer_parity(mg, case):
     """Volume-weighted restriction and Kwak prolongation (Sec. 2.7.3)."""
