@@ -120,9 +120,10 @@ FP64_FMA_PER_SM_CLK = 2
 
 # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of the current kernel version (cold caches): the
-# level-0 FP32 vector colour pass and the FP64 vector residual of the
-# 128x64x64 spherical solve, and the 256^3 one-launch FP32 sweep.
-TRAFFIC_PER_LAUNCH = {"smooth32_vec": 9.62e6, "resid64_vec": 29.80e6, "sweep32_fused": 185.34e6}
+# level-0 FP32 vector colour pass (ghost push included) and the FP64 vector
+# residual of the 128x64x64 spherical solve, and the 256^3 one-launch FP32
+# sweep.  A kernel changed since its capture has none.
+TRAFFIC_PER_LAUNCH = {"smooth32_vec": 9.82e6, "resid64_vec": 29.80e6, "sweep32_fused": 185.34e6}
 
 
 class ClockSampler:
