@@ -855,3 +855,56 @@ def test_beta_source_terms():
     for k, a in zip(range(3), (A6[0], A6[3], A6[4])):
         want = 16 * PI * alpha1 * Si[k] + 2 * a * slope
         assert np.allclose(f[k][inner], want[inner], rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------- Anderson mixing
+
+
+def test_anderson_mixing_is_gmres_on_the_cycle_map():
+    """Anderson mixing of the V-cycle map (the oracle's accel_depth), pinned
+    by Walker & Ni (SIAM J. Numer. Anal. 49, 2011, Thm. 2.2): for an affine
+    map g(x) = M x + b and a history long enough that nothing is dropped, the
+    mixed iterate x_{k+1} equals g(x_k^GMRES), where x_k^GMRES is the k-th
+    GMRES iterate for (I - M) x = b from the same x_0.  A linear equation
+    makes one V-cycle affine; GMRES is built here independently (Arnoldi with
+    modified Gram-Schmidt and a least-squares solve), applying M only as
+    g(v) - g(0) through plain single cycles."""
+    n, lo, hi = [16, 8], [0.0, 0.0], [30.0, PI]
+    rng = np.random.default_rng(11)
+    shp = o.shape(o.desc("sph", n, lo, hi))
+    f = rng.uniform(-0.01, 0.01, shp)
+    c = rng.uniform(0.0, 0.05, shp)
+
+    def g(v, cycles=1, accel=0):
+        d = o.desc("sph", n, lo, hi, tol=0.0, max_cycles=cycles, stall_window=0, accel_depth=accel)
+        u = np.array(v, dtype=np.float64, copy=True)
+        rep = o.solve_scalar(d, "lin", "robin", u, c=c, f=f)
+        assert rep["cycles"] == cycles
+        return u
+
+    x0 = rng.uniform(-0.05, 0.05, shp)
+    b = g(np.zeros(shp))
+    r0 = (g(x0) - x0).ravel()  # b - (I - M) x0
+    K = 6
+    beta = np.linalg.norm(r0)
+    V = np.zeros((r0.size, K + 1))
+    H = np.zeros((K + 1, K))
+    V[:, 0] = r0 / beta
+    for j in range(K):
+        w = V[:, j] - (g(V[:, j].reshape(shp)) - b).ravel()  # (I - M) v
+        for i in range(j + 1):
+            H[i, j] = V[:, i] @ w
+            w -= H[i, j] * V[:, i]
+        H[j + 1, j] = np.linalg.norm(w)
+        V[:, j + 1] = w / H[j + 1, j]
+    for k in range(1, K + 1):
+        rhs = np.zeros(k + 1)
+        rhs[0] = beta
+        y = np.linalg.lstsq(H[:k + 1, :k], rhs, rcond=None)[0]
+        want = g(x0 + (V[:, :k] @ y).reshape(shp))
+        scale = np.abs(want).max()
+        mixed = g(x0, cycles=k + 1, accel=8)
+        plain = g(x0, cycles=k + 1)
+        # the mixing is what makes the difference: plain cycles are 1e-3..1e-2 away
+        assert np.abs(plain - want).max() > 1e-3 * scale, k
+        assert np.abs(mixed - want).max() <= 1e-7 * scale, k
