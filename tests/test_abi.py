@@ -50,3 +50,75 @@ def test_host_only_entry_points():
     with pytest.raises(mg.MgError):
         mg.mg_hierarchy_bytes(bad)
     assert mg.lib().mg_strerror(3) == b"not converged"
+
+
+def _set(d, **kw):
+    for k, v in kw.items():
+        if isinstance(v, tuple):
+            arr = getattr(d, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("what,geom,n,kw", [
+    ("empty grid", "cart", [0, 8, 8], {}),
+    ("one cell", "cart", [1, 8], {}),
+    ("n not a power of two", "cart", [12, 8, 8], {}),
+    ("negative n", "cart", [-8, 8], {}),
+    ("ndim 1", "cart", [8, 8], {"ndim": 1}),
+    ("ndim 4", "cart", [8, 8, 8], {"ndim": 4}),
+    ("geometry", "cart", [8, 8], {"geom": 7}),
+    ("lo == hi", "cart", [8, 8], {"hi": (-1.0, 1.0, 1.0)}),
+    ("spherical r from 1", "sph", [8, 8], {"lo": (1.0, 0.0, 0.0)}),
+    ("spherical phi short of 2 pi", "sph", [8, 8, 8], {"hi": (10.0, 3.141592653589793, 6.0)}),
+    ("cylindrical R from 1", "cyl", [8, 8], {"lo": (1.0, -1.0, 0.0)}),
+    ("cylindrical phi short of 2 pi", "cyl", [8, 8, 8], {"hi": (10.0, 1.0, 6.0)}),
+    ("grid above 2^31 cells", "cart", [4096, 4096, 256], {}),
+    ("precision", "cart", [8, 8], {"precision": 9}),
+    ("no smoothing", "cart", [8, 8], {"nu1": 0, "nu2": 0}),
+    ("negative nu1", "cart", [8, 8], {"nu1": -1}),
+    ("nu2 above 64", "cart", [8, 8], {"nu2": 65}),
+    ("negative max_cycles", "cart", [8, 8], {"max_cycles": -1}),
+    ("max_cycles beyond the history", "cart", [8, 8], {"max_cycles": 1024}),
+    ("negative tol", "cart", [8, 8], {"tol": -1e-10}),
+    ("NaN tol", "cart", [8, 8], {"tol": float("nan")}),
+    ("mixed-derivative form", "cart", [8, 8], {"mixed_deriv": 5}),
+    ("negative stall window", "cart", [8, 8], {"stall_window": -1}),
+    ("Anderson depth above 16", "cart", [8, 8], {"accel_depth": 17}),
+    ("negative Anderson depth", "cart", [8, 8], {"accel_depth": -1}),
+])
+def test_descriptor_validation_rejects(what, geom, n, kw):
+    """Every rule of the descriptor (grid, domain of the geometry, solver
+    settings) answers MG_ERR_INVALID with a message, without a device."""
+    from paper_2012_07322_gb300 import mg
+    import numpy as np
+    nd = len(n)
+    lo = {"cart": [-1.0] * nd, "cyl": [0.0, -1.0, 0.0][:nd], "sph": [0.0] * nd}[geom]
+    hi = {"cart": [1.0] * nd, "cyl": [10.0, 1.0, 2 * np.pi][:nd], "sph": [10.0, np.pi, 2 * np.pi][:nd]}[geom]
+    d = _set(mg.grid_desc(geom, [max(x, 1) for x in n], lo=lo, hi=hi), **kw)
+    for k in range(nd):
+        d.n[k] = n[k]
+    with pytest.raises(mg.MgError) as e:
+        mg.mg_hierarchy_bytes(d)
+    assert e.value.status == mg.MG_ERR_INVALID, what
+    assert mg.lib().mg_last_error(), what
+
+
+@pytest.mark.parametrize("geom,n", [
+    ("cart", [2, 2]), ("cart", [2, 2, 2]), ("sph", [2, 2]), ("cyl", [2, 2, 2]),
+    ("sph", [1024, 2]), ("cart", [4, 4096]),
+])
+def test_degenerate_but_valid_grids(geom, n):
+    """The smallest grids (one level of two cells per direction) and the most
+    anisotropic ones are accepted: the hierarchy then has one level, or
+    stops halving where the short direction reaches two cells."""
+    from paper_2012_07322_gb300 import mg
+    import numpy as np
+    nd = len(n)
+    lo = {"cart": [-1.0] * nd, "cyl": [0.0, -1.0, 0.0][:nd], "sph": [0.0] * nd}[geom]
+    hi = {"cart": [1.0] * nd, "cyl": [10.0, 1.0, 2 * np.pi][:nd], "sph": [10.0, np.pi, 2 * np.pi][:nd]}[geom]
+    b = mg.mg_hierarchy_bytes(mg.grid_desc(geom, n, lo=lo, hi=hi))
+    assert b >= int(np.prod(n)) * 8
