@@ -1067,7 +1067,8 @@ int ensure_ghost_push(mg_hierarchy* H) {
     const LevelView<double> v = with_bc(H->L[l].v64, MG_BC_DIRICHLET);
     const long ng = ghost_count_host(v);
     for (int c = 0; c < 3; ++c) launch_ghost_sources(v, c, dgc + 8 * c * ng, dfac + c * ng, H->st);
-    ce = cudaMemcpyAsync(gc.data(), dgc, sizeof(int) * 8 * 3 * ng, cudaMemcpyDeviceToHost, H->st);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(gc.data(), dgc, sizeof(int) * 8 * 3 * ng, cudaMemcpyDeviceToHost, H->st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(fac.data(), dfac, sizeof(double) * 3 * ng, cudaMemcpyDeviceToHost, H->st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(H->st);
     if (ce != cudaSuccess) break;
@@ -1108,11 +1109,10 @@ int ensure_ghost_push(mg_hierarchy* H) {
         buf.resize(buf.size() + nb + 1, 0);
         if (buf.size() & 1) buf.push_back(0);  // entries 8-byte aligned
         w.ent = (long)buf.size();
-        int* offp = nullptr;
         long cnt = 0;
         for (long g = 0; g < ng; ++g) cnt += col[g] == colour;
         buf.resize(buf.size() + 2 * cnt);
-        offp = buf.data() + w.off;
+        int* offp = buf.data() + w.off;  // after the last resize
         for (long g = 0; g < ng; ++g)
           if (col[g] == colour) offp[blk[g] + 1] += 1;
         for (int b = 0; b < nb; ++b) offp[b + 1] += offp[b];
