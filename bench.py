@@ -135,9 +135,9 @@ class ClockSampler:
 
     def __init__(self, gpu_id):
         self.proc = None
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        self.fh = os.fdopen(fd, "w")
         try:
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
@@ -146,6 +146,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            self.fh.close()
+            os.unlink(self.path)
             return None
         self.proc.terminate()
         try:
