@@ -334,6 +334,32 @@ def test_xcfc_parity(mg, geom, n, hi, accel):
     assert max(errs.values()) < 1e-9, errs
 
 
+@pytest.mark.parametrize("precision,accel", [("fp64", 0), ("mixed", 8)])
+@pytest.mark.parametrize("geom,n,lo,hi", [
+    ("sph", [16, 8], [0, 0], [50, PI]),
+    ("cyl", [8, 8, 4], [0, -50, 0], [50, 50, 2 * PI]),
+    ("cart", [8, 8, 8], [-50] * 3, [50] * 3),
+])
+def test_flat_vacuum_is_exact_in_zero_cycles(mg, geom, n, lo, hi, precision, accel):
+    """The degenerate case of the xCFC system: U = S = S_i = 0 from the flat
+    guess is already the solution (psi = alpha = 1, beta = X = 0, exactly),
+    and every equation stops before its first cycle, as the oracle does."""
+    d, gd = descs(mg, geom, n, lo, hi, precision=precision, accel_depth=accel)
+    h = mg.Hierarchy(gd)
+    shp = o.shape(d)
+    z = torch.zeros(shp, dtype=torch.float64, device="cuda")
+    psi, alpha = torch.ones_like(z), torch.ones_like(z)
+    beta = [torch.zeros_like(z) for _ in range(3)]
+    X = [torch.zeros_like(z) for _ in range(3)]
+    rep = mg.mg_solve_cfc(h, z, z.clone(), [z.clone() for _ in range(3)], psi, alpha, beta, X)
+    h.close()
+    assert rep["status"] == "ok"
+    for k in ("X", "psi", "alphapsi", "beta"):
+        assert rep[k]["cycles"] == 0 and rep[k]["rel"] <= 1e-10, (k, rep[k])
+    assert (host(psi) == 1).all() and (host(alpha) == 1).all()
+    assert all((host(b) == 0).all() for b in beta) and all((host(x) == 0).all() for x in X)
+
+
 @pytest.mark.parametrize("n", [32, 64])
 def test_divb_cleaning_parity(mg, n):
     """Elliptic divergence cleaning on a curl field with noise (at 64^3 the
