@@ -514,7 +514,8 @@ def main():
             e2e_ms += e0.elapsed_time(e1)
             e2e_up += sum(rep[k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta"))
         nb = 8 * int(np.prod(shp))
-        e2e = {"value": e2e_up / (e2e_ms * 1e-3) / 1e9 * world, "unit": UNIT, "h2d_bytes_per_step": 13 * nb,
+        e2e_ms, e2e_up = aggregate_ranks(dist, e2e_ms, e2e_up, "cuda")
+        e2e = {"value": e2e_up / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 13 * nb,
                "d2h_bytes_per_step": 8 * nb}
 
     # ------------------------------------------------------------ roofline
