@@ -47,8 +47,9 @@
  *     every level, solve the coarsest, then per level up: FAS correction from
  *     below and one V-cycle from that level;
  *   - optional Anderson mixing of successive V-cycle iterates (not in the
- *     paper; off when accel_depth = 0): point smoothing converges slowly on
- *     spherical grids (the paper notes it), mixing restores the rate.
+ *     paper; off when accel_depth = 0), in the difference form of Walker &
+ *     Ni (SIAM J. Numer. Anal. 49, 2011): point smoothing converges slowly
+ *     on spherical grids (the paper notes it), mixing restores the rate.
  *
  * Layout of every ghosted array: one ghost layer in each active dimension,
  * index (i, j, k) with i in [-1, n0], j in [-1, n1], k in [-1, n2] (3D) or
