@@ -122,3 +122,20 @@ def test_degenerate_but_valid_grids(geom, n):
     hi = {"cart": [1.0] * nd, "cyl": [10.0, 1.0, 2 * np.pi][:nd], "sph": [10.0, np.pi, 2 * np.pi][:nd]}[geom]
     b = mg.mg_hierarchy_bytes(mg.grid_desc(geom, n, lo=lo, hi=hi))
     assert b >= int(np.prod(n)) * 8
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the CUDA library and without a toolkit to
+    build it, the binding raises instead of computing anything."""
+    from paper_2012_07322_gb300 import build, mg
+
+    def no_nvcc():
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libgmunu_mg.so")
+
+    monkeypatch.setattr(mg, "_lib", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "libgmunu_mg.so"))
+    monkeypatch.setattr(build, "nvcc", no_nvcc)
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        mg.lib()
+    with pytest.raises(RuntimeError):
+        mg.mg_hierarchy_bytes(mg.grid_desc("cart", [8, 8], [-1.0, -1.0], [1.0, 1.0]))
