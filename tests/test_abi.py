@@ -139,3 +139,45 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         mg.lib()
     with pytest.raises(RuntimeError):
         mg.mg_hierarchy_bytes(mg.grid_desc("cart", [8, 8], [-1.0, -1.0], [1.0, 1.0]))
+
+
+def test_null_arguments_are_rejected_without_a_device():
+    """Every entry point checks its pointers before any device work: null
+    handles and outputs answer MG_ERR_INVALID (destroying null is a no-op),
+    and an invalid descriptor never reaches an allocation."""
+    from paper_2012_07322_gb300 import mg
+    L = mg.lib()
+    INV = mg.MG_ERR_INVALID
+    good = mg.grid_desc("sph", [64, 32], hi=[100.0, 3.141592653589793])
+    bad = mg.grid_desc("sph", [64, 24], hi=[100.0, 3.141592653589793])
+    out = ctypes.c_void_p()
+    assert L.mg_create_hierarchy(None, None, ctypes.byref(out)) == INV
+    assert L.mg_create_hierarchy(ctypes.byref(bad), None, ctypes.byref(out)) == INV and not out.value
+    assert L.mg_create_hierarchy(ctypes.byref(good), None, None) == INV
+    assert L.mg_hierarchy_bytes(ctypes.byref(good), None) == INV
+    assert L.mg_hierarchy_bytes(None, ctypes.byref(ctypes.c_size_t())) == INV
+    assert L.mg_destroy_hierarchy(None) == mg.MG_OK
+    assert L.mg_num_levels(None, None) == INV
+    assert L.mg_solve_cfc(None, None, None, 0, None) == INV
+    assert L.mg_clean_divB(None, None, None, 0, None) == INV
+    assert L.mg_solve_scalar(None, 0, 0, 0, None, None, None, None, None, None) == INV
+    assert L.mg_solve_vector(None, 0, None, None, None) == INV
+    assert L.mg_apply_operator(None, 0, 0, None, None, None, None, None) == INV
+    assert L.mg_smooth(None, 0, 0, 1, None, None, None, None, None) == INV
+    assert L.mg_compute_a2(None, None, None) == INV
+    assert L.mg_divergence(None, None, None) == INV
+    assert L.mg_restrict(None, None, None) == INV
+    assert L.mg_prolong_add(None, 0, None, None) == INV
+    assert L.mg_profile_enable(None, 1) == INV
+    assert L.mg_profile_read(None, 0, None, None, None) == INV
+    srv = ctypes.c_void_p()
+    assert L.mg_server_create(0, 4, 8, ctypes.byref(srv)) == INV and not srv.value
+    assert L.mg_server_create(1 << 30, 0, 8, ctypes.byref(srv)) == INV
+    assert L.mg_server_create(1 << 30, 4, 8, None) == INV
+    assert L.mg_server_destroy(None) == mg.MG_OK
+    ticket = ctypes.c_uint64()
+    assert L.mg_submit(None, None, ctypes.byref(ticket)) == INV
+    done = ctypes.c_int()
+    assert L.mg_poll(None, 0, ctypes.byref(done), None) == INV
+    assert L.mg_kernel_launches() == 0
+    assert L.mg_last_error()
