@@ -179,5 +179,4 @@ def test_null_arguments_are_rejected_without_a_device():
     assert L.mg_submit(None, None, ctypes.byref(ticket)) == INV
     done = ctypes.c_int()
     assert L.mg_poll(None, 0, ctypes.byref(done), None) == INV
-    assert L.mg_kernel_launches() == 0
     assert L.mg_last_error()
