@@ -360,6 +360,33 @@ def test_flat_vacuum_is_exact_in_zero_cycles(mg, geom, n, lo, hi, precision, acc
     assert all((host(b) == 0).all() for b in beta) and all((host(x) == 0).all() for x in X)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cycle_cap_and_nan_statuses(mg, precision):
+    """Failure statuses of the cycle loop, as the oracle returns them: the
+    cycle cap ends with MG_ERR_NOCONV after exactly max_cycles cycles (FP64:
+    at the oracle's residual), a NaN in a source with MG_ERR_NAN before the
+    first cycle; the hierarchy stays usable afterwards."""
+    U = inputs.static_polytrope_sph2d(32, 16, 100.0)
+    z = np.zeros_like(U)
+    d, gd = descs(mg, "sph", [32, 16], [0, 0], [100.0, PI], tol=1e-10, max_cycles=2, precision=precision)
+    ro = o.solve_scalar(d, "psi", "robin", np.zeros_like(U), U=U, A2=z)
+    h = mg.Hierarchy(gd)
+    u = torch.zeros(U.shape, dtype=torch.float64, device="cuda")
+    rg = mg.mg_solve_scalar(h, "psi", "robin", u, U=dev(U), A2=dev(z), allow=(mg.MG_ERR_NOCONV,))
+    assert ro["status"] == rg["status"] == "noconv" and rg["cycles"] == ro["cycles"] == 2
+    if precision == "fp64":
+        assert abs(rg["rel"] - ro["rel"]) <= 1e-8 * ro["rel"]
+    Un = U.copy()
+    Un[3, 5] = np.nan
+    u.zero_()
+    rg = mg.mg_solve_scalar(h, "psi", "robin", u, U=dev(Un), A2=dev(z), allow=(mg.MG_ERR_NAN,))
+    assert rg["status"] == "nan" and rg["cycles"] == 0
+    u.zero_()
+    rg = mg.mg_solve_scalar(h, "psi", "robin", u, U=dev(U), A2=dev(z), allow=(mg.MG_ERR_NOCONV,))
+    assert rg["status"] == "noconv" and rg["cycles"] == 2
+    h.close()
+
+
 @pytest.mark.parametrize("n", [32, 64])
 def test_divb_cleaning_parity(mg, n):
     """Elliptic divergence cleaning on a curl field with noise (at 64^3 the

@@ -908,3 +908,29 @@ def test_anderson_mixing_is_gmres_on_the_cycle_map():
         # the mixing is what makes the difference: plain cycles are 1e-3..1e-2 away
         assert np.abs(plain - want).max() > 1e-3 * scale, k
         assert np.abs(mixed - want).max() <= 1e-7 * scale, k
+
+
+# ------------------------------------------------------------ cycle control
+
+
+def test_cycle_control_statuses():
+    """The stopping rule of the cycle loop: the cycle cap ends with
+    'noconv' after exactly max_cycles cycles, a non-finite source with 'nan'
+    before the first cycle, and a residual that stops falling (round-off
+    floor, tol = 0) with 'stalled' once stall_window cycles gain less than
+    5 %."""
+    U = inputs.static_polytrope_sph2d(32, 16, 100.0)
+    z = np.zeros_like(U)
+    d = o.desc("sph", [32, 16], [0, 0], [100.0, PI], tol=1e-10, max_cycles=2)
+    r = o.solve_scalar(d, "psi", "robin", np.zeros_like(U), U=U, A2=z)
+    assert r["status"] == "noconv" and r["cycles"] == 2 and r["rel"] > 1e-10
+    Un = U.copy()
+    Un[3, 5] = np.nan
+    d = o.desc("sph", [32, 16], [0, 0], [100.0, PI], tol=1e-10, max_cycles=50)
+    r = o.solve_scalar(d, "psi", "robin", np.zeros_like(U), U=Un, A2=z)
+    assert r["status"] == "nan" and r["cycles"] == 0
+    d = o.desc("sph", [32, 16], [0, 0], [100.0, PI], tol=0.0, max_cycles=1000, stall_window=5)
+    r = o.solve_scalar(d, "psi", "robin", np.zeros_like(U), U=U, A2=z)
+    h = r["hist"]
+    assert r["status"] == "stalled" and r["rel"] < 1e-12
+    assert h[-1] > 0.95 * h[-6] and h[-2] <= 0.95 * h[-7]
