@@ -7,6 +7,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# Parallel test workers (pytest-xdist) would each start an OpenMP team of
+# every core for the oracle's colour loops; one thread per worker keeps the
+# machine from being oversubscribed.  The oracle's results do not depend on
+# the thread count (a colour's updates are independent).
+if os.environ.get("PYTEST_XDIST_WORKER"):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built CUDA library")
