@@ -405,6 +405,77 @@ def test_red_black_sweep_matches_sequential_definition():
     np.testing.assert_allclose(u[1:-1, 1:-1], ref[1:-1, 1:-1], rtol=1e-7, atol=1e-9)
 
 
+# tiny grids of every geometry for the sweep definition below
+SWEEP_GRIDS = {
+    "cart2d": ("cart", [6, 4], [-1.3, -1.1], [1.2, 1.4]),
+    "cart3d": ("cart", [6, 4, 4], [-1.3, -1.1, -1.2], [1.2, 1.4, 1.3]),
+    "cyl2d": ("cyl", [6, 4], [0.0, -1.5], [2.0, 1.7]),
+    "cyl3d": ("cyl", [6, 4, 4], [0.0, -1.5, 0.0], [2.0, 1.7, 2 * PI]),
+    "sph2d": ("sph", [6, 4], [0.0, 0.0], [3.0, PI]),
+    "sph3d": ("sph", [6, 4, 4], [0.0, 0.0, 0.0], [3.0, PI, 2 * PI]),
+}
+
+
+@pytest.mark.parametrize("eq", ["vec4pt", "veccorner", "linc"])
+@pytest.mark.parametrize("grid", list(SWEEP_GRIDS))
+def test_newton_diagonal_sweep_matches_sequential_definition(grid, eq):
+    """One red-black sweep of the vector equation (both mixed-derivative
+    stencils) and of the linear equation lap u - c u = f, in every geometry,
+    equals the sequential definition of eq. (ngs_iteration): per colour (and,
+    for vectors, per component in the order 0, 1, 2) the ghosts are refilled,
+    then every cell of the colour in turn takes u <- u - (L(u) - f) / D with
+    D the derivative of L at that cell with respect to its own value, ghosts
+    held fixed.  D is measured here as a central difference of the oracle's
+    own operator (exact up to rounding: L is affine in the cell's value), so
+    a wrong term in the oracle's diagonals (vec_diag, lap_diag, the -c of the
+    linear equation) fails this test even though it leaves the fixed point
+    unchanged."""
+    geom, n, lo, hi = SWEEP_GRIDS[grid]
+    nd = len(n)
+    kind = "vec" if eq.startswith("vec") else "lin"
+    d = o.desc(geom, n, lo, hi, mixed="corner" if eq == "veccorner" else "4pt")
+    bc = "dirichlet" if kind == "vec" else "robin"
+    ncomp = 3 if kind == "vec" else 1
+    rng = np.random.default_rng(31 + nd)
+    gs = o.shape(d, True)
+    u = [np.zeros(gs) for _ in range(ncomp)]
+    f = [np.zeros(gs) for _ in range(ncomp)]
+    inner = (slice(1, -1),) * nd
+    for c in range(ncomp):
+        u[c][inner] = rng.uniform(-0.5, 0.5, o.shape(d))
+        f[c][inner] = rng.uniform(-0.3, 0.3, o.shape(d))
+    cc = rng.uniform(0.1, 0.9, gs) if kind == "lin" else None
+    ref = [a.copy() for a in u]
+    got = [a.copy() for a in u]
+    if kind == "vec":
+        o.smooth(d, "vec", bc, 1, got, f)
+    else:
+        o.smooth(d, "lin", bc, 1, got[0], f[0], c=cc)
+
+    def op(V, comp):
+        out = o.apply_raw(d, kind, V if kind == "vec" else V[0], c=cc)
+        return out[comp] if kind == "vec" else out
+
+    cells = list(np.ndindex(*o.shape(d)))  # (k, j, i) or (j, i), i fastest last
+    for colour in (0, 1):
+        for comp in range(ncomp):
+            for c in range(ncomp):
+                o.fill_ghosts(d, bc, c if kind == "vec" else -1, ref[c])
+            for cell in cells:
+                if sum(cell) % 2 != colour:
+                    continue
+                g = tuple(x + 1 for x in cell)
+                Lu = op(ref, comp)[g]
+                v0 = ref[comp][g]
+                ref[comp][g] = v0 + 0.5
+                Lp = op(ref, comp)[g]
+                ref[comp][g] = v0 - 0.5
+                Lm = op(ref, comp)[g]
+                ref[comp][g] = v0 - (Lu - f[comp][g]) / (Lp - Lm)
+    for c in range(ncomp):
+        np.testing.assert_allclose(got[c][inner], ref[c][inner], rtol=1e-10, atol=1e-12)
+
+
 # ------------------------------------------------ brute force (tiny grids)
 
 
@@ -657,6 +728,57 @@ def test_divb_cleaning_removes_gradient_part():
         errs.append(max(np.abs(B[c] - sol[c]).max() for c in range(3)))
     assert div_in[0] / div_in[1] > 3.0, div_in
     assert errs[0] / errs[1] > 1.5, errs
+
+
+def _single_mode_field(n, m):
+    """B = (B_x, 0, 0) on the cube [-1, 1]^3 whose central divergence, with
+    the copied (zero-gradient) B ghosts, is exactly the DCT-II mode
+    b = cos(pi m0 (i+1/2)/n) cos(pi m1 (j+1/2)/n) cos(pi m2 (k+1/2)/n).
+    B_x = X(i) times the y, z factors, with X solving the central-difference
+    recurrence X(i+1) = X(i-1) + 2 h b_x(i) from X(-1) = X(0) = 0; the last
+    cell closes it (X(n) = X(n-1)) exactly when m0 is even."""
+    h = 2.0 / n
+    t = (np.arange(n) + 0.5) / n
+    cx, cy, cz = (np.cos(PI * m[a] * t) for a in range(3))
+    X = np.zeros(n)
+    X[1] = X[0] + 2 * h * cx[0]
+    for i in range(1, n - 1):
+        X[i + 1] = X[i - 1] + 2 * h * cx[i]
+    assert abs((X[n - 1] - X[n - 2]) / (2 * h) - cx[n - 1]) < 1e-13  # compatible closure
+    b = cz[:, None, None] * cy[None, :, None] * cx[None, None, :]
+    Bx = np.ascontiguousarray(cz[:, None, None] * cy[None, :, None] * X[None, None, :])
+    return [Bx, np.zeros_like(Bx), np.zeros_like(Bx)], b
+
+
+@pytest.mark.parametrize("m", [(2, 0, 0), (6, 0, 0), (4, 3, 0), (2, 5, 7)])
+def test_divb_cleaning_single_mode_law(m):
+    """Cleaning a single divergence mode (eqs. poisson, update_bfield).  The
+    compact Neumann Laplacian has the DCT-II mode b as an eigenvector with
+    lambda_c = -sum_d (2 sin(k_d h / 2) / h)^2, so Phi = b / lambda_c; the
+    central divergence of the central gradient acts on it, away from the
+    walls, as lambda_w = -sum_d (sin(k_d h) / h)^2.  So on every cell whose
+    stencils stay inside, div B after = (1 - lambda_w / lambda_c) b: for a
+    mode along one direction the factor sin^2(k h / 2) per direction.  Fixed
+    by the discrete operators alone, to 1e-10."""
+    n = 16
+    h = 2.0 / n
+    B, b = _single_mode_field(n, m)
+    d = o.desc("cart", [n] * 3, [-1] * 3, [1] * 3, tol=1e-13, max_cycles=1000)
+    np.testing.assert_allclose(o.div_c(d, B), b, rtol=0, atol=1e-12)
+    phi = np.zeros((n, n, n))
+    rep = o.clean_divb(d, B, phi)
+    assert rep["status"] == "ok"
+    kh = PI * np.array(m) / n
+    lam_c = -np.sum((2 * np.sin(kh / 2) / h) ** 2)
+    lam_w = -np.sum((np.sin(kh) / h) ** 2)
+    np.testing.assert_allclose(phi, b / lam_c, rtol=0, atol=1e-10 * np.abs(b / lam_c).max())
+    after = o.div_c(d, B)
+    inner = (slice(1, -1),) * 3
+    law = (1 - lam_w / lam_c) * b
+    np.testing.assert_allclose(after[inner], law[inner], rtol=0, atol=1e-10)
+    if sum(1 for x in m if x) == 1:
+        k = kh[np.nonzero(m)[0][0]]
+        np.testing.assert_allclose(1 - lam_w / lam_c, np.sin(k / 2) ** 2, rtol=1e-13)
 
 
 # -------------------------------------------------------- FMG cycle
