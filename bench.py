@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-divb", action="store_true", help="skip the 256^3 div-B cleaning measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the request-serving measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the 512-solve batch measurement")
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 solve beside the mixed one")
+    p.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 solves (each ~1 s)")
     return p.parse_args()
 
 
@@ -94,18 +96,20 @@ def level_cells():
     return out
 
 
-# Algorithmic bytes per cell processed by one launch of each profiled kernel
-# class (every array streamed once per launch):
-#   colour pass, scalar: read all u (2 cells per updated cell), write u, read
-#     two per-cell inputs                        -> 5 words per updated cell
-#   colour pass, vector component: read the 3 components (6 words), write
-#     one, read its right-hand side             -> 8 words per updated cell
-#   finest residual, scalar: read u, 2 inputs, write r -> 4 words per cell
-#   finest residual, vector: read 3 u, 3 f, write 3 r  -> 9 words per cell
-#   fused red-black sweep (Cartesian scalar): read u and f (and c), write u
-#                                               -> 3 words per cell (4 with c)
-BYTES_PER_CELL = {"smooth64_scalar": 5 * 8, "smooth64_vec": 8 * 8, "smooth32_scalar": 5 * 4,
-                  "smooth32_vec": 8 * 4, "resid64_scalar": 4 * 8, "resid64_vec": 9 * 8,
+# Algorithmic bytes per cell one launch of each profiled kernel class
+# processes, from the bytes the method itself must move: one red-black sweep
+# streams s (2 n_u + n_in) bytes per cell (read and write each of the n_u
+# unknowns, read each of the n_in per-cell inputs; s = 8 FP64, 4 FP32), and a
+# colour pass, which updates half of the cells for one component, carries
+# 1 / (2 n_comp) of it, i.e. s (2 n_u + n_in) / n_comp per updated cell:
+#   colour pass, scalar (n_u = 1, n_in = 2: U and A2 of eq. psi, c and f of a
+#     linear equation, or f32 and K of the FP32 correction) -> 4 s
+#   colour pass, vector (n_u = 3, n_in = 3 right-hand sides) -> 3 s
+#   one-launch red-black sweep (Cartesian scalar: u and f, and c)
+#                                                   -> 3 s per cell (4 s with c)
+# (the finest residuals are FP64-pipe bound: FLOPS_PER_CELL below).
+BYTES_PER_CELL = {"smooth64_scalar": 4 * 8, "smooth64_vec": 3 * 8, "smooth32_scalar": 4 * 4,
+                  "smooth32_vec": 3 * 4, "resid64_scalar": 4 * 8, "resid64_vec": 9 * 8,
                   "sweep64_fused": 3 * 8, "sweep32_fused": 3 * 4}
 
 # The finest FP64 residuals are bound by the FP64 pipe (GB300 issues 2 FP64
@@ -363,6 +367,59 @@ def serving_measurement(mg, torch, n_requests=160, rate=2000.0, slots=8):
             "ok": sum(1 for s in statuses if s == "ok"), "requests": n_requests}
 
 
+def fp64_arm(mg, torch, stream, Ud, Sd, Sid, shp, steps, warmup, accel, max_cycles, mixed_fields):
+    """The plain FP64 GPU solve of the same workload (every kernel FP64), timed
+    like the headline (L2 flushed between solves), and the per-field
+    difference of the mixed-precision solution from it: max |mixed - fp64| /
+    max |fp64| for psi, alpha, beta_i and X_i.  The FP64 GPU path matches the
+    FP64 oracle to 1e-9 on every field (parity tests), so it stands in for the
+    oracle at this size."""
+    desc = mg.grid_desc("sph", list(N_GRID), hi=[R_MAX, np.pi, 2 * np.pi], precision="fp64", tol=TOL,
+                        max_cycles=max_cycles, accel_depth=accel, stall_window=0)
+    h = mg.Hierarchy(desc, stream)
+    psi = torch.ones(shp, dtype=torch.float64, device="cuda")
+    alpha = torch.ones_like(psi)
+    beta = [torch.zeros_like(psi) for _ in range(3)]
+    X = [torch.zeros_like(psi) for _ in range(3)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def reset():
+        psi.fill_(1.0)
+        alpha.fill_(1.0)
+        for t in beta + X:
+            t.zero_()
+
+    for _ in range(warmup):
+        reset()
+        mg.mg_solve_cfc(h, Ud, Sd, Sid, psi, alpha, beta, X)
+    ms, ups, rep = [], 0, None
+    for _ in range(steps):
+        reset()
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = mg.mg_solve_cfc(h, Ud, Sd, Sid, psi, alpha, beta, X)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        ups += sum(rep[k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta"))
+    h.close()
+    names = ["psi", "alpha", "beta_r", "beta_theta", "beta_phi", "X_r", "X_theta", "X_phi"]
+    ref = [psi, alpha] + beta + X
+    err = {}
+    for nm, a, b in zip(names, mixed_fields, ref):
+        den = float(b.abs().max())
+        num = float((a - b).abs().max())
+        err[nm] = num / den if den > 0 else num
+    lat = sorted(ms)
+    return {"precision": "fp64", "value": ups / (sum(ms) * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_solve": sum(ms) / len(ms), "solves_per_s": 1e3 * len(ms) / sum(ms),
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "solves": len(ms), "cycles": {k: rep[k]["cycles"] for k in ("X", "psi", "alphapsi", "beta")},
+            "rel": {k: rep[k]["rel"] for k in ("X", "psi", "alphapsi", "beta")}}, err
+
+
 def oracle_sample(threads):
     """Bounded sample of the workload on the CPU oracle: 2 V-cycles of the X
     (vector) equation and 2 of the psi equation on the full grid.  Returns
@@ -490,6 +547,12 @@ def main():
     mg.mg_profile_enable(h, False)
     prof_step_ms = prof_rep["ms"]
     total_ms, all_updates = aggregate_ranks(dist, sum(ms_steps), updates, "cuda")
+    fp64, mixed_vs_fp64 = None, None
+    if args.precision == "mixed" and not args.no_fp64:
+        # the mixed solution of the last timed solve (the profiled solve ran
+        # the same arithmetic from the same start)
+        fp64, mixed_vs_fp64 = fp64_arm(mg, torch, stream, Ud, Sd, Sid, shp, args.fp64_steps, 1, args.accel,
+                                       args.max_cycles, [psi, alpha] + beta + X)
     value = all_updates / (total_ms * 1e-3) / 1e9
 
     # ------------------------------------------------------------------ e2e
@@ -598,7 +661,8 @@ def main():
                        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "parallelism": "replicas (independent solves per GPU)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "divb_256": divb, "serving": serving, "batch_2d": batch,
+            "clocks": clocks, "fp64": fp64, "mixed_vs_fp64_err": mixed_vs_fp64,
+            "divb_256": divb, "serving": serving, "batch_2d": batch,
         }
         print(json.dumps(line))
     h.close()

@@ -115,6 +115,9 @@ extern "C" int mg_divb_norms_noalloc(int ndim, const int n[3], const double lo[3
                             "grid larger than MG_NOALLOC_MAX_CELLS (2097152 cells), the size of the static "
                             "scratch of the allocation-free entry point");
   }
+  // an error left by earlier, unrelated work of the caller must not be
+  // reported as this call's: drop it (launch errors are checked below)
+  (void)cudaGetLastError();
   double* scratch = nullptr;
   int st = scratch_address(&scratch);
   if (st) return set_last_error(st, "looking up the device address of the static scratch failed");
@@ -134,11 +137,12 @@ extern "C" int mg_divb_norms_noalloc(int ndim, const int n[3], const double lo[3
   gmg::launch_k(k_noalloc_div, (unsigned)g, 256, 0, s, n0, n1, n2, ndim == 3, c0, c1, c2, B[0], B[1],
                                              ndim == 3 ? B[2] : B[0], div);
   gmg::launch_k(k_noalloc_norms, NOALLOC_BLOCKS, 256, 0, s, cells, div, part, maxw);
+  if (cudaGetLastError() != cudaSuccess) return set_last_error(MG_ERR_CUDA, "launching the divergence kernels failed");
   double hpart[NOALLOC_BLOCKS];
   unsigned long long hmax = 0;
   if (cudaMemcpyAsync(hpart, part, sizeof(hpart), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&hmax, maxw, sizeof(hmax), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      cudaStreamSynchronize(s) != cudaSuccess)
     return set_last_error(MG_ERR_CUDA, "divergence kernels or read-back failed");
   double sum = 0.0;
   for (int b = 0; b < NOALLOC_BLOCKS; ++b) sum += hpart[b];

@@ -8,8 +8,10 @@
 // kept resident on the device and used as the next initial guess of that
 // stream (the paper reuses the previous time step's metric the same way,
 // Sec. 4.2.1).  Device memory of cached hierarchies and resident solutions
-// stays within the HBM budget given at creation: idle hierarchies are
-// evicted least recently used first; a request that cannot fit waits.
+// stays within the HBM budget given at creation: idle hierarchies, then the
+// resident solutions of streams with nothing in flight, are evicted least
+// recently used first; a request that still cannot fit waits for a running
+// request to release memory, or fails with MG_ERR_OOM when none runs.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -70,6 +72,7 @@ struct Warm {
   double* buf = nullptr;
   size_t bytes = 0;
   bool valid = false;
+  uint64_t last = 0;  // use stamp (eviction order)
 };
 
 }  // namespace
@@ -87,17 +90,49 @@ struct mg_server {
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
   std::unordered_map<uint64_t, int> running_ids;  // stream ids with a job in flight
+  int creating = 0;  // hierarchies being created (memory counted, not yet cached)
   bool stop = false;
   uint64_t next_ticket = 1, clock = 0;
 };
 
 namespace {
 
+// Free the resident solution of one stream id that has nothing in flight
+// (own_id counts as free: its request is the caller), least recently used
+// first and own_id last.  Called with the lock held; false if none.
+bool evict_warm(mg_server* S, uint64_t own_id) {
+  uint64_t victim = 0;
+  bool found = false, victim_own = false;
+  for (auto& kv : S->warm) {
+    if (!kv.second.buf) continue;
+    const bool own = kv.first == own_id;
+    if (!own && S->running_ids[kv.first] != 0) continue;
+    const bool better = !found || (victim_own && !own) ||
+                        (victim_own == own && kv.second.last < S->warm[victim].last);
+    if (better) {
+      victim = kv.first;
+      victim_own = own;
+      found = true;
+    }
+  }
+  if (!found) return false;
+  Warm& w = S->warm[victim];
+  cudaFree(w.buf);
+  S->used -= w.bytes;
+  w.buf = nullptr;
+  w.bytes = 0;
+  w.valid = false;
+  return true;
+}
+
 // Take an idle cached hierarchy for desc, or create one within the budget
-// (evicting idle ones, least recently used first).  Called with the lock
-// held; may release it while waiting or allocating.  Returns null on error.
+// (evicting idle hierarchies, then resident solutions of idle streams,
+// least recently used first).  Called with the lock held; may release it
+// while waiting or allocating.  Waits only while another request holds
+// memory it will release; otherwise a request that cannot fit fails with
+// MG_ERR_OOM.  Returns null on error.
 mg_hierarchy* acquire(mg_server* S, std::unique_lock<std::mutex>& lk, const mg_grid_desc& d, cudaStream_t st,
-                      int* status) {
+                      uint64_t own_id, int* status) {
   size_t need = 0;
   if (mg_hierarchy_bytes(&d, &need) != MG_OK) {
     *status = MG_ERR_INVALID;
@@ -114,25 +149,39 @@ mg_hierarchy* acquire(mg_server* S, std::unique_lock<std::mutex>& lk, const mg_g
       int victim = -1;
       for (int q = 0; q < (int)S->cache.size(); ++q)
         if (!S->cache[q].busy && (victim < 0 || S->cache[q].last < S->cache[victim].last)) victim = q;
-      if (victim < 0) break;
-      mg_destroy_hierarchy(S->cache[victim].h);
-      S->used -= S->cache[victim].bytes;
-      S->cache.erase(S->cache.begin() + victim);
+      if (victim >= 0) {
+        mg_destroy_hierarchy(S->cache[victim].h);
+        S->used -= S->cache[victim].bytes;
+        S->cache.erase(S->cache.begin() + victim);
+        continue;
+      }
+      if (!evict_warm(S, own_id)) break;
     }
     if (S->used + need <= S->budget) break;
     if (S->stop) {
       *status = MG_ERR_BUSY;
       return nullptr;
     }
+    int holders = S->creating;
+    for (const Cached& c : S->cache) holders += c.busy ? 1 : 0;
+    if (holders == 0) {
+      *status = gmg::set_last_error(MG_ERR_OOM,
+                                    "request does not fit the HBM budget beside the resident solutions of "
+                                    "running streams, and no running request will release memory");
+      return nullptr;
+    }
     S->cv_free.wait(lk);  // a running request will release memory
   }
   S->used += need;
+  S->creating += 1;
   lk.unlock();
   mg_hierarchy* h = nullptr;
   int st2 = mg_create_hierarchy(&d, (void*)st, &h);
   lk.lock();
+  S->creating -= 1;
   if (st2 != MG_OK) {
     S->used -= need;
+    S->cv_free.notify_all();
     *status = st2;
     return nullptr;
   }
@@ -167,7 +216,7 @@ void run_job(mg_server* S, Job* J, cudaStream_t st, std::unique_lock<std::mutex>
   int status = MG_OK;
   // the request's inputs were produced on the submitter's stream
   if (J->ready) cudaStreamWaitEvent(st, J->ready, 0);
-  mg_hierarchy* h = acquire(S, lk, r.desc, st, &status);
+  mg_hierarchy* h = acquire(S, lk, r.desc, st, r.stream_id, &status);
   if (!h) {
     J->res.status = status;
     return;
@@ -180,6 +229,7 @@ void run_job(mg_server* S, Job* J, cudaStream_t st, std::unique_lock<std::mutex>
     if (it != S->warm.end() && it->second.valid && desc_equal(it->second.desc, r.desc)) w = &it->second;
   }
   double* wbuf = w ? w->buf : nullptr;
+  if (w) w->last = S->clock++;
   lk.unlock();
   if (wbuf) {
     copy_fields(r, wbuf, n, true, st);
@@ -213,6 +263,7 @@ void run_job(mg_server* S, Job* J, cudaStream_t st, std::unique_lock<std::mutex>
     }
     if (ww.buf) {
       ww.desc = r.desc;
+      ww.last = S->clock++;
       copy_fields(r, ww.buf, n, false, st);
       cudaStreamSynchronize(st);
       ww.valid = true;

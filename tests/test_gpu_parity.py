@@ -415,19 +415,21 @@ def test_divb_cleaning_parity(mg, n):
 MIXED_CASES = {
     # the finest level is above the one-block cycle's size: levels 1.. run in one block
     "sph3d": ("sph", [32, 16, 16], [0, 0, 0], [100.0, PI, 2 * PI]),
+    # levels 0 and 1 run the launched FP32 passes (levels 2.. in one block)
+    "sph3d64": ("sph", [64, 32, 32], [0, 0, 0], [100.0, PI, 2 * PI]),
     # the whole correction cycle runs in one block (2048 and 2048 cells)
     "sph2d": ("sph", [64, 32], [0, 0], [100.0, PI]),
     "cyl2d": ("cyl", [32, 64], [0.0, -100.0], [100.0, 100.0]),
 }
 
 
-@pytest.mark.parametrize("case,accel", [("sph3d", 0), ("sph3d", 8), ("sph2d", 8), ("cyl2d", 8)])
+@pytest.mark.parametrize("case,accel", [("sph3d", 0), ("sph3d", 8), ("sph3d64", 16), ("sph2d", 8), ("cyl2d", 8)])
 def test_mixed_precision_xcfc_error_vs_oracle(mg, case, accel):
     """FP32 smoothing inside FP64 defect correction: every equation reaches
-    the FP64 relative residual 1e-10 and every field stays within 1e-8 of
+    the FP64 relative residual 1e-10 and every field stays within 1e-9 of
     the FP64 oracle."""
     geom, n, lo, hi = MIXED_CASES[case]
-    if case == "sph3d":
+    if case.startswith("sph3d"):
         U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
     elif case == "sph2d":
         U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], 100.0)
@@ -437,7 +439,7 @@ def test_mixed_precision_xcfc_error_vs_oracle(mg, case, accel):
     for k in ("X", "psi", "alphapsi", "beta"):
         assert rg[k]["status"] == "ok" and rg[k]["rel"] <= 1e-10
     errs = field_errors(got, want)
-    assert max(errs.values()) < 1e-8, errs
+    assert max(errs.values()) < 1e-9, errs
 
 
 @pytest.mark.parametrize("n", [32, 64])
@@ -453,9 +455,9 @@ def test_mixed_precision_divb_error_vs_oracle(mg, n):
     rg = mg.mg_clean_divB(h, Bt, pt)
     h.close()
     assert rg["status"] == "ok" and rg["solve"]["rel"] <= 1e-10
-    assert relerr(host(pt), phi) < 1e-8
+    assert relerr(host(pt), phi) < 1e-9
     for k in range(3):
-        assert relerr(host(Bt[k]), Bo[k]) < 1e-8
+        assert relerr(host(Bt[k]), Bo[k]) < 1e-9
 
 
 FUSED_CASES = [
@@ -531,7 +533,7 @@ def test_fmg_xcfc_parity(mg, precision):
     """Full xCFC system on the 3D spherical 32x16x16 grid with FMG cycles
     and Anderson mixing: FP64 matches the oracle's FMG (cycles within one,
     fields within 1e-9); the mixed-precision FMG path reaches the FP64
-    tolerance with every field within 1e-8 of the oracle."""
+    tolerance with every field within 1e-9 of the oracle."""
     n = [32, 16, 16]
     U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
     rg, ro, got, want = run_cfc_pair(mg, "sph", n, [0, 0, 0], [100.0, PI, 2 * PI], U, S, Si, precision=precision,
@@ -544,7 +546,7 @@ def test_fmg_xcfc_parity(mg, precision):
     else:
         for k in ("X", "psi", "alphapsi", "beta"):
             assert rg[k]["status"] == "ok" and rg[k]["rel"] <= 1e-10
-        assert max(errs.values()) < 1e-8, errs
+        assert max(errs.values()) < 1e-9, errs
 
 
 # ------------------------------------------- curvilinear divergence cleaning

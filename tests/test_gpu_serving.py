@@ -189,3 +189,36 @@ def test_uneven_2d_batch_identical_alone_and_batched(mg):
     for q, (a, b) in enumerate(zip(outs, alone)):
         for x, y in zip(a, b):
             assert torch.equal(x, y), q
+
+
+def test_resident_solutions_are_evicted_before_waiting(mg):
+    """A budget of the largest hierarchy plus half a resident solution.  Two
+    warm-started streams leave their solutions resident; a third grid then
+    fits only once those are evicted (their streams have nothing in flight).
+    Every request completes within the host timeout, and the third result
+    equals its direct solve."""
+    a_args, Ua, Sa, Sia = cfc_case("sph2d", 31)
+    b_args, Ub, Sb, Sib = cfc_case("cyl2d", 32)
+    c_args, Uc, Sc, Sic = cfc_case("sph3d", 33)
+    da, db, dc = desc_of(mg, a_args), desc_of(mg, b_args), desc_of(mg, c_args)
+    need = [mg.mg_hierarchy_bytes(d) for d in (da, db, dc)]
+    warm_a = 8 * 8 * Ua.size
+    assert need[2] == max(need)
+    srv = mg.Server(hbm_budget=need[2] + warm_a // 2, max_slots=1, max_queue=8)
+    outs, tickets = [], []
+    for d, U, S, Si, sid in [(da, Ua, Sa, Sia, 1), (db, Ub, Sb, Sib, 2), (dc, Uc, Sc, Sic, 0),
+                             (da, Ua, Sa, Sia, 1)]:
+        f = fields(U.shape)
+        tickets.append(srv.submit_cfc(d, dev(U), dev(S), [dev(x) for x in Si], *f, stream_id=sid))
+        outs.append(f)
+    res = [srv.wait(t, timeout_s=120.0) for t in tickets]
+    srv.close()
+    assert all(r["status"] == "ok" for r in res)
+    assert not res[3]["warm_started"]  # stream 1's solution made room for the third grid
+    h = mg.Hierarchy(dc)
+    f = fields(Uc.shape)
+    mg.mg_solve_cfc(h, dev(Uc), dev(Sc), [dev(x) for x in Sic], *f)
+    h.close()
+    for x, y in zip([outs[2][0], outs[2][1]] + outs[2][2] + outs[2][3], [f[0], f[1]] + f[2] + f[3]):
+        assert torch.equal(x, y)
+

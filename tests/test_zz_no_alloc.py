@@ -5,13 +5,15 @@ owns all device memory, or code that must not let cudaMalloc synchronise
 the device): it keeps its scratch in a static device array instead of a
 hierarchy.  Its max |div B| and |div B|_2 must equal the before-cleaning
 numbers the allocating entry point mg_clean_divB reports for the same field,
-on two calls in a row (the scratch keeps the previous call's contents).
+on two calls in a row (the scratch keeps the previous call's contents), and
+the norms of the oracle's central divergence.
 This file is collected last so that a run stopping at the first failure has
 already run every other test; it also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
 
+import oracle.oracle as o
 from paper_2012_07322_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -47,11 +49,17 @@ def test_noalloc_norms_match_allocating_entry_point(mg, case):
         B = [torch.from_numpy(rng.standard_normal((32, 64))).cuda() for _ in range(2)]
         lo, hi = [-1.0, -0.5], [1.0, 0.75]
     want_max, want_l2 = _reference_norms(mg, B, lo, hi)
+    nd = len(B)
+    n = [B[0].shape[nd - 1 - d] for d in range(nd)]
+    div = o.div_c(o.desc("cart", n, lo, hi), [np.ascontiguousarray(b.cpu().numpy()) for b in B])
+    orc_max, orc_l2 = np.abs(div).max(), np.sqrt(np.mean(div ** 2))
     for call in range(2):
         st, mx, l2 = mg.mg_divb_norms_noalloc(B, lo, hi)
         assert st == mg.MG_OK
         assert abs(mx - want_max) <= 1e-12 * want_max, (call, mx, want_max)
         assert abs(l2 - want_l2) <= 1e-12 * want_l2, (call, l2, want_l2)
+        assert abs(mx - orc_max) <= 1e-12 * orc_max, (call, mx, orc_max)
+        assert abs(l2 - orc_l2) <= 1e-12 * orc_l2, (call, l2, orc_l2)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(mg):
