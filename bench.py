@@ -405,13 +405,21 @@ def fp64_arm(mg, torch, stream, Ud, Sd, Sid, shp, steps, warmup, accel, max_cycl
         ms.append(e0.elapsed_time(e1))
         ups += sum(rep[k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta"))
     h.close()
+    # scalars relative to their own maximum, vector components relative to
+    # the vector's largest component (as the parity tests measure them): the
+    # r and theta components of X and beta vanish in the axisymmetric limit,
+    # and their own maxima are iteration noise
     names = ["psi", "alpha", "beta_r", "beta_theta", "beta_phi", "X_r", "X_theta", "X_phi"]
     ref = [psi, alpha] + beta + X
+    scale_b = max(float(t.abs().max()) for t in beta)
+    scale_x = max(float(t.abs().max()) for t in X)
     err = {}
-    for nm, a, b in zip(names, mixed_fields, ref):
-        den = float(b.abs().max())
+    for q, (nm, a, b) in enumerate(zip(names, mixed_fields, ref)):
+        den = float(b.abs().max()) if q < 2 else (scale_b if q < 5 else scale_x)
         num = float((a - b).abs().max())
         err[nm] = num / den if den > 0 else num
+    err["delta_psi"] = float((mixed_fields[0] - psi).abs().max()) / float((psi - 1).abs().max())
+    err["delta_alpha"] = float((mixed_fields[1] - alpha).abs().max()) / float((alpha - 1).abs().max())
     lat = sorted(ms)
     return {"precision": "fp64", "value": ups / (sum(ms) * 1e-3) / 1e9, "unit": UNIT,
             "ms_per_solve": sum(ms) / len(ms), "solves_per_s": 1e3 * len(ms) / sum(ms),

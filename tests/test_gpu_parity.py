@@ -265,9 +265,9 @@ def test_vector_solve_parity(mg, geom, n, lo, hi, mixed):
 
 
 def run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="fp64", psi_only=False, tol=1e-10, accel_depth=0,
-                 cycle="v"):
+                 cycle="v", **kw):
     d, gd = descs(mg, geom, n, lo, hi, tol=tol, max_cycles=1000, precision=precision, accel_depth=accel_depth,
-                  cycle=cycle)
+                  cycle=cycle, **kw)
     shp = o.shape(d)
     psi, alpha = np.ones(shp), np.ones(shp)
     beta = [np.zeros(shp) for _ in range(3)]
@@ -435,8 +435,12 @@ def test_mixed_precision_xcfc_error_vs_oracle(mg, case, accel):
         U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], 100.0)
     else:
         U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0)
-    rg, ro, got, want = run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="mixed", accel_depth=accel)
+    # mixed iterations do not decrease monotonically on the larger grid: no
+    # stall check there (as in the benchmark)
+    kw = {"stall_window": 0} if case == "sph3d64" else {}
+    rg, ro, got, want = run_cfc_pair(mg, geom, n, lo, hi, U, S, Si, precision="mixed", accel_depth=accel, **kw)
     for k in ("X", "psi", "alphapsi", "beta"):
+        assert ro[k]["status"] == "ok"
         assert rg[k]["status"] == "ok" and rg[k]["rel"] <= 1e-10
     errs = field_errors(got, want)
     assert max(errs.values()) < 1e-9, errs
