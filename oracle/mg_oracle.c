@@ -1426,3 +1426,119 @@ void or_div_c(const or_desc* d, double* const B[3], double* div) {
   div_c(&g, Bg, div);
   for (int c = 0; c < d->ndim; ++c) free(Bg[c]);
 }
+
+/* ------------------------------------ divergence cleaning, exact projection */
+
+/* Exact-projection variant of the divergence cleaning on Cartesian grids
+ * (not the paper's method: Sec. 2.2 eqs. (poisson) and (update_bfield) with
+ * the compact Laplacian replaced by div_c grad_c, the operator the update
+ * actually applies).
+ *   grad_c Phi: central differences, the Phi ghost mirrored about the
+ *     boundary cell's centre (Phi_{-1} = Phi_1, Phi_n = Phi_{n-2}), so the
+ *     normal gradient vanishes in the boundary cells;
+ *   div_c: central differences, ghosts of its argument copied from the
+ *     boundary cell (the rule of B).
+ * With these rules div_c grad_c restricted to one parity class of cells
+ * (i mod 2, j mod 2, k mod 2) is the compact Laplacian of spacing 2 h with
+ * copied (Neumann) ghosts, and classes do not couple: the solve splits into
+ * 2^d compact Neumann problems of n/2 cells per dimension.  Each needs a
+ * mean-free right-hand side: b = div_c B minus its mean over the class.
+ * After B <- B - grad_c Phi, div_c B equals that class mean on every cell
+ * of the class.  Each class is solved by the same multigrid (d's solver
+ * settings, n/2 cells, spacing 2 h); rep->solve gets the largest cycle
+ * count and residual over the classes and the worst status. */
+static int parity_of(int i, int j, int k) { return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2); }
+
+int or_clean_divb_exact(const or_desc* d, double* const B[3], double* phi, or_divb_report* rep) {
+  if (d->geom != GEOM_CART) return 1;
+  OGrid g;
+  finest_grid(d, &g);
+  const long N = ncells(d);
+  const int three = d->ndim == 3;
+  const int nclass = three ? 8 : 4;
+  double* Bg[3] = {NULL, NULL, NULL};
+  for (int c = 0; c < d->ndim; ++c) {
+    Bg[c] = calloc(g.size, sizeof(double));
+    load_interior(&g, Bg[c], B[c]);
+  }
+  double* div = calloc(N, sizeof(double));
+  div_c(&g, Bg, div);
+  div_norms(div, N, &rep->max_div_before, &rep->l2_div_before);
+  or_desc ds = *d;
+  for (int a = 0; a < d->ndim; ++a) ds.n[a] = d->n[a] / 2;
+  const int m0 = ds.n[0], m1 = ds.n[1], m2 = three ? ds.n[2] : 1;
+  const long M = (long)m0 * m1 * m2;
+  double* bs = calloc(M, sizeof(double));
+  double* ps = calloc(M, sizeof(double));
+  int status = 0;
+  memset(&rep->solve, 0, sizeof(rep->solve));
+  for (int s = 0; s < nclass; ++s) {
+    const int pi = s & 1, pj = (s >> 1) & 1, pk = (s >> 2) & 1;
+    /* gather the class (dimension 0 fastest) and remove its mean */
+    double sum = 0.0;
+    for (int k = 0; k < m2; ++k)
+      for (int j = 0; j < m1; ++j)
+        for (int i = 0; i < m0; ++i) {
+          const int fi = 2 * i + pi, fj = 2 * j + pj, fk = three ? 2 * k + pk : 0;
+          const double v = div[fi + (long)d->n[0] * (fj + (long)d->n[1] * fk)];
+          bs[i + (long)m0 * (j + (long)m1 * k)] = v;
+          sum += v;
+        }
+    const double mean = sum / (double)M;
+    for (long q = 0; q < M; ++q) {
+      bs[q] -= mean;
+      ps[q] = 0.0;
+    }
+    or_report r;
+    const int st = or_solve_scalar(&ds, EQ_LIN, BC_NEUMANN, 1, NULL, NULL, NULL, bs, ps, &r);
+    if (st != 0 && status == 0) status = st;
+    if (r.cycles > rep->solve.cycles) rep->solve.cycles = r.cycles;
+    if (r.rel > rep->solve.rel || s == 0) rep->solve.rel = r.rel;
+    for (int k = 0; k < m2; ++k)
+      for (int j = 0; j < m1; ++j)
+        for (int i = 0; i < m0; ++i) {
+          const int fi = 2 * i + pi, fj = 2 * j + pj, fk = three ? 2 * k + pk : 0;
+          phi[fi + (long)d->n[0] * (fj + (long)d->n[1] * fk)] = ps[i + (long)m0 * (j + (long)m1 * k)];
+        }
+  }
+  rep->solve.status = status;
+  /* Phi with mirrored ghosts, dimensions filled in the order 0, 1, 2 over
+   * the ranges already extended */
+  double* pg = calloc(g.size, sizeof(double));
+  load_interior(&g, pg, phi);
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  for (int k = 0; k < n2; ++k)
+    for (int j = 0; j < n1; ++j) {
+      pg[IX(&g, -1, j, k)] = pg[IX(&g, 1, j, k)];
+      pg[IX(&g, n0, j, k)] = pg[IX(&g, n0 - 2, j, k)];
+    }
+  for (int k = 0; k < n2; ++k)
+    for (int i = -1; i <= n0; ++i) {
+      pg[IX(&g, i, -1, k)] = pg[IX(&g, i, 1, k)];
+      pg[IX(&g, i, n1, k)] = pg[IX(&g, i, n1 - 2, k)];
+    }
+  if (three)
+    for (int j = -1; j <= n1; ++j)
+      for (int i = -1; i <= n0; ++i) {
+        pg[IX(&g, i, j, -1)] = pg[IX(&g, i, j, 1)];
+        pg[IX(&g, i, j, n2)] = pg[IX(&g, i, j, n2 - 2)];
+      }
+  for (int k = 0; k < n2; ++k)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n0; ++i) {
+        double G[3];
+        grad_phys(&g, pg, i, j, k, G);
+        for (int c = 0; c < d->ndim; ++c) Bg[c][IX(&g, i, j, k)] -= G[c];
+      }
+  div_c(&g, Bg, div);
+  div_norms(div, N, &rep->max_div_after, &rep->l2_div_after);
+  for (int c = 0; c < d->ndim; ++c) {
+    store_interior(&g, B[c], Bg[c]);
+    free(Bg[c]);
+  }
+  free(pg);
+  free(bs);
+  free(ps);
+  free(div);
+  return status;
+}

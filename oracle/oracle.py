@@ -94,6 +94,7 @@ def lib():
             _lib.or_aij.argtypes = [D, P, P, P]
             _lib.or_solve_cfc.argtypes = [D, P, P, P, P, P, P, P, C.POINTER(CfcReport)]
             _lib.or_clean_divb.argtypes = [D, P, P, C.POINTER(DivbReport)]
+            _lib.or_clean_divb_exact.argtypes = [D, P, P, C.POINTER(DivbReport)]
             _lib.or_div_c.argtypes = [D, P, P]
             _lib.or_beta_rhs.argtypes = [D, P, P, P, P, P]
         return _lib
@@ -217,11 +218,14 @@ def solve_cfc(d, U, S, Si, psi, alpha, beta, X, psi_only=False):
     return {"status": STATUS.get(st, st), **{names[k]: r.rep[k].as_dict() for k in range(4)}}
 
 
-def clean_divb(d, B, phi):
-    """Elliptic divergence cleaning (eqs. poisson, update_bfield); B in place."""
+def clean_divb(d, B, phi, exact=False):
+    """Elliptic divergence cleaning (eqs. poisson, update_bfield); B in place.
+    exact: the exact-projection variant (Cartesian; div_c grad_c Phi = b,
+    split into its 2^d compact parity-class problems)."""
     r = DivbReport()
     Bs = list(B) + [B[0]] * (3 - len(B))
-    st = lib().or_clean_divb(C.byref(d), _parr(Bs), _p(phi), C.byref(r))
+    fn = lib().or_clean_divb_exact if exact else lib().or_clean_divb
+    st = fn(C.byref(d), _parr(Bs), _p(phi), C.byref(r))
     return {"status": STATUS.get(st, st), "solve": r.solve.as_dict(),
             "max_div_before": r.max_div_before, "l2_div_before": r.l2_div_before,
             "max_div_after": r.max_div_after, "l2_div_after": r.l2_div_after}
