@@ -66,6 +66,7 @@ enum { MG_MIXED_4PT = 0, MG_MIXED_CORNER = 1 };            /* mixed derivative *
 enum { MG_BC_ROBIN = 0, MG_BC_DIRICHLET = 1, MG_BC_NEUMANN = 2 };
 enum { MG_EQ_PSI = 0, MG_EQ_LIN = 1, MG_EQ_VEC = 2 };      /* equation kinds */
 enum { MG_CYCLE_V = 0, MG_CYCLE_FMG = 1 };                 /* iteration */
+enum { MG_DIVB_COMPACT = 0, MG_DIVB_EXACT = 1 };           /* div-B cleaning */
 
 /*
  * Grid and solver settings.
@@ -101,6 +102,13 @@ enum { MG_CYCLE_V = 0, MG_CYCLE_FMG = 1 };                 /* iteration */
  *             V-cycle from that level.  In MG_MIXED the FP32 correction
  *             equation gets the same structure from a zero correction.
  *             One FMG cycle counts as one cycle.
+ *   divb_variant  MG_DIVB_COMPACT: mg_clean_divB solves the paper's compact
+ *             Poisson equation (Sec. 2.2, eq. poisson).  MG_DIVB_EXACT
+ *             (Cartesian grids with every n >= 4; not the paper's method):
+ *             it solves div_c grad_c Phi = b, the operator the update of
+ *             eq. (update_bfield) applies, so that the cleaned field's
+ *             central divergence is exactly removed up to one constant per
+ *             parity class of cells (see mg_clean_divB).
  */
 typedef struct {
   int ndim;
@@ -116,6 +124,7 @@ typedef struct {
   int stall_window;
   int accel_depth;
   int cycle;
+  int divb_variant;
 } mg_grid_desc;
 
 #define MG_HIST 1024
@@ -224,6 +233,16 @@ typedef struct {
  *     Neumann ghosts sums to zero (so the Neumann problem is compatible);
  *     grad Phi in physical components.
  * The report's divergence norms are unweighted over the cells.
+ * With desc.divb_variant = MG_DIVB_EXACT (Cartesian) the Poisson operator is
+ * div_c grad_c, grad_c taking Phi ghosts mirrored about the boundary cell's
+ * centre (Phi_{-1} = Phi_1, Phi_n = Phi_{n-2}) and div_c copied ghosts of
+ * its argument.  It splits into 2^ndim compact Neumann problems, one per
+ * parity class of cells (i mod 2, j mod 2[, k mod 2]), of n / 2 cells per
+ * dimension and spacing 2 h; each is solved by the multigrid of the same
+ * settings for b = div B minus its mean over the class.  After the update
+ * div_c B equals that class mean on every cell of the class.  The report's
+ * solve entry holds the largest cycle count and residual over the classes,
+ * the summed time and cell updates, and the first failing status.
  */
 int mg_clean_divB(mg_hierarchy* h, double* B[3], double* phi_out, int flags, mg_divb_report* rep);
 

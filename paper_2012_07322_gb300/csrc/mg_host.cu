@@ -90,6 +90,9 @@ struct mg_hierarchy {
   // built, -1 unavailable; one device buffer holds every level's tables
   int push_state = 0;
   int* push_buf = nullptr;
+  // MG_DIVB_EXACT: the hierarchy of the parity-class problems (n / 2 cells
+  // per dimension), on this hierarchy's stream
+  mg_hierarchy* sub = nullptr;
   bool prof_on = false;
   bool fold_k32 = false;  // while capturing a V-cycle of eq. psi: K is restricted on the way down
   std::vector<cudaEvent_t> ev;
@@ -182,7 +185,24 @@ int validate(const mg_grid_desc* d) {
   if (d->stall_window < 0) return fail(MG_ERR_INVALID, "bad stall_window");
   if (d->accel_depth < 0 || d->accel_depth > AA_MAX) return fail(MG_ERR_INVALID, "accel_depth must be in 0..16");
   if (d->cycle != MG_CYCLE_V && d->cycle != MG_CYCLE_FMG) return fail(MG_ERR_INVALID, "cycle must be V or FMG");
+  if (d->divb_variant != MG_DIVB_COMPACT && d->divb_variant != MG_DIVB_EXACT)
+    return fail(MG_ERR_INVALID, "divb_variant must be MG_DIVB_COMPACT or MG_DIVB_EXACT");
+  if (d->divb_variant == MG_DIVB_EXACT) {
+    if (d->geom != MG_CART) return fail(MG_ERR_INVALID, "MG_DIVB_EXACT needs a Cartesian grid");
+    for (int k = 0; k < d->ndim; ++k)
+      if (d->n[k] < 4) return fail(MG_ERR_INVALID, "MG_DIVB_EXACT needs every n >= 4");
+  }
   return MG_OK;
+}
+
+// Descriptor of the parity-class problems of the exact-projection cleaning:
+// n / 2 cells per dimension over the same domain (spacing 2 h), the same
+// solver settings.
+mg_grid_desc class_desc(const mg_grid_desc* d) {
+  mg_grid_desc c = *d;
+  for (int k = 0; k < d->ndim; ++k) c.n[k] = d->n[k] / 2;
+  c.divb_variant = MG_DIVB_COMPACT;
+  return c;
 }
 
 // Level sizes: halve every dimension while all are even and >= 4.
@@ -1322,6 +1342,7 @@ int gmg::set_last_error(int status, const char* msg) { return fail(status, msg);
 void gmg::hier_set_stream(mg_hierarchy* H, cudaStream_t st) {
   if (H->own_stream || st == nullptr) return;
   H->st = st;
+  if (H->sub) H->sub->st = st;
 }
 
 // ================================================================== C ABI
@@ -1350,6 +1371,10 @@ int mg_hierarchy_bytes(const mg_grid_desc* desc, size_t* bytes) {
   if (st) return st;
   if (!bytes) return fail(MG_ERR_INVALID, "null output");
   *bytes = layout(nullptr, desc, nullptr);
+  if (desc->divb_variant == MG_DIVB_EXACT) {
+    const mg_grid_desc c = class_desc(desc);
+    *bytes += layout(nullptr, &c, nullptr);
+  }
   return MG_OK;
 }
 
@@ -1444,6 +1469,15 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
     L.v32 = make_view<float>(&H->d, L, L.ti32, L.tj32);
     L.v32.vc = L.vc32;
   }
+  if (H->d.divb_variant == MG_DIVB_EXACT) {
+    const mg_grid_desc c = class_desc(&H->d);
+    const int sst = mg_create_hierarchy(&c, (void*)H->st, &H->sub);
+    if (sst != MG_OK) {
+      H->sub = nullptr;
+      mg_destroy_hierarchy(H);
+      return sst;
+    }
+  }
   *out = H;
   return MG_OK;
 }
@@ -1481,6 +1515,7 @@ int mg_profile_read(mg_hierarchy* H, int klass, int64_t* launches, double* ms, i
 int mg_destroy_hierarchy(mg_hierarchy* H) {
   if (!H) return MG_OK;
   if (H->st) cudaStreamSynchronize(H->st);
+  if (H->sub) mg_destroy_hierarchy(H->sub);
   for (cudaEvent_t e : H->ev) cudaEventDestroy(e);
   for (double* p : H->stage) cudaFree(p);
   if (H->aa) cudaFree(H->aa);
@@ -1707,6 +1742,56 @@ int mg_clean_divB(mg_hierarchy* H, double* B[3], double* phi_out, int flags, mg_
     wsum = si * sj * L0.n[2];
   }
   double mb, lb, ma, la;
+  if (H->d.divb_variant == MG_DIVB_EXACT) {
+    // the parity classes of div minus their means (class-major in r[1]),
+    // one compact Neumann solve per class on the half-size hierarchy (Phi
+    // class-major in r[2]), B -= grad Phi with mirrored Phi ghosts
+    const int ncl = nd == 3 ? 8 : 4;
+    const long M = (long)L0.cells() / ncl;
+    div_into_r();
+    launch_class_gather(v, L0.r[0], H->d_part, NPARTS / 8, L0.r[1], H->st);
+    if ((st = norms(&mb, &lb))) return st;
+    CK(cudaMemsetAsync(L0.r[2], 0, sizeof(double) * L0.cells(), H->st));
+    mg_solve_report agg{};
+    for (int q = 0; q < ncl; ++q) {
+      mg_solve_report r{};
+      const int sq = mg_solve_scalar(H->sub, MG_EQ_LIN, MG_BC_NEUMANN, 1, nullptr, nullptr, nullptr,
+                                     L0.r[1] + q * M, L0.r[2] + q * M, &r);
+      if (sq == MG_ERR_CUDA || sq == MG_ERR_INVALID || sq == MG_ERR_OOM) return sq;
+      if (q == 0 || r.cycles > agg.cycles) {
+        agg.cycles = r.cycles;
+        agg.nhist = r.nhist;
+        std::memcpy(agg.hist, r.hist, sizeof(double) * (size_t)r.nhist);
+      }
+      agg.rel = q == 0 ? r.rel : std::max(agg.rel, r.rel);
+      agg.ms += r.ms;
+      agg.cell_updates += r.cell_updates;
+      if (st == MG_OK && sq != MG_OK) st = sq;
+    }
+    agg.status = st;
+    if (rep) rep->solve = agg;
+    double* pd = nullptr;
+    int s2 = MG_OK;
+    if (phi_out) {
+      pd = phi_out;
+      if (host && (s2 = stage_get(H, 3, &pd))) return s2;
+    }
+    launch_grad_update_exact(v, L0.r[2], Bd, pd, H->st);
+    div_into_r();
+    if ((s2 = norms(&ma, &la))) return s2;
+    if (phi_out && host && (s2 = stage_out(H, pd, phi_out))) return s2;
+    if (host)
+      for (int c = 0; c < nd; ++c)
+        if ((s2 = stage_out(H, Bd[c], B[c]))) return s2;
+    CK(cudaStreamSynchronize(H->st));
+    if (rep) {
+      rep->max_div_before = mb;
+      rep->l2_div_before = lb;
+      rep->max_div_after = ma;
+      rep->l2_div_after = la;
+    }
+    return st;
+  }
   div_into_r();
   if (curv)
     launch_sub_wmean_into(v, L0.r[0], H->d_part, NPARTS, wsum, L0.f[0], H->st);

@@ -202,6 +202,14 @@ void launch_grad_update_curv(const LevelView<double>& L, const double* phi, doub
 void launch_sub_mean_into(const LevelView<double>& L, const double* div, const double* part, int nparts,
                           double* b, cudaStream_t st);
 void launch_grad_update(const LevelView<double>& L, const double* phi, double* const B[3], cudaStream_t st);
+// Exact-projection cleaning (Cartesian, n >= 4): the parity classes of div
+// minus their class means into a class-major buffer (nparts blocks per
+// class; part holds nparts x 2^d doubles), and B -= grad Phi with mirrored
+// Phi ghosts from the class-major Phi (phi_out nullable, ghost-free).
+void launch_class_gather(const LevelView<double>& L, const double* div, double* part, int nparts, double* dst,
+                         cudaStream_t st);
+void launch_grad_update_exact(const LevelView<double>& L, const double* phis, double* const B[3], double* phi_out,
+                              cudaStream_t st);
 void launch_xcfc_ap_init(const LevelView<double>& L, const double* alpha, const double* dpsi, double* dap,
                          cudaStream_t st);
 void launch_xcfc_alpha_out(const LevelView<double>& L, const double* dap, const double* dpsi, double* alpha,

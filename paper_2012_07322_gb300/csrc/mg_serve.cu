@@ -34,7 +34,8 @@ double now_ms() {
 bool desc_equal(const mg_grid_desc& a, const mg_grid_desc& b) {
   if (a.ndim != b.ndim || a.geom != b.geom || a.precision != b.precision || a.nu1 != b.nu1 ||
       a.nu2 != b.nu2 || a.max_cycles != b.max_cycles || a.tol != b.tol || a.mixed_deriv != b.mixed_deriv ||
-      a.stall_window != b.stall_window || a.accel_depth != b.accel_depth)
+      a.stall_window != b.stall_window || a.accel_depth != b.accel_depth || a.cycle != b.cycle ||
+      a.divb_variant != b.divb_variant)
     return false;
   for (int d = 0; d < a.ndim; ++d)
     if (a.n[d] != b.n[d] || a.lo[d] != b.lo[d] || a.hi[d] != b.hi[d]) return false;

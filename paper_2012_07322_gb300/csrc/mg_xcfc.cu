@@ -409,6 +409,123 @@ void launch_grad_update(const LevelView<double>& L, const double* phi, double* c
   launch_k(k_grad_update, (unsigned)g, 256, 0, st, L, phi, B[0], B[1], B[2]);
 }
 
+// ------------------------------------------ exact-projection div-B cleaning
+// Cartesian grids, every n >= 4.  The parity classes of the cells, s = (i &
+// 1) | (j & 1) << 1 | (k & 1) << 2, are solved as separate compact Neumann
+// problems of n / 2 cells per dimension (div_c grad_c with mirrored Phi
+// ghosts and copied ghosts of its argument splits that way).  Class-major
+// buffers: class s holds [s M, (s + 1) M), M = N / 2^d, its cell (i, j, k)
+// at (i >> 1) + m0 ((j >> 1) + m1 (k >> 1)), m = n / 2.
+
+struct ClassGrid {
+  int lm0, lm1;  // log2 of n0 / 2, n1 / 2
+  long M;        // cells per class
+  __device__ __forceinline__ void fine(int s, long r, int three, int& i, int& j, int& k) const {
+    const int a = (int)(r & ((1L << lm0) - 1));
+    const long t = r >> lm0;
+    const int b = (int)(t & ((1L << lm1) - 1));
+    const int c = (int)(t >> lm1);
+    i = 2 * a + (s & 1);
+    j = 2 * b + ((s >> 1) & 1);
+    k = three ? 2 * c + ((s >> 2) & 1) : 0;
+  }
+  __device__ __forceinline__ long at(int i, int j, int k) const {
+    const int s = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+    return (long)s * M + (i >> 1) + ((long)(j >> 1) << lm0) + ((long)(k >> 1) << (lm0 + lm1));
+  }
+};
+
+__host__ __device__ inline ClassGrid class_grid(const LevelView<double>& L) {
+  ClassGrid g;
+  g.lm0 = L.ln0 - 1;
+  g.lm1 = L.ln1 - 1;
+  g.M = ((long)L.n0 * L.n1 * L.n2) >> (L.three ? 3 : 2);
+  return g;
+}
+
+// Block sums of div over each class: block (p, s) strides over class s.
+__global__ void k_class_sums(LevelView<double> L, ClassGrid G, const double* __restrict__ div,
+                             double* __restrict__ part) {
+  pdl_entry();
+  __shared__ double sm[32];
+  const int s = blockIdx.y;
+  double acc = 0.0;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < G.M; r += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    G.fine(s, r, L.three, i, j, k);
+    acc += div[L.idx(i, j, k)];
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += sm[w];
+    part[s * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Class s of div minus its mean into the class-major buffer dst.
+__global__ void k_class_gather(LevelView<double> L, ClassGrid G, const double* __restrict__ div,
+                               const double* __restrict__ part, int nparts, double* __restrict__ dst) {
+  pdl_entry();
+  __shared__ double mean;
+  const int s = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < nparts; ++q) t += part[s * nparts + q];
+    mean = t / (double)G.M;
+  }
+  __syncthreads();
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < G.M; r += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    G.fine(s, r, L.three, i, j, k);
+    dst[s * G.M + r] = div[L.idx(i, j, k)] - mean;
+  }
+}
+
+// B <- B - grad Phi, central differences with Phi ghosts mirrored about the
+// boundary cell's centre (Phi_{-1} = Phi_1, Phi_n = Phi_{n-2}), Phi read
+// from the class-major buffer; phi_out (nullable, ghost-free) receives Phi.
+__global__ void k_grad_update_exact(LevelView<double> L, ClassGrid G, const double* __restrict__ phis,
+                                    double* __restrict__ B0, double* __restrict__ B1, double* __restrict__ B2,
+                                    double* __restrict__ phi_out) {
+  pdl_entry();
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  const double c0 = 0.5 / L.h0, c1 = 0.5 / L.h1, c2 = 0.5 / L.h2;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const int ip = i < L.n0 - 1 ? i + 1 : L.n0 - 2, im = i > 0 ? i - 1 : 1;
+    const int jp = j < L.n1 - 1 ? j + 1 : L.n1 - 2, jm = j > 0 ? j - 1 : 1;
+    B0[q] -= (phis[G.at(ip, j, k)] - phis[G.at(im, j, k)]) * c0;
+    B1[q] -= (phis[G.at(i, jp, k)] - phis[G.at(i, jm, k)]) * c1;
+    if (L.three) {
+      const int kp = k < L.n2 - 1 ? k + 1 : L.n2 - 2, km = k > 0 ? k - 1 : 1;
+      B2[q] -= (phis[G.at(i, j, kp)] - phis[G.at(i, j, km)]) * c2;
+    }
+    if (phi_out) phi_out[q] = phis[G.at(i, j, k)];
+  }
+}
+
+void launch_class_gather(const LevelView<double>& L, const double* div, double* part, int nparts, double* dst,
+                         cudaStream_t st) {
+  count_launch(2);
+  const ClassGrid G = class_grid(L);
+  const dim3 grid(nparts, L.three ? 8 : 4);
+  launch_k(k_class_sums, grid, 256, 0, st, L, G, div, part);
+  launch_k(k_class_gather, grid, 256, 0, st, L, G, div, (const double*)part, nparts, dst);
+}
+
+void launch_grad_update_exact(const LevelView<double>& L, const double* phis, double* const B[3], double* phi_out,
+                              cudaStream_t st) {
+  count_launch();
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  long g = (n + 255) / 256;
+  if (g > 8192) g = 8192;
+  launch_k(k_grad_update_exact, (unsigned)g, 256, 0, st, L, class_grid(L), phis, B[0], B[1], B[2], phi_out);
+}
+
 void launch_div_curv(const LevelView<double>& L, double* const Bg[3], double* div, double* part, int nparts,
                      cudaStream_t st) {
   count_launch();

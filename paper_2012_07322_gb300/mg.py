@@ -23,6 +23,7 @@ MG_MIXED_4PT, MG_MIXED_CORNER = 0, 1
 MG_BC_ROBIN, MG_BC_DIRICHLET, MG_BC_NEUMANN = 0, 1, 2
 MG_EQ_PSI, MG_EQ_LIN, MG_EQ_VEC = 0, 1, 2
 MG_CFC_PSI_ONLY, MG_HOST_POINTERS = 1, 2
+MG_DIVB_COMPACT, MG_DIVB_EXACT = 0, 1
 MG_HIST = 1024
 
 GEOM = {"cart": MG_CART, "cyl": MG_CYL, "sph": MG_SPH}
@@ -47,7 +48,8 @@ class mg_grid_desc(C.Structure):
     _fields_ = [("ndim", C.c_int), ("geom", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("precision", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("max_cycles", C.c_int), ("tol", C.c_double), ("mixed_deriv", C.c_int),
-                ("stall_window", C.c_int), ("accel_depth", C.c_int), ("cycle", C.c_int)]
+                ("stall_window", C.c_int), ("accel_depth", C.c_int), ("cycle", C.c_int),
+                ("divb_variant", C.c_int)]
 
 
 class mg_solve_report(C.Structure):
@@ -148,7 +150,7 @@ def _check(status, where, allow=(MG_OK,)):
 
 
 def grid_desc(geom, n, lo=None, hi=None, precision="fp64", nu1=2, nu2=2, max_cycles=1000, tol=1e-10,
-              mixed="4pt", stall_window=10, accel_depth=0, cycle="v"):
+              mixed="4pt", stall_window=10, accel_depth=0, cycle="v", divb="compact"):
     """Build an mg_grid_desc; lo / hi default to the natural domain of the
     geometry where it is fixed (spherical angles, cylindrical phi)."""
     d = mg_grid_desc()
@@ -167,6 +169,7 @@ def grid_desc(geom, n, lo=None, hi=None, precision="fp64", nu1=2, nu2=2, max_cyc
     d.stall_window = stall_window
     d.accel_depth = accel_depth
     d.cycle = {"v": 0, "fmg": 1}[cycle]
+    d.divb_variant = {"compact": MG_DIVB_COMPACT, "exact": MG_DIVB_EXACT}[divb]
     return d
 
 

@@ -45,6 +45,11 @@ def test_host_only_entry_points():
     with pytest.raises(mg.MgError):
         mg.mg_hierarchy_bytes(bad)
     assert mg.mg_hierarchy_bytes(mg.grid_desc("sph", [64, 32], hi=[100.0, np.pi], cycle="fmg")) > 0
+    # the exact projection adds the half-size hierarchy of its parity classes
+    lo3, hi3 = [-1.0] * 3, [1.0] * 3
+    plain = mg.mg_hierarchy_bytes(mg.grid_desc("cart", [32] * 3, lo3, hi3))
+    exact = mg.mg_hierarchy_bytes(mg.grid_desc("cart", [32] * 3, lo3, hi3, divb="exact"))
+    assert exact == plain + mg.mg_hierarchy_bytes(mg.grid_desc("cart", [16] * 3, lo3, hi3))
     bad = mg.grid_desc("sph", [64, 32], hi=[100.0, np.pi])
     bad.cycle = 7                                                     # neither V nor FMG
     with pytest.raises(mg.MgError):
@@ -89,6 +94,9 @@ def _set(d, **kw):
     ("negative stall window", "cart", [8, 8], {"stall_window": -1}),
     ("Anderson depth above 16", "cart", [8, 8], {"accel_depth": 17}),
     ("negative Anderson depth", "cart", [8, 8], {"accel_depth": -1}),
+    ("div-B variant", "cart", [8, 8], {"divb_variant": 2}),
+    ("exact projection on a spherical grid", "sph", [8, 8], {"divb_variant": 1}),
+    ("exact projection with n = 2", "cart", [8, 2], {"divb_variant": 1}),
 ])
 def test_descriptor_validation_rejects(what, geom, n, kw):
     """Every rule of the descriptor (grid, domain of the geometry, solver

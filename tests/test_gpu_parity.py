@@ -586,3 +586,55 @@ def test_curvilinear_divb_cleaning_parity(mg, case):
         assert relerr(host(Bt[k]), Bo[k]) < 1e-9
     for key in ("max_div_before", "l2_div_before", "max_div_after", "l2_div_after"):
         assert abs(rg[key] - ro[key]) <= 1e-9 * ro["max_div_before"], key
+
+
+# ------------------------------------------- exact-projection div-B cleaning
+
+
+@pytest.mark.parametrize("case,precision", [("cube32", "fp64"), ("cube64", "fp64"), ("cube64", "mixed"),
+                                            ("slab2d", "fp64"), ("slab2d", "mixed")])
+def test_exact_projection_divb_parity(mg, case, precision):
+    """MG_DIVB_EXACT: Phi, B and the divergence norms match the oracle's
+    exact projection (2^d parity-class solves) to 1e-9; the cleaned field's
+    central divergence is constant on every parity class (the class mean of
+    the divergence before) to round-off."""
+    if case == "slab2d":
+        rng = np.random.default_rng(13)
+        n = [64, 32]
+        B = [rng.standard_normal((32, 64)) for _ in range(2)]
+        lo, hi = [-1.0, -0.5], [1.0, 0.5]
+    else:
+        m = 32 if case == "cube32" else 64
+        n = [m] * 3
+        B = inputs.divb_field(n=m)
+        lo, hi = [-1.0] * 3, [1.0] * 3
+    nd = len(n)
+    d = o.desc("cart", n, lo, hi, tol=1e-10, max_cycles=1000)
+    gd = mg.grid_desc("cart", n, lo, hi, tol=1e-10, max_cycles=1000, precision=precision, divb="exact")
+    Bo = [b.copy() for b in B]
+    phi = np.zeros(o.shape(d))
+    ro = o.clean_divb(d, Bo, phi, exact=True)
+    assert ro["status"] == "ok"
+    h = mg.Hierarchy(gd)
+    Bt = [dev(b) for b in B]
+    pt = torch.zeros(o.shape(d), dtype=torch.float64, device="cuda")
+    rg = mg.mg_clean_divB(h, Bt, pt)
+    h.close()
+    assert rg["status"] == "ok" and rg["solve"]["rel"] <= 1e-10
+    if precision == "fp64":
+        assert abs(rg["solve"]["cycles"] - ro["solve"]["cycles"]) <= 1
+    got_phi = host(pt)
+    # Phi is defined up to one constant per class: compare class-mean-free
+    for cls in np.ndindex(*([2] * nd)):
+        sl = tuple(slice(p, None, 2) for p in cls)
+        a, b = got_phi[sl], phi[sl]
+        assert np.abs((a - a.mean()) - (b - b.mean())).max() <= 1e-9 * np.abs(phi).max()
+    for k in range(nd):
+        assert relerr(host(Bt[k]), Bo[k]) < 1e-9
+    for key in ("max_div_before", "l2_div_before", "max_div_after", "l2_div_after"):
+        assert abs(rg[key] - ro[key]) <= 1e-9 * ro["max_div_before"], key
+    div0 = o.div_c(d, B)
+    div1 = o.div_c(d, [host(b) for b in Bt])
+    for cls in np.ndindex(*([2] * nd)):
+        sl = tuple(slice(p, None, 2) for p in cls)
+        assert np.abs(div1[sl] - div0[sl].mean()).max() <= 1e-8 * np.abs(div0).max()
