@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-divb", action="store_true", help="skip the 256^3 div-B cleaning measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the request-serving measurement")
+    p.add_argument("--serve-sweep", action="store_true",
+                   help="serving at arrival rates 250..4000/s, 1000 requests each, mixed and FP64 (minutes)")
     p.add_argument("--no-batch", action="store_true", help="skip the 512-solve batch measurement")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 solve beside the mixed one")
     p.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 solves (each ~1 s)")
@@ -300,89 +302,180 @@ def batch_measurement(mg, torch, count=512, slots=16):
             "cycles_psi_plus_alphapsi": {"min": min(cyc), "median": sorted(cyc)[len(cyc) // 2], "max": max(cyc)}}
 
 
-def serving_measurement(mg, torch, n_requests=160, rate=2000.0, slots=8):
-    """Request serving: Poisson arrivals (mean `rate` per second, seed 3) of
-    a mix of xCFC solves (80 %) and div-B cleanings (20 %) of several sizes,
-    16 warm-started streams, through mg_submit / mg_poll."""
-    import time
+# The serving mix: xCFC request kinds (geometry, grid) and their shares of
+# the xCFC requests.  The largest is the 3D spherical 128 x 64 x 64 grid:
+# the solver needs power-of-two grids, and 192 x 96 x 96 is not one.
+SERVE_KINDS = [(("sph", [64, 32], [0.0, 0.0], [100.0, np.pi]), 0.30),
+               (("sph", [128, 64], [0.0, 0.0], [100.0, np.pi]), 0.20),
+               (("cyl", [64, 128], [0.0, -100.0], [100.0, 100.0]), 0.20),
+               (("sph", [32, 16, 16], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.15),
+               (("sph", [64, 32, 32], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.10),
+               (("sph", [128, 64, 64], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.05)]
+SERVE_STREAMS = 24
+SERVE_STEPS = 4   # source variants per stream: consecutive "time steps" of a slowly changing star
+
+
+class UtilSampler:
+    """nvidia-smi utilization.gpu samples (share of time a kernel ran) while
+    requests are served."""
+
+    def __init__(self, gpu_id):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        self.fh = os.fdopen(fd, "w")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), "--query-gpu=utilization.gpu",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.fh.close()
+        vals = []
+        for line in open(self.path):
+            try:
+                vals.append(float(line.strip()))
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        return statistics.median(vals) if vals else None
+
+
+def serving_setup(mg, torch, precision):
+    """Resident inputs of the serving mix: SERVE_STREAMS warm-started xCFC
+    streams (seed 3), each with SERVE_STEPS source variants (rho_c grows by
+    0.2 % per step), and two div-B fields."""
     from paper_2012_07322_gb300 import inputs
     rng = np.random.default_rng(3)
-    kinds = [("sph", [64, 32], [0.0, 0.0], [100.0, np.pi]),
-             ("sph", [128, 64], [0.0, 0.0], [100.0, np.pi]),
-             ("cyl", [64, 128], [0.0, -100.0], [100.0, 100.0]),
-             ("sph", [32, 16, 16], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]),
-             ("sph", [64, 32, 32], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi])]
     dev = lambda a: torch.from_numpy(np.array(a)).cuda()
+    shares = np.array([w for _, w in SERVE_KINDS])
     streams = []
-    for sid in range(16):
-        geom, n, lo, hi = kinds[sid % len(kinds)]
+    for sid in range(SERVE_STREAMS):
+        geom, n, lo, hi = SERVE_KINDS[int(rng.choice(len(SERVE_KINDS), p=shares / shares.sum()))][0]
         rho_c, R = rng.uniform(5e-4, 2e-3), rng.uniform(8.0, 14.0)
-        if geom == "cyl":
-            U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0, rho_c, R)
-        elif len(n) == 2:
-            U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], 100.0, rho_c, R)
-        else:
-            U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0, rho_c, R)
-        desc = mg.grid_desc(geom, n, lo, hi, precision="mixed", tol=TOL, max_cycles=800, accel_depth=16,
+        steps = []
+        for t in range(SERVE_STEPS):
+            rc = rho_c * (1.0 + 0.002 * t)
+            if geom == "cyl":
+                U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0, rc, R)
+            elif len(n) == 2:
+                U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], 100.0, rc, R)
+            else:
+                U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0, rc, R)
+            steps.append((dev(U), dev(S), [dev(x) for x in Si]))
+        desc = mg.grid_desc(geom, n, lo, hi, precision=precision, tol=TOL, max_cycles=800, accel_depth=16,
                             stall_window=0)
-        streams.append((desc, dev(U), dev(S), [dev(x) for x in Si]))
+        streams.append((desc, steps, "%s%s" % (geom, "x".join(map(str, n)))))
     divbs = []
     for n in (32, 64):
         B = inputs.divb_field(n=n, n_modes=16, k_max=6)
-        desc = mg.grid_desc("cart", [n] * 3, [-1.0] * 3, [1.0] * 3, precision="mixed", tol=TOL, max_cycles=200,
+        desc = mg.grid_desc("cart", [n] * 3, [-1.0] * 3, [1.0] * 3, precision=precision, tol=TOL, max_cycles=200,
                             stall_window=0)
         divbs.append((desc, [dev(b) for b in B]))
+    return streams, divbs
+
+
+def serving_measurement(mg, torch, precision="mixed", rate=2000.0, n_requests=400, slots=8, gpu_id=None,
+                        setup=None):
+    """Request serving (continuous batching through mg_submit / mg_poll):
+    Poisson arrivals (mean `rate` per second, seed 3) of xCFC solves (80 %,
+    SERVE_KINDS; each request of a stream is its next time step, warm-started
+    from the stream's resident previous solution) and div-B cleanings (20 %,
+    32^3 and 64^3).  Requests are admitted into `slots` worker slots as they
+    free up; their kernels overlap on the device.  Reports solves/s, p50 and
+    p99 latency (submission to completion), the mean number of requests in
+    service (summed service time / wall time) and the median GPU utilization
+    (share of time a kernel ran) while serving."""
+    import time
+    rng = np.random.default_rng(3)
+    streams, divbs = setup if setup is not None else serving_setup(mg, torch, precision)
     plan = []
     t = 0.0
     for q in range(n_requests):
         t += rng.exponential(1.0 / rate)
-        plan.append((t, "divb" if rng.uniform() < 0.2 else "cfc", int(rng.integers(0, 16)), int(rng.integers(0, 2))))
-    srv = mg.Server(hbm_budget=48 << 30, max_slots=slots, max_queue=4 * n_requests)
-    # warm the hierarchy cache and the resident streams once
-    for sid, (desc, U, S, Si) in enumerate(streams):
+        plan.append((t, "divb" if rng.uniform() < 0.2 else "cfc", int(rng.integers(0, len(streams))),
+                     int(rng.integers(0, 2))))
+    srv = mg.Server(hbm_budget=96 << 30, max_slots=slots, max_queue=4 * n_requests)
+
+    def fields(U):
         psi = torch.ones(U.shape, dtype=torch.float64, device="cuda")
-        f = (psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)],
-             [torch.zeros_like(psi) for _ in range(3)])
-        srv.wait(srv.submit_cfc(desc, U, S, Si, *f, stream_id=sid + 1))
+        return (psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)],
+                [torch.zeros_like(psi) for _ in range(3)])
+
+    # warm the hierarchy cache and the resident streams (first time step)
+    for sid, (desc, steps, _) in enumerate(streams):
+        U, S, Si = steps[0]
+        srv.wait(srv.submit_cfc(desc, U, S, Si, *fields(U), stream_id=sid + 1))
     for desc, B in divbs:
         srv.wait(srv.submit_divb(desc, [b.clone() for b in B]))
     torch.cuda.synchronize()
-    pending, lat, statuses = {}, [], []
+    step_of = [1] * len(streams)
+    pending, lat, service, statuses, kinds_done = {}, [], [], [], {}
+    util = UtilSampler(gpu_id) if gpu_id is not None else None
+
+    def collect(tk):
+        done, res = srv.poll(tk)
+        if done:
+            lat.append(res["latency_ms"])
+            service.append(res["latency_ms"] - res["queue_ms"])
+            statuses.append(res["status"])
+            k = pending.pop(tk)
+            kinds_done.setdefault(k, []).append(res["latency_ms"])
+        return done
+
     t0 = time.perf_counter()
     for (ta, kind, sid, which) in plan:
         while time.perf_counter() - t0 < ta:
             for tk in list(pending):
-                done, res = srv.poll(tk)
-                if done:
-                    lat.append(res["latency_ms"])
-                    statuses.append(res["status"])
-                    del pending[tk]
+                collect(tk)
         if kind == "cfc":
-            desc, U, S, Si = streams[sid]
-            psi = torch.ones(U.shape, dtype=torch.float64, device="cuda")
-            f = (psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)],
-                 [torch.zeros_like(psi) for _ in range(3)])
-            tk = srv.submit_cfc(desc, U, S, Si, *f, stream_id=sid + 1)
+            desc, steps, name = streams[sid]
+            U, S, Si = steps[step_of[sid] % SERVE_STEPS]
+            step_of[sid] += 1
+            tk = srv.submit_cfc(desc, U, S, Si, *fields(U), stream_id=sid + 1)
         else:
             desc, B = divbs[which]
+            name = "divb%d" % desc.n[0]
             tk = srv.submit_divb(desc, [b.clone() for b in B])
-        pending[tk] = True
+        pending[tk] = name
     while pending:
         for tk in list(pending):
-            done, res = srv.poll(tk)
-            if done:
-                lat.append(res["latency_ms"])
-                statuses.append(res["status"])
-                del pending[tk]
+            collect(tk)
     wall = time.perf_counter() - t0
+    gpu_util = util.stop() if util else None
     srv.close()
     lat.sort()
-    return {"workload": "Poisson arrivals (mean %.0f/s, seed 3) of %d requests: 80%% xCFC (2D sph 64x32, "
-                        "128x64, 2D cyl 64x128, 3D sph 32x16x16, 64x32x32; 16 warm-started streams), 20%% "
-                        "div-B (32^3, 64^3); mixed precision, %d slots" % (rate, n_requests, slots),
-            "solves_per_s": n_requests / wall, "p50_ms": lat[len(lat) // 2],
-            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "wall_s": wall,
-            "ok": sum(1 for s in statuses if s == "ok"), "requests": n_requests}
+    pct = lambda a, q: a[min(len(a) - 1, int(q * len(a)))]
+    return {"precision": precision, "rate_per_s": rate, "requests": n_requests, "slots": slots,
+            "solves_per_s": n_requests / wall, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+            "wall_s": wall, "ok": sum(1 for x in statuses if x == "ok"),
+            "mean_in_service": sum(service) / (wall * 1e3), "gpu_util_pct": gpu_util,
+            "p50_ms_by_kind": {k: sorted(v)[len(v) // 2] for k, v in sorted(kinds_done.items())}}
+
+
+def serving_block(mg, torch, gpu_id, sweep):
+    """The serving measurement of the bench line: one point (mixed precision,
+    2000 requests/s, 400 requests); with sweep, arrival rates 250 ... 4000/s
+    with 1000 requests per point in mixed precision and FP64."""
+    work = ("Poisson arrivals (seed 3): 80%% xCFC on %d warm-started streams (each request the next of %d "
+            "time steps of a rotating star; grids %s), 20%% div-B (32^3, 64^3); continuous admission into "
+            "worker slots; uniform grids stand in for the two-level AMR of the serving workload"
+            % (SERVE_STREAMS, SERVE_STEPS, ", ".join("%s %s" % (k[0], "x".join(map(str, k[1])))
+                                                      for k, _ in SERVE_KINDS)))
+    if not sweep:
+        return {"workload": work, **serving_measurement(mg, torch, gpu_id=gpu_id)}
+    points = []
+    for precision in ("mixed", "fp64"):
+        setup = serving_setup(mg, torch, precision)
+        for rate in (250.0, 500.0, 1000.0, 2000.0, 4000.0):
+            points.append(serving_measurement(mg, torch, precision, rate, 1000, gpu_id=gpu_id, setup=setup))
+    return {"workload": work, "sweep": points}
 
 
 def fp64_arm(mg, torch, stream, Ud, Sd, Sid, shp, steps, warmup, accel, max_cycles, mixed_fields):
@@ -666,7 +759,7 @@ def main():
         divb_exact = divb_measurement(mg, torch, stream, args.steps, args.precision, peak, variant="exact")
     serving = None
     if not args.no_serve and world == 1:
-        serving = serving_measurement(mg, torch)
+        serving = serving_block(mg, torch, gpu_id, args.serve_sweep)
     batch = None
     if not args.no_batch and world == 1:
         batch = batch_measurement(mg, torch)

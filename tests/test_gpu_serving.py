@@ -8,6 +8,7 @@ hierarchies), so results are compared bit for bit."""
 import numpy as np
 import pytest
 
+import oracle.oracle as o
 from paper_2012_07322_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -95,6 +96,22 @@ def test_results_identical_alone_and_in_the_mix(mg):
         ref = alone[q % len(reqs)]
         for a, b in zip(out, ref):
             assert torch.equal(a, b), q
+    # the first request (2D spherical 64 x 32), the same alone and in the
+    # mix, is also the oracle's solution
+    args, U, S, Si = cfc_case("sph2d", 1)
+    geom, n, lo, hi = args
+    d = o.desc(geom, n, lo, hi, tol=1e-10, max_cycles=600, accel_depth=8, stall_window=0)
+    psi, alpha = np.ones(U.shape), np.ones(U.shape)
+    beta, X = [np.zeros(U.shape) for _ in range(3)], [np.zeros(U.shape) for _ in range(3)]
+    ro = o.solve_cfc(d, U, S, Si, psi, alpha, beta, X)
+    assert ro["status"] == "ok"
+    got = [t.cpu().numpy() for t in outs[0]]
+    for a, b in zip(got[:2], [psi, alpha]):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+    for lo_, hi_ in ((2, 5), (5, 8)):
+        want = (beta if lo_ == 2 else X)
+        scale = max(np.abs(w).max() for w in want)
+        assert max(np.abs(a - b).max() for a, b in zip(got[lo_:hi_], want)) <= 1e-9 * scale
 
 
 def test_warm_start_of_a_stream(mg):
