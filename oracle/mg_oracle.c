@@ -1447,8 +1447,6 @@ void or_div_c(const or_desc* d, double* const B[3], double* div) {
  * of the class.  Each class is solved by the same multigrid (d's solver
  * settings, n/2 cells, spacing 2 h); rep->solve gets the largest cycle
  * count and residual over the classes and the worst status. */
-static int parity_of(int i, int j, int k) { return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2); }
-
 int or_clean_divb_exact(const or_desc* d, double* const B[3], double* phi, or_divb_report* rep) {
   if (d->geom != GEOM_CART) return 1;
   OGrid g;
@@ -1541,4 +1539,620 @@ int or_clean_divb_exact(const or_desc* d, double* const B[3], double* phi, or_di
   free(ps);
   free(div);
   return status;
+}
+
+/* ------------------------------------------ two-level composite grid (AMR) */
+
+/* A two-level composite grid: the base grid (the hierarchy of d) and one
+ * refined patch of ratio 2 over the box a <= I < b of base cells (the block
+ * tree of Sec. 2.8 on one device: a box of whole blocks).  The paper's
+ * multigrid on its block-AMR grids lives in the library it cites and is not
+ * printed; the readings used here (each listed in the design notes):
+ *   - composite cells: the patch's fine cells and the base cells it does not
+ *     cover ("uncovered");
+ *   - fine operator: the operator of Sec. 2.7.1 on the patch grid.  Patch
+ *     faces on the domain boundary take the boundary rules; faces inside
+ *     the domain take coarse-fine ghosts, quadratic in both directions:
+ *     the base solution interpolated to the ghost's tangential position
+ *     (second-order centred differences of the uncovered base cells around
+ *     the parent, offsets +-h/4 per tangential dimension, with the cross
+ *     term in 3D), then g = 8/15 u~ + 2/3 u_1 - 1/5 u_2 from it and the two
+ *     patch cells inward (the quadratic through the points at -3/2, -1/2
+ *     and +1 fine spacings from the interface, evaluated at +1/2);
+ *   - coarse operator on an uncovered cell next to the patch: the flux of
+ *     its face to the patch replaced by the sum of the fine fluxes through
+ *     that face (area x difference, in the pseudo-volume form of the printed
+ *     operators: V = 1 / r_i^2 sin(theta_j) / R_i x dx dy dz, areas from the
+ *     face radii and sines), so the composite operator is conservative;
+ *   - FAS across the two levels: restrict u and the residual of the patch
+ *     to the cells it covers (volume-weighted, Sec. 2.7.3), right-hand side
+ *     L_H(R u) + R r there and f + L_H(u) - L_comp(u) on uncovered cells,
+ *     one FAS V-cycle of the base hierarchy, the Kwak prolongation of the
+ *     base change onto the patch, smoothing of the patch before and after;
+ *   - stopping rule: the weighted relative residual over the composite
+ *     cells (w = r^2 sin(theta), R, 1 at each cell's own centre).
+ * Scalar equations (eq. psi, linear equations) only. */
+
+typedef struct {
+  OSolver s;       /* base hierarchy */
+  OGrid gp;        /* patch grid */
+  int a[3], b[3];  /* patch box in base cells */
+  OLevel P;        /* patch arrays (u, f, r, U, A2, c) */
+  double* f0;      /* original right-hand side of the base grid */
+  double* e;       /* scratch, base level 0 */
+} OComp;
+
+static int comp_covered(const OComp* C, int I, int J, int K) {
+  const OGrid* g = &C->s.lev[0].g;
+  if (I < C->a[0] || I >= C->b[0] || J < C->a[1] || J >= C->b[1]) return 0;
+  if (g->ndim == 3 && (K < C->a[2] || K >= C->b[2])) return 0;
+  return 1;
+}
+
+/* Pseudo volume of a cell and area of its face on side sd (+-1) along dim
+ * d, in the form the printed operators take when multiplied by the volume
+ * (dims absent in 2D drop out). */
+static double comp_volume(const OGrid* g, int i, int j) {
+  double v = g->h[0] * g->h[1] * (g->ndim == 3 ? g->h[2] : 1.0);
+  if (g->geom == GEOM_CYL) v *= xc(g, 0, i);
+  if (g->geom == GEOM_SPH) v *= xc(g, 0, i) * xc(g, 0, i) * sin(xc(g, 1, j));
+  return v;
+}
+static double comp_area(const OGrid* g, int d, int sd, int i, int j) {
+  const double h2 = g->ndim == 3 ? g->h[2] : 1.0;
+  if (g->geom == GEOM_CART) return g->h[0] * g->h[1] * h2 / g->h[d];
+  if (g->geom == GEOM_CYL) {
+    if (d == 0) return xf(g, 0, sd > 0 ? i + 1 : i) * g->h[1] * h2;
+    if (d == 1) return xc(g, 0, i) * g->h[0] * h2;
+    return g->h[0] * g->h[1] / xc(g, 0, i);
+  }
+  if (d == 0) {
+    const double rf = xf(g, 0, sd > 0 ? i + 1 : i);
+    return rf * rf * sin(xc(g, 1, j)) * g->h[1] * h2;
+  }
+  if (d == 1) return sin_face(g, sd > 0 ? j + 1 : j) * g->h[0] * h2;
+  return g->h[0] * g->h[1] / sin(xc(g, 1, j));
+}
+
+/* Base solution interpolated to the tangential position of a patch ghost:
+ * parent base cell P (its index along d is outside the patch), offsets
+ * dt = +-1/4 base spacing per tangential dimension (0 along d). */
+static double comp_tangential(const OComp* C, const double* uc, int d, const int P[3], const double dt[3]) {
+  const OGrid* g = &C->s.lev[0].g;
+  const int nd = g->ndim;
+  double v = uc[IX(g, P[0], P[1], P[2])];
+  int tt[2], nt = 0;
+  for (int t = 0; t < nd; ++t)
+    if (t != d) tt[nt++] = t;
+  for (int q = 0; q < nt; ++q) {
+    const int t = tt[q];
+    int Pp[3] = {P[0], P[1], P[2]}, Pm[3] = {P[0], P[1], P[2]};
+    Pp[t] += 1;
+    Pm[t] -= 1;
+    const double up = uc[IX(g, Pp[0], Pp[1], Pp[2])], um = uc[IX(g, Pm[0], Pm[1], Pm[2])];
+    v += dt[t] * 0.5 * (up - um) + 0.5 * dt[t] * dt[t] * (up - 2.0 * uc[IX(g, P[0], P[1], P[2])] + um);
+  }
+  if (nt == 2) {
+    const int t1 = tt[0], t2 = tt[1];
+    int q1[3], q2[3], q3[3], q4[3];
+    for (int x = 0; x < 3; ++x) q1[x] = q2[x] = q3[x] = q4[x] = P[x];
+    q1[t1] += 1; q1[t2] += 1;
+    q2[t1] += 1; q2[t2] -= 1;
+    q3[t1] -= 1; q3[t2] += 1;
+    q4[t1] -= 1; q4[t2] -= 1;
+    const double mix = 0.25 * (uc[IX(g, q1[0], q1[1], q1[2])] - uc[IX(g, q2[0], q2[1], q2[2])] -
+                               uc[IX(g, q3[0], q3[1], q3[2])] + uc[IX(g, q4[0], q4[1], q4[2])]);
+    v += dt[t1] * dt[t2] * mix;
+  }
+  return v;
+}
+
+/* Is face (d, side) of the patch a coarse-fine interface (else it lies on
+ * the domain boundary)? */
+static int comp_cf_face(const OComp* C, int d, int side) {
+  const OGrid* g = &C->s.lev[0].g;
+  return side < 0 ? C->a[d] > 0 : C->b[d] < g->n[d];
+}
+
+/* Fill the patch ghosts of up: boundary rules on faces on the domain
+ * boundary, coarse-fine ghosts from the base solution uc (ghosts filled)
+ * on the others. */
+static void comp_fill_patch(const OComp* C, double* up, const double* uc) {
+  const OGrid* gp = &C->gp;
+  const int nd = gp->ndim;
+  fill_ghosts(gp, up, C->s.bc, -1);
+  for (int d = 0; d < nd; ++d)
+    for (int side = -1; side <= 1; side += 2) {
+      if (!comp_cf_face(C, d, side)) continue;
+      const int n0 = gp->n[0], n1 = gp->n[1], n2 = gp->n[2];
+      for (int k = 0; k < n2; ++k)
+        for (int j = 0; j < n1; ++j)
+          for (int i = 0; i < n0; ++i) {
+            const int idx[3] = {i, j, k};
+            const int edge = side < 0 ? 0 : gp->n[d] - 1;
+            if (idx[d] != edge) continue;
+            int g3[3] = {i, j, k}, u1[3] = {i, j, k}, u2[3] = {i, j, k}, P[3];
+            g3[d] = side < 0 ? -1 : gp->n[d];
+            u2[d] = side < 0 ? 1 : gp->n[d] - 2;
+            double dt[3] = {0.0, 0.0, 0.0};
+            for (int t = 0; t < 3; ++t) {
+              if (t >= nd) {
+                P[t] = 0;
+                continue;
+              }
+              if (t == d) {
+                P[t] = side < 0 ? C->a[d] - 1 : C->b[d];
+              } else {
+                P[t] = C->a[t] + idx[t] / 2;
+                dt[t] = (idx[t] % 2 == 0) ? -0.25 : 0.25;
+              }
+            }
+            const double ut = comp_tangential(C, uc, d, P, dt);
+            up[IX(gp, g3[0], g3[1], g3[2])] = (8.0 / 15.0) * ut + (2.0 / 3.0) * up[IX(gp, u1[0], u1[1], u1[2])] -
+                                             (1.0 / 5.0) * up[IX(gp, u2[0], u2[1], u2[2])];
+          }
+    }
+}
+
+/* The composite operator minus the base operator on the uncovered base
+ * cells next to the patch (the fine fluxes through their face to the patch
+ * in place of the coarse one), added into corr (base ghosted layout); the
+ * patch ghosts of up must be current. */
+static void comp_flux_correction(const OComp* C, const double* up, const double* uc, double* corr) {
+  const OGrid* g = &C->s.lev[0].g;
+  const OGrid* gp = &C->gp;
+  const int nd = g->ndim;
+  memset(corr, 0, sizeof(double) * g->size);
+  for (int d = 0; d < nd; ++d)
+    for (int side = -1; side <= 1; side += 2) {
+      if (!comp_cf_face(C, d, side)) continue;
+      /* coarse cells just outside this face of the patch: the box's range
+       * in the tangential dimensions, one index along d */
+      int rlo[3], rhi[3];
+      for (int t = 0; t < 3; ++t) {
+        rlo[t] = (t < nd && t != d) ? C->a[t] : 0;
+        rhi[t] = (t < nd && t != d) ? C->b[t] : 1;
+      }
+      for (int K = rlo[2]; K < rhi[2]; ++K)
+        for (int J = rlo[1]; J < rhi[1]; ++J)
+          for (int I = rlo[0]; I < rhi[0]; ++I) {
+            int Q[3] = {I, J, K};
+            Q[d] = side < 0 ? C->a[d] - 1 : C->b[d];   /* the uncovered cell */
+            int Qin[3] = {Q[0], Q[1], Q[2]};
+            Qin[d] = side < 0 ? C->a[d] : C->b[d] - 1;   /* its covered neighbour */
+            /* the coarse flux out of Q through this face (toward the patch) */
+            const int sd = side < 0 ? 1 : -1;             /* the face is on Q's side sd */
+            const double Ac = comp_area(g, d, sd, Q[0], Q[1]);
+            const double Dc = (uc[IX(g, Qin[0], Qin[1], Qin[2])] - uc[IX(g, Q[0], Q[1], Q[2])]) / g->h[d];
+            /* the fine fluxes through the same face */
+            double fsum = 0.0;
+            const int nf1 = nd == 3 ? 2 : 1;
+            for (int q2 = 0; q2 < nf1; ++q2)
+              for (int q1 = 0; q1 < 2; ++q1) {
+                int f[3];
+                int tq = 0;
+                for (int t = 0; t < 3; ++t) {
+                  if (t >= nd) {
+                    f[t] = 0;
+                  } else if (t == d) {
+                    f[t] = side < 0 ? 0 : gp->n[d] - 1;
+                  } else {
+                    f[t] = 2 * (Q[t] - C->a[t]) + (tq == 0 ? q1 : q2);
+                    ++tq;
+                  }
+                }
+                int gg[3] = {f[0], f[1], f[2]};
+                gg[d] = side < 0 ? -1 : gp->n[d];
+                const double Af = comp_area(gp, d, side, f[0], f[1]);
+                const double Df = (up[IX(gp, f[0], f[1], f[2])] - up[IX(gp, gg[0], gg[1], gg[2])]) / gp->h[d];
+                fsum += Af * Df;
+              }
+            corr[IX(g, Q[0], Q[1], Q[2])] += (fsum - Ac * Dc) / comp_volume(g, Q[0], Q[1]);
+          }
+    }
+}
+
+/* One red-black Newton-Gauss-Seidel sweep of the patch (eq. ngs_iteration),
+ * the patch ghosts refilled from the current patch and base values before
+ * each colour (the Newton diagonal holds them fixed). */
+static void comp_patch_sweep(OComp* C) {
+  const OGrid* gp = &C->gp;
+  const double* uc = C->s.lev[0].u[0];
+  for (int colour = 0; colour < 2; ++colour) {
+    comp_fill_patch(C, C->P.u[0], uc);
+    for (int k = 0; k < gp->n[2]; ++k)
+      for (int j = 0; j < gp->n[1]; ++j)
+        for (int i = 0; i < gp->n[0]; ++i) {
+          if (((i + j + k) & 1) != colour) continue;
+          double diag;
+          const double Lu = op_at(&C->s, &C->P, 0, i, j, k, &diag);
+          const long p = IX(gp, i, j, k);
+          C->P.u[0][p] = C->P.u[0][p] - (Lu - C->P.f[0][p]) / diag;
+        }
+  }
+}
+
+/* Source S(u) of the equation at a cell (the right-hand side as the paper
+ * writes it), with the original right-hand side f. */
+static double comp_source(const OComp* C, const OLevel* L, long p, double f) {
+  if (C->s.kind == EQ_PSI) {
+    const double psi = 1.0 + L->u[0][p];
+    return -2.0 * OR_PI * L->U[p] / psi - 0.125 * L->A2[p] / pow(psi, 7);
+  }
+  return (L->c ? L->c[p] * L->u[0][p] : 0.0) + f;
+}
+
+/* Base ghosts, patch ghosts and the flux correction at the current state
+ * (into C->e). */
+static void comp_refresh(OComp* C) {
+  OLevel* B = &C->s.lev[0];
+  fill_ghosts(&B->g, B->u[0], C->s.bc, -1);
+  comp_fill_patch(C, C->P.u[0], B->u[0]);
+  comp_flux_correction(C, C->P.u[0], B->u[0], C->e);
+}
+
+/* Relative weighted residual over the composite cells (stopping rule). */
+static double comp_rel(OComp* C) {
+  OLevel* B = &C->s.lev[0];
+  const OGrid* g = &B->g;
+  const OGrid* gp = &C->gp;
+  comp_refresh(C);
+  double num = 0.0, den = 0.0;
+  for (int k = 0; k < gp->n[2]; ++k)
+    for (int j = 0; j < gp->n[1]; ++j)
+      for (int i = 0; i < gp->n[0]; ++i) {
+        const long p = IX(gp, i, j, k);
+        const double w = norm_weight(gp, i, j);
+        const double r = C->P.f[0][p] - op_at(&C->s, &C->P, 0, i, j, k, NULL);
+        const double S = comp_source(C, &C->P, p, C->P.f[0][p]);
+        if (r != r || S != S) return NAN;
+        if (fabs(w * r) > num) num = fabs(w * r);
+        if (fabs(w * S) > den) den = fabs(w * S);
+      }
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i) {
+        if (comp_covered(C, i, j, k)) continue;
+        const long p = IX(g, i, j, k);
+        const double w = norm_weight(g, i, j);
+        const double r = C->f0[p] - op_at(&C->s, B, 0, i, j, k, NULL) - C->e[p];
+        const double S = comp_source(C, B, p, C->f0[p]);
+        if (r != r || S != S) return NAN;
+        if (fabs(w * r) > num) num = fabs(w * r);
+        if (fabs(w * S) > den) den = fabs(w * S);
+      }
+  return num / (den > 1e-300 ? den : 1e-300);
+}
+
+/* One composite FAS V(nu1, nu2) cycle (the readings above). */
+static void comp_cycle(OComp* C) {
+  OSolver* s = &C->s;
+  OLevel* B = &s->lev[0];
+  const OGrid* g = &B->g;
+  const OGrid* gp = &C->gp;
+  const int three = g->ndim == 3;
+  for (int it = 0; it < s->nu1; ++it) comp_patch_sweep(C);
+  /* patch residual */
+  comp_fill_patch(C, C->P.u[0], B->u[0]);
+  for (int k = 0; k < gp->n[2]; ++k)
+    for (int j = 0; j < gp->n[1]; ++j)
+      for (int i = 0; i < gp->n[0]; ++i) {
+        const long p = IX(gp, i, j, k);
+        C->P.r[0][p] = C->P.f[0][p] - op_at(s, &C->P, 0, i, j, k, NULL);
+      }
+  /* restriction to the covered cells (volume-weighted children); R r kept
+   * in the base residual array */
+  for (int K = 0; K < g->n[2]; ++K)
+    for (int J = 0; J < g->n[1]; ++J)
+      for (int I = 0; I < g->n[0]; ++I) {
+        if (!comp_covered(C, I, J, K)) continue;
+        double su = 0.0, sr = 0.0, vol = 0.0;
+        for (int dk = 0; dk <= three; ++dk)
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+              const int fi = 2 * (I - C->a[0]) + di, fj = 2 * (J - C->a[1]) + dj;
+              const int fk = three ? 2 * (K - C->a[2]) + dk : 0;
+              const double v = cell_volume(gp, fi, fj);
+              su += v * C->P.u[0][IX(gp, fi, fj, fk)];
+              sr += v * C->P.r[0][IX(gp, fi, fj, fk)];
+              vol += v;
+            }
+        B->u[0][IX(g, I, J, K)] = su / vol;
+        B->r[0][IX(g, I, J, K)] = sr / vol;
+      }
+  memcpy(B->uh[0], B->u[0], sizeof(double) * g->size);
+  /* FAS right-hand side of the base level */
+  comp_refresh(C);
+  for (int K = 0; K < g->n[2]; ++K)
+    for (int J = 0; J < g->n[1]; ++J)
+      for (int I = 0; I < g->n[0]; ++I) {
+        const long p = IX(g, I, J, K);
+        if (comp_covered(C, I, J, K))
+          B->f[0][p] = op_at(s, B, 0, I, J, K, NULL) + B->r[0][p];
+        else
+          B->f[0][p] = C->f0[p] - C->e[p];
+      }
+  /* one FAS V-cycle of the base hierarchy */
+  vcycle(s, s, 0);
+  /* the base change onto the patch (Kwak), homogeneous ghosts */
+  for (long p = 0; p < g->size; ++p) C->e[p] = B->u[0][p] - B->uh[0][p];
+  fill_ghosts(g, C->e, s->bc, -1);
+  for (int k = 0; k < gp->n[2]; ++k)
+    for (int j = 0; j < gp->n[1]; ++j)
+      for (int i = 0; i < gp->n[0]; ++i) {
+        const int I = C->a[0] + i / 2, J = C->a[1] + j / 2, K = three ? C->a[2] + k / 2 : 0;
+        const int si = (i % 2 == 0) ? -1 : 1, sj = (j % 2 == 0) ? -1 : 1, sk = (k % 2 == 0) ? -1 : 1;
+        const double ec = C->e[IX(g, I, J, K)];
+        const double ex = C->e[IX(g, I + si, J, K)], ey = C->e[IX(g, I, J + sj, K)];
+        double add;
+        if (three)
+          add = 0.25 * (ec + ex + ey + C->e[IX(g, I, J, K + sk)]);
+        else
+          add = 0.25 * (2.0 * ec + ex + ey);
+        C->P.u[0][IX(gp, i, j, k)] += add;
+      }
+  for (int it = 0; it < s->nu2; ++it) comp_patch_sweep(C);
+}
+
+/* Composite unknowns (patch cells, then uncovered base cells) <-> a flat
+ * vector. */
+static long comp_nv(const OComp* C) {
+  const OGrid* g = &C->s.lev[0].g;
+  long n = (long)C->gp.n[0] * C->gp.n[1] * C->gp.n[2];
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i) n += !comp_covered(C, i, j, k);
+  return n;
+}
+static void comp_gather(const OComp* C, double* x) {
+  const OGrid* g = &C->s.lev[0].g;
+  const OGrid* gp = &C->gp;
+  long q = 0;
+  for (int k = 0; k < gp->n[2]; ++k)
+    for (int j = 0; j < gp->n[1]; ++j)
+      for (int i = 0; i < gp->n[0]; ++i) x[q++] = C->P.u[0][IX(gp, i, j, k)];
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i)
+        if (!comp_covered(C, i, j, k)) x[q++] = C->s.lev[0].u[0][IX(g, i, j, k)];
+}
+static void comp_scatter(OComp* C, const double* x) {
+  const OGrid* g = &C->s.lev[0].g;
+  const OGrid* gp = &C->gp;
+  long q = 0;
+  for (int k = 0; k < gp->n[2]; ++k)
+    for (int j = 0; j < gp->n[1]; ++j)
+      for (int i = 0; i < gp->n[0]; ++i) C->P.u[0][IX(gp, i, j, k)] = x[q++];
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i)
+        if (!comp_covered(C, i, j, k)) C->s.lev[0].u[0][IX(g, i, j, k)] = x[q++];
+}
+
+/* Cycle control of the composite iteration: the rule of run_cycles (tol,
+ * max_cycles, stall window, non-finite values, optional Anderson mixing of
+ * depth accel over the composite unknowns). */
+static int comp_run_cycles(OComp* C, or_report* rep) {
+  OSolver* s = &C->s;
+  double rel = comp_rel(C);
+  int cyc = 0, status = 0;
+  double hist[OR_HIST];
+  int nh = 0;
+  hist[nh++] = rel;
+  const int m = s->accel < 0 ? 0 : (s->accel > 32 ? 32 : s->accel);
+  const long nv = comp_nv(C);
+  double *x = NULL, *g = NULL, *fcur = NULL, *fprev = NULL, *gprev = NULL, *dF = NULL, *dG = NULL;
+  int ncol = 0, head = 0;
+  if (m > 0) {
+    x = malloc(sizeof(double) * nv);
+    g = malloc(sizeof(double) * nv);
+    fcur = malloc(sizeof(double) * nv);
+    fprev = malloc(sizeof(double) * nv);
+    gprev = malloc(sizeof(double) * nv);
+    dF = malloc(sizeof(double) * nv * m);
+    dG = malloc(sizeof(double) * nv * m);
+  }
+  while (1) {
+    if (rel != rel) { status = 5; break; }
+    if (rel <= s->tol) break;
+    if (cyc >= s->max_cycles) { status = 3; break; }
+    if (s->stall_window > 0 && cyc >= s->stall_window && rel > 0.95 * hist[cyc - s->stall_window]) {
+      status = 4;
+      break;
+    }
+    if (m == 0) {
+      comp_cycle(C);
+    } else {
+      comp_gather(C, x);
+      comp_cycle(C);
+      comp_gather(C, g);
+      for (long q = 0; q < nv; ++q) fcur[q] = g[q] - x[q];
+      if (cyc > 0) {
+        double* cf = dF + (long)head * nv;
+        double* cg = dG + (long)head * nv;
+        for (long q = 0; q < nv; ++q) {
+          cf[q] = fcur[q] - fprev[q];
+          cg[q] = g[q] - gprev[q];
+        }
+        head = (head + 1) % m;
+        if (ncol < m) ++ncol;
+      }
+      memcpy(fprev, fcur, sizeof(double) * nv);
+      memcpy(gprev, g, sizeof(double) * nv);
+      if (ncol > 0) {
+        double M[32 * 32], b[32], gam[32];
+        int col[32];
+        for (int a = 0; a < ncol; ++a) col[a] = (head - ncol + a + m) % m;
+        for (int a = 0; a < ncol; ++a) {
+          const double* fa = dF + (long)col[a] * nv;
+          double sb = 0.0;
+          for (long q = 0; q < nv; ++q) sb += fa[q] * fcur[q];
+          b[a] = sb;
+          for (int c2 = 0; c2 <= a; ++c2) {
+            const double* fc = dF + (long)col[c2] * nv;
+            double sm = 0.0;
+            for (long q = 0; q < nv; ++q) sm += fa[q] * fc[q];
+            M[a * ncol + c2] = sm;
+            M[c2 * ncol + a] = sm;
+          }
+        }
+        if (small_spd_solve(ncol, M, b, gam) == 0) {
+          for (int a = 0; a < ncol; ++a) {
+            const double* ga = dG + (long)col[a] * nv;
+            for (long q = 0; q < nv; ++q) g[q] -= gam[a] * ga[q];
+          }
+        } else {
+          ncol = 0;
+        }
+      }
+      comp_scatter(C, g);
+    }
+    ++cyc;
+    rel = comp_rel(C);
+    if (nh < OR_HIST) hist[nh++] = rel;
+  }
+  free(x);
+  free(g);
+  free(fcur);
+  free(fprev);
+  free(gprev);
+  free(dF);
+  free(dG);
+  if (rep) {
+    rep->status = status;
+    rep->cycles = cyc;
+    rep->rel = rel;
+    rep->nhist = nh;
+    memcpy(rep->hist, hist, sizeof(double) * nh);
+  }
+  return status;
+}
+
+/* Set up a composite grid: the base hierarchy of d, the patch over base
+ * cells a <= I < b.  Returns 0, or 1 if the box is not inside the grid, is
+ * empty, or does not span the whole angular range where a rule across the
+ * origin or axis needs it (spherical: theta and phi; cylindrical: phi). */
+static int comp_setup(OComp* C, const or_desc* d, const int a[3], const int b[3], int kind, int bc) {
+  memset(C, 0, sizeof(*C));
+  const int nd = d->ndim;
+  for (int t = 0; t < 3; ++t) {
+    C->a[t] = t < nd ? a[t] : 0;
+    C->b[t] = t < nd ? b[t] : 1;
+    if (t < nd && !(0 <= a[t] && a[t] < b[t] && b[t] <= d->n[t])) return 1;
+  }
+  if (d->geom == GEOM_SPH && (C->a[1] != 0 || C->b[1] != d->n[1])) return 1;
+  if (d->geom != GEOM_CART && nd == 3 && (C->a[2] != 0 || C->b[2] != d->n[2])) return 1;
+  setup(&C->s, d, kind, bc, 1);
+  const OGrid* g = &C->s.lev[0].g;
+  int np[3];
+  double lop[3], hp[3];
+  for (int t = 0; t < 3; ++t) {
+    np[t] = t < nd ? 2 * (C->b[t] - C->a[t]) : 1;
+    lop[t] = t < nd ? g->lo[t] + C->a[t] * g->h[t] : g->lo[t];
+    hp[t] = t < nd ? 0.5 * g->h[t] : g->h[t];
+  }
+  grid_init(&C->gp, nd, d->geom, np, lop, hp);
+  const long sz = C->gp.size;
+  C->P.g = C->gp;
+  C->P.u[0] = calloc(sz, sizeof(double));
+  C->P.f[0] = calloc(sz, sizeof(double));
+  C->P.r[0] = calloc(sz, sizeof(double));
+  C->P.U = calloc(sz, sizeof(double));
+  C->P.A2 = calloc(sz, sizeof(double));
+  C->P.c = calloc(sz, sizeof(double));
+  C->f0 = calloc(g->size, sizeof(double));
+  C->e = calloc(g->size, sizeof(double));
+  return 0;
+}
+
+static void comp_free(OComp* C) {
+  free(C->P.u[0]);
+  free(C->P.f[0]);
+  free(C->P.r[0]);
+  free(C->P.U);
+  free(C->P.A2);
+  free(C->P.c);
+  free(C->f0);
+  free(C->e);
+  free_levels(&C->s);
+}
+
+static void comp_load(OComp* C, const double* U, const double* A2, const double* c, const double* f,
+                      const double* Up, const double* A2p, const double* cp, const double* fp, const double* u,
+                      const double* up) {
+  OLevel* B = &C->s.lev[0];
+  if (U) load_interior(&B->g, B->U, U);
+  if (A2) load_interior(&B->g, B->A2, A2);
+  if (c) load_interior(&B->g, B->c, c);
+  if (f) load_interior(&B->g, C->f0, f);
+  load_interior(&B->g, B->u[0], u);
+  if (Up) load_interior(&C->gp, C->P.U, Up);
+  if (A2p) load_interior(&C->gp, C->P.A2, A2p);
+  if (cp) load_interior(&C->gp, C->P.c, cp);
+  if (fp) load_interior(&C->gp, C->P.f[0], fp);
+  load_interior(&C->gp, C->P.u[0], up);
+  restrict_sources(&C->s);
+}
+
+/* Composite solve of a scalar equation (kind EQ_PSI with U, A2; EQ_LIN with
+ * c (nullable) and f) on the base grid of d and the patch a <= I < b.
+ * Base-grid and patch arrays are interior layout (the patch has 2 (b - a)
+ * cells per dimension); u and up: initial guess in, solution out (covered
+ * base cells receive the restriction of the patch). */
+int or_solve_scalar_amr(const or_desc* d, const int a[3], const int b[3], int kind, int bc, const double* U,
+                        const double* A2, const double* c, const double* f, const double* Up, const double* A2p,
+                        const double* cp, const double* fp, double* u, double* up, or_report* rep) {
+  OComp C;
+  if (comp_setup(&C, d, a, b, kind, bc)) return 1;
+  comp_load(&C, U, A2, c, f, Up, A2p, cp, fp, u, up);
+  const int st = comp_run_cycles(&C, rep);
+  OLevel* B = &C.s.lev[0];
+  const OGrid* g = &B->g;
+  const int three = g->ndim == 3;
+  /* covered base cells: the volume-weighted restriction of the patch */
+  for (int K = 0; K < g->n[2]; ++K)
+    for (int J = 0; J < g->n[1]; ++J)
+      for (int I = 0; I < g->n[0]; ++I) {
+        if (!comp_covered(&C, I, J, K)) continue;
+        double su = 0.0, vol = 0.0;
+        for (int dk = 0; dk <= three; ++dk)
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+              const int fi = 2 * (I - C.a[0]) + di, fj = 2 * (J - C.a[1]) + dj;
+              const int fk = three ? 2 * (K - C.a[2]) + dk : 0;
+              const double v = cell_volume(&C.gp, fi, fj);
+              su += v * C.P.u[0][IX(&C.gp, fi, fj, fk)];
+              vol += v;
+            }
+        B->u[0][IX(g, I, J, K)] = su / vol;
+      }
+  store_interior(g, u, B->u[0]);
+  store_interior(&C.gp, up, C.P.u[0]);
+  comp_free(&C);
+  return st;
+}
+
+/* The composite operator applied to (u, up) (interior layout, sources as in
+ * or_solve_scalar_amr): out on the uncovered base cells (0 on covered ones),
+ * outp on the patch cells. */
+int or_apply_amr(const or_desc* d, const int a[3], const int b[3], int kind, int bc, const double* U,
+                 const double* A2, const double* c, const double* Up, const double* A2p, const double* cp,
+                 const double* u, const double* up, double* out, double* outp) {
+  OComp C;
+  if (comp_setup(&C, d, a, b, kind, bc)) return 1;
+  comp_load(&C, U, A2, c, NULL, Up, A2p, cp, NULL, u, up);
+  comp_refresh(&C);
+  OLevel* B = &C.s.lev[0];
+  const OGrid* g = &B->g;
+  long q = 0;
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i, ++q)
+        out[q] = comp_covered(&C, i, j, k) ? 0.0 : op_at(&C.s, B, 0, i, j, k, NULL) + C.e[IX(g, i, j, k)];
+  q = 0;
+  for (int k = 0; k < C.gp.n[2]; ++k)
+    for (int j = 0; j < C.gp.n[1]; ++j)
+      for (int i = 0; i < C.gp.n[0]; ++i, ++q) outp[q] = op_at(&C.s, &C.P, 0, i, j, k, NULL);
+  comp_free(&C);
+  return 0;
 }

@@ -95,6 +95,10 @@ def lib():
             _lib.or_solve_cfc.argtypes = [D, P, P, P, P, P, P, P, C.POINTER(CfcReport)]
             _lib.or_clean_divb.argtypes = [D, P, P, C.POINTER(DivbReport)]
             _lib.or_clean_divb_exact.argtypes = [D, P, P, C.POINTER(DivbReport)]
+            I3 = C.c_int * 3
+            _lib.or_solve_scalar_amr.argtypes = [D, I3, I3, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P,
+                                                 C.POINTER(Report)]
+            _lib.or_apply_amr.argtypes = [D, I3, I3, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P]
             _lib.or_div_c.argtypes = [D, P, P]
             _lib.or_beta_rhs.argtypes = [D, P, P, P, P, P]
         return _lib
@@ -243,3 +247,36 @@ def beta_rhs(d, X, psi, alpha, Si):
     f = [np.zeros(shape(d)) for _ in range(3)]
     lib().or_beta_rhs(C.byref(d), _parr(X), _p(psi), _p(alpha), _parr(Si), _parr(f))
     return f
+
+
+def patch_shape(d, a, b):
+    """numpy shape of the refined patch over base cells a <= I < b."""
+    return tuple(reversed([2 * (b[k] - a[k]) for k in range(d.ndim)]))
+
+
+def _box(v, nd):
+    return (C.c_int * 3)(*([int(x) for x in v] + [0] * (3 - nd)))
+
+
+def solve_scalar_amr(d, a, b, kind, bc, u, up, U=None, A2=None, c=None, f=None, Up=None, A2p=None, cp=None,
+                     fp=None):
+    """Two-level composite-grid solve (base grid of d, refined patch over
+    base cells a <= I < b); u (base) and up (patch) updated in place."""
+    r = Report()
+    st = lib().or_solve_scalar_amr(C.byref(d), _box(a, d.ndim), _box(b, d.ndim), EQ[kind], BC[bc], _p(U), _p(A2),
+                                   _p(c), _p(f), _p(Up), _p(A2p), _p(cp), _p(fp), _p(u), _p(up), C.byref(r))
+    if st == 1 and r.cycles == 0 and r.nhist == 0:
+        raise ValueError("patch box rejected")
+    return r.as_dict()
+
+
+def apply_amr(d, a, b, kind, bc, u, up, U=None, A2=None, c=None, Up=None, A2p=None, cp=None):
+    """The composite operator on (u, up): (out on uncovered base cells, 0 on
+    covered ones; out on the patch)."""
+    out = np.zeros(shape(d))
+    outp = np.zeros(patch_shape(d, a, b))
+    st = lib().or_apply_amr(C.byref(d), _box(a, d.ndim), _box(b, d.ndim), EQ[kind], BC[bc], _p(U), _p(A2), _p(c),
+                            _p(Up), _p(A2p), _p(cp), _p(u), _p(up), _p(out), _p(outp))
+    if st:
+        raise ValueError("patch box rejected")
+    return out, outp
