@@ -264,6 +264,54 @@ int mg_solve_scalar(mg_hierarchy* h, int kind, int bc, int zero_mean, const doub
  * (MG_BC_DIRICHLET for X and beta). */
 int mg_solve_vector(mg_hierarchy* h, int bc, const double* f[3], double* V[3], mg_solve_report* rep);
 
+/* ------------------------------------- two-level composite grid (AMR) */
+
+/*
+ * Solve one scalar equation (kind MG_EQ_PSI or MG_EQ_LIN, as in
+ * mg_solve_scalar) on a two-level composite grid: the hierarchy's grid (the
+ * base) and one refined patch of ratio 2 over the base cells box_lo[d] <=
+ * I_d < box_hi[d] (the block tree of Sec. 2.8 on one device: a box of whole
+ * blocks).  The patch has 2 (box_hi - box_lo) cells per dimension, each a
+ * power of two; a spherical patch spans theta (and phi in 3D), a
+ * cylindrical 3D patch spans phi.  The paper's multigrid on AMR grids lives
+ * in the library it cites; this one takes the following readings:
+ *   - the composite cells are the patch cells and the base cells the patch
+ *     does not cover;
+ *   - patch faces on the domain boundary take its rules; the others take
+ *     coarse-fine ghosts, quadratic in both directions (the base solution
+ *     interpolated to the ghost's tangential position from the uncovered
+ *     base cells around its parent, then g = 8/15 u~ + 2/3 u_1 - 1/5 u_2
+ *     with the two patch cells inward);
+ *   - an uncovered base cell next to the patch takes, for its face to the
+ *     patch, the sum of the fine fluxes through that face: the composite
+ *     operator is conservative;
+ *   - FAS across the two levels: patch smoothing (red-black NGS, ghosts
+ *     refilled per colour), the patch residual and solution restricted
+ *     (volume-weighted) to the covered cells, one FAS V-cycle of the base
+ *     hierarchy, the Kwak prolongation of the base change onto the patch,
+ *     patch smoothing; FP64 throughout whatever desc.precision says;
+ *   - stopping rule: rel over the composite cells (see mg_solve_report),
+ *     Anderson mixing (accel_depth) over the composite unknowns; V-cycles
+ *     only (desc.cycle ignored).
+ * Base-grid arrays (U, A2 or c, f, u) have the hierarchy's size; patch
+ * arrays (Up, A2p or cp, fp, up) the patch's, both ghost-free, dimension 0
+ * fastest, device pointers.  Sources are given on both levels (sampled at
+ * each level's cell centres).  u, up: initial guess in, solution out; on
+ * return the covered base cells hold the restriction of the patch.  The
+ * patch arrays of the hierarchy are allocated at the first call with a box
+ * and kept while the box is the same.
+ */
+int mg_solve_scalar_amr(mg_hierarchy* h, const int box_lo[3], const int box_hi[3], int kind, int bc,
+                        const double* U, const double* A2, const double* c, const double* f, const double* Up,
+                        const double* A2p, const double* cp, const double* fp, double* u, double* up,
+                        mg_solve_report* rep);
+
+/* The composite operator of mg_solve_scalar_amr applied to (u, up): out on
+ * the uncovered base cells (0 on covered ones), outp on the patch. */
+int mg_apply_amr(mg_hierarchy* h, const int box_lo[3], const int box_hi[3], int kind, int bc, const double* U,
+                 const double* A2, const double* c, const double* Up, const double* A2p, const double* cp,
+                 const double* u, const double* up, double* out, double* outp);
+
 /* ----------------------------------------------- unit-level (testing) */
 
 /*

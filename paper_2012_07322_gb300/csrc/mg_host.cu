@@ -93,6 +93,23 @@ struct mg_hierarchy {
   // MG_DIVB_EXACT: the hierarchy of the parity-class problems (n / 2 cells
   // per dimension), on this hierarchy's stream
   mg_hierarchy* sub = nullptr;
+  // composite grid (mg_solve_scalar_amr): the refined patch of the last box
+  // used, allocated on first use
+  struct Amr {
+    AmrBox box{};
+    bool valid = false;
+    int n[3] = {1, 1, 1};
+    long sx = 0, sy = 0, off = 0, ng = 0;
+    LevelView<double> v{};
+    double *ti = nullptr, *tj = nullptr;
+    double *u = nullptr, *f = nullptr, *r = nullptr, *s0 = nullptr, *s1 = nullptr;
+    int* bmap = nullptr;     // ghosted offsets of the uncovered base cells
+    long nbase = 0, nvec = 0;
+    LevelView<double> flat{};  // the composite unknowns as one row (Anderson mixing)
+    double* aa = nullptr;    // g, x, fprev, gprev, then 2 m history columns of flat.n0 doubles
+    int aa_m = 0;
+    char* mem = nullptr;
+  } amr;
   bool prof_on = false;
   bool fold_k32 = false;  // while capturing a V-cycle of eq. psi: K is restricted on the way down
   std::vector<cudaEvent_t> ev;
@@ -134,6 +151,7 @@ void prof_end(mg_hierarchy* H, long tok) {
 struct Eq {
   int kind, bc, zero_mean, ncomp;
   bool has_c;    // EQ_LIN with a coefficient array
+  bool amr = false;  // composite-grid solve: the finest base level carries an FAS right-hand side
 };
 
 int fail(int status, const char* what) {
@@ -482,7 +500,7 @@ GhostPush ghost_push(const mg_hierarchy* H, int l, int c, int colour, int bc) {
 // ------------------------------------------------------------- FP64 FAS
 
 const double* fptr(const mg_hierarchy* H, const Eq& e, int l, int c) {
-  if (l == 0 && e.kind == EQ_PSI) return nullptr;  // finest right-hand side is zero
+  if (l == 0 && e.kind == EQ_PSI && !e.amr) return nullptr;  // finest right-hand side is zero
   return H->L[l].f[c];
 }
 const double* s0ptr(const mg_hierarchy* H, const Eq& e, int l) {
@@ -1286,6 +1304,333 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   return status;
 }
 
+// ------------------------------------------------- composite grid (AMR)
+
+// The box of a refined patch over base cells a <= I < b, with its
+// coarse-fine faces; MG_ERR_INVALID unless it lies inside the grid, every
+// patch size 2 (b - a) is a power of two, and it spans the whole angular
+// range where a rule across the origin or axis needs it (spherical: theta
+// and phi; cylindrical 3D: phi).
+int amr_box(const mg_hierarchy* H, const int a[3], const int b[3], AmrBox* out) {
+  const mg_grid_desc& d = H->d;
+  AmrBox box{};
+  box.cf = 0;
+  for (int t = 0; t < 3; ++t) {
+    if (t >= d.ndim) {
+      box.a[t] = 0;
+      box.b[t] = 1;
+      continue;
+    }
+    if (!(0 <= a[t] && a[t] < b[t] && b[t] <= d.n[t])) return fail(MG_ERR_INVALID, "patch box outside the grid");
+    if (!pow2(2 * (b[t] - a[t]))) return fail(MG_ERR_INVALID, "patch sizes 2 (b - a) must be powers of two");
+    box.a[t] = a[t];
+    box.b[t] = b[t];
+    if (a[t] > 0) box.cf |= 1 << (2 * t);
+    if (b[t] < d.n[t]) box.cf |= 1 << (2 * t + 1);
+  }
+  if (d.geom == MG_SPH && (box.a[1] != 0 || box.b[1] != d.n[1]))
+    return fail(MG_ERR_INVALID, "a spherical patch must span theta");
+  if (d.geom != MG_CART && d.ndim == 3 && (box.a[2] != 0 || box.b[2] != d.n[2]))
+    return fail(MG_ERR_INVALID, "a curvilinear 3D patch must span phi");
+  *out = box;
+  return MG_OK;
+}
+
+// Patch level of a box (tables, arrays, the map of the uncovered base
+// cells), allocated on first use and kept while the box is the same.
+int ensure_amr(mg_hierarchy* H, const AmrBox& box) {
+  auto& A = H->amr;
+  if (A.valid && std::memcmp(A.box.a, box.a, sizeof(box.a)) == 0 && std::memcmp(A.box.b, box.b, sizeof(box.b)) == 0)
+    return MG_OK;
+  CK(cudaStreamSynchronize(H->st));
+  if (A.mem) cudaFree(A.mem);
+  if (A.aa) cudaFree(A.aa);
+  A = mg_hierarchy::Amr{};
+  const Level& B = H->L[0];
+  const int three = H->d.ndim == 3;
+  mg_grid_desc dp = H->d;
+  Level Lp;
+  for (int t = 0; t < 3; ++t) {
+    const bool act = t < H->d.ndim;
+    Lp.n[t] = act ? 2 * (box.b[t] - box.a[t]) : 1;
+    Lp.h[t] = act ? 0.5 * B.h[t] : B.h[t];
+    Lp.lo[t] = act ? B.lo[t] + box.a[t] * B.h[t] : B.lo[t];
+    dp.n[t] = Lp.n[t];
+    dp.lo[t] = Lp.lo[t];
+    dp.hi[t] = act ? B.lo[t] + box.b[t] * B.h[t] : H->d.hi[t];
+  }
+  Lp.sx = row_stride(Lp.n[0]);
+  Lp.sy = Lp.sx * (Lp.n[1] + 2);
+  Lp.off = ROW_PAD + Lp.sx + three * Lp.sy;
+  Lp.ng = Lp.sy * (Lp.n[2] + 2 * three);
+  std::vector<double> ti, tj;
+  make_tables(&dp, Lp, ti, tj);
+  // uncovered base cells, interior order
+  std::vector<int> bmap;
+  for (int k = 0; k < B.n[2]; ++k)
+    for (int j = 0; j < B.n[1]; ++j)
+      for (int i = 0; i < B.n[0]; ++i) {
+        const bool cov = i >= box.a[0] && i < box.b[0] && j >= box.a[1] && j < box.b[1] &&
+                         (!three || (k >= box.a[2] && k < box.b[2]));
+        if (!cov) bmap.push_back((int)(B.off + i + j * B.sx + (long)k * B.sy));
+      }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    const size_t at = off;
+    off += bytes;
+    return at;
+  };
+  const size_t o_ti = take(sizeof(double) * ti.size()), o_tj = take(sizeof(double) * tj.size());
+  size_t o_arr[5];
+  for (int q = 0; q < 5; ++q) o_arr[q] = take(sizeof(double) * Lp.ng);
+  const size_t o_map = take(sizeof(int) * std::max<size_t>(bmap.size(), 1));
+  if (cudaMalloc(&A.mem, off) != cudaSuccess) {
+    A.mem = nullptr;
+    return fail(MG_ERR_OOM, "patch allocation failed");
+  }
+  CK(cudaMemsetAsync(A.mem, 0, off, H->st));
+  A.ti = (double*)(A.mem + o_ti);
+  A.tj = (double*)(A.mem + o_tj);
+  double** arr[5] = {&A.u, &A.f, &A.r, &A.s0, &A.s1};
+  for (int q = 0; q < 5; ++q) *arr[q] = (double*)(A.mem + o_arr[q]);
+  A.bmap = (int*)(A.mem + o_map);
+  CK(cudaMemcpyAsync(A.ti, ti.data(), sizeof(double) * ti.size(), cudaMemcpyHostToDevice, H->st));
+  CK(cudaMemcpyAsync(A.tj, tj.data(), sizeof(double) * tj.size(), cudaMemcpyHostToDevice, H->st));
+  if (!bmap.empty())
+    CK(cudaMemcpyAsync(A.bmap, bmap.data(), sizeof(int) * bmap.size(), cudaMemcpyHostToDevice, H->st));
+  CK(cudaStreamSynchronize(H->st));  // host tables go out of scope
+  for (int t = 0; t < 3; ++t) A.n[t] = Lp.n[t];
+  A.sx = Lp.sx;
+  A.sy = Lp.sy;
+  A.off = Lp.off;
+  A.ng = Lp.ng;
+  A.v = make_view<double>(&dp, Lp, A.ti, A.tj);
+  A.box = box;
+  A.nbase = (long)bmap.size();
+  A.nvec = Lp.cells() + A.nbase;
+  long nf = 4;
+  int lg = 2;
+  while (nf < A.nvec) nf <<= 1, ++lg;
+  A.flat = LevelView<double>{};
+  A.flat.n0 = (int)nf;
+  A.flat.n1 = A.flat.n2 = 1;
+  A.flat.three = 0;
+  A.flat.sx = A.flat.sy = nf;
+  A.flat.off = 0;
+  A.flat.ln0 = lg;
+  A.flat.ln1 = 0;
+  A.valid = true;
+  return MG_OK;
+}
+
+// Anderson storage of the composite iteration: g, x, fprev, gprev and 2 m
+// history columns of flat.n0 doubles (zero beyond the composite unknowns).
+int ensure_amr_aa(mg_hierarchy* H, int m) {
+  auto& A = H->amr;
+  if (A.aa && A.aa_m >= m) return MG_OK;
+  if (A.aa) cudaFree(A.aa);
+  A.aa = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)A.flat.n0 * (4 + 2 * (size_t)m);
+  if (cudaMalloc(&A.aa, bytes) != cudaSuccess) {
+    A.aa = nullptr;
+    return fail(MG_ERR_OOM, "composite mixing storage allocation failed");
+  }
+  CK(cudaMemsetAsync(A.aa, 0, bytes, H->st));
+  A.aa_m = m;
+  if (!H->d_aa_part) {
+    if (cudaMalloc(&H->d_aa_part, sizeof(double) * AA_SCRATCH_DOUBLES) != cudaSuccess) {
+      H->d_aa_part = nullptr;
+      return fail(MG_ERR_OOM, "mixing scratch failed");
+    }
+    CK(cudaMemsetAsync(H->d_aa_part, 0, sizeof(double) * AA_SCRATCH_DOUBLES, H->st));
+  }
+  return MG_OK;
+}
+
+// Arrays of the composite iteration on the finest base level (scalar
+// equations leave components 1 and 2 free): the original right-hand side,
+// the flux correction, the restricted patch residual, the base state before
+// the base V-cycle and its change.
+struct AmrArrays {
+  double *f0, *corr, *rr, *uh, *eb;
+};
+AmrArrays amr_arrays(mg_hierarchy* H, const Eq& e) {
+  Level& L0 = H->L[0];
+  return AmrArrays{e.kind == EQ_LIN ? L0.f[1] : nullptr, L0.f[2], L0.r[1], L0.u[2], L0.r[2]};
+}
+
+// Base ghosts, patch ghosts (boundary rules, then the coarse-fine values)
+// and the flux correction of the uncovered interface cells.
+void amr_refresh(mg_hierarchy* H, const Eq& e, bool corr) {
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const auto vb = with_bc(L0.v64, e.bc);
+  const auto vp = with_bc(A.v, e.bc);
+  launch_fill_ghosts(vb, L0.u[0], -1, H->st);
+  launch_fill_ghosts(vp, A.u, -1, H->st);
+  launch_amr_cf_ghosts(vp, vb, A.box, A.u, L0.u[0], H->st);
+  if (corr) {
+    const AmrArrays W = amr_arrays(H, e);
+    cudaMemsetAsync(W.corr, 0, sizeof(double) * L0.ng, H->st);
+    launch_amr_flux_corr(vp, vb, A.box, A.u, L0.u[0], W.corr, H->st);
+  }
+}
+
+// Relative weighted residual over the composite cells (stopping rule).
+int amr_norm(mg_hierarchy* H, const Eq& e, double* rel) {
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const AmrArrays W = amr_arrays(H, e);
+  amr_refresh(H, e, true);
+  CK(cudaMemsetAsync(H->d_red, 0, sizeof(unsigned long long) * 3, H->st));
+  const double* s0p = e.kind == EQ_PSI ? A.s0 : nullptr;
+  const double* s1p = (e.kind == EQ_PSI || e.has_c) ? A.s1 : nullptr;
+  launch_amr_patch_resid(with_bc(A.v, e.bc), e.kind, A.u, A.f, s0p, s1p, nullptr, H->d_red, 0, H->st);
+  launch_amr_base(with_bc(L0.v64, e.bc), A.box, e.kind, L0.u[0], s0ptr(H, e, 0), s1ptr(H, e, 0), W.f0, nullptr,
+                  W.corr, nullptr, H->d_red, 1, H->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(H->h_red, H->d_red, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, H->st));
+  CK(cudaStreamSynchronize(H->st));
+  const double num = bits_to_double(H->h_red[1]), den = bits_to_double(H->h_red[2]);
+  if (std::isinf(num) || std::isinf(den) || std::isnan(num) || std::isnan(den))
+    *rel = NAN;
+  else
+    *rel = num / (den > 1e-300 ? den : 1e-300);
+  return MG_OK;
+}
+
+// Red-black Newton-Gauss-Seidel sweeps of the patch, its ghosts refilled
+// before each colour (the base ghosts are current).
+void amr_patch_sweeps(mg_hierarchy* H, const Eq& e, int nsweeps) {
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const auto vb = with_bc(L0.v64, e.bc);
+  const auto vp = with_bc(A.v, e.bc);
+  const double* s0p = e.kind == EQ_PSI ? A.s0 : nullptr;
+  const double* s1p = (e.kind == EQ_PSI || e.has_c) ? A.s1 : nullptr;
+  for (int sw = 0; sw < nsweeps; ++sw)
+    for (int colour = 0; colour < 2; ++colour) {
+      launch_fill_ghosts(vp, A.u, -1, H->st);
+      launch_amr_cf_ghosts(vp, vb, A.box, A.u, L0.u[0], H->st);
+      launch_amr_smooth(vp, e.kind, A.u, A.f, s0p, s1p, colour, H->st);
+    }
+  H->updates += (int64_t)nsweeps * (int64_t)A.n[0] * A.n[1] * A.n[2];
+}
+
+// One composite FAS V(nu1, nu2) cycle.
+void amr_cycle(mg_hierarchy* H, const Eq& e) {
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const auto vb = with_bc(L0.v64, e.bc);
+  const auto vp = with_bc(A.v, e.bc);
+  const AmrArrays W = amr_arrays(H, e);
+  const double* s0p = e.kind == EQ_PSI ? A.s0 : nullptr;
+  const double* s1p = (e.kind == EQ_PSI || e.has_c) ? A.s1 : nullptr;
+  launch_fill_ghosts(vb, L0.u[0], -1, H->st);
+  amr_patch_sweeps(H, e, H->d.nu1);
+  launch_fill_ghosts(vp, A.u, -1, H->st);
+  launch_amr_cf_ghosts(vp, vb, A.box, A.u, L0.u[0], H->st);
+  launch_amr_patch_resid(vp, e.kind, A.u, A.f, s0p, s1p, A.r, nullptr, 0, H->st);
+  launch_amr_restrict(vp, vb, A.box, A.u, A.r, L0.u[0], W.rr, H->st);
+  cudaMemcpyAsync(W.uh, L0.u[0], sizeof(double) * L0.ng, cudaMemcpyDeviceToDevice, H->st);
+  amr_refresh(H, e, true);
+  launch_amr_base(vb, A.box, e.kind, L0.u[0], s0ptr(H, e, 0), s1ptr(H, e, 0), W.f0, W.rr, W.corr, L0.f[0], nullptr,
+                  0, H->st);
+  vcycle64(H, e, 0);
+  launch_amr_diff(vb, L0.u[0], W.uh, W.eb, H->st);
+  launch_fill_ghosts(vb, W.eb, -1, H->st);  // the rules are linear: homogeneous for a change
+  launch_amr_prolong(vp, vb, A.box, W.eb, A.u, H->st);
+  launch_fill_ghosts(vb, L0.u[0], -1, H->st);
+  amr_patch_sweeps(H, e, H->d.nu2);
+}
+
+// Cycle control of the composite iteration, as run_solve: tol, max_cycles,
+// stall window, non-finite values, Anderson mixing of depth accel_depth
+// over the composite unknowns (FP64 columns).
+int run_solve_amr(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
+  auto t0 = std::chrono::steady_clock::now();
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const mg_grid_desc& d = H->d;
+  const int m = d.accel_depth;
+  H->updates = 0;
+  restrict_sources(H, e);
+  const long nfl = A.flat.n0;
+  double *ag = nullptr, *ax = nullptr, *afp = nullptr, *agp = nullptr, *adF = nullptr, *adG = nullptr;
+  if (m > 0) {
+    if (int st = ensure_amr_aa(H, m)) return st;
+    ag = A.aa;
+    ax = ag + nfl;
+    afp = ax + nfl;
+    agp = afp + nfl;
+    adF = agp + nfl;
+    adG = adF + (long)m * nfl;
+  }
+  auto flat = [&](double* x, int to_flat) {
+    launch_amr_flat(A.v, L0.v64, A.box, A.u, L0.u[0], A.bmap, A.nbase, x, to_flat, H->st);
+  };
+  std::vector<double> hist;
+  double rel;
+  int st = amr_norm(H, e, &rel);
+  if (st) return st;
+  hist.push_back(rel);
+  int cyc = 0, status = MG_OK, ncol = 0, head = 0;
+  for (;;) {
+    if (std::isnan(rel)) {
+      status = MG_ERR_NAN;
+      break;
+    }
+    if (rel <= d.tol) break;
+    if (cyc >= d.max_cycles) {
+      status = MG_ERR_NOCONV;
+      break;
+    }
+    if (d.stall_window > 0 && cyc >= d.stall_window && rel > 0.95 * hist[cyc - d.stall_window]) {
+      status = MG_ERR_STALLED;
+      break;
+    }
+    if (m > 0 && cyc == 0) flat(ax, 1);
+    amr_cycle(H, e);
+    bool mixed_step = false;
+    if (m > 0) {
+      flat(ag, 1);
+      AACols cols{};
+      if (cyc > 0) {
+        const int slot = head;
+        head = (head + 1) % m;
+        if (ncol < m) ++ncol;
+        cols.n = ncol;
+        for (int a = 0; a < ncol; ++a) cols.slot[a] = (slot - ncol + 1 + a + m) % m;
+      }
+      double* const g3[3] = {ag, ag, ag};
+      launch_aa_update_dots<double>(A.flat, 1, nfl, g3, ax, afp, agp, adF, adG, cols, H->d_aa_part, H->d_red + 3,
+                                    H->st);
+      if (cols.n > 0) {
+        launch_aa_combine<double>(A.flat, 1, nfl, g3, ax, adG, cols, H->d_aa_part, H->d_red + 3, H->st);
+        flat(ag, 0);
+        mixed_step = true;
+      }
+    }
+    ++cyc;
+    if ((st = amr_norm(H, e, &rel))) return st;
+    if (mixed_step && H->h_red[3] != 0) ncol = 0;
+    hist.push_back(rel);
+  }
+  CK(cudaGetLastError());
+  auto t1 = std::chrono::steady_clock::now();
+  if (rep) {
+    rep->status = status;
+    rep->cycles = cyc;
+    rep->rel = rel;
+    rep->nhist = (int)std::min<size_t>(hist.size(), MG_HIST);
+    for (int q = 0; q < rep->nhist; ++q) rep->hist[q] = hist[q];
+    rep->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    rep->cell_updates = H->updates;
+  }
+  return status;
+}
+
 // ------------------------------------------------------------ staging
 
 long interior_cells(const mg_hierarchy* H) { return H->L[0].cells(); }
@@ -1516,6 +1861,8 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   if (!H) return MG_OK;
   if (H->st) cudaStreamSynchronize(H->st);
   if (H->sub) mg_destroy_hierarchy(H->sub);
+  if (H->amr.mem) cudaFree(H->amr.mem);
+  if (H->amr.aa) cudaFree(H->amr.aa);
   for (cudaEvent_t e : H->ev) cudaEventDestroy(e);
   for (double* p : H->stage) cudaFree(p);
   if (H->aa) cudaFree(H->aa);
@@ -1951,3 +2298,93 @@ int mg_prolong_add(mg_hierarchy* H, int bc, const double* coarse_e, double* fine
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ composite grid (AMR)
+
+namespace {
+
+// Argument checks and the copies of a composite call into the level arrays
+// (interior layout in, ghosted arrays of the base's finest level and the
+// patch out); the box's patch level is set up first.
+int amr_enter(mg_hierarchy* H, const int box_lo[3], const int box_hi[3], int kind, int bc, const double* U,
+              const double* A2, const double* c, const double* f, const double* Up, const double* A2p,
+              const double* cp, const double* fp, const double* u, const double* up, bool need_f, Eq* eq) {
+  if (!H || !box_lo || !box_hi || !u || !up) return fail(MG_ERR_INVALID, "null argument");
+  if (kind != MG_EQ_PSI && kind != MG_EQ_LIN) return fail(MG_ERR_INVALID, "bad equation kind");
+  if (bc < MG_BC_ROBIN || bc > MG_BC_NEUMANN) return fail(MG_ERR_INVALID, "bad boundary condition");
+  if (kind == MG_EQ_PSI && (!U || !A2 || !Up || !A2p))
+    return fail(MG_ERR_INVALID, "psi equation needs U and A2 on both levels");
+  if (kind == MG_EQ_LIN && need_f && (!f || !fp)) return fail(MG_ERR_INVALID, "linear equation needs f on both levels");
+  if (kind == MG_EQ_LIN && (!c) != (!cp)) return fail(MG_ERR_INVALID, "give c on both levels or on neither");
+  AmrBox box;
+  if (int st = amr_box(H, box_lo, box_hi, &box)) return st;
+  if (int st = enter(H)) return st;
+  if (int st = ensure_amr(H, box)) return st;
+  Eq e{kind, bc, 0, 1, kind == MG_EQ_LIN && c != nullptr};
+  e.amr = true;
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const AmrArrays W = amr_arrays(H, e);
+  copy_in(H, u, L0.u[0]);
+  launch_copy_in<double, double>(A.v, up, A.u, 0.0, H->st);
+  if (kind == MG_EQ_PSI) {
+    copy_in(H, U, L0.s0);
+    copy_in(H, A2, L0.s1);
+    launch_copy_in<double, double>(A.v, Up, A.s0, 0.0, H->st);
+    launch_copy_in<double, double>(A.v, A2p, A.s1, 0.0, H->st);
+    CK(cudaMemsetAsync(A.f, 0, sizeof(double) * A.ng, H->st));
+  } else {
+    if (c) {
+      copy_in(H, c, L0.s1);
+      launch_copy_in<double, double>(A.v, cp, A.s1, 0.0, H->st);
+    }
+    if (f) copy_in(H, f, W.f0);
+    if (fp) launch_copy_in<double, double>(A.v, fp, A.f, 0.0, H->st);
+  }
+  *eq = e;
+  return MG_OK;
+}
+
+}  // namespace
+
+int mg_solve_scalar_amr(mg_hierarchy* H, const int box_lo[3], const int box_hi[3], int kind, int bc,
+                        const double* U, const double* A2, const double* c, const double* f, const double* Up,
+                        const double* A2p, const double* cp, const double* fp, double* u, double* up,
+                        mg_solve_report* rep) {
+  Eq e{};
+  if (int st = amr_enter(H, box_lo, box_hi, kind, bc, U, A2, c, f, Up, A2p, cp, fp, u, up, true, &e)) return st;
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const int st = run_solve_amr(H, e, rep);
+  // covered base cells: the restriction of the patch
+  const AmrArrays W = amr_arrays(H, e);
+  launch_amr_restrict(with_bc(A.v, e.bc), with_bc(L0.v64, e.bc), A.box, A.u, A.r, L0.u[0], W.rr, H->st);
+  copy_out(H, L0.u[0], u);
+  launch_copy_out<double, double>(A.v, A.u, up, 0.0, H->st);
+  CK(cudaStreamSynchronize(H->st));
+  return st;
+}
+
+int mg_apply_amr(mg_hierarchy* H, const int box_lo[3], const int box_hi[3], int kind, int bc, const double* U,
+                 const double* A2, const double* c, const double* Up, const double* A2p, const double* cp,
+                 const double* u, const double* up, double* out, double* outp) {
+  if (!out || !outp) return fail(MG_ERR_INVALID, "null output");
+  Eq e{};
+  if (int st = amr_enter(H, box_lo, box_hi, kind, bc, U, A2, c, nullptr, Up, A2p, cp, nullptr, u, up, false, &e))
+    return st;
+  auto& A = H->amr;
+  Level& L0 = H->L[0];
+  const AmrArrays W = amr_arrays(H, e);
+  restrict_sources(H, e);
+  amr_refresh(H, e, true);
+  const double* s0p = e.kind == EQ_PSI ? A.s0 : nullptr;
+  const double* s1p = (e.kind == EQ_PSI || e.has_c) ? A.s1 : nullptr;
+  launch_amr_patch_resid(with_bc(A.v, e.bc), e.kind, A.u, nullptr, s0p, s1p, A.r, nullptr, 1, H->st);
+  launch_amr_base(with_bc(L0.v64, e.bc), A.box, e.kind, L0.u[0], s0ptr(H, e, 0), s1ptr(H, e, 0), nullptr, nullptr,
+                  W.corr, L0.r[0], nullptr, 2, H->st);
+  copy_out(H, L0.r[0], out);
+  launch_copy_out<double, double>(A.v, A.r, outp, 0.0, H->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(H->st));
+  return MG_OK;
+}

@@ -215,6 +215,40 @@ void launch_xcfc_ap_init(const LevelView<double>& L, const double* alpha, const 
 void launch_xcfc_alpha_out(const LevelView<double>& L, const double* dap, const double* dpsi, double* alpha,
                            cudaStream_t st);
 
+// Two-level composite grid (mg_amr.cu): the refined patch covers base cells
+// a <= I < b (b[2] = 1 in 2D); bit 2 d + (side > 0) of cf marks the patch
+// faces that are coarse-fine interfaces (the others lie on the domain
+// boundary and take its rules).
+struct AmrBox {
+  int a[3], b[3];
+  int cf;
+};
+void launch_amr_cf_ghosts(const LevelView<double>& Pv, const LevelView<double>& B, const AmrBox& box, double* up,
+                          const double* ub, cudaStream_t st);
+void launch_amr_smooth(const LevelView<double>& L, int kind, double* u, const double* f, const double* s0,
+                       const double* s1, int colour, cudaStream_t st);
+// r = f - L(u) on the patch (f nullable; apply: r = L(u)), norms into red.
+void launch_amr_patch_resid(const LevelView<double>& L, int kind, const double* u, const double* f, const double* s0,
+                            const double* s1, double* r, unsigned long long* red, int apply, cudaStream_t st);
+void launch_amr_restrict(const LevelView<double>& Pv, const LevelView<double>& B, const AmrBox& box, const double* up,
+                         const double* rp, double* ub, double* rr, cudaStream_t st);
+void launch_amr_flux_corr(const LevelView<double>& Pv, const LevelView<double>& B, const AmrBox& box,
+                          const double* up, const double* ub, double* corr, cudaStream_t st);
+// Base level of the composite grid: mode 0 the FAS right-hand side f, 1 the
+// composite residual norms of the uncovered cells into red, 2 the composite
+// operator into f (0 on covered cells).
+void launch_amr_base(const LevelView<double>& B, const AmrBox& box, int kind, const double* u, const double* s0,
+                     const double* s1, const double* f0, const double* rr, const double* corr, double* f,
+                     unsigned long long* red, int mode, cudaStream_t st);
+void launch_amr_prolong(const LevelView<double>& Pv, const LevelView<double>& B, const AmrBox& box, const double* e,
+                        double* up, cudaStream_t st);
+// Composite unknowns <-> flat vector x (patch cells, then the uncovered
+// base cells at the ghosted offsets bmap[0 .. nbase - 1]).
+void launch_amr_flat(const LevelView<double>& Pv, const LevelView<double>& B, const AmrBox& box, double* up,
+                     double* ub, const int* bmap, long nbase, double* x, int to_flat, cudaStream_t st);
+// out = a - b over the interior (ghosted arrays of L).
+void launch_amr_diff(const LevelView<double>& L, const double* a, const double* b, double* out, cudaStream_t st);
+
 // Anderson mixing (mg_accel.cu): live ring slots of the difference columns
 // in age order (the newest last).
 constexpr int AA_MAX = 16;

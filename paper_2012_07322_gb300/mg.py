@@ -37,7 +37,7 @@ EXPORTS = ["mg_strerror", "mg_last_error", "mg_hierarchy_bytes", "mg_create_hier
            "mg_num_levels", "mg_solve_cfc", "mg_clean_divB", "mg_solve_scalar", "mg_solve_vector",
            "mg_apply_operator", "mg_smooth", "mg_compute_a2", "mg_divergence", "mg_restrict", "mg_prolong_add",
            "mg_kernel_launches", "mg_profile_enable", "mg_profile_read", "mg_divb_norms_noalloc",
-           "mg_server_create", "mg_server_destroy", "mg_submit", "mg_poll"]
+           "mg_server_create", "mg_server_destroy", "mg_submit", "mg_poll", "mg_solve_scalar_amr", "mg_apply_amr"]
 MG_REQ_CFC, MG_REQ_DIVB = 0, 1
 MG_NOALLOC_MAX_CELLS = 2097152
 PROF_CLASSES = ["smooth64_scalar", "smooth64_vec", "smooth32_scalar", "smooth32_vec", "resid64_scalar",
@@ -129,6 +129,10 @@ def lib():
         L.mg_server_destroy.argtypes = [P]
         L.mg_submit.argtypes = [P, C.POINTER(mg_request), C.POINTER(C.c_uint64)]
         L.mg_poll.argtypes = [P, C.c_uint64, C.POINTER(I), C.POINTER(mg_result)]
+        I3 = C.c_int * 3
+        L.mg_solve_scalar_amr.argtypes = [P, C.POINTER(I3), C.POINTER(I3), I, I, P, P, P, P, P, P, P, P, P, P,
+                                          C.POINTER(mg_solve_report)]
+        L.mg_apply_amr.argtypes = [P, C.POINTER(I3), C.POINTER(I3), I, I, P, P, P, P, P, P, P, P, P, P]
         L.mg_divb_norms_noalloc.argtypes = [I, C.POINTER(C.c_int * 3), C.POINTER(C.c_double * 3),
                                             C.POINTER(C.c_double * 3), C.POINTER(P), P,
                                             C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -291,6 +295,44 @@ def mg_solve_scalar(h, kind, bc, u, U=None, A2=None, c=None, f=None, zero_mean=F
                                _ptr(u, h, name="u"), C.byref(rep))
     _check(st, "mg_solve_scalar", allow)
     return rep.as_dict()
+
+
+def patch_shape(h, box_lo, box_hi):
+    """Shape (n2, n1, n0) / (n1, n0) of the refined patch over base cells
+    box_lo <= I < box_hi."""
+    nd = h.desc.ndim
+    return tuple(2 * (box_hi[k] - box_lo[k]) for k in reversed(range(nd)))
+
+
+def _box3(v):
+    return (C.c_int * 3)(*(list(v) + [0] * (3 - len(v))))
+
+
+def mg_solve_scalar_amr(h, box_lo, box_hi, kind, bc, u, up, U=None, A2=None, c=None, f=None, Up=None, A2p=None,
+                        cp=None, fp=None, allow=(MG_OK,)):
+    """Two-level composite-grid solve (base grid of h, refined patch over
+    base cells box_lo <= I < box_hi); u and up updated in place."""
+    ps = patch_shape(h, box_lo, box_hi)
+    rep = mg_solve_report()
+    st = lib().mg_solve_scalar_amr(h.handle, C.byref(_box3(box_lo)), C.byref(_box3(box_hi)), KIND[kind], BC[bc],
+                                   _ptr(U, h, name="U"), _ptr(A2, h, name="A2"), _ptr(c, h, name="c"),
+                                   _ptr(f, h, name="f"), _ptr(Up, h, shape=ps, name="Up"),
+                                   _ptr(A2p, h, shape=ps, name="A2p"), _ptr(cp, h, shape=ps, name="cp"),
+                                   _ptr(fp, h, shape=ps, name="fp"), _ptr(u, h, name="u"),
+                                   _ptr(up, h, shape=ps, name="up"), C.byref(rep))
+    _check(st, "mg_solve_scalar_amr", allow)
+    return rep.as_dict()
+
+
+def mg_apply_amr(h, box_lo, box_hi, kind, bc, u, up, out, outp, U=None, A2=None, c=None, Up=None, A2p=None,
+                 cp=None):
+    ps = patch_shape(h, box_lo, box_hi)
+    st = lib().mg_apply_amr(h.handle, C.byref(_box3(box_lo)), C.byref(_box3(box_hi)), KIND[kind], BC[bc],
+                            _ptr(U, h, name="U"), _ptr(A2, h, name="A2"), _ptr(c, h, name="c"),
+                            _ptr(Up, h, shape=ps, name="Up"), _ptr(A2p, h, shape=ps, name="A2p"),
+                            _ptr(cp, h, shape=ps, name="cp"), _ptr(u, h, name="u"), _ptr(up, h, shape=ps, name="up"),
+                            _ptr(out, h, name="out"), _ptr(outp, h, shape=ps, name="outp"))
+    _check(st, "mg_apply_amr")
 
 
 def mg_solve_vector(h, bc, f, V, allow=(MG_OK,)):
