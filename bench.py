@@ -460,20 +460,26 @@ def serving_measurement(mg, torch, precision="mixed", rate=2000.0, n_requests=40
 
 
 def serving_block(mg, torch, gpu_id, sweep):
-    """The serving measurement of the bench line: one point (mixed precision,
-    2000 requests/s, 400 requests); with sweep, arrival rates 250 ... 4000/s
-    with 1000 requests per point in mixed precision and FP64."""
+    """The serving measurement of the bench line: mixed precision at 2000
+    requests/s (the serving workload's rate, beyond the server's capacity:
+    the queue grows) and at 60/s (below it), 300 requests each; with sweep,
+    1000 requests per point at 15 ... 400/s in mixed precision and 5 ... 80/s
+    in FP64, across the capacity of each."""
     work = ("Poisson arrivals (seed 3): 80%% xCFC on %d warm-started streams (each request the next of %d "
             "time steps of a rotating star; grids %s), 20%% div-B (32^3, 64^3); continuous admission into "
             "worker slots; uniform grids stand in for the two-level AMR of the serving workload"
             % (SERVE_STREAMS, SERVE_STEPS, ", ".join("%s %s" % (k[0], "x".join(map(str, k[1])))
                                                       for k, _ in SERVE_KINDS)))
     if not sweep:
-        return {"workload": work, **serving_measurement(mg, torch, gpu_id=gpu_id)}
+        setup = serving_setup(mg, torch, "mixed")
+        return {"workload": work,
+                "points": [serving_measurement(mg, torch, "mixed", rate, 300, gpu_id=gpu_id, setup=setup)
+                           for rate in (2000.0, 60.0)]}
     points = []
-    for precision in ("mixed", "fp64"):
+    for precision, rates in (("mixed", (15.0, 30.0, 60.0, 100.0, 150.0, 400.0)),
+                             ("fp64", (5.0, 10.0, 20.0, 30.0, 80.0))):
         setup = serving_setup(mg, torch, precision)
-        for rate in (250.0, 500.0, 1000.0, 2000.0, 4000.0):
+        for rate in rates:
             points.append(serving_measurement(mg, torch, precision, rate, 1000, gpu_id=gpu_id, setup=setup))
     return {"workload": work, "sweep": points}
 
