@@ -276,10 +276,18 @@ __global__ void __launch_bounds__(256, 2)
     k_aa_update_dots(LevelView<double> L, int ncomp, long stride, const double* __restrict__ g0,
                      const double* __restrict__ g1, const double* __restrict__ g2, double* __restrict__ x,
                      double* __restrict__ fprev, double* __restrict__ gprev, TC* __restrict__ dF,
-                     TC* __restrict__ dG, const __grid_constant__ AACols cols, double* __restrict__ part,
-                     unsigned int* __restrict__ done, double* __restrict__ M, double* __restrict__ gamma,
-                     unsigned long long* __restrict__ status) {
+                     TC* __restrict__ dG, const __grid_constant__ AACols hcols, const AACols* __restrict__ dcols,
+                     double* __restrict__ part, unsigned int* __restrict__ done, double* __restrict__ M,
+                     double* __restrict__ gamma, unsigned long long* __restrict__ status) {
   pdl_entry();
+  // the live columns: from the launch, or (device-side cycle loop) from
+  // device memory written by the preceding loop step
+  __shared__ AACols scols;
+  if (dcols) {
+    if (threadIdx.x == 0) scols = *dcols;
+    __syncthreads();
+  }
+  const AACols& cols = dcols ? scols : hcols;
   const long nq = (long)L.n0 * L.n1 * L.n2 / G;
   const long vstride = (long)ncomp * stride;
   const int nc = cols.n;
@@ -370,10 +378,16 @@ template <typename TC, int G>
 __global__ void __launch_bounds__(256)
     k_aa_combine(LevelView<double> L, int ncomp, long stride, double* __restrict__ u0, double* __restrict__ u1,
                  double* __restrict__ u2, double* __restrict__ x, const TC* __restrict__ dG,
-                 const __grid_constant__ AACols cols, const double* __restrict__ gamma,
-                 const unsigned long long* __restrict__ status) {
+                 const __grid_constant__ AACols hcols, const AACols* __restrict__ dcols,
+                 const double* __restrict__ gamma, const unsigned long long* __restrict__ status) {
   pdl_entry();
-  if (*status) return;
+  __shared__ AACols scols;
+  if (dcols) {
+    if (threadIdx.x == 0) scols = *dcols;
+    __syncthreads();
+  }
+  const AACols& cols = dcols ? scols : hcols;
+  if (*status || cols.n == 0) return;
   const long nq = (long)L.n0 * L.n1 * L.n2 / G;
   const long vstride = (long)ncomp * stride;
   const int nc = cols.n;
@@ -419,36 +433,100 @@ static unsigned aa_grid(const LevelView<double>& L, int ncomp, int per_block, in
 template <typename TC>
 void launch_aa_update_dots(const LevelView<double>& L, int ncomp, long stride, double* const g[3], double* x,
                            double* fprev, double* gprev, TC* dF, TC* dG, const AACols& cols, double* scratch,
-                           unsigned long long* status, cudaStream_t st) {
+                           unsigned long long* status, cudaStream_t st, const AACols* dcols) {
   count_launch();
   AAScratch S = aa_scratch(scratch);
+  const unsigned gb = aa_grid(L, ncomp, 256, AA_BLOCKS);
   if (L.n0 >= 4)
-    launch_k(k_aa_update_dots<TC, 4>, aa_grid(L, ncomp, 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
-                                                       cols, S.part, S.done, S.M, S.gamma, status);
+    launch_k(k_aa_update_dots<TC, 4>, gb, 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
+             cols, dcols, S.part, S.done, S.M, S.gamma, status);
   else
-    launch_k(k_aa_update_dots<TC, 1>, aa_grid(L, ncomp, 256, AA_BLOCKS), 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
-                                                       cols, S.part, S.done, S.M, S.gamma, status);
+    launch_k(k_aa_update_dots<TC, 1>, gb, 256, 0, st, L, ncomp, stride, g[0], g[1], g[2], x, fprev, gprev, dF, dG,
+             cols, dcols, S.part, S.done, S.M, S.gamma, status);
 }
 template <typename TC>
 void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], double* x,
                        const TC* dG, const AACols& cols, const double* scratch, const unsigned long long* status,
-                       cudaStream_t st) {
+                       cudaStream_t st, const AACols* dcols) {
   count_launch();
   const double* gamma = aa_scratch(const_cast<double*>(scratch)).gamma;
+  const unsigned gb = aa_grid(L, ncomp, 256, AA_BLOCKS * 2);
   if (L.n0 >= 4)
-    launch_k(k_aa_combine<TC, 4>, aa_grid(L, ncomp, 256, AA_BLOCKS * 2), 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, gamma,
-                                                       status);
+    launch_k(k_aa_combine<TC, 4>, gb, 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, dcols, gamma,
+             status);
   else
-    launch_k(k_aa_combine<TC, 1>, aa_grid(L, ncomp, 256, AA_BLOCKS * 2), 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, gamma,
-                                                       status);
+    launch_k(k_aa_combine<TC, 1>, gb, 256, 0, st, L, ncomp, stride, u[0], u[1], u[2], x, dG, cols, dcols, gamma,
+             status);
+}
+
+// One step of the device-side cycle loop (one thread): the weighted
+// relative residual rel = red[1] / max(red[2], 1e-300) of the residual just
+// evaluated (non-finite norms give NaN), the cycle count, the mixing ring
+// (restarted when the last mixing step found a degenerate history, red[3]),
+// the stopping rule in the order of the host loop, the live columns of the
+// next cycle's mixing step, and the while node's condition.
+__global__ void k_loop_decide(LoopState* __restrict__ S, const unsigned long long* __restrict__ red, LoopParams P,
+                              cudaGraphConditionalHandle h, int first) {
+  pdl_entry();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double num = __longlong_as_double((long long)red[1]), den = __longlong_as_double((long long)red[2]);
+  double rel;
+  if (isinf(num) || isinf(den) || isnan(num) || isnan(den))
+    rel = __longlong_as_double(0x7ff8000000000000LL);
+  else
+    rel = num / (den > 1e-300 ? den : 1e-300);
+  if (first) {
+    S->cyc = 0;
+    S->ncol = 0;
+    S->head = 0;
+    S->mixstep = 0;
+  } else {
+    S->cyc += 1;
+    if (S->mixstep && red[3] != 0ULL) S->ncol = 0;
+  }
+  const int cyc = S->cyc;
+  if (cyc < 1024) S->hist[cyc] = rel;
+  S->rel = rel;
+  int stop = 1, status = 0;
+  if (rel != rel)
+    status = 5;  // MG_ERR_NAN
+  else if (rel <= P.tol)
+    status = 0;
+  else if (cyc >= P.max_cycles)
+    status = 3;  // MG_ERR_NOCONV
+  else if (P.stall_window > 0 && cyc >= P.stall_window && rel > 0.95 * S->hist[cyc - P.stall_window])
+    status = 4;  // MG_ERR_STALLED
+  else
+    stop = 0;
+  AACols c;
+  c.n = 0;
+  if (!stop && P.m > 0 && cyc > 0) {
+    const int m = P.m, slot = S->head;
+    S->head = (S->head + 1) % m;
+    if (S->ncol < m) S->ncol += 1;
+    c.n = S->ncol;
+    for (int a = 0; a < c.n; ++a) c.slot[a] = (slot - c.n + 1 + a + m) % m;
+  }
+  S->cols = c;
+  S->mixstep = c.n > 0;
+  S->status = status;
+  S->stop = stop;
+  cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+void launch_loop_decide(LoopState* S, const unsigned long long* red, const LoopParams& P,
+                        cudaGraphConditionalHandle h, int first, cudaStream_t st) {
+  count_launch();
+  launch_k(k_loop_decide, 1, 32, 0, st, S, red, P, h, first);
 }
 
 #define GMG_AA_INST(TC)                                                                                         \
   template void launch_aa_update_dots<TC>(const LevelView<double>&, int, long, double* const[3], double*,        \
                                           double*, double*, TC*, TC*, const AACols&, double*,                    \
-                                          unsigned long long*, cudaStream_t);                                    \
+                                          unsigned long long*, cudaStream_t, const AACols*);                     \
   template void launch_aa_combine<TC>(const LevelView<double>&, int, long, double* const[3], double*, const TC*, \
-                                      const AACols&, const double*, const unsigned long long*, cudaStream_t);
+                                      const AACols&, const double*, const unsigned long long*, cudaStream_t,     \
+                                      const AACols*);
 GMG_AA_INST(double)
 GMG_AA_INST(float)
 

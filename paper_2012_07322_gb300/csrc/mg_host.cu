@@ -93,6 +93,19 @@ struct mg_hierarchy {
   // MG_DIVB_EXACT: the hierarchy of the parity-class problems (n / 2 cells
   // per dimension), on this hierarchy's stream
   mg_hierarchy* sub = nullptr;
+  // device-side cycle loops: one executable graph per equation signature
+  // (a while node around the cycle), their state, and whether the device
+  // refused graphs with conditional nodes (then the host loop runs)
+  struct LoopGraph {
+    int key;
+    cudaGraphExec_t exec;
+    int64_t updates;                 // smoother updates of one cycle
+    uint64_t launches_pre, launches; // kernels before the loop and per cycle
+  };
+  std::vector<LoopGraph> loops;
+  LoopState* d_loop = nullptr;
+  LoopState* h_loop = nullptr;
+  bool loop_off = false;
   // composite grid (mg_solve_scalar_amr): the refined patch of the last box
   // used, allocated on first use
   struct Amr {
@@ -633,9 +646,10 @@ double bits_to_double(unsigned long long b) {
   return x;
 }
 
-// Finest-level residual and its weighted relative norm; in mixed precision
-// the residual is also stored, rounded, as the FP32 right-hand side f32.
-int finest_norm(mg_hierarchy* H, const Eq& e, double* rel) {
+// Finest-level residual with the norms of the stopping rule into the
+// reduction slots 0..2 (enqueued only); in mixed precision the residual is
+// also stored, rounded, as the FP32 right-hand side f32.
+int finest_residual(mg_hierarchy* H, const Eq& e) {
   Level& L = H->L[0];
   auto v = with_bc(L.v64, e.bc);
   CK(cudaMemsetAsync(H->d_red, 0, sizeof(unsigned long long) * 3, H->st));
@@ -654,6 +668,12 @@ int finest_norm(mg_hierarchy* H, const Eq& e, double* rel) {
   }
   prof_end(H, tok);
   CK(cudaGetLastError());
+  return MG_OK;
+}
+
+// Finest-level residual and its weighted relative norm, read on the host.
+int finest_norm(mg_hierarchy* H, const Eq& e, double* rel) {
+  if (int st = finest_residual(H, e)) return st;
   // slot 3: status of this cycle's mixing solve (read by run_solve)
   CK(cudaMemcpyAsync(H->h_red, H->d_red, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, H->st));
   CK(cudaStreamSynchronize(H->st));
@@ -1193,6 +1213,145 @@ int ensure_ghost_push(mg_hierarchy* H) {
   return MG_OK;
 }
 
+// The whole cycle loop of one equation as one graph launch: the initial
+// residual, then a while node whose body is one cycle (the cycle map, the
+// mixing step, the residual and k_loop_decide, which applies the stopping
+// rule on the device and sets the node's condition).  No host round trip
+// per cycle; the host reads the loop state once at the end.  Returns
+// LOOP_UNSUPPORTED (nothing enqueued) when the graph cannot be built.
+constexpr int LOOP_UNSUPPORTED = -1;
+
+int build_loop_graph(mg_hierarchy* H, const Eq& e, int key, double* ax, double* afp, double* agp, double* adF,
+                     double* adG, float* adF32, float* adG32) {
+  const mg_grid_desc& d = H->d;
+  const bool mixed = d.precision == MG_MIXED;
+  Level& L0 = H->L[0];
+  const int m = d.accel_depth;
+  const long stride = L0.ng;
+  cudaGraph_t top = nullptr, pre = nullptr, body = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle hc;
+  auto cleanup = [&]() {
+    if (pre) cudaGraphDestroy(pre);
+    if (body) cudaGraphDestroy(body);
+    if (top) cudaGraphDestroy(top);
+  };
+  if (cudaGraphCreate(&top, 0) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&hc, top, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return LOOP_UNSUPPORTED;
+  }
+  const LoopParams P{d.tol, d.max_cycles, d.stall_window, m};
+  const int64_t u0 = H->updates;
+  // before the loop: the mixing's starting iterate, the initial residual
+  const unsigned long long l0 = launch_count();
+  CK(cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
+  if (m > 0)
+    for (int c = 0; c < e.ncomp; ++c)
+      cudaMemcpyAsync(ax + (long)c * stride, L0.u[c], sizeof(double) * L0.ng, cudaMemcpyDeviceToDevice, H->st);
+  int st = finest_residual(H, e);
+  launch_loop_decide(H->d_loop, H->d_red, P, hc, 1, H->st);
+  cudaError_t ce = cudaStreamEndCapture(H->st, &pre);
+  const unsigned long long lpre = launch_count() - l0;
+  if (st || ce != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    count_launch(-(int)lpre);
+    return st ? st : LOOP_UNSUPPORTED;
+  }
+  // one cycle
+  const unsigned long long l1 = launch_count();
+  const int64_t u1 = H->updates;
+  CK(cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
+  st = cycle_map(H, e);
+  if (m > 0) {
+    const AACols none{};
+    const AACols* dc = &H->d_loop->cols;
+    double* scr = H->d_aa_part;
+    if (mixed) {
+      launch_aa_update_dots<float>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF32, adG32, none, scr,
+                                   H->d_red + 3, H->st, dc);
+      launch_aa_combine<float>(L0.v64, e.ncomp, stride, L0.u, ax, adG32, none, scr, H->d_red + 3, H->st, dc);
+    } else {
+      launch_aa_update_dots<double>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF, adG, none, scr, H->d_red + 3,
+                                    H->st, dc);
+      launch_aa_combine<double>(L0.v64, e.ncomp, stride, L0.u, ax, adG, none, scr, H->d_red + 3, H->st, dc);
+    }
+    if (e.kind == EQ_VEC) fill_all64(H, e, 0);
+  }
+  if (!st) st = finest_residual(H, e);
+  launch_loop_decide(H->d_loop, H->d_red, P, hc, 0, H->st);
+  ce = cudaStreamEndCapture(H->st, &body);
+  const unsigned long long lbody = launch_count() - l1;
+  const int64_t ubody = H->updates - u1;
+  H->updates = u0;
+  count_launch(-(int)(lpre + lbody));  // counted per run below
+  if (st || ce != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return st ? st : LOOP_UNSUPPORTED;
+  }
+  cudaGraphNode_t npre, ncond, nbody;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddChildGraphNode(&npre, top, nullptr, 0, pre) != cudaSuccess ||
+      cudaGraphAddNode(&ncond, top, &npre, nullptr, 1, &cp) != cudaSuccess ||
+      cudaGraphAddChildGraphNode(&nbody, cp.conditional.phGraph_out[0], nullptr, 0, body) != cudaSuccess ||
+      cudaGraphInstantiate(&exec, top, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return LOOP_UNSUPPORTED;
+  }
+  cleanup();
+  H->loops.push_back(mg_hierarchy::LoopGraph{key, exec, ubody, lpre, lbody});
+  return MG_OK;
+}
+
+int run_loop_graph(mg_hierarchy* H, const Eq& e, double* ax, double* afp, double* agp, double* adF, double* adG,
+                   float* adF32, float* adG32, mg_solve_report* rep, std::chrono::steady_clock::time_point t0) {
+  if (!H->d_loop) {
+    if (cudaMalloc(&H->d_loop, sizeof(LoopState)) != cudaSuccess) {
+      H->d_loop = nullptr;
+      return fail(MG_ERR_OOM, "loop state allocation failed");
+    }
+    if (cudaMallocHost(&H->h_loop, sizeof(LoopState)) != cudaSuccess) {
+      H->h_loop = nullptr;
+      return fail(MG_ERR_OOM, "pinned loop state allocation failed");
+    }
+  }
+  const int key = e.kind | (e.bc << 2) | (e.zero_mean << 4) | ((int)e.has_c << 5) | (H->d.precision << 6);
+  const mg_hierarchy::LoopGraph* g = nullptr;
+  for (const auto& q : H->loops)
+    if (q.key == key) g = &q;
+  if (!g) {
+    const int st = build_loop_graph(H, e, key, ax, afp, agp, adF, adG, adF32, adG32);
+    if (st) return st;
+    g = &H->loops.back();
+  }
+  CK(cudaGraphLaunch(g->exec, H->st));
+  CK(cudaMemcpyAsync(H->h_loop, H->d_loop, sizeof(LoopState), cudaMemcpyDeviceToHost, H->st));
+  CK(cudaStreamSynchronize(H->st));
+  const LoopState& S = *H->h_loop;
+  const int cyc = S.cyc;
+  H->updates += (int64_t)cyc * g->updates;
+  count_launch((int)(g->launches_pre + (uint64_t)cyc * g->launches));
+  auto t1 = std::chrono::steady_clock::now();
+  if (rep) {
+    rep->status = S.status;
+    rep->cycles = cyc;
+    rep->rel = S.rel;
+    rep->nhist = std::min(cyc + 1, (int)MG_HIST);
+    for (int q = 0; q < rep->nhist; ++q) rep->hist[q] = S.hist[q];
+    rep->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    rep->cell_updates = H->updates;
+  }
+  return S.status;
+}
+
 int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   auto t0 = std::chrono::steady_clock::now();
   H->updates = 0;
@@ -1229,6 +1388,11 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
       adF = agp + vlen;
       adG = adF + (long)m * vlen;
     }
+  }
+  if (!H->prof_on && !H->loop_off) {
+    st = run_loop_graph(H, e, ax, afp, agp, adF, adG, adF32, adG32, rep, t0);
+    if (st != LOOP_UNSUPPORTED) return st;
+    H->loop_off = true;  // no graphs with while nodes here: the host loop from now on
   }
   std::vector<double> hist;
   double rel;
@@ -1871,6 +2035,9 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   if (H->d_aa_part) cudaFree(H->d_aa_part);
   if (H->push_buf) cudaFree(H->push_buf);
   for (GraphEntry& g : H->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : H->loops) cudaGraphExecDestroy(g.exec);
+  if (H->d_loop) cudaFree(H->d_loop);
+  if (H->h_loop) cudaFreeHost(H->h_loop);
   if (H->own_stream) cudaStreamDestroy(H->st);
   if (H->ev_in) cudaEventDestroy(H->ev_in);
   cudaFree(H->arena);

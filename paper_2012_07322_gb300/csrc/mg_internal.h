@@ -88,17 +88,17 @@ void launch_fill_ghosts3(const LevelView<T>& L, T* const u[3], int ncomp, int ve
 constexpr long ROW_PAD = 4;
 inline long row_stride(int n0) { return (n0 + 2 * ROW_PAD + ROW_PAD - 1) / ROW_PAD * ROW_PAD; }
 
-// One red-black sweep in one launch (Cartesian 3D linear scalar equations,
-// levels of at least one 64 x 8 column), out of place: uin -> uout, which
-// must not alias; only the interior of uout is written.  Returns false when
-// it does not apply.
+// One red-black sweep in one launch (3D linear scalar equations on levels
+// of at least one 64 x 8 column; Cartesian, cylindrical and spherical), out
+// of place: uin -> uout, which must not alias; only the interior of uout is
+// written.  Returns false when it does not apply.
 template <typename T>
 bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st);
 template <typename T>
 void init_fused_sweep_attributes();
 template <typename T>
 inline bool fused_sweep_applies(const LevelView<T>& L) {
-  return L.geom == CART && L.three && L.n0 >= 64 && L.n1 >= 8 && L.n2 >= 4;
+  return L.three && L.n0 >= 64 && L.n1 >= 8 && L.n2 >= 4;
 }
 // Ghost push of the vector smoother's colour passes.  With a table, the
 // pass of component c also rewrites, at its end, every ghost of c whose
@@ -276,21 +276,45 @@ inline AAScratch aa_scratch(double* s) {
   return o;
 }
 // History columns TC: double, or float in mixed precision.  status gets the
-// least-squares outcome (0 solved, 1 degenerate) when cols.n > 0.
+// least-squares outcome (0 solved, 1 degenerate) when cols.n > 0.  With
+// dcols non-null the live columns are read from device memory instead of
+// cols (the device-side cycle loop), and the combination does nothing when
+// they are none.
 template <typename TC>
 void launch_aa_update_dots(const LevelView<double>& L, int ncomp, long stride, double* const g[3], double* x,
                            double* fprev, double* gprev, TC* dF, TC* dG, const AACols& cols, double* scratch,
-                           unsigned long long* status, cudaStream_t st);
+                           unsigned long long* status, cudaStream_t st, const AACols* dcols = nullptr);
 template <typename TC>
 void launch_aa_combine(const LevelView<double>& L, int ncomp, long stride, double* const u[3], double* x,
                        const TC* dG, const AACols& cols, const double* scratch, const unsigned long long* status,
-                       cudaStream_t st);
+                       cudaStream_t st, const AACols* dcols = nullptr);
+
+// Device-side cycle loop: the state one solve's loop keeps on the device
+// (cycle count, status, the mixing ring and the live columns of the next
+// mixing step, the residual history) and the step that ends every cycle:
+// it reads the stopping norms, records them, applies the stopping rule of
+// the host loop (non-finite, tol, max_cycles, stall window), advances the
+// mixing ring and sets the condition of the enclosing while node.
+struct LoopState {
+  int cyc, status, stop, ncol, head, mixstep, pad0, pad1;
+  AACols cols;
+  double rel;
+  double hist[1024];
+};
+struct LoopParams {
+  double tol;
+  int max_cycles, stall_window, m;
+};
+void launch_loop_decide(LoopState* S, const unsigned long long* red, const LoopParams& P,
+                        cudaGraphConditionalHandle h, int first, cudaStream_t st);
 
 // One-block FP32 correction V-cycle over the coarse levels (mg_block.cu):
 // the levels l0 .. l0 + nl - 1 of a hierarchy, the last the coarsest, all
 // held in the block's shared memory (same ghosted layout as in HBM).
 constexpr int BC_MAX = 8;                     // levels one block cycle may span
-constexpr long BLOCK_CYCLE_CELLS = 4096;       // levels this small run in the block cycle
+// Levels this small run in the block cycle (when the levels from there down
+// fit BC_SMEM_MAX: a scalar 32 x 16 x 16 level does, a vector one does not).
+constexpr long BLOCK_CYCLE_CELLS = 8192;
 constexpr size_t BC_SMEM_MAX = 200 * 1024;     // dynamic shared memory of the block cycle
 struct BlockLevel32 {
   LevelView<float> v;        // boundary rule applied

@@ -77,8 +77,11 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
   }
 }
 
-// One full red-black sweep of a Cartesian 3D linear scalar equation in one
-// launch, out of place (uin -> uout).  A block owns a column of TX x RB_TY
+// One full red-black sweep of a 3D linear scalar equation in one launch,
+// out of place (uin -> uout): Cartesian levels, and cylindrical / spherical
+// levels, whose dimension 2 (phi) is periodic: the march along k then wraps
+// (plane -1 is plane n2 - 1), and the coefficients come per (i, j) from the
+// level's tables.  A block owns a column of TX x RB_TY
 // cells over a chunk of planes [z0, z1) and marches along k.  Plane by
 // plane it stages a (TX + 8) x (RB_TY + 4) box of u, f and c (the column
 // with a 4-cell halo in i, 2 cells in j; rows are 16-byte aligned, so the
@@ -164,13 +167,43 @@ struct RbPlanes {
   const T* Cc;  // c of plane s
 };
 
+// Stencil coefficients of one cell of the flux-form Laplacian (Sec. 2.7.1,
+// the terms of lap_scalar): east / west fluxes, the dimension-1 pair (north
+// and south on spherical levels, where they carry sin(theta) at the faces;
+// one value on the others), the dimension-2 coefficient, and the diagonal.
+template <typename T>
+struct RbCoef {
+  T cE, cW, cN, cS, cZ, D;
+};
+template <typename T, int G>
+__device__ __forceinline__ RbCoef<T> rb_coef(const LevelView<T>& L, int i, int j) {
+  RbCoef<T> c;
+  c.cE = L.TI(TI_CE, i);
+  c.cW = L.TI(TI_CW, i);
+  c.D = -(c.cE + c.cW);
+  if (G == SPH) {
+    const T ir2 = L.TI(TI_IX2, i);
+    c.cN = ir2 * L.TJ(TJ_TN, j);
+    c.cS = ir2 * L.TJ(TJ_TS, j);
+    c.D -= c.cN + c.cS;
+    c.cZ = ir2 * L.TJ(TJ_PF, j);
+  } else {
+    c.cN = c.cS = L.ih1s;
+    c.D -= T(2) * L.ih1s;
+    c.cZ = G == CART ? L.ih2s : L.TI(TI_PHI, i);
+  }
+  c.D -= T(2) * c.cZ;
+  return c;
+}
+
 // Newton-Gauss-Seidel update of cell (i0 + x, j0 + y, s): the arithmetic of
-// lap_scalar<CART> and scalar_update<EQ_LIN>.  The outer ghosts a boundary
-// cell needs sit in the staged planes already (rb_fix_ghosts), so every
+// lap_scalar and scalar_update<EQ_LIN>.  The outer ghosts a boundary cell
+// needs sit in the staged planes already (rb_fix_ghosts; across the origin
+// or the axis, and at the poles, the flux coefficient is zero), so every
 // cell takes the same path; RING cells outside the domain are skipped.
-template <typename T, int TX, bool HAS_C, bool RING>
+template <typename T, int G, int TX, bool HAS_C, bool RING>
 __device__ __forceinline__ void rb_relax(const LevelView<T>& L, const RbPlanes<T>& R, int i0, int j0, int x, int y,
-                                         T cE, T cW, T D0, T iD0) {
+                                         const RbCoef<T>& k, T iD0) {
   constexpr int BX = RbShape<TX>::BX;
   if (RING) {
     const int i = i0 + x, j = j0 + y;
@@ -178,15 +211,20 @@ __device__ __forceinline__ void rb_relax(const LevelView<T>& L, const RbPlanes<T
   }
   const int q = (x + RB_HX) + (y + RB_HY) * BX;
   const T uc = R.P[q];
-  T Lu = cE * (R.P[q + 1] - uc) - cW * (uc - R.P[q - 1]);
-  Lu += L.ih1s * (R.P[q + BX] - T(2) * uc + R.P[q - BX]);
-  Lu += L.ih2s * (R.Pu[q] - T(2) * uc + R.Pd[q]);
+  T Lu = k.cE * (R.P[q + 1] - uc) - k.cW * (uc - R.P[q - 1]);
+  if (G == SPH)
+    Lu += k.cN * (R.P[q + BX] - uc) - k.cS * (uc - R.P[q - BX]);
+  else
+    Lu += k.cN * (R.P[q + BX] - T(2) * uc + R.P[q - BX]);
+  Lu += k.cZ * (R.Pu[q] - T(2) * uc + R.Pd[q]);
   if (HAS_C) {
     const T cv = R.Cc[q];
     Lu -= cv * uc;
-    R.P[q] = uc - (Lu - R.F[q]) / (D0 - cv);
-  } else {
+    R.P[q] = uc - (Lu - R.F[q]) / (k.D - cv);
+  } else if (G == CART) {
     R.P[q] = uc - (Lu - R.F[q]) * iD0;
+  } else {
+    R.P[q] = uc - (Lu - R.F[q]) / k.D;
   }
 }
 
@@ -235,15 +273,24 @@ __device__ __forceinline__ void rb_ghost_plane(const LevelView<T>& L, T* G, cons
   }
 }
 
+// The coefficients of the cells a lane relaxes in its row: for pair h, the
+// even (q = 0) and odd (q = 1) cell, whichever the colour of the plane
+// selects.
+template <typename T, int TX>
+struct RbLaneCoef {
+  RbCoef<T> k[TX / 64][2];
+};
+
 // Red cells of plane s: the lane's cells of its row, then the ring.
-template <typename T, int TX, bool HAS_C>
+template <typename T, int G, int TX, bool HAS_C>
 __device__ __forceinline__ void rb_red_plane(const LevelView<T>& L, const RbPlanes<T>& R, int i0, int j0, int s,
-                                             T cE, T cW, T D0, T iD0) {
+                                             const RbLaneCoef<T, TX>& lc, T iD0) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
   const int par = (i0 + j0 + s) & 1;  // red: (i + j + s) even
+  const int q = (par + w) & 1;
 #pragma unroll
   for (int h = 0; h < TX / 64; ++h)
-    rb_relax<T, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + ((par + w) & 1), w, cE, cW, D0, iD0);
+    rb_relax<T, G, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + q, w, q ? lc.k[h][1] : lc.k[h][0], iD0);
   if (t < RbShape<TX>::RING) {
     constexpr int HR = (TX + 2) / 2, HC = RB_TY / 2;
     int x, y;
@@ -260,16 +307,18 @@ __device__ __forceinline__ void rb_red_plane(const LevelView<T>& L, const RbPlan
       x = TX;
       y = 2 * (t - 2 * HR - HC) + par;
     }
-    rb_relax<T, TX, HAS_C, true>(L, R, i0, j0, x, y, cE, cW, D0, iD0);
+    const int ic = min(max(i0 + x, 0), L.n0 - 1), jc = min(max(j0 + y, 0), L.n1 - 1);
+    rb_relax<T, G, TX, HAS_C, true>(L, R, i0, j0, x, y, rb_coef<T, G>(L, ic, jc), iD0);
   }
 }
 
-template <typename T, int TX, bool HAS_C>
-__global__ void __launch_bounds__(RB_THREADS) k_sweep_rb_cart(LevelView<T> L, const T* __restrict__ uin,
-                                                              T* __restrict__ uout, const T* __restrict__ f,
-                                                              const T* __restrict__ c, int zc) {
+template <typename T, int G, int TX, bool HAS_C>
+__global__ void __launch_bounds__(RB_THREADS) k_sweep_rb(LevelView<T> L, const T* __restrict__ uin,
+                                                         T* __restrict__ uout, const T* __restrict__ f,
+                                                         const T* __restrict__ c, int zc) {
   pdl_entry();
   constexpr int BX = RbShape<TX>::BX, BP = RbShape<TX>::BP;
+  constexpr bool PER = G != CART;  // periodic dimension 2
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);
   T* sf = su + RB_NU * BP;
@@ -277,20 +326,26 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb_cart(LevelView<T> L, co
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * RB_TY;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.n2);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const T cE = L.TI(TI_CE, 0), cW = L.TI(TI_CW, 0);  // uniform on a Cartesian grid
-  const T D0 = -(cE + cW) - T(2) * L.ih1s - T(2) * L.ih2s;
-  const T iD0 = T(1) / D0;
+  // coefficients of the lane's cells (uniform on a Cartesian grid)
+  RbLaneCoef<T, TX> lc;
+#pragma unroll
+  for (int h = 0; h < TX / 64; ++h)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) lc.k[h][q] = rb_coef<T, G>(L, i0 + 64 * h + 2 * lane + q, min(j0 + w, L.n1 - 1));
+  const T iD0 = T(1) / lc.k[0][0].D;
   const bool edge_xy = i0 == 0 || j0 == 0 || i0 + TX >= L.n0 || j0 + RB_TY >= L.n1;
   const RbPieces<T, TX> pc(L, i0, j0);
+  auto wrap = [&](int p) { return PER ? (p + L.n2) % L.n2 : p; };
   // group p: u plane p (into u buffer bu) and f, c plane p - 1, for the
-  // planes the chunk needs
+  // planes the chunk needs (periodic levels: the wrapped planes)
   auto stage = [&](int p, int bu) {
-    if (p >= 0 && p < L.n2 && p >= z0 - 2 && p <= z1 + 1) pc.copy(su + bu * BP, uin, (long)p * L.sy);
+    if ((PER || (p >= 0 && p < L.n2)) && p >= z0 - 2 && p <= z1 + 1)
+      pc.copy(su + bu * BP, uin, (long)wrap(p) * L.sy);
     const int pf = p - 1;
-    if (pf >= 0 && pf < L.n2 && pf >= z0 - 1 && pf <= z1) {
+    if ((PER || (pf >= 0 && pf < L.n2)) && pf >= z0 - 1 && pf <= z1) {
       const int bf = (pf & (RB_NF - 1)) * BP;
-      pc.copy(sf + bf, f, (long)pf * L.sy);
-      if (HAS_C) pc.copy(sc + bf, c, (long)pf * L.sy);
+      pc.copy(sf + bf, f, (long)wrap(pf) * L.sy);
+      if (HAS_C) pc.copy(sc + bf, c, (long)wrap(pf) * L.sy);
     }
     cp_async_commit();
   };
@@ -314,16 +369,18 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb_cart(LevelView<T> L, co
     __syncthreads();
     // outer ghosts of the planes about to be relaxed
     if (edge_xy) {
-      if (s == z0 - 1 && s >= 0) rb_fix_ghosts<T, TX>(L, su + bs * BP, i0, j0, s);
-      if (s + 1 >= 0 && s + 1 < L.n2) rb_fix_ghosts<T, TX>(L, su + bu * BP, i0, j0, s + 1);
+      if (s == z0 - 1 && (PER || s >= 0)) rb_fix_ghosts<T, TX>(L, su + bs * BP, i0, j0, wrap(s));
+      if (PER || (s + 1 >= 0 && s + 1 < L.n2)) rb_fix_ghosts<T, TX>(L, su + bu * BP, i0, j0, wrap(s + 1));
     }
-    if (s + 1 == 0) rb_ghost_plane<T, TX>(L, su + bs * BP, su + bu * BP, i0, j0, -1, 0);
-    if (s + 1 == L.n2 - 1) rb_ghost_plane<T, TX>(L, su + bn2 * BP, su + bu * BP, i0, j0, L.n2, L.n2 - 1);
+    if (!PER) {
+      if (s + 1 == 0) rb_ghost_plane<T, TX>(L, su + bs * BP, su + bu * BP, i0, j0, -1, 0);
+      if (s + 1 == L.n2 - 1) rb_ghost_plane<T, TX>(L, su + bn2 * BP, su + bu * BP, i0, j0, L.n2, L.n2 - 1);
+    }
     if (s == z0 - 1) __syncthreads();
-    if (s >= 0 && s < L.n2) {
+    if (PER || (s >= 0 && s < L.n2)) {
       const int bf = (s & (RB_NF - 1)) * BP;
       const RbPlanes<T> R{su + bd * BP, su + bs * BP, su + bu * BP, sf + bf, sc + bf};
-      rb_red_plane<T, TX, HAS_C>(L, R, i0, j0, s, cE, cW, D0, iD0);
+      rb_red_plane<T, G, TX, HAS_C>(L, R, i0, j0, s, lc, iD0);
     }
     __syncthreads();
     const int sb = s - 1;
@@ -334,7 +391,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb_cart(LevelView<T> L, co
       const int par = (i0 + j0 + sb + w + 1) & 1;  // black: (i + j + sb) odd
 #pragma unroll
       for (int h = 0; h < TX / 64; ++h)
-        rb_relax<T, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + par, w, cE, cW, D0, iD0);
+        rb_relax<T, G, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + par, w, par ? lc.k[h][1] : lc.k[h][0],
+                                         iD0);
       using V2 = typename Vec2<T>::type;  // pairs (i, i + 1): n0 a multiple of TX, rows 16-byte aligned
 #pragma unroll
       for (int h = 0; h < TX / 64; ++h) {
@@ -912,25 +970,35 @@ int fused_sweep_tx(const LevelView<T>& L) {
   return (sizeof(T) == 4 && L.n0 >= 128) ? 128 : 64;
 }
 
-// Blocks of k_sweep_rb_cart resident on the whole device, [TX == 128][with
-// c], set when a hierarchy is created (outside any stream capture).
+// Blocks of k_sweep_rb resident on the whole device, [geometry][TX == 128]
+// [with c], set when a hierarchy is created (outside any stream capture).
 template <typename T>
 struct FusedCapacity {
-  static int blocks[2][2];
+  static int blocks[3][2][2];
 };
 template <typename T>
-int FusedCapacity<T>::blocks[2][2] = {{1, 1}, {1, 1}};
+int FusedCapacity<T>::blocks[3][2][2] = {{{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}};
 
-template <typename T, int TX, bool HAS_C>
+template <typename T, int G, int TX, bool HAS_C>
 static void set_fused_capacity(int sms) {
   const size_t smem = fused_sweep_smem<T, TX>(HAS_C);
-  cudaFuncSetAttribute(k_sweep_rb_cart<T, TX, HAS_C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_sweep_rb<T, G, TX, HAS_C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_rb_cart<T, TX, HAS_C>, RB_THREADS, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_rb<T, G, TX, HAS_C>, RB_THREADS, smem) !=
           cudaSuccess ||
       nb < 1)
     nb = 1;
-  FusedCapacity<T>::blocks[TX == 128][HAS_C] = nb * sms;
+  FusedCapacity<T>::blocks[G][TX == 128][HAS_C] = nb * sms;
+}
+
+template <typename T, int G>
+static void set_fused_capacity_g(int sms) {
+  set_fused_capacity<T, G, 64, false>(sms);
+  set_fused_capacity<T, G, 64, true>(sms);
+  if constexpr (sizeof(T) == 4) {
+    set_fused_capacity<T, G, 128, false>(sms);
+    set_fused_capacity<T, G, 128, true>(sms);
+  }
 }
 
 template <typename T>
@@ -938,12 +1006,9 @@ void init_fused_sweep_attributes() {
   int d = 0, sms = 0;
   cudaGetDevice(&d);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms < 1) sms = 1;
-  set_fused_capacity<T, 64, false>(sms);
-  set_fused_capacity<T, 64, true>(sms);
-  if constexpr (sizeof(T) == 4) {
-    set_fused_capacity<T, 128, false>(sms);
-    set_fused_capacity<T, 128, true>(sms);
-  }
+  set_fused_capacity_g<T, CART>(sms);
+  set_fused_capacity_g<T, CYL>(sms);
+  set_fused_capacity_g<T, SPH>(sms);
 }
 
 // Planes per block: each block re-relaxes two red planes beyond its chunk,
@@ -952,7 +1017,7 @@ void init_fused_sweep_attributes() {
 template <typename T>
 int fused_sweep_chunk(const LevelView<T>& L, int tx, bool with_c) {
   const long cols = (long)cdiv(L.n0, tx) * cdiv(L.n1, RB_TY);
-  const long cap = FusedCapacity<T>::blocks[tx == 128][with_c];
+  const long cap = FusedCapacity<T>::blocks[L.geom][tx == 128][with_c];
   int best = 8;
   long best_cost = -1;
   for (int zc = 4; zc <= 64; zc *= 2) {
@@ -966,28 +1031,38 @@ int fused_sweep_chunk(const LevelView<T>& L, int tx, bool with_c) {
   return best;
 }
 
-template <typename T, int TX>
+template <typename T, int G, int TX>
 static void launch_rb(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
   const int zc = fused_sweep_chunk(L, TX, c != nullptr);
   dim3 g(cdiv(L.n0, TX), cdiv(L.n1, RB_TY), cdiv(L.n2, zc));
   if (c)
-    launch_k(k_sweep_rb_cart<T, TX, true>, g, RB_THREADS, fused_sweep_smem<T, TX>(true), st, L, uin, uout, f, c, zc);
+    launch_k(k_sweep_rb<T, G, TX, true>, g, RB_THREADS, fused_sweep_smem<T, TX>(true), st, L, uin, uout, f, c, zc);
   else
-    launch_k(k_sweep_rb_cart<T, TX, false>, g, RB_THREADS, fused_sweep_smem<T, TX>(false), st, L, uin, uout, f, nullptr,
-                                                                                         zc);
+    launch_k(k_sweep_rb<T, G, TX, false>, g, RB_THREADS, fused_sweep_smem<T, TX>(false), st, L, uin, uout, f,
+             nullptr, zc);
+}
+
+template <typename T, int G>
+static void launch_rb_g(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (fused_sweep_tx(L) == 128) {
+      launch_rb<T, G, 128>(L, uin, uout, f, c, st);
+      return;
+    }
+  }
+  launch_rb<T, G, 64>(L, uin, uout, f, c, st);
 }
 
 template <typename T>
 bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
   if (!fused_sweep_applies(L)) return false;
   count_launch();
-  if constexpr (sizeof(T) == 4) {
-    if (fused_sweep_tx(L) == 128) {
-      launch_rb<T, 128>(L, uin, uout, f, c, st);
-      return true;
-    }
-  }
-  launch_rb<T, 64>(L, uin, uout, f, c, st);
+  if (L.geom == CART)
+    launch_rb_g<T, CART>(L, uin, uout, f, c, st);
+  else if (L.geom == CYL)
+    launch_rb_g<T, CYL>(L, uin, uout, f, c, st);
+  else
+    launch_rb_g<T, SPH>(L, uin, uout, f, c, st);
   return true;
 }
 
