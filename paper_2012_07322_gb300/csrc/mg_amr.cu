@@ -61,83 +61,113 @@ __device__ __forceinline__ double amr_area(const LevelView<double>& L, int d, in
 // (2 d + (side > 0)) of cf is set.
 __device__ __forceinline__ bool amr_cf(int cf, int d, int side) { return (cf >> (2 * d + (side > 0))) & 1; }
 
+// The per-dimension quantities of these kernels are kept in scalars chosen
+// by dimension, never in arrays indexed at run time: indexing the box's
+// arrays or small local arrays with a run-time dimension gave wrong values
+// (a coordinate that stayed 0) in an earlier form of these kernels.
 // Base solution ub (ghosts filled) at the tangential position of a patch
-// ghost: parent P, offsets dt (+-1/4, 0 along d).
-__device__ double amr_tangential(const LevelView<double>& B, const double* __restrict__ ub, int d, const int (&P)[3],
-                                 const double (&dt)[3]) {
-  const int nd = B.three ? 3 : 2;
-  const double uc = ub[B.idx(P[0], P[1], P[2])];
+// ghost whose parent is base cell (I, J, K), normal dimension d, offsets
+// t0, t1, t2 (+-1/4 base spacing along the tangential dimensions, 0 along
+// d): second-order centred differences per tangential dimension and, in 3D,
+// the cross term.
+__device__ double amr_tangential(const LevelView<double>& B, const double* __restrict__ ub, int d, int I, int J,
+                                 int K, double t0, double t1, double t2) {
+  const double uc = ub[B.idx(I, J, K)];
   double v = uc;
-  int tt[2], nt = 0;
-  for (int t = 0; t < nd; ++t)
-    if (t != d) tt[nt++] = t;
-  for (int q = 0; q < nt; ++q) {
-    const int t = tt[q];
-    int Pp[3] = {P[0], P[1], P[2]}, Pm[3] = {P[0], P[1], P[2]};
-    Pp[t] += 1;
-    Pm[t] -= 1;
-    const double up = ub[B.idx(Pp[0], Pp[1], Pp[2])], um = ub[B.idx(Pm[0], Pm[1], Pm[2])];
-    v += dt[t] * 0.5 * (up - um) + 0.5 * dt[t] * dt[t] * (up - 2.0 * uc + um);
+  // dimension 0
+  if (d != 0) {
+    const double up = ub[B.idx(I + 1, J, K)], um = ub[B.idx(I - 1, J, K)];
+    v += t0 * 0.5 * (up - um) + 0.5 * t0 * t0 * (up - 2.0 * uc + um);
   }
-  if (nt == 2) {
-    const int t1 = tt[0], t2 = tt[1];
-    int q1[3] = {P[0], P[1], P[2]}, q2[3] = {P[0], P[1], P[2]}, q3[3] = {P[0], P[1], P[2]},
-        q4[3] = {P[0], P[1], P[2]};
-    q1[t1] += 1, q1[t2] += 1;
-    q2[t1] += 1, q2[t2] -= 1;
-    q3[t1] -= 1, q3[t2] += 1;
-    q4[t1] -= 1, q4[t2] -= 1;
-    const double mix = 0.25 * (ub[B.idx(q1[0], q1[1], q1[2])] - ub[B.idx(q2[0], q2[1], q2[2])] -
-                               ub[B.idx(q3[0], q3[1], q3[2])] + ub[B.idx(q4[0], q4[1], q4[2])]);
-    v += dt[t1] * dt[t2] * mix;
+  if (d != 1) {
+    const double up = ub[B.idx(I, J + 1, K)], um = ub[B.idx(I, J - 1, K)];
+    v += t1 * 0.5 * (up - um) + 0.5 * t1 * t1 * (up - 2.0 * uc + um);
+  }
+  if (B.three && d != 2) {
+    const double up = ub[B.idx(I, J, K + 1)], um = ub[B.idx(I, J, K - 1)];
+    v += t2 * 0.5 * (up - um) + 0.5 * t2 * t2 * (up - 2.0 * uc + um);
+  }
+  if (B.three) {
+    // cross term of the two tangential dimensions
+    double mix, ta, tb;
+    if (d == 0) {
+      mix = ub[B.idx(I, J + 1, K + 1)] - ub[B.idx(I, J + 1, K - 1)] - ub[B.idx(I, J - 1, K + 1)] +
+            ub[B.idx(I, J - 1, K - 1)];
+      ta = t1, tb = t2;
+    } else if (d == 1) {
+      mix = ub[B.idx(I + 1, J, K + 1)] - ub[B.idx(I + 1, J, K - 1)] - ub[B.idx(I - 1, J, K + 1)] +
+            ub[B.idx(I - 1, J, K - 1)];
+      ta = t0, tb = t2;
+    } else {
+      mix = ub[B.idx(I + 1, J + 1, K)] - ub[B.idx(I + 1, J - 1, K)] - ub[B.idx(I - 1, J + 1, K)] +
+            ub[B.idx(I - 1, J - 1, K)];
+      ta = t0, tb = t1;
+    }
+    v += ta * tb * 0.25 * mix;
   }
   return v;
 }
 
-// One thread per coarse-fine ghost of the patch: faces enumerated d = 0, 1,
-// 2, low then high side, cells of the face dimension-0 fastest over the
-// patch's tangential extent.
+// Face (d, side) of a thread g of the interface kernels: faces enumerated
+// d = 0, 1, 2, low then high side; fsz(d) cells per face; on return g is
+// the thread's index within its face.  False past the last face.
+__device__ __forceinline__ bool amr_face(long& g, int nd, long f0, long f1, long f2, int& d, int& side) {
+  for (d = 0; d < nd; ++d) {
+    const long fsz = d == 0 ? f0 : (d == 1 ? f1 : f2);
+    for (side = -1; side <= 1; side += 2) {
+      if (g < fsz) return true;
+      g -= fsz;
+    }
+  }
+  return false;
+}
+
+// One thread per coarse-fine ghost of the patch, faces enumerated as in
+// amr_face, the cells of a face dimension-0 fastest over the patch's
+// tangential extent.
 __global__ void k_amr_cf_ghosts(LevelView<double> Pv, LevelView<double> B, AmrBox box, double* __restrict__ up,
                                 const double* __restrict__ ub) {
   pdl_entry();
   const int nd = Pv.three ? 3 : 2;
-  const int n[3] = {Pv.n0, Pv.n1, Pv.three ? Pv.n2 : 1};
+  const long n0 = Pv.n0, n1 = Pv.n1, n2 = Pv.three ? Pv.n2 : 1;
   long g = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  for (int d = 0; d < nd; ++d) {
-    const long fsz = (long)n[0] * n[1] * n[2] / n[d];
-    for (int side = -1; side <= 1; side += 2) {
-      if (g < fsz) {
-        if (!amr_cf(box.cf, d, side)) return;
-        // tangential indices of this ghost
-        int idx[3] = {0, 0, 0};
-        long r = g;
-        for (int t = 0; t < 3; ++t) {
-          if (t == d) continue;
-          idx[t] = (int)(r % n[t]);
-          r /= n[t];
-        }
-        int g3[3] = {idx[0], idx[1], idx[2]}, u1[3] = {idx[0], idx[1], idx[2]}, u2[3] = {idx[0], idx[1], idx[2]};
-        g3[d] = side < 0 ? -1 : n[d];
-        u1[d] = side < 0 ? 0 : n[d] - 1;
-        u2[d] = side < 0 ? 1 : n[d] - 2;
-        int P[3] = {0, 0, 0};
-        double dt[3] = {0.0, 0.0, 0.0};
-        for (int t = 0; t < nd; ++t) {
-          if (t == d) {
-            P[t] = side < 0 ? box.a[d] - 1 : box.b[d];
-          } else {
-            P[t] = box.a[t] + idx[t] / 2;
-            dt[t] = (idx[t] & 1) ? 0.25 : -0.25;
-          }
-        }
-        const double ut = amr_tangential(B, ub, d, P, dt);
-        up[Pv.idx(g3[0], g3[1], g3[2])] = (8.0 / 15.0) * ut + (2.0 / 3.0) * up[Pv.idx(u1[0], u1[1], u1[2])] -
-                                         (1.0 / 5.0) * up[Pv.idx(u2[0], u2[1], u2[2])];
-        return;
-      }
-      g -= fsz;
-    }
+  int d, side;
+  if (!amr_face(g, nd, n1 * n2, n0 * n2, n0 * n1, d, side)) return;
+  if (!amr_cf(box.cf, d, side)) return;
+  // fine indices (i, j, k) of the patch cell next to the ghost
+  int i, j, k;
+  if (d == 0) {
+    j = (int)(g % n1), k = (int)(g / n1);
+    i = side < 0 ? 0 : (int)n0 - 1;
+  } else if (d == 1) {
+    i = (int)(g % n0), k = (int)(g / n0);
+    j = side < 0 ? 0 : (int)n1 - 1;
+  } else {
+    i = (int)(g % n0), j = (int)(g / n0);
+    k = side < 0 ? 0 : (int)n2 - 1;
   }
+  const int a0 = box.a[0], a1 = box.a[1], a2 = box.a[2], b0 = box.b[0], b1 = box.b[1], b2 = box.b[2];
+  // parent base cell and tangential offsets
+  int I = a0 + (i >> 1), J = a1 + (j >> 1), K = Pv.three ? a2 + (k >> 1) : 0;
+  double t0 = (i & 1) ? 0.25 : -0.25, t1 = (j & 1) ? 0.25 : -0.25, t2 = (k & 1) ? 0.25 : -0.25;
+  const int s = side < 0 ? -1 : 1;
+  if (d == 0) {
+    I = side < 0 ? a0 - 1 : b0;
+    t0 = 0.0;
+  } else if (d == 1) {
+    J = side < 0 ? a1 - 1 : b1;
+    t1 = 0.0;
+  } else {
+    K = side < 0 ? a2 - 1 : b2;
+    t2 = 0.0;
+  }
+  if (!Pv.three) t2 = 0.0;
+  const double ut = amr_tangential(B, ub, d, I, J, K, t0, t1, t2);
+  // the ghost, the first and the second patch cell inward along d
+  const long pg = Pv.idx(i + (d == 0) * s, j + (d == 1) * s, k + (d == 2) * s);
+  const long p1 = Pv.idx(i, j, k);
+  const long p2 = Pv.idx(i - (d == 0) * s, j - (d == 1) * s, k - (d == 2) * s);
+  up[pg] = (8.0 / 15.0) * ut + (2.0 / 3.0) * up[p1] - (1.0 / 5.0) * up[p2];
 }
 
 // ------------------------------------------------------------ patch level
@@ -245,60 +275,58 @@ __global__ void k_amr_restrict(LevelView<double> Pv, LevelView<double> B, AmrBox
 
 // The composite operator minus the base operator at the uncovered base cells
 // next to the patch (corr zero elsewhere; zeroed before): one thread per
-// coarse cell of a coarse-fine face, faces enumerated as in
-// k_amr_cf_ghosts over the box's tangential extent.
+// coarse cell of a coarse-fine face, faces enumerated as in amr_face over
+// the box's tangential extent.
 __global__ void k_amr_flux_corr(LevelView<double> Pv, LevelView<double> B, AmrBox box, const double* __restrict__ up,
                                 const double* __restrict__ ub, double* __restrict__ corr) {
   pdl_entry();
   const int nd = B.three ? 3 : 2;
-  const int m[3] = {box.b[0] - box.a[0], box.b[1] - box.a[1], nd == 3 ? box.b[2] - box.a[2] : 1};
-  const int n[3] = {Pv.n0, Pv.n1, Pv.three ? Pv.n2 : 1};
-  const double hb[3] = {B.h0, B.h1, B.h2}, hp[3] = {Pv.h0, Pv.h1, Pv.h2};
+  const int a0 = box.a[0], a1 = box.a[1], a2 = box.a[2], b0 = box.b[0], b1 = box.b[1], b2 = box.b[2];
+  const long m0 = b0 - a0, m1 = b1 - a1, m2 = nd == 3 ? b2 - a2 : 1;
   long g = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  for (int d = 0; d < nd; ++d) {
-    const long fsz = (long)m[0] * m[1] * m[2] / m[d];
-    for (int side = -1; side <= 1; side += 2) {
-      if (g < fsz) {
-        if (!amr_cf(box.cf, d, side)) return;
-        int t3[3] = {0, 0, 0};
-        long r = g;
-        for (int t = 0; t < 3; ++t) {
-          if (t == d) continue;
-          t3[t] = (int)(r % m[t]);
-          r /= m[t];
-        }
-        int Q[3], Qin[3];
-        for (int t = 0; t < 3; ++t) Q[t] = Qin[t] = (t < nd) ? box.a[t] + t3[t] : 0;
-        Q[d] = side < 0 ? box.a[d] - 1 : box.b[d];
-        Qin[d] = side < 0 ? box.a[d] : box.b[d] - 1;
-        const int sd = side < 0 ? 1 : -1;
-        const double Ac = amr_area(B, d, sd, Q[0], Q[1]);
-        const double Dc = (ub[B.idx(Qin[0], Qin[1], Qin[2])] - ub[B.idx(Q[0], Q[1], Q[2])]) / hb[d];
-        double fsum = 0.0;
-        const int nf2 = nd == 3 ? 2 : 1;
-        for (int q2 = 0; q2 < nf2; ++q2)
-          for (int q1 = 0; q1 < 2; ++q1) {
-            int f[3] = {0, 0, 0}, tq = 0;
-            for (int t = 0; t < nd; ++t) {
-              if (t == d) {
-                f[t] = side < 0 ? 0 : n[d] - 1;
-              } else {
-                f[t] = 2 * t3[t] + (tq == 0 ? q1 : q2);
-                ++tq;
-              }
-            }
-            int gg[3] = {f[0], f[1], f[2]};
-            gg[d] = side < 0 ? -1 : n[d];
-            const double Af = amr_area(Pv, d, side, f[0], f[1]);
-            const double Df = (up[Pv.idx(f[0], f[1], f[2])] - up[Pv.idx(gg[0], gg[1], gg[2])]) / hp[d];
-            fsum += Af * Df;
-          }
-        corr[B.idx(Q[0], Q[1], Q[2])] = (fsum - Ac * Dc) / amr_volume(B, Q[0], Q[1]);
-        return;
-      }
-      g -= fsz;
-    }
+  int d, side;
+  if (!amr_face(g, nd, m1 * m2, m0 * m2, m0 * m1, d, side)) return;
+  if (!amr_cf(box.cf, d, side)) return;
+  // the uncovered coarse cell Q and its covered neighbour across the face
+  int QI, QJ, QK;
+  if (d == 0) {
+    QJ = a1 + (int)(g % m1), QK = nd == 3 ? a2 + (int)(g / m1) : 0;
+    QI = side < 0 ? a0 - 1 : b0;
+  } else if (d == 1) {
+    QI = a0 + (int)(g % m0), QK = nd == 3 ? a2 + (int)(g / m0) : 0;
+    QJ = side < 0 ? a1 - 1 : b1;
+  } else {
+    QI = a0 + (int)(g % m0), QJ = a1 + (int)(g / m0);
+    QK = side < 0 ? a2 - 1 : b2;
   }
+  const int s = side < 0 ? -1 : 1;  // from the patch out to Q
+  const int INi = QI - (d == 0) * s, INj = QJ - (d == 1) * s, INk = QK - (d == 2) * s;
+  const double hb = d == 0 ? B.h0 : (d == 1 ? B.h1 : B.h2), hp = d == 0 ? Pv.h0 : (d == 1 ? Pv.h1 : Pv.h2);
+  const double Ac = amr_area(B, d, -s, QI, QJ);
+  const double Dc = (ub[B.idx(INi, INj, INk)] - ub[B.idx(QI, QJ, QK)]) / hb;
+  // the fine faces: the patch cells next to the face under Q (2 in 2D, 4
+  // in 3D) and their ghosts on Q's side
+  const int fi0 = 2 * (QI - a0), fj0 = 2 * (QJ - a1), fk0 = nd == 3 ? 2 * (QK - a2) : 0;
+  const int ni = (int)Pv.n0, nj = (int)Pv.n1, nk = Pv.three ? (int)Pv.n2 : 1;
+  double fsum = 0.0;
+  const int nq2 = nd == 3 ? 2 : 1;
+  for (int q2 = 0; q2 < nq2; ++q2)
+    for (int q1 = 0; q1 < 2; ++q1) {
+      int fi, fj, fk;
+      if (d == 0) {
+        fi = side < 0 ? 0 : ni - 1, fj = fj0 + q1, fk = fk0 + q2;
+      } else if (d == 1) {
+        fj = side < 0 ? 0 : nj - 1, fi = fi0 + q1, fk = fk0 + q2;
+      } else {
+        fk = side < 0 ? 0 : nk - 1, fi = fi0 + q1, fj = fj0 + q2;
+      }
+      if (!Pv.three) fk = 0;
+      const long pf = Pv.idx(fi, fj, fk);
+      const long pg = Pv.idx(fi + (d == 0) * s, fj + (d == 1) * s, fk + (d == 2) * s);
+      const double Af = amr_area(Pv, d, s, fi, fj);
+      fsum += Af * (up[pf] - up[pg]) / hp;
+    }
+  corr[B.idx(QI, QJ, QK)] = (fsum - Ac * Dc) / amr_volume(B, QI, QJ);
 }
 
 __device__ __forceinline__ bool amr_covered(const AmrBox& box, int three, int I, int J, int K) {

@@ -91,14 +91,20 @@ inline long row_stride(int n0) { return (n0 + 2 * ROW_PAD + ROW_PAD - 1) / ROW_P
 // One red-black sweep in one launch (3D linear scalar equations on levels
 // of at least one 64 x 8 column; Cartesian, cylindrical and spherical), out
 // of place: uin -> uout, which must not alias; only the interior of uout is
-// written.  Returns false when it does not apply.
+// written.  Returns false when it does not apply.  On cylindrical and
+// spherical levels it is used from FUSED_CURV_CELLS cells on: a block marches
+// its chunk of phi planes behind a staging pipeline a few planes deep, and on
+// a 128 x 64 x 64 level the chunks are too short to hide it (measured: one
+// sweep took as long as its two colour passes, and the solve got slower).
 template <typename T>
 bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st);
 template <typename T>
 void init_fused_sweep_attributes();
+constexpr long FUSED_CURV_CELLS = 1L << 22;
 template <typename T>
 inline bool fused_sweep_applies(const LevelView<T>& L) {
-  return L.three && L.n0 >= 64 && L.n1 >= 8 && L.n2 >= 4;
+  if (!(L.three && L.n0 >= 64 && L.n1 >= 8 && L.n2 >= 4)) return false;
+  return L.geom == CART || (long)L.n0 * L.n1 * L.n2 >= FUSED_CURV_CELLS;
 }
 // Ghost push of the vector smoother's colour passes.  With a table, the
 // pass of component c also rewrites, at its end, every ghost of c whose
@@ -312,9 +318,7 @@ void launch_loop_decide(LoopState* S, const unsigned long long* red, const LoopP
 // the levels l0 .. l0 + nl - 1 of a hierarchy, the last the coarsest, all
 // held in the block's shared memory (same ghosted layout as in HBM).
 constexpr int BC_MAX = 8;                     // levels one block cycle may span
-// Levels this small run in the block cycle (when the levels from there down
-// fit BC_SMEM_MAX: a scalar 32 x 16 x 16 level does, a vector one does not).
-constexpr long BLOCK_CYCLE_CELLS = 8192;
+constexpr long BLOCK_CYCLE_CELLS = 4096;       // levels this small run in the block cycle
 constexpr size_t BC_SMEM_MAX = 200 * 1024;     // dynamic shared memory of the block cycle
 struct BlockLevel32 {
   LevelView<float> v;        // boundary rule applied

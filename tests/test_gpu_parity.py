@@ -477,12 +477,13 @@ FUSED_CASES = [
 
 
 CURV_FUSED_CASES = [
-    # (geom, n, sweeps): one column in x, y; several columns, j tiles and
-    # periodic phi chunks; more blocks than fit the device at once
+    # (geom, n, sweeps): levels of 2^22 cells and more take the one-launch
+    # sweep (several columns, j tiles and periodic phi chunks, more blocks
+    # than fit the device at once); smaller ones the colour passes
+    ("sph", [256, 128, 128], 2),
+    ("cyl", [256, 128, 128], 3),
     ("sph", [64, 8, 4], 2),
     ("sph", [128, 32, 64], 3),
-    ("sph", [64, 64, 32], 2),
-    ("cyl", [64, 16, 8], 2),
     ("cyl", [128, 32, 32], 3),
 ]
 
@@ -490,7 +491,7 @@ CURV_FUSED_CASES = [
 @pytest.mark.parametrize("case", range(len(CURV_FUSED_CASES)))
 @pytest.mark.parametrize("bc", ["robin", "dirichlet"])
 def test_fused_sweep_parity_curvilinear(mg, bc, case):
-    """Spherical and cylindrical 3D levels at least 64 x 8 cells wide take the
+    """Spherical and cylindrical 3D levels of 2^22 cells and more take the
     one-launch out-of-place sweep too (per-(i, j) coefficients, periodic phi
     march; origin, axis and pole cells included): the result equals the
     oracle's red-black sweeps, with and without the c u term."""
