@@ -1228,42 +1228,76 @@ int build_loop_graph(mg_hierarchy* H, const Eq& e, int key, double* ax, double* 
   Level& L0 = H->L[0];
   const int m = d.accel_depth;
   const long stride = L0.ng;
-  cudaGraph_t top = nullptr, pre = nullptr, body = nullptr;
+  cudaGraph_t top = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle hc;
-  auto cleanup = [&]() {
-    if (pre) cudaGraphDestroy(pre);
-    if (body) cudaGraphDestroy(body);
-    if (top) cudaGraphDestroy(top);
-  };
   if (cudaGraphCreate(&top, 0) != cudaSuccess ||
       cudaGraphConditionalHandleCreate(&hc, top, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
     cudaGetLastError();
-    cleanup();
+    if (top) cudaGraphDestroy(top);
     return LOOP_UNSUPPORTED;
   }
   const LoopParams P{d.tol, d.max_cycles, d.stall_window, m};
   const int64_t u0 = H->updates;
-  // before the loop: the mixing's starting iterate, the initial residual
+  // The kernels are captured straight into the graph and into the while
+  // node's body (no child-graph nodes), so the programmatic edges between
+  // consecutive kernels stay.
+  auto abort_capture = [&]() {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(H->st, &g);
+    cudaGetLastError();
+    cudaGraphDestroy(top);
+  };
+  // before the loop: the mixing's starting iterate, the initial residual,
+  // the first decision; then the while node after them
   const unsigned long long l0 = launch_count();
-  CK(cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
+  if (cudaStreamBeginCaptureToGraph(H->st, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(top);
+    return LOOP_UNSUPPORTED;
+  }
   if (m > 0)
     for (int c = 0; c < e.ncomp; ++c)
       cudaMemcpyAsync(ax + (long)c * stride, L0.u[c], sizeof(double) * L0.ng, cudaMemcpyDeviceToDevice, H->st);
   int st = finest_residual(H, e);
   launch_loop_decide(H->d_loop, H->d_red, P, hc, 1, H->st);
-  cudaError_t ce = cudaStreamEndCapture(H->st, &pre);
   const unsigned long long lpre = launch_count() - l0;
-  if (st || ce != cudaSuccess) {
-    cudaGetLastError();
-    cleanup();
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphNode_t ncond;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (st || cudaStreamGetCaptureInfo(H->st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess ||
+      cudaGraphAddNode(&ncond, top, deps, nullptr, ndeps, &cp) != cudaSuccess ||
+      cudaStreamUpdateCaptureDependencies(H->st, &ncond, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+          cudaSuccess) {
+    abort_capture();
     count_launch(-(int)lpre);
     return st ? st : LOOP_UNSUPPORTED;
   }
-  // one cycle
+  cudaGraph_t done = nullptr;
+  if (cudaStreamEndCapture(H->st, &done) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(top);
+    count_launch(-(int)lpre);
+    return LOOP_UNSUPPORTED;
+  }
+  // one cycle, captured into the body of the while node
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
   const unsigned long long l1 = launch_count();
   const int64_t u1 = H->updates;
-  CK(cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
+  if (cudaStreamBeginCaptureToGraph(H->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(top);
+    count_launch(-(int)lpre);
+    return LOOP_UNSUPPORTED;
+  }
   st = cycle_map(H, e);
   if (m > 0) {
     const AACols none{};
@@ -1282,31 +1316,18 @@ int build_loop_graph(mg_hierarchy* H, const Eq& e, int key, double* ax, double* 
   }
   if (!st) st = finest_residual(H, e);
   launch_loop_decide(H->d_loop, H->d_red, P, hc, 0, H->st);
-  ce = cudaStreamEndCapture(H->st, &body);
+  cudaGraph_t body_out = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(H->st, &body_out);
   const unsigned long long lbody = launch_count() - l1;
   const int64_t ubody = H->updates - u1;
   H->updates = u0;
   count_launch(-(int)(lpre + lbody));  // counted per run below
-  if (st || ce != cudaSuccess) {
+  if (st || ce != cudaSuccess || cudaGraphInstantiate(&exec, top, 0) != cudaSuccess) {
     cudaGetLastError();
-    cleanup();
+    cudaGraphDestroy(top);
     return st ? st : LOOP_UNSUPPORTED;
   }
-  cudaGraphNode_t npre, ncond, nbody;
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = hc;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  if (cudaGraphAddChildGraphNode(&npre, top, nullptr, 0, pre) != cudaSuccess ||
-      cudaGraphAddNode(&ncond, top, &npre, nullptr, 1, &cp) != cudaSuccess ||
-      cudaGraphAddChildGraphNode(&nbody, cp.conditional.phGraph_out[0], nullptr, 0, body) != cudaSuccess ||
-      cudaGraphInstantiate(&exec, top, 0) != cudaSuccess) {
-    cudaGetLastError();
-    cleanup();
-    return LOOP_UNSUPPORTED;
-  }
-  cleanup();
+  cudaGraphDestroy(top);
   H->loops.push_back(mg_hierarchy::LoopGraph{key, exec, ubody, lpre, lbody});
   return MG_OK;
 }

@@ -444,7 +444,27 @@ class Server:
         except Exception:
             pass
 
+    @staticmethod
+    def _check_shapes(desc, named):
+        """The request's arrays must have the grid's shape and dtype: the
+        server reads and writes them through raw device pointers."""
+        import torch
+        want = tuple(desc.n[k] for k in reversed(range(desc.ndim)))
+        for name, t in named:
+            if t is None:
+                continue
+            if not isinstance(t, torch.Tensor) or not t.is_cuda:
+                raise ValueError("%s must be a CUDA tensor" % name)
+            if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != want:
+                raise ValueError("%s must be contiguous float64 of shape %s, got %s %s"
+                                 % (name, want, t.dtype, tuple(t.shape)))
+
     def submit_cfc(self, desc, U, S, Si, psi, alpha, beta, X, psi_only=False, stream_id=0, allow=(MG_OK,)):
+        named = [("U", U), ("psi", psi)]
+        if not psi_only:
+            named += [("S", S), ("alpha", alpha)] + [("Si[%d]" % k, Si[k]) for k in range(3)]
+            named += [("beta[%d]" % k, beta[k]) for k in range(3)] + [("X[%d]" % k, X[k]) for k in range(3)]
+        self._check_shapes(desc, named)
         r = mg_request()
         r.desc = desc
         r.kind = MG_REQ_CFC
@@ -462,6 +482,7 @@ class Server:
         return self._submit(r, (U, S, Si, psi, alpha, beta, X), allow)
 
     def submit_divb(self, desc, B, phi=None, allow=(MG_OK,)):
+        self._check_shapes(desc, [("B[%d]" % k, b) for k, b in enumerate(B)] + [("phi", phi)])
         r = mg_request()
         r.desc = desc
         r.kind = MG_REQ_DIVB

@@ -239,3 +239,19 @@ def test_resident_solutions_are_evicted_before_waiting(mg):
     for x, y in zip([outs[2][0], outs[2][1]] + outs[2][2] + outs[2][3], [f[0], f[1]] + f[2] + f[3]):
         assert torch.equal(x, y)
 
+
+
+def test_requests_with_wrong_shapes_are_refused(mg):
+    """The server reads and writes a request's arrays through raw device
+    pointers: the binding refuses arrays whose shape differs from the grid's
+    before anything is queued."""
+    args, U, S, Si = cfc_case("sph2d", 51)
+    d = desc_of(mg, args)
+    srv = mg.Server(hbm_budget=1 << 30, max_slots=1, max_queue=4)
+    small = fields((16, 32))
+    with pytest.raises(ValueError):
+        srv.submit_cfc(d, dev(U), dev(S), [dev(x) for x in Si], *small)
+    with pytest.raises(ValueError):
+        srv.submit_divb(mg.grid_desc("cart", [16] * 3, [-1.0] * 3, [1.0] * 3),
+                        [torch.zeros((8, 16, 16), dtype=torch.float64, device="cuda")] * 3)
+    srv.close()
