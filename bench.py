@@ -253,13 +253,22 @@ def divb_measurement(mg, torch, stream, steps, precision, peak, variant="compact
                          "algorithmic_bytes_per_launch": bpl, "launches": nl}}
 
 
-def batch_measurement(mg, torch, count=512, slots=16):
+# Schedules the batch's autotuner tries per shape class (nu1, nu2,
+# accel_depth): the paper's V(2, 2) with mixing depths 16, 8 and none, and
+# V(1, 1) with depth 16.
+BATCH_CANDIDATES = [(2, 2, 16), (2, 2, 8), (2, 2, 0), (1, 1, 16)]
+
+
+def batch_measurement(mg, torch, count=512, slots=16, tune=True):
     """Batched solves: 512 uneven 2D static stars (seed 2; half spherical,
     half cylindrical, 32 grid shapes) submitted at once to worker slots that
     overlap their kernels on the device; hierarchies and CUDA graphs are
-    cached per shape (warmed once), inputs resident in HBM."""
+    cached per shape (warmed once), inputs resident in HBM.  Run with the
+    default schedule (V(2, 2), mixing depth 16) and, with tune, with the
+    schedule the autotuner picked per shape class (tuning time reported
+    apart)."""
     import time
-    from paper_2012_07322_gb300 import inputs
+    from paper_2012_07322_gb300 import autotune, inputs
     batch = inputs.batch_static_stars_2d(count=count, seed=2)
     dev = lambda a: torch.from_numpy(np.array(a, copy=True)).cuda()
     items = []
@@ -274,32 +283,48 @@ def batch_measurement(mg, torch, count=512, slots=16):
         return (psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)],
                 [torch.zeros_like(psi) for _ in range(3)])
 
-    srv = mg.Server(hbm_budget=64 << 30, max_slots=slots, max_queue=2 * count)
-    seen = set()
-    for desc, U, S, Si, g, n in items:  # one solve per shape: hierarchies and graphs
-        if (g, n) in seen:
-            continue
-        seen.add((g, n))
-        srv.wait(srv.submit_cfc(desc, U, S, Si, *fields(U)))
-    outs = [fields(it[1]) for it in items]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tickets = [srv.submit_cfc(desc, U, S, Si, *f) for (desc, U, S, Si, _, _), f in zip(items, outs)]
-    res = [srv.wait(t) for t in tickets]
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    srv.close()
-    lat = sorted(r["latency_ms"] for r in res)
-    ups = sum(sum(r["cfc"][k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta")) for r in res)
-    cyc = [r["cfc"]["psi"]["cycles"] + r["cfc"]["alphapsi"]["cycles"] for r in res]
-    return {"workload": "%d uneven 2D static stars (seed 2): spherical N_r 32..256 x N_theta 16..128, cylindrical "
-                        "N_R 32..256 x N_z 64..512, rho_c ~ U[5e-4, 2e-3], R ~ U[8, 14]; full xCFC system, mixed "
-                        "precision, %d worker slots" % (count, slots),
-            "solves_per_s": count / wall, "wall_ms": wall * 1e3, "cells": cells,
-            "value": ups / wall / 1e9, "unit": UNIT, "p50_ms": lat[len(lat) // 2],
-            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "ok": sum(r["status"] == "ok" for r in res), "shapes": len(seen),
-            "cycles_psi_plus_alphapsi": {"min": min(cyc), "median": sorted(cyc)[len(cyc) // 2], "max": max(cyc)}}
+    def run(descs):
+        srv = mg.Server(hbm_budget=64 << 30, max_slots=slots, max_queue=2 * count)
+        seen = set()
+        for d, (_, U, S, Si, g, n) in zip(descs, items):  # one solve per shape: hierarchies and graphs
+            if (g, n) in seen:
+                continue
+            seen.add((g, n))
+            srv.wait(srv.submit_cfc(d, U, S, Si, *fields(U)))
+        outs = [fields(it[1]) for it in items]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = [srv.submit_cfc(d, U, S, Si, *f) for d, (_, U, S, Si, _, _), f in zip(descs, items, outs)]
+        res = [srv.wait(t) for t in tickets]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = sorted(r["latency_ms"] for r in res)
+        ups = sum(sum(r["cfc"][k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta")) for r in res)
+        cyc = [r["cfc"]["psi"]["cycles"] + r["cfc"]["alphapsi"]["cycles"] for r in res]
+        return {"solves_per_s": count / wall, "wall_ms": wall * 1e3, "value": ups / wall / 1e9, "unit": UNIT,
+                "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "ok": sum(r["status"] == "ok" for r in res), "shapes": len(seen),
+                "cycles_psi_plus_alphapsi": {"min": min(cyc), "median": sorted(cyc)[len(cyc) // 2],
+                                             "max": max(cyc)}}
+
+    out = {"workload": "%d uneven 2D static stars (seed 2): spherical N_r 32..256 x N_theta 16..128, cylindrical "
+                       "N_R 32..256 x N_z 64..512, rho_c ~ U[5e-4, 2e-3], R ~ U[8, 14]; full xCFC system, mixed "
+                       "precision, %d worker slots" % (count, slots), "cells": cells}
+    out["default_schedule"] = run([it[0] for it in items])
+    if tune:
+        t0 = time.perf_counter()
+        table = autotune.tune(mg, torch, [(it[0], (it[1], it[2], it[3])) for it in items],
+                              candidates=BATCH_CANDIDATES, repeats=1)
+        tuning_s = time.perf_counter() - t0
+        tuned = run([autotune.tuned(mg, it[0], table) for it in items])
+        picks = {}
+        for k, e in table.items():
+            key = "nu%d%d_m%d" % (e["nu1"], e["nu2"], e["accel_depth"])
+            picks[key] = picks.get(key, 0) + 1
+        tuned.update({"tuning_s": tuning_s, "schedules_picked": picks})
+        out["autotuned"] = tuned
+    return out
 
 
 # The serving mix: xCFC request kinds (geometry, grid) and their shares of

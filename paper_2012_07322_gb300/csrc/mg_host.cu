@@ -1869,6 +1869,11 @@ void copy_out(mg_hierarchy* H, const double* src, double* dst, double shift = 0.
 
 int gmg::set_last_error(int status, const char* msg) { return fail(status, msg); }
 
+void gmg::hier_set_host_loop(mg_hierarchy* H, bool on) {
+  H->loop_off = on;
+  if (H->sub) H->sub->loop_off = on;
+}
+
 void gmg::hier_set_stream(mg_hierarchy* H, cudaStream_t st) {
   if (H->own_stream || st == nullptr) return;
   H->st = st;

@@ -35,6 +35,12 @@ int set_last_error(int status, const char* msg);
 // Move a hierarchy's work to another stream (serving workers share cached
 // hierarchies; captured graphs are stream-independent).
 void hier_set_stream(mg_hierarchy* h, cudaStream_t st);
+// Run the hierarchy's cycle loops on the host (one stream synchronisation
+// per cycle) instead of as device-side loops.  Device-side loops save the
+// per-cycle round trip of one solve, but several of them on concurrent
+// streams ran slower than host loops: 64 small 2D solves on 16 streams took
+// 304 ms against 181 ms.  The request server's slots therefore use host loops.
+void hier_set_host_loop(mg_hierarchy* h, bool on);
 
 // Count of kernel launches issued by the library (all hierarchies).
 // Up to three field pointers passed by value to a kernel (entries past

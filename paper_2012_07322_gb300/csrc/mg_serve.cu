@@ -186,6 +186,7 @@ mg_hierarchy* acquire(mg_server* S, std::unique_lock<std::mutex>& lk, const mg_g
     *status = st2;
     return nullptr;
   }
+  gmg::hier_set_host_loop(h, true);  // concurrent slots: host cycle loops (see hier_set_host_loop)
   S->cache.push_back(Cached{d, h, need, true, S->clock++});
   return h;
 }
