@@ -327,15 +327,19 @@ def batch_measurement(mg, torch, count=512, slots=16, tune=True):
     return out
 
 
-# The serving mix: xCFC request kinds (geometry, grid) and their shares of
-# the xCFC requests.  The largest is the 3D spherical 128 x 64 x 64 grid:
-# the solver needs power-of-two grids, and 192 x 96 x 96 is not one.
-SERVE_KINDS = [(("sph", [64, 32], [0.0, 0.0], [100.0, np.pi]), 0.30),
-               (("sph", [128, 64], [0.0, 0.0], [100.0, np.pi]), 0.20),
-               (("cyl", [64, 128], [0.0, -100.0], [100.0, 100.0]), 0.20),
+# The serving mix: request kinds of the metric streams (geometry, grid) and
+# their shares.  The largest uniform grid is the 3D spherical 128 x 64 x 64
+# one: the solver needs power-of-two grids, and 192 x 96 x 96 is not one.
+# The "amr" kinds are eq. psi on a two-level composite grid refined 2x for
+# r < r_max / 4 (static stars; the composite path solves the scalar
+# equations); the others the full xCFC system on uniform grids.
+SERVE_KINDS = [(("sph", [64, 32], [0.0, 0.0], [100.0, np.pi]), 0.25),
+               (("sph", [128, 64], [0.0, 0.0], [100.0, np.pi]), 0.15),
+               (("cyl", [64, 128], [0.0, -100.0], [100.0, 100.0]), 0.15),
                (("sph", [32, 16, 16], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.15),
                (("sph", [64, 32, 32], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.10),
-               (("sph", [128, 64, 64], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.05)]
+               (("sph", [128, 64, 64], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.05),
+               (("amr", [64, 32, 32], [0.0, 0.0, 0.0], [100.0, np.pi, 2 * np.pi]), 0.15)]
 SERVE_STREAMS = 24
 SERVE_STEPS = 4   # source variants per stream: consecutive "time steps" of a slowly changing star
 
@@ -384,6 +388,18 @@ def serving_setup(mg, torch, precision):
     for sid in range(SERVE_STREAMS):
         geom, n, lo, hi = SERVE_KINDS[int(rng.choice(len(SERVE_KINDS), p=shares / shares.sum()))][0]
         rho_c, R = rng.uniform(5e-4, 2e-3), rng.uniform(8.0, 14.0)
+        if geom == "amr":
+            # base grid and the patch over base cells r < r_max / 4
+            box = ([0, 0, 0], [n[0] // 4, n[1], n[2]])
+            steps = []
+            for t in range(SERVE_STEPS):
+                rc = rho_c * (1.0 + 0.002 * t)
+                U = inputs.static_polytrope_sph3d(tuple(n), 100.0, rc, R)
+                Up = inputs.static_polytrope_sph3d((n[0] // 2, 2 * n[1], 2 * n[2]), 25.0, rc, R)
+                steps.append((dev(U), dev(np.zeros_like(U)), dev(Up), dev(np.zeros_like(Up))))
+            desc = mg.grid_desc("sph", n, lo, hi, tol=TOL, max_cycles=800, accel_depth=16, stall_window=0)
+            streams.append((desc, steps, "amr_sph%s" % "x".join(map(str, n)), box))
+            continue
         steps = []
         for t in range(SERVE_STEPS):
             rc = rho_c * (1.0 + 0.002 * t)
@@ -396,7 +412,7 @@ def serving_setup(mg, torch, precision):
             steps.append((dev(U), dev(S), [dev(x) for x in Si]))
         desc = mg.grid_desc(geom, n, lo, hi, precision=precision, tol=TOL, max_cycles=800, accel_depth=16,
                             stall_window=0)
-        streams.append((desc, steps, "%s%s" % (geom, "x".join(map(str, n)))))
+        streams.append((desc, steps, "%s%s" % (geom, "x".join(map(str, n))), None))
     divbs = []
     for n in (32, 64):
         B = inputs.divb_field(n=n, n_modes=16, k_max=6)
@@ -433,10 +449,17 @@ def serving_measurement(mg, torch, precision="mixed", rate=2000.0, n_requests=40
         return (psi, torch.ones_like(psi), [torch.zeros_like(psi) for _ in range(3)],
                 [torch.zeros_like(psi) for _ in range(3)])
 
+    def submit_stream(sid, t):
+        desc, steps, name, box = streams[sid]
+        if box is not None:
+            U, A2, Up, A2p = steps[t % SERVE_STEPS]
+            return srv.submit_amr(desc, box[0], box[1], U, A2, Up, A2p, torch.zeros_like(U), torch.zeros_like(Up))
+        U, S, Si = steps[t % SERVE_STEPS]
+        return srv.submit_cfc(desc, U, S, Si, *fields(U), stream_id=sid + 1)
+
     # warm the hierarchy cache and the resident streams (first time step)
-    for sid, (desc, steps, _) in enumerate(streams):
-        U, S, Si = steps[0]
-        srv.wait(srv.submit_cfc(desc, U, S, Si, *fields(U), stream_id=sid + 1))
+    for sid in range(len(streams)):
+        srv.wait(submit_stream(sid, 0))
     for desc, B in divbs:
         srv.wait(srv.submit_divb(desc, [b.clone() for b in B]))
     torch.cuda.synchronize()
@@ -460,10 +483,9 @@ def serving_measurement(mg, torch, precision="mixed", rate=2000.0, n_requests=40
             for tk in list(pending):
                 collect(tk)
         if kind == "cfc":
-            desc, steps, name = streams[sid]
-            U, S, Si = steps[step_of[sid] % SERVE_STEPS]
+            name = streams[sid][2]
+            tk = submit_stream(sid, step_of[sid])
             step_of[sid] += 1
-            tk = srv.submit_cfc(desc, U, S, Si, *fields(U), stream_id=sid + 1)
         else:
             desc, B = divbs[which]
             name = "divb%d" % desc.n[0]
@@ -490,9 +512,10 @@ def serving_block(mg, torch, gpu_id, sweep):
     the queue grows) and at 60/s (below it), 300 requests each; with sweep,
     1000 requests per point at 15 ... 400/s in mixed precision and 5 ... 80/s
     in FP64, across the capacity of each."""
-    work = ("Poisson arrivals (seed 3): 80%% xCFC on %d warm-started streams (each request the next of %d "
-            "time steps of a rotating star; grids %s), 20%% div-B (32^3, 64^3); continuous admission into "
-            "worker slots; uniform grids stand in for the two-level AMR of the serving workload"
+    work = ("Poisson arrivals (seed 3): 80%% metric requests on %d streams (each request the next of %d "
+            "time steps of a star; xCFC on uniform grids, warm-started, and eq. psi on two-level AMR grids "
+            "refined 2x for r < r_max/4; grids %s), 20%% div-B (32^3, 64^3); continuous admission into "
+            "worker slots"
             % (SERVE_STREAMS, SERVE_STEPS, ", ".join("%s %s" % (k[0], "x".join(map(str, k[1])))
                                                       for k, _ in SERVE_KINDS)))
     if not sweep:

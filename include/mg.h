@@ -353,7 +353,20 @@ int mg_prolong_add(mg_hierarchy* h, int bc, const double* coarse_e, double* fine
  */
 typedef struct mg_server mg_server;
 
-enum { MG_REQ_CFC = 0, MG_REQ_DIVB = 1 };
+enum { MG_REQ_CFC = 0, MG_REQ_DIVB = 1, MG_REQ_AMR = 2 };
+
+/* Arrays of an MG_REQ_AMR request: eq. psi on a two-level composite grid
+ * (mg_solve_scalar_amr with MG_EQ_PSI and the Robin outer condition), the
+ * base grid the request's descriptor, the patch over base cells box_lo <= I
+ * < box_hi.  Deviations u = psi - 1: initial guess in, solution out. */
+typedef struct {
+  int box_lo[3], box_hi[3];
+  const double* A2;        /* base grid A~^2 (U~ is src.U) */
+  const double* Up;        /* patch U~ */
+  const double* A2p;       /* patch A~^2 */
+  double* u;               /* base grid psi - 1 */
+  double* up;              /* patch psi - 1 */
+} mg_amr_arrays;
 
 typedef struct {
   mg_grid_desc desc;       /* grid and solver settings of the request */
@@ -366,6 +379,8 @@ typedef struct {
   double* phi;             /* DIVB: optional potential out */
   void* wait_stream;       /* cudaStream_t whose work queued before mg_submit
                               produced the inputs (NULL: the legacy stream) */
+  mg_amr_arrays amr;       /* AMR: eq. psi on the composite grid (its report
+                              in the result's cfc.eq[1]); no warm start */
 } mg_request;
 
 typedef struct {

@@ -12,6 +12,7 @@
 // resident solutions of streams with nothing in flight, are evicted least
 // recently used first; a request that still cannot fit waits for a running
 // request to release memory, or fails with MG_ERR_OOM when none runs.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -62,9 +63,10 @@ struct Job {
 struct Cached {
   mg_grid_desc desc;
   mg_hierarchy* h;
-  size_t bytes;
+  size_t bytes;  // with the patch of AMR requests
   bool busy;
   uint64_t last;
+  bool amr;      // serves AMR requests (its bytes count their patch)
 };
 
 // Resident solution of a stream id: psi, alpha, beta[3], X[3] back to back.
@@ -97,6 +99,19 @@ struct mg_server {
 };
 
 namespace {
+
+// Device bytes of the refined patch an AMR request adds to its hierarchy
+// (five ghosted arrays of the patch and its tables; an estimate with room
+// for the row padding).
+size_t amr_patch_bytes(const mg_grid_desc& d, const mg_amr_arrays& a) {
+  size_t cells = 1, side = 0;
+  for (int k = 0; k < d.ndim; ++k) {
+    const size_t m = 2 * (size_t)std::max(a.box_hi[k] - a.box_lo[k], 1) + 2 + (k == 0 ? 8 : 0);
+    cells *= m;
+    side += m;
+  }
+  return 5 * sizeof(double) * cells + 16 * sizeof(double) * side + (1 << 16);
+}
 
 // Free the resident solution of one stream id that has nothing in flight
 // (own_id counts as free: its request is the caller), least recently used
@@ -133,15 +148,16 @@ bool evict_warm(mg_server* S, uint64_t own_id) {
 // memory it will release; otherwise a request that cannot fit fails with
 // MG_ERR_OOM.  Returns null on error.
 mg_hierarchy* acquire(mg_server* S, std::unique_lock<std::mutex>& lk, const mg_grid_desc& d, cudaStream_t st,
-                      uint64_t own_id, int* status) {
+                      uint64_t own_id, size_t extra, int* status) {
   size_t need = 0;
   if (mg_hierarchy_bytes(&d, &need) != MG_OK) {
     *status = MG_ERR_INVALID;
     return nullptr;
   }
+  need += extra;  // the patch an AMR request adds, counted with its hierarchy
   for (;;) {
     for (Cached& c : S->cache)
-      if (!c.busy && desc_equal(c.desc, d)) {
+      if (!c.busy && c.amr == (extra > 0) && desc_equal(c.desc, d)) {
         c.busy = true;
         gmg::hier_set_stream(c.h, st);
         return c.h;
@@ -187,7 +203,7 @@ mg_hierarchy* acquire(mg_server* S, std::unique_lock<std::mutex>& lk, const mg_g
     return nullptr;
   }
   gmg::hier_set_host_loop(h, true);  // concurrent slots: host cycle loops (see hier_set_host_loop)
-  S->cache.push_back(Cached{d, h, need, true, S->clock++});
+  S->cache.push_back(Cached{d, h, need, true, S->clock++, extra > 0});
   return h;
 }
 
@@ -218,7 +234,8 @@ void run_job(mg_server* S, Job* J, cudaStream_t st, std::unique_lock<std::mutex>
   int status = MG_OK;
   // the request's inputs were produced on the submitter's stream
   if (J->ready) cudaStreamWaitEvent(st, J->ready, 0);
-  mg_hierarchy* h = acquire(S, lk, r.desc, st, r.stream_id, &status);
+  mg_hierarchy* h = acquire(S, lk, r.desc, st, r.stream_id, r.kind == MG_REQ_AMR ? amr_patch_bytes(r.desc, r.amr) : 0,
+                            &status);
   if (!h) {
     J->res.status = status;
     return;
@@ -241,6 +258,10 @@ void run_job(mg_server* S, Job* J, cudaStream_t st, std::unique_lock<std::mutex>
     mg_cfc_sources src = r.src;
     mg_cfc_fields io = r.io;
     status = mg_solve_cfc(h, &src, &io, r.flags & MG_CFC_PSI_ONLY, &J->res.cfc);
+  } else if (r.kind == MG_REQ_AMR) {
+    const mg_amr_arrays& a = r.amr;
+    status = mg_solve_scalar_amr(h, a.box_lo, a.box_hi, MG_EQ_PSI, MG_BC_ROBIN, r.src.U, a.A2, nullptr, nullptr,
+                                 a.Up, a.A2p, nullptr, nullptr, a.u, a.up, &J->res.cfc.eq[1]);
   } else {
     double* B[3] = {r.B[0], r.B[1], r.B[2]};
     status = mg_clean_divB(h, B, r.phi, 0, &J->res.divb);
@@ -369,10 +390,12 @@ int mg_server_destroy(mg_server* S) {
 
 int mg_submit(mg_server* S, const mg_request* req, uint64_t* ticket) {
   if (!S || !req || !ticket) return gmg::set_last_error(MG_ERR_INVALID, "null argument");
-  if (req->kind != MG_REQ_CFC && req->kind != MG_REQ_DIVB) return gmg::set_last_error(MG_ERR_INVALID, "bad kind");
+  if (req->kind != MG_REQ_CFC && req->kind != MG_REQ_DIVB && req->kind != MG_REQ_AMR)
+    return gmg::set_last_error(MG_ERR_INVALID, "bad kind");
   size_t need = 0;
   int st = mg_hierarchy_bytes(&req->desc, &need);
   if (st) return st;
+  if (req->kind == MG_REQ_AMR) need += amr_patch_bytes(req->desc, req->amr);
   if (need > S->budget) return gmg::set_last_error(MG_ERR_OOM, "request larger than the server's HBM budget");
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) return gmg::set_last_error(MG_ERR_BUSY, "server stopping");

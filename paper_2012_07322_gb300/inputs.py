@@ -42,6 +42,15 @@ def static_polytrope_sph2d(n_r=64, n_theta=32, r_max=100.0, rho_c=1.28e-3, R=10.
     return np.ascontiguousarray(rho + K_POLY * rho * rho)
 
 
+def static_polytrope_sph3d(n=(64, 32, 32), r_max=100.0, rho_c=1.28e-3, R=10.0):
+    """The static star of :func:`static_polytrope_sph2d` on a 3D spherical
+    grid (r in [0, r_max], theta in [0, pi], phi in [0, 2 pi)): U~ = rho +
+    K rho^2, K = 100, shaped (n_phi, n_theta, n_r).  A patch refined over
+    r < r_max' is the same star on the grid of r_max' with its own cells."""
+    U2 = static_polytrope_sph2d(n[0], n[1], r_max, rho_c, R)
+    return np.ascontiguousarray(np.broadcast_to(U2[None, :, :], (n[2], n[1], n[0])))
+
+
 def rotating_polytrope_sph3d(n=(128, 64, 64), r_max=100.0, rho_c=1.28e-3, R=10.0, axis_ratio=0.8,
                              omega=0.02):
     """Uniformly rotating oblate polytrope on a 3D spherical grid.

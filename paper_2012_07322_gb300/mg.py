@@ -38,7 +38,7 @@ EXPORTS = ["mg_strerror", "mg_last_error", "mg_hierarchy_bytes", "mg_create_hier
            "mg_apply_operator", "mg_smooth", "mg_compute_a2", "mg_divergence", "mg_restrict", "mg_prolong_add",
            "mg_kernel_launches", "mg_profile_enable", "mg_profile_read", "mg_divb_norms_noalloc",
            "mg_server_create", "mg_server_destroy", "mg_submit", "mg_poll", "mg_solve_scalar_amr", "mg_apply_amr"]
-MG_REQ_CFC, MG_REQ_DIVB = 0, 1
+MG_REQ_CFC, MG_REQ_DIVB, MG_REQ_AMR = 0, 1, 2
 MG_NOALLOC_MAX_CELLS = 2097152
 PROF_CLASSES = ["smooth64_scalar", "smooth64_vec", "smooth32_scalar", "smooth32_vec", "resid64_scalar",
                 "resid64_vec", "sweep64_fused", "sweep32_fused"]
@@ -78,10 +78,15 @@ class mg_divb_report(C.Structure):
                 ("max_div_after", C.c_double), ("l2_div_after", C.c_double)]
 
 
+class mg_amr_arrays(C.Structure):
+    _fields_ = [("box_lo", C.c_int * 3), ("box_hi", C.c_int * 3), ("A2", C.c_void_p), ("Up", C.c_void_p),
+                ("A2p", C.c_void_p), ("u", C.c_void_p), ("up", C.c_void_p)]
+
+
 class mg_request(C.Structure):
     _fields_ = [("desc", mg_grid_desc), ("kind", C.c_int), ("flags", C.c_int), ("stream_id", C.c_uint64),
                 ("src", mg_cfc_sources), ("io", mg_cfc_fields), ("B", C.c_void_p * 3), ("phi", C.c_void_p),
-                ("wait_stream", C.c_void_p)]
+                ("wait_stream", C.c_void_p), ("amr", mg_amr_arrays)]
 
 
 class mg_result(C.Structure):
@@ -480,6 +485,28 @@ class Server:
                 r.io.beta[k] = beta[k].data_ptr()
                 r.io.X[k] = X[k].data_ptr()
         return self._submit(r, (U, S, Si, psi, alpha, beta, X), allow)
+
+    def submit_amr(self, desc, box_lo, box_hi, U, A2, Up, A2p, u, up, allow=(MG_OK,)):
+        """Eq. psi on the two-level composite grid (deviations u = psi - 1 on
+        the base grid and up on the patch, updated in place)."""
+        nd = desc.ndim
+        pshape = tuple(2 * (box_hi[k] - box_lo[k]) for k in reversed(range(nd)))
+        self._check_shapes(desc, [("U", U), ("A2", A2), ("u", u)])
+        pd = mg_grid_desc()
+        pd.ndim = nd
+        for k in range(3):
+            pd.n[k] = pshape[nd - 1 - k] if k < nd else 1
+        self._check_shapes(pd, [("Up", Up), ("A2p", A2p), ("up", up)])
+        r = mg_request()
+        r.desc = desc
+        r.kind = MG_REQ_AMR
+        r.src.U = U.data_ptr()
+        for k in range(3):
+            r.amr.box_lo[k] = box_lo[k] if k < nd else 0
+            r.amr.box_hi[k] = box_hi[k] if k < nd else 1
+        r.amr.A2, r.amr.Up, r.amr.A2p = A2.data_ptr(), Up.data_ptr(), A2p.data_ptr()
+        r.amr.u, r.amr.up = u.data_ptr(), up.data_ptr()
+        return self._submit(r, (U, A2, Up, A2p, u, up), allow)
 
     def submit_divb(self, desc, B, phi=None, allow=(MG_OK,)):
         self._check_shapes(desc, [("B[%d]" % k, b) for k, b in enumerate(B)] + [("phi", phi)])

@@ -255,3 +255,50 @@ def test_requests_with_wrong_shapes_are_refused(mg):
         srv.submit_divb(mg.grid_desc("cart", [16] * 3, [-1.0] * 3, [1.0] * 3),
                         [torch.zeros((8, 16, 16), dtype=torch.float64, device="cuda")] * 3)
     srv.close()
+
+
+def _amr_case(n=(32, 16, 16), seed=61):
+    """A static star on a 3D spherical grid refined for r < r_max / 4 (the
+    serving workload's two-level AMR): base and patch U~ at their own cell
+    centres."""
+    rng = np.random.default_rng(seed)
+    rho_c, R = rng.uniform(8e-4, 1.6e-3), rng.uniform(8.0, 12.0)
+    a, b = [0, 0, 0], [n[0] // 4, n[1], n[2]]
+    U = inputs.static_polytrope_sph3d(n, 100.0, rho_c, R)
+    Up = inputs.static_polytrope_sph3d((2 * b[0], 2 * n[1], 2 * n[2]), 100.0 / 4, rho_c, R)
+    return a, b, U, Up
+
+
+def test_amr_requests_identical_alone_and_in_the_mix(mg):
+    """Composite-grid requests (eq. psi, patch r < r_max / 4) served beside
+    xCFC requests give bitwise the result of the direct composite solve."""
+    n = (32, 16, 16)
+    a, b, U, Up = _amr_case(n)
+    desc = mg.grid_desc("sph", list(n), hi=[100.0, PI, 2 * PI], tol=1e-10, max_cycles=600, accel_depth=8,
+                        stall_window=0)
+    z, zp = np.zeros_like(U), np.zeros_like(Up)
+    h = mg.Hierarchy(desc)
+    u0, up0 = dev(z), dev(zp)
+    rep = mg.mg_solve_scalar_amr(h, a, b, "psi", "robin", u0, up0, U=dev(U), A2=dev(z), Up=dev(Up), A2p=dev(zp))
+    h.close()
+    assert rep["status"] == "ok" and rep["cycles"] > 0
+    srv = mg.Server(hbm_budget=8 << 30, max_slots=4, max_queue=64)
+    outs, tickets = [], []
+    for q in range(6):
+        if q % 2 == 0:
+            u, up = dev(z), dev(zp)
+            tickets.append(srv.submit_amr(desc, a, b, dev(U), dev(z), dev(Up), dev(zp), u, up))
+            outs.append((u, up))
+        else:
+            args, Uc, Sc, Sic = cfc_case("sph3d", 70 + q)
+            tickets.append(srv.submit_cfc(desc_of(mg, args), dev(Uc), dev(Sc), [dev(x) for x in Sic],
+                                          *fields(Uc.shape)))
+            outs.append(None)
+    res = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert all(r["status"] == "ok" for r in res)
+    for q, o_ in enumerate(outs):
+        if o_ is None:
+            continue
+        assert res[q]["cfc"]["psi"]["cycles"] == rep["cycles"]
+        assert torch.equal(o_[0], u0) and torch.equal(o_[1], up0)
