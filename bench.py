@@ -509,7 +509,7 @@ def serving_measurement(mg, torch, precision="mixed", rate=2000.0, n_requests=40
 def serving_block(mg, torch, gpu_id, sweep):
     """The serving measurement of the bench line: mixed precision at 2000
     requests/s (the serving workload's rate, beyond the server's capacity:
-    the queue grows) and at 60/s (below it), 300 requests each; with sweep,
+    the queue grows) and at 30/s (below it), 300 requests each; with sweep,
     1000 requests per point at 15 ... 400/s in mixed precision and 5 ... 80/s
     in FP64, across the capacity of each."""
     work = ("Poisson arrivals (seed 3): 80%% metric requests on %d streams (each request the next of %d "
@@ -522,7 +522,7 @@ def serving_block(mg, torch, gpu_id, sweep):
         setup = serving_setup(mg, torch, "mixed")
         return {"workload": work,
                 "points": [serving_measurement(mg, torch, "mixed", rate, 300, gpu_id=gpu_id, setup=setup)
-                           for rate in (2000.0, 60.0)]}
+                           for rate in (2000.0, 30.0)]}
     points = []
     for precision, rates in (("mixed", (15.0, 30.0, 60.0, 100.0, 150.0, 400.0)),
                              ("fp64", (5.0, 10.0, 20.0, 30.0, 80.0))):

@@ -122,6 +122,11 @@ struct mg_hierarchy {
     double* aa = nullptr;    // g, x, fprev, gprev, then 2 m history columns of flat.n0 doubles
     int aa_m = 0;
     char* mem = nullptr;
+    // the composite cycle replayed from a CUDA graph, per equation signature
+    int graph_key = -1;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_updates = 0;
+    uint64_t graph_launches = 0;
   } amr;
   bool prof_on = false;
   bool fold_k32 = false;  // while capturing a V-cycle of eq. psi: K is restricted on the way down
@@ -1530,6 +1535,7 @@ int ensure_amr(mg_hierarchy* H, const AmrBox& box) {
   CK(cudaStreamSynchronize(H->st));
   if (A.mem) cudaFree(A.mem);
   if (A.aa) cudaFree(A.aa);
+  if (A.graph) cudaGraphExecDestroy(A.graph);
   A = mg_hierarchy::Amr{};
   const Level& B = H->L[0];
   const int three = H->d.ndim == 3;
@@ -1730,6 +1736,45 @@ void amr_cycle(mg_hierarchy* H, const Eq& e) {
   amr_patch_sweeps(H, e, H->d.nu2);
 }
 
+// The composite cycle replayed from a CUDA graph captured on first use for
+// the patch and the equation signature (direct launches while profiling).
+int run_amr_cycle(mg_hierarchy* H, const Eq& e) {
+  auto& A = H->amr;
+  if (H->prof_on) {
+    amr_cycle(H, e);
+    return MG_OK;
+  }
+  const int key = e.kind | (e.bc << 2) | ((int)e.has_c << 5);
+  if (A.graph && A.graph_key == key) {
+    CK(cudaGraphLaunch(A.graph, H->st));
+    H->updates += A.graph_updates;
+    count_launch((int)A.graph_launches);
+    return MG_OK;
+  }
+  if (A.graph) {
+    cudaGraphExecDestroy(A.graph);
+    A.graph = nullptr;
+  }
+  const int64_t u0 = H->updates;
+  const unsigned long long l0 = launch_count();
+  CK(cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
+  amr_cycle(H, e);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(H->st, &graph);
+  if (ce != cudaSuccess || !graph) return fail(MG_ERR_CUDA, "composite cycle capture failed");
+  ce = cudaGraphInstantiate(&A.graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    A.graph = nullptr;
+    return fail(MG_ERR_CUDA, "composite cycle instantiation failed");
+  }
+  A.graph_key = key;
+  A.graph_updates = H->updates - u0;
+  A.graph_launches = launch_count() - l0;
+  CK(cudaGraphLaunch(A.graph, H->st));
+  return MG_OK;
+}
+
 // Cycle control of the composite iteration, as run_solve: tol, max_cycles,
 // stall window, non-finite values, Anderson mixing of depth accel_depth
 // over the composite unknowns (FP64 columns).
@@ -1776,7 +1821,7 @@ int run_solve_amr(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
       break;
     }
     if (m > 0 && cyc == 0) flat(ax, 1);
-    amr_cycle(H, e);
+    if ((st = run_amr_cycle(H, e))) return st;
     bool mixed_step = false;
     if (m > 0) {
       flat(ag, 1);
@@ -2053,6 +2098,7 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   if (H->sub) mg_destroy_hierarchy(H->sub);
   if (H->amr.mem) cudaFree(H->amr.mem);
   if (H->amr.aa) cudaFree(H->amr.aa);
+  if (H->amr.graph) cudaGraphExecDestroy(H->amr.graph);
   for (cudaEvent_t e : H->ev) cudaEventDestroy(e);
   for (double* p : H->stage) cudaFree(p);
   if (H->aa) cudaFree(H->aa);
