@@ -413,7 +413,11 @@ uint64_t mg_kernel_launches(void);
 /* Kernel classes timed by mg_profile_*: red-black colour passes (one
  * launch updates half of the finest cells, one component), fused
  * red-black sweeps (both colours of a Cartesian scalar level in one launch)
- * and the finest residual with its norms (every cell, every component). */
+ * and the finest residual with its norms (every cell, every component),
+ * all on the finest level; and, for a breakdown of the cycle, the FP32
+ * colour passes of the coarser launched levels (cells: those updated), the
+ * two Anderson mixing kernels (cells: the finest unknowns, components
+ * counted) and the one-block FP32 cycle (cells: those of its top level). */
 enum {
   MG_PROF_SMOOTH64_SCALAR = 0,
   MG_PROF_SMOOTH64_VEC = 1,
@@ -423,7 +427,12 @@ enum {
   MG_PROF_RESID64_VEC = 5,
   MG_PROF_SWEEP64_FUSED = 6,  /* fused red-black sweep: all finest cells */
   MG_PROF_SWEEP32_FUSED = 7,
-  MG_PROF_NCLASS = 8
+  MG_PROF_SMOOTH32_COARSE = 8,
+  MG_PROF_AA_UPDATE = 9,
+  MG_PROF_AA_COMBINE = 10,
+  MG_PROF_BLOCK_CYCLE32 = 11,
+  MG_PROF_RESID64_PSI = 12,   /* the finest residual of eq. psi (RESID64_SCALAR: linear equations) */
+  MG_PROF_NCLASS = 13
 };
 
 /* Enable (1) or disable (0) CUDA-event timing, on the hierarchy's stream,

@@ -138,10 +138,11 @@ struct mg_hierarchy {
 
 namespace {
 
-// Event pair around a finest-level launch when profiling is on; returns
-// the pair's slot or -1.
+// Event pair around a finest-level launch when profiling is on (any level
+// for the classes that are not finest-level ones); returns the pair's slot
+// or -1.
 long prof_begin(mg_hierarchy* H, int l, int cls, int64_t cells) {
-  if (!H->prof_on || l != 0) return -1;
+  if (!H->prof_on || (l != 0 && cls < MG_PROF_SMOOTH32_COARSE)) return -1;
   const size_t pair = H->ev_used / 2;
   if (H->ev_used + 2 > H->ev.size()) {
     for (int q = 0; q < 512; ++q) {
@@ -658,7 +659,10 @@ int finest_residual(mg_hierarchy* H, const Eq& e) {
   Level& L = H->L[0];
   auto v = with_bc(L.v64, e.bc);
   CK(cudaMemsetAsync(H->d_red, 0, sizeof(unsigned long long) * 3, H->st));
-  long tok = prof_begin(H, 0, e.kind == EQ_VEC ? MG_PROF_RESID64_VEC : MG_PROF_RESID64_SCALAR, L.cells());
+  long tok = prof_begin(H, 0,
+                        e.kind == EQ_VEC ? MG_PROF_RESID64_VEC
+                                         : (e.kind == EQ_PSI ? MG_PROF_RESID64_PSI : MG_PROF_RESID64_SCALAR),
+                        L.cells());
   // the residual itself is needed only as the FP32 right-hand side of the
   // next correction cycle (mixed); the FP64 V-cycle recomputes its own
   const bool mixed = H->d.precision == MG_MIXED;
@@ -725,12 +729,12 @@ void smooth32(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
   for (int s = s0; s < nsweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
       if (e.kind != EQ_VEC) {
-        long tok = prof_begin(H, l, MG_PROF_SMOOTH32_SCALAR, L.cells() / 2);
+        long tok = prof_begin(H, l, l ? MG_PROF_SMOOTH32_COARSE : MG_PROF_SMOOTH32_SCALAR, L.cells() / 2);
         launch_smooth_scalar<float>(v, EQ_LIN, L.e[0], L.f32[0], nullptr, K, colour, H->st);
         prof_end(H, tok);
       } else {
         for (int c = 0; c < 3; ++c) {
-          long tok = prof_begin(H, l, MG_PROF_SMOOTH32_VEC, L.cells() / 2);
+          long tok = prof_begin(H, l, l ? MG_PROF_SMOOTH32_COARSE : MG_PROF_SMOOTH32_VEC, L.cells() / 2);
           const GhostPush gp = ghost_push(H, l, c, colour, e.bc);
           launch_smooth_vec<float>(v, L.e, L.f32[c], c, colour, H->st, gp);
           prof_end(H, tok);
@@ -846,7 +850,9 @@ void block_vcycle32(mg_hierarchy* H, const Eq& e, int l0) {
   if (H->fold_k32) restrict_k32(H, l0 + 1);
   const BlockCycle32 P = block_cycle_params(H, e, l0);
   for (int l = l0; l + 1 < H->nlev; ++l) H->updates += (int64_t)(H->d.nu1 + H->d.nu2) * H->L[l].cells() * e.ncomp;
+  long tok = prof_begin(H, l0, MG_PROF_BLOCK_CYCLE32, H->L[l0].cells());
   launch_block_vcycle32(P, H->d.geom, H->st);
+  prof_end(H, tok);
 }
 
 // Linear correction-scheme V-cycle on (L - K) e = f32, e = 0 initially.
@@ -1459,17 +1465,22 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
         for (int a = 0; a < ncol; ++a) cols.slot[a] = (slot - ncol + 1 + a + m) % m;  // oldest first
       }
       double* scr = H->d_aa_part;
+      const int64_t nval = L0.cells() * e.ncomp;
+      long tok = prof_begin(H, 0, MG_PROF_AA_UPDATE, nval);
       if (mixed)
         launch_aa_update_dots<float>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF32, adG32, cols, scr,
                                      H->d_red + 3, H->st);
       else
         launch_aa_update_dots<double>(L0.v64, e.ncomp, stride, L0.u, ax, afp, agp, adF, adG, cols, scr,
                                       H->d_red + 3, H->st);
+      prof_end(H, tok);
       if (cols.n > 0) {
+        tok = prof_begin(H, 0, MG_PROF_AA_COMBINE, nval);
         if (mixed)
           launch_aa_combine<float>(L0.v64, e.ncomp, stride, L0.u, ax, adG32, cols, scr, H->d_red + 3, H->st);
         else
           launch_aa_combine<double>(L0.v64, e.ncomp, stride, L0.u, ax, adG, cols, scr, H->d_red + 3, H->st);
+        prof_end(H, tok);
         if (e.kind == EQ_VEC) fill_all64(H, e, 0);
         mixed_step = true;
       }

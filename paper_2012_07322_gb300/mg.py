@@ -41,7 +41,8 @@ EXPORTS = ["mg_strerror", "mg_last_error", "mg_hierarchy_bytes", "mg_create_hier
 MG_REQ_CFC, MG_REQ_DIVB, MG_REQ_AMR = 0, 1, 2
 MG_NOALLOC_MAX_CELLS = 2097152
 PROF_CLASSES = ["smooth64_scalar", "smooth64_vec", "smooth32_scalar", "smooth32_vec", "resid64_scalar",
-                "resid64_vec", "sweep64_fused", "sweep32_fused"]
+                "resid64_vec", "sweep64_fused", "sweep32_fused", "smooth32_coarse", "aa_update", "aa_combine",
+                "block_cycle32", "resid64_psi"]
 
 
 class mg_grid_desc(C.Structure):

@@ -5,7 +5,10 @@
     python -m paper_2012_07322_gb300.profile_cases xcfc      # one full mixed xCFC solve, 128x64x64
 
 Each case runs through the C ABI and exits 0 on success, so the same command
-can be profiled after it has run once without a profiler.
+can be profiled after it has run once without a profiler.  The xCFC cases
+switch the library's event timing on, which makes every cycle run as direct
+launches under a host loop (no CUDA graphs), so that a profiler sees each
+kernel as its own launch.
 """
 import sys
 
@@ -35,6 +38,7 @@ def xeq(precision="mixed"):
                                   max_cycles=10, stall_window=0, accel_depth=16))
     f = [torch.from_numpy(8 * np.pi * x).cuda() for x in Si]
     V = [torch.zeros(U.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    mg.mg_profile_enable(h, True)
     rep = mg.mg_solve_vector(h, "dirichlet", f, V, allow=(mg.MG_OK, mg.MG_ERR_NOCONV))
     h.close()
     print("xeq", precision, rep["status"], rep["cycles"], rep["rel"])
@@ -53,9 +57,14 @@ def xcfc(precision="mixed"):
     alpha = torch.ones_like(psi)
     beta = [torch.zeros_like(psi) for _ in range(3)]
     X = [torch.zeros_like(psi) for _ in range(3)]
+    mg.mg_profile_enable(h, True)
     rep = mg.mg_solve_cfc(h, dev[0], dev[1], Sid, psi, alpha, beta, X)
+    prof = mg.mg_profile_read(h)
     h.close()
     print("xcfc", precision, {k: rep[k]["cycles"] for k in ("X", "psi", "alphapsi", "beta")})
+    for k, (n, ms, cells) in prof.items():
+        if n:
+            print("  %-16s %6d launches %9.3f ms %8.2f us/launch" % (k, n, ms, ms / n * 1e3))
 
 
 if __name__ == "__main__":
