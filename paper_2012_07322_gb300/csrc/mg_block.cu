@@ -118,7 +118,7 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
   }
   __syncthreads();
   if (!VEC) {
-    coarse_scalar_body<double, G, EQ_LIN>(L, cu[0], cf[0], nullptr, ck, P.coarse_sweeps);
+    coarse_scalar_body<double, G, EQ_LIN, false>(L, cu[0], cf[0], nullptr, ck, P.coarse_sweeps);
   } else if (P.cinv) {
     // exact solve with the precomputed inverse of the coarsest operator:
     // unknown r = c * cells + q (q the interior flat index)
@@ -131,13 +131,24 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
       fp[r] = (c == 0 ? cf[0] : (c == 1 ? cf[1] : cf[2]))[L.idx(i, j, k)];
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    // row r is summed by the BC_SPLIT lanes of one group, each over every
+    // BC_SPLIT-th column, and the partial sums folded by shuffles: the
+    // dependent FP64 chain of a row is n / BC_SPLIT long instead of n
+    constexpr int BC_SPLIT = 8;
+    const int sub = threadIdx.x % BC_SPLIT, rows = blockDim.x / BC_SPLIT;
+    for (int base = 0; base < n; base += rows) {  // the same trip count in every thread
+      const int r = base + (int)threadIdx.x / BC_SPLIT;
       double x = 0.0;
-      for (int col = 0; col < n; ++col) x += P.cinv[(long)col * n + r] * fp[col];
-      int i, j, k;
-      L.cell(r % cells, i, j, k);
-      const int c = r / cells;
-      (c == 0 ? cu[0] : (c == 1 ? cu[1] : cu[2]))[L.idx(i, j, k)] = x;
+      if (r < n)
+        for (int col = sub; col < n; col += BC_SPLIT) x += P.cinv[(long)col * n + r] * fp[col];
+#pragma unroll
+      for (int o = BC_SPLIT / 2; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, BC_SPLIT);
+      if (r < n && sub == 0) {
+        int i, j, k;
+        L.cell(r % cells, i, j, k);
+        const int c = r / cells;
+        (c == 0 ? cu[0] : (c == 1 ? cu[1] : cu[2]))[L.idx(i, j, k)] = x;
+      }
     }
   } else {
     coarse_vec_body<double, G>(L, cu[0], cu[1], cu[2], cf[0], cf[1], cf[2], P.coarse_sweeps);

@@ -312,7 +312,12 @@ __device__ __forceinline__ double block_max_abs(unsigned long long m) {
   return __longlong_as_double((long long)b);
 }
 
-template <typename T, int G, int KIND>
+// NGS sweeps of the coarsest level in one block.  CHECK: until the residual
+// has dropped 1e-12 x or max_sweeps (the FP64 cycle's coarsest solve);
+// without it exactly max_sweeps sweeps from the given start (the FP32
+// correction cycle's: its residual maxima, a block reduction after every
+// sweep, cost more than the sweeps on a few cells).
+template <typename T, int G, int KIND, bool CHECK = true>
 __device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, const T* __restrict__ f,
                                    const T* __restrict__ s0, const T* __restrict__ s1, int max_sweeps) {
   __shared__ double r0s;
@@ -330,10 +335,12 @@ __device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, con
     }
     return block_max_abs(m);
   };
-  const double r0 = resmax();
-  if (tid == 0) r0s = r0;
-  __syncthreads();
-  if (!(r0s > 0.0)) return;
+  if (CHECK) {
+    const double r0 = resmax();
+    if (tid == 0) r0s = r0;
+    __syncthreads();
+    if (!(r0s > 0.0)) return;
+  }
   // linear equations: the Newton diagonal is fixed, invert it once
   __shared__ T invd[COARSE_INV_MAX];
   const bool use_inv = KIND == EQ_LIN && n <= COARSE_INV_MAX;
@@ -361,8 +368,10 @@ __device__ void coarse_scalar_body(const LevelView<T>& L, T* __restrict__ u, con
       }
       __syncthreads();
     }
-    const double r = resmax();
-    if (!(r > 1e-12 * r0s)) break;
+    if (CHECK) {
+      const double r = resmax();
+      if (!(r > 1e-12 * r0s)) break;
+    }
   }
 }
 
