@@ -117,7 +117,46 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
     for (long q = threadIdx.x; q < ng; q += blockDim.x) cu[c][q] = 0.0;
   }
   __syncthreads();
-  if (!VEC) {
+  if (!VEC && P.cA) {
+    // red-black NGS sweeps with dense rows of the coarsest operator (its
+    // boundary rules folded in), K subtracted on the diagonal: row r of a
+    // colour is summed by the BC_SPLIT lanes of one group and folded by
+    // shuffles; the cells of one colour couple only to the other colour
+    constexpr int BC_SPLIT = 8;
+    __shared__ double uq[BC_CMAT_MAX], fq[BC_CMAT_MAX], kq[BC_CMAT_MAX], dq[BC_CMAT_MAX];
+    __shared__ long pq[BC_CMAT_MAX];
+    __shared__ unsigned char colq[BC_CMAT_MAX];
+    const int n = P.cn;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      const double kv = ck ? ck[p] : 0.0;
+      pq[q] = p;
+      colq[q] = (unsigned char)((i + j + k) & 1);
+      fq[q] = cf[0][p];
+      kq[q] = kv;
+      uq[q] = 0.0;
+      dq[q] = 1.0 / (P.cA[(long)q * n + q] - kv);
+    }
+    __syncthreads();
+    const int sub = threadIdx.x % BC_SPLIT, rows = blockDim.x / BC_SPLIT;
+    for (int it = 0; it < P.coarse_sweeps; ++it)
+      for (int colour = 0; colour < 2; ++colour) {
+        for (int base = 0; base < n; base += rows) {  // the same trip count in every thread
+          const int r = base + (int)threadIdx.x / BC_SPLIT;
+          const bool on = r < n && colq[r] == colour;
+          double x = 0.0;
+          if (on)
+            for (int col = sub; col < n; col += BC_SPLIT) x += P.cA[(long)col * n + r] * uq[col];
+#pragma unroll
+          for (int o = BC_SPLIT / 2; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, BC_SPLIT);
+          if (on && sub == 0) uq[r] -= (x - kq[r] * uq[r] - fq[r]) * dq[r];
+        }
+        __syncthreads();
+      }
+    for (int q = threadIdx.x; q < n; q += blockDim.x) cu[0][pq[q]] = uq[q];
+  } else if (!VEC) {
     coarse_scalar_body<double, G, EQ_LIN, false>(L, cu[0], cf[0], nullptr, ck, P.coarse_sweeps);
   } else if (P.cinv) {
     // exact solve with the precomputed inverse of the coarsest operator:
@@ -265,6 +304,42 @@ __global__ void k_coarse_assemble_vec(LevelView<double> L, double* __restrict__ 
     double D;
     A[(long)col * n + r] = vec_op<double, G>(L, U[0], U[1], U[2], r / cells, i, j, L.idx(i, j, k), D);
   }
+}
+
+// Column col of the coarsest scalar operator: lap_scalar (its boundary rule
+// folded in) applied to unit field col, into A[col * n + r].  One block per
+// column; scratch holds n ghosted fields.
+template <int G>
+__global__ void k_coarse_assemble_scalar(LevelView<double> L, double* __restrict__ scratch, double* __restrict__ A,
+                                         int n) {
+  pdl_entry();
+  const int col = blockIdx.x;
+  const long ng = L.sy * (L.n2 + 2 * L.three);
+  double* U = scratch + (long)col * ng;
+  for (long q = threadIdx.x; q < ng; q += blockDim.x) U[q] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int i, j, k;
+    L.cell(col, i, j, k);
+    U[L.idx(i, j, k)] = 1.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    int i, j, k;
+    L.cell(r, i, j, k);
+    double D;
+    A[(long)col * n + r] = lap_scalar<double, G>(L, U, i, j, k, L.idx(i, j, k), D);
+  }
+}
+
+void launch_coarse_assemble_scalar(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st) {
+  count_launch();
+  if (L.geom == CART)
+    launch_k(k_coarse_assemble_scalar<CART>, n, 256, 0, st, L, scratch, A, n);
+  else if (L.geom == CYL)
+    launch_k(k_coarse_assemble_scalar<CYL>, n, 256, 0, st, L, scratch, A, n);
+  else
+    launch_k(k_coarse_assemble_scalar<SPH>, n, 256, 0, st, L, scratch, A, n);
 }
 
 void launch_coarse_assemble_vec(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st) {

@@ -85,6 +85,8 @@ struct mg_hierarchy {
   // boundary rule (transposed), state 0 not built, 1 built, -1 unavailable
   double* cinv[3] = {};
   int cinv_state[3] = {0, 0, 0};
+  double* cmat[3] = {};  // scalar equations: the coarsest operator per boundary rule (same states)
+  int cmat_state[3] = {0, 0, 0};
   double* d_aa_part = nullptr;  // AA_SCRATCH_DOUBLES of device scratch
   // ghost-push tables of the vector colour passes: state 0 not built, 1
   // built, -1 unavailable; one device buffer holds every level's tables
@@ -822,6 +824,10 @@ BlockCycle32 block_cycle_params(mg_hierarchy* H, const Eq& e, int l0) {
     P.cinv = H->cinv[e.bc];
     P.cn = (int)(3 * Lc.cells());
   }
+  if (!P.vec && H->cmat_state[e.bc] == 1) {
+    P.cA = H->cmat[e.bc];
+    P.cn = (int)Lc.cells();
+  }
   Level& L0 = H->L[l0];
   P.ng0 = L0.ng;
   for (int c = 0; c < 3; ++c) {
@@ -1097,6 +1103,37 @@ int ensure_coarse_inverse(mg_hierarchy* H, int bc) {
   }
   H->cinv[bc] = d;
   H->cinv_state[bc] = 1;
+  return MG_OK;
+}
+
+// Mixed precision, scalar equations: the coarsest operator as dense rows
+// (its boundary rule folded in), assembled once per boundary rule before the
+// first cycle (outside graph capture), for the one-block cycle's coarsest
+// sweeps.  Coarsest levels of more than BC_CMAT_MAX cells keep the stencil
+// sweeps.
+int ensure_coarse_matrix(mg_hierarchy* H, int bc) {
+  if (H->cmat_state[bc] != 0) return MG_OK;
+  H->cmat_state[bc] = -1;
+  Level& Lc = H->L[H->nlev - 1];
+  const int n = (int)Lc.cells();
+  if (n > BC_CMAT_MAX) return MG_OK;
+  double *scratch = nullptr, *dA = nullptr;
+  if (cudaMalloc(&scratch, sizeof(double) * (size_t)n * Lc.ng) != cudaSuccess ||
+      cudaMalloc(&dA, sizeof(double) * (size_t)n * n) != cudaSuccess) {
+    cudaFree(scratch);
+    cudaFree(dA);
+    cudaGetLastError();
+    return MG_OK;
+  }
+  launch_coarse_assemble_scalar(with_bc(Lc.v64, bc), scratch, dA, n, H->st);
+  const cudaError_t ce = cudaStreamSynchronize(H->st);
+  cudaFree(scratch);
+  if (ce != cudaSuccess) {
+    cudaFree(dA);
+    return fail(MG_ERR_CUDA, cudaGetErrorString(ce));
+  }
+  H->cmat[bc] = dA;
+  H->cmat_state[bc] = 1;
   return MG_OK;
 }
 
@@ -1393,6 +1430,8 @@ int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   const int m = d.accel_depth;
   if (mixed && e.kind == EQ_VEC)
     if (int est = ensure_coarse_inverse(H, e.bc)) return est;
+  if (mixed && e.kind != EQ_VEC)
+    if (int est = ensure_coarse_matrix(H, e.bc)) return est;
   if (e.kind == EQ_VEC && e.bc == MG_BC_DIRICHLET)
     if (int est = ensure_ghost_push(H)) return est;
   if (e.kind == EQ_VEC) fill_all64(H, e, 0);
@@ -2114,6 +2153,8 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   for (double* p : H->stage) cudaFree(p);
   if (H->aa) cudaFree(H->aa);
   for (double* p : H->cinv)
+    if (p) cudaFree(p);
+  for (double* p : H->cmat)
     if (p) cudaFree(p);
   if (H->d_aa_part) cudaFree(H->d_aa_part);
   if (H->push_buf) cudaFree(H->push_buf);

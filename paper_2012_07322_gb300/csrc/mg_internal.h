@@ -95,13 +95,17 @@ constexpr long ROW_PAD = 4;
 inline long row_stride(int n0) { return (n0 + 2 * ROW_PAD + ROW_PAD - 1) / ROW_PAD * ROW_PAD; }
 
 // One red-black sweep in one launch (3D linear scalar equations on levels
-// of at least one 64 x 8 column; Cartesian, cylindrical and spherical), out
-// of place: uin -> uout, which must not alias; only the interior of uout is
-// written.  Returns false when it does not apply.  On cylindrical and
-// spherical levels it is used from FUSED_CURV_CELLS cells on: a block marches
-// its chunk of phi planes behind a staging pipeline a few planes deep, and on
-// a 128 x 64 x 64 level the chunks are too short to hide it (measured: one
-// sweep took as long as its two colour passes, and the solve got slower).
+// tiled by 64 x 8 columns: n0 a multiple of 64, n1 of 8; Cartesian,
+// cylindrical and spherical), out of place: uin -> uout, which must not
+// alias; only the interior of uout is written.  Returns false when it does
+// not apply.  On cylindrical and spherical levels it is used from
+// FUSED_CURV_CELLS cells on.  Below that the colour passes win: measured on
+// the 128 x 64 x 64 xCFC solve, a block marching a short chunk of phi planes
+// behind its staging pipeline took as long as the two colour passes of a
+// sweep, and a block staging all planes of its chunk at once (one copy
+// latency per sweep) made the solve slower by 9-11 ms, since programmatic
+// dependent launch hides most of each colour pass's launch latency while
+// the one-launch sweep's staging is a serial prologue.
 template <typename T>
 bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st);
 template <typename T>
@@ -109,7 +113,7 @@ void init_fused_sweep_attributes();
 constexpr long FUSED_CURV_CELLS = 1L << 22;
 template <typename T>
 inline bool fused_sweep_applies(const LevelView<T>& L) {
-  if (!(L.three && L.n0 >= 64 && L.n1 >= 8 && L.n2 >= 4)) return false;
+  if (!(L.three && L.n0 % 64 == 0 && L.n1 % 8 == 0 && L.n2 >= 4)) return false;
   return L.geom == CART || (long)L.n0 * L.n1 * L.n2 >= FUSED_CURV_CELLS;
 }
 // Ghost push of the vector smoother's colour passes.  With a table, the
@@ -338,7 +342,8 @@ struct BlockCycle32 {
   int cu[3], cf[3], ck;   // offsets (doubles, from fp64_at) of the FP64 coarsest solve; ck < 0: no c
   long fp64_at;           // byte offset of the FP64 area in shared memory
   const double* cinv;     // vector equations: inverse of the coarsest operator (transposed), or null
-  int cn;                 // its order (3 x coarsest cells)
+  int cn;                 // its order (3 x coarsest cells); scalar equations: the cells
+  const double* cA;       // scalar equations: the coarsest operator, A[col * cn + r], or null
   long ng0;               // ghosted size of level l0
   const float* f_in[3];   // level l0 right-hand side in HBM
   float* e_out[3];        // level l0 correction in HBM (written at the end)
@@ -348,6 +353,12 @@ void launch_block_vcycle32(const BlockCycle32& P, int geom, cudaStream_t st);
 void init_block_cycle_attributes();
 // The largest coarsest vector system solved exactly (3 x cells).
 constexpr int BC_CINV_MAX = 768;
+// The largest coarsest scalar level swept with dense operator rows (cells).
+constexpr int BC_CMAT_MAX = 64;
+// Columns of the coarsest scalar operator (the flux-form Laplacian with its
+// boundary rule folded in) into A[col * n + r], n = coarsest cells; scratch
+// holds n ghosted fields.
+void launch_coarse_assemble_scalar(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st);
 // Columns of the coarsest vector operator (L with its boundary rule) into
 // A[col * n + r], n = 3 x coarsest cells; scratch holds 3 n ghosted fields.
 void launch_coarse_assemble_vec(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st);

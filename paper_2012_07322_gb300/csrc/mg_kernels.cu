@@ -967,7 +967,7 @@ size_t fused_sweep_smem(bool with_c) {
 // that wide (fewer instructions per cell), else 64.
 template <typename T>
 int fused_sweep_tx(const LevelView<T>& L) {
-  return (sizeof(T) == 4 && L.n0 >= 128) ? 128 : 64;
+  return (sizeof(T) == 4 && L.n0 % 128 == 0) ? 128 : 64;
 }
 
 // Blocks of k_sweep_rb resident on the whole device, [geometry][TX == 128]

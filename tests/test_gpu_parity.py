@@ -468,23 +468,29 @@ FUSED_CASES = [
     # (n, sweeps): one 64 x 8 column in x, y with fewer planes than a chunk;
     # several columns and z-chunks (re-relaxed red planes at chunk edges);
     # more blocks than fit on the device at once (blocks of a later wave
-    # must still read only the sweep's input)
+    # must still read only the sweep's input); a level narrower than one
+    # 64-cell column (colour passes)
     ([64, 8, 4], 2),
     ([128, 32, 64], 3),
     ([64, 16, 32], 4),
     ([256, 128, 64], 2),
+    ([32, 16, 8], 2),
 ]
 
 
 CURV_FUSED_CASES = [
     # (geom, n, sweeps): levels of 2^22 cells and more take the one-launch
     # sweep (several columns, j tiles and periodic phi chunks, more blocks
-    # than fit the device at once); smaller ones the colour passes
+    # than fit the device at once); smaller ones, and a level of fewer than
+    # 8 rows, the colour passes
     ("sph", [256, 128, 128], 2),
     ("cyl", [256, 128, 128], 3),
     ("sph", [64, 8, 4], 2),
     ("sph", [128, 32, 64], 3),
     ("cyl", [128, 32, 32], 3),
+    ("sph", [128, 64, 64], 2),
+    ("sph", [64, 32, 32], 2),
+    ("cyl", [64, 4, 8], 2),
 ]
 
 
@@ -493,8 +499,9 @@ CURV_FUSED_CASES = [
 def test_fused_sweep_parity_curvilinear(mg, bc, case):
     """Spherical and cylindrical 3D levels of 2^22 cells and more take the
     one-launch out-of-place sweep too (per-(i, j) coefficients, periodic phi
-    march; origin, axis and pole cells included): the result equals the
-    oracle's red-black sweeps, with and without the c u term."""
+    march; origin, axis and pole cells included), smaller ones the colour
+    passes: the result equals the oracle's red-black sweeps, with and
+    without the c u term."""
     geom, n, sweeps = CURV_FUSED_CASES[case]
     if geom == "sph":
         lo, hi = [0.0, 0.0, 0.0], [40.0, PI, 2 * PI]
