@@ -81,9 +81,9 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
 // out of place (uin -> uout): Cartesian levels, and cylindrical / spherical
 // levels, whose dimension 2 (phi) is periodic: the march along k then wraps
 // (plane -1 is plane n2 - 1), and the coefficients come per (i, j) from the
-// level's tables.  A block owns a column of TX x RB_TY
+// level's tables.  A block owns a column of TX x TY
 // cells over a chunk of planes [z0, z1) and marches along k.  Plane by
-// plane it stages a (TX + 8) x (RB_TY + 4) box of u, f and c (the column
+// plane it stages a (TX + 8) x (TY + 4) box of u, f and c (the column
 // with a 4-cell halo in i, 2 cells in j; rows are 16-byte aligned, so the
 // box moves in 16-byte asynchronous copies issued two planes ahead),
 // relaxes the red cells of plane s over its column and a one-cell ring
@@ -94,18 +94,21 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
 // the result is the red-black sweep of k_smooth_scalar whatever order the
 // blocks run in, and u, f and c cross DRAM once per sweep instead of once
 // per colour.  Warp w owns row w; each lane owns TX / 64 pairs of cells.
-constexpr int RB_TY = 8, RB_THREADS = 256;
 constexpr int RB_HX = 4, RB_HY = 2;  // staged halo
-constexpr int RB_BY = RB_TY + 2 * RB_HY;
 // plane buffers: u planes s-3..s+2 and f, c planes s-2..s+1 are in use or
 // in flight at step s (the f ring is indexed by plane & 3)
 constexpr int RB_NU = 6, RB_NF = 4;
 static_assert(RB_HX == ROW_PAD, "the staged box starts on a 16-byte boundary");
 
+// Column shape: TX cells by TY rows, one warp per row (128-cell columns
+// take 16 rows: the ring and the staged halo rows cost half as much per
+// cell as with 8).
 template <int TX>
 struct RbShape {
-  static constexpr int BX = TX + 2 * RB_HX, BP = BX * RB_BY;
-  static constexpr int RING = TX + 2 + RB_TY;  // red ring cells: two rows of (TX+2)/2, two columns of TY/2
+  static constexpr int TY = TX == 128 ? 16 : 8, THREADS = 32 * TY;
+  static constexpr int BY = TY + 2 * RB_HY;
+  static constexpr int BX = TX + 2 * RB_HX, BP = BX * BY;
+  static constexpr int RING = TX + 2 + TY;  // red ring cells: two rows of (TX+2)/2, two columns of TY/2
 };
 
 template <typename T>
@@ -133,16 +136,16 @@ __device__ __forceinline__ void cp_async_wait() {
 // whole march: global offset within a plane, offset in the plane buffer.
 template <typename T, int TX>
 struct RbPieces {
-  static constexpr int BX = RbShape<TX>::BX;
-  static constexpr int PER_ROW = BX * (int)sizeof(T) / 16, N = RB_BY * PER_ROW;
-  static constexpr int ITEMS = (N + RB_THREADS - 1) / RB_THREADS;
+  static constexpr int BX = RbShape<TX>::BX, THREADS = RbShape<TX>::THREADS;
+  static constexpr int PER_ROW = BX * (int)sizeof(T) / 16, N = RbShape<TX>::BY * PER_ROW;
+  static constexpr int ITEMS = (N + THREADS - 1) / THREADS;
   long g[ITEMS];
   int s[ITEMS];
   bool ok[ITEMS];
   __device__ __forceinline__ RbPieces(const LevelView<T>& L, int i0, int j0) {
 #pragma unroll
     for (int m = 0; m < ITEMS; ++m) {
-      const int q = threadIdx.x + m * RB_THREADS;
+      const int q = threadIdx.x + m * THREADS;
       const int ly = q / PER_ROW, cx = q - ly * PER_ROW;
       const int j = j0 - RB_HY + ly, x = cx * (16 / (int)sizeof(T));
       ok[m] = q < N && j >= -1 && j <= L.n1;  // rows of the ghosted array
@@ -228,6 +231,41 @@ __device__ __forceinline__ void rb_relax(const LevelView<T>& L, const RbPlanes<T
   }
 }
 
+// Coefficients of cell q (0 or 1) of a lane's pair, member by member (a
+// select of the whole struct would put it in local memory).
+template <typename T>
+__device__ __forceinline__ RbCoef<T> rb_pick(int q, const RbCoef<T>& a, const RbCoef<T>& b) {
+  RbCoef<T> c;
+  c.cE = q ? b.cE : a.cE;
+  c.cW = q ? b.cW : a.cW;
+  c.cN = q ? b.cN : a.cN;
+  c.cS = q ? b.cS : a.cS;
+  c.cZ = q ? b.cZ : a.cZ;
+  c.D = q ? b.D : a.D;
+  return c;
+}
+
+// The same update from operand values: centre uc, neighbours e, w, n, s (in
+// i and j), up and down (in k), right-hand side fv and coefficient cv.
+template <typename T, int G, bool HAS_C>
+__device__ __forceinline__ T rb_new_value(const RbCoef<T>& k, T iD0, T uc, T ue, T uw, T un, T us, T uu, T ud, T fv,
+                                          T cv) {
+  T Lu = k.cE * (ue - uc) - k.cW * (uc - uw);
+  if (G == SPH)
+    Lu += k.cN * (un - uc) - k.cS * (uc - us);
+  else
+    Lu += k.cN * (un - T(2) * uc + us);
+  Lu += k.cZ * (uu - T(2) * uc + ud);
+  if (HAS_C) {
+    Lu -= cv * uc;
+    return uc - (Lu - fv) / (k.D - cv);
+  } else if (G == CART) {
+    return uc - (Lu - fv) * iD0;
+  } else {
+    return uc - (Lu - fv) / k.D;
+  }
+}
+
 // Outer ghosts of staged plane p (just landed, still the sweep's input) in
 // the i and j directions: g = factor * u of the boundary cell, the values
 // lap_scalar folds in.  A ghost is read only by its own boundary cell, whose
@@ -235,8 +273,8 @@ __device__ __forceinline__ void rb_relax(const LevelView<T>& L, const RbPlanes<T
 // the input stays exact.
 template <typename T, int TX>
 __device__ __forceinline__ void rb_fix_ghosts(const LevelView<T>& L, T* P, int i0, int j0, int p) {
-  constexpr int BX = RbShape<TX>::BX, NY = RB_TY + 2, NX = TX + 2;
-  const bool xl = i0 == 0, xh = i0 + TX == L.n0, yl = j0 == 0, yh = j0 + RB_TY == L.n1;
+  constexpr int BX = RbShape<TX>::BX, TY = RbShape<TX>::TY, NY = TY + 2, NX = TX + 2;
+  const bool xl = i0 == 0, xh = i0 + TX == L.n0, yl = j0 == 0, yh = j0 + TY == L.n1;
   const int t = threadIdx.x;
   // i ghosts of rows y = -1 .. TY on the low / high faces (threads 0 .. 2 NY)
   if (t < 2 * NY) {
@@ -250,11 +288,11 @@ __device__ __forceinline__ void rb_fix_ghosts(const LevelView<T>& L, T* P, int i
   }
   // j ghosts of columns x = -1 .. TX, only on blocks at a j face
   if (yl || yh)
-    for (int u = t; u < 2 * NX; u += RB_THREADS) {
+    for (int u = t; u < 2 * NX; u += RbShape<TX>::THREADS) {
       const bool hi = u >= NX;
       const int x = (hi ? u - NX : u) - 1, i = i0 + x;
       if (!(hi ? yh : yl) || i < 0 || i >= L.n0) continue;
-      const int ys = hi ? RB_TY - 1 : 0, yg = hi ? RB_TY : -1;
+      const int ys = hi ? TY - 1 : 0, yg = hi ? TY : -1;
       const T fac = hi ? outer_factor(L, i, L.n1, p, i, L.n1 - 1, p) : outer_factor(L, i, -1, p, i, 0, p);
       P[(x + RB_HX) + (yg + RB_HY) * BX] = fac * P[(x + RB_HX) + (ys + RB_HY) * BX];
     }
@@ -264,8 +302,8 @@ __device__ __forceinline__ void rb_fix_ghosts(const LevelView<T>& L, T* P, int i
 template <typename T, int TX>
 __device__ __forceinline__ void rb_ghost_plane(const LevelView<T>& L, T* G, const T* S, int i0, int j0, int pg,
                                                int ps) {
-  constexpr int BX = RbShape<TX>::BX, NY = RB_TY + 2, NX = TX + 2;
-  for (int t = threadIdx.x; t < NX * NY; t += RB_THREADS) {
+  constexpr int BX = RbShape<TX>::BX, NY = RbShape<TX>::TY + 2, NX = TX + 2;
+  for (int t = threadIdx.x; t < NX * NY; t += RbShape<TX>::THREADS) {
     const int y = t / NX - 1, x = t % NX - 1, i = i0 + x, j = j0 + y;
     if (i < 0 || i >= L.n0 || j < 0 || j >= L.n1) continue;
     const int q = (x + RB_HX) + (y + RB_HY) * BX;
@@ -281,24 +319,22 @@ struct RbLaneCoef {
   RbCoef<T> k[TX / 64][2];
 };
 
-// Red cells of plane s: the lane's cells of its row, then the ring.
+// Red cells of plane s on the ring around the column (the lane cells are
+// relaxed from registers in k_sweep_rb).  On a Cartesian level every cell
+// has the lane cells' coefficients.
 template <typename T, int G, int TX, bool HAS_C>
-__device__ __forceinline__ void rb_red_plane(const LevelView<T>& L, const RbPlanes<T>& R, int i0, int j0, int s,
-                                             const RbLaneCoef<T, TX>& lc, T iD0) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
+__device__ __forceinline__ void rb_red_ring(const LevelView<T>& L, const RbPlanes<T>& R, int i0, int j0, int s,
+                                            const RbLaneCoef<T, TX>& lc, T iD0) {
+  const int t = threadIdx.x;
   const int par = (i0 + j0 + s) & 1;  // red: (i + j + s) even
-  const int q = (par + w) & 1;
-#pragma unroll
-  for (int h = 0; h < TX / 64; ++h)
-    rb_relax<T, G, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + q, w, q ? lc.k[h][1] : lc.k[h][0], iD0);
   if (t < RbShape<TX>::RING) {
-    constexpr int HR = (TX + 2) / 2, HC = RB_TY / 2;
+    constexpr int TY = RbShape<TX>::TY, HR = (TX + 2) / 2, HC = TY / 2;
     int x, y;
     if (t < HR) {
       y = -1;
       x = -1 + 2 * t + par;
     } else if (t < 2 * HR) {
-      y = RB_TY;
+      y = TY;
       x = -1 + 2 * (t - HR) + (par ^ 1);
     } else if (t < 2 * HR + HC) {
       x = -1;
@@ -307,13 +343,17 @@ __device__ __forceinline__ void rb_red_plane(const LevelView<T>& L, const RbPlan
       x = TX;
       y = 2 * (t - 2 * HR - HC) + par;
     }
-    const int ic = min(max(i0 + x, 0), L.n0 - 1), jc = min(max(j0 + y, 0), L.n1 - 1);
-    rb_relax<T, G, TX, HAS_C, true>(L, R, i0, j0, x, y, rb_coef<T, G>(L, ic, jc), iD0);
+    if (G == CART) {
+      rb_relax<T, G, TX, HAS_C, true>(L, R, i0, j0, x, y, lc.k[0][0], iD0);
+    } else {
+      const int ic = min(max(i0 + x, 0), L.n0 - 1), jc = min(max(j0 + y, 0), L.n1 - 1);
+      rb_relax<T, G, TX, HAS_C, true>(L, R, i0, j0, x, y, rb_coef<T, G>(L, ic, jc), iD0);
+    }
   }
 }
 
 template <typename T, int G, int TX, bool HAS_C>
-__global__ void __launch_bounds__(RB_THREADS) k_sweep_rb(LevelView<T> L, const T* __restrict__ uin,
+__global__ void __launch_bounds__(RbShape<TX>::THREADS, G == CART && TX == 128 ? 2 : 1) k_sweep_rb(LevelView<T> L, const T* __restrict__ uin,
                                                          T* __restrict__ uout, const T* __restrict__ f,
                                                          const T* __restrict__ c, int zc) {
   pdl_entry();
@@ -323,7 +363,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb(LevelView<T> L, const T
   T* su = reinterpret_cast<T*>(smem_raw);
   T* sf = su + RB_NU * BP;
   T* sc = sf + RB_NF * BP;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * RB_TY;
+  constexpr int TY = RbShape<TX>::TY;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.n2);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // coefficients of the lane's cells (uniform on a Cartesian grid)
@@ -333,7 +374,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb(LevelView<T> L, const T
 #pragma unroll
     for (int q = 0; q < 2; ++q) lc.k[h][q] = rb_coef<T, G>(L, i0 + 64 * h + 2 * lane + q, min(j0 + w, L.n1 - 1));
   const T iD0 = T(1) / lc.k[0][0].D;
-  const bool edge_xy = i0 == 0 || j0 == 0 || i0 + TX >= L.n0 || j0 + RB_TY >= L.n1;
+  const bool edge_xy = i0 == 0 || j0 == 0 || i0 + TX >= L.n0 || j0 + TY >= L.n1;
   const RbPieces<T, TX> pc(L, i0, j0);
   auto wrap = [&](int p) { return PER ? (p + L.n2) % L.n2 : p; };
   // group p: u plane p (into u buffer bu) and f, c plane p - 1, for the
@@ -362,6 +403,17 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb(LevelView<T> L, const T
   bs = bd;
   bd = b;
   b = (b + RB_NU - 1) % RB_NU;
+  // The lane's pairs (i, i + 1), i = i0 + 64 h + 2 lane, of row w in
+  // registers for planes s - 2 .. s + 1.  A pair's red cell of plane s and
+  // its black cell of plane s - 1 are the same column q: in k a cell's
+  // neighbours are the lane's own values, in i one of them is; the other
+  // neighbours (other lanes and rows, the ring, the outer ghosts) are read
+  // from the staged planes.  Red values are written back to the plane for
+  // the other threads; black values are read by nobody before the store.
+  constexpr int NH = TX / 64;
+  using V2 = typename Vec2<T>::type;  // pairs (i, i + 1): n0 a multiple of TX, rows 16-byte aligned
+  V2 rm2[NH], rm1[NH], r0[NH], rp1[NH];
+  const int po = (2 * lane + RB_HX) + (w + RB_HY) * BX;  // the lane's first pair in a staged plane
   for (int s = z0 - 1; s <= z1; ++s) {
     const int bn2 = next6(bu);
     stage(s + 2, bn2);
@@ -376,30 +428,65 @@ __global__ void __launch_bounds__(RB_THREADS) k_sweep_rb(LevelView<T> L, const T
       if (s + 1 == 0) rb_ghost_plane<T, TX>(L, su + bs * BP, su + bu * BP, i0, j0, -1, 0);
       if (s + 1 == L.n2 - 1) rb_ghost_plane<T, TX>(L, su + bn2 * BP, su + bu * BP, i0, j0, L.n2, L.n2 - 1);
     }
-    if (s == z0 - 1) __syncthreads();
+    if (s == z0 - 1) {
+      __syncthreads();
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        // plane z0 - 2 (not staged below a non-periodic edge: unused there) and z0 - 1
+        rm1[h] = *reinterpret_cast<const V2*>(su + bd * BP + po + 64 * h);
+        r0[h] = *reinterpret_cast<const V2*>(su + bs * BP + po + 64 * h);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < NH; ++h) rp1[h] = *reinterpret_cast<const V2*>(su + bu * BP + po + 64 * h);  // plane s + 1
+    const int q = (i0 + j0 + s + w) & 1;  // the pair's red cell of plane s, black cell of plane s - 1
     if (PER || (s >= 0 && s < L.n2)) {
       const int bf = (s & (RB_NF - 1)) * BP;
-      const RbPlanes<T> R{su + bd * BP, su + bs * BP, su + bu * BP, sf + bf, sc + bf};
-      rb_red_plane<T, G, TX, HAS_C>(L, R, i0, j0, s, lc, iD0);
+      T* P = su + bs * BP;
+      const T* F = sf + bf;
+      const T* Cc = sc + bf;
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        const int o = po + 64 * h + q;
+        const T uc = q ? r0[h].y : r0[h].x, other = q ? r0[h].x : r0[h].y;
+        const T ue = q ? P[o + 1] : other, uw = q ? other : P[o - 1];
+        const T v = rb_new_value<T, G, HAS_C>(rb_pick(q, lc.k[h][0], lc.k[h][1]), iD0, uc, ue, uw, P[o + BX],
+                                              P[o - BX], q ? rp1[h].y : rp1[h].x, q ? rm1[h].y : rm1[h].x, F[o],
+                                              HAS_C ? Cc[o] : T(0));
+        P[o] = v;
+        r0[h].x = q ? r0[h].x : v;
+        r0[h].y = q ? v : r0[h].y;
+      }
+      const RbPlanes<T> R{su + bd * BP, P, su + bu * BP, F, Cc};
+      rb_red_ring<T, G, TX, HAS_C>(L, R, i0, j0, s, lc, iD0);
     }
     __syncthreads();
     const int sb = s - 1;
     if (sb >= z0) {
-      // black cells of plane sb = s - 1 (planes s - 2, s - 1, s), then store
+      // black cells of plane sb = s - 1 (its red neighbours: planes s - 2,
+      // s - 1, s), then store the pairs
       const int bf = (sb & (RB_NF - 1)) * BP;
-      const RbPlanes<T> R{su + b * BP, su + bd * BP, su + bs * BP, sf + bf, sc + bf};
-      const int par = (i0 + j0 + sb + w + 1) & 1;  // black: (i + j + sb) odd
+      const T* P = su + bd * BP;
+      const T* F = sf + bf;
+      const T* Cc = sc + bf;
 #pragma unroll
-      for (int h = 0; h < TX / 64; ++h)
-        rb_relax<T, G, TX, HAS_C, false>(L, R, i0, j0, 64 * h + 2 * lane + par, w, par ? lc.k[h][1] : lc.k[h][0],
-                                         iD0);
-      using V2 = typename Vec2<T>::type;  // pairs (i, i + 1): n0 a multiple of TX, rows 16-byte aligned
-#pragma unroll
-      for (int h = 0; h < TX / 64; ++h) {
-        const int x = 64 * h + 2 * lane;
-        *reinterpret_cast<V2*>(uout + L.idx(i0 + x, j0 + w, sb)) =
-            *reinterpret_cast<const V2*>(R.P + (x + RB_HX) + (w + RB_HY) * BX);
+      for (int h = 0; h < NH; ++h) {
+        const int o = po + 64 * h + q;
+        const T uc = q ? rm1[h].y : rm1[h].x, other = q ? rm1[h].x : rm1[h].y;
+        const T ue = q ? P[o + 1] : other, uw = q ? other : P[o - 1];
+        const T v = rb_new_value<T, G, HAS_C>(rb_pick(q, lc.k[h][0], lc.k[h][1]), iD0, uc, ue, uw, P[o + BX],
+                                              P[o - BX], q ? r0[h].y : r0[h].x, q ? rm2[h].y : rm2[h].x, F[o],
+                                              HAS_C ? Cc[o] : T(0));
+        rm1[h].x = q ? rm1[h].x : v;
+        rm1[h].y = q ? v : rm1[h].y;
+        *reinterpret_cast<V2*>(uout + L.idx(i0 + 64 * h + 2 * lane, j0 + w, sb)) = rm1[h];
       }
+    }
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      rm2[h] = rm1[h];
+      rm1[h] = r0[h];
+      r0[h] = rp1[h];
     }
     b = bd;
     bd = bs;
@@ -967,7 +1054,7 @@ size_t fused_sweep_smem(bool with_c) {
 // that wide (fewer instructions per cell), else 64.
 template <typename T>
 int fused_sweep_tx(const LevelView<T>& L) {
-  return (sizeof(T) == 4 && L.n0 % 128 == 0) ? 128 : 64;
+  return (sizeof(T) == 4 && L.n0 % 128 == 0 && L.n1 % RbShape<128>::TY == 0) ? 128 : 64;
 }
 
 // Blocks of k_sweep_rb resident on the whole device, [geometry][TX == 128]
@@ -984,7 +1071,7 @@ static void set_fused_capacity(int sms) {
   const size_t smem = fused_sweep_smem<T, TX>(HAS_C);
   cudaFuncSetAttribute(k_sweep_rb<T, G, TX, HAS_C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_rb<T, G, TX, HAS_C>, RB_THREADS, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_rb<T, G, TX, HAS_C>, RbShape<TX>::THREADS, smem) !=
           cudaSuccess ||
       nb < 1)
     nb = 1;
@@ -1016,7 +1103,7 @@ void init_fused_sweep_attributes() {
 // length with the fewest plane steps per SM slot.
 template <typename T>
 int fused_sweep_chunk(const LevelView<T>& L, int tx, bool with_c) {
-  const long cols = (long)cdiv(L.n0, tx) * cdiv(L.n1, RB_TY);
+  const long cols = (long)cdiv(L.n0, tx) * cdiv(L.n1, tx == 128 ? RbShape<128>::TY : RbShape<64>::TY);
   const long cap = FusedCapacity<T>::blocks[L.geom][tx == 128][with_c];
   int best = 8;
   long best_cost = -1;
@@ -1034,11 +1121,12 @@ int fused_sweep_chunk(const LevelView<T>& L, int tx, bool with_c) {
 template <typename T, int G, int TX>
 static void launch_rb(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
   const int zc = fused_sweep_chunk(L, TX, c != nullptr);
-  dim3 g(cdiv(L.n0, TX), cdiv(L.n1, RB_TY), cdiv(L.n2, zc));
+  constexpr int NT = RbShape<TX>::THREADS;
+  dim3 g(cdiv(L.n0, TX), cdiv(L.n1, RbShape<TX>::TY), cdiv(L.n2, zc));
   if (c)
-    launch_k(k_sweep_rb<T, G, TX, true>, g, RB_THREADS, fused_sweep_smem<T, TX>(true), st, L, uin, uout, f, c, zc);
+    launch_k(k_sweep_rb<T, G, TX, true>, g, NT, fused_sweep_smem<T, TX>(true), st, L, uin, uout, f, c, zc);
   else
-    launch_k(k_sweep_rb<T, G, TX, false>, g, RB_THREADS, fused_sweep_smem<T, TX>(false), st, L, uin, uout, f,
+    launch_k(k_sweep_rb<T, G, TX, false>, g, NT, fused_sweep_smem<T, TX>(false), st, L, uin, uout, f,
              nullptr, zc);
 }
 

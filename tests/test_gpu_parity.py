@@ -468,12 +468,14 @@ FUSED_CASES = [
     # (n, sweeps): one 64 x 8 column in x, y with fewer planes than a chunk;
     # several columns and z-chunks (re-relaxed red planes at chunk edges);
     # more blocks than fit on the device at once (blocks of a later wave
-    # must still read only the sweep's input); a level narrower than one
-    # 64-cell column (colour passes)
+    # must still read only the sweep's input); 128-cell columns of 16 rows
+    # and, on a level of 8 rows, 64-cell columns of 8; a level narrower than
+    # one 64-cell column (colour passes)
     ([64, 8, 4], 2),
     ([128, 32, 64], 3),
     ([64, 16, 32], 4),
     ([256, 128, 64], 2),
+    ([128, 8, 8], 2),
     ([32, 16, 8], 2),
 ]
 
