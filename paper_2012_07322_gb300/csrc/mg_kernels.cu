@@ -3,6 +3,7 @@
 // restriction, Kwak prolongation) and the single-block coarsest solver, with
 // their host-side launchers.  Sec. 2.7 of the paper.
 #include <atomic>
+#include <type_traits>
 
 #include "mg_internal.h"
 #include "mg_kernels.cuh"
@@ -353,7 +354,7 @@ __device__ __forceinline__ void rb_red_ring(const LevelView<T>& L, const RbPlane
 }
 
 template <typename T, int G, int TX, bool HAS_C>
-__global__ void __launch_bounds__(RbShape<TX>::THREADS, G == CART && TX == 128 ? 2 : 1) k_sweep_rb(LevelView<T> L, const T* __restrict__ uin,
+__global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ? 2 : 1) : (sizeof(T) == 4 ? 4 : 2)) k_sweep_rb(LevelView<T> L, const T* __restrict__ uin,
                                                          T* __restrict__ uout, const T* __restrict__ f,
                                                          const T* __restrict__ c, int zc) {
   pdl_entry();
@@ -414,6 +415,7 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, G == CART && TX == 128 ?
   using V2 = typename Vec2<T>::type;  // pairs (i, i + 1): n0 a multiple of TX, rows 16-byte aligned
   V2 rm2[NH], rm1[NH], r0[NH], rp1[NH];
   const int po = (2 * lane + RB_HX) + (w + RB_HY) * BX;  // the lane's first pair in a staged plane
+  T* const orow = uout + L.idx(i0 + 2 * lane, j0 + w, 0);  // ... and in plane 0 of uout
   for (int s = z0 - 1; s <= z1; ++s) {
     const int bn2 = next6(bu);
     stage(s + 2, bn2);
@@ -439,24 +441,35 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, G == CART && TX == 128 ?
     }
 #pragma unroll
     for (int h = 0; h < NH; ++h) rp1[h] = *reinterpret_cast<const V2*>(su + bu * BP + po + 64 * h);  // plane s + 1
-    const int q = (i0 + j0 + s + w) & 1;  // the pair's red cell of plane s, black cell of plane s - 1
+    // the pair's red cell of plane s and black cell of plane s - 1: the same
+    // for the whole warp, so each update below is compiled for both values
+    const int q = (i0 + j0 + s + w) & 1;
     if (PER || (s >= 0 && s < L.n2)) {
       const int bf = (s & (RB_NF - 1)) * BP;
       T* P = su + bs * BP;
       const T* F = sf + bf;
       const T* Cc = sc + bf;
+      auto red = [&](auto QC) {
+        constexpr int Q = decltype(QC)::value;
 #pragma unroll
-      for (int h = 0; h < NH; ++h) {
-        const int o = po + 64 * h + q;
-        const T uc = q ? r0[h].y : r0[h].x, other = q ? r0[h].x : r0[h].y;
-        const T ue = q ? P[o + 1] : other, uw = q ? other : P[o - 1];
-        const T v = rb_new_value<T, G, HAS_C>(rb_pick(q, lc.k[h][0], lc.k[h][1]), iD0, uc, ue, uw, P[o + BX],
-                                              P[o - BX], q ? rp1[h].y : rp1[h].x, q ? rm1[h].y : rm1[h].x, F[o],
-                                              HAS_C ? Cc[o] : T(0));
-        P[o] = v;
-        r0[h].x = q ? r0[h].x : v;
-        r0[h].y = q ? v : r0[h].y;
-      }
+        for (int h = 0; h < NH; ++h) {
+          const int o = po + 64 * h + Q;
+          const T uc = Q ? r0[h].y : r0[h].x, other = Q ? r0[h].x : r0[h].y;
+          const T ue = Q ? P[o + 1] : other, uw = Q ? other : P[o - 1];
+          const T v = rb_new_value<T, G, HAS_C>(G == CART ? lc.k[0][0] : lc.k[h][Q], iD0, uc, ue, uw, P[o + BX],
+                                                P[o - BX], Q ? rp1[h].y : rp1[h].x, Q ? rm1[h].y : rm1[h].x, F[o],
+                                                HAS_C ? Cc[o] : T(0));
+          P[o] = v;
+          if (Q)
+            r0[h].y = v;
+          else
+            r0[h].x = v;
+        }
+      };
+      if (q)
+        red(std::integral_constant<int, 1>{});
+      else
+        red(std::integral_constant<int, 0>{});
       const RbPlanes<T> R{su + bd * BP, P, su + bu * BP, F, Cc};
       rb_red_ring<T, G, TX, HAS_C>(L, R, i0, j0, s, lc, iD0);
     }
@@ -469,18 +482,28 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, G == CART && TX == 128 ?
       const T* P = su + bd * BP;
       const T* F = sf + bf;
       const T* Cc = sc + bf;
+      T* out = orow + (long)sb * L.sy;
+      auto black = [&](auto QC) {
+        constexpr int Q = decltype(QC)::value;
 #pragma unroll
-      for (int h = 0; h < NH; ++h) {
-        const int o = po + 64 * h + q;
-        const T uc = q ? rm1[h].y : rm1[h].x, other = q ? rm1[h].x : rm1[h].y;
-        const T ue = q ? P[o + 1] : other, uw = q ? other : P[o - 1];
-        const T v = rb_new_value<T, G, HAS_C>(rb_pick(q, lc.k[h][0], lc.k[h][1]), iD0, uc, ue, uw, P[o + BX],
-                                              P[o - BX], q ? r0[h].y : r0[h].x, q ? rm2[h].y : rm2[h].x, F[o],
-                                              HAS_C ? Cc[o] : T(0));
-        rm1[h].x = q ? rm1[h].x : v;
-        rm1[h].y = q ? v : rm1[h].y;
-        *reinterpret_cast<V2*>(uout + L.idx(i0 + 64 * h + 2 * lane, j0 + w, sb)) = rm1[h];
-      }
+        for (int h = 0; h < NH; ++h) {
+          const int o = po + 64 * h + Q;
+          const T uc = Q ? rm1[h].y : rm1[h].x, other = Q ? rm1[h].x : rm1[h].y;
+          const T ue = Q ? P[o + 1] : other, uw = Q ? other : P[o - 1];
+          const T v = rb_new_value<T, G, HAS_C>(G == CART ? lc.k[0][0] : lc.k[h][Q], iD0, uc, ue, uw, P[o + BX],
+                                                P[o - BX], Q ? r0[h].y : r0[h].x, Q ? rm2[h].y : rm2[h].x, F[o],
+                                                HAS_C ? Cc[o] : T(0));
+          if (Q)
+            rm1[h].y = v;
+          else
+            rm1[h].x = v;
+          *reinterpret_cast<V2*>(out + 64 * h) = rm1[h];
+        }
+      };
+      if (q)
+        black(std::integral_constant<int, 1>{});
+      else
+        black(std::integral_constant<int, 0>{});
     }
 #pragma unroll
     for (int h = 0; h < NH; ++h) {

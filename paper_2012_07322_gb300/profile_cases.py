@@ -5,10 +5,11 @@
     python -m paper_2012_07322_gb300.profile_cases xcfc      # one full mixed xCFC solve, 128x64x64
 
 Each case runs through the C ABI and exits 0 on success, so the same command
-can be profiled after it has run once without a profiler.  The xCFC cases
-switch the library's event timing on, which makes every cycle run as direct
-launches under a host loop (no CUDA graphs), so that a profiler sees each
-kernel as its own launch.
+can be profiled after it has run once without a profiler.  Every case
+switches the library's event timing on, which makes every cycle run as
+direct launches under a host loop (no CUDA graphs): a profiler does not see
+the kernels of a graph that holds a conditional (while) node, which is how
+the library otherwise runs the cycle loop.
 """
 import sys
 
@@ -23,6 +24,7 @@ def divb256(precision="mixed"):
     h = mg.Hierarchy(mg.grid_desc("cart", [n] * 3, [-1.0] * 3, [1.0] * 3, precision=precision, tol=1e-10,
                                   max_cycles=200, stall_window=0))
     rep = None
+    mg.mg_profile_enable(h, True)
     for _ in range(2):
         rep = mg.mg_clean_divB(h, [b.clone() for b in B])
     h.close()
