@@ -133,7 +133,7 @@ FP64_FMA_PER_SM_CLK = 2
 # level-0 FP32 vector colour pass (ghost push included) and the FP64 vector
 # residual of the 128x64x64 spherical solve, and the 256^3 one-launch FP32
 # sweep.  A kernel changed since its capture has none.
-TRAFFIC_PER_LAUNCH = {"smooth32_vec": 9.82e6, "resid64_vec": 29.80e6, "sweep32_fused": 185.34e6}
+TRAFFIC_PER_LAUNCH = {"smooth32_vec": 9.82e6, "resid64_vec": 29.80e6, "sweep32_fused": 188.61e6}
 
 
 class ClockSampler:

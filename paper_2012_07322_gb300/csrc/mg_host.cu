@@ -44,6 +44,10 @@ struct Level {
   double *u[3] = {}, *uh[3] = {}, *f[3] = {}, *r[3] = {}, *s0 = nullptr, *s1 = nullptr;
   float *e[3] = {}, *f32[3] = {}, *k32 = nullptr;
   GhostPush push[3][2];  // per component and colour (Dirichlet-0 ghosts), or empty
+  // tensor maps of the FP32 one-launch sweep (inputs e[leg], f32[0], k32)
+  // per sweep leg, when the level stages its planes with them
+  SweepMaps sweep_maps[2];
+  bool maps_on = false;
   long cells() const { return (long)n[0] * n[1] * n[2]; }
 };
 
@@ -131,6 +135,7 @@ struct mg_hierarchy {
     uint64_t graph_launches = 0;
   } amr;
   bool prof_on = false;
+  bool maps_on = false;  // some level's one-launch sweeps stage with tensor maps (d_red[7]: their timeout flag)
   bool fold_k32 = false;  // while capturing a V-cycle of eq. psi: K is restricted on the way down
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_cls;
@@ -723,7 +728,8 @@ void smooth32(mg_hierarchy* H, const Eq& e, int l, int nsweeps) {
     for (; s0 + 2 <= nsweeps; s0 += 2) {
       for (int leg = 0; leg < 2; ++leg) {
         long tok = prof_begin(H, l, MG_PROF_SWEEP32_FUSED, L.cells());
-        launch_sweep_fused<float>(v, L.e[leg], L.e[1 - leg], L.f32[0], K, H->st);
+        launch_sweep_fused<float>(v, L.e[leg], L.e[1 - leg], L.f32[0], K, H->st,
+                                  L.maps_on ? &L.sweep_maps[leg] : nullptr);
         prof_end(H, tok);
       }
     }
@@ -1421,7 +1427,25 @@ int run_loop_graph(mg_hierarchy* H, const Eq& e, double* ax, double* afp, double
   return S.status;
 }
 
+int run_solve_body(mg_hierarchy* H, const Eq& e, mg_solve_report* rep);
+
+// A solve, then the timeout flag of the tensor-map staged sweeps (set when a
+// block gave up waiting for a staged plane and stopped early).
 int run_solve(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
+  const int st = run_solve_body(H, e, rep);
+  if (H->maps_on) {
+    unsigned long long flag = 0;
+    CK(cudaMemcpyAsync(&flag, H->d_red + 7, sizeof(flag), cudaMemcpyDeviceToHost, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    if (flag) {
+      CK(cudaMemsetAsync(H->d_red + 7, 0, sizeof(flag), H->st));
+      return fail(MG_ERR_CUDA, "one-launch sweep: a staged plane did not arrive");
+    }
+  }
+  return st;
+}
+
+int run_solve_body(mg_hierarchy* H, const Eq& e, mg_solve_report* rep) {
   auto t0 = std::chrono::steady_clock::now();
   H->updates = 0;
   const mg_grid_desc& d = H->d;
@@ -2098,6 +2122,19 @@ int mg_create_hierarchy(const mg_grid_desc* desc, void* cuda_stream, mg_hierarch
     L.v64.vc = L.vc64;
     L.v32 = make_view<float>(&H->d, L, L.ti32, L.tj32);
     L.v32.vc = L.vc32;
+    if (H->d.precision == MG_MIXED && sweep_uses_maps(L.v32)) {
+      bool ok = true;
+      for (int leg = 0; leg < 2; ++leg) {
+        SweepMaps& m = L.sweep_maps[leg];
+        std::memset(&m, 0, sizeof(m));
+        ok = ok && sweep_plane_map(&m.u, L.e[leg], L.v32) && sweep_plane_map(&m.f, L.f32[0], L.v32) &&
+             (!L.k32 || sweep_plane_map(&m.c, L.k32, L.v32));
+        m.err = H->d_red + 7;
+        m.on = 1;
+      }
+      L.maps_on = ok;
+      H->maps_on = H->maps_on || ok;
+    }
   }
   if (H->d.divb_variant == MG_DIVB_EXACT) {
     const mg_grid_desc c = class_desc(&H->d);

@@ -1,5 +1,6 @@
 // Host-side declarations shared by the library's translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -106,8 +107,26 @@ inline long row_stride(int n0) { return (n0 + 2 * ROW_PAD + ROW_PAD - 1) / ROW_P
 // latency per sweep) made the solve slower by 9-11 ms, since programmatic
 // dependent launch hides most of each colour pass's launch latency while
 // the one-launch sweep's staging is a serial prologue.
+// Tensor maps of the one-launch sweep's inputs, for staging its planes with
+// the tensor memory accelerator (cp.async.bulk.tensor, one thread per block,
+// mbarrier completion): FP32 Cartesian levels of 128-cell columns.  Each map
+// views a level array as (padded row, row, plane) with a box of one staged
+// plane (136 x 20 values); err (device) is set when a wait for a staged
+// plane exceeds its iteration limit (the launch then stops early).
+struct SweepMaps {
+  CUtensorMap u, f, c;
+  unsigned long long* err;
+  int on;
+};
+// Encodes the map of one FP32 level array for the sweep's plane box; false
+// when the driver entry point is missing or rejects the layout.
+bool sweep_plane_map(CUtensorMap* m, const float* base, const LevelView<float>& L);
+// Whether the level's sweeps stage with tensor maps (FP32, Cartesian,
+// 128-cell columns).
+bool sweep_uses_maps(const LevelView<float>& L);
 template <typename T>
-bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st);
+bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st,
+                        const SweepMaps* maps = nullptr);
 template <typename T>
 void init_fused_sweep_attributes();
 constexpr long FUSED_CURV_CELLS = 1L << 22;

@@ -3,6 +3,7 @@
 // restriction, Kwak prolongation) and the single-block coarsest solver, with
 // their host-side launchers.  Sec. 2.7 of the paper.
 #include <atomic>
+#include <cstring>
 #include <type_traits>
 
 #include "mg_internal.h"
@@ -132,6 +133,36 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+// Tensor-memory-accelerator staging: one thread per block issues a plane's
+// copy, which signals the plane slot's mbarrier with its byte count.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* m, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_plane(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                          unsigned long long* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(m))
+      : "memory");
+}
+// Iterations of mbarrier.try_wait (each suspends for a bounded time) before
+// a wait for a staged plane gives up.
+constexpr long RB_WAIT_LIMIT = 1L << 22;
 
 // The 16-byte pieces of the staged box this thread copies, fixed for the
 // whole march: global offset within a plane, offset in the plane buffer.
@@ -353,14 +384,40 @@ __device__ __forceinline__ void rb_red_ring(const LevelView<T>& L, const RbPlane
   }
 }
 
+// FP32 Cartesian sweeps of 128-cell columns stage their planes with the
+// tensor memory accelerator when the launch carries tensor maps: one thread
+// issues a plane group's copies (u plane p, f and c plane p - 1) into the
+// group's slot and arms the slot's mbarrier with their bytes; the block
+// waits on the slot instead of on its own 16-byte copies.
+template <typename T, int G, int TX>
+__host__ __device__ constexpr bool rb_tma() {
+  return sizeof(T) == 4 && G == CART && TX == 128;
+}
+
 template <typename T, int G, int TX, bool HAS_C>
-__global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ? 2 : 1) : (sizeof(T) == 4 ? 4 : 2)) k_sweep_rb(LevelView<T> L, const T* __restrict__ uin,
-                                                         T* __restrict__ uout, const T* __restrict__ f,
-                                                         const T* __restrict__ c, int zc) {
+__global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ? 2 : 1) : (sizeof(T) == 4 ? 4 : 2))
+    k_sweep_rb(LevelView<T> L, const T* __restrict__ uin, T* __restrict__ uout, const T* __restrict__ f,
+               const T* __restrict__ c, int zc, const __grid_constant__ SweepMaps M) {
   pdl_entry();
   constexpr int BX = RbShape<TX>::BX, BP = RbShape<TX>::BP;
   constexpr bool PER = G != CART;  // periodic dimension 2
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool TMA = rb_tma<T, G, TX>();
+  static_assert(!TMA || (BP * sizeof(T)) % 128 == 0, "plane buffers 128-byte aligned");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long mbar[RB_NU];
+  __shared__ int s_abort;
+  // (copies land on 128-byte boundaries: a misaligned dynamic shared
+  // memory base would take the 16-byte copies instead)
+  const bool tma = TMA && M.on && (smem_u32(smem_raw) & 127u) == 0;
+  if (tma) {
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < RB_NU; ++q) mbar_init(&mbar[q]);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      s_abort = 0;
+    }
+    __syncthreads();
+  }
+  unsigned ph = 0, pending = 0;  // per slot: parity of its next phase, copies not yet waited for
   T* su = reinterpret_cast<T*>(smem_raw);
   T* sf = su + RB_NU * BP;
   T* sc = sf + RB_NF * BP;
@@ -381,15 +438,46 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
   // group p: u plane p (into u buffer bu) and f, c plane p - 1, for the
   // planes the chunk needs (periodic levels: the wrapped planes)
   auto stage = [&](int p, int bu) {
-    if ((PER || (p >= 0 && p < L.n2)) && p >= z0 - 2 && p <= z1 + 1)
-      pc.copy(su + bu * BP, uin, (long)wrap(p) * L.sy);
+    const bool uok = (PER || (p >= 0 && p < L.n2)) && p >= z0 - 2 && p <= z1 + 1;
     const int pf = p - 1;
-    if ((PER || (pf >= 0 && pf < L.n2)) && pf >= z0 - 1 && pf <= z1) {
-      const int bf = (pf & (RB_NF - 1)) * BP;
+    const bool fok = (PER || (pf >= 0 && pf < L.n2)) && pf >= z0 - 1 && pf <= z1;
+    const int bf = (pf & (RB_NF - 1)) * BP;
+    if constexpr (TMA) {
+      if (tma) {
+        // box origin: column i0 - 4 (padded-row index i0), row j0 - 2 (row
+        // index j0 - 1: the row above the ghost row reads as zeros), plane
+        if (threadIdx.x == 0) {
+          constexpr unsigned PB = (unsigned)(BP * sizeof(T));
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_expect(&mbar[bu], (uok ? PB : 0u) + (fok ? PB * (HAS_C ? 2u : 1u) : 0u));
+          if (uok) tma_plane(su + bu * BP, &M.u, i0, j0 - 1, wrap(p) + 1, &mbar[bu]);
+          if (fok) {
+            tma_plane(sf + bf, &M.f, i0, j0 - 1, wrap(pf) + 1, &mbar[bu]);
+            if (HAS_C) tma_plane(sc + bf, &M.c, i0, j0 - 1, wrap(pf) + 1, &mbar[bu]);
+          }
+        }
+        pending |= 1u << bu;
+        return;
+      }
+    }
+    if (uok) pc.copy(su + bu * BP, uin, (long)wrap(p) * L.sy);
+    if (fok) {
       pc.copy(sf + bf, f, (long)wrap(pf) * L.sy);
       if (HAS_C) pc.copy(sc + bf, c, (long)wrap(pf) * L.sy);
     }
     cp_async_commit();
+  };
+  // wait for the group in slot q (tensor-map staging); false after the
+  // iteration limit
+  auto wait_slot = [&](int q) {
+    const unsigned par = (ph >> q) & 1u;
+    for (long it = 0; it < RB_WAIT_LIMIT; ++it)
+      if (mbar_try(&mbar[q], par)) {
+        ph ^= 1u << q;
+        pending &= ~(1u << q);
+        return true;
+      }
+    return false;
   };
   auto next6 = [](int b) { return b == RB_NU - 1 ? 0 : b + 1; };
   // u buffers of consecutive planes are consecutive modulo RB_NU
@@ -419,8 +507,25 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
   for (int s = z0 - 1; s <= z1; ++s) {
     const int bn2 = next6(bu);
     stage(s + 2, bn2);
-    cp_async_wait<1>();  // u plane s + 1 and f, c plane s have landed
-    __syncthreads();
+    if (tma) {
+      // u plane s + 1 and f, c plane s (the first step: the prologue's three)
+      bool ok = true;
+      if (s == z0 - 1) ok = wait_slot(bd) && wait_slot(bs);
+      ok = ok && wait_slot(bu);
+      if (!ok) s_abort = 1;
+      __syncthreads();
+      if (s_abort) {
+        // a staged plane never arrived: report it, let the copies still in
+        // flight land (again within the limit) and stop
+        if (threadIdx.x == 0) atomicExch(M.err, 1ULL);
+        for (int q = 0; q < RB_NU; ++q)
+          if (pending & (1u << q)) wait_slot(q);
+        return;
+      }
+    } else {
+      cp_async_wait<1>();  // u plane s + 1 and f, c plane s have landed
+      __syncthreads();
+    }
     // outer ghosts of the planes about to be relaxed
     if (edge_xy) {
       if (s == z0 - 1 && (PER || s >= 0)) rb_fix_ghosts<T, TX>(L, su + bs * BP, i0, j0, wrap(s));
@@ -516,7 +621,7 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
     bs = bu;
     bu = bn2;
   }
-  cp_async_wait<0>();
+  if (!tma) cp_async_wait<0>();
 }
 
 template <typename T>
@@ -1142,39 +1247,79 @@ int fused_sweep_chunk(const LevelView<T>& L, int tx, bool with_c) {
 }
 
 template <typename T, int G, int TX>
-static void launch_rb(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
+static void launch_rb(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st,
+                      const SweepMaps* maps) {
   const int zc = fused_sweep_chunk(L, TX, c != nullptr);
   constexpr int NT = RbShape<TX>::THREADS;
   dim3 g(cdiv(L.n0, TX), cdiv(L.n1, RbShape<TX>::TY), cdiv(L.n2, zc));
+  SweepMaps none;
+  std::memset(&none, 0, sizeof(none));
+  const SweepMaps& M = (rb_tma<T, G, TX>() && maps) ? *maps : none;
   if (c)
-    launch_k(k_sweep_rb<T, G, TX, true>, g, NT, fused_sweep_smem<T, TX>(true), st, L, uin, uout, f, c, zc);
+    launch_k(k_sweep_rb<T, G, TX, true>, g, NT, fused_sweep_smem<T, TX>(true), st, L, uin, uout, f, c, zc, M);
   else
     launch_k(k_sweep_rb<T, G, TX, false>, g, NT, fused_sweep_smem<T, TX>(false), st, L, uin, uout, f,
-             nullptr, zc);
+             nullptr, zc, M);
 }
 
 template <typename T, int G>
-static void launch_rb_g(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
+static void launch_rb_g(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st,
+                        const SweepMaps* maps) {
   if constexpr (sizeof(T) == 4) {
     if (fused_sweep_tx(L) == 128) {
-      launch_rb<T, G, 128>(L, uin, uout, f, c, st);
+      launch_rb<T, G, 128>(L, uin, uout, f, c, st, maps);
       return;
     }
   }
-  launch_rb<T, G, 64>(L, uin, uout, f, c, st);
+  launch_rb<T, G, 64>(L, uin, uout, f, c, st, maps);
 }
 
 template <typename T>
-bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st) {
+bool launch_sweep_fused(const LevelView<T>& L, const T* uin, T* uout, const T* f, const T* c, cudaStream_t st,
+                        const SweepMaps* maps) {
   if (!fused_sweep_applies(L)) return false;
   count_launch();
   if (L.geom == CART)
-    launch_rb_g<T, CART>(L, uin, uout, f, c, st);
+    launch_rb_g<T, CART>(L, uin, uout, f, c, st, maps);
   else if (L.geom == CYL)
-    launch_rb_g<T, CYL>(L, uin, uout, f, c, st);
+    launch_rb_g<T, CYL>(L, uin, uout, f, c, st, maps);
   else
-    launch_rb_g<T, SPH>(L, uin, uout, f, c, st);
+    launch_rb_g<T, SPH>(L, uin, uout, f, c, st, maps);
   return true;
+}
+
+bool sweep_uses_maps(const LevelView<float>& L) {
+  return fused_sweep_applies(L) && L.geom == CART && fused_sweep_tx(L) == 128;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+bool sweep_plane_map(CUtensorMap* m, const float* base, const LevelView<float>& L) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<Encode>(fn);
+    cudaGetLastError();
+  }
+  if (!enc || !base) return false;
+  // (padded row index, row index, plane index) of the ghosted array; cell
+  // (i, j, k) sits at (i + ROW_PAD, j + 1, k + 1)
+  const cuuint64_t dims[3] = {(cuuint64_t)L.sx, (cuuint64_t)(L.n1 + 2), (cuuint64_t)(L.n2 + 2)};
+  const cuuint64_t strides[2] = {(cuuint64_t)L.sx * sizeof(float), (cuuint64_t)L.sy * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)RbShape<128>::BX, (cuuint32_t)RbShape<128>::BY, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename T>
@@ -1413,7 +1558,8 @@ void launch_add_correction(const LevelView<double>& L, int ncomp, double* const 
 
 // explicit instantiations
 #define GMG_INST(T)                                                                                            \
-  template bool launch_sweep_fused<T>(const LevelView<T>&, const T*, T*, const T*, const T*, cudaStream_t);    \
+  template bool launch_sweep_fused<T>(const LevelView<T>&, const T*, T*, const T*, const T*, cudaStream_t,      \
+                                      const SweepMaps*);                                                          \
   template void init_fused_sweep_attributes<T>();                                                              \
   template void launch_smooth_scalar<T>(const LevelView<T>&, int, T*, const T*, const T*, const T*, int,       \
                                         cudaStream_t);                                                          \

@@ -409,6 +409,31 @@ def test_divb_cleaning_parity(mg, n):
         assert abs(rg[key] - ro[key]) <= 1e-9 * ro["max_div_before"], key
 
 
+def test_divb_cleaning_parity_mixed_staged_planes(mg):
+    """Mixed precision on a Cartesian level of 128-cell rows: the finest
+    level's one-launch FP32 sweeps stage their planes with tensor maps (the
+    next level's with 16-byte copies); the cleaned field and Phi agree with
+    the FP64 oracle's fixed point within 1e-9.  Both iterate to the relative
+    residual 1e-12: the two take different routes, and at 1e-10 their Phi
+    differ by up to the error that residual leaves on this Neumann problem
+    (2.6e-9 measured)."""
+    B = [b[:16, :32].copy() for b in inputs.divb_field(n=128, n_modes=32, k_max=8)]
+    d, gd = descs(mg, "cart", [128, 32, 16], [-1.0, -1.0, -1.0], [1.0, -0.5, -0.75], tol=1e-12, max_cycles=1000,
+                  precision="mixed")
+    Bo = [b.copy() for b in B]
+    phi = np.zeros((16, 32, 128))
+    ro = o.clean_divb(d, Bo, phi)
+    h = mg.Hierarchy(gd)
+    Bt = [dev(b) for b in B]
+    pt = torch.zeros((16, 32, 128), dtype=torch.float64, device="cuda")
+    rg = mg.mg_clean_divB(h, Bt, pt)
+    h.close()
+    assert rg["solve"]["status"] == "ok" and rg["solve"]["rel"] <= 1e-12
+    assert relerr(host(pt), phi) < 1e-9
+    for k in range(3):
+        assert relerr(host(Bt[k]), Bo[k]) < 1e-9
+
+
 # ------------------------------------------------------ mixed precision
 
 
