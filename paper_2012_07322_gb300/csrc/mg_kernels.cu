@@ -405,19 +405,21 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
   static_assert(!TMA || (BP * sizeof(T)) % 128 == 0, "plane buffers 128-byte aligned");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long mbar[RB_NU];
-  __shared__ int s_abort;
   // (copies land on 128-byte boundaries: a misaligned dynamic shared
   // memory base would take the 16-byte copies instead)
   const bool tma = TMA && M.on && (smem_u32(smem_raw) & 127u) == 0;
+  // the copies are issued by lane 0 of the last warp (the ring cells fall
+  // on the first warps)
+  constexpr int ISSUER = RbShape<TX>::THREADS - 32;
   if (tma) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == ISSUER) {
       for (int q = 0; q < RB_NU; ++q) mbar_init(&mbar[q]);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      s_abort = 0;
     }
     __syncthreads();
   }
   unsigned ph = 0, pending = 0;  // per slot: parity of its next phase, copies not yet waited for
+  bool timed_out = false;
   T* su = reinterpret_cast<T*>(smem_raw);
   T* sf = su + RB_NU * BP;
   T* sc = sf + RB_NF * BP;
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
       if (tma) {
         // box origin: column i0 - 4 (padded-row index i0), row j0 - 2 (row
         // index j0 - 1: the row above the ghost row reads as zeros), plane
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == ISSUER) {
           constexpr unsigned PB = (unsigned)(BP * sizeof(T));
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_expect(&mbar[bu], (uok ? PB : 0u) + (fok ? PB * (HAS_C ? 2u : 1u) : 0u));
@@ -508,20 +510,15 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
     const int bn2 = next6(bu);
     stage(s + 2, bn2);
     if (tma) {
-      // u plane s + 1 and f, c plane s (the first step: the prologue's three)
+      // u plane s + 1 and f, c plane s (the first step: the prologue's
+      // three).  Each thread waits for the copies itself, so no barrier
+      // follows: the ghosts fixed below (plane s + 1) are read in the next
+      // step, after this step's second barrier, and the first step has a
+      // barrier of its own.
       bool ok = true;
       if (s == z0 - 1) ok = wait_slot(bd) && wait_slot(bs);
       ok = ok && wait_slot(bu);
-      if (!ok) s_abort = 1;
-      __syncthreads();
-      if (s_abort) {
-        // a staged plane never arrived: report it, let the copies still in
-        // flight land (again within the limit) and stop
-        if (threadIdx.x == 0) atomicExch(M.err, 1ULL);
-        for (int q = 0; q < RB_NU; ++q)
-          if (pending & (1u << q)) wait_slot(q);
-        return;
-      }
+      timed_out = timed_out || !ok;
     } else {
       cp_async_wait<1>();  // u plane s + 1 and f, c plane s have landed
       __syncthreads();
@@ -578,7 +575,18 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
       const RbPlanes<T> R{su + bd * BP, P, su + bu * BP, F, Cc};
       rb_red_ring<T, G, TX, HAS_C>(L, R, i0, j0, s, lc, iD0);
     }
-    __syncthreads();
+    if (tma) {
+      if (__syncthreads_or(timed_out)) {
+        // a staged plane never arrived: report it, let the copies still in
+        // flight land (again within the limit) and stop
+        if (threadIdx.x == ISSUER) atomicExch(M.err, 1ULL);
+        for (int q = 0; q < RB_NU; ++q)
+          if (pending & (1u << q)) wait_slot(q);
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
     const int sb = s - 1;
     if (sb >= z0) {
       // black cells of plane sb = s - 1 (its red neighbours: planes s - 2,
