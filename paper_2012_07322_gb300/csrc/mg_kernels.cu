@@ -2,6 +2,7 @@
 // fused norms, FAS coarse right-hand side, ghost fill, volume-weighted
 // restriction, Kwak prolongation) and the single-block coarsest solver, with
 // their host-side launchers.  Sec. 2.7 of the paper.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <type_traits>
@@ -1195,6 +1196,8 @@ int fused_sweep_tx(const LevelView<T>& L) {
 
 // Blocks of k_sweep_rb resident on the whole device, [geometry][TX == 128]
 // [with c], set when a hierarchy is created (outside any stream capture).
+static int g_fused_sms = 0;
+
 template <typename T>
 struct FusedCapacity {
   static int blocks[3][2][2];
@@ -1229,23 +1232,31 @@ void init_fused_sweep_attributes() {
   int d = 0, sms = 0;
   cudaGetDevice(&d);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms < 1) sms = 1;
+  g_fused_sms = sms;
   set_fused_capacity_g<T, CART>(sms);
   set_fused_capacity_g<T, CYL>(sms);
   set_fused_capacity_g<T, SPH>(sms);
 }
 
-// Planes per block: each block re-relaxes two red planes beyond its chunk,
-// and blocks beyond one device-full run in further waves; take the chunk
-// length with the fewest plane steps per SM slot.
+// Planes per block: each block re-relaxes two red planes beyond its chunk
+// and marches two steps more than it stores.  The busiest SM decides the
+// time, so take the chunk length (any, 4 to 64 planes) with the fewest
+// plane steps on the SM that gets the most blocks: with the blocks resident
+// at once, a 256^3 level of 32 columns takes 9 chunks of 29 planes (288
+// blocks, two on almost every SM) rather than 8 of 32 (256 blocks: one SM
+// in three runs a single block, the others two blocks of 34 steps).
 template <typename T>
 int fused_sweep_chunk(const LevelView<T>& L, int tx, bool with_c) {
   const long cols = (long)cdiv(L.n0, tx) * cdiv(L.n1, tx == 128 ? RbShape<128>::TY : RbShape<64>::TY);
   const long cap = FusedCapacity<T>::blocks[L.geom][tx == 128][with_c];
+  const long sms = g_fused_sms > 0 ? g_fused_sms : 1;
   int best = 8;
   long best_cost = -1;
-  for (int zc = 4; zc <= 64; zc *= 2) {
-    const long blocks = cols * (long)cdiv(L.n2, zc);
-    const long cost = ((blocks + cap - 1) / cap) * (2L * (zc < L.n2 ? zc : L.n2) + 5);
+  for (int zc = 4; zc <= 64; ++zc) {
+    const long chunks = cdiv(L.n2, zc), blocks = cols * chunks;
+    const long len = cdiv(L.n2, chunks);  // the longest chunk
+    const long per_sm = ((blocks + cap - 1) / cap) * ((std::min(blocks, cap) + sms - 1) / sms);
+    const long cost = per_sm * (2L * len + 5);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       best = zc;
