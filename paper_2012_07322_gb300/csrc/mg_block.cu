@@ -29,13 +29,32 @@ __device__ __forceinline__ BcLevel bc_level(const BlockCycle32& P, float* sm, in
   const BlockLevel32& B = P.lv[l];
   BcLevel o;
   o.v = B.v;
+  // the coefficient tables and c were copied into shared memory when the
+  // kernel started: every phase reads them, and from HBM (through an L1
+  // mostly given to shared memory) each read is an L2 round trip
+  o.v.ti = sm + B.ti_at;
+  o.v.tj = sm + B.tj_at;
   for (int c = 0; c < 3; ++c) {
     o.e[c] = sm + B.e[c];
     o.f[c] = sm + B.f32[c];
     o.r[c] = sm + B.r32[c];
   }
-  o.k = B.k32;
+  o.k = B.k32 ? sm + B.k_at : nullptr;
   return o;
+}
+
+// Copies of every level's coefficient tables and c into shared memory.
+__device__ void bc_stage_tables(const BlockCycle32& P, float* sm) {
+  for (int l = 0; l < P.nl; ++l) {
+    const BlockLevel32& B = P.lv[l];
+    const int nti = NTI * (B.v.n0 + 2), ntj = NTJ * (B.v.n1 + 2);
+    for (int q = threadIdx.x; q < nti; q += blockDim.x) sm[B.ti_at + q] = B.v.ti[q];
+    for (int q = threadIdx.x; q < ntj; q += blockDim.x) sm[B.tj_at + q] = B.v.tj[q];
+    if (B.k32) {
+      const long ng = B.v.sy * (B.v.n2 + 2 * B.v.three);
+      for (long q = threadIdx.x; q < ng; q += blockDim.x) sm[B.k_at + q] = B.k32[q];
+    }
+  }
 }
 
 template <typename T>
@@ -214,6 +233,7 @@ __global__ void __launch_bounds__(BC_THREADS) k_block_vcycle32(const __grid_cons
   float* sm = reinterpret_cast<float*>(smem_raw);
   double* smd = reinterpret_cast<double*>(smem_raw + P.fp64_at);
   constexpr int nc = VEC ? 3 : 1;
+  bc_stage_tables(P, sm);
   {
     // level l0: right-hand side in, zero correction
     const BcLevel B = bc_level(P, sm, 0);

@@ -811,6 +811,9 @@ BlockCycle32 block_cycle_params(mg_hierarchy* H, const Eq& e, int l0) {
       }
     }
     B.k32 = hasK ? L.k32 : nullptr;
+    B.ti_at = take((long)NTI * (L.n[0] + 2));
+    B.tj_at = take((long)NTJ * (L.n[1] + 2));
+    B.k_at = hasK ? take(L.ng) : -1;
   }
   Level& Lc = H->L[H->nlev - 1];
   P.c64 = with_bc(Lc.v64, e.bc);

@@ -353,6 +353,7 @@ struct BlockLevel32 {
   LevelView<float> v;        // boundary rule applied
   int e[3], f32[3], r32[3];  // offsets (floats) of correction, right-hand side, residual in shared memory
   const float* k32;          // c of (L - c) e = f in HBM, null without
+  int ti_at, tj_at, k_at;    // offsets (floats) of the level's coefficient tables and of c in shared memory
 };
 struct BlockCycle32 {
   int nl, vec, nu1, nu2, coarse_sweeps;
