@@ -50,6 +50,14 @@ __device__ __forceinline__ void aa_st(T* p, const T (&v)[G]) {
   }
 }
 
+// An L2 prefetch of the 16-byte (or 8-byte) group at p.  The mixing kernels
+// issue them before waiting for the kernel they depend on, for data that
+// kernel does not write, so the DRAM reads overlap its tail; a prefetch
+// changes no value.
+__device__ __forceinline__ void l2_prefetch(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // u itself stays cached (the residual reads it next).
 template <int G>
 __device__ __forceinline__ void aa_ld_u(const double* p, double (&v)[G]) {
@@ -279,6 +287,23 @@ __global__ void __launch_bounds__(256, 2)
                      TC* __restrict__ dG, const __grid_constant__ AACols hcols, const AACols* __restrict__ dcols,
                      double* __restrict__ part, unsigned int* __restrict__ done, double* __restrict__ M,
                      double* __restrict__ gamma, unsigned long long* __restrict__ status) {
+  // Before waiting for the cycle's last kernel: L2 prefetches of this
+  // thread's first group of x, f', g' and the older dF columns (written by
+  // earlier cycles, not by that kernel).  The live columns come from the
+  // launch, or (device-side cycle loop) from the loop step of the previous
+  // cycle, several kernels back.
+  {
+    const long q0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (q0 < (long)L.n0 * L.n1 * L.n2 / G) {
+      const long o = aa_pos<G>(L, q0), vs = (long)ncomp * stride;
+      l2_prefetch(x + o);
+      l2_prefetch(fprev + o);
+      l2_prefetch(gprev + o);
+      const int n = dcols ? __ldcg(&dcols->n) : hcols.n;
+      for (int a = 0; a + 1 < n && a < AA_MAX; ++a)
+        l2_prefetch(dF + (long)(dcols ? __ldcg(&dcols->slot[a]) : hcols.slot[a]) * vs + o);
+    }
+  }
   pdl_entry();
   // the live columns: from the launch, or (device-side cycle loop) from
   // device memory written by the preceding loop step
@@ -380,6 +405,20 @@ __global__ void __launch_bounds__(256)
                  double* __restrict__ u2, double* __restrict__ x, const TC* __restrict__ dG,
                  const __grid_constant__ AACols hcols, const AACols* __restrict__ dcols,
                  const double* __restrict__ gamma, const unsigned long long* __restrict__ status) {
+  // Before waiting for the update kernel (whose last block solves the
+  // least-squares problem while the other SMs idle): L2 prefetches of this
+  // thread's first group of u and of the older dG columns, which that
+  // kernel does not write (it writes the newest column, gamma and status).
+  {
+    const long q0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (q0 < (long)L.n0 * L.n1 * L.n2 / G) {
+      const long p = aa_pos<G>(L, q0), vs = (long)ncomp * stride;
+      l2_prefetch(u0 + p);
+      const int n = dcols ? __ldcg(&dcols->n) : hcols.n;
+      for (int a = 0; a + 1 < n && a < AA_MAX; ++a)
+        l2_prefetch(dG + (long)(dcols ? __ldcg(&dcols->slot[a]) : hcols.slot[a]) * vs + p);
+    }
+  }
   pdl_entry();
   __shared__ AACols scols;
   if (dcols) {
