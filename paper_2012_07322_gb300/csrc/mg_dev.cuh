@@ -262,12 +262,15 @@ __device__ __noinline__ Nb6<T> lap_edge_neighbours(const LevelView<T>& L, const 
 // taken from the boundary rule on the fly and the origin / axis fluxes
 // (whose face areas vanish) dropped; periodic phi neighbours wrap.  D gets
 // the derivative with respect to the cell's own value (ghosts held fixed).
-template <typename T, int G>
+// INNER: the caller knows the cell is interior (a block whose cells all
+// are), and no edge code is compiled in.
+template <typename T, int G, bool INNER = false>
 __device__ __forceinline__ T lap_scalar(const LevelView<T>& L, const T* __restrict__ u, int i, int j, int k,
                                         long p, T& D) {
   const T uc = u[p];
   Nb6<T> nb;
-  const bool inner = i > 0 && i < L.n0 - 1 && j > 0 && j < L.n1 - 1 && (!L.three || (k > 0 && k < L.n2 - 1));
+  const bool inner =
+      INNER || (i > 0 && i < L.n0 - 1 && j > 0 && j < L.n1 - 1 && (!L.three || (k > 0 && k < L.n2 - 1)));
   if (inner) {
     nb.e = u[p + 1];
     nb.w = u[p - 1];
@@ -275,6 +278,7 @@ __device__ __forceinline__ T lap_scalar(const LevelView<T>& L, const T* __restri
     nb.s = u[p - L.sx];
     nb.up = L.three ? u[p + L.sy] : uc;
     nb.dn = L.three ? u[p - L.sy] : uc;
+  } else if constexpr (INNER) {
   } else if constexpr (sizeof(T) == 4) {
     // FP32: the edge rules inline (speculating them costs the FP32 units
     // little; a call passes the neighbours through local memory)

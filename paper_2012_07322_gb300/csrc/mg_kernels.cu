@@ -870,6 +870,18 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> Cv, T* __restrict__ u, co
   prolong_cell(F, Cv, u, uH, uhH, comp, i, j, k);
 }
 
+// A block of fine cells whose coarse reads (the parent and its face
+// neighbours) all lie inside the coarse level: i in [i0, i1) reads coarse
+// columns i0 / 2 - 1 .. (i1 - 1) / 2 + 1, likewise in j and k.  Such blocks
+// run the prolongation and the residual without the boundary rules, which
+// FP32 code otherwise evaluates for every cell.
+__device__ __forceinline__ bool block_coarse_interior(int n0, int n1, int n2, bool three) {
+  const int i0 = blockIdx.x * blockDim.x, i1 = i0 + blockDim.x;
+  const int j0 = blockIdx.y * blockDim.y, j1 = j0 + blockDim.y;
+  const int k0 = blockIdx.z * blockDim.z, k1 = k0 + blockDim.z;
+  return i0 >= 2 && i1 + 2 <= n0 && j0 >= 2 && j1 + 2 <= n1 && (!three || (k0 >= 2 && k1 + 2 <= n2));
+}
+
 template <typename T, int NC>
 __global__ void k_prolong3(LevelView<T> F, LevelView<T> Cv, Ptr3<T> u, CPtr3<T> uH, CPtr3<T> uhH, int vec) {
   pdl_entry();
@@ -877,8 +889,14 @@ __global__ void k_prolong3(LevelView<T> F, LevelView<T> Cv, Ptr3<T> u, CPtr3<T> 
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
   if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
+  if (block_coarse_interior(F.n0, F.n1, F.n2, F.three)) {
 #pragma unroll
-  for (int c = 0; c < NC; ++c) prolong_cell(F, Cv, u.at(c), uH.at(c), uhH.at(c), vec ? c : -1, i, j, k);
+    for (int c = 0; c < NC; ++c)
+      prolong_cell<T, true>(F, Cv, u.at(c), uH.at(c), uhH.at(c), vec ? c : -1, i, j, k);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) prolong_cell(F, Cv, u.at(c), uH.at(c), uhH.at(c), vec ? c : -1, i, j, k);
+  }
 }
 
 // Down leg of the FP32 correction cycle at one level in one launch: the
@@ -909,6 +927,9 @@ __global__ void __launch_bounds__(256) k_resid_restrict32(LevelView<float> F, Le
     if (VEC) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) rt[c][t] = vec_residual_cell<float, G>(F, e.p[0], e.p[1], e.p[2], f.at(c), c, i, j, p);
+    } else if (block_coarse_interior(F.n0, F.n1, F.n2, F.three)) {
+      float Sv;
+      rt[0][t] = scalar_residual_cell<float, G, EQ_LIN, true>(F, e.p[0], f.p[0], nullptr, K, i, j, k, p, Sv);
     } else {
       float Sv;
       rt[0][t] = scalar_residual_cell<float, G, EQ_LIN>(F, e.p[0], f.p[0], nullptr, K, i, j, k, p, Sv);

@@ -167,11 +167,12 @@ __device__ __forceinline__ void fill_one_ghost(const LevelView<T>& L, T* __restr
 // Coarse correction e = uH - uhH at coarse cell (I, J, K), which may be a
 // face ghost: then the boundary rule of that face applies (homogeneous in
 // every case, Sec. 2.6 eq. robin / eq. bc).
-template <typename T>
+template <typename T, bool INNER = false>
 __device__ __forceinline__ T coarse_corr(const LevelView<T>& C, const T* __restrict__ uH,
                                          const T* __restrict__ uhH, int comp, int I, int J, int K) {
   T f = T(1);
-  if (I < 0 || I >= C.n0)
+  if (INNER) {
+  } else if (I < 0 || I >= C.n0)
     f = ghost_rule(C, comp, 0, I, J, K);
   else if (J < 0 || J >= C.n1)
     f = ghost_rule(C, comp, 1, I, J, K);
@@ -188,13 +189,13 @@ __device__ __forceinline__ T coarse_corr(const LevelView<T>& C, const T* __restr
 // For eq. psi, kpsi (if non-null) also receives its linearisation
 // dS/du = 2 pi U (1+u)^-2 + 7/8 A2 (1+u)^-8 at the same u, the c of the
 // mixed-precision correction equation (L - c) e = r.
-template <typename T, int G, int KIND>
+template <typename T, int G, int KIND, bool INNER = false>
 __device__ __forceinline__ T scalar_residual_cell(const LevelView<T>& L, const T* __restrict__ u,
                                                   const T* __restrict__ f, const T* __restrict__ s0,
                                                   const T* __restrict__ s1, int i, int j, int k, long p, T& Sv,
                                                   T* kpsi = nullptr) {
   T D;
-  const T lap = lap_scalar<T, G>(L, u, i, j, k, p, D);
+  const T lap = lap_scalar<T, G, INNER>(L, u, i, j, k, p, D);
   const T fv = f ? f[p] : T(0);
   T Lu;
   if (KIND == EQ_PSI) {
@@ -264,18 +265,19 @@ __device__ __forceinline__ void restrict_cell(const LevelView<T>& F, const Level
 // null: e = uH) into fine cell (i, j, k): the parent and, per dimension,
 // the parent's face neighbour on the cell's side;
 // 2D 1/4 (2 e_c + e_x + e_y), 3D 1/4 (e_c + e_x + e_y + e_z).
-template <typename T>
+// INNER: every coarse cell read is interior (no ghost rule compiled in).
+template <typename T, bool INNER = false>
 __device__ __forceinline__ void prolong_cell(const LevelView<T>& F, const LevelView<T>& Cv, T* __restrict__ u,
                                              const T* __restrict__ uH, const T* __restrict__ uhH, int comp, int i,
                                              int j, int k) {
   const int I = i >> 1, J = j >> 1, K = F.three ? (k >> 1) : 0;
   const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
-  const T ec = coarse_corr(Cv, uH, uhH, comp, I, J, K);
-  const T ex = coarse_corr(Cv, uH, uhH, comp, I + si, J, K);
-  const T ey = coarse_corr(Cv, uH, uhH, comp, I, J + sj, K);
+  const T ec = coarse_corr<T, INNER>(Cv, uH, uhH, comp, I, J, K);
+  const T ex = coarse_corr<T, INNER>(Cv, uH, uhH, comp, I + si, J, K);
+  const T ey = coarse_corr<T, INNER>(Cv, uH, uhH, comp, I, J + sj, K);
   T add;
   if (F.three) {
-    const T ez = coarse_corr(Cv, uH, uhH, comp, I, J, K + sk);
+    const T ez = coarse_corr<T, INNER>(Cv, uH, uhH, comp, I, J, K + sk);
     add = T(0.25) * (ec + ex + ey + ez);
   } else {
     add = T(0.25) * (T(2) * ec + ex + ey);
