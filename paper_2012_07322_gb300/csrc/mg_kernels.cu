@@ -576,22 +576,11 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
       const RbPlanes<T> R{su + bd * BP, P, su + bu * BP, F, Cc};
       rb_red_ring<T, G, TX, HAS_C>(L, R, i0, j0, s, lc, iD0);
     }
-    if (tma) {
-      if (__syncthreads_or(timed_out)) {
-        // a staged plane never arrived: report it, let the copies still in
-        // flight land (again within the limit) and stop
-        if (threadIdx.x == ISSUER) atomicExch(M.err, 1ULL);
-        for (int q = 0; q < RB_NU; ++q)
-          if (pending & (1u << q)) wait_slot(q);
-        return;
-      }
-    } else {
-      __syncthreads();
-    }
     const int sb = s - 1;
     if (sb >= z0) {
       // black cells of plane sb = s - 1 (its red neighbours: planes s - 2,
-      // s - 1, s), then store the pairs
+      // s - 1, s; those of plane s - 1 relaxed before the last barrier, the
+      // others in this lane's registers), then store the pairs
       const int bf = (sb & (RB_NF - 1)) * BP;
       const T* P = su + bd * BP;
       const T* F = sf + bf;
@@ -618,6 +607,23 @@ __global__ void __launch_bounds__(RbShape<TX>::THREADS, TX == 128 ? (G == CART ?
         black(std::integral_constant<int, 1>{});
       else
         black(std::integral_constant<int, 0>{});
+    }
+    // One barrier per plane step.  Black cells read only red values of
+    // other threads from the previous step's plane (and their own registers),
+    // and red cells only black values, which no thread writes to the staged
+    // planes: the barrier orders this step's red values before the next
+    // step's black cells, and the staged planes' reuse.
+    if (tma) {
+      if (__syncthreads_or(timed_out)) {
+        // a staged plane never arrived: report it, let the copies still in
+        // flight land (again within the limit) and stop
+        if (threadIdx.x == ISSUER) atomicExch(M.err, 1ULL);
+        for (int q = 0; q < RB_NU; ++q)
+          if (pending & (1u << q)) wait_slot(q);
+        return;
+      }
+    } else {
+      __syncthreads();
     }
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
