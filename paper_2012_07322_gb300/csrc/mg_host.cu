@@ -1205,7 +1205,7 @@ int ensure_ghost_push(mg_hierarchy* H) {
         }
         push_slot(v, o[3], o[4], o[5], &blk[g], &slot[g]);
         col[g] = (o[3] + o[4] + o[5]) & 1;
-        if (blk[g] < 0 || blk[g] >= nb || slot[g] < 0 || slot[g] >= 256) ok = false;
+        if (blk[g] < 0 || blk[g] >= nb || slot[g] < 0 || slot[g] >= 256 * vec_cells_per_thread(v)) ok = false;
         // face neighbours of the ghost updated in the same pass as its source
         for (int d = 0; d < (v.three ? 3 : 2) && ok; ++d)
           for (int s = -1; s <= 1 && ok; s += 2) {

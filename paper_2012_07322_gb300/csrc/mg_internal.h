@@ -151,12 +151,16 @@ struct GhostPush {
 template <typename T>
 void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int colour, cudaStream_t st,
                        GhostPush gp = GhostPush{});
-// Block count of a pass with a ghost-push table, and the block and thread
-// of that pass which update cell (i, j, k).
+// Block count of a pass with a ghost-push table, and the block of that pass
+// which updates cell (i, j, k) with the cell's slot in its new values.
 template <typename T>
 int push_blocks(const LevelView<T>& L);
+// Cells a thread of the vector colour pass updates when it pushes ghosts
+// (2 on 3D levels of 2^19 cells and more, whose pass then fits one wave).
 template <typename T>
-void push_slot(const LevelView<T>& L, int i, int j, int k, int* block, int* thread);
+int vec_cells_per_thread(const LevelView<T>& L);
+template <typename T>
+void push_slot(const LevelView<T>& L, int i, int j, int k, int* block, int* slot);
 // Source of every ghost of vector component comp, in the enumeration of
 // the ghost fill: gc[8 g ..] = ghost i, j, k, source i, j, k, ghost index,
 // source index; fac[g] = the product of the boundary factors.

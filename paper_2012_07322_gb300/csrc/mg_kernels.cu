@@ -38,8 +38,10 @@ __global__ void k_smooth_scalar(LevelView<T> L, T* __restrict__ u, const T* __re
 // One colour of component comp of the vector sweep.  With a ghost-push
 // table the block then rewrites the ghosts sourced by the cells it updated
 // (their new values kept in shared memory), and in 3D thread z takes plane
-// blockIdx.z + z n2 / 2.
-template <typename T, int G>
+// blockIdx.z + z n2 / 2; with NK = 2 (levels of 2^19 cells and more) each
+// thread also takes the plane n2 / 4 above, so the pass runs in one wave of
+// blocks.  A colour's cells of one component are independent of each other.
+template <typename T, int G, int NK>
 __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ B, T* __restrict__ C,
                              const T* __restrict__ f, int comp, int colour, GhostPush gp) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,7 +54,7 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
     vec_update<T, G>(L, A, B, C, f, comp, i, j, k);
     return;
   }
-  __shared__ T nv[256];
+  __shared__ T nv[NK * 256];
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -62,14 +64,19 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
   int2 q0 = make_int2(0, 0);
   if (e0 + tid < e1) q0 = gp.ent[e0 + tid];
   pdl_entry();
-  const int k = L.three ? (int)blockIdx.z + (int)threadIdx.z * (L.n2 >> 1) : 0;
+  const int k0 = L.three ? (int)blockIdx.z + (int)threadIdx.z * (L.n2 >> 1) : 0;
   T* V = comp == 0 ? A : (comp == 1 ? B : C);
-  if (2 * t < L.n0 && j < L.n1 && k < L.n2) {
-    const int i = 2 * t + ((j + k + colour) & 1);
-    const long p = L.idx(i, j, k);
-    const T v = vec_new_value<T, G>(L, A, B, C, f, comp, i, j, p);
-    V[p] = v;
-    nv[tid] = v;
+  if (2 * t < L.n0 && j < L.n1 && k0 < L.n2) {
+    // nv slot of the w-th cell: tid + 256 w
+#pragma unroll
+    for (int w = 0; w < NK; ++w) {
+      const int k = k0 + w * (L.n2 >> 2);
+      const int i = 2 * t + ((j + k + colour) & 1);
+      const long p = L.idx(i, j, k);
+      const T v = vec_new_value<T, G>(L, A, B, C, f, comp, i, j, p);
+      V[p] = v;
+      nv[tid + 256 * w] = v;
+    }
   }
   if (e0 == e1) return;  // the same for the whole block
   __syncthreads();
@@ -1374,25 +1381,41 @@ void launch_smooth_vec(const LevelView<T>& L, T* V[3], const T* f, int comp, int
                        GhostPush gp) {
   count_launch();
   dim3 b = block_for(L.three), g = grid_colour(L, b);
-  if (gp.off && L.three) g.z = (unsigned)(L.n2 / 2);  // b.z = 2: planes k and k + n2 / 2
-  GMG_GEOM_DISPATCH(L.geom,
-                    launch_k(k_smooth_vec<T, GG>, g, b, 0, st, L, V[0], V[1], V[2], f, comp, colour, gp));
+  const int nk = gp.off ? vec_cells_per_thread(L) : 1;
+  if (gp.off && L.three) g.z = (unsigned)(L.n2 / (2 * nk));  // b.z = 2: planes k and k + n2 / 2 (and n2 / 4 up)
+  if (nk == 2) {
+    GMG_GEOM_DISPATCH(L.geom,
+                      launch_k(k_smooth_vec<T, GG, 2>, g, b, 0, st, L, V[0], V[1], V[2], f, comp, colour, gp));
+  } else {
+    GMG_GEOM_DISPATCH(L.geom,
+                      launch_k(k_smooth_vec<T, GG, 1>, g, b, 0, st, L, V[0], V[1], V[2], f, comp, colour, gp));
+  }
+}
+
+template <typename T>
+int vec_cells_per_thread(const LevelView<T>& L) {
+  return (L.three && L.n2 % 4 == 0 && (long)L.n0 * L.n1 * L.n2 >= (1L << 19)) ? 2 : 1;
 }
 
 template <typename T>
 int push_blocks(const LevelView<T>& L) {
   const dim3 b = block_for(L.three), g = grid_colour(L, b);
-  return (int)(g.x * g.y * (L.three ? L.n2 / 2 : 1));
+  return (int)(g.x * g.y * (L.three ? L.n2 / (2 * vec_cells_per_thread(L)) : 1));
 }
 
+// The block of a pass with a ghost-push table that updates cell (i, j, k),
+// and the cell's slot in the block's shared new values: with NK cells per
+// thread, plane k = bz + (2 tz + w) q (q = n2 / (2 NK)) is thread z = tz's
+// w-th cell, slot = thread + 256 w.
 template <typename T>
-void push_slot(const LevelView<T>& L, int i, int j, int k, int* block, int* thread) {
+void push_slot(const LevelView<T>& L, int i, int j, int k, int* block, int* slot) {
   const dim3 b = block_for(L.three), g = grid_colour(L, b);
-  const int t = i >> 1;
-  const int h = L.three ? L.n2 / 2 : 1;
-  const int bz = L.three ? k % h : 0, tz = L.three ? k / h : 0;
+  const int t = i >> 1, nk = vec_cells_per_thread(L);
+  const int q = L.three ? L.n2 / (2 * nk) : 1;
+  const int bz = L.three ? k % q : 0, r = L.three ? k / q : 0;  // r = nk tz + w
+  const int tz = r / nk, w = r % nk;
   *block = (int)(t / b.x + g.x * (j / b.y + g.y * bz));
-  *thread = (int)(t % b.x + b.x * (j % b.y + b.y * tz));
+  *slot = (int)(t % b.x + b.x * (j % b.y + b.y * tz)) + 256 * w;
 }
 
 template <typename T>
@@ -1608,6 +1631,7 @@ void launch_add_correction(const LevelView<double>& L, int ncomp, double* const 
                                    const T* const[3], int, int, cudaStream_t);                                 \
   template void launch_smooth_vec<T>(const LevelView<T>&, T* [3], const T*, int, int, cudaStream_t, GhostPush); \
   template int push_blocks<T>(const LevelView<T>&);                                                            \
+  template int vec_cells_per_thread<T>(const LevelView<T>&);                                                   \
   template void push_slot<T>(const LevelView<T>&, int, int, int, int*, int*);                                  \
   template void launch_residual_scalar<T>(const LevelView<T>&, int, const T*, const T*, const T*, const T*, T*, \
                                           unsigned long long*, int, cudaStream_t, float*, float*);              \

@@ -136,11 +136,14 @@ def test_red_black_sweep_parity(mg, case):
     ("sph", [128, 16, 16], [0.0, 0.0, 0.0], [30.0, PI, 2 * PI], "corner"),
     ("cyl", [128, 16, 8], [0.0, -30.0, 0.0], [30.0, 34.0, 2 * PI], "4pt"),
     ("sph", [128, 64], [0.0, 0.0], [30.0, PI], "4pt"),
+    ("sph", [128, 64, 64], [0.0, 0.0, 0.0], [30.0, PI, 2 * PI], "4pt"),
+    ("cyl", [64, 64, 128], [0.0, -30.0, 0.0], [30.0, 34.0, 2 * PI], "corner"),
 ])
 def test_vector_sweep_parity_many_blocks(mg, geom, n, lo, hi, mixed):
     """Vector sweeps (Dirichlet-0) on levels of several blocks in every
     direction: the colour passes rewrite the ghosts of the cells they update
-    themselves, and the pole ghosts of 3D grids pair planes k and k + n/2;
+    themselves, and the pole ghosts of 3D grids pair planes k and k + n/2
+    (on levels of 2^19 cells and more a thread takes two planes, n/4 apart);
     the result is the oracle's, whose ghosts are refilled before each
     colour."""
     d, gd = descs(mg, geom, n, lo, hi, mixed=mixed)
