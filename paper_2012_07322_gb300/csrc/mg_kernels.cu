@@ -105,6 +105,7 @@ __global__ void k_smooth_vec(LevelView<T> L, T* __restrict__ A, T* __restrict__ 
 // blocks run in, and u, f and c cross DRAM once per sweep instead of once
 // per colour.  Warp w owns row w; each lane owns TX / 64 pairs of cells.
 constexpr int RB_HX = 4, RB_HY = 2;  // staged halo
+constexpr int RB_RING_FIRST = 64;     // first thread of the ring cells
 // plane buffers: u planes s-1..s+2 and f, c planes s-1..s+1 are in use or
 // in flight at step s (the f ring is indexed by plane & 3); groups are
 // staged RB_AHEAD planes beyond the plane the step waits for (2 measured
@@ -121,6 +122,7 @@ struct RbShape {
   static constexpr int BY = TY + 2 * RB_HY;
   static constexpr int BX = TX + 2 * RB_HX, BP = BX * BY;
   static constexpr int RING = TX + 2 + TY;  // red ring cells: two rows of (TX+2)/2, two columns of TY/2
+  static_assert(RB_RING_FIRST + RING <= THREADS - 32, "ring threads clear of the last warp");
 };
 
 template <typename T>
@@ -367,9 +369,11 @@ struct RbLaneCoef {
 template <typename T, int G, int TX, bool HAS_C>
 __device__ __forceinline__ void rb_red_ring(const LevelView<T>& L, const RbPlanes<T>& R, int i0, int j0, int s,
                                             const RbLaneCoef<T, TX>& lc, T iD0) {
-  const int t = threadIdx.x;
+  // threads 64 .. 64 + RING - 1 (from warp 2 on: warps 0 and 1 fix the
+  // outer ghosts of blocks on an i face, and the last warp issues the copies)
+  const int t = (int)threadIdx.x - RB_RING_FIRST;
   const int par = (i0 + j0 + s) & 1;  // red: (i + j + s) even
-  if (t < RbShape<TX>::RING) {
+  if (t >= 0 && t < RbShape<TX>::RING) {
     constexpr int TY = RbShape<TX>::TY, HR = (TX + 2) / 2, HC = TY / 2;
     int x, y;
     if (t < HR) {
