@@ -208,6 +208,37 @@ typedef struct {
 int mg_solve_cfc(mg_hierarchy* h, const mg_cfc_sources* src, mg_cfc_fields* io, int flags,
                  mg_cfc_report* rep);
 
+typedef struct {
+  double kernel_ms;   /* the persistent launch (CUDA events) */
+  int blocks;         /* thread blocks it ran, each taking one problem at a time */
+  int persistent;     /* problems solved inside the launch */
+  int general;        /* problems passed on to mg_solve_cfc afterwards */
+} mg_batch_report;
+
+/*
+ * count independent xCFC solves (the same Steps as mg_solve_cfc) in ONE
+ * persistent launch: each thread block takes problems from a queue,
+ * largest grid first, and runs a problem's whole solve (eq. psi, the
+ * alpha-psi coefficient, eq. alpha, alpha = (alpha psi) / psi), every
+ * phase of its V-cycles, residuals and mixing steps separated by block
+ * barriers.  Problem i is hs[i] (one hierarchy per problem, all distinct,
+ * on the current device; MG_MIXED, MG_CYCLE_V, accel_depth <= 16,
+ * max_cycles < MG_HIST) with src[i], io[i] as in mg_solve_cfc (device
+ * pointers only: MG_HOST_POINTERS is refused).  Problems whose S_i, X or
+ * beta guesses are not all zero need the vector equations (Steps 1 and 6)
+ * and are solved by mg_solve_cfc after the launch; for the others X = beta
+ * = 0 exactly (zero right-hand sides and guesses: cycle 0).  flags:
+ * MG_CFC_PSI_ONLY.  The launch runs on hs[0]'s stream after the work queued
+ * on every hierarchy's stream; the call returns when all problems are done.
+ * rep (NULL or count entries): per-equation reports as mg_solve_cfc's, and
+ * rep[i].ms = the time from the launch's first problem start to problem i's
+ * end (its latency in the batch; eq[].ms are 0).  brep may be NULL.
+ * Returns MG_OK or the first failing status; MG_ERR_INVALID before any work
+ * for a bad argument or a hierarchy outside the limits above.
+ */
+int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources* src, mg_cfc_fields* io,
+                       int flags, mg_cfc_report* rep, mg_batch_report* brep);
+
 /* --------------------------------------------------- divergence cleaning */
 
 typedef struct {

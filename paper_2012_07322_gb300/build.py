@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgmunu_mg.so")
-SOURCES = ["mg_kernels.cu", "mg_block.cu", "mg_xcfc.cu", "mg_accel.cu", "mg_amr.cu", "mg_noalloc.cu",
+SOURCES = ["mg_kernels.cu", "mg_block.cu", "mg_xcfc.cu", "mg_accel.cu", "mg_amr.cu", "mg_noalloc.cu", "mg_batch.cu",
            "mg_serve.cu", "mg_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),

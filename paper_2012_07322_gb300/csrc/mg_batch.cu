@@ -1,0 +1,504 @@
+// Batched xCFC solves in one persistent launch.  Each thread block takes a
+// problem from a shared queue (largest first) and runs its whole static-star
+// xCFC solve: eq. psi (Sec. 2.6 Step 3), the alpha-psi coefficient, eq.
+// alpha (Step 5) and alpha = (alpha psi) / psi, each equation by the
+// mixed-precision defect correction of the launched path: the FP64 residual
+// and stopping norm (Sec. 2.7.2), a V-cycle of the FP32 correction equation
+// (red-black NGS, volume-weighted restriction, Kwak prolongation; Secs.
+// 2.7.2-2.7.3) whose levels of at most BLOCK_CYCLE_CELLS cells run the
+// one-block cycle in shared memory, the FP64 update and the Anderson mixing
+// step.  The phases are those of the launched kernels, with the same
+// per-cell functions, separated by block barriers: a 2D problem of a few
+// thousand to a hundred thousand cells leaves a launched V-cycle
+// latency-bound, and one block per problem lets many problems of different
+// sizes fill the GPU together without a launch per phase.
+//
+// Problems with momentum (S_i, or a non-zero X or beta guess) need the
+// vector equations of Steps 1 and 6; they are marked BATCH_GENERAL and the
+// host solves them through mg_solve_cfc.  For the others X = beta = 0 is
+// exact: both right-hand sides vanish and the solves stop at cycle 0.
+#include "mg_internal.h"
+#include "mg_kernels.cuh"
+#include "mg_block.cuh"
+#include "mg_accel.cuh"
+
+namespace gmg {
+
+static_assert(BATCH_THREADS == BC_THREADS, "the batch kernel runs the one-block cycle");
+
+struct BtShared {
+  unsigned long long red[3];
+  float part[BATCH_THREADS / 32][2 * AA_MAX];
+  float s[2 * AA_MAX];
+  float M[AA_MAX * AA_MAX];  // Gram matrix over ring slots (lives for one equation)
+  float gamma[AA_MAX];
+  AACols cols;
+  int status;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ long bt_cells(const LevelView<double>& L) { return (long)L.n0 * L.n1 * L.n2; }
+template <typename T>
+__device__ __forceinline__ long bt_ghosted(const LevelView<T>& L) {
+  return L.sy * (L.n2 + 2 * L.three);
+}
+
+// FP64 residual of the finest level with the stopping norms (as
+// k_residual_scalar, weighted): the FP32 right-hand side of the correction
+// cycle into lv[0].f32 and, for eq. psi, its linearisation K into lv[0].k32;
+// returns rel = max |w r| / max |w S| (NaN when a norm is not finite).
+template <int G, int KIND>
+__device__ double bt_norm(const BatchItem& I, const double* f, const double* s0, const double* s1, BtShared& S) {
+  const LevelView<double>& L = I.v64;
+  if (threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
+  __syncthreads();
+  float* r32 = I.lv[0].f32;
+  float* k32 = I.lv[0].k32;
+  unsigned long long m0 = 0ULL, m1 = 0ULL, m2 = 0ULL;
+  const long n = bt_cells(L);
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    const double w = (double)norm_weight(L, i, j);
+    double Sv, kp;
+    const double rv =
+        scalar_residual_cell<double, G, KIND>(L, I.u, f, s0, s1, i, j, k, p, Sv, KIND == EQ_PSI ? &kp : nullptr);
+    r32[p] = (float)rv;
+    if (KIND == EQ_PSI) k32[p] = (float)kp;
+    m0 = umax64(m0, abs_bits(rv));
+    if (G != CART) m1 = umax64(m1, abs_bits(w * rv));
+    m2 = umax64(m2, abs_bits(G == CART ? Sv : w * Sv));
+  }
+  if (G == CART) m1 = m0;
+  m0 = warp_max_bits(m0);
+  m1 = warp_max_bits(m1);
+  m2 = warp_max_bits(m2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&S.red[0], m0);
+    atomicMax(&S.red[1], m1);
+    atomicMax(&S.red[2], m2);
+  }
+  __syncthreads();
+  const double num = __longlong_as_double((long long)S.red[1]), den = __longlong_as_double((long long)S.red[2]);
+  __syncthreads();
+  if (isinf(num) || isinf(den) || isnan(num) || isnan(den)) return __longlong_as_double(0x7ff8000000000000LL);
+  return num / (den > 1e-300 ? den : 1e-300);
+}
+
+// nsweeps red-black sweeps of the correction equation (L - K) e = f at one
+// level (the cells of a colour are independent).
+template <int G>
+__device__ void bt_smooth(const BatchLevel& B, int nsweeps) {
+  const LevelView<float>& L = B.v;
+  const long nh = (long)L.n0 * L.n1 * L.n2 / 2;
+  for (int s = 0; s < nsweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      for (long q = threadIdx.x; q < nh; q += blockDim.x) {
+        int i, j, k;
+        L.colour_cell(q, colour, i, j, k);
+        scalar_update<float, G, EQ_LIN>(L, B.e, B.f32, nullptr, B.k32, i, j, k);
+      }
+      __syncthreads();
+    }
+}
+
+// Residual of level F restricted into the coarse right-hand side, coarse
+// correction zeroed; with fold K is restricted alongside (eq. psi: K is
+// evaluated at the current iterate and restricted on the way down).
+template <int G>
+__device__ void bt_resid_restrict(const BatchLevel& F, const BatchLevel& C, bool fold) {
+  const LevelView<float>& L = F.v;
+  const long n = (long)L.n0 * L.n1 * L.n2;
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    float Sv;
+    F.r32[p] = scalar_residual_cell<float, G, EQ_LIN>(L, F.e, F.f32, nullptr, F.k32, i, j, k, p, Sv);
+  }
+  __syncthreads();
+  const LevelView<float>& Cv = C.v;
+  const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2, ngC = bt_ghosted(Cv);
+  const float* const as[4] = {F.r32, F.k32, nullptr, nullptr};
+  float* const bs[4] = {C.f32, C.k32, nullptr, nullptr};
+  float* const cs[3] = {nullptr, nullptr, nullptr};
+  for (long q = threadIdx.x; q < nC; q += blockDim.x) {
+    int I, J, K;
+    Cv.cell(q, I, J, K);
+    restrict_cell(L, Cv, fold ? 2 : 1, as, bs, cs, I, J, K);
+  }
+  for (long q = threadIdx.x; q < ngC; q += blockDim.x) C.e[q] = 0.0f;
+  __syncthreads();
+}
+
+// K of a level restricted into the next coarser one.
+__device__ void bt_restrict_k(const LevelView<float>& F, const float* kF, const LevelView<float>& Cv, float* kC) {
+  const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2;
+  const float* const as[4] = {kF, nullptr, nullptr, nullptr};
+  float* const bs[4] = {kC, nullptr, nullptr, nullptr};
+  float* const cs[3] = {nullptr, nullptr, nullptr};
+  for (long q = threadIdx.x; q < nC; q += blockDim.x) {
+    int I, J, K;
+    Cv.cell(q, I, J, K);
+    restrict_cell(F, Cv, 1, as, bs, cs, I, J, K);
+  }
+  __syncthreads();
+}
+
+// K from level 0 down to the coarsest (linear equation: c is fixed).
+__device__ void bt_restrict_k_all(const BatchItem& I) {
+  for (int l = 1; l <= I.nl; ++l) bt_restrict_k(I.lv[l - 1].v, I.lv[l - 1].k32, I.lv[l].v, I.lv[l].k32);
+  for (int q = 1; q < I.bc.nl; ++q)
+    bt_restrict_k(I.bc.lv[q - 1].v, I.bc.lv[q - 1].k32, I.bc.lv[q].v, const_cast<float*>(I.bc.lv[q].k32));
+}
+
+// One V-cycle of the FP32 correction equation from e = 0 at level 0 (lv[0].e
+// zeroed by the caller): pre-smoothing and residual restriction down to
+// level nl, the one-block cycle from there, prolongation and post-smoothing
+// back up.
+template <int G>
+__device__ void bt_vcycle(const BatchItem& I, bool fold, float* sm, double* smd) {
+  for (int l = 0; l < I.nl; ++l) {
+    bt_smooth<G>(I.lv[l], I.nu1);
+    bt_resid_restrict<G>(I.lv[l], I.lv[l + 1], fold);
+  }
+  if (fold)
+    for (int q = 1; q < I.bc.nl; ++q)
+      bt_restrict_k(I.bc.lv[q - 1].v, I.bc.lv[q - 1].k32, I.bc.lv[q].v, const_cast<float*>(I.bc.lv[q].k32));
+  bc_run<G, false>(I.bc, sm, smd);
+  __syncthreads();
+  for (int l = I.nl - 1; l >= 0; --l) {
+    const BatchLevel& F = I.lv[l];
+    const BatchLevel& C = I.lv[l + 1];
+    const LevelView<float>& Fv = F.v;
+    const long nF = (long)Fv.n0 * Fv.n1 * Fv.n2;
+    for (long q = threadIdx.x; q < nF; q += blockDim.x) {
+      int i, j, k;
+      Fv.cell(q, i, j, k);
+      prolong_cell(Fv, C.v, F.e, C.e, (const float*)nullptr, -1, i, j, k);
+    }
+    __syncthreads();
+    bt_smooth<G>(F, I.nu2);
+  }
+}
+
+// The mixing step after a cycle (as k_aa_update_dots + k_aa_combine with
+// FP32 history): g = u, f = g - x, the newest difference columns, their dot
+// products with the live columns, the Gram solve by warp 0, and
+// u = g - sum gamma_a dG_a, x = u.  Returns the solve's status (0 solved,
+// 1 degenerate history; 0 when no column is live).
+__device__ int bt_mix(const BatchItem& I, const AACols& cols, BtShared& S) {
+  const LevelView<double>& L = I.v64;
+  const long n = bt_cells(L), vs = bt_ghosted(L);
+  const int nc = cols.n;
+  const long onew = nc > 0 ? (long)cols.slot[nc - 1] * vs : 0;
+  if (threadIdx.x == 0) S.cols = cols;
+  float v[32];
+#pragma unroll
+  for (int a = 0; a < 32; ++a) v[a] = 0.0f;
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    const double g = I.u[p], xv = I.x[p], fpv = I.fp[p], gpv = I.gp[p];
+    const double f = g - xv;
+    I.x[p] = g;
+    I.fp[p] = f;
+    I.gp[p] = g;
+    if (nc == 0) continue;
+    const float dn = (float)(f - fpv), dg = (float)(g - gpv), ft = (float)f;
+    I.dF[onew + p] = dn;
+    I.dG[onew + p] = dg;
+#pragma unroll
+    for (int a = 0; a < AA_MAX; ++a) {
+      float da;
+      if (a < nc - 1)
+        da = I.dF[(long)cols.slot[a] * vs + p];
+      else if (a == nc - 1)
+        da = dn;
+      else
+        continue;
+      v[a] += da * ft;
+      v[AA_MAX + a] += da * dn;
+    }
+  }
+  if (nc == 0) {
+    __syncthreads();
+    return 0;
+  }
+  const float w = warp_sum32(v);
+  S.part[threadIdx.x >> 5][threadIdx.x & 31] = w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int t = threadIdx.x;
+    float s = 0.0f;
+#pragma unroll
+    for (int b = 0; b < BATCH_THREADS / 32; ++b) s += S.part[b][t];
+    S.s[t] = s;
+    __syncwarp();
+    // the newest column's row of the Gram matrix, then the scaled,
+    // shifted system solved by Cholesky (as aa_solve_block in FP32)
+    const int newest = S.cols.slot[nc - 1];
+    if (t < nc) {
+      const int c = S.cols.slot[t];
+      const float g = S.s[AA_MAX + t];
+      S.M[newest * AA_MAX + c] = g;
+      S.M[c * AA_MAX + newest] = g;
+    }
+    __syncwarp();
+    float dmax = 0.0f;
+    for (int a = 0; a < nc; ++a) dmax = fmaxf(dmax, S.M[S.cols.slot[a] * AA_MAX + S.cols.slot[a]]);
+    bool ok = dmax > 0.0f && dmax <= 3.4e38f;
+    const float sc = ok ? 1.0f / dmax : 0.0f;
+    float row[AA_MAX];
+    const int ra = t < nc ? S.cols.slot[t] : 0;
+#pragma unroll
+    for (int k = 0; k < AA_MAX; ++k)
+      row[k] = (t < nc && k < nc) ? S.M[ra * AA_MAX + S.cols.slot[k]] * sc + (k == t ? AA_SHIFT<float> : 0.0f)
+                                  : (k == t ? 1.0f : 0.0f);
+    float z = t < nc ? S.s[t] * sc : 0.0f;
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) ok = chol_warp_f32(row, z, t);
+    if (ok) ok = __all_sync(0xffffffffu, z - z == 0.0f);
+    if (ok && t < nc) S.gamma[t] = z;
+    if (t == 0) S.status = ok ? 0 : 1;
+  }
+  __syncthreads();
+  const int st = S.status;
+  if (st == 0) {
+    float gm[AA_MAX];
+#pragma unroll
+    for (int a = 0; a < AA_MAX; ++a) gm[a] = a < nc ? S.gamma[a] : 0.0f;
+    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      float sacc = 0.0f;
+#pragma unroll
+      for (int a = 0; a < AA_MAX; ++a) {
+        if (a >= nc) break;
+        sacc += gm[a] * I.dG[(long)cols.slot[a] * vs + p];
+      }
+      const double uv = I.u[p] - (double)sacc;
+      I.u[p] = uv;
+      I.x[p] = uv;
+    }
+  }
+  __syncthreads();
+  return st;
+}
+
+// One scalar equation by the defect-correction loop of the launched path
+// (the stopping rule in its order: non-finite, tol, max_cycles, stall
+// window); u, f, s0, s1 as the equation's operator takes them.
+template <int G, int KIND>
+__device__ void bt_solve(const BatchItem& I, const double* f, const double* s0, const double* s1, BatchOut& O,
+                         int eq, double* hist, float* sm, double* smd, BtShared& S) {
+  const LevelView<double>& L = I.v64;
+  const long n = bt_cells(L), ng = bt_ghosted(L);
+  if (KIND == EQ_LIN) {
+    // c of the correction equation: the FP64 coefficient rounded, restricted
+    // to every level once
+    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      I.lv[0].k32[p] = (float)s1[p];
+    }
+    __syncthreads();
+    bt_restrict_k_all(I);
+  }
+  const int m = I.m;
+  int cyc = 0, ncol = 0, head = 0, status = 0;
+  double rel = bt_norm<G, KIND>(I, f, s0, s1, S);
+  if (threadIdx.x == 0) hist[0] = rel;
+  for (;;) {
+    if (rel != rel) {
+      status = 5;  // MG_ERR_NAN
+      break;
+    }
+    if (rel <= I.tol) break;
+    if (cyc >= I.max_cycles) {
+      status = 3;  // MG_ERR_NOCONV
+      break;
+    }
+    if (I.stall_window > 0 && cyc >= I.stall_window && rel > 0.95 * hist[cyc - I.stall_window]) {
+      status = 4;  // MG_ERR_STALLED
+      break;
+    }
+    if (m > 0 && cyc == 0)
+      for (long q = threadIdx.x; q < ng; q += blockDim.x) I.x[q] = I.u[q];
+    for (long q = threadIdx.x; q < ng; q += blockDim.x) I.lv[0].e[q] = 0.0f;
+    __syncthreads();
+    bt_vcycle<G>(I, KIND == EQ_PSI, sm, smd);
+    // u += e (FP64 update of the defect correction)
+    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+      I.u[p] += (double)I.lv[0].e[p];
+    }
+    __syncthreads();
+    bool mixstep = false;
+    int mst = 0;
+    if (m > 0) {
+      AACols cols;
+      cols.n = 0;
+#pragma unroll
+      for (int a = 0; a < AA_MAX; ++a) cols.slot[a] = 0;
+      if (cyc > 0) {
+        const int slot = head;
+        head = (head + 1) % m;
+        if (ncol < m) ++ncol;
+        cols.n = ncol;
+#pragma unroll
+        for (int a = 0; a < AA_MAX; ++a)
+          if (a < ncol) cols.slot[a] = (slot - ncol + 1 + a + m) % m;  // oldest first
+      }
+      mst = bt_mix(I, cols, S);
+      mixstep = cols.n > 0;
+    }
+    ++cyc;
+    rel = bt_norm<G, KIND>(I, f, s0, s1, S);
+    if (mixstep && mst != 0) ncol = 0;  // degenerate history: restart the mixing
+    if (threadIdx.x == 0 && cyc < BATCH_HIST) hist[cyc] = rel;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    O.status[eq] = status;
+    O.cycles[eq] = cyc;
+    O.rel[eq] = rel;
+  }
+}
+
+// X, beta and the vector guesses all zero (the static-star case)?
+__device__ bool bt_momentum_free(const BatchItem& I) {
+  const long n = bt_cells(I.v64);
+  int nz = 0;
+  for (long q = threadIdx.x; q < n; q += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nz |= (I.Si[c][q] != 0.0) | (I.X[c][q] != 0.0) | (I.beta[c][q] != 0.0);
+  return !__syncthreads_or(nz);
+}
+
+// The xCFC sequence of mg_solve_cfc for one momentum-free problem.
+template <int G>
+__device__ void bt_problem(const BatchItem& I, BatchOut& O, double* hist, float* sm, double* smd, BtShared& S) {
+  const LevelView<double>& L = I.v64;
+  const long n = bt_cells(L);
+  if (!I.psi_only && !bt_momentum_free(I)) {
+    if (threadIdx.x == 0) O.status[0] = BATCH_GENERAL;
+    return;
+  }
+  // Steps 1-2: X = 0 exactly, so A~^2 = 0.  Step 3: eq. psi for psi - 1
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    I.u[p] = I.psi[q] + -1.0;
+    I.s0[p] = I.U[q];
+    I.s1[p] = 0.0;
+  }
+  __syncthreads();
+  bt_solve<G, EQ_PSI>(I, nullptr, I.s0, I.s1, O, 1, hist, sm, smd, S);
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    I.psi[q] = I.u[p] + 1.0;
+    I.dpsi[p] = I.u[p];
+  }
+  __syncthreads();
+  if (I.psi_only || O.status[1] != 0) return;
+  // Step 5: c = 2 pi (U + 2 S) psi^-2 + 7/8 A~^2 psi^-8 (A~^2 = 0), the
+  // equation lap d - c d = c for d = alpha psi - 1
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    const double ip = 1.0 / (1.0 + I.dpsi[p]);
+    const double ip2 = ip * ip;
+    const double ip8 = (ip2 * ip2) * (ip2 * ip2);
+    const double a2 = 0.0;
+    const double c = 2.0 * PI_D * (I.U[q] + 2.0 * I.S[q]) * ip2 + 0.875 * a2 * ip8;
+    I.f[p] = c;
+    I.s1[p] = c;
+    I.u[p] = I.alpha[q] * (1.0 + I.dpsi[p]) - 1.0;
+  }
+  __syncthreads();
+  bt_solve<G, EQ_LIN>(I, I.f, nullptr, I.s1, O, 2, hist + BATCH_HIST, sm, smd, S);
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    I.alpha[q] = (1.0 + I.u[p]) / (1.0 + I.dpsi[p]);
+  }
+  __syncthreads();
+  // Step 6: the shift's right-hand side is zero and its guess is zero
+}
+
+__global__ void __launch_bounds__(BATCH_THREADS, 1)
+    k_batch_cfc(const BatchItem* __restrict__ items, BatchOut* __restrict__ outs, double* __restrict__ hist,
+                const int* __restrict__ order, int count, unsigned int* __restrict__ next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) BatchItem I;
+  __shared__ BtShared S;
+  __shared__ int item;
+  for (;;) {
+    if (threadIdx.x == 0) item = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int it = item;
+    if (it >= count) break;
+    const int idx = order[it];
+    {
+      const int* src = reinterpret_cast<const int*>(items + idx);
+      int* dst = reinterpret_cast<int*>(&I);
+      for (int w = threadIdx.x; w < (int)(sizeof(BatchItem) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    }
+    if (threadIdx.x == 0) {
+      BatchOut& O = outs[idx];
+      O.t_start = global_ns();
+      for (int e = 0; e < 4; ++e) {
+        O.status[e] = 0;
+        O.cycles[e] = 0;
+        O.rel[e] = 0.0;
+      }
+    }
+    __syncthreads();
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    double* smd = reinterpret_cast<double*>(smem_raw + I.bc.fp64_at);
+    double* h = hist + (long)idx * 2 * BATCH_HIST;
+    if (I.geom == CART)
+      bt_problem<CART>(I, outs[idx], h, sm, smd, S);
+    else if (I.geom == CYL)
+      bt_problem<CYL>(I, outs[idx], h, sm, smd, S);
+    else
+      bt_problem<SPH>(I, outs[idx], h, sm, smd, S);
+    __syncthreads();
+    if (threadIdx.x == 0) outs[idx].t_end = global_ns();
+  }
+}
+
+int batch_blocks_per_sm(size_t smem) {
+  if (cudaFuncSetAttribute(k_batch_cfc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_cfc, BATCH_THREADS, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+void launch_batch_cfc(const BatchItem* items, BatchOut* outs, double* hist, const int* order, int count,
+                      unsigned int* next, int blocks, size_t smem, cudaStream_t st) {
+  count_launch();
+  k_batch_cfc<<<blocks, BATCH_THREADS, smem, st>>>(items, outs, hist, order, count, next);
+}
+
+}  // namespace gmg

@@ -134,6 +134,17 @@ struct mg_hierarchy {
     int64_t graph_updates = 0;
     uint64_t graph_launches = 0;
   } amr;
+  // persistent batched solves led by this hierarchy (mg_solve_cfc_batch):
+  // one device allocation for the descriptors, outcomes, histories, order
+  // and queue counter of up to batch_cap problems; events around the launch
+  char* batch_mem = nullptr;
+  int batch_cap = 0;
+  BatchItem* b_items = nullptr;
+  BatchOut* b_outs = nullptr;
+  double* b_hist = nullptr;
+  int* b_order = nullptr;
+  unsigned int* b_next = nullptr;
+  cudaEvent_t b_ev[3] = {};
   bool prof_on = false;
   bool maps_on = false;  // some level's one-launch sweeps stage with tensor maps (d_red[7]: their timeout flag)
   bool fold_k32 = false;  // while capturing a V-cycle of eq. psi: K is restricted on the way down
@@ -2197,6 +2208,9 @@ int mg_destroy_hierarchy(mg_hierarchy* H) {
   for (double* p : H->cmat)
     if (p) cudaFree(p);
   if (H->d_aa_part) cudaFree(H->d_aa_part);
+  if (H->batch_mem) cudaFree(H->batch_mem);
+  for (cudaEvent_t e : H->b_ev)
+    if (e) cudaEventDestroy(e);
   if (H->push_buf) cudaFree(H->push_buf);
   for (GraphEntry& g : H->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : H->loops) cudaGraphExecDestroy(g.exec);
@@ -2361,6 +2375,218 @@ out:
   CK(cudaGetLastError());
   if (rep) rep->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
+}
+
+static_assert(BATCH_HIST == MG_HIST, "batched reports keep MG_HIST residuals per equation");
+
+namespace {
+
+// Device workspace of a batch of count problems, led by hierarchy H.
+int ensure_batch_ws(mg_hierarchy* H, int count) {
+  if (H->batch_cap >= count) return MG_OK;
+  CK(cudaStreamSynchronize(H->st));
+  if (H->batch_mem) cudaFree(H->batch_mem);
+  H->batch_mem = nullptr;
+  H->batch_cap = 0;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    const size_t at = off;
+    off += bytes;
+    return at;
+  };
+  const size_t o_items = take(sizeof(BatchItem) * count), o_outs = take(sizeof(BatchOut) * count),
+               o_hist = take(sizeof(double) * 2 * BATCH_HIST * count), o_order = take(sizeof(int) * count),
+               o_next = take(sizeof(unsigned int));
+  if (cudaMalloc(&H->batch_mem, off) != cudaSuccess) {
+    H->batch_mem = nullptr;
+    return fail(MG_ERR_OOM, "batch workspace allocation failed");
+  }
+  H->b_items = (BatchItem*)(H->batch_mem + o_items);
+  H->b_outs = (BatchOut*)(H->batch_mem + o_outs);
+  H->b_hist = (double*)(H->batch_mem + o_hist);
+  H->b_order = (int*)(H->batch_mem + o_order);
+  H->b_next = (unsigned int*)(H->batch_mem + o_next);
+  for (cudaEvent_t& e : H->b_ev)
+    if (!e) CK(cudaEventCreate(&e));
+  H->batch_cap = count;
+  return MG_OK;
+}
+
+// Descriptor of problem (h, src, io) for the persistent launch.
+int batch_item(mg_hierarchy* h, const mg_cfc_sources& src, const mg_cfc_fields& io, bool psi_only, BatchItem* B) {
+  const mg_grid_desc& d = h->d;
+  if (d.precision != MG_MIXED) return fail(MG_ERR_INVALID, "batched solves run in mixed precision");
+  if (d.cycle != MG_CYCLE_V) return fail(MG_ERR_INVALID, "batched solves run V-cycles");
+  if (d.accel_depth < 0 || d.accel_depth > AA_MAX) return fail(MG_ERR_INVALID, "accel_depth out of range");
+  if (d.max_cycles >= BATCH_HIST) return fail(MG_ERR_INVALID, "batched solves take max_cycles < MG_HIST");
+  if (!src.U || !io.psi) return fail(MG_ERR_INVALID, "missing U or psi");
+  if (!psi_only) {
+    if (!src.S || !io.alpha) return fail(MG_ERR_INVALID, "missing S or alpha");
+    for (int c = 0; c < 3; ++c)
+      if (!src.Si[c] || !io.beta[c] || !io.X[c]) return fail(MG_ERR_INVALID, "missing vector component");
+  }
+  const Eq ep{MG_EQ_PSI, MG_BC_ROBIN, 0, 1, false};
+  if (int est = ensure_coarse_matrix(h, MG_BC_ROBIN)) return est;
+  const int lb = block_cycle_level(h, ep);
+  if (lb >= h->nlev || lb > BATCH_MAX_LEVELS)
+    return fail(MG_ERR_INVALID, "batched solves need coarse levels that fit the one-block cycle");
+  const BlockCycle32 P = block_cycle_params(h, ep, lb);
+  if (!P.smem) return fail(MG_ERR_INVALID, "one-block cycle does not fit shared memory");
+  const int m = d.accel_depth;
+  if (m > 0)
+    if (int est = ensure_aa(h, 1, m, sizeof(float))) return est;
+  std::memset(B, 0, sizeof(*B));
+  Level& L0 = h->L[0];
+  B->geom = d.geom;
+  B->nl = lb;
+  B->nlev = h->nlev;
+  B->nu1 = d.nu1;
+  B->nu2 = d.nu2;
+  B->m = m;
+  B->max_cycles = d.max_cycles;
+  B->stall_window = d.stall_window;
+  B->psi_only = psi_only ? 1 : 0;
+  B->tol = d.tol;
+  B->v64 = with_bc(L0.v64, MG_BC_ROBIN);
+  for (int l = 0; l <= lb; ++l) {
+    Level& L = h->L[l];
+    B->lv[l] = BatchLevel{with_bc(L.v32, MG_BC_ROBIN), L.e[0], L.f32[0], L.f32[1], L.k32};
+  }
+  B->bc = P;
+  B->u = L0.u[0];
+  B->f = L0.f[0];
+  B->s0 = L0.s0;
+  B->s1 = L0.s1;
+  B->dpsi = h->dpsi;
+  if (m > 0) {
+    const long vlen = L0.ng;
+    B->x = h->aa;
+    B->fp = B->x + vlen;
+    B->gp = B->fp + vlen;
+    B->dF = reinterpret_cast<float*>(B->gp + vlen);
+    B->dG = B->dF + (long)m * vlen;
+  }
+  B->U = src.U;
+  B->S = src.S;
+  B->psi = io.psi;
+  B->alpha = io.alpha;
+  for (int c = 0; c < 3; ++c) {
+    B->Si[c] = src.Si[c];
+    B->beta[c] = io.beta[c];
+    B->X[c] = io.X[c];
+  }
+  return MG_OK;
+}
+
+// Smoother cell updates of one cycle (as the launched path counts them).
+int64_t cycle_updates(const mg_hierarchy* h) {
+  int64_t u = 0;
+  for (int l = 0; l + 1 < h->nlev; ++l) u += (int64_t)(h->d.nu1 + h->d.nu2) * h->L[l].cells();
+  return u;
+}
+
+}  // namespace
+
+int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources* src, mg_cfc_fields* io, int flags,
+                       mg_cfc_report* rep, mg_batch_report* brep) {
+  if (!hs || !src || !io || count <= 0) return fail(MG_ERR_INVALID, "null argument or empty batch");
+  if (flags & MG_HOST_POINTERS) return fail(MG_ERR_INVALID, "batched solves take device pointers");
+  const bool psi_only = flags & MG_CFC_PSI_ONLY;
+  {
+    std::vector<mg_hierarchy*> seen(hs, hs + count);
+    std::sort(seen.begin(), seen.end());
+    if (!seen[0]) return fail(MG_ERR_INVALID, "null hierarchy");
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(MG_ERR_INVALID, "each problem of a batch needs its own hierarchy");
+  }
+  mg_hierarchy* H0 = hs[0];
+  const cudaStream_t st = H0->st;
+  std::vector<BatchItem> items(count);
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) {
+    if (int est = enter(hs[i])) return est;
+    if (int est = batch_item(hs[i], src[i], io[i], psi_only, &items[i])) return est;
+    smem = std::max(smem, items[i].bc.smem);
+  }
+  if (int est = ensure_batch_ws(H0, count)) return est;
+  // the launch runs on the first hierarchy's stream, after the work queued
+  // on every other one
+  for (int i = 1; i < count; ++i)
+    if (hs[i]->st != st) {
+      CK(cudaEventRecord(H0->b_ev[2], hs[i]->st));
+      CK(cudaStreamWaitEvent(st, H0->b_ev[2], 0));
+    }
+  // largest problems first: the last ones to start are the shortest
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return hs[a]->L[0].cells() > hs[b]->L[0].cells();
+  });
+  const int bps = batch_blocks_per_sm(smem);
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (bps < 1) return fail(MG_ERR_INVALID, "batch kernel does not fit an SM");
+  const int blocks = std::min(count, sms * bps);
+  CK(cudaMemcpyAsync(H0->b_items, items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(H0->b_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(H0->b_next, 0, sizeof(unsigned int), st));
+  CK(cudaEventRecord(H0->b_ev[0], st));
+  launch_batch_cfc(H0->b_items, H0->b_outs, H0->b_hist, H0->b_order, count, H0->b_next, blocks, smem, st);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(H0->b_ev[1], st));
+  std::vector<BatchOut> outs(count);
+  CK(cudaMemcpyAsync(outs.data(), H0->b_outs, sizeof(BatchOut) * count, cudaMemcpyDeviceToHost, st));
+  std::vector<double> hist;
+  if (rep) {
+    hist.resize((size_t)2 * BATCH_HIST * count);
+    CK(cudaMemcpyAsync(hist.data(), H0->b_hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  float kms = 0.0f;
+  CK(cudaEventElapsedTime(&kms, H0->b_ev[0], H0->b_ev[1]));
+  unsigned long long t0 = ~0ULL;
+  for (const BatchOut& o : outs) t0 = std::min(t0, o.t_start);
+  int status = MG_OK, general = 0;
+  for (int i = 0; i < count; ++i) {
+    const BatchOut& o = outs[i];
+    if (o.status[0] == BATCH_GENERAL) {
+      ++general;
+      const int s = mg_solve_cfc(hs[i], &src[i], &io[i], flags, rep ? &rep[i] : nullptr);
+      if (s && !status) status = s;
+      continue;
+    }
+    for (int e = 1; e <= 2; ++e)
+      if (o.status[e] && !status) status = o.status[e];
+    if (!rep) continue;
+    mg_cfc_report& r = rep[i];
+    std::memset(&r, 0, sizeof(r));
+    const int64_t cu = cycle_updates(hs[i]);
+    for (int e = 0; e < 4; ++e) {
+      mg_solve_report& q = r.eq[e];
+      q.status = o.status[e];
+      q.cycles = o.cycles[e];
+      q.rel = o.rel[e];
+      q.cell_updates = (int64_t)o.cycles[e] * cu;
+      const bool solved = e == 1 || (e == 2 && !psi_only && o.status[1] == MG_OK);
+      if (solved) {
+        q.nhist = std::min(o.cycles[e] + 1, MG_HIST);
+        const double* h = hist.data() + ((size_t)i * 2 + (e - 1)) * BATCH_HIST;
+        for (int c = 0; c < q.nhist; ++c) q.hist[c] = h[c];
+      } else if (!psi_only && (e == 0 || e == 3)) {
+        q.nhist = 1;  // zero right-hand side: converged at cycle 0
+      }
+    }
+    r.ms = (double)(o.t_end - t0) * 1e-6;
+  }
+  if (brep) {
+    brep->kernel_ms = kms;
+    brep->blocks = blocks;
+    brep->persistent = count - general;
+    brep->general = general;
+  }
+  return status;
 }
 
 int mg_clean_divB(mg_hierarchy* H, double* B[3], double* phi_out, int flags, mg_divb_report* rep) {

@@ -387,4 +387,44 @@ void launch_coarse_assemble_scalar(const LevelView<double>& L, double* scratch, 
 // A[col * n + r], n = 3 x coarsest cells; scratch holds 3 n ghosted fields.
 void launch_coarse_assemble_vec(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st);
 
+// Persistent batched xCFC solves (mg_batch.cu): one thread block takes one
+// problem at a time from a shared queue and runs its whole solve (eq. psi,
+// then eq. alpha psi, mixed precision, with mixing), every phase separated
+// by block barriers instead of kernel boundaries.
+constexpr int BATCH_THREADS = 512;
+constexpr int BATCH_MAX_LEVELS = 16;
+constexpr int BATCH_HIST = 1024;  // residual history entries per equation (the reports' length)
+// Status of a problem whose momentum sources or vector fields are not all
+// zero: its X and beta equations need the vector solves, so the host runs
+// it through mg_solve_cfc after the launch.
+constexpr int BATCH_GENERAL = -1;
+struct BatchLevel {
+  LevelView<float> v;  // Robin rule applied
+  float *e, *f32, *r32, *k32;
+};
+struct BatchItem {
+  int geom, nl;  // nl levels run phase by phase; level nl is the first of the one-block cycle
+  int nlev, nu1, nu2, m, max_cycles, stall_window, psi_only;
+  double tol;
+  LevelView<double> v64;                  // level 0, Robin rule applied
+  BatchLevel lv[BATCH_MAX_LEVELS + 1];    // levels 0 .. nl (HBM arrays)
+  BlockCycle32 bc;                        // levels nl .. nlev - 1 (Robin rule, c present)
+  double *u, *f, *s0, *s1, *dpsi;         // level 0, ghosted
+  double *x, *fp, *gp;                    // mixing: iterate, previous f and g (ghosted layout)
+  float *dF, *dG;                         // mixing: m columns each of v64's ghosted size
+  const double *U, *S, *Si[3];            // the caller's arrays (interior order)
+  double *psi, *alpha, *beta[3], *X[3];
+};
+struct BatchOut {
+  int status[4], cycles[4];
+  double rel[4];
+  unsigned long long t_start, t_end;  // %globaltimer (ns) when the problem was taken and finished
+};
+// One launch over count problems (items in device memory, taken in the
+// order order[0 ..]); hist receives 2 x BATCH_HIST residual histories per
+// problem (eq. psi, eq. alpha psi); next is a zeroed counter.
+void launch_batch_cfc(const BatchItem* items, BatchOut* outs, double* hist, const int* order, int count,
+                      unsigned int* next, int blocks, size_t smem, cudaStream_t st);
+int batch_blocks_per_sm(size_t smem);
+
 }  // namespace gmg

@@ -37,7 +37,8 @@ EXPORTS = ["mg_strerror", "mg_last_error", "mg_hierarchy_bytes", "mg_create_hier
            "mg_num_levels", "mg_solve_cfc", "mg_clean_divB", "mg_solve_scalar", "mg_solve_vector",
            "mg_apply_operator", "mg_smooth", "mg_compute_a2", "mg_divergence", "mg_restrict", "mg_prolong_add",
            "mg_kernel_launches", "mg_profile_enable", "mg_profile_read", "mg_divb_norms_noalloc",
-           "mg_server_create", "mg_server_destroy", "mg_submit", "mg_poll", "mg_solve_scalar_amr", "mg_apply_amr"]
+           "mg_server_create", "mg_server_destroy", "mg_submit", "mg_poll", "mg_solve_scalar_amr", "mg_apply_amr",
+           "mg_solve_cfc_batch"]
 MG_REQ_CFC, MG_REQ_DIVB, MG_REQ_AMR = 0, 1, 2
 MG_NOALLOC_MAX_CELLS = 2097152
 PROF_CLASSES = ["smooth64_scalar", "smooth64_vec", "smooth32_scalar", "smooth32_vec", "resid64_scalar",
@@ -72,6 +73,10 @@ class mg_cfc_fields(C.Structure):
 
 class mg_cfc_report(C.Structure):
     _fields_ = [("eq", mg_solve_report * 4), ("ms", C.c_double)]
+
+
+class mg_batch_report(C.Structure):
+    _fields_ = [("kernel_ms", C.c_double), ("blocks", C.c_int), ("persistent", C.c_int), ("general", C.c_int)]
 
 
 class mg_divb_report(C.Structure):
@@ -118,6 +123,8 @@ def lib():
         L.mg_num_levels.argtypes = [P, C.POINTER(I)]
         L.mg_solve_cfc.argtypes = [P, C.POINTER(mg_cfc_sources), C.POINTER(mg_cfc_fields), I,
                                    C.POINTER(mg_cfc_report)]
+        L.mg_solve_cfc_batch.argtypes = [C.POINTER(P), I, C.POINTER(mg_cfc_sources), C.POINTER(mg_cfc_fields), I,
+                                         C.POINTER(mg_cfc_report), C.POINTER(mg_batch_report)]
         L.mg_clean_divB.argtypes = [P, C.POINTER(P), P, I, C.POINTER(mg_divb_report)]
         L.mg_solve_scalar.argtypes = [P, I, I, I, P, P, P, P, P, C.POINTER(mg_solve_report)]
         L.mg_solve_vector.argtypes = [P, I, C.POINTER(P), C.POINTER(P), C.POINTER(mg_solve_report)]
@@ -278,6 +285,37 @@ def mg_solve_cfc(h, U, S, Si, psi, alpha, beta, X, psi_only=False, host=False, a
     _check(st, "mg_solve_cfc", allow)
     names = ["X", "psi", "alphapsi", "beta"]
     return {"status": STATUS[st], "ms": rep.ms, **{names[k]: rep.eq[k].as_dict() for k in range(4)}}
+
+
+def mg_solve_cfc_batch(problems, psi_only=False, reports=True, allow=(MG_OK,)):
+    """Independent xCFC solves in one persistent launch (mg_solve_cfc_batch).
+    problems: sequence of (h, U, S, Si, psi, alpha, beta, X) as mg_solve_cfc
+    takes them (device tensors, one hierarchy per problem).  Returns
+    (per-problem reports or None, batch report dict)."""
+    count = len(problems)
+    hs = (C.c_void_p * count)()
+    srcs = (mg_cfc_sources * count)()
+    ios = (mg_cfc_fields * count)()
+    for q, (h, U, S, Si, psi, alpha, beta, X) in enumerate(problems):
+        hs[q] = h.handle
+        srcs[q].U = _ptr(U, h, name="U").value
+        ios[q].psi = _ptr(psi, h, name="psi").value
+        if not psi_only:
+            srcs[q].S = _ptr(S, h, name="S").value
+            ios[q].alpha = _ptr(alpha, h, name="alpha").value
+            srcs[q].Si = _parr(Si, h, name="Si")
+            ios[q].beta = _parr(beta, h, name="beta")
+            ios[q].X = _parr(X, h, name="X")
+    reps = (mg_cfc_report * count)() if reports else None
+    brep = mg_batch_report()
+    st = lib().mg_solve_cfc_batch(hs, count, srcs, ios, MG_CFC_PSI_ONLY if psi_only else 0, reps, C.byref(brep))
+    _check(st, "mg_solve_cfc_batch", allow)
+    names = ["X", "psi", "alphapsi", "beta"]
+    out = None
+    if reports:
+        out = [{"ms": r.ms, **{names[k]: r.eq[k].as_dict() for k in range(4)}} for r in reps]
+    return out, {"status": STATUS[st], "kernel_ms": brep.kernel_ms, "blocks": brep.blocks,
+                 "persistent": brep.persistent, "general": brep.general}
 
 
 def mg_clean_divB(h, B, phi=None, host=False, allow=(MG_OK,)):

@@ -1,0 +1,206 @@
+"""The persistent batched xCFC solve (mg_solve_cfc_batch): uneven 2D static
+stars solved in one launch, one thread block per problem at a time.
+
+Parity: every field within 1e-9 of the FP64 oracle at a converged relative
+residual of 1e-10 (the bar of the mixed-precision solves), X = beta = 0
+exactly, cycle counts close to the launched mixed path's.  A problem's
+result does not depend on the batch it runs in (one block runs it with the
+same instructions), and problems with momentum go through mg_solve_cfc."""
+import numpy as np
+import pytest
+
+import oracle.oracle as o
+from paper_2012_07322_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PI = np.pi
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_07322_gb300 import mg as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.array(a, dtype=np.float64, copy=True)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def relerr(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+# (geom, n, rho_c, R): the whole correction cycle in one block (2048 cells),
+# and grids whose finest levels run the block-strided phases (8192, 16384
+# and 32768 cells)
+STARS = [("sph", [64, 32], 1.28e-3, 10.0), ("cyl", [32, 64], 9e-4, 12.0), ("sph", [128, 64], 1.6e-3, 9.0),
+         ("cyl", [64, 128], 7e-4, 13.0), ("sph", [64, 128], 1.1e-3, 11.0), ("cyl", [32, 512], 1.9e-3, 8.5)]
+
+
+def star(geom, n, rho_c, R, omega=0.0):
+    if geom == "sph":
+        U, S, Si = inputs.rotating_polytrope_sph2d(n[0], n[1], 100.0, rho_c, R, axis_ratio=1.0, omega=omega)
+        return U, S, Si, [0.0, 0.0], [100.0, PI]
+    U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0, rho_c, R, axis_ratio=1.0, omega=omega)
+    return U, S, Si, [0.0, -100.0], [100.0, 100.0]
+
+
+def problem(mg, geom, n, rho_c, R, accel=16, omega=0.0, **kw):
+    U, S, Si, lo, hi = star(geom, n, rho_c, R, omega)
+    d = mg.grid_desc(geom, n, lo, hi, precision="mixed", tol=1e-10, max_cycles=800, accel_depth=accel,
+                     stall_window=0, **kw)
+    h = mg.Hierarchy(d)
+    shp = U.shape
+    f = (torch.ones(shp, dtype=torch.float64, device="cuda"), torch.ones(shp, dtype=torch.float64, device="cuda"),
+         [torch.zeros(shp, dtype=torch.float64, device="cuda") for _ in range(3)],
+         [torch.zeros(shp, dtype=torch.float64, device="cuda") for _ in range(3)])
+    return {"h": h, "desc": d, "np": (U, S, Si, lo, hi), "dev": (dev(U), dev(S), [dev(x) for x in Si]), "f": f,
+            "geom": geom, "n": n}
+
+
+def as_tuple(p):
+    U, S, Si = p["dev"]
+    psi, alpha, beta, X = p["f"]
+    return (p["h"], U, S, Si, psi, alpha, beta, X)
+
+
+def close(ps):
+    for p in ps:
+        p["h"].close()
+
+
+def test_batch_matches_oracle(mg):
+    """Six uneven static stars in one launch against the FP64 oracle's xCFC
+    solve: psi and alpha within 1e-9, residual 1e-10, X and beta exactly 0."""
+    ps = [problem(mg, *s) for s in STARS]
+    reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
+    assert b["status"] == "ok" and b["persistent"] == len(ps) and b["general"] == 0, b
+    for p, r in zip(ps, reps):
+        U, S, Si, lo, hi = p["np"]
+        d = o.desc(p["geom"], p["n"], lo, hi, tol=1e-10, max_cycles=1000, stall_window=0, accel_depth=16)
+        shp = U.shape
+        psi, alpha = np.ones(shp), np.ones(shp)
+        beta = [np.zeros(shp) for _ in range(3)]
+        X = [np.zeros(shp) for _ in range(3)]
+        ro = o.solve_cfc(d, U, S, Si, psi, alpha, beta, X)
+        for k in ("psi", "alphapsi"):
+            assert ro[k]["status"] == "ok" and r[k]["status"] == "ok", (p["n"], k, r[k]["status"])
+            assert r[k]["rel"] <= 1e-10 and r[k]["cycles"] > 0
+            assert r[k]["hist"][-1] == r[k]["rel"] and len(r[k]["hist"]) == r[k]["cycles"] + 1
+        for k in ("X", "beta"):
+            assert r[k]["status"] == "ok" and r[k]["cycles"] == 0 and r[k]["rel"] == 0.0
+        gp, ga = host(p["f"][0]), host(p["f"][1])
+        errs = {"psi": relerr(gp, psi), "dpsi": relerr(gp - 1, psi - 1), "alpha": relerr(ga, alpha),
+                "dalpha": relerr(ga - 1, alpha - 1)}
+        assert max(errs.values()) < 1e-9, (p["geom"], p["n"], errs)
+        assert all((host(x) == 0).all() for x in p["f"][2] + p["f"][3])
+        assert r["ms"] > 0
+    close(ps)
+
+
+def test_batch_cycles_close_to_launched_path(mg):
+    """The same problems through mg_solve_cfc (launched kernels, CUDA
+    graphs): the persistent solve runs the same iteration, so its cycle
+    counts differ only through the rounding order of the mixing sums."""
+    ps = [problem(mg, *s) for s in STARS]
+    reps, _ = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
+    for s, p, r in zip(STARS, ps, reps):
+        q = problem(mg, *s)
+        ra = mg.mg_solve_cfc(*as_tuple(q))
+        for k in ("psi", "alphapsi"):
+            c0, c1 = ra[k]["cycles"], r[k]["cycles"]
+            assert abs(c0 - c1) <= max(2, 0.15 * c0), (p["n"], k, c0, c1)
+        for a, b in [(q["f"][0], p["f"][0]), (q["f"][1], p["f"][1])]:
+            assert relerr(host(b), host(a)) < 2e-9
+        q["h"].close()
+    close(ps)
+
+
+def test_batch_result_independent_of_the_mix(mg):
+    """One block runs a problem from start to end with the same
+    instructions whatever else the launch holds: a problem solved alone
+    (a batch of one) and inside the batch gives bitwise the same fields,
+    and so does a second run of the whole batch."""
+    ps = [problem(mg, *s) for s in STARS]
+    mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
+    first = [(p["f"][0].clone(), p["f"][1].clone()) for p in ps]
+    for p in ps:
+        p["f"][0].fill_(1.0)
+        p["f"][1].fill_(1.0)
+    mg.mg_solve_cfc_batch([as_tuple(p) for p in reversed(ps)])
+    for p, (a, b) in zip(ps, first):
+        assert torch.equal(p["f"][0], a) and torch.equal(p["f"][1], b)
+    alone = problem(mg, *STARS[3])
+    mg.mg_solve_cfc_batch([as_tuple(alone)])
+    assert torch.equal(alone["f"][0], first[3][0]) and torch.equal(alone["f"][1], first[3][1])
+    close(ps + [alone])
+
+
+def test_batch_psi_only_and_no_mixing(mg):
+    """Eq. psi alone (MG_CFC_PSI_ONLY), and plain cycles without mixing,
+    against the oracle."""
+    for accel, psi_only, stars in [(0, False, STARS[:2]), (16, True, STARS[:4])]:
+        ps = [problem(mg, *s, accel=accel) for s in stars]
+        reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps], psi_only=psi_only)
+        assert b["status"] == "ok"
+        for p, r in zip(ps, reps):
+            U, S, Si, lo, hi = p["np"]
+            d = o.desc(p["geom"], p["n"], lo, hi, tol=1e-10, max_cycles=1000, stall_window=0, accel_depth=accel)
+            psi, alpha = np.ones(U.shape), np.ones(U.shape)
+            z = [np.zeros(U.shape) for _ in range(3)]
+            o.solve_cfc(d, U, S, Si, psi, alpha, z, [x.copy() for x in z], psi_only=psi_only)
+            assert r["psi"]["status"] == "ok" and r["psi"]["rel"] <= 1e-10
+            assert relerr(host(p["f"][0]) - 1, psi - 1) < 1e-9
+            if psi_only:
+                assert (host(p["f"][1]) == 1).all() and r["alphapsi"]["cycles"] == 0
+            else:
+                assert relerr(host(p["f"][1]) - 1, alpha - 1) < 1e-9
+        close(ps)
+
+
+def test_batch_hands_momentum_to_the_general_path(mg):
+    """A rotating star in the batch (S_i != 0) is solved by mg_solve_cfc
+    after the launch: its fields equal that call's bitwise, the static stars
+    are still solved in the launch."""
+    ps = [problem(mg, *STARS[0]), problem(mg, "sph", [64, 32], 1.28e-3, 10.0, omega=0.02),
+          problem(mg, *STARS[1])]
+    reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
+    assert b["persistent"] == 2 and b["general"] == 1 and b["status"] == "ok"
+    ref = problem(mg, "sph", [64, 32], 1.28e-3, 10.0, omega=0.02)
+    ra = mg.mg_solve_cfc(*as_tuple(ref))
+    assert reps[1]["X"]["cycles"] == ra["X"]["cycles"] > 0
+    for a, c in zip([ref["f"][0], ref["f"][1]] + ref["f"][2] + ref["f"][3],
+                    [ps[1]["f"][0], ps[1]["f"][1]] + ps[1]["f"][2] + ps[1]["f"][3]):
+        assert torch.equal(a, c)
+    close(ps + [ref])
+
+
+def test_batch_rejects_bad_arguments(mg):
+    """Before any work: the same hierarchy twice, an FP64 hierarchy, and
+    FMG cycles."""
+    a, b = problem(mg, *STARS[0]), problem(mg, *STARS[1])
+    with pytest.raises(mg.MgError):
+        mg.mg_solve_cfc_batch([as_tuple(a), as_tuple(a)])
+    for kw in [{"precision": "fp64"}, {"cycle": "fmg"}]:
+        U, S, Si, lo, hi = b["np"]
+        args = dict(precision="mixed", tol=1e-10, max_cycles=800, accel_depth=16)
+        args.update(kw)
+        d = mg.grid_desc(b["geom"], b["n"], lo, hi, **args)
+        h = mg.Hierarchy(d)
+        t = as_tuple(b)
+        with pytest.raises(mg.MgError):
+            mg.mg_solve_cfc_batch([as_tuple(a), (h,) + t[1:]])
+        h.close()
+    # nothing was written: the guesses are untouched
+    assert (host(a["f"][0]) == 1).all() and (host(b["f"][0]) == 1).all()
+    close([a, b])
