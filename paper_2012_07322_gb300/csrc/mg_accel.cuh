@@ -1,9 +1,64 @@
-// Warp-level pieces of the Anderson mixing step (mg_accel.cu), shared with
-// the persistent batched solve (mg_batch.cu).
+// Pieces of the Anderson mixing step (mg_accel.cu) shared with the
+// persistent batched solve (mg_batch.cu): the grouped loads and stores of
+// its streams, the warp sums and the warp Cholesky solve.
 #pragma once
 #include "mg_internal.h"
+#include "mg_kernels.cuh"
 
 namespace gmg {
+
+// G consecutive interior cells of a row (G = 4 when n0 >= 4, else 1).
+template <int G>
+__device__ __forceinline__ long aa_pos(const LevelView<double>& L, long q) {
+  if (G == 4) return group4(L, q);
+  return interior_p(L, q);
+}
+// Loads and stores of the mixing streams are marked evict-first: every
+// array is touched once per cycle, and the multigrid cycle's working set
+// (which fits the L2 at the bench sizes) should stay cached across them.
+template <int G, typename T>
+__device__ __forceinline__ void aa_ld(const T* p, T (&v)[G]) {
+  if constexpr (G == 1) {
+    v[0] = __ldcs(p);
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  } else {
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p)), b = __ldcs(reinterpret_cast<const double2*>(p + 2));
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+}
+template <int G, typename T>
+__device__ __forceinline__ void aa_st(T* p, const T (&v)[G]) {
+  if constexpr (G == 1) {
+    __stcs(p, v[0]);
+  } else if constexpr (sizeof(T) == 4) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  } else {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+    __stcs(reinterpret_cast<double2*>(p + 2), make_double2(v[2], v[3]));
+  }
+}
+
+// u itself stays cached (the residual reads it next).
+template <int G>
+__device__ __forceinline__ void aa_ld_u(const double* p, double (&v)[G]) {
+  if constexpr (G == 1) {
+    v[0] = *p;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+}
+template <int G>
+__device__ __forceinline__ void aa_st_u(double* p, const double (&v)[G]) {
+  if constexpr (G == 1) {
+    *p = v[0];
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
 
 // Sum over the warp of 32 values per lane; afterwards lane l holds the sum
 // of value l (31 exchanges instead of 32 x 5).

@@ -26,6 +26,7 @@ namespace gmg {
 
 static_assert(BATCH_THREADS == BC_THREADS, "the batch kernel runs the one-block cycle");
 
+
 struct BtShared {
   unsigned long long red[3];
   float part[BATCH_THREADS / 32][2 * AA_MAX];
@@ -57,8 +58,9 @@ __device__ double bt_norm(const BatchItem& I, const double* f, const double* s0,
   const LevelView<double>& L = I.v64;
   if (threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
   __syncthreads();
-  float* r32 = I.lv[0].f32;
-  float* k32 = I.lv[0].k32;
+  float* __restrict__ r32 = I.lv[0].f32;
+  float* __restrict__ k32 = I.lv[0].k32;
+  const double* __restrict__ u = I.u;
   unsigned long long m0 = 0ULL, m1 = 0ULL, m2 = 0ULL;
   const long n = bt_cells(L);
   for (long q = threadIdx.x; q < n; q += blockDim.x) {
@@ -68,7 +70,7 @@ __device__ double bt_norm(const BatchItem& I, const double* f, const double* s0,
     const double w = (double)norm_weight(L, i, j);
     double Sv, kp;
     const double rv =
-        scalar_residual_cell<double, G, KIND>(L, I.u, f, s0, s1, i, j, k, p, Sv, KIND == EQ_PSI ? &kp : nullptr);
+        scalar_residual_cell<double, G, KIND>(L, u, f, s0, s1, i, j, k, p, Sv, KIND == EQ_PSI ? &kp : nullptr);
     r32[p] = (float)rv;
     if (KIND == EQ_PSI) k32[p] = (float)kp;
     m0 = umax64(m0, abs_bits(rv));
@@ -96,13 +98,16 @@ __device__ double bt_norm(const BatchItem& I, const double* f, const double* s0,
 template <int G>
 __device__ void bt_smooth(const BatchLevel& B, int nsweeps) {
   const LevelView<float>& L = B.v;
+  float* __restrict__ e = B.e;
+  const float* __restrict__ f = B.f32;
+  const float* __restrict__ K = B.k32;
   const long nh = (long)L.n0 * L.n1 * L.n2 / 2;
   for (int s = 0; s < nsweeps; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       for (long q = threadIdx.x; q < nh; q += blockDim.x) {
         int i, j, k;
         L.colour_cell(q, colour, i, j, k);
-        scalar_update<float, G, EQ_LIN>(L, B.e, B.f32, nullptr, B.k32, i, j, k);
+        scalar_update<float, G, EQ_LIN>(L, e, f, nullptr, K, i, j, k);
       }
       __syncthreads();
     }
@@ -115,12 +120,14 @@ template <int G>
 __device__ void bt_resid_restrict(const BatchLevel& F, const BatchLevel& C, bool fold) {
   const LevelView<float>& L = F.v;
   const long n = (long)L.n0 * L.n1 * L.n2;
+  float* __restrict__ r32 = F.r32;
+  const float* __restrict__ e = F.e;
   for (long q = threadIdx.x; q < n; q += blockDim.x) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     float Sv;
-    F.r32[p] = scalar_residual_cell<float, G, EQ_LIN>(L, F.e, F.f32, nullptr, F.k32, i, j, k, p, Sv);
+    r32[p] = scalar_residual_cell<float, G, EQ_LIN>(L, e, F.f32, nullptr, F.k32, i, j, k, p, Sv);
   }
   __syncthreads();
   const LevelView<float>& Cv = C.v;
@@ -178,10 +185,12 @@ __device__ void bt_vcycle(const BatchItem& I, bool fold, float* sm, double* smd)
     const BatchLevel& C = I.lv[l + 1];
     const LevelView<float>& Fv = F.v;
     const long nF = (long)Fv.n0 * Fv.n1 * Fv.n2;
+    float* __restrict__ e = F.e;
+    const float* __restrict__ eC = C.e;
     for (long q = threadIdx.x; q < nF; q += blockDim.x) {
       int i, j, k;
       Fv.cell(q, i, j, k);
-      prolong_cell(Fv, C.v, F.e, C.e, (const float*)nullptr, -1, i, j, k);
+      prolong_cell(Fv, C.v, e, eC, (const float*)nullptr, -1, i, j, k);
     }
     __syncthreads();
     bt_smooth<G>(F, I.nu2);
@@ -191,41 +200,63 @@ __device__ void bt_vcycle(const BatchItem& I, bool fold, float* sm, double* smd)
 // The mixing step after a cycle (as k_aa_update_dots + k_aa_combine with
 // FP32 history): g = u, f = g - x, the newest difference columns, their dot
 // products with the live columns, the Gram solve by warp 0, and
-// u = g - sum gamma_a dG_a, x = u.  Returns the solve's status (0 solved,
-// 1 degenerate history; 0 when no column is live).
-__device__ int bt_mix(const BatchItem& I, const AACols& cols, BtShared& S) {
+// u = g - sum gamma_a dG_a, x = u.  Values stream in groups of G4
+// consecutive cells of a row.  Returns the solve's status (0 solved, 1
+// degenerate history; 0 when no column is live).
+template <int G4>
+__device__ int bt_mix_g(const BatchItem& I, const AACols& cols, BtShared& S) {
   const LevelView<double>& L = I.v64;
-  const long n = bt_cells(L), vs = bt_ghosted(L);
+  const long nq = bt_cells(L) / G4, vs = bt_ghosted(L);
   const int nc = cols.n;
   const long onew = nc > 0 ? (long)cols.slot[nc - 1] * vs : 0;
   if (threadIdx.x == 0) S.cols = cols;
+  double* __restrict__ u = I.u;
+  double* __restrict__ x = I.x;
+  double* __restrict__ fpr = I.fp;
+  double* __restrict__ gpr = I.gp;
+  const float* __restrict__ dFr = I.dF;
+  float* __restrict__ dFw = I.dF + onew;
+  float* __restrict__ dGw = I.dG + onew;
   float v[32];
 #pragma unroll
   for (int a = 0; a < 32; ++a) v[a] = 0.0f;
-  for (long q = threadIdx.x; q < n; q += blockDim.x) {
-    int i, j, k;
-    L.cell(q, i, j, k);
-    const long p = L.idx(i, j, k);
-    const double g = I.u[p], xv = I.x[p], fpv = I.fp[p], gpv = I.gp[p];
-    const double f = g - xv;
-    I.x[p] = g;
-    I.fp[p] = f;
-    I.gp[p] = g;
+  for (long q = threadIdx.x; q < nq; q += blockDim.x) {
+    const long p = aa_pos<G4>(L, q);
+    double g[G4], xv[G4], fp[G4], gp[G4], f[G4];
+    aa_ld_u<G4>(u + p, g);
+    aa_ld<G4>(x + p, xv);
+    aa_ld<G4>(fpr + p, fp);
+    aa_ld<G4>(gpr + p, gp);
+#pragma unroll
+    for (int t = 0; t < G4; ++t) f[t] = g[t] - xv[t];
+    aa_st<G4>(x + p, g);
+    aa_st<G4>(fpr + p, f);
+    aa_st<G4>(gpr + p, g);
     if (nc == 0) continue;
-    const float dn = (float)(f - fpv), dg = (float)(g - gpv), ft = (float)f;
-    I.dF[onew + p] = dn;
-    I.dG[onew + p] = dg;
+    float dn[G4], dg[G4], ft[G4];
+#pragma unroll
+    for (int t = 0; t < G4; ++t) {
+      dn[t] = (float)(f[t] - fp[t]);
+      dg[t] = (float)(g[t] - gp[t]);
+      ft[t] = (float)f[t];
+    }
+    aa_st<G4>(dFw + p, dn);
+    aa_st<G4>(dGw + p, dg);
 #pragma unroll
     for (int a = 0; a < AA_MAX; ++a) {
-      float da;
+      float da[G4];
       if (a < nc - 1)
-        da = I.dF[(long)cols.slot[a] * vs + p];
+        aa_ld<G4>(dFr + (long)cols.slot[a] * vs + p, da);
       else if (a == nc - 1)
-        da = dn;
+#pragma unroll
+        for (int t = 0; t < G4; ++t) da[t] = dn[t];
       else
         continue;
-      v[a] += da * ft;
-      v[AA_MAX + a] += da * dn;
+#pragma unroll
+      for (int t = 0; t < G4; ++t) {
+        v[a] += da[t] * ft[t];
+        v[AA_MAX + a] += da[t] * dn[t];
+      }
     }
   }
   if (nc == 0) {
@@ -247,9 +278,9 @@ __device__ int bt_mix(const BatchItem& I, const AACols& cols, BtShared& S) {
     const int newest = S.cols.slot[nc - 1];
     if (t < nc) {
       const int c = S.cols.slot[t];
-      const float g = S.s[AA_MAX + t];
-      S.M[newest * AA_MAX + c] = g;
-      S.M[c * AA_MAX + newest] = g;
+      const float gv = S.s[AA_MAX + t];
+      S.M[newest * AA_MAX + c] = gv;
+      S.M[c * AA_MAX + newest] = gv;
     }
     __syncwarp();
     float dmax = 0.0f;
@@ -275,23 +306,60 @@ __device__ int bt_mix(const BatchItem& I, const AACols& cols, BtShared& S) {
     float gm[AA_MAX];
 #pragma unroll
     for (int a = 0; a < AA_MAX; ++a) gm[a] = a < nc ? S.gamma[a] : 0.0f;
-    for (long q = threadIdx.x; q < n; q += blockDim.x) {
-      int i, j, k;
-      L.cell(q, i, j, k);
-      const long p = L.idx(i, j, k);
-      float sacc = 0.0f;
+    const float* __restrict__ dGr = I.dG;
+    for (long q = threadIdx.x; q < nq; q += blockDim.x) {
+      const long p = aa_pos<G4>(L, q);
+      float sacc[G4];
+#pragma unroll
+      for (int t = 0; t < G4; ++t) sacc[t] = 0.0f;
 #pragma unroll
       for (int a = 0; a < AA_MAX; ++a) {
         if (a >= nc) break;
-        sacc += gm[a] * I.dG[(long)cols.slot[a] * vs + p];
+        float d[G4];
+        aa_ld<G4>(dGr + (long)cols.slot[a] * vs + p, d);
+#pragma unroll
+        for (int t = 0; t < G4; ++t) sacc[t] += gm[a] * d[t];
       }
-      const double uv = I.u[p] - (double)sacc;
-      I.u[p] = uv;
-      I.x[p] = uv;
+      double uv[G4];
+      aa_ld_u<G4>(u + p, uv);
+#pragma unroll
+      for (int t = 0; t < G4; ++t) uv[t] -= (double)sacc[t];
+      aa_st_u<G4>(u + p, uv);
+      aa_st<G4>(x + p, uv);
     }
   }
   __syncthreads();
   return st;
+}
+
+__device__ int bt_mix(const BatchItem& I, const AACols& cols, BtShared& S) {
+  return I.v64.n0 >= 4 ? bt_mix_g<4>(I, cols, S) : bt_mix_g<1>(I, cols, S);
+}
+
+// u += e on the interior of level 0 (the FP64 update of the defect
+// correction), in groups of four cells of a row where n0 allows.
+__device__ void bt_add_correction(const BatchItem& I) {
+  const LevelView<double>& L = I.v64;
+  const long n = bt_cells(L);
+  double* __restrict__ u = I.u;
+  const float* __restrict__ e = I.lv[0].e;
+  if (L.n0 >= 4) {
+    for (long q = threadIdx.x; q < n / 4; q += blockDim.x) {
+      const long p = group4(L, q);
+      double a[4], b[4];
+      ld4(u + p, a);
+      ld4(e + p, b);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) a[t] += b[t];
+      st4(u + p, a);
+    }
+  } else {
+    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+      const long p = interior_p(L, q);
+      u[p] += (double)e[p];
+    }
+  }
+  __syncthreads();
 }
 
 // One scalar equation by the defect-correction loop of the launched path
@@ -337,14 +405,7 @@ __device__ void bt_solve(const BatchItem& I, const double* f, const double* s0, 
     for (long q = threadIdx.x; q < ng; q += blockDim.x) I.lv[0].e[q] = 0.0f;
     __syncthreads();
     bt_vcycle<G>(I, KIND == EQ_PSI, sm, smd);
-    // u += e (FP64 update of the defect correction)
-    for (long q = threadIdx.x; q < n; q += blockDim.x) {
-      int i, j, k;
-      L.cell(q, i, j, k);
-      const long p = L.idx(i, j, k);
-      I.u[p] += (double)I.lv[0].e[p];
-    }
-    __syncthreads();
+    bt_add_correction(I);
     bool mixstep = false;
     int mst = 0;
     if (m > 0) {
