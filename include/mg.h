@@ -210,18 +210,20 @@ int mg_solve_cfc(mg_hierarchy* h, const mg_cfc_sources* src, mg_cfc_fields* io, 
 
 typedef struct {
   double kernel_ms;   /* the persistent launch (CUDA events) */
-  int blocks;         /* thread blocks it ran, each taking one problem at a time */
+  int blocks;         /* thread blocks it ran */
+  int team;           /* blocks of a cluster that run one large problem together (1: none) */
   int persistent;     /* problems solved inside the launch */
   int general;        /* problems passed on to mg_solve_cfc afterwards */
 } mg_batch_report;
 
 /*
  * count independent xCFC solves (the same Steps as mg_solve_cfc) in ONE
- * persistent launch: each thread block takes problems from a queue,
- * largest grid first, and runs a problem's whole solve (eq. psi, the
- * alpha-psi coefficient, eq. alpha, alpha = (alpha psi) / psi), every
- * phase of its V-cycles, residuals and mixing steps separated by block
- * barriers.  Problem i is hs[i] (one hierarchy per problem, all distinct,
+ * persistent launch: thread blocks take problems from a queue, largest
+ * grid first, and run a problem's whole solve (eq. psi, the alpha-psi
+ * coefficient, eq. alpha, alpha = (alpha psi) / psi), every phase of its
+ * V-cycles, residuals and mixing steps separated by barriers.  Grids of
+ * 32768 cells and more are run by a cluster of 4 blocks together (cluster
+ * barriers), smaller ones by one block each.  Problem i is hs[i] (one hierarchy per problem, all distinct,
  * on the current device; MG_MIXED, MG_CYCLE_V, accel_depth <= 16,
  * max_cycles < MG_HIST) with src[i], io[i] as in mg_solve_cfc (device
  * pointers only: MG_HOST_POINTERS is refused).  Problems whose S_i, X or

@@ -17,24 +17,54 @@
 // vector equations of Steps 1 and 6; they are marked BATCH_GENERAL and the
 // host solves them through mg_solve_cfc.  For the others X = beta = 0 is
 // exact: both right-hand sides vanish and the solves stop at cycle 0.
+#include <cooperative_groups.h>
+
 #include "mg_internal.h"
 #include "mg_kernels.cuh"
 #include "mg_block.cuh"
 #include "mg_accel.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gmg {
 
 static_assert(BATCH_THREADS == BC_THREADS, "the batch kernel runs the one-block cycle");
 
 
+// The blocks that run one problem: a whole thread-block cluster (a team of
+// size BATCH_TEAM) for the largest grids, else one block alone.  Passes
+// stride over the team's threads; its barrier is the cluster barrier
+// (release / acquire at cluster scope, which orders the team's global
+// memory accesses too); reductions meet in rank 0's shared memory.
+struct Team {
+  int rank, size;
+  __device__ __forceinline__ long start() const { return (long)rank * blockDim.x + threadIdx.x; }
+  __device__ __forceinline__ long stride() const { return (long)size * blockDim.x; }
+  __device__ __forceinline__ void sync() const {
+    if (size > 1)
+      cg::this_cluster().sync();
+    else
+      __syncthreads();
+  }
+  // p (a shared-memory address of this block) in rank 0's shared memory
+  template <typename T>
+  __device__ __forceinline__ T* at0(T* p) const {
+    return size > 1 ? cg::this_cluster().map_shared_rank(p, 0) : p;
+  }
+};
+
 struct BtShared {
   unsigned long long red[3];
   float part[BATCH_THREADS / 32][2 * AA_MAX];
+  float cpart[BATCH_TEAM][2 * AA_MAX];  // rank 0: the team's per-block dot products
   float s[2 * AA_MAX];
   float M[AA_MAX * AA_MAX];  // Gram matrix over ring slots (lives for one equation)
   float gamma[AA_MAX];
   AACols cols;
   int status;
+  int flags[BATCH_TEAM];  // rank 0: the team's per-block flags
+  int item;
+  double hist[BATCH_HIST];  // this block's copy of the residual history (stall window)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -54,16 +84,18 @@ __device__ __forceinline__ long bt_ghosted(const LevelView<T>& L) {
 // cycle into lv[0].f32 and, for eq. psi, its linearisation K into lv[0].k32;
 // returns rel = max |w r| / max |w S| (NaN when a norm is not finite).
 template <int G, int KIND>
-__device__ double bt_norm(const BatchItem& I, const double* f, const double* s0, const double* s1, BtShared& S) {
+__device__ double bt_norm(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
+                          BtShared& S) {
   const LevelView<double>& L = I.v64;
-  if (threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
-  __syncthreads();
+  unsigned long long* red = T.at0(S.red);
+  if (T.rank == 0 && threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
+  T.sync();
   float* __restrict__ r32 = I.lv[0].f32;
   float* __restrict__ k32 = I.lv[0].k32;
   const double* __restrict__ u = I.u;
   unsigned long long m0 = 0ULL, m1 = 0ULL, m2 = 0ULL;
   const long n = bt_cells(L);
-  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+  for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
@@ -82,13 +114,13 @@ __device__ double bt_norm(const BatchItem& I, const double* f, const double* s0,
   m1 = warp_max_bits(m1);
   m2 = warp_max_bits(m2);
   if ((threadIdx.x & 31) == 0) {
-    atomicMax(&S.red[0], m0);
-    atomicMax(&S.red[1], m1);
-    atomicMax(&S.red[2], m2);
+    atomicMax(&red[0], m0);
+    atomicMax(&red[1], m1);
+    atomicMax(&red[2], m2);
   }
-  __syncthreads();
-  const double num = __longlong_as_double((long long)S.red[1]), den = __longlong_as_double((long long)S.red[2]);
-  __syncthreads();
+  T.sync();
+  const double num = __longlong_as_double((long long)red[1]), den = __longlong_as_double((long long)red[2]);
+  T.sync();
   if (isinf(num) || isinf(den) || isnan(num) || isnan(den)) return __longlong_as_double(0x7ff8000000000000LL);
   return num / (den > 1e-300 ? den : 1e-300);
 }
@@ -96,7 +128,7 @@ __device__ double bt_norm(const BatchItem& I, const double* f, const double* s0,
 // nsweeps red-black sweeps of the correction equation (L - K) e = f at one
 // level (the cells of a colour are independent).
 template <int G>
-__device__ void bt_smooth(const BatchLevel& B, int nsweeps) {
+__device__ void bt_smooth(const Team& T, const BatchLevel& B, int nsweeps) {
   const LevelView<float>& L = B.v;
   float* __restrict__ e = B.e;
   const float* __restrict__ f = B.f32;
@@ -104,12 +136,12 @@ __device__ void bt_smooth(const BatchLevel& B, int nsweeps) {
   const long nh = (long)L.n0 * L.n1 * L.n2 / 2;
   for (int s = 0; s < nsweeps; ++s)
     for (int colour = 0; colour < 2; ++colour) {
-      for (long q = threadIdx.x; q < nh; q += blockDim.x) {
+      for (long q = T.start(); q < nh; q += T.stride()) {
         int i, j, k;
         L.colour_cell(q, colour, i, j, k);
         scalar_update<float, G, EQ_LIN>(L, e, f, nullptr, K, i, j, k);
       }
-      __syncthreads();
+      T.sync();
     }
 }
 
@@ -117,69 +149,70 @@ __device__ void bt_smooth(const BatchLevel& B, int nsweeps) {
 // correction zeroed; with fold K is restricted alongside (eq. psi: K is
 // evaluated at the current iterate and restricted on the way down).
 template <int G>
-__device__ void bt_resid_restrict(const BatchLevel& F, const BatchLevel& C, bool fold) {
+__device__ void bt_resid_restrict(const Team& T, const BatchLevel& F, const BatchLevel& C, bool fold) {
   const LevelView<float>& L = F.v;
   const long n = (long)L.n0 * L.n1 * L.n2;
   float* __restrict__ r32 = F.r32;
   const float* __restrict__ e = F.e;
-  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+  for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     float Sv;
     r32[p] = scalar_residual_cell<float, G, EQ_LIN>(L, e, F.f32, nullptr, F.k32, i, j, k, p, Sv);
   }
-  __syncthreads();
+  T.sync();
   const LevelView<float>& Cv = C.v;
   const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2, ngC = bt_ghosted(Cv);
   const float* const as[4] = {F.r32, F.k32, nullptr, nullptr};
   float* const bs[4] = {C.f32, C.k32, nullptr, nullptr};
   float* const cs[3] = {nullptr, nullptr, nullptr};
-  for (long q = threadIdx.x; q < nC; q += blockDim.x) {
+  for (long q = T.start(); q < nC; q += T.stride()) {
     int I, J, K;
     Cv.cell(q, I, J, K);
     restrict_cell(L, Cv, fold ? 2 : 1, as, bs, cs, I, J, K);
   }
-  for (long q = threadIdx.x; q < ngC; q += blockDim.x) C.e[q] = 0.0f;
-  __syncthreads();
+  for (long q = T.start(); q < ngC; q += T.stride()) C.e[q] = 0.0f;
+  T.sync();
 }
 
 // K of a level restricted into the next coarser one.
-__device__ void bt_restrict_k(const LevelView<float>& F, const float* kF, const LevelView<float>& Cv, float* kC) {
+__device__ void bt_restrict_k(const Team& T, const LevelView<float>& F, const float* kF, const LevelView<float>& Cv,
+                              float* kC) {
   const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2;
   const float* const as[4] = {kF, nullptr, nullptr, nullptr};
   float* const bs[4] = {kC, nullptr, nullptr, nullptr};
   float* const cs[3] = {nullptr, nullptr, nullptr};
-  for (long q = threadIdx.x; q < nC; q += blockDim.x) {
+  for (long q = T.start(); q < nC; q += T.stride()) {
     int I, J, K;
     Cv.cell(q, I, J, K);
     restrict_cell(F, Cv, 1, as, bs, cs, I, J, K);
   }
-  __syncthreads();
+  T.sync();
 }
 
 // K from level 0 down to the coarsest (linear equation: c is fixed).
-__device__ void bt_restrict_k_all(const BatchItem& I) {
-  for (int l = 1; l <= I.nl; ++l) bt_restrict_k(I.lv[l - 1].v, I.lv[l - 1].k32, I.lv[l].v, I.lv[l].k32);
+__device__ void bt_restrict_k_all(const Team& T, const BatchItem& I) {
+  for (int l = 1; l <= I.nl; ++l) bt_restrict_k(T, I.lv[l - 1].v, I.lv[l - 1].k32, I.lv[l].v, I.lv[l].k32);
   for (int q = 1; q < I.bc.nl; ++q)
-    bt_restrict_k(I.bc.lv[q - 1].v, I.bc.lv[q - 1].k32, I.bc.lv[q].v, const_cast<float*>(I.bc.lv[q].k32));
+    bt_restrict_k(T, I.bc.lv[q - 1].v, I.bc.lv[q - 1].k32, I.bc.lv[q].v, const_cast<float*>(I.bc.lv[q].k32));
 }
 
 // One V-cycle of the FP32 correction equation from e = 0 at level 0 (lv[0].e
 // zeroed by the caller): pre-smoothing and residual restriction down to
-// level nl, the one-block cycle from there, prolongation and post-smoothing
-// back up.
+// level nl, the one-block cycle from there (rank 0 of a team runs it alone),
+// prolongation and post-smoothing back up.
 template <int G>
-__device__ void bt_vcycle(const BatchItem& I, bool fold, float* sm, double* smd) {
+__device__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* sm, double* smd) {
   for (int l = 0; l < I.nl; ++l) {
-    bt_smooth<G>(I.lv[l], I.nu1);
-    bt_resid_restrict<G>(I.lv[l], I.lv[l + 1], fold);
+    bt_smooth<G>(T, I.lv[l], I.nu1);
+    bt_resid_restrict<G>(T, I.lv[l], I.lv[l + 1], fold);
   }
   if (fold)
     for (int q = 1; q < I.bc.nl; ++q)
-      bt_restrict_k(I.bc.lv[q - 1].v, I.bc.lv[q - 1].k32, I.bc.lv[q].v, const_cast<float*>(I.bc.lv[q].k32));
-  bc_run<G, false>(I.bc, sm, smd);
-  __syncthreads();
+      bt_restrict_k(T, I.bc.lv[q - 1].v, I.bc.lv[q - 1].k32, I.bc.lv[q].v, const_cast<float*>(I.bc.lv[q].k32));
+  if (T.rank == 0) bc_run<G, false>(I.bc, sm, smd);
+  T.sync();
   for (int l = I.nl - 1; l >= 0; --l) {
     const BatchLevel& F = I.lv[l];
     const BatchLevel& C = I.lv[l + 1];
@@ -187,13 +220,13 @@ __device__ void bt_vcycle(const BatchItem& I, bool fold, float* sm, double* smd)
     const long nF = (long)Fv.n0 * Fv.n1 * Fv.n2;
     float* __restrict__ e = F.e;
     const float* __restrict__ eC = C.e;
-    for (long q = threadIdx.x; q < nF; q += blockDim.x) {
+    for (long q = T.start(); q < nF; q += T.stride()) {
       int i, j, k;
       Fv.cell(q, i, j, k);
       prolong_cell(Fv, C.v, e, eC, (const float*)nullptr, -1, i, j, k);
     }
-    __syncthreads();
-    bt_smooth<G>(F, I.nu2);
+    T.sync();
+    bt_smooth<G>(T, F, I.nu2);
   }
 }
 
@@ -204,7 +237,7 @@ __device__ void bt_vcycle(const BatchItem& I, bool fold, float* sm, double* smd)
 // consecutive cells of a row.  Returns the solve's status (0 solved, 1
 // degenerate history; 0 when no column is live).
 template <int G4>
-__device__ int bt_mix_g(const BatchItem& I, const AACols& cols, BtShared& S) {
+__device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, BtShared& S) {
   const LevelView<double>& L = I.v64;
   const long nq = bt_cells(L) / G4, vs = bt_ghosted(L);
   const int nc = cols.n;
@@ -220,7 +253,7 @@ __device__ int bt_mix_g(const BatchItem& I, const AACols& cols, BtShared& S) {
   float v[32];
 #pragma unroll
   for (int a = 0; a < 32; ++a) v[a] = 0.0f;
-  for (long q = threadIdx.x; q < nq; q += blockDim.x) {
+  for (long q = T.start(); q < nq; q += T.stride()) {
     const long p = aa_pos<G4>(L, q);
     double g[G4], xv[G4], fp[G4], gp[G4], f[G4];
     aa_ld_u<G4>(u + p, g);
@@ -260,17 +293,25 @@ __device__ int bt_mix_g(const BatchItem& I, const AACols& cols, BtShared& S) {
     }
   }
   if (nc == 0) {
-    __syncthreads();
+    T.sync();
     return 0;
   }
+  // the block's sums (fixed order) into row rank of rank 0's cpart, then
+  // rank 0 adds the rows in rank order and solves
   const float w = warp_sum32(v);
   S.part[threadIdx.x >> 5][threadIdx.x & 31] = w;
   __syncthreads();
   if (threadIdx.x < 32) {
-    const int t = threadIdx.x;
     float s = 0.0f;
 #pragma unroll
-    for (int b = 0; b < BATCH_THREADS / 32; ++b) s += S.part[b][t];
+    for (int b = 0; b < BATCH_THREADS / 32; ++b) s += S.part[b][threadIdx.x];
+    T.at0(S.cpart[T.rank])[threadIdx.x] = s;
+  }
+  T.sync();
+  if (T.rank == 0 && threadIdx.x < 32) {
+    const int t = threadIdx.x;
+    float s = 0.0f;
+    for (int r = 0; r < T.size; ++r) s += S.cpart[r][t];
     S.s[t] = s;
     __syncwarp();
     // the newest column's row of the Gram matrix, then the scaled,
@@ -300,14 +341,21 @@ __device__ int bt_mix_g(const BatchItem& I, const AACols& cols, BtShared& S) {
     if (ok && t < nc) S.gamma[t] = z;
     if (t == 0) S.status = ok ? 0 : 1;
   }
-  __syncthreads();
+  T.sync();
+  if (T.rank != 0) {
+    // the weights and status from rank 0 (rewritten there only after the
+    // barriers of the next cycle)
+    if (threadIdx.x < AA_MAX) S.gamma[threadIdx.x] = T.at0(S.gamma)[threadIdx.x];
+    if (threadIdx.x == 0) S.status = *T.at0(&S.status);
+    __syncthreads();
+  }
   const int st = S.status;
   if (st == 0) {
     float gm[AA_MAX];
 #pragma unroll
     for (int a = 0; a < AA_MAX; ++a) gm[a] = a < nc ? S.gamma[a] : 0.0f;
     const float* __restrict__ dGr = I.dG;
-    for (long q = threadIdx.x; q < nq; q += blockDim.x) {
+    for (long q = T.start(); q < nq; q += T.stride()) {
       const long p = aa_pos<G4>(L, q);
       float sacc[G4];
 #pragma unroll
@@ -328,23 +376,23 @@ __device__ int bt_mix_g(const BatchItem& I, const AACols& cols, BtShared& S) {
       aa_st<G4>(x + p, uv);
     }
   }
-  __syncthreads();
+  T.sync();
   return st;
 }
 
-__device__ int bt_mix(const BatchItem& I, const AACols& cols, BtShared& S) {
-  return I.v64.n0 >= 4 ? bt_mix_g<4>(I, cols, S) : bt_mix_g<1>(I, cols, S);
+__device__ int bt_mix(const Team& T, const BatchItem& I, const AACols& cols, BtShared& S) {
+  return I.v64.n0 >= 4 ? bt_mix_g<4>(T, I, cols, S) : bt_mix_g<1>(T, I, cols, S);
 }
 
 // u += e on the interior of level 0 (the FP64 update of the defect
 // correction), in groups of four cells of a row where n0 allows.
-__device__ void bt_add_correction(const BatchItem& I) {
+__device__ void bt_add_correction(const Team& T, const BatchItem& I) {
   const LevelView<double>& L = I.v64;
   const long n = bt_cells(L);
   double* __restrict__ u = I.u;
   const float* __restrict__ e = I.lv[0].e;
   if (L.n0 >= 4) {
-    for (long q = threadIdx.x; q < n / 4; q += blockDim.x) {
+    for (long q = T.start(); q < n / 4; q += T.stride()) {
       const long p = group4(L, q);
       double a[4], b[4];
       ld4(u + p, a);
@@ -354,38 +402,44 @@ __device__ void bt_add_correction(const BatchItem& I) {
       st4(u + p, a);
     }
   } else {
-    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    for (long q = T.start(); q < n; q += T.stride()) {
       const long p = interior_p(L, q);
       u[p] += (double)e[p];
     }
   }
-  __syncthreads();
+  T.sync();
 }
 
 // One scalar equation by the defect-correction loop of the launched path
 // (the stopping rule in its order: non-finite, tol, max_cycles, stall
-// window); u, f, s0, s1 as the equation's operator takes them.
+// window); u, f, s0, s1 as the equation's operator takes them.  Every block
+// of a team takes the same decisions: they depend only on values read from
+// rank 0's shared memory after a barrier.  Returns the status.
 template <int G, int KIND>
-__device__ void bt_solve(const BatchItem& I, const double* f, const double* s0, const double* s1, BatchOut& O,
-                         int eq, double* hist, float* sm, double* smd, BtShared& S) {
+__device__ int bt_solve(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
+                        BatchOut& O, int eq, double* hist, float* sm, double* smd, BtShared& S) {
   const LevelView<double>& L = I.v64;
   const long n = bt_cells(L), ng = bt_ghosted(L);
   if (KIND == EQ_LIN) {
     // c of the correction equation: the FP64 coefficient rounded, restricted
     // to every level once
-    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    for (long q = T.start(); q < n; q += T.stride()) {
       int i, j, k;
       L.cell(q, i, j, k);
       const long p = L.idx(i, j, k);
       I.lv[0].k32[p] = (float)s1[p];
     }
-    __syncthreads();
-    bt_restrict_k_all(I);
+    T.sync();
+    bt_restrict_k_all(T, I);
   }
   const int m = I.m;
   int cyc = 0, ncol = 0, head = 0, status = 0;
-  double rel = bt_norm<G, KIND>(I, f, s0, s1, S);
-  if (threadIdx.x == 0) hist[0] = rel;
+  double rel = bt_norm<G, KIND>(T, I, f, s0, s1, S);
+  if (threadIdx.x == 0) {
+    S.hist[0] = rel;
+    if (T.rank == 0) hist[0] = rel;
+  }
+  __syncthreads();
   for (;;) {
     if (rel != rel) {
       status = 5;  // MG_ERR_NAN
@@ -396,16 +450,16 @@ __device__ void bt_solve(const BatchItem& I, const double* f, const double* s0, 
       status = 3;  // MG_ERR_NOCONV
       break;
     }
-    if (I.stall_window > 0 && cyc >= I.stall_window && rel > 0.95 * hist[cyc - I.stall_window]) {
+    if (I.stall_window > 0 && cyc >= I.stall_window && rel > 0.95 * S.hist[cyc - I.stall_window]) {
       status = 4;  // MG_ERR_STALLED
       break;
     }
     if (m > 0 && cyc == 0)
-      for (long q = threadIdx.x; q < ng; q += blockDim.x) I.x[q] = I.u[q];
-    for (long q = threadIdx.x; q < ng; q += blockDim.x) I.lv[0].e[q] = 0.0f;
-    __syncthreads();
-    bt_vcycle<G>(I, KIND == EQ_PSI, sm, smd);
-    bt_add_correction(I);
+      for (long q = T.start(); q < ng; q += T.stride()) I.x[q] = I.u[q];
+    for (long q = T.start(); q < ng; q += T.stride()) I.lv[0].e[q] = 0.0f;
+    T.sync();
+    bt_vcycle<G>(T, I, KIND == EQ_PSI, sm, smd);
+    bt_add_correction(T, I);
     bool mixstep = false;
     int mst = 0;
     if (m > 0) {
@@ -422,43 +476,55 @@ __device__ void bt_solve(const BatchItem& I, const double* f, const double* s0, 
         for (int a = 0; a < AA_MAX; ++a)
           if (a < ncol) cols.slot[a] = (slot - ncol + 1 + a + m) % m;  // oldest first
       }
-      mst = bt_mix(I, cols, S);
+      mst = bt_mix(T, I, cols, S);
       mixstep = cols.n > 0;
     }
     ++cyc;
-    rel = bt_norm<G, KIND>(I, f, s0, s1, S);
+    rel = bt_norm<G, KIND>(T, I, f, s0, s1, S);
     if (mixstep && mst != 0) ncol = 0;  // degenerate history: restart the mixing
-    if (threadIdx.x == 0 && cyc < BATCH_HIST) hist[cyc] = rel;
+    if (threadIdx.x == 0 && cyc < BATCH_HIST) {
+      S.hist[cyc] = rel;
+      if (T.rank == 0) hist[cyc] = rel;
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  if (T.rank == 0 && threadIdx.x == 0) {
     O.status[eq] = status;
     O.cycles[eq] = cyc;
     O.rel[eq] = rel;
   }
+  return status;
 }
 
 // X, beta and the vector guesses all zero (the static-star case)?
-__device__ bool bt_momentum_free(const BatchItem& I) {
+__device__ bool bt_momentum_free(const Team& T, const BatchItem& I, BtShared& S) {
   const long n = bt_cells(I.v64);
   int nz = 0;
-  for (long q = threadIdx.x; q < n; q += blockDim.x)
+  for (long q = T.start(); q < n; q += T.stride())
 #pragma unroll
     for (int c = 0; c < 3; ++c) nz |= (I.Si[c][q] != 0.0) | (I.X[c][q] != 0.0) | (I.beta[c][q] != 0.0);
-  return !__syncthreads_or(nz);
+  nz = __syncthreads_or(nz);
+  if (threadIdx.x == 0) T.at0(S.flags)[T.rank] = nz;
+  T.sync();
+  const int* flags = T.at0(S.flags);
+  int any = 0;
+  for (int r = 0; r < T.size; ++r) any |= flags[r];
+  T.sync();
+  return !any;
 }
 
 // The xCFC sequence of mg_solve_cfc for one momentum-free problem.
 template <int G>
-__device__ void bt_problem(const BatchItem& I, BatchOut& O, double* hist, float* sm, double* smd, BtShared& S) {
+__device__ void bt_problem(const Team& T, const BatchItem& I, BatchOut& O, double* hist, float* sm, double* smd,
+                           BtShared& S) {
   const LevelView<double>& L = I.v64;
   const long n = bt_cells(L);
-  if (!I.psi_only && !bt_momentum_free(I)) {
-    if (threadIdx.x == 0) O.status[0] = BATCH_GENERAL;
+  if (!I.psi_only && !bt_momentum_free(T, I, S)) {
+    if (T.rank == 0 && threadIdx.x == 0) O.status[0] = BATCH_GENERAL;
     return;
   }
   // Steps 1-2: X = 0 exactly, so A~^2 = 0.  Step 3: eq. psi for psi - 1
-  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+  for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
@@ -466,20 +532,20 @@ __device__ void bt_problem(const BatchItem& I, BatchOut& O, double* hist, float*
     I.s0[p] = I.U[q];
     I.s1[p] = 0.0;
   }
-  __syncthreads();
-  bt_solve<G, EQ_PSI>(I, nullptr, I.s0, I.s1, O, 1, hist, sm, smd, S);
-  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+  T.sync();
+  const int st = bt_solve<G, EQ_PSI>(T, I, nullptr, I.s0, I.s1, O, 1, hist, sm, smd, S);
+  for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     I.psi[q] = I.u[p] + 1.0;
     I.dpsi[p] = I.u[p];
   }
-  __syncthreads();
-  if (I.psi_only || O.status[1] != 0) return;
+  T.sync();
+  if (I.psi_only || st != 0) return;
   // Step 5: c = 2 pi (U + 2 S) psi^-2 + 7/8 A~^2 psi^-8 (A~^2 = 0), the
   // equation lap d - c d = c for d = alpha psi - 1
-  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+  for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
@@ -492,74 +558,145 @@ __device__ void bt_problem(const BatchItem& I, BatchOut& O, double* hist, float*
     I.s1[p] = c;
     I.u[p] = I.alpha[q] * (1.0 + I.dpsi[p]) - 1.0;
   }
-  __syncthreads();
-  bt_solve<G, EQ_LIN>(I, I.f, nullptr, I.s1, O, 2, hist + BATCH_HIST, sm, smd, S);
-  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+  T.sync();
+  bt_solve<G, EQ_LIN>(T, I, I.f, nullptr, I.s1, O, 2, hist + BATCH_HIST, sm, smd, S);
+  for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     I.alpha[q] = (1.0 + I.u[p]) / (1.0 + I.dpsi[p]);
   }
-  __syncthreads();
+  T.sync();
   // Step 6: the shift's right-hand side is zero and its guess is zero
 }
 
+// Problem idx by team T (each block holds its own copy of the descriptor).
+__device__ void bt_run(const Team& T, const BatchItem* items, BatchOut* outs, double* hist, int idx,
+                       unsigned char* smem_raw, BatchItem& I, BtShared& S) {
+  {
+    const int* src = reinterpret_cast<const int*>(items + idx);
+    int* dst = reinterpret_cast<int*>(&I);
+    for (int w = threadIdx.x; w < (int)(sizeof(BatchItem) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+  }
+  BatchOut& O = outs[idx];
+  if (T.rank == 0 && threadIdx.x == 0) {
+    O.t_start = global_ns();
+    for (int e = 0; e < 4; ++e) {
+      O.status[e] = 0;
+      O.cycles[e] = 0;
+      O.rel[e] = 0.0;
+    }
+  }
+  __syncthreads();
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  double* smd = reinterpret_cast<double*>(smem_raw + I.bc.fp64_at);
+  double* h = hist + (long)idx * 2 * BATCH_HIST;
+  if (I.geom == CART)
+    bt_problem<CART>(T, I, O, h, sm, smd, S);
+  else if (I.geom == CYL)
+    bt_problem<CYL>(T, I, O, h, sm, smd, S);
+  else
+    bt_problem<SPH>(T, I, O, h, sm, smd, S);
+  T.sync();
+  if (T.rank == 0 && threadIdx.x == 0) O.t_end = global_ns();
+}
+
+// Problems are taken in the order order[0 ..] (largest grid first).  Launched
+// in clusters of BATCH_TEAM blocks, a cluster takes the problems of at least
+// team_cells cells together; at the first smaller one it splits, its rank 0
+// keeping that problem, and from then on every block takes problems alone.
+// A launch without clusters is all single blocks.
 __global__ void __launch_bounds__(BATCH_THREADS, 1)
     k_batch_cfc(const BatchItem* __restrict__ items, BatchOut* __restrict__ outs, double* __restrict__ hist,
-                const int* __restrict__ order, int count, unsigned int* __restrict__ next) {
+                const int* __restrict__ order, int count, unsigned int* __restrict__ next, long team_cells) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) BatchItem I;
   __shared__ BtShared S;
-  __shared__ int item;
-  for (;;) {
-    if (threadIdx.x == 0) item = (int)atomicAdd(next, 1u);
-    __syncthreads();
-    const int it = item;
-    if (it >= count) break;
-    const int idx = order[it];
-    {
-      const int* src = reinterpret_cast<const int*>(items + idx);
-      int* dst = reinterpret_cast<int*>(&I);
-      for (int w = threadIdx.x; w < (int)(sizeof(BatchItem) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-    }
-    if (threadIdx.x == 0) {
-      BatchOut& O = outs[idx];
-      O.t_start = global_ns();
-      for (int e = 0; e < 4; ++e) {
-        O.status[e] = 0;
-        O.cycles[e] = 0;
-        O.rel[e] = 0.0;
+  int first = -1;
+  const int csize = (int)cg::this_cluster().num_blocks();
+  if (csize > 1) {
+    const Team T{(int)cg::this_cluster().block_rank(), csize};
+    for (;;) {
+      if (T.rank == 0 && threadIdx.x == 0) S.item = (int)atomicAdd(next, 1u);
+      T.sync();
+      const int it = *T.at0(&S.item);
+      T.sync();
+      if (it >= count) return;
+      const int idx = order[it];
+      const LevelView<double>& v = items[idx].v64;
+      if ((long)v.n0 * v.n1 * v.n2 < team_cells) {
+        if (T.rank == 0) first = it;
+        break;
       }
+      bt_run(T, items, outs, hist, idx, smem_raw, I, S);
     }
-    __syncthreads();
-    float* sm = reinterpret_cast<float*>(smem_raw);
-    double* smd = reinterpret_cast<double*>(smem_raw + I.bc.fp64_at);
-    double* h = hist + (long)idx * 2 * BATCH_HIST;
-    if (I.geom == CART)
-      bt_problem<CART>(I, outs[idx], h, sm, smd, S);
-    else if (I.geom == CYL)
-      bt_problem<CYL>(I, outs[idx], h, sm, smd, S);
-    else
-      bt_problem<SPH>(I, outs[idx], h, sm, smd, S);
-    __syncthreads();
-    if (threadIdx.x == 0) outs[idx].t_end = global_ns();
+  }
+  const Team T{0, 1};
+  for (;;) {
+    int it = first;
+    first = -1;
+    if (it < 0) {
+      if (threadIdx.x == 0) S.item = (int)atomicAdd(next, 1u);
+      __syncthreads();
+      it = S.item;
+      __syncthreads();
+    }
+    if (it >= count) return;
+    bt_run(T, items, outs, hist, order[it], smem_raw, I, S);
   }
 }
 
-int batch_blocks_per_sm(size_t smem) {
+int batch_clusters(size_t smem, int team) {
   if (cudaFuncSetAttribute(k_batch_cfc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_cfc, BATCH_THREADS, smem) != cudaSuccess) return 0;
-  return nb;
+  int n = 0;
+  if (team == 1) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_cfc, BATCH_THREADS, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n * sms;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3(team);
+  cfg.blockDim = dim3(BATCH_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = team;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaOccupancyMaxActiveClusters(&n, k_batch_cfc, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
-void launch_batch_cfc(const BatchItem* items, BatchOut* outs, double* hist, const int* order, int count,
-                      unsigned int* next, int blocks, size_t smem, cudaStream_t st) {
+int launch_batch_cfc(const BatchItem* items, BatchOut* outs, double* hist, const int* order, int count,
+                     unsigned int* next, int clusters, int team, long team_cells, size_t smem, cudaStream_t st) {
   count_launch();
-  k_batch_cfc<<<blocks, BATCH_THREADS, smem, st>>>(items, outs, hist, order, count, next);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3(clusters * team);
+  cfg.blockDim = dim3(BATCH_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = team;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = team > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_batch_cfc, items, outs, hist, order, count, next, team_cells) == cudaSuccess
+             ? 0
+             : 1;
 }
 
 }  // namespace gmg

@@ -2523,18 +2523,28 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return hs[a]->L[0].cells() > hs[b]->L[0].cells();
   });
-  const int bps = batch_blocks_per_sm(smem);
-  int dev = 0, sms = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (bps < 1) return fail(MG_ERR_INVALID, "batch kernel does not fit an SM");
-  const int blocks = std::min(count, sms * bps);
+  // clusters of BATCH_TEAM blocks when some grid has BATCH_TEAM_CELLS cells
+  // or more (those problems run on a whole cluster), else single blocks
+  bool big = false;
+  for (int i = 0; i < count; ++i) big = big || hs[i]->L[0].cells() >= BATCH_TEAM_CELLS;
+  int team = big ? BATCH_TEAM : 1;
+  int clusters = batch_clusters(smem, team);
+  if (clusters < 1 && team > 1) {
+    team = 1;
+    clusters = batch_clusters(smem, 1);
+  }
+  if (clusters < 1) return fail(MG_ERR_INVALID, "batch kernel does not fit an SM");
+  clusters = std::min(clusters, count);
+  const int blocks = clusters * team;
   CK(cudaMemcpyAsync(H0->b_items, items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(H0->b_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(H0->b_next, 0, sizeof(unsigned int), st));
   CK(cudaEventRecord(H0->b_ev[0], st));
-  launch_batch_cfc(H0->b_items, H0->b_outs, H0->b_hist, H0->b_order, count, H0->b_next, blocks, smem, st);
-  CK(cudaGetLastError());
+  if (launch_batch_cfc(H0->b_items, H0->b_outs, H0->b_hist, H0->b_order, count, H0->b_next, clusters, team,
+                       BATCH_TEAM_CELLS, smem, st)) {
+    CK(cudaGetLastError());
+    return fail(MG_ERR_CUDA, "batch launch refused");
+  }
   CK(cudaEventRecord(H0->b_ev[1], st));
   std::vector<BatchOut> outs(count);
   CK(cudaMemcpyAsync(outs.data(), H0->b_outs, sizeof(BatchOut) * count, cudaMemcpyDeviceToHost, st));
@@ -2583,6 +2593,7 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   if (brep) {
     brep->kernel_ms = kms;
     brep->blocks = blocks;
+    brep->team = team;
     brep->persistent = count - general;
     brep->general = general;
   }

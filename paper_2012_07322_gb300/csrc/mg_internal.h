@@ -420,11 +420,18 @@ struct BatchOut {
   double rel[4];
   unsigned long long t_start, t_end;  // %globaltimer (ns) when the problem was taken and finished
 };
+// Blocks a cluster of the batch kernel (team = blocks per cluster, 1 for
+// none) holds; the clusters of that shape co-resident on the device (0 when
+// it does not fit).
+constexpr int BATCH_TEAM = 4;
+constexpr long BATCH_TEAM_CELLS = 32768;  // grids this large run on a whole cluster
+int batch_clusters(size_t smem, int team);
 // One launch over count problems (items in device memory, taken in the
-// order order[0 ..]); hist receives 2 x BATCH_HIST residual histories per
-// problem (eq. psi, eq. alpha psi); next is a zeroed counter.
-void launch_batch_cfc(const BatchItem* items, BatchOut* outs, double* hist, const int* order, int count,
-                      unsigned int* next, int blocks, size_t smem, cudaStream_t st);
-int batch_blocks_per_sm(size_t smem);
+// order order[0 ..]) on clusters x team blocks; problems of at least
+// team_cells cells are run by a whole cluster.  hist receives 2 x
+// BATCH_HIST residual histories per problem (eq. psi, eq. alpha psi); next
+// is a zeroed counter.  Returns 0, or 1 when the launch was refused.
+int launch_batch_cfc(const BatchItem* items, BatchOut* outs, double* hist, const int* order, int count,
+                     unsigned int* next, int clusters, int team, long team_cells, size_t smem, cudaStream_t st);
 
 }  // namespace gmg

@@ -76,7 +76,8 @@ class mg_cfc_report(C.Structure):
 
 
 class mg_batch_report(C.Structure):
-    _fields_ = [("kernel_ms", C.c_double), ("blocks", C.c_int), ("persistent", C.c_int), ("general", C.c_int)]
+    _fields_ = [("kernel_ms", C.c_double), ("blocks", C.c_int), ("team", C.c_int), ("persistent", C.c_int),
+                ("general", C.c_int)]
 
 
 class mg_divb_report(C.Structure):
@@ -314,7 +315,7 @@ def mg_solve_cfc_batch(problems, psi_only=False, reports=True, allow=(MG_OK,)):
     out = None
     if reports:
         out = [{"ms": r.ms, **{names[k]: r.eq[k].as_dict() for k in range(4)}} for r in reps]
-    return out, {"status": STATUS[st], "kernel_ms": brep.kernel_ms, "blocks": brep.blocks,
+    return out, {"status": STATUS[st], "kernel_ms": brep.kernel_ms, "blocks": brep.blocks, "team": brep.team,
                  "persistent": brep.persistent, "general": brep.general}
 
 
