@@ -218,8 +218,9 @@ typedef struct {
 
 /*
  * count independent xCFC solves (the same Steps as mg_solve_cfc) in ONE
- * persistent launch: thread blocks take problems from a queue, largest
- * grid first, and run a problem's whole solve (eq. psi, the alpha-psi
+ * persistent launch: thread blocks take problems from a queue, longest
+ * first (cells x the cycles of the problem's previous batched solve), and
+ * run a problem's whole solve (eq. psi, the alpha-psi
  * coefficient, eq. alpha, alpha = (alpha psi) / psi), every phase of its
  * V-cycles, residuals and mixing steps separated by barriers.  Grids of
  * 32768 cells and more are run by a cluster of 4 blocks together (cluster

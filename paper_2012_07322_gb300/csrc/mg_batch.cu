@@ -1,5 +1,5 @@
 // Batched xCFC solves in one persistent launch.  Each thread block takes a
-// problem from a shared queue (largest first) and runs its whole static-star
+// problem from a shared queue (longest first) and runs its whole static-star
 // xCFC solve: eq. psi (Sec. 2.6 Step 3), the alpha-psi coefficient, eq.
 // alpha (Step 5) and alpha = (alpha psi) / psi, each equation by the
 // mixed-precision defect correction of the launched path: the FP64 residual
@@ -61,6 +61,7 @@ struct BtShared {
   float M[AA_MAX * AA_MAX];  // Gram matrix over ring slots (lives for one equation)
   float gamma[AA_MAX];
   AACols cols;
+  long coff[AA_MAX];  // offsets of the live history columns (cols.slot x the column length)
   int status;
   int flags[BATCH_TEAM];  // rank 0: the team's per-block flags
   int item;
@@ -242,7 +243,11 @@ __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, B
   const long nq = bt_cells(L) / G4, vs = bt_ghosted(L);
   const int nc = cols.n;
   const long onew = nc > 0 ? (long)cols.slot[nc - 1] * vs : 0;
+  // the live columns' offsets in shared memory: read there in the streaming
+  // loops (broadcast), they leave the registers to the streams
   if (threadIdx.x == 0) S.cols = cols;
+  if (threadIdx.x < AA_MAX) S.coff[threadIdx.x] = (long)cols.slot[threadIdx.x] * vs;
+  __syncthreads();
   double* __restrict__ u = I.u;
   double* __restrict__ x = I.x;
   double* __restrict__ fpr = I.fp;
@@ -279,7 +284,7 @@ __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, B
     for (int a = 0; a < AA_MAX; ++a) {
       float da[G4];
       if (a < nc - 1)
-        aa_ld<G4>(dFr + (long)cols.slot[a] * vs + p, da);
+        aa_ld<G4>(dFr + S.coff[a] + p, da);
       else if (a == nc - 1)
 #pragma unroll
         for (int t = 0; t < G4; ++t) da[t] = dn[t];
@@ -364,7 +369,7 @@ __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, B
       for (int a = 0; a < AA_MAX; ++a) {
         if (a >= nc) break;
         float d[G4];
-        aa_ld<G4>(dGr + (long)cols.slot[a] * vs + p, d);
+        aa_ld<G4>(dGr + S.coff[a] + p, d);
 #pragma unroll
         for (int t = 0; t < G4; ++t) sacc[t] += gm[a] * d[t];
       }
@@ -601,7 +606,7 @@ __device__ void bt_run(const Team& T, const BatchItem* items, BatchOut* outs, do
   if (T.rank == 0 && threadIdx.x == 0) O.t_end = global_ns();
 }
 
-// Problems are taken in the order order[0 ..] (largest grid first).  Launched
+// Problems are taken in the order order[0 ..] (the team's first).  Launched
 // in clusters of BATCH_TEAM blocks, a cluster takes the problems of at least
 // team_cells cells together; at the first smaller one it splits, its rank 0
 // keeping that problem, and from then on every block takes problems alone.

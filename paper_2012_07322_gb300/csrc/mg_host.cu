@@ -139,6 +139,7 @@ struct mg_hierarchy {
   // and queue counter of up to batch_cap problems; events around the launch
   char* batch_mem = nullptr;
   int batch_cap = 0;
+  int batch_cycles = 0;  // cycles (psi + alpha psi) of this problem's last batched solve, 0 before one
   BatchItem* b_items = nullptr;
   BatchOut* b_outs = nullptr;
   double* b_hist = nullptr;
@@ -2517,11 +2518,17 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
       CK(cudaEventRecord(H0->b_ev[2], hs[i]->st));
       CK(cudaStreamWaitEvent(st, H0->b_ev[2], 0));
     }
-  // largest problems first: the last ones to start are the shortest
+  // longest problems first, so that the last ones to start are the
+  // shortest: the estimated cost is cells x cycles, the cycles those of the
+  // problem's previous batched solve (100 before one); the problems a whole
+  // cluster runs come before the others
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
+  auto team_of = [&](int a) { return hs[a]->L[0].cells() >= BATCH_TEAM_CELLS; };
+  auto cost = [&](int a) { return (double)hs[a]->L[0].cells() * (hs[a]->batch_cycles > 0 ? hs[a]->batch_cycles : 100); };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return hs[a]->L[0].cells() > hs[b]->L[0].cells();
+    if (team_of(a) != team_of(b)) return team_of(a);
+    return cost(a) > cost(b);
   });
   // clusters of BATCH_TEAM blocks when some grid has BATCH_TEAM_CELLS cells
   // or more (those problems run on a whole cluster), else single blocks
@@ -2569,6 +2576,7 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
     }
     for (int e = 1; e <= 2; ++e)
       if (o.status[e] && !status) status = o.status[e];
+    hs[i]->batch_cycles = o.cycles[1] + o.cycles[2];
     if (!rep) continue;
     mg_cfc_report& r = rep[i];
     std::memset(&r, 0, sizeof(r));
