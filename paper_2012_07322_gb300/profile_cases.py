@@ -3,13 +3,15 @@
     python -m paper_2012_07322_gb300.profile_cases divb256   # mixed 256^3 div-B cleaning, twice
     python -m paper_2012_07322_gb300.profile_cases xeq       # 10 mixed cycles of eq. X, 128x64x64
     python -m paper_2012_07322_gb300.profile_cases xcfc      # one full mixed xCFC solve, 128x64x64
+    python -m paper_2012_07322_gb300.profile_cases batch24   # 24 static stars in one persistent launch, twice
 
 Each case runs through the C ABI and exits 0 on success, so the same command
 can be profiled after it has run once without a profiler.  Every case
 switches the library's event timing on, which makes every cycle run as
 direct launches under a host loop (no CUDA graphs): a profiler does not see
 the kernels of a graph that holds a conditional (while) node, which is how
-the library otherwise runs the cycle loop.
+the library otherwise runs the cycle loop.  The batch case is one kernel
+launch per batch and needs no such switch.
 """
 import sys
 
@@ -69,7 +71,28 @@ def xcfc(precision="mixed"):
             print("  %-16s %6d launches %9.3f ms %8.2f us/launch" % (k, n, ms, ms / n * 1e3))
 
 
+def batch24(precision="mixed"):
+    import torch
+    from . import inputs, mg
+    dev = lambda a: torch.from_numpy(np.array(a, copy=True)).cuda()
+    probs = []
+    for (g, n, lo, hi, U, S, Si) in inputs.batch_static_stars_2d(count=24, seed=2):
+        h = mg.Hierarchy(mg.grid_desc(g, n, lo, hi, precision=precision, tol=1e-10, max_cycles=800, accel_depth=16,
+                                      stall_window=0))
+        z = lambda: torch.zeros(U.shape, dtype=torch.float64, device="cuda")
+        probs.append((h, dev(U), dev(S), [dev(x) for x in Si], z() + 1, z() + 1, [z() for _ in range(3)],
+                      [z() for _ in range(3)]))
+    for _ in range(2):
+        for p in probs:
+            p[4].fill_(1.0)
+            p[5].fill_(1.0)
+        reps, b = mg.mg_solve_cfc_batch(probs)
+        print("batch24", b, sum(r["psi"]["status"] == "ok" and r["alphapsi"]["status"] == "ok" for r in reps))
+    for p in probs:
+        p[0].close()
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "divb256"
     prec = sys.argv[2] if len(sys.argv) > 2 else "mixed"
-    {"divb256": divb256, "xeq": xeq, "xcfc": xcfc}[case](prec)
+    {"divb256": divb256, "xeq": xeq, "xcfc": xcfc, "batch24": batch24}[case](prec)
