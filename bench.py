@@ -313,7 +313,7 @@ def batch_measurement(mg, torch, count=512, slots=16, tune=True):
                 "cycles_psi_plus_alphapsi": {"min": min(cyc), "median": sorted(cyc)[len(cyc) // 2],
                                              "max": max(cyc)}}
 
-    def run_persistent(descs, reps=3):
+    def run_persistent(descs, reps=3, launch=None):
         """All solves in one persistent launch (mg_solve_cfc_batch): one
         hierarchy per problem, created once; each timed call starts from the
         flat guess.  Wall time of the call (descriptor upload, the launch,
@@ -322,14 +322,23 @@ def batch_measurement(mg, torch, count=512, slots=16, tune=True):
         hs = [mg.Hierarchy(d) for d in descs]
         outs = [fields(it[1]) for it in items]
         probs = [(h, U, S, Si) + tuple(f) for h, (_, U, S, Si, _, _), f in zip(hs, items, outs)]
-        best = None
-        for r in range(reps + 1):  # the first call builds the coarsest operators and mixing storage
+
+        def reset():
             for f in outs:
                 f[0].fill_(1.0)
                 f[1].fill_(1.0)
+        tuned = None
+        if launch == "tune":
+            t0 = time.perf_counter()
+            tuned = autotune.tune_launch(mg, torch, probs, reset)
+            tuned["tuning_s"] = time.perf_counter() - t0
+        shape = {"team": tuned["team"], "team_cells": tuned["team_cells"]} if tuned else {}
+        best = None
+        for r in range(reps + 1):  # the first call builds the coarsest operators and mixing storage
+            reset()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res, b = mg.mg_solve_cfc_batch(probs)
+            res, b = mg.mg_solve_cfc_batch(probs, **shape)
             wall = time.perf_counter() - t0
             if r > 0 and (best is None or wall < best[0]):
                 best = (wall, res, b)
@@ -339,13 +348,17 @@ def batch_measurement(mg, torch, count=512, slots=16, tune=True):
         lat = sorted(x["ms"] for x in res)
         ups = sum(sum(x[k]["cell_updates"] for k in ("X", "psi", "alphapsi", "beta")) for x in res)
         cyc = [x["psi"]["cycles"] + x["alphapsi"]["cycles"] for x in res]
-        return {"solves_per_s": count / wall, "wall_ms": wall * 1e3, "kernel_ms": b["kernel_ms"],
-                "value": ups / wall / 1e9, "unit": UNIT, "blocks": b["blocks"], "persistent": b["persistent"],
+        line = {"solves_per_s": count / wall, "wall_ms": wall * 1e3, "kernel_ms": b["kernel_ms"],
+                "value": ups / wall / 1e9, "unit": UNIT, "blocks": b["blocks"], "team": b["team"],
+                "persistent": b["persistent"],
                 "general": b["general"], "p50_ms": lat[len(lat) // 2],
                 "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                 "ok": sum(x["psi"]["status"] == "ok" and x["alphapsi"]["status"] == "ok" for x in res),
                 "cycles_psi_plus_alphapsi": {"min": min(cyc), "median": sorted(cyc)[len(cyc) // 2],
                                              "max": max(cyc)}}
+        if tuned:
+            line["launch_tuned"] = tuned
+        return line
 
     out = {"workload": "%d uneven 2D static stars (seed 2): spherical N_r 32..256 x N_theta 16..128, cylindrical "
                        "N_R 32..256 x N_z 64..512, rho_c ~ U[5e-4, 2e-3], R ~ U[8, 14]; full xCFC system, mixed "
@@ -364,7 +377,8 @@ def batch_measurement(mg, torch, count=512, slots=16, tune=True):
             picks[key] = picks.get(key, 0) + 1
         tuned.update({"tuning_s": tuning_s, "schedules_picked": picks})
         out["autotuned"] = tuned
-        out["persistent_autotuned"] = run_persistent([autotune.tuned(mg, it[0], table) for it in items])
+        out["persistent_autotuned"] = run_persistent([autotune.tuned(mg, it[0], table) for it in items],
+                                                     launch="tune")
     return out
 
 

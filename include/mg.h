@@ -208,6 +208,12 @@ typedef struct {
 int mg_solve_cfc(mg_hierarchy* h, const mg_cfc_sources* src, mg_cfc_fields* io, int flags,
                  mg_cfc_report* rep);
 
+/* Launch shape of mg_solve_cfc_batch (NULL, or 0 in a field: the default). */
+typedef struct {
+  int team;            /* blocks of a cluster that run one large problem: 1, 2 (default), 4 or 8 */
+  int64_t team_cells;  /* grids of at least this many cells run on a cluster (default 16384) */
+} mg_batch_opts;
+
 typedef struct {
   double kernel_ms;   /* the persistent launch (CUDA events) */
   int blocks;         /* thread blocks it ran */
@@ -223,15 +229,15 @@ typedef struct {
  * run a problem's whole solve (eq. psi, the alpha-psi
  * coefficient, eq. alpha, alpha = (alpha psi) / psi), every phase of its
  * V-cycles, residuals and mixing steps separated by barriers.  Grids of
- * 32768 cells and more are run by a cluster of 4 blocks together (cluster
- * barriers), smaller ones by one block each.  Problem i is hs[i] (one hierarchy per problem, all distinct,
+ * opts->team_cells cells and more are run by a cluster of opts->team blocks
+ * together (cluster barriers), smaller ones by one block each.  Problem i is hs[i] (one hierarchy per problem, all distinct,
  * on the current device; MG_MIXED, MG_CYCLE_V, accel_depth <= 16,
  * max_cycles < MG_HIST) with src[i], io[i] as in mg_solve_cfc (device
  * pointers only: MG_HOST_POINTERS is refused).  Problems whose S_i, X or
  * beta guesses are not all zero need the vector equations (Steps 1 and 6)
  * and are solved by mg_solve_cfc after the launch; for the others X = beta
  * = 0 exactly (zero right-hand sides and guesses: cycle 0).  flags:
- * MG_CFC_PSI_ONLY.  The launch runs on hs[0]'s stream after the work queued
+ * MG_CFC_PSI_ONLY.  opts may be NULL.  The launch runs on hs[0]'s stream after the work queued
  * on every hierarchy's stream; the call returns when all problems are done.
  * rep (NULL or count entries): per-equation reports as mg_solve_cfc's, and
  * rep[i].ms = the time from the launch's first problem start to problem i's
@@ -240,7 +246,7 @@ typedef struct {
  * for a bad argument or a hierarchy outside the limits above.
  */
 int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources* src, mg_cfc_fields* io,
-                       int flags, mg_cfc_report* rep, mg_batch_report* brep);
+                       int flags, const mg_batch_opts* opts, mg_cfc_report* rep, mg_batch_report* brep);
 
 /* --------------------------------------------------- divergence cleaning */
 

@@ -14,6 +14,11 @@ that later runs reuse.
 Every candidate is the same multigrid (Sec. 2.7) with the same stopping
 rule, so the tuned solves reach the same tolerance; only the route there
 changes (V(nu1, nu2) counts and the mixing depth).
+
+tune_launch picks the launch shape of the persistent batch kernel for a
+given batch: the cluster size that runs one large grid and the grid size
+from which a cluster takes a problem (the rest run one block each), by the
+measured time of the whole batch per candidate.
 """
 from __future__ import annotations
 
@@ -124,3 +129,34 @@ def tuned(mg, desc, table):
     if not e:
         return desc
     return with_schedule(mg, desc, (e["nu1"], e["nu2"], e["accel_depth"]))
+
+
+# Candidate launch shapes of the persistent batch: (team, team_cells).
+LAUNCH_CANDIDATES = [(2, 16384), (2, 32768), (2, 8192), (4, 16384), (4, 32768), (8, 32768), (1, 0)]
+
+
+def tune_launch(mg, torch, problems, reset, candidates=LAUNCH_CANDIDATES, repeats=1):
+    """The fastest launch shape for a batch.  problems: the tuple list
+    mg.mg_solve_cfc_batch takes; reset(): restores the initial guesses.
+    Each candidate runs once untimed (the problems' cycle history orders the
+    queue) and then repeats timed times; returns {"team", "team_cells",
+    "ms", "tried"}."""
+    best, tried = None, []
+    for team, cells in candidates:
+        ms = []
+        for r in range(repeats + 1):
+            reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps, b = mg.mg_solve_cfc_batch(problems, reports=False, team=team, team_cells=cells,
+                                            allow=(mg.MG_OK, mg.MG_ERR_NOCONV, mg.MG_ERR_STALLED))
+            if r > 0:
+                ms.append((time.perf_counter() - t0) * 1e3)
+        t = sorted(ms)[len(ms) // 2]
+        ok = b["status"] == "ok"
+        tried.append({"team": team, "team_cells": cells, "ms": t, "ok": ok, "blocks": b["blocks"]})
+        if ok and (best is None or t < best[0]):
+            best = (t, team, cells)
+    if best is None:
+        return {"team": 0, "team_cells": 0, "ms": None, "tried": tried}
+    return {"team": best[1], "team_cells": best[2], "ms": best[0], "tried": tried}

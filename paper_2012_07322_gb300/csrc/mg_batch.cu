@@ -32,7 +32,7 @@ static_assert(BATCH_THREADS == BC_THREADS, "the batch kernel runs the one-block 
 
 
 // The blocks that run one problem: a whole thread-block cluster (a team of
-// size BATCH_TEAM) for the largest grids, else one block alone.  Passes
+// up to BATCH_TEAM blocks) for the largest grids, else one block alone.  Passes
 // stride over the team's threads; its barrier is the cluster barrier
 // (release / acquire at cluster scope, which orders the team's global
 // memory accesses too); reductions meet in rank 0's shared memory.
@@ -607,7 +607,7 @@ __device__ void bt_run(const Team& T, const BatchItem* items, BatchOut* outs, do
 }
 
 // Problems are taken in the order order[0 ..] (the team's first).  Launched
-// in clusters of BATCH_TEAM blocks, a cluster takes the problems of at least
+// in clusters (of at most BATCH_TEAM blocks), a cluster takes the problems of at least
 // team_cells cells together; at the first smaller one it splits, its rank 0
 // keeping that problem, and from then on every block takes problems alone.
 // A launch without clusters is all single blocks.

@@ -2490,8 +2490,12 @@ int64_t cycle_updates(const mg_hierarchy* h) {
 }  // namespace
 
 int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources* src, mg_cfc_fields* io, int flags,
-                       mg_cfc_report* rep, mg_batch_report* brep) {
+                       const mg_batch_opts* opts, mg_cfc_report* rep, mg_batch_report* brep) {
   if (!hs || !src || !io || count <= 0) return fail(MG_ERR_INVALID, "null argument or empty batch");
+  int team_opt = opts && opts->team ? opts->team : BATCH_TEAM_DEFAULT;
+  const long team_cells = opts && opts->team_cells > 0 ? (long)opts->team_cells : BATCH_TEAM_CELLS;
+  if (team_opt != 1 && team_opt != 2 && team_opt != 4 && team_opt != 8)
+    return fail(MG_ERR_INVALID, "team must be 1, 2, 4 or 8");
   if (flags & MG_HOST_POINTERS) return fail(MG_ERR_INVALID, "batched solves take device pointers");
   const bool psi_only = flags & MG_CFC_PSI_ONLY;
   {
@@ -2524,17 +2528,17 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   // cluster runs come before the others
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
-  auto team_of = [&](int a) { return hs[a]->L[0].cells() >= BATCH_TEAM_CELLS; };
+  auto team_of = [&](int a) { return team_opt > 1 && hs[a]->L[0].cells() >= team_cells; };
   auto cost = [&](int a) { return (double)hs[a]->L[0].cells() * (hs[a]->batch_cycles > 0 ? hs[a]->batch_cycles : 100); };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     if (team_of(a) != team_of(b)) return team_of(a);
     return cost(a) > cost(b);
   });
-  // clusters of BATCH_TEAM blocks when some grid has BATCH_TEAM_CELLS cells
-  // or more (those problems run on a whole cluster), else single blocks
+  // clusters of team_opt blocks when some grid has team_cells cells or more
+  // (those problems run on a whole cluster), else single blocks
   bool big = false;
-  for (int i = 0; i < count; ++i) big = big || hs[i]->L[0].cells() >= BATCH_TEAM_CELLS;
-  int team = big ? BATCH_TEAM : 1;
+  for (int i = 0; i < count; ++i) big = big || team_of(i);
+  int team = big ? team_opt : 1;
   int clusters = batch_clusters(smem, team);
   if (clusters < 1 && team > 1) {
     team = 1;
@@ -2548,7 +2552,7 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   CK(cudaMemsetAsync(H0->b_next, 0, sizeof(unsigned int), st));
   CK(cudaEventRecord(H0->b_ev[0], st));
   if (launch_batch_cfc(H0->b_items, H0->b_outs, H0->b_hist, H0->b_order, count, H0->b_next, clusters, team,
-                       BATCH_TEAM_CELLS, smem, st)) {
+                       team_cells, smem, st)) {
     CK(cudaGetLastError());
     return fail(MG_ERR_CUDA, "batch launch refused");
   }

@@ -423,8 +423,9 @@ struct BatchOut {
 // Blocks a cluster of the batch kernel (team = blocks per cluster, 1 for
 // none) holds; the clusters of that shape co-resident on the device (0 when
 // it does not fit).
-constexpr int BATCH_TEAM = 4;
-constexpr long BATCH_TEAM_CELLS = 32768;  // grids this large run on a whole cluster
+constexpr int BATCH_TEAM = 8;                     // the largest cluster a launch may use
+constexpr int BATCH_TEAM_DEFAULT = 2;
+constexpr long BATCH_TEAM_CELLS = 16384;  // default: grids this large run on a whole cluster
 int batch_clusters(size_t smem, int team);
 // One launch over count problems (items in device memory, taken in the
 // order order[0 ..]) on clusters x team blocks; problems of at least

@@ -75,6 +75,10 @@ class mg_cfc_report(C.Structure):
     _fields_ = [("eq", mg_solve_report * 4), ("ms", C.c_double)]
 
 
+class mg_batch_opts(C.Structure):
+    _fields_ = [("team", C.c_int), ("team_cells", C.c_int64)]
+
+
 class mg_batch_report(C.Structure):
     _fields_ = [("kernel_ms", C.c_double), ("blocks", C.c_int), ("team", C.c_int), ("persistent", C.c_int),
                 ("general", C.c_int)]
@@ -125,7 +129,8 @@ def lib():
         L.mg_solve_cfc.argtypes = [P, C.POINTER(mg_cfc_sources), C.POINTER(mg_cfc_fields), I,
                                    C.POINTER(mg_cfc_report)]
         L.mg_solve_cfc_batch.argtypes = [C.POINTER(P), I, C.POINTER(mg_cfc_sources), C.POINTER(mg_cfc_fields), I,
-                                         C.POINTER(mg_cfc_report), C.POINTER(mg_batch_report)]
+                                         C.POINTER(mg_batch_opts), C.POINTER(mg_cfc_report),
+                                         C.POINTER(mg_batch_report)]
         L.mg_clean_divB.argtypes = [P, C.POINTER(P), P, I, C.POINTER(mg_divb_report)]
         L.mg_solve_scalar.argtypes = [P, I, I, I, P, P, P, P, P, C.POINTER(mg_solve_report)]
         L.mg_solve_vector.argtypes = [P, I, C.POINTER(P), C.POINTER(P), C.POINTER(mg_solve_report)]
@@ -288,11 +293,12 @@ def mg_solve_cfc(h, U, S, Si, psi, alpha, beta, X, psi_only=False, host=False, a
     return {"status": STATUS[st], "ms": rep.ms, **{names[k]: rep.eq[k].as_dict() for k in range(4)}}
 
 
-def mg_solve_cfc_batch(problems, psi_only=False, reports=True, allow=(MG_OK,)):
+def mg_solve_cfc_batch(problems, psi_only=False, reports=True, team=0, team_cells=0, allow=(MG_OK,)):
     """Independent xCFC solves in one persistent launch (mg_solve_cfc_batch).
     problems: sequence of (h, U, S, Si, psi, alpha, beta, X) as mg_solve_cfc
-    takes them (device tensors, one hierarchy per problem).  Returns
-    (per-problem reports or None, batch report dict)."""
+    takes them (device tensors, one hierarchy per problem); team, team_cells:
+    the launch shape (0: the library's default).  Returns (per-problem
+    reports or None, batch report dict)."""
     count = len(problems)
     hs = (C.c_void_p * count)()
     srcs = (mg_cfc_sources * count)()
@@ -309,7 +315,9 @@ def mg_solve_cfc_batch(problems, psi_only=False, reports=True, allow=(MG_OK,)):
             ios[q].X = _parr(X, h, name="X")
     reps = (mg_cfc_report * count)() if reports else None
     brep = mg_batch_report()
-    st = lib().mg_solve_cfc_batch(hs, count, srcs, ios, MG_CFC_PSI_ONLY if psi_only else 0, reps, C.byref(brep))
+    opts = mg_batch_opts(team, team_cells)
+    st = lib().mg_solve_cfc_batch(hs, count, srcs, ios, MG_CFC_PSI_ONLY if psi_only else 0, C.byref(opts), reps,
+                                  C.byref(brep))
     _check(st, "mg_solve_cfc_batch", allow)
     names = ["X", "psi", "alphapsi", "beta"]
     out = None

@@ -185,12 +185,36 @@ def test_batch_hands_momentum_to_the_general_path(mg):
     close(ps + [ref])
 
 
+@pytest.mark.parametrize("team,team_cells", [(1, 0), (4, 8192), (8, 8192)])
+def test_batch_launch_shapes(mg, team, team_cells):
+    """Single blocks only, and clusters of 4 and 8 blocks taking every grid
+    of 8192 cells and more: the same iteration, so the fields agree with the
+    default launch's within the rounding of the mixing sums, and every solve
+    converges."""
+    ps = [problem(mg, *s) for s in STARS]
+    ref, _ = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
+    want = [(host(p["f"][0]), host(p["f"][1])) for p in ps]
+    for p in ps:
+        p["f"][0].fill_(1.0)
+        p["f"][1].fill_(1.0)
+    reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps], team=team, team_cells=team_cells)
+    assert b["status"] == "ok" and b["team"] == team, b
+    for p, r, r0, (a, c) in zip(ps, reps, ref, want):
+        for k in ("psi", "alphapsi"):
+            assert r[k]["status"] == "ok" and r[k]["rel"] <= 1e-10
+            assert abs(r[k]["cycles"] - r0[k]["cycles"]) <= max(2, 0.15 * r0[k]["cycles"])
+        assert relerr(host(p["f"][0]), a) < 2e-9 and relerr(host(p["f"][1]), c) < 2e-9
+    close(ps)
+
+
 def test_batch_rejects_bad_arguments(mg):
-    """Before any work: the same hierarchy twice, an FP64 hierarchy, and
-    FMG cycles."""
+    """Before any work: the same hierarchy twice, a cluster of 3 blocks, an
+    FP64 hierarchy, and FMG cycles."""
     a, b = problem(mg, *STARS[0]), problem(mg, *STARS[1])
     with pytest.raises(mg.MgError):
         mg.mg_solve_cfc_batch([as_tuple(a), as_tuple(a)])
+    with pytest.raises(mg.MgError):
+        mg.mg_solve_cfc_batch([as_tuple(a), as_tuple(b)], team=3)
     for kw in [{"precision": "fp64"}, {"cycle": "fmg"}]:
         U, S, Si, lo, hi = b["np"]
         args = dict(precision="mixed", tol=1e-10, max_cycles=800, accel_depth=16)
