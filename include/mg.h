@@ -235,7 +235,8 @@ typedef struct {
  * max_cycles < MG_HIST) with src[i], io[i] as in mg_solve_cfc (device
  * pointers only: MG_HOST_POINTERS is refused).  Problems whose S_i, X or
  * beta guesses are not all zero need the vector equations (Steps 1 and 6)
- * and are solved by mg_solve_cfc after the launch; for the others X = beta
+ * and are solved by mg_solve_cfc after the launch (up to 16 at once, from
+ * host threads, each on its hierarchy's stream); for the others X = beta
  * = 0 exactly (zero right-hand sides and guesses: cycle 0).  flags:
  * MG_CFC_PSI_ONLY.  opts may be NULL.  The launch runs on hs[0]'s stream after the work queued
  * on every hierarchy's stream; the call returns when all problems are done.

@@ -3,11 +3,13 @@
 // loop, the xCFC solve order and divergence cleaning, behind the C ABI of
 // include/mg.h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "mg.h"
@@ -2379,6 +2381,7 @@ out:
 }
 
 static_assert(BATCH_HIST == MG_HIST, "batched reports keep MG_HIST residuals per equation");
+constexpr int BATCH_GENERAL_THREADS = 16;
 
 namespace {
 
@@ -2570,14 +2573,38 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   unsigned long long t0 = ~0ULL;
   for (const BatchOut& o : outs) t0 = std::min(t0, o.t_start);
   int status = MG_OK, general = 0;
+  // problems with momentum: mg_solve_cfc on up to BATCH_GENERAL_THREADS host
+  // threads, each hierarchy on its own stream so that their kernels overlap
+  // (host cycle loops, as in the request server's slots)
+  std::vector<int> gen;
+  for (int i = 0; i < count; ++i)
+    if (outs[i].status[0] == BATCH_GENERAL) gen.push_back(i);
+  general = (int)gen.size();
+  if (!gen.empty()) {
+    std::vector<int> gst(gen.size(), MG_OK);
+    std::atomic<int> take{0};
+    auto work = [&]() {
+      for (;;) {
+        const int q = take.fetch_add(1);
+        if (q >= (int)gen.size()) return;
+        mg_hierarchy* h = hs[gen[q]];
+        const bool host_loop = h->loop_off;
+        hier_set_host_loop(h, true);
+        gst[q] = mg_solve_cfc(h, &src[gen[q]], &io[gen[q]], flags, rep ? &rep[gen[q]] : nullptr);
+        hier_set_host_loop(h, host_loop);
+      }
+    };
+    const int nt = std::min<int>((int)gen.size(), BATCH_GENERAL_THREADS);
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (std::thread& t : pool) t.join();
+    for (int s : gst)
+      if (s && !status) status = s;
+  }
   for (int i = 0; i < count; ++i) {
     const BatchOut& o = outs[i];
-    if (o.status[0] == BATCH_GENERAL) {
-      ++general;
-      const int s = mg_solve_cfc(hs[i], &src[i], &io[i], flags, rep ? &rep[i] : nullptr);
-      if (s && !status) status = s;
-      continue;
-    }
+    if (o.status[0] == BATCH_GENERAL) continue;
     for (int e = 1; e <= 2; ++e)
       if (o.status[e] && !status) status = o.status[e];
     hs[i]->batch_cycles = o.cycles[1] + o.cycles[2];

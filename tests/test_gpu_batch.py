@@ -168,21 +168,27 @@ def test_batch_psi_only_and_no_mixing(mg):
         close(ps)
 
 
+ROTATING = [("sph", [64, 32], 1.28e-3, 10.0), ("cyl", [32, 64], 9e-4, 12.0), ("sph", [32, 16], 1.6e-3, 9.0),
+            ("cyl", [64, 128], 1.1e-3, 11.0)]
+
+
 def test_batch_hands_momentum_to_the_general_path(mg):
-    """A rotating star in the batch (S_i != 0) is solved by mg_solve_cfc
-    after the launch: its fields equal that call's bitwise, the static stars
-    are still solved in the launch."""
-    ps = [problem(mg, *STARS[0]), problem(mg, "sph", [64, 32], 1.28e-3, 10.0, omega=0.02),
-          problem(mg, *STARS[1])]
+    """Rotating stars in the batch (S_i != 0) are solved by mg_solve_cfc
+    after the launch, several at once from host threads: each one's fields
+    equal that call's alone bitwise; the static stars are still solved in
+    the launch."""
+    ps = [problem(mg, *STARS[0])] + [problem(mg, *s, omega=0.02) for s in ROTATING] + [problem(mg, *STARS[1])]
     reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
-    assert b["persistent"] == 2 and b["general"] == 1 and b["status"] == "ok"
-    ref = problem(mg, "sph", [64, 32], 1.28e-3, 10.0, omega=0.02)
-    ra = mg.mg_solve_cfc(*as_tuple(ref))
-    assert reps[1]["X"]["cycles"] == ra["X"]["cycles"] > 0
-    for a, c in zip([ref["f"][0], ref["f"][1]] + ref["f"][2] + ref["f"][3],
-                    [ps[1]["f"][0], ps[1]["f"][1]] + ps[1]["f"][2] + ps[1]["f"][3]):
-        assert torch.equal(a, c)
-    close(ps + [ref])
+    assert b["persistent"] == 2 and b["general"] == len(ROTATING) and b["status"] == "ok", b
+    for s, p, r in zip(ROTATING, ps[1:], reps[1:]):
+        ref = problem(mg, *s, omega=0.02)
+        ra = mg.mg_solve_cfc(*as_tuple(ref))
+        assert r["X"]["cycles"] == ra["X"]["cycles"] > 0 and r["psi"]["cycles"] == ra["psi"]["cycles"]
+        for a, c in zip([ref["f"][0], ref["f"][1]] + ref["f"][2] + ref["f"][3],
+                        [p["f"][0], p["f"][1]] + p["f"][2] + p["f"][3]):
+            assert torch.equal(a, c)
+        ref["h"].close()
+    close(ps)
 
 
 @pytest.mark.parametrize("team,team_cells", [(1, 0), (4, 8192), (8, 8192)])
