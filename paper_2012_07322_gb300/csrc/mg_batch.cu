@@ -80,6 +80,10 @@ __device__ __forceinline__ long bt_ghosted(const LevelView<T>& L) {
   return L.sy * (L.n2 + 2 * L.three);
 }
 
+// The FP32 passes and the mixing below copy the level views they stream
+// over out of shared memory: held by reference, every field would be read
+// back after each global store (the compiler cannot tell the two apart).
+
 // FP64 residual of the finest level with the stopping norms (as
 // k_residual_scalar, weighted): the FP32 right-hand side of the correction
 // cycle into lv[0].f32 and, for eq. psi, its linearisation K into lv[0].k32;
@@ -87,7 +91,7 @@ __device__ __forceinline__ long bt_ghosted(const LevelView<T>& L) {
 template <int G, int KIND>
 __device__ double bt_norm(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
                           BtShared& S) {
-  const LevelView<double>& L = I.v64;
+  const LevelView<double>& L = I.v64;  // passed on to the out-of-line FP64 edge rules: stays in shared memory
   unsigned long long* red = T.at0(S.red);
   if (T.rank == 0 && threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
   T.sync();
@@ -130,7 +134,7 @@ __device__ double bt_norm(const Team& T, const BatchItem& I, const double* f, co
 // level (the cells of a colour are independent).
 template <int G>
 __device__ void bt_smooth(const Team& T, const BatchLevel& B, int nsweeps) {
-  const LevelView<float>& L = B.v;
+  const LevelView<float> L = B.v;
   float* __restrict__ e = B.e;
   const float* __restrict__ f = B.f32;
   const float* __restrict__ K = B.k32;
@@ -151,7 +155,7 @@ __device__ void bt_smooth(const Team& T, const BatchLevel& B, int nsweeps) {
 // evaluated at the current iterate and restricted on the way down).
 template <int G>
 __device__ void bt_resid_restrict(const Team& T, const BatchLevel& F, const BatchLevel& C, bool fold) {
-  const LevelView<float>& L = F.v;
+  const LevelView<float> L = F.v;
   const long n = (long)L.n0 * L.n1 * L.n2;
   float* __restrict__ r32 = F.r32;
   const float* __restrict__ e = F.e;
@@ -163,7 +167,7 @@ __device__ void bt_resid_restrict(const Team& T, const BatchLevel& F, const Batc
     r32[p] = scalar_residual_cell<float, G, EQ_LIN>(L, e, F.f32, nullptr, F.k32, i, j, k, p, Sv);
   }
   T.sync();
-  const LevelView<float>& Cv = C.v;
+  const LevelView<float> Cv = C.v;
   const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2, ngC = bt_ghosted(Cv);
   const float* const as[4] = {F.r32, F.k32, nullptr, nullptr};
   float* const bs[4] = {C.f32, C.k32, nullptr, nullptr};
@@ -217,7 +221,7 @@ __device__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* s
   for (int l = I.nl - 1; l >= 0; --l) {
     const BatchLevel& F = I.lv[l];
     const BatchLevel& C = I.lv[l + 1];
-    const LevelView<float>& Fv = F.v;
+    const LevelView<float> Fv = F.v;
     const long nF = (long)Fv.n0 * Fv.n1 * Fv.n2;
     float* __restrict__ e = F.e;
     const float* __restrict__ eC = C.e;
@@ -239,7 +243,7 @@ __device__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* s
 // degenerate history; 0 when no column is live).
 template <int G4>
 __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, BtShared& S) {
-  const LevelView<double>& L = I.v64;
+  const LevelView<double> L = I.v64;
   const long nq = bt_cells(L) / G4, vs = bt_ghosted(L);
   const int nc = cols.n;
   const long onew = nc > 0 ? (long)cols.slot[nc - 1] * vs : 0;
@@ -392,7 +396,7 @@ __device__ int bt_mix(const Team& T, const BatchItem& I, const AACols& cols, BtS
 // u += e on the interior of level 0 (the FP64 update of the defect
 // correction), in groups of four cells of a row where n0 allows.
 __device__ void bt_add_correction(const Team& T, const BatchItem& I) {
-  const LevelView<double>& L = I.v64;
+  const LevelView<double> L = I.v64;
   const long n = bt_cells(L);
   double* __restrict__ u = I.u;
   const float* __restrict__ e = I.lv[0].e;
