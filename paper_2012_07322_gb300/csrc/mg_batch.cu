@@ -1,5 +1,6 @@
-// Batched xCFC solves in one persistent launch.  Each thread block takes a
-// problem from a shared queue (longest first) and runs its whole static-star
+// Batched xCFC solves in one persistent launch.  Each thread block (a
+// cluster of blocks for the largest grids) takes a problem from a shared
+// queue (longest first) and runs its whole static-star
 // xCFC solve: eq. psi (Sec. 2.6 Step 3), the alpha-psi coefficient, eq.
 // alpha (Step 5) and alpha = (alpha psi) / psi, each equation by the
 // mixed-precision defect correction of the launched path: the FP64 residual
@@ -8,14 +9,14 @@
 // 2.7.2-2.7.3) whose levels of at most BLOCK_CYCLE_CELLS cells run the
 // one-block cycle in shared memory, the FP64 update and the Anderson mixing
 // step.  The phases are those of the launched kernels, with the same
-// per-cell functions, separated by block barriers: a 2D problem of a few
+// per-cell functions, separated by block (or cluster) barriers: a 2D problem of a few
 // thousand to a hundred thousand cells leaves a launched V-cycle
 // latency-bound, and one block per problem lets many problems of different
 // sizes fill the GPU together without a launch per phase.
 //
 // Problems with momentum (S_i, or a non-zero X or beta guess) need the
 // vector equations of Steps 1 and 6; they are marked BATCH_GENERAL and the
-// host solves them through mg_solve_cfc.  For the others X = beta = 0 is
+// host solves them through mg_solve_cfc after the launch.  For the others X = beta = 0 is
 // exact: both right-hand sides vanish and the solves stop at cycle 0.
 #include <cooperative_groups.h>
 
@@ -29,7 +30,6 @@ namespace cg = cooperative_groups;
 namespace gmg {
 
 static_assert(BATCH_THREADS == BC_THREADS, "the batch kernel runs the one-block cycle");
-
 
 // The blocks that run one problem: a whole thread-block cluster (a team of
 // up to BATCH_TEAM blocks) for the largest grids, else one block alone.  Passes
