@@ -1,8 +1,8 @@
 // Batched xCFC solves in one persistent launch.  Each thread block (a
 // cluster of blocks for the largest grids) takes a problem from a shared
-// queue (longest first) and runs its whole static-star
-// xCFC solve: eq. psi (Sec. 2.6 Step 3), the alpha-psi coefficient, eq.
-// alpha (Step 5) and alpha = (alpha psi) / psi, each equation by the
+// queue (longest first) and runs its whole xCFC solve in the order of
+// Sec. 2.6 (Steps 1-6: eq. X, A~^2, eq. psi, the alpha-psi coefficient,
+// eq. alpha, the shift source and eq. beta), each equation by the
 // mixed-precision defect correction of the launched path: the FP64 residual
 // and stopping norm (Sec. 2.7.2), a V-cycle of the FP32 correction equation
 // (red-black NGS, volume-weighted restriction, Kwak prolongation; Secs.
@@ -14,16 +14,18 @@
 // latency-bound, and one block per problem lets many problems of different
 // sizes fill the GPU together without a launch per phase.
 //
-// Problems with momentum (S_i, or a non-zero X or beta guess) need the
-// vector equations of Steps 1 and 6; they are marked BATCH_GENERAL and the
-// host solves them through mg_solve_cfc after the launch.  For the others X = beta = 0 is
-// exact: both right-hand sides vanish and the solves stop at cycle 0.
+// Without momentum (S_i and the X and beta guesses all zero) X = beta = 0
+// is exact: both right-hand sides vanish and the solves stop at cycle 0, so
+// those steps are skipped.  Problems with momentum on a hierarchy whose
+// vector levels do not fit the kernel are marked BATCH_GENERAL and the host
+// solves them through mg_solve_cfc after the launch.
 #include <cooperative_groups.h>
 
 #include "mg_internal.h"
 #include "mg_kernels.cuh"
 #include "mg_block.cuh"
 #include "mg_accel.cuh"
+#include "mg_xcfc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -89,7 +91,7 @@ __device__ __forceinline__ long bt_ghosted(const LevelView<T>& L) {
 // cycle into lv[0].f32 and, for eq. psi, its linearisation K into lv[0].k32;
 // returns rel = max |w r| / max |w S| (NaN when a norm is not finite).
 template <int G, int KIND>
-__device__ double bt_norm(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
+__device__ __noinline__ double bt_norm(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
                           BtShared& S) {
   const LevelView<double>& L = I.v64;  // passed on to the out-of-line FP64 edge rules: stays in shared memory
   unsigned long long* red = T.at0(S.red);
@@ -208,7 +210,7 @@ __device__ void bt_restrict_k_all(const Team& T, const BatchItem& I) {
 // level nl, the one-block cycle from there (rank 0 of a team runs it alone),
 // prolongation and post-smoothing back up.
 template <int G>
-__device__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* sm, double* smd) {
+__device__ __noinline__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* sm, double* smd) {
   for (int l = 0; l < I.nl; ++l) {
     bt_smooth<G>(T, I.lv[l], I.nu1);
     bt_resid_restrict<G>(T, I.lv[l], I.lv[l + 1], fold);
@@ -216,7 +218,7 @@ __device__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* s
   if (fold)
     for (int q = 1; q < I.bc.nl; ++q)
       bt_restrict_k(T, I.bc.lv[q - 1].v, I.bc.lv[q - 1].k32, I.bc.lv[q].v, const_cast<float*>(I.bc.lv[q].k32));
-  if (T.rank == 0) bc_run<G, false>(I.bc, sm, smd);
+  if (T.rank == 0) bc_run<G, false, true>(I.bc, sm, smd);
   T.sync();
   for (int l = I.nl - 1; l >= 0; --l) {
     const BatchLevel& F = I.lv[l];
@@ -239,12 +241,14 @@ __device__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* s
 // FP32 history): g = u, f = g - x, the newest difference columns, their dot
 // products with the live columns, the Gram solve by warp 0, and
 // u = g - sum gamma_a dG_a, x = u.  Values stream in groups of G4
-// consecutive cells of a row.  Returns the solve's status (0 solved, 1
-// degenerate history; 0 when no column is live).
+// consecutive cells of a row; a vector of ncomp components is ncomp ghosted
+// arrays back to back (the storage at I.aa holds x, f', g' and the m
+// columns of dF and dG in that layout).  Returns the solve's status (0
+// solved, 1 degenerate history; 0 when no column is live).
 template <int G4>
-__device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, BtShared& S) {
+__device__ int bt_mix_g(const Team& T, const BatchItem& I, int ncomp, const AACols& cols, BtShared& S) {
   const LevelView<double> L = I.v64;
-  const long nq = bt_cells(L) / G4, vs = bt_ghosted(L);
+  const long nq = bt_cells(L) / G4, ng = bt_ghosted(L), vs = ncomp * ng;
   const int nc = cols.n;
   const long onew = nc > 0 ? (long)cols.slot[nc - 1] * vs : 0;
   // the live columns' offsets in shared memory: read there in the streaming
@@ -252,20 +256,23 @@ __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, B
   if (threadIdx.x == 0) S.cols = cols;
   if (threadIdx.x < AA_MAX) S.coff[threadIdx.x] = (long)cols.slot[threadIdx.x] * vs;
   __syncthreads();
-  double* __restrict__ u = I.u;
-  double* __restrict__ x = I.x;
-  double* __restrict__ fpr = I.fp;
-  double* __restrict__ gpr = I.gp;
-  const float* __restrict__ dFr = I.dF;
-  float* __restrict__ dFw = I.dF + onew;
-  float* __restrict__ dGw = I.dG + onew;
+  double* __restrict__ x = I.aa;
+  double* __restrict__ fpr = x + vs;
+  double* __restrict__ gpr = fpr + vs;
+  float* const dF = reinterpret_cast<float*>(gpr + vs);
+  float* const dG = dF + (long)I.m * vs;
+  const float* __restrict__ dFr = dF;
+  float* __restrict__ dFw = dF + onew;
+  float* __restrict__ dGw = dG + onew;
   float v[32];
 #pragma unroll
   for (int a = 0; a < 32; ++a) v[a] = 0.0f;
+  for (int c = 0; c < ncomp; ++c)
   for (long q = T.start(); q < nq; q += T.stride()) {
-    const long p = aa_pos<G4>(L, q);
+    double* __restrict__ u = I.u3[c];
+    const long pu = aa_pos<G4>(L, q), p = (long)c * ng + pu;
     double g[G4], xv[G4], fp[G4], gp[G4], f[G4];
-    aa_ld_u<G4>(u + p, g);
+    aa_ld_u<G4>(u + pu, g);
     aa_ld<G4>(x + p, xv);
     aa_ld<G4>(fpr + p, fp);
     aa_ld<G4>(gpr + p, gp);
@@ -363,9 +370,11 @@ __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, B
     float gm[AA_MAX];
 #pragma unroll
     for (int a = 0; a < AA_MAX; ++a) gm[a] = a < nc ? S.gamma[a] : 0.0f;
-    const float* __restrict__ dGr = I.dG;
+    const float* __restrict__ dGr = dG;
+    for (int c = 0; c < ncomp; ++c)
     for (long q = T.start(); q < nq; q += T.stride()) {
-      const long p = aa_pos<G4>(L, q);
+      double* __restrict__ u = I.u3[c];
+      const long pu = aa_pos<G4>(L, q), p = (long)c * ng + pu;
       float sacc[G4];
 #pragma unroll
       for (int t = 0; t < G4; ++t) sacc[t] = 0.0f;
@@ -378,10 +387,10 @@ __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, B
         for (int t = 0; t < G4; ++t) sacc[t] += gm[a] * d[t];
       }
       double uv[G4];
-      aa_ld_u<G4>(u + p, uv);
+      aa_ld_u<G4>(u + pu, uv);
 #pragma unroll
       for (int t = 0; t < G4; ++t) uv[t] -= (double)sacc[t];
-      aa_st_u<G4>(u + p, uv);
+      aa_st_u<G4>(u + pu, uv);
       aa_st<G4>(x + p, uv);
     }
   }
@@ -389,8 +398,8 @@ __device__ int bt_mix_g(const Team& T, const BatchItem& I, const AACols& cols, B
   return st;
 }
 
-__device__ int bt_mix(const Team& T, const BatchItem& I, const AACols& cols, BtShared& S) {
-  return I.v64.n0 >= 4 ? bt_mix_g<4>(T, I, cols, S) : bt_mix_g<1>(T, I, cols, S);
+__device__ int bt_mix(const Team& T, const BatchItem& I, int ncomp, const AACols& cols, BtShared& S) {
+  return I.v64.n0 >= 4 ? bt_mix_g<4>(T, I, ncomp, cols, S) : bt_mix_g<1>(T, I, ncomp, cols, S);
 }
 
 // u += e on the interior of level 0 (the FP64 update of the defect
@@ -419,13 +428,176 @@ __device__ void bt_add_correction(const Team& T, const BatchItem& I) {
   T.sync();
 }
 
+// ------------------------------------------------- vector equations (X, beta)
+// The vector equation lap V + 1/3 grad div V = f with the Dirichlet outer
+// rule (eqs. X, beta): ghosts are stored, refreshed after every pass that
+// changes a component, as in the launched path.  The FP32 passes use the
+// flux form of the operator (as the one-block cycle does).
+
+// The ghosts of one component of a level (each ghost reads only interior
+// cells, so one pass suffices); the caller's barrier follows.
+template <typename TT>
+__device__ void bt_fill(const Team& T, const LevelView<TT>& L, TT* u, int comp) {
+  const long ng = ghost_count(L);
+  for (long g = T.start(); g < ng; g += T.stride()) fill_one_ghost(L, u, comp, g);
+}
+
+// FP64 residual of the finest level (ghosts current) with the stopping
+// norms (as k_residual_vec, weighted), the FP32 right-hand sides of the
+// correction cycle into lv[0].f3.
+template <int G>
+__device__ __noinline__ double bt_norm_vec(const Team& T, const BatchItem& I, BtShared& S) {
+  const LevelView<double>& L = I.v64;
+  unsigned long long* red = T.at0(S.red);
+  if (T.rank == 0 && threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
+  T.sync();
+  unsigned long long m0 = 0ULL, m1 = 0ULL, m2 = 0ULL;
+  const long n = bt_cells(L);
+  for (long q = T.start(); q < n; q += T.stride()) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    const double w = (double)norm_weight(L, i, j);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double fv = I.f3[c][p];
+      const double rv = vec_residual_cell<double, G>(L, I.u3[0], I.u3[1], I.u3[2], I.f3[c], c, i, j, p);
+      I.lv[0].f3[c][p] = (float)rv;
+      m0 = umax64(m0, abs_bits(rv));
+      m1 = umax64(m1, abs_bits(w * rv));
+      m2 = umax64(m2, abs_bits(w * fv));
+    }
+  }
+  m0 = warp_max_bits(m0);
+  m1 = warp_max_bits(m1);
+  m2 = warp_max_bits(m2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&red[0], m0);
+    atomicMax(&red[1], m1);
+    atomicMax(&red[2], m2);
+  }
+  T.sync();
+  const double num = __longlong_as_double((long long)red[1]), den = __longlong_as_double((long long)red[2]);
+  T.sync();
+  if (isinf(num) || isinf(den) || isnan(num) || isnan(den)) return __longlong_as_double(0x7ff8000000000000LL);
+  return num / (den > 1e-300 ? den : 1e-300);
+}
+
+// nsweeps red-black sweeps, component by component, each component's
+// ghosts refreshed after its pass.
+template <int G>
+__device__ void bt_smooth_vec(const Team& T, const BatchLevel& B, int nsweeps) {
+  LevelView<float> L = B.v;
+  L.bc = BC_DIRICHLET;
+  float* const e0 = B.e3[0];
+  float* const e1 = B.e3[1];
+  float* const e2 = B.e3[2];
+  const long nh = (long)L.n0 * L.n1 * L.n2 / 2;
+  for (int s = 0; s < nsweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour)
+#pragma unroll 1
+      for (int c = 0; c < 3; ++c) {
+        for (long q = T.start(); q < nh; q += T.stride()) {
+          int i, j, k;
+          L.colour_cell(q, colour, i, j, k);
+          vec_update<float, G, false>(L, e0, e1, e2, B.f3[c], c, i, j, k);
+        }
+        T.sync();
+        bt_fill(T, L, B.e3[c], c);
+        T.sync();
+      }
+}
+
+// Residual of every component restricted into the coarse right-hand sides
+// (each coarse cell evaluates the residuals of its own children, with the
+// weights and summation order of restrict_cell); coarse corrections zeroed.
+template <int G>
+__device__ void bt_resid_restrict_vec(const Team& T, const BatchLevel& F, const BatchLevel& C) {
+  const LevelView<float> L = F.v;
+  const LevelView<float> Cv = C.v;
+  const long nC = (long)Cv.n0 * Cv.n1 * Cv.n2, ngC = bt_ghosted(Cv);
+  const int nk = L.three ? 2 : 1;
+  for (long q = T.start(); q < nC; q += T.stride()) {
+    int I, J, K;
+    Cv.cell(q, I, J, K);
+    float wi[2], wj[2];
+    wi[0] = L.TI(TI_VW, 2 * I);
+    wi[1] = L.TI(TI_VW, 2 * I + 1);
+    wj[0] = L.TJ(TJ_VW, 2 * J);
+    wj[1] = L.TJ(TJ_VW, 2 * J + 1);
+    float wsum = 0.0f;
+    for (int dk = 0; dk < nk; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) wsum += wi[di] * wj[dj];
+    const float inv = 1.0f / wsum;
+    const long qc = Cv.idx(I, J, K);
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      float sr = 0.0f;
+      for (int dk = 0; dk < nk; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+          for (int di = 0; di < 2; ++di) {
+            const int i = 2 * I + di, j = 2 * J + dj, k = L.three ? 2 * K + dk : 0;
+            const float r = vec_residual_cell<float, G, false>(L, F.e3[0], F.e3[1], F.e3[2], F.f3[c], c, i, j,
+                                                               L.idx(i, j, k));
+            sr += wi[di] * wj[dj] * r;
+          }
+      C.f3[c][qc] = sr * inv;
+    }
+  }
+  for (long q = T.start(); q < ngC; q += T.stride())
+#pragma unroll
+    for (int c = 0; c < 3; ++c) C.e3[c][q] = 0.0f;
+  T.sync();
+}
+
+// One FP32 correction V-cycle of the vector equation from e = 0 at level 0.
+template <int G>
+__device__ __noinline__ void bt_vcycle_vec(const Team& T, const BatchItem& I, unsigned char* smem_raw) {
+  for (int l = 0; l < I.nlv; ++l) {
+    bt_smooth_vec<G>(T, I.lv[l], I.nu1);
+    bt_resid_restrict_vec<G>(T, I.lv[l], I.lv[l + 1]);
+  }
+  if (T.rank == 0)
+    bc_run<G, true, true>(I.bcv, reinterpret_cast<float*>(smem_raw),
+                    reinterpret_cast<double*>(smem_raw + I.bcv.fp64_at));
+  T.sync();
+  for (int l = I.nlv - 1; l >= 0; --l) {
+    const BatchLevel& F = I.lv[l];
+    const BatchLevel& C = I.lv[l + 1];
+    LevelView<float> Fv = F.v;
+    Fv.bc = BC_DIRICHLET;
+    const long nF = (long)Fv.n0 * Fv.n1 * Fv.n2;
+    for (long q = T.start(); q < nF; q += T.stride()) {
+      int i, j, k;
+      Fv.cell(q, i, j, k);
+#pragma unroll 1
+      for (int c = 0; c < 3; ++c) prolong_cell(Fv, C.v, F.e3[c], C.e3[c], (const float*)nullptr, c, i, j, k);
+    }
+    T.sync();
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) bt_fill(T, Fv, F.e3[c], c);
+    T.sync();
+    bt_smooth_vec<G>(T, F, I.nu2);
+  }
+}
+
+// The finest FP64 components' ghosts (Dirichlet rule).
+__device__ void bt_fill_u3(const Team& T, const BatchItem& I) {
+  LevelView<double> L = I.v64;
+  L.bc = BC_DIRICHLET;
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) bt_fill(T, L, I.u3[c], c);
+  T.sync();
+}
+
 // One scalar equation by the defect-correction loop of the launched path
 // (the stopping rule in its order: non-finite, tol, max_cycles, stall
 // window); u, f, s0, s1 as the equation's operator takes them.  Every block
 // of a team takes the same decisions: they depend only on values read from
 // rank 0's shared memory after a barrier.  Returns the status.
 template <int G, int KIND>
-__device__ int bt_solve(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
+__device__ __noinline__ int bt_solve(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
                         BatchOut& O, int eq, double* hist, float* sm, double* smd, BtShared& S) {
   const LevelView<double>& L = I.v64;
   const long n = bt_cells(L), ng = bt_ghosted(L);
@@ -464,7 +636,7 @@ __device__ int bt_solve(const Team& T, const BatchItem& I, const double* f, cons
       break;
     }
     if (m > 0 && cyc == 0)
-      for (long q = T.start(); q < ng; q += T.stride()) I.x[q] = I.u[q];
+      for (long q = T.start(); q < ng; q += T.stride()) I.aa[q] = I.u[q];
     for (long q = T.start(); q < ng; q += T.stride()) I.lv[0].e[q] = 0.0f;
     T.sync();
     bt_vcycle<G>(T, I, KIND == EQ_PSI, sm, smd);
@@ -485,7 +657,7 @@ __device__ int bt_solve(const Team& T, const BatchItem& I, const double* f, cons
         for (int a = 0; a < AA_MAX; ++a)
           if (a < ncol) cols.slot[a] = (slot - ncol + 1 + a + m) % m;  // oldest first
       }
-      mst = bt_mix(T, I, cols, S);
+      mst = bt_mix(T, I, 1, cols, S);
       mixstep = cols.n > 0;
     }
     ++cyc;
@@ -522,27 +694,177 @@ __device__ bool bt_momentum_free(const Team& T, const BatchItem& I, BtShared& S)
   return !any;
 }
 
-// The xCFC sequence of mg_solve_cfc for one momentum-free problem.
+// One vector equation (X or beta) by the defect-correction loop, as
+// bt_solve (the mixing over the three components); u3 and f3 set by the
+// caller.  Returns the status.
 template <int G>
-__device__ void bt_problem(const Team& T, const BatchItem& I, BatchOut& O, double* hist, float* sm, double* smd,
-                           BtShared& S) {
+__device__ __noinline__ int bt_solve_vec(const Team& T, const BatchItem& I, BatchOut& O, int eq, double* hist,
+                            unsigned char* smem_raw, BtShared& S) {
   const LevelView<double>& L = I.v64;
-  const long n = bt_cells(L);
-  if (!I.psi_only && !bt_momentum_free(T, I, S)) {
-    if (T.rank == 0 && threadIdx.x == 0) O.status[0] = BATCH_GENERAL;
-    return;
+  const long n = bt_cells(L), ng = bt_ghosted(L);
+  bt_fill_u3(T, I);
+  const int m = I.m;
+  int cyc = 0, ncol = 0, head = 0, status = 0;
+  double rel = bt_norm_vec<G>(T, I, S);
+  if (threadIdx.x == 0) {
+    S.hist[0] = rel;
+    if (T.rank == 0) hist[0] = rel;
   }
-  // Steps 1-2: X = 0 exactly, so A~^2 = 0.  Step 3: eq. psi for psi - 1
+  __syncthreads();
+  for (;;) {
+    if (rel != rel) {
+      status = 5;  // MG_ERR_NAN
+      break;
+    }
+    if (rel <= I.tol) break;
+    if (cyc >= I.max_cycles) {
+      status = 3;  // MG_ERR_NOCONV
+      break;
+    }
+    if (I.stall_window > 0 && cyc >= I.stall_window && rel > 0.95 * S.hist[cyc - I.stall_window]) {
+      status = 4;  // MG_ERR_STALLED
+      break;
+    }
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      if (m > 0 && cyc == 0)
+        for (long q = T.start(); q < ng; q += T.stride()) I.aa[c * ng + q] = I.u3[c][q];
+      for (long q = T.start(); q < ng; q += T.stride()) I.lv[0].e3[c][q] = 0.0f;
+    }
+    T.sync();
+    bt_vcycle_vec<G>(T, I, smem_raw);
+    // u += e, then the FP64 ghosts
+    for (long q = T.start(); q < n; q += T.stride()) {
+      int i, j, k;
+      L.cell(q, i, j, k);
+      const long p = L.idx(i, j, k);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) I.u3[c][p] += (double)I.lv[0].e3[c][p];
+    }
+    T.sync();
+    bt_fill_u3(T, I);
+    bool mixstep = false;
+    int mst = 0;
+    if (m > 0) {
+      AACols cols;
+      cols.n = 0;
+#pragma unroll
+      for (int a = 0; a < AA_MAX; ++a) cols.slot[a] = 0;
+      if (cyc > 0) {
+        const int slot = head;
+        head = (head + 1) % m;
+        if (ncol < m) ++ncol;
+        cols.n = ncol;
+#pragma unroll
+        for (int a = 0; a < AA_MAX; ++a)
+          if (a < ncol) cols.slot[a] = (slot - ncol + 1 + a + m) % m;  // oldest first
+      }
+      mst = bt_mix(T, I, 3, cols, S);
+      mixstep = cols.n > 0;
+      if (mixstep) bt_fill_u3(T, I);
+    }
+    ++cyc;
+    rel = bt_norm_vec<G>(T, I, S);
+    if (mixstep && mst != 0) ncol = 0;  // degenerate history: restart the mixing
+    if (threadIdx.x == 0 && cyc < BATCH_HIST) {
+      S.hist[cyc] = rel;
+      if (T.rank == 0) hist[cyc] = rel;
+    }
+    __syncthreads();
+  }
+  if (T.rank == 0 && threadIdx.x == 0) {
+    O.status[eq] = status;
+    O.cycles[eq] = cyc;
+    O.rel[eq] = rel;
+    O.ran |= 1 << eq;
+  }
+  return status;
+}
+
+// The report of an equation that stops at cycle 0 with rel = 0 (zero
+// right-hand side and guess).
+__device__ void bt_trivial(const Team& T, BatchOut& O, int eq, double* hist) {
+  if (T.rank == 0 && threadIdx.x == 0) {
+    O.status[eq] = 0;
+    O.cycles[eq] = 0;
+    O.rel[eq] = 0.0;
+    O.ran |= 1 << eq;
+    hist[0] = 0.0;
+  }
+}
+
+// The xCFC sequence of mg_solve_cfc (Steps 1-6) for one problem; hist holds
+// the four equations' histories.  Problems with momentum on a hierarchy
+// whose vector levels do not fit are marked BATCH_GENERAL.
+template <int G>
+__device__ void bt_problem(const Team& T, const BatchItem& I, BatchOut& O, double* hist, unsigned char* smem_raw,
+                           BtShared& S) {
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  double* smd = reinterpret_cast<double*>(smem_raw + I.bc.fp64_at);
+  const LevelView<double>& L = I.v64;
+  const long n = bt_cells(L), ng = bt_ghosted(L);
+  bool mf = true;  // momentum-free: X = beta = 0 exactly
+  if (!I.psi_only) {
+    mf = bt_momentum_free(T, I, S);
+    if (!mf && !I.vec_ok) {
+      if (T.rank == 0 && threadIdx.x == 0) O.status[0] = BATCH_GENERAL;
+      return;
+    }
+    if (mf) {
+      bt_trivial(T, O, 0, hist);
+    } else {
+      // Step 1: lap X + 1/3 grad div X = 8 pi S_i
+      for (long q = T.start(); q < n; q += T.stride()) {
+        int i, j, k;
+        L.cell(q, i, j, k);
+        const long p = L.idx(i, j, k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          I.u3[c][p] = I.X[c][q];
+          I.f3[c][p] = 8.0 * PI_D * I.Si[c][q];
+        }
+      }
+      T.sync();
+      const int sx = bt_solve_vec<G>(T, I, O, 0, hist, smem_raw, S);
+      for (long q = T.start(); q < ng; q += T.stride())
+#pragma unroll
+        for (int c = 0; c < 3; ++c) I.Xg[c][q] = I.u3[c][q];
+      for (long q = T.start(); q < n; q += T.stride()) {
+        int i, j, k;
+        L.cell(q, i, j, k);
+        const long p = L.idx(i, j, k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) I.X[c][q] = I.u3[c][p];
+      }
+      T.sync();
+      {
+        LevelView<double> Ld = I.v64;
+        Ld.bc = BC_DIRICHLET;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) bt_fill(T, Ld, I.Xg[c], c);
+      }
+      T.sync();
+      if (sx != 0) return;
+    }
+  }
+  // Step 2: A~^2 from X (0 without momentum).  Step 3: eq. psi for psi - 1
   for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
     const long p = L.idx(i, j, k);
     I.u[p] = I.psi[q] + -1.0;
     I.s0[p] = I.U[q];
-    I.s1[p] = 0.0;
+    double a2 = 0.0;
+    if (!mf) {
+      double A[6];
+      aij_cell<G>(L, I.Xg[0], I.Xg[1], I.Xg[2], i, j, p, A);
+      a2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] + 2.0 * (A[3] * A[3] + A[4] * A[4] + A[5] * A[5]);
+    }
+    I.s1[p] = a2;
   }
   T.sync();
-  const int st = bt_solve<G, EQ_PSI>(T, I, nullptr, I.s0, I.s1, O, 1, hist, sm, smd, S);
+  const int st = bt_solve<G, EQ_PSI>(T, I, nullptr, I.s0, I.s1, O, 1, hist + BATCH_HIST, sm, smd, S);
+  if (T.rank == 0 && threadIdx.x == 0) O.ran |= 1 << 1;
   for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
@@ -552,8 +874,8 @@ __device__ void bt_problem(const Team& T, const BatchItem& I, BatchOut& O, doubl
   }
   T.sync();
   if (I.psi_only || st != 0) return;
-  // Step 5: c = 2 pi (U + 2 S) psi^-2 + 7/8 A~^2 psi^-8 (A~^2 = 0), the
-  // equation lap d - c d = c for d = alpha psi - 1
+  // Step 5: c = 2 pi (U + 2 S) psi^-2 + 7/8 A~^2 psi^-8, the equation
+  // lap d - c d = c for d = alpha psi - 1
   for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
@@ -561,14 +883,16 @@ __device__ void bt_problem(const Team& T, const BatchItem& I, BatchOut& O, doubl
     const double ip = 1.0 / (1.0 + I.dpsi[p]);
     const double ip2 = ip * ip;
     const double ip8 = (ip2 * ip2) * (ip2 * ip2);
-    const double a2 = 0.0;
+    const double a2 = I.s1[p];
     const double c = 2.0 * PI_D * (I.U[q] + 2.0 * I.S[q]) * ip2 + 0.875 * a2 * ip8;
     I.f[p] = c;
     I.s1[p] = c;
     I.u[p] = I.alpha[q] * (1.0 + I.dpsi[p]) - 1.0;
   }
   T.sync();
-  bt_solve<G, EQ_LIN>(T, I, I.f, nullptr, I.s1, O, 2, hist + BATCH_HIST, sm, smd, S);
+  const int sa = bt_solve<G, EQ_LIN>(T, I, I.f, nullptr, I.s1, O, 2, hist + 2 * BATCH_HIST, sm, smd, S);
+  if (T.rank == 0 && threadIdx.x == 0) O.ran |= 1 << 2;
+  for (long q = T.start(); q < ng; q += T.stride()) I.dap[q] = I.u[q];
   for (long q = T.start(); q < n; q += T.stride()) {
     int i, j, k;
     L.cell(q, i, j, k);
@@ -576,7 +900,46 @@ __device__ void bt_problem(const Team& T, const BatchItem& I, BatchOut& O, doubl
     I.alpha[q] = (1.0 + I.u[p]) / (1.0 + I.dpsi[p]);
   }
   T.sync();
-  // Step 6: the shift's right-hand side is zero and its guess is zero
+  if (sa != 0) return;
+  if (mf) {
+    // Step 6: the shift's right-hand side and guess are zero
+    bt_trivial(T, O, 3, hist + 3 * BATCH_HIST);
+    return;
+  }
+  // Step 6: s = alpha psi^-6 on every cell (the deviations' Robin ghosts
+  // first), the source 16 pi s S_i + 2 A~_ij grad_j s, eq. beta
+  bt_fill(T, L, I.dpsi, -1);
+  bt_fill(T, L, I.dap, -1);
+  T.sync();
+  for (long q = T.start(); q < ng; q += T.stride()) {
+    const double ip = 1.0 / (1.0 + I.dpsi[q]);
+    const double ip2 = ip * ip;
+    I.sg[q] = (1.0 + I.dap[q]) * (ip2 * ip2 * ip2 * ip);
+  }
+  T.sync();
+  for (long q = T.start(); q < n; q += T.stride()) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+    const double Sv[3] = {I.Si[0][q], I.Si[1][q], I.Si[2][q]};
+    double f[3];
+    beta_rhs_cell<G>(L, I.Xg[0], I.Xg[1], I.Xg[2], I.sg, i, j, p, Sv, f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      I.f3[c][p] = f[c];
+      I.u3[c][p] = I.beta[c][q];
+    }
+  }
+  T.sync();
+  bt_solve_vec<G>(T, I, O, 3, hist + 3 * BATCH_HIST, smem_raw, S);
+  for (long q = T.start(); q < n; q += T.stride()) {
+    int i, j, k;
+    L.cell(q, i, j, k);
+    const long p = L.idx(i, j, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) I.beta[c][q] = I.u3[c][p];
+  }
+  T.sync();
 }
 
 // Problem idx by team T (each block holds its own copy of the descriptor).
@@ -590,6 +953,7 @@ __device__ void bt_run(const Team& T, const BatchItem* items, BatchOut* outs, do
   BatchOut& O = outs[idx];
   if (T.rank == 0 && threadIdx.x == 0) {
     O.t_start = global_ns();
+    O.ran = 0;
     for (int e = 0; e < 4; ++e) {
       O.status[e] = 0;
       O.cycles[e] = 0;
@@ -597,15 +961,13 @@ __device__ void bt_run(const Team& T, const BatchItem* items, BatchOut* outs, do
     }
   }
   __syncthreads();
-  float* sm = reinterpret_cast<float*>(smem_raw);
-  double* smd = reinterpret_cast<double*>(smem_raw + I.bc.fp64_at);
-  double* h = hist + (long)idx * 2 * BATCH_HIST;
+  double* h = hist + (long)idx * 4 * BATCH_HIST;
   if (I.geom == CART)
-    bt_problem<CART>(T, I, O, h, sm, smd, S);
+    bt_problem<CART>(T, I, O, h, smem_raw, S);
   else if (I.geom == CYL)
-    bt_problem<CYL>(T, I, O, h, sm, smd, S);
+    bt_problem<CYL>(T, I, O, h, smem_raw, S);
   else
-    bt_problem<SPH>(T, I, O, h, sm, smd, S);
+    bt_problem<SPH>(T, I, O, h, smem_raw, S);
   T.sync();
   if (T.rank == 0 && threadIdx.x == 0) O.t_end = global_ns();
 }
@@ -653,6 +1015,17 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
     if (it >= count) return;
     bt_run(T, items, outs, hist, order[it], smem_raw, I, S);
   }
+}
+
+size_t batch_smem_limit() {
+  cudaFuncAttributes a{};
+  int dev = 0, optin = 0;
+  if (cudaFuncGetAttributes(&a, k_batch_cfc) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return optin > (int)a.sharedSizeBytes ? (size_t)optin - a.sharedSizeBytes : 0;
 }
 
 int batch_clusters(size_t smem, int team) {

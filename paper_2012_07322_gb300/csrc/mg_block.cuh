@@ -110,7 +110,22 @@ __device__ void bc_residual(const BcLevel& B) {
 
 // coarse32: the coarsest correction equation in FP64 (right-hand side and
 // c converted up, zero start), the solution rounded back into e.
-template <int G, bool VEC>
+// Shared-memory scratch of the coarsest solves with a dense operator: one
+// per translation unit, so that the instantiations of bc_coarse in one
+// kernel share it.
+union BcCoarseShared {
+  struct {
+    double uq[BC_CMAT_MAX], fq[BC_CMAT_MAX], kq[BC_CMAT_MAX], dq[BC_CMAT_MAX];
+    long pq[BC_CMAT_MAX];
+    unsigned char colq[BC_CMAT_MAX];
+  } rows;
+  double fp[BC_CINV_MAX];
+};
+static __shared__ BcCoarseShared bc_coarse_sh;
+
+// DENSE_ONLY: the hierarchy is known to carry the dense coarsest operator
+// (scalar) or its inverse (vector); the sweeping fallbacks are not compiled.
+template <int G, bool VEC, bool DENSE_ONLY = false>
 __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) {
   const LevelView<double>& L = P.c64;
   constexpr int nc = VEC ? 3 : 1;
@@ -137,9 +152,12 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
     // colour is summed by the BC_SPLIT lanes of one group and folded by
     // shuffles; the cells of one colour couple only to the other colour
     constexpr int BC_SPLIT = 8;
-    __shared__ double uq[BC_CMAT_MAX], fq[BC_CMAT_MAX], kq[BC_CMAT_MAX], dq[BC_CMAT_MAX];
-    __shared__ long pq[BC_CMAT_MAX];
-    __shared__ unsigned char colq[BC_CMAT_MAX];
+    double* const uq = bc_coarse_sh.rows.uq;
+    double* const fq = bc_coarse_sh.rows.fq;
+    double* const kq = bc_coarse_sh.rows.kq;
+    double* const dq = bc_coarse_sh.rows.dq;
+    long* const pq = bc_coarse_sh.rows.pq;
+    unsigned char* const colq = bc_coarse_sh.rows.colq;
     const int n = P.cn;
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
       int i, j, k;
@@ -171,11 +189,12 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
       }
     for (int q = threadIdx.x; q < n; q += blockDim.x) cu[0][pq[q]] = uq[q];
   } else if (!VEC) {
-    coarse_scalar_body<double, G, EQ_LIN, false>(L, cu[0], cf[0], nullptr, ck, P.coarse_sweeps);
+    if constexpr (!DENSE_ONLY) coarse_scalar_body<double, G, EQ_LIN, false>(L, cu[0], cf[0], nullptr, ck,
+                                                                            P.coarse_sweeps);
   } else if (P.cinv) {
     // exact solve with the precomputed inverse of the coarsest operator:
     // unknown r = c * cells + q (q the interior flat index)
-    __shared__ double fp[BC_CINV_MAX];
+    double* const fp = bc_coarse_sh.fp;
     const int n = P.cn, cells = n / 3;
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
       int i, j, k;
@@ -204,7 +223,7 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
       }
     }
   } else {
-    coarse_vec_body<double, G>(L, cu[0], cu[1], cu[2], cf[0], cf[1], cf[2], P.coarse_sweeps);
+    if constexpr (!DENSE_ONLY) coarse_vec_body<double, G>(L, cu[0], cu[1], cu[2], cf[0], cf[1], cf[2], P.coarse_sweeps);
   }
   __syncthreads();
   #pragma unroll
@@ -224,8 +243,9 @@ __device__ void bc_coarse(const BlockCycle32& P, const BcLevel& B, double* smd) 
 // The whole cycle from level l0 of P: its right-hand side in from P.f_in,
 // the correction out to P.e_out (ghosts included); sm is the dynamic shared
 // memory, smd its FP64 area (sm + P.fp64_at bytes).  No barrier after the
-// final stores.
-template <int G, bool VEC>
+// final stores.  DENSE_ONLY: P carries the dense coarsest operator (cA) or
+// its inverse (cinv).
+template <int G, bool VEC, bool DENSE_ONLY = false>
 __device__ void bc_run(const BlockCycle32& P, float* sm, double* smd) {
   constexpr int nc = VEC ? 3 : 1;
   bc_stage_tables(P, sm);
@@ -263,7 +283,7 @@ __device__ void bc_run(const BlockCycle32& P, float* sm, double* smd) {
     }
     __syncthreads();
   }
-  bc_coarse<G, VEC>(P, bc_level(P, sm, P.nl - 1), smd);
+  bc_coarse<G, VEC, DENSE_ONLY>(P, bc_level(P, sm, P.nl - 1), smd);
   // up: Kwak prolongation of the correction, post-smooth
   for (int l = P.nl - 2; l >= 0; --l) {
     const BcLevel F = bc_level(P, sm, l), C = bc_level(P, sm, l + 1);

@@ -2400,7 +2400,7 @@ int ensure_batch_ws(mg_hierarchy* H, int count) {
     return at;
   };
   const size_t o_items = take(sizeof(BatchItem) * count), o_outs = take(sizeof(BatchOut) * count),
-               o_hist = take(sizeof(double) * 2 * BATCH_HIST * count), o_order = take(sizeof(int) * count),
+               o_hist = take(sizeof(double) * 4 * BATCH_HIST * count), o_order = take(sizeof(int) * count),
                o_next = take(sizeof(unsigned int));
   if (cudaMalloc(&H->batch_mem, off) != cudaSuccess) {
     H->batch_mem = nullptr;
@@ -2430,16 +2430,38 @@ int batch_item(mg_hierarchy* h, const mg_cfc_sources& src, const mg_cfc_fields& 
     for (int c = 0; c < 3; ++c)
       if (!src.Si[c] || !io.beta[c] || !io.X[c]) return fail(MG_ERR_INVALID, "missing vector component");
   }
+  // the first level (of at most BLOCK_CYCLE_CELLS cells) whose one-block
+  // cycle fits the batch kernel's shared memory beside its static arrays
+  const size_t limit = batch_smem_limit();
+  auto first_fit = [&](const Eq& e, BlockCycle32* out) {
+    for (int l = block_cycle_level(h, e); l < h->nlev && l <= BATCH_MAX_LEVELS; ++l) {
+      const BlockCycle32 Q = block_cycle_params(h, e, l);
+      if (Q.smem && Q.smem <= limit) {
+        *out = Q;
+        return l;
+      }
+    }
+    return -1;
+  };
   const Eq ep{MG_EQ_PSI, MG_BC_ROBIN, 0, 1, false};
   if (int est = ensure_coarse_matrix(h, MG_BC_ROBIN)) return est;
-  const int lb = block_cycle_level(h, ep);
-  if (lb >= h->nlev || lb > BATCH_MAX_LEVELS)
-    return fail(MG_ERR_INVALID, "batched solves need coarse levels that fit the one-block cycle");
-  const BlockCycle32 P = block_cycle_params(h, ep, lb);
-  if (!P.smem) return fail(MG_ERR_INVALID, "one-block cycle does not fit shared memory");
+  BlockCycle32 P{};
+  const int lb = first_fit(ep, &P);
+  if (lb < 0) return fail(MG_ERR_INVALID, "batched solves need coarse levels that fit the one-block cycle");
+  if (!P.cA) return fail(MG_ERR_INVALID, "batched solves need the dense coarsest operator (at most 64 cells)");
+  // the vector equations (X, beta) in the kernel when their levels fit
+  int vec_ok = 0, nlv = 0;
+  BlockCycle32 Pv{};
+  if (!psi_only) {
+    const Eq ex{MG_EQ_VEC, MG_BC_DIRICHLET, 0, 3, false};
+    if (int est = ensure_coarse_inverse(h, MG_BC_DIRICHLET)) return est;
+    nlv = first_fit(ex, &Pv);
+    vec_ok = nlv >= 0 && Pv.cinv;
+    if (!vec_ok) nlv = 0;
+  }
   const int m = d.accel_depth;
   if (m > 0)
-    if (int est = ensure_aa(h, 1, m, sizeof(float))) return est;
+    if (int est = ensure_aa(h, vec_ok ? 3 : 1, m, sizeof(float))) return est;
   std::memset(B, 0, sizeof(*B));
   Level& L0 = h->L[0];
   B->geom = d.geom;
@@ -2452,25 +2474,37 @@ int batch_item(mg_hierarchy* h, const mg_cfc_sources& src, const mg_cfc_fields& 
   B->stall_window = d.stall_window;
   B->psi_only = psi_only ? 1 : 0;
   B->tol = d.tol;
+  B->vec_ok = vec_ok;
+  B->nlv = nlv;
   B->v64 = with_bc(L0.v64, MG_BC_ROBIN);
-  for (int l = 0; l <= lb; ++l) {
+  for (int l = 0; l <= std::max(lb, vec_ok ? nlv : 0); ++l) {
     Level& L = h->L[l];
-    B->lv[l] = BatchLevel{with_bc(L.v32, MG_BC_ROBIN), L.e[0], L.f32[0], L.f32[1], L.k32};
+    BatchLevel& b = B->lv[l];
+    b.v = with_bc(L.v32, MG_BC_ROBIN);
+    b.e = L.e[0];
+    b.f32 = L.f32[0];
+    b.r32 = L.f32[1];
+    b.k32 = L.k32;
+    for (int c = 0; c < 3; ++c) {
+      b.e3[c] = L.e[c];
+      b.f3[c] = L.f32[c];
+    }
   }
   B->bc = P;
+  B->bcv = Pv;
   B->u = L0.u[0];
   B->f = L0.f[0];
   B->s0 = L0.s0;
   B->s1 = L0.s1;
   B->dpsi = h->dpsi;
-  if (m > 0) {
-    const long vlen = L0.ng;
-    B->x = h->aa;
-    B->fp = B->x + vlen;
-    B->gp = B->fp + vlen;
-    B->dF = reinterpret_cast<float*>(B->gp + vlen);
-    B->dG = B->dF + (long)m * vlen;
+  B->dap = h->dap;
+  B->sg = h->sg;
+  for (int c = 0; c < 3; ++c) {
+    B->u3[c] = L0.u[c];
+    B->f3[c] = L0.f[c];
+    B->Xg[c] = h->Xg[c];
   }
+  B->aa = h->aa;
   B->U = src.U;
   B->S = src.S;
   B->psi = io.psi;
@@ -2515,7 +2549,7 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   for (int i = 0; i < count; ++i) {
     if (int est = enter(hs[i])) return est;
     if (int est = batch_item(hs[i], src[i], io[i], psi_only, &items[i])) return est;
-    smem = std::max(smem, items[i].bc.smem);
+    smem = std::max(smem, std::max(items[i].bc.smem, items[i].bcv.smem));
   }
   if (int est = ensure_batch_ws(H0, count)) return est;
   // the launch runs on the first hierarchy's stream, after the work queued
@@ -2564,7 +2598,7 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   CK(cudaMemcpyAsync(outs.data(), H0->b_outs, sizeof(BatchOut) * count, cudaMemcpyDeviceToHost, st));
   std::vector<double> hist;
   if (rep) {
-    hist.resize((size_t)2 * BATCH_HIST * count);
+    hist.resize((size_t)4 * BATCH_HIST * count);
     CK(cudaMemcpyAsync(hist.data(), H0->b_hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, st));
   }
   CK(cudaStreamSynchronize(st));
@@ -2605,27 +2639,23 @@ int mg_solve_cfc_batch(mg_hierarchy* const* hs, int count, const mg_cfc_sources*
   for (int i = 0; i < count; ++i) {
     const BatchOut& o = outs[i];
     if (o.status[0] == BATCH_GENERAL) continue;
-    for (int e = 1; e <= 2; ++e)
-      if (o.status[e] && !status) status = o.status[e];
+    for (int e = 0; e < 4; ++e)
+      if ((o.ran & (1 << e)) && o.status[e] && !status) status = o.status[e];
     hs[i]->batch_cycles = o.cycles[1] + o.cycles[2];
     if (!rep) continue;
     mg_cfc_report& r = rep[i];
     std::memset(&r, 0, sizeof(r));
     const int64_t cu = cycle_updates(hs[i]);
     for (int e = 0; e < 4; ++e) {
+      if (!(o.ran & (1 << e))) continue;
       mg_solve_report& q = r.eq[e];
       q.status = o.status[e];
       q.cycles = o.cycles[e];
       q.rel = o.rel[e];
-      q.cell_updates = (int64_t)o.cycles[e] * cu;
-      const bool solved = e == 1 || (e == 2 && !psi_only && o.status[1] == MG_OK);
-      if (solved) {
-        q.nhist = std::min(o.cycles[e] + 1, MG_HIST);
-        const double* h = hist.data() + ((size_t)i * 2 + (e - 1)) * BATCH_HIST;
-        for (int c = 0; c < q.nhist; ++c) q.hist[c] = h[c];
-      } else if (!psi_only && (e == 0 || e == 3)) {
-        q.nhist = 1;  // zero right-hand side: converged at cycle 0
-      }
+      q.cell_updates = (int64_t)o.cycles[e] * cu * (e == 0 || e == 3 ? 3 : 1);
+      q.nhist = std::min(o.cycles[e] + 1, MG_HIST);
+      const double* hh = hist.data() + ((size_t)i * 4 + e) * BATCH_HIST;
+      for (int c = 0; c < q.nhist; ++c) q.hist[c] = hh[c];
     }
     r.ms = (double)(o.t_end - t0) * 1e-6;
   }

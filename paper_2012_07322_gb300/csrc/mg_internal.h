@@ -387,36 +387,42 @@ void launch_coarse_assemble_scalar(const LevelView<double>& L, double* scratch, 
 // A[col * n + r], n = 3 x coarsest cells; scratch holds 3 n ghosted fields.
 void launch_coarse_assemble_vec(const LevelView<double>& L, double* scratch, double* A, int n, cudaStream_t st);
 
-// Persistent batched xCFC solves (mg_batch.cu): one thread block takes one
-// problem at a time from a shared queue and runs its whole solve (eq. psi,
-// then eq. alpha psi, mixed precision, with mixing), every phase separated
-// by block barriers instead of kernel boundaries.
+// Persistent batched xCFC solves (mg_batch.cu): one thread block (or a
+// cluster) takes one problem at a time from a shared queue and runs its
+// whole solve (Steps 1-6 of the xCFC order, mixed precision, with mixing),
+// every phase separated by barriers instead of kernel boundaries.
 constexpr int BATCH_THREADS = 512;
 constexpr int BATCH_MAX_LEVELS = 16;
 constexpr int BATCH_HIST = 1024;  // residual history entries per equation (the reports' length)
-// Status of a problem whose momentum sources or vector fields are not all
-// zero: its X and beta equations need the vector solves, so the host runs
-// it through mg_solve_cfc after the launch.
+// Status of a problem whose X and beta equations need vector solves (its
+// momentum sources or vector guesses are not all zero) on a hierarchy whose
+// vector levels do not fit the kernel: the host runs it through
+// mg_solve_cfc after the launch.
 constexpr int BATCH_GENERAL = -1;
 struct BatchLevel {
   LevelView<float> v;  // Robin rule applied
   float *e, *f32, *r32, *k32;
+  float *e3[3], *f3[3];  // vector equations: the components' correction and right-hand side
 };
 struct BatchItem {
   int geom, nl;  // nl levels run phase by phase; level nl is the first of the one-block cycle
   int nlev, nu1, nu2, m, max_cycles, stall_window, psi_only;
+  int vec_ok, nlv;  // vector equations solvable in the kernel; their first one-block-cycle level
   double tol;
   LevelView<double> v64;                  // level 0, Robin rule applied
-  BatchLevel lv[BATCH_MAX_LEVELS + 1];    // levels 0 .. nl (HBM arrays)
+  BatchLevel lv[BATCH_MAX_LEVELS + 1];    // levels 0 .. max(nl, nlv) (HBM arrays)
   BlockCycle32 bc;                        // levels nl .. nlev - 1 (Robin rule, c present)
-  double *u, *f, *s0, *s1, *dpsi;         // level 0, ghosted
-  double *x, *fp, *gp;                    // mixing: iterate, previous f and g (ghosted layout)
-  float *dF, *dG;                         // mixing: m columns each of v64's ghosted size
+  BlockCycle32 bcv;                       // vector equations: levels nlv .. nlev - 1 (Dirichlet rule)
+  double *u, *f, *s0, *s1, *dpsi, *dap;   // level 0, ghosted
+  double *u3[3], *f3[3];                  // level 0 components (u3[0] = u, f3[0] = f)
+  double *Xg[3], *sg;                     // X with its ghosts; alpha psi^-6 (ghosted)
+  double* aa;  // mixing: iterate, previous f and g, then m columns each of dF and dG (FP32), per component
   const double *U, *S, *Si[3];            // the caller's arrays (interior order)
   double *psi, *alpha, *beta[3], *X[3];
 };
 struct BatchOut {
   int status[4], cycles[4];
+  int ran;  // bit e: equation e (X, psi, alpha psi, beta) was solved and its report is set
   double rel[4];
   unsigned long long t_start, t_end;  // %globaltimer (ns) when the problem was taken and finished
 };
@@ -427,11 +433,14 @@ constexpr int BATCH_TEAM = 8;                     // the largest cluster a launc
 constexpr int BATCH_TEAM_DEFAULT = 2;
 constexpr long BATCH_TEAM_CELLS = 16384;  // default: grids this large run on a whole cluster
 int batch_clusters(size_t smem, int team);
+// Dynamic shared memory a block of the batch kernel may take beside its
+// static arrays (0 when unknown).
+size_t batch_smem_limit();
 // One launch over count problems (items in device memory, taken in the
 // order order[0 ..]) on clusters x team blocks; problems of at least
-// team_cells cells are run by a whole cluster.  hist receives 2 x
-// BATCH_HIST residual histories per problem (eq. psi, eq. alpha psi); next
-// is a zeroed counter.  Returns 0, or 1 when the launch was refused.
+// team_cells cells are run by a whole cluster.  hist receives 4 x
+// BATCH_HIST residual histories per problem (X, psi, alpha psi, beta);
+// next is a zeroed counter.  Returns 0, or 1 when the launch was refused.
 int launch_batch_cfc(const BatchItem* items, BatchOut* outs, double* hist, const int* order, int count,
                      unsigned int* next, int clusters, int team, long team_cells, size_t smem, cudaStream_t st);
 

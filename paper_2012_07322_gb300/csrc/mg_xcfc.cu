@@ -2,6 +2,7 @@
 // divergence cleaning (Sec. 2.2).
 #include "mg_internal.h"
 #include "mg_kernels.cuh"
+#include "mg_xcfc.cuh"
 
 namespace gmg {
 
@@ -11,47 +12,9 @@ static inline dim3 grd(const LevelView<double>& L, dim3 b) {
   return dim3(cdiv(L.n0, b.x), cdiv(L.n1, b.y), cdiv(L.n2, b.z));
 }
 
-// A~_ij = 2 E_ij - 2/3 div X delta_ij, E the symmetric gradient of X in
-// orthonormal components (eq. Aij); order rr, tt, pp, rt, rp, tp.
-template <int G>
-__device__ __forceinline__ void aij_cell(const LevelView<double>& L, const double* __restrict__ a,
-                                         const double* __restrict__ b, const double* __restrict__ c, int i,
-                                         int j, long p, double A[6]) {
-  Stencil<double> s{L, p};
-  double E00, E11, E22, E01, E02, E12;
-  if (G == CART) {
-    E00 = s.d1(a, 0);
-    E11 = s.d1(b, 1);
-    E22 = s.d1(c, 2);
-    E01 = 0.5 * (s.d1(a, 1) + s.d1(b, 0));
-    E02 = 0.5 * (s.d1(a, 2) + s.d1(c, 0));
-    E12 = 0.5 * (s.d1(b, 2) + s.d1(c, 1));
-  } else if (G == CYL) {
-    const double iR = L.TI(TI_IX, i);
-    E00 = s.d1(a, 0);
-    E11 = s.d1(b, 1);
-    E22 = iR * (s.d1(c, 2) + a[p]);
-    E01 = 0.5 * (s.d1(a, 1) + s.d1(b, 0));
-    E02 = 0.5 * (iR * s.d1(a, 2) + s.d1(c, 0) - iR * c[p]);
-    E12 = 0.5 * (s.d1(c, 1) + iR * s.d1(b, 2));
-  } else {
-    const double ir = L.TI(TI_IX, i), ist = L.TJ(TJ_IS, j), cot = L.TJ(TJ_COT, j);
-    E00 = s.d1(a, 0);
-    E11 = ir * (s.d1(b, 1) + a[p]);
-    E22 = ir * (ist * s.d1(c, 2) + a[p] + cot * b[p]);
-    E01 = 0.5 * (s.d1(b, 0) - ir * b[p] + ir * s.d1(a, 1));
-    E02 = 0.5 * (ir * ist * s.d1(a, 2) + s.d1(c, 0) - ir * c[p]);
-    E12 = 0.5 * (ir * s.d1(c, 1) - ir * cot * c[p] + ir * ist * s.d1(b, 2));
-  }
-  const double div = E00 + E11 + E22;
-  A[0] = 2.0 * E00 - (2.0 / 3.0) * div;
-  A[1] = 2.0 * E11 - (2.0 / 3.0) * div;
-  A[2] = 2.0 * E22 - (2.0 / 3.0) * div;
-  A[3] = 2.0 * E01;
-  A[4] = 2.0 * E02;
-  A[5] = 2.0 * E12;
-}
-
+// A~^2 = A~_ij A~^ij with A~_ij = 2 E_ij - 2/3 div X delta_ij, E the
+// symmetric gradient of X in orthonormal components (eq. Aij); order rr,
+// tt, pp, rt, rp, tp.
 template <int G>
 __global__ void k_a2(LevelView<double> L, const double* __restrict__ a, const double* __restrict__ b,
                      const double* __restrict__ c, double* __restrict__ A2) {
@@ -107,22 +70,12 @@ __global__ void k_beta_rhs(LevelView<double> L, const double* __restrict__ a, co
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
   if (i >= L.n0 || j >= L.n1 || k >= L.n2) return;
   const long p = L.idx(i, j, k);
-  double A[6];
-  aij_cell<G>(L, a, b, c, i, j, p, A);
-  Stencil<double> st{L, p};
-  double g0 = st.d1(sg, 0), g1 = st.d1(sg, 1), g2 = st.d1(sg, 2);
-  if (G == CYL) {
-    g2 *= L.TI(TI_IX, i);
-  } else if (G == SPH) {
-    const double ir = L.TI(TI_IX, i);
-    g1 *= ir;
-    g2 *= ir * L.TJ(TJ_IS, j);
-  }
-  const double sv = sg[p];
-  const double k16 = 16.0 * PI_D * sv;
-  f0[p] = k16 * S0[p] + 2.0 * (A[0] * g0 + A[3] * g1 + A[4] * g2);
-  f1[p] = k16 * S1[p] + 2.0 * (A[3] * g0 + A[1] * g1 + A[5] * g2);
-  f2[p] = k16 * S2[p] + 2.0 * (A[4] * g0 + A[5] * g1 + A[2] * g2);
+  const double Sv[3] = {S0[p], S1[p], S2[p]};
+  double f[3];
+  beta_rhs_cell<G>(L, a, b, c, sg, i, j, p, Sv, f);
+  f0[p] = f[0];
+  f1[p] = f[1];
+  f2[p] = f[2];
 }
 
 __global__ void k_scale_into(LevelView<double> L, const double* __restrict__ src, double a,

@@ -3,9 +3,9 @@ stars solved in one launch, one thread block per problem at a time.
 
 Parity: every field within 1e-9 of the FP64 oracle at a converged relative
 residual of 1e-10 (the bar of the mixed-precision solves), X = beta = 0
-exactly, cycle counts close to the launched mixed path's.  A problem's
-result does not depend on the batch it runs in (one block runs it with the
-same instructions), and problems with momentum go through mg_solve_cfc."""
+exactly for static stars, cycle counts close to the launched mixed path's,
+for static and rotating stars.  A problem's result does not depend on the
+batch it runs in (one block runs it with the same instructions)."""
 import numpy as np
 import pytest
 
@@ -169,25 +169,59 @@ def test_batch_psi_only_and_no_mixing(mg):
 
 
 ROTATING = [("sph", [64, 32], 1.28e-3, 10.0), ("cyl", [32, 64], 9e-4, 12.0), ("sph", [32, 16], 1.6e-3, 9.0),
-            ("cyl", [64, 128], 1.1e-3, 11.0)]
+            ("cyl", [64, 128], 1.1e-3, 11.0), ("sph", [128, 64], 1.3e-3, 10.5)]
 
 
-def test_batch_hands_momentum_to_the_general_path(mg):
-    """Rotating stars in the batch (S_i != 0) are solved by mg_solve_cfc
-    after the launch, several at once from host threads: each one's fields
-    equal that call's alone bitwise; the static stars are still solved in
-    the launch."""
+def test_batch_rotating_stars_match_oracle(mg):
+    """Rotating stars (S_i != 0) in the launch with static ones: the kernel
+    solves all four equations (X and beta by the vector V-cycle), every
+    field within 1e-9 of the FP64 oracle's xCFC solve (vector components
+    scaled by the vector's maximum), residual 1e-10 in every equation."""
     ps = [problem(mg, *STARS[0])] + [problem(mg, *s, omega=0.02) for s in ROTATING] + [problem(mg, *STARS[1])]
     reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
-    assert b["persistent"] == 2 and b["general"] == len(ROTATING) and b["status"] == "ok", b
-    for s, p, r in zip(ROTATING, ps[1:], reps[1:]):
-        ref = problem(mg, *s, omega=0.02)
-        ra = mg.mg_solve_cfc(*as_tuple(ref))
-        assert r["X"]["cycles"] == ra["X"]["cycles"] > 0 and r["psi"]["cycles"] == ra["psi"]["cycles"]
-        for a, c in zip([ref["f"][0], ref["f"][1]] + ref["f"][2] + ref["f"][3],
-                        [p["f"][0], p["f"][1]] + p["f"][2] + p["f"][3]):
-            assert torch.equal(a, c)
-        ref["h"].close()
+    assert b["persistent"] == len(ps) and b["general"] == 0 and b["status"] == "ok", b
+    for p, r in zip(ps, reps):
+        U, S, Si, lo, hi = p["np"]
+        d = o.desc(p["geom"], p["n"], lo, hi, tol=1e-10, max_cycles=1000, stall_window=0, accel_depth=16)
+        shp = U.shape
+        psi, alpha = np.ones(shp), np.ones(shp)
+        beta = [np.zeros(shp) for _ in range(3)]
+        X = [np.zeros(shp) for _ in range(3)]
+        ro = o.solve_cfc(d, U, S, Si, psi, alpha, beta, X)
+        moving = any(np.abs(x).max() > 0 for x in Si)
+        for k in ("X", "psi", "alphapsi", "beta"):
+            assert ro[k]["status"] == "ok" and r[k]["status"] == "ok", (p["n"], k, r[k]["status"])
+            assert r[k]["rel"] <= 1e-10 and len(r[k]["hist"]) == r[k]["cycles"] + 1
+            if k in ("X", "beta"):
+                assert (r[k]["cycles"] > 0) == moving, (p["n"], k, r[k]["cycles"])
+        got = {"psi": host(p["f"][0]), "alpha": host(p["f"][1])}
+        errs = {"psi": relerr(got["psi"], psi), "dpsi": relerr(got["psi"] - 1, psi - 1),
+                "alpha": relerr(got["alpha"], alpha), "dalpha": relerr(got["alpha"] - 1, alpha - 1)}
+        for name, want, t in (("beta", beta, p["f"][2]), ("X", X, p["f"][3])):
+            scale = max(np.abs(x).max() for x in want)
+            errs[name] = max(np.abs(host(g) - w).max() for g, w in zip(t, want)) / (scale or 1.0)
+        assert max(errs.values()) < 1e-9, (p["geom"], p["n"], errs)
+    close(ps)
+
+
+def test_batch_rotating_stars_close_to_launched_path(mg):
+    """The same rotating stars through mg_solve_cfc: the same iteration, so
+    the fields agree within the rounding of the mixing sums and the cycle
+    counts within 15 %."""
+    ps = [problem(mg, *s, omega=0.02) for s in ROTATING]
+    reps, _ = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
+    for s, p, r in zip(ROTATING, ps, reps):
+        q = problem(mg, *s, omega=0.02)
+        ra = mg.mg_solve_cfc(*as_tuple(q))
+        for k in ("X", "psi", "alphapsi", "beta"):
+            c0, c1 = ra[k]["cycles"], r[k]["cycles"]
+            assert abs(c0 - c1) <= max(2, 0.15 * c0), (p["n"], k, c0, c1)
+        for a, c in zip([q["f"][0], q["f"][1]], [p["f"][0], p["f"][1]]):
+            assert relerr(host(c), host(a)) < 2e-9
+        for name in (2, 3):
+            scale = max(np.abs(host(x)).max() for x in q["f"][name])
+            assert max(np.abs(host(c) - host(a)).max() for a, c in zip(q["f"][name], p["f"][name])) < 2e-9 * scale
+        q["h"].close()
     close(ps)
 
 
