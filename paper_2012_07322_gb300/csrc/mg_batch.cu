@@ -35,16 +35,18 @@ static_assert(BATCH_THREADS == BC_THREADS, "the batch kernel runs the one-block 
 
 // The blocks that run one problem: a whole thread-block cluster (a team of
 // up to BATCH_TEAM blocks) for the largest grids, else one block alone.  Passes
-// stride over the team's threads; its barrier is the cluster barrier
-// (release / acquire at cluster scope, which orders the team's global
-// memory accesses too); reductions meet in rank 0's shared memory.
+// stride over the team's threads; its barrier is the cluster barrier with
+// release / acquire semantics at cluster scope (which orders the team's
+// global and shared memory accesses) and a compiler memory barrier;
+// reductions meet in rank 0's shared memory, each block writing its own row
+// there (no shared slot that a block resets while another updates it).
 struct Team {
   int rank, size;
   __device__ __forceinline__ long start() const { return (long)rank * blockDim.x + threadIdx.x; }
   __device__ __forceinline__ long stride() const { return (long)size * blockDim.x; }
   __device__ __forceinline__ void sync() const {
     if (size > 1)
-      cg::this_cluster().sync();
+      asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
     else
       __syncthreads();
   }
@@ -57,6 +59,7 @@ struct Team {
 
 struct BtShared {
   unsigned long long red[3];
+  unsigned long long cred[BATCH_TEAM][3];  // rank 0: the team's per-block maxima
   float part[BATCH_THREADS / 32][2 * AA_MAX];
   float cpart[BATCH_TEAM][2 * AA_MAX];  // rank 0: the team's per-block dot products
   float s[2 * AA_MAX];
@@ -82,6 +85,32 @@ __device__ __forceinline__ long bt_ghosted(const LevelView<T>& L) {
   return L.sy * (L.n2 + 2 * L.three);
 }
 
+// The team's maxima of three non-negative values given as abs_bits: each
+// block reduces its own, writes them into its row of rank 0's cred, and
+// every block takes the maximum over the rows.
+__device__ void bt_team_max3(const Team& T, unsigned long long (&m)[3], BtShared& S) {
+  if (threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) m[c] = warp_max_bits(m[c]);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) atomicMax(&S.red[c], m[c]);
+  __syncthreads();
+  if (threadIdx.x < 3) T.at0(S.cred[T.rank])[threadIdx.x] = S.red[threadIdx.x];
+  T.sync();
+  if (threadIdx.x < 3) {
+    const unsigned long long* rows = T.at0(&S.cred[0][0]);
+    unsigned long long v = 0ULL;
+    for (int r = 0; r < T.size; ++r) v = umax64(v, rows[3 * r + threadIdx.x]);
+    S.red[threadIdx.x] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) m[c] = S.red[c];
+  T.sync();  // rank 0's rows are rewritten only after every block has read them
+}
+
 // The FP32 passes and the mixing below copy the level views they stream
 // over out of shared memory: held by reference, every field would be read
 // back after each global store (the compiler cannot tell the two apart).
@@ -91,12 +120,9 @@ __device__ __forceinline__ long bt_ghosted(const LevelView<T>& L) {
 // cycle into lv[0].f32 and, for eq. psi, its linearisation K into lv[0].k32;
 // returns rel = max |w r| / max |w S| (NaN when a norm is not finite).
 template <int G, int KIND>
-__device__ __noinline__ double bt_norm(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
+__device__ double bt_norm(const Team& T, const BatchItem& I, const double* f, const double* s0, const double* s1,
                           BtShared& S) {
   const LevelView<double>& L = I.v64;  // passed on to the out-of-line FP64 edge rules: stays in shared memory
-  unsigned long long* red = T.at0(S.red);
-  if (T.rank == 0 && threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
-  T.sync();
   float* __restrict__ r32 = I.lv[0].f32;
   float* __restrict__ k32 = I.lv[0].k32;
   const double* __restrict__ u = I.u;
@@ -117,17 +143,9 @@ __device__ __noinline__ double bt_norm(const Team& T, const BatchItem& I, const 
     m2 = umax64(m2, abs_bits(G == CART ? Sv : w * Sv));
   }
   if (G == CART) m1 = m0;
-  m0 = warp_max_bits(m0);
-  m1 = warp_max_bits(m1);
-  m2 = warp_max_bits(m2);
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&red[0], m0);
-    atomicMax(&red[1], m1);
-    atomicMax(&red[2], m2);
-  }
-  T.sync();
-  const double num = __longlong_as_double((long long)red[1]), den = __longlong_as_double((long long)red[2]);
-  T.sync();
+  unsigned long long mm[3] = {m0, m1, m2};
+  bt_team_max3(T, mm, S);
+  const double num = __longlong_as_double((long long)mm[1]), den = __longlong_as_double((long long)mm[2]);
   if (isinf(num) || isinf(den) || isnan(num) || isnan(den)) return __longlong_as_double(0x7ff8000000000000LL);
   return num / (den > 1e-300 ? den : 1e-300);
 }
@@ -210,7 +228,7 @@ __device__ void bt_restrict_k_all(const Team& T, const BatchItem& I) {
 // level nl, the one-block cycle from there (rank 0 of a team runs it alone),
 // prolongation and post-smoothing back up.
 template <int G>
-__device__ __noinline__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* sm, double* smd) {
+__device__ void bt_vcycle(const Team& T, const BatchItem& I, bool fold, float* sm, double* smd) {
   for (int l = 0; l < I.nl; ++l) {
     bt_smooth<G>(T, I.lv[l], I.nu1);
     bt_resid_restrict<G>(T, I.lv[l], I.lv[l + 1], fold);
@@ -448,9 +466,6 @@ __device__ void bt_fill(const Team& T, const LevelView<TT>& L, TT* u, int comp) 
 template <int G>
 __device__ __noinline__ double bt_norm_vec(const Team& T, const BatchItem& I, BtShared& S) {
   const LevelView<double>& L = I.v64;
-  unsigned long long* red = T.at0(S.red);
-  if (T.rank == 0 && threadIdx.x < 3) S.red[threadIdx.x] = 0ULL;
-  T.sync();
   unsigned long long m0 = 0ULL, m1 = 0ULL, m2 = 0ULL;
   const long n = bt_cells(L);
   for (long q = T.start(); q < n; q += T.stride()) {
@@ -468,17 +483,9 @@ __device__ __noinline__ double bt_norm_vec(const Team& T, const BatchItem& I, Bt
       m2 = umax64(m2, abs_bits(w * fv));
     }
   }
-  m0 = warp_max_bits(m0);
-  m1 = warp_max_bits(m1);
-  m2 = warp_max_bits(m2);
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&red[0], m0);
-    atomicMax(&red[1], m1);
-    atomicMax(&red[2], m2);
-  }
-  T.sync();
-  const double num = __longlong_as_double((long long)red[1]), den = __longlong_as_double((long long)red[2]);
-  T.sync();
+  unsigned long long mm[3] = {m0, m1, m2};
+  bt_team_max3(T, mm, S);
+  const double num = __longlong_as_double((long long)mm[1]), den = __longlong_as_double((long long)mm[2]);
   if (isinf(num) || isinf(den) || isnan(num) || isnan(den)) return __longlong_as_double(0x7ff8000000000000LL);
   return num / (den > 1e-300 ? den : 1e-300);
 }
