@@ -70,12 +70,22 @@ __global__ void k_beta_rhs(LevelView<double> L, const double* __restrict__ a, co
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
   if (i >= L.n0 || j >= L.n1 || k >= L.n2) return;
   const long p = L.idx(i, j, k);
-  const double Sv[3] = {S0[p], S1[p], S2[p]};
-  double f[3];
-  beta_rhs_cell<G>(L, a, b, c, sg, i, j, p, Sv, f);
-  f0[p] = f[0];
-  f1[p] = f[1];
-  f2[p] = f[2];
+  double A[6];
+  aij_cell<G>(L, a, b, c, i, j, p, A);
+  Stencil<double> st{L, p};
+  double g0 = st.d1(sg, 0), g1 = st.d1(sg, 1), g2 = st.d1(sg, 2);
+  if (G == CYL) {
+    g2 *= L.TI(TI_IX, i);
+  } else if (G == SPH) {
+    const double ir = L.TI(TI_IX, i);
+    g1 *= ir;
+    g2 *= ir * L.TJ(TJ_IS, j);
+  }
+  const double sv = sg[p];
+  const double k16 = 16.0 * PI_D * sv;
+  f0[p] = k16 * S0[p] + 2.0 * (A[0] * g0 + A[3] * g1 + A[4] * g2);
+  f1[p] = k16 * S1[p] + 2.0 * (A[3] * g0 + A[1] * g1 + A[5] * g2);
+  f2[p] = k16 * S2[p] + 2.0 * (A[4] * g0 + A[5] * g1 + A[2] * g2);
 }
 
 __global__ void k_scale_into(LevelView<double> L, const double* __restrict__ src, double a,
