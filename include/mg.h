@@ -226,20 +226,22 @@ typedef struct {
  * count independent xCFC solves (the same Steps as mg_solve_cfc) in ONE
  * persistent launch: thread blocks take problems from a queue, longest
  * first (cells x the cycles of the problem's previous batched solve), and
- * run a problem's whole solve (eq. psi, the alpha-psi
- * coefficient, eq. alpha, alpha = (alpha psi) / psi), every phase of its
- * V-cycles, residuals and mixing steps separated by barriers.  Grids of
- * opts->team_cells cells and more are run by a cluster of opts->team blocks
- * together (cluster barriers), smaller ones by one block each.  Problem i is hs[i] (one hierarchy per problem, all distinct,
- * on the current device; MG_MIXED, MG_CYCLE_V, accel_depth <= 16,
- * max_cycles < MG_HIST) with src[i], io[i] as in mg_solve_cfc (device
- * pointers only: MG_HOST_POINTERS is refused).  Problems whose S_i, X or
- * beta guesses are not all zero need the vector equations (Steps 1 and 6)
- * and are solved by mg_solve_cfc after the launch (up to 16 at once, from
- * host threads, each on its hierarchy's stream); for the others X = beta
- * = 0 exactly (zero right-hand sides and guesses: cycle 0).  flags:
- * MG_CFC_PSI_ONLY.  opts may be NULL.  The launch runs on hs[0]'s stream after the work queued
- * on every hierarchy's stream; the call returns when all problems are done.
+ * run a problem's whole solve (eq. X, A~^2, eq. psi, the alpha-psi
+ * coefficient, eq. alpha, the shift source, eq. beta, alpha = (alpha psi) /
+ * psi), every phase of its V-cycles, residuals and mixing steps separated
+ * by barriers.  Grids of opts->team_cells cells and more are run by a
+ * cluster of opts->team blocks together (cluster barriers), smaller ones by
+ * one block each.  Problem i is hs[i] (one hierarchy per problem, all
+ * distinct, on the current device; MG_MIXED, MG_CYCLE_V, accel_depth <= 16,
+ * max_cycles < MG_HIST, a coarsest level of at most 64 cells) with src[i],
+ * io[i] as in mg_solve_cfc (device pointers only: MG_HOST_POINTERS is
+ * refused).  Without momentum (S_i and the X and beta guesses all zero) X
+ * = beta = 0 exactly and those equations stop at cycle 0.  A problem with
+ * momentum whose vector levels do not fit the kernel's shared memory is
+ * solved by mg_solve_cfc after the launch (up to 16 at once, from host
+ * threads, each on its hierarchy's stream).  flags: MG_CFC_PSI_ONLY.  opts
+ * may be NULL.  The launch runs on hs[0]'s stream after the work queued on
+ * every hierarchy's stream; the call returns when all problems are done.
  * rep (NULL or count entries): per-equation reports as mg_solve_cfc's, and
  * rep[i].ms = the time from the launch's first problem start to problem i's
  * end (its latency in the batch; eq[].ms are 0).  brep may be NULL.
