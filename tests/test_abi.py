@@ -187,4 +187,13 @@ def test_null_arguments_are_rejected_without_a_device():
     assert L.mg_submit(None, None, ctypes.byref(ticket)) == INV
     done = ctypes.c_int()
     assert L.mg_poll(None, 0, ctypes.byref(done), None) == INV
+    # batched solves: null arrays, an empty batch, host pointers, a cluster
+    # of 3 blocks and a null hierarchy are refused before any device work
+    hs = (ctypes.c_void_p * 1)(None)
+    srcs, ios = (mg.mg_cfc_sources * 1)(), (mg.mg_cfc_fields * 1)()
+    assert L.mg_solve_cfc_batch(None, 1, srcs, ios, 0, None, None, None) == INV
+    assert L.mg_solve_cfc_batch(hs, 0, srcs, ios, 0, None, None, None) == INV
+    assert L.mg_solve_cfc_batch(hs, 1, srcs, ios, mg.MG_HOST_POINTERS, None, None, None) == INV
+    assert L.mg_solve_cfc_batch(hs, 1, srcs, ios, 0, ctypes.byref(mg.mg_batch_opts(3, 0)), None, None) == INV
+    assert L.mg_solve_cfc_batch(hs, 1, srcs, ios, 0, None, None, None) == INV
     assert L.mg_last_error()
