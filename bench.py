@@ -263,7 +263,7 @@ def divb_measurement(mg, torch, stream, steps, precision, peak, variant="compact
 BATCH_CANDIDATES = [(2, 2, 16), (2, 2, 8), (2, 2, 0), (1, 1, 16)]
 
 
-def batch_measurement(mg, torch, count=512, slots=16, tune=True):
+def batch_measurement(mg, torch, count=512, slots=16, tune=True, rotating=False):
     """Batched solves: 512 uneven 2D static stars (seed 2; half spherical,
     half cylindrical, 32 grid shapes) submitted at once to worker slots that
     overlap their kernels on the device; hierarchies and CUDA graphs are
@@ -274,7 +274,8 @@ def batch_measurement(mg, torch, count=512, slots=16, tune=True):
     reported apart)."""
     import time
     from paper_2012_07322_gb300 import autotune, inputs
-    batch = inputs.batch_static_stars_2d(count=count, seed=2)
+    batch = (inputs.batch_static_stars_2d(count=count, seed=2, axis_ratio=0.8, omega=0.02) if rotating else
+             inputs.batch_static_stars_2d(count=count, seed=2))
     dev = lambda a: torch.from_numpy(np.array(a, copy=True)).cuda()
     items = []
     for (g, n, lo, hi, U, S, Si) in batch:
@@ -360,9 +361,11 @@ def batch_measurement(mg, torch, count=512, slots=16, tune=True):
             line["launch_tuned"] = tuned
         return line
 
-    out = {"workload": "%d uneven 2D static stars (seed 2): spherical N_r 32..256 x N_theta 16..128, cylindrical "
+    out = {"workload": "%d uneven 2D %s (seed 2): spherical N_r 32..256 x N_theta 16..128, cylindrical "
                        "N_R 32..256 x N_z 64..512, rho_c ~ U[5e-4, 2e-3], R ~ U[8, 14]; full xCFC system, mixed "
-                       "precision; worker slots (%d) and one persistent launch" % (count, slots), "cells": cells}
+                       "precision; worker slots (%d) and one persistent launch"
+                       % (count, "rotating stars (Omega = 0.02, axis ratio 0.8)" if rotating else "static stars",
+                          slots), "cells": cells}
     out["default_schedule"] = run([it[0] for it in items])
     out["persistent"] = run_persistent([it[0] for it in items])
     if tune:
@@ -875,9 +878,10 @@ def main():
     serving = None
     if not args.no_serve and world == 1:
         serving = serving_block(mg, torch, gpu_id, args.serve_sweep)
-    batch = None
+    batch = batch_rot = None
     if not args.no_batch and world == 1:
         batch = batch_measurement(mg, torch)
+        batch_rot = batch_measurement(mg, torch, tune=False, rotating=True)
 
     r0 = reps[-1]
     if rank == 0:
@@ -898,6 +902,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "fp64": fp64, "mixed_vs_fp64_err": mixed_vs_fp64,
             "divb_256": divb, "divb_256_exact": divb_exact, "serving": serving, "batch_2d": batch,
+            "batch_2d_rotating": batch_rot,
         }
         print(json.dumps(line))
     h.close()

@@ -161,11 +161,13 @@ def random_field(shape, seed, scale=1.0):
     return rng.uniform(-scale, scale, size=shape)
 
 
-def batch_static_stars_2d(count=512, seed=2):
-    """Uneven batch of 2D axisymmetric static stars (Omega = 0, spherical
-    n = 1 polytropes): half on spherical grids N_r in {32..256} x N_theta in
-    {16..128} (r <= 100), half on cylindrical grids N_R in {32..256} x N_z in
-    {64..512} (R <= 100, |z| <= 100); rho_c ~ U[5e-4, 2e-3], R ~ U[8, 14].
+def batch_static_stars_2d(count=512, seed=2, axis_ratio=1.0, omega=0.0):
+    """Uneven batch of 2D axisymmetric stars, static by default (Omega = 0,
+    spherical n = 1 polytropes): half on spherical grids N_r in {32..256} x
+    N_theta in {16..128} (r <= 100), half on cylindrical grids N_R in
+    {32..256} x N_z in {64..512} (R <= 100, |z| <= 100); rho_c ~ U[5e-4,
+    2e-3], R ~ U[8, 14].  With omega != 0 the same grids and draws carry
+    uniformly rotating stars of the given axis ratio (momentum sources S_i).
     Returns (geom, n, lo, hi, U, S, Si) tuples."""
     rng = np.random.default_rng(seed)
     out = []
@@ -173,10 +175,10 @@ def batch_static_stars_2d(count=512, seed=2):
         rho_c, R = rng.uniform(5e-4, 2e-3), rng.uniform(8.0, 14.0)
         if q % 2 == 0:
             n = [int(rng.choice([32, 64, 128, 256])), int(rng.choice([16, 32, 64, 128]))]
-            U, S, Si = rotating_polytrope_sph2d(n[0], n[1], 100.0, rho_c, R, axis_ratio=1.0, omega=0.0)
+            U, S, Si = rotating_polytrope_sph2d(n[0], n[1], 100.0, rho_c, R, axis_ratio=axis_ratio, omega=omega)
             out.append(("sph", n, [0.0, 0.0], [100.0, np.pi], U, S, Si))
         else:
             n = [int(rng.choice([32, 64, 128, 256])), int(rng.choice([64, 128, 256, 512]))]
-            U, S, Si = rotating_polytrope_cyl(n, 100.0, rho_c, R, axis_ratio=1.0, omega=0.0)
+            U, S, Si = rotating_polytrope_cyl(n, 100.0, rho_c, R, axis_ratio=axis_ratio, omega=omega)
             out.append(("cyl", n, [0.0, -100.0], [100.0, 100.0], U, S, Si))
     return out
