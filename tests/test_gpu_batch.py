@@ -225,6 +225,47 @@ def test_batch_rotating_stars_close_to_launched_path(mg):
     close(ps)
 
 
+def test_batch_3d_grids_match_oracle(mg):
+    """3D grids in the launch (the kernel's passes are dimension-generic):
+    rotating stars on a spherical 32 x 16 x 16 and a cylindrical 16 x 32 x 8
+    grid beside a 2D static star, every field within 1e-9 of the oracle."""
+    cases = [("sph", [32, 16, 16], [0.0, 0.0, 0.0], [100.0, PI, 2 * PI]),
+             ("cyl", [16, 32, 8], [0.0, -100.0, 0.0], [100.0, 100.0, 2 * PI])]
+    ps, srcs = [], []
+    for geom, n, lo, hi in cases:
+        if geom == "sph":
+            U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
+        else:
+            U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0)
+        d = mg.grid_desc(geom, n, lo, hi, precision="mixed", tol=1e-10, max_cycles=800, accel_depth=16,
+                         stall_window=0)
+        shp = U.shape
+        f = (torch.ones(shp, dtype=torch.float64, device="cuda"), torch.ones(shp, dtype=torch.float64, device="cuda"),
+             [torch.zeros(shp, dtype=torch.float64, device="cuda") for _ in range(3)],
+             [torch.zeros(shp, dtype=torch.float64, device="cuda") for _ in range(3)])
+        ps.append({"h": mg.Hierarchy(d), "dev": (dev(U), dev(S), [dev(x) for x in Si]), "f": f})
+        srcs.append((geom, n, lo, hi, U, S, Si))
+    ps.append(problem(mg, *STARS[2]))
+    reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
+    assert b["status"] == "ok" and b["persistent"] == 3 and b["general"] == 0, b
+    for p, r, (geom, n, lo, hi, U, S, Si) in zip(ps, reps, srcs):
+        d = o.desc(geom, n, lo, hi, tol=1e-10, max_cycles=1000, stall_window=0, accel_depth=16)
+        shp = U.shape
+        psi, alpha = np.ones(shp), np.ones(shp)
+        beta = [np.zeros(shp) for _ in range(3)]
+        X = [np.zeros(shp) for _ in range(3)]
+        ro = o.solve_cfc(d, U, S, Si, psi, alpha, beta, X)
+        for k in ("X", "psi", "alphapsi", "beta"):
+            assert ro[k]["status"] == "ok" and r[k]["status"] == "ok", (n, k, r[k]["status"])
+            assert r[k]["rel"] <= 1e-10 and r[k]["cycles"] > 0
+        errs = {"psi": relerr(host(p["f"][0]) - 1, psi - 1), "alpha": relerr(host(p["f"][1]) - 1, alpha - 1)}
+        for name, want, t in (("beta", beta, p["f"][2]), ("X", X, p["f"][3])):
+            scale = max(np.abs(x).max() for x in want)
+            errs[name] = max(np.abs(host(g) - w).max() for g, w in zip(t, want)) / (scale or 1.0)
+        assert max(errs.values()) < 1e-9, (geom, n, errs)
+    close(ps)
+
+
 @pytest.mark.parametrize("team,team_cells", [(1, 0), (4, 8192), (8, 8192)])
 def test_batch_launch_shapes(mg, team, team_cells):
     """Single blocks only, and clusters of 4 and 8 blocks taking every grid
