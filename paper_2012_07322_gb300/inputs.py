@@ -117,6 +117,31 @@ def rotating_polytrope_cyl(n, extent=100.0, rho_c=1.28e-3, R=10.0, axis_ratio=0.
             [zero.copy(), zero.copy(), np.ascontiguousarray(Sphi)])
 
 
+def rotating_polytrope_cart3d(n=(32, 32, 32), extent=30.0, rho_c=1.28e-3, R=10.0, axis_ratio=0.8, omega=0.02):
+    """The rotating star of :func:`rotating_polytrope_sph3d` on a 3D
+    Cartesian grid [-extent, extent]^3, shaped (n_z, n_y, n_x); velocity
+    omega (-y, x, 0), momentum components (x, y, z)."""
+    x, y, z = cell_centres(list(n), [-extent] * 3, [extent] * 3)
+    xx = x[None, None, :]
+    yy = y[None, :, None]
+    zz = z[:, None, None]
+    varpi = np.sqrt(xx * xx + yy * yy)
+    xi = np.sqrt((varpi / R) ** 2 + (zz / (axis_ratio * R)) ** 2)
+    rho = _lane_emden_n1(xi, rho_c)
+    v = omega * varpi
+    W2 = 1.0 / (1.0 - v * v)
+    p = K_POLY * rho * rho
+    h = 1.0 + 2.0 * K_POLY * rho
+    shp = (n[2], n[1], n[0])
+    a = rho * h * W2
+    U = np.broadcast_to(a - p, shp)
+    S = np.broadcast_to(a * v * v + 3.0 * p, shp)
+    Sx = np.broadcast_to(-a * omega * yy, shp)
+    Sy = np.broadcast_to(a * omega * xx, shp)
+    return (np.ascontiguousarray(U), np.ascontiguousarray(S),
+            [np.ascontiguousarray(Sx), np.ascontiguousarray(Sy), np.zeros(shp)])
+
+
 def divb_field(n=256, n_modes=32, k_max=8, noise=1e-3, seed_modes=0, seed_noise=1):
     """Magnetic field on the Cartesian cube [-1, 1]^3 (n^3 cells).
 

@@ -226,17 +226,21 @@ def test_batch_rotating_stars_close_to_launched_path(mg):
 
 
 def test_batch_3d_grids_match_oracle(mg):
-    """3D grids in the launch (the kernel's passes are dimension-generic):
-    rotating stars on a spherical 32 x 16 x 16 and a cylindrical 16 x 32 x 8
-    grid beside a 2D static star, every field within 1e-9 of the oracle."""
+    """3D grids in the launch (the kernel's passes are dimension- and
+    geometry-generic): rotating stars on a spherical 32 x 16 x 16, a
+    cylindrical 16 x 32 x 8 and a Cartesian 16^3 grid beside a 2D static
+    star, every field within 1e-9 of the oracle."""
     cases = [("sph", [32, 16, 16], [0.0, 0.0, 0.0], [100.0, PI, 2 * PI]),
-             ("cyl", [16, 32, 8], [0.0, -100.0, 0.0], [100.0, 100.0, 2 * PI])]
+             ("cyl", [16, 32, 8], [0.0, -100.0, 0.0], [100.0, 100.0, 2 * PI]),
+             ("cart", [16, 16, 16], [-30.0] * 3, [30.0] * 3)]
     ps, srcs = [], []
     for geom, n, lo, hi in cases:
         if geom == "sph":
             U, S, Si = inputs.rotating_polytrope_sph3d(tuple(n), 100.0)
-        else:
+        elif geom == "cyl":
             U, S, Si = inputs.rotating_polytrope_cyl(n, 100.0)
+        else:
+            U, S, Si = inputs.rotating_polytrope_cart3d(tuple(n), 30.0)
         d = mg.grid_desc(geom, n, lo, hi, precision="mixed", tol=1e-10, max_cycles=800, accel_depth=16,
                          stall_window=0)
         shp = U.shape
@@ -247,7 +251,7 @@ def test_batch_3d_grids_match_oracle(mg):
         srcs.append((geom, n, lo, hi, U, S, Si))
     ps.append(problem(mg, *STARS[2]))
     reps, b = mg.mg_solve_cfc_batch([as_tuple(p) for p in ps])
-    assert b["status"] == "ok" and b["persistent"] == 3 and b["general"] == 0, b
+    assert b["status"] == "ok" and b["persistent"] == 4 and b["general"] == 0, b
     for p, r, (geom, n, lo, hi, U, S, Si) in zip(ps, reps, srcs):
         d = o.desc(geom, n, lo, hi, tol=1e-10, max_cycles=1000, stall_window=0, accel_depth=16)
         shp = U.shape

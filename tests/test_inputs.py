@@ -62,3 +62,19 @@ def test_magnetic_field_seeds_and_noise():
     # another mode seed gives another field
     B3 = inputs.divb_field(n=n, seed_modes=5)
     assert np.abs(B3[0] - B1[0]).max() > 0.1 * np.abs(B1[0]).max()
+
+
+def test_cartesian_rotating_star_symmetries():
+    """The Cartesian rotating star: U and S even in x, y and z, the momentum
+    omega (-y, x, 0) a rigid rotation about z (S_x odd in y and even in x,
+    S_y the reverse, S_z = 0), and the same U as the spherical generator at
+    the centre."""
+    U, S, Si = inputs.rotating_polytrope_cart3d((16, 16, 16), 30.0)
+    for A in (U, S):
+        for ax in range(3):
+            assert np.allclose(A, np.flip(A, axis=ax))
+    assert np.allclose(Si[0], -np.flip(Si[0], axis=1)) and np.allclose(Si[0], np.flip(Si[0], axis=2))
+    assert np.allclose(Si[1], -np.flip(Si[1], axis=2)) and np.allclose(Si[1], np.flip(Si[1], axis=1))
+    assert (Si[2] == 0).all() and np.abs(Si[0]).max() > 0
+    Us, _, _ = inputs.rotating_polytrope_sph3d((64, 32, 4), 100.0)
+    assert U.max() <= Us.max() * (1 + 1e-12)
